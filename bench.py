@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark: GPCG solves/s on the single large QP (2-D 1600x1600, n = 2.56e6,
+5-point weighted-Laplacian Hessian with shift 1e-3, b ~ U[-1,1], two-sided
+bounds l ~ U[-0.5,0], u ~ U[0,0.5], seed 2), stopping at
+||grad_Omega q(x)|| <= 1e-6 ||grad_Omega q(x0)||.
+
+One step = one complete GPCG solve (every pass of the hot path) of that QP.
+`value` is the mixed-precision (FP32-stream / FP64-reduce) rate; the plain
+FP64 path is reported beside it.  Inputs are resident in HBM before the
+timed region; `e2e` repeats the measurement through the C ABI with pinned
+host buffers (create + solve + result per step).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own replica (weak scaling, no collective
+in the data path; a barrier brackets the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gpcg_inputs as gi  # noqa: E402
+
+WORKLOAD = "single_large_2d_1600x1600"
+METRIC = "GPCG solves/s (single large QP, 1600x1600 5-point, tau_rel 1e-6)"
+TAU_REL = 1e-6
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.file:
+            return None
+        try:
+            with open(self.file.name) as f:
+                rows = [r.split(",") for r in f.read().strip().splitlines() if r.strip()]
+            os.unlink(self.file.name)
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available()
+                     else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(qp, budget_s: float = 25.0):
+    """The oracle as it stands, on one host core: full solves of the workload
+    until about budget_s seconds have passed (at least one)."""
+    import oracle
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        r = oracle.solve(qp, tau_rel=TAU_REL)
+        k += 1
+        if time.perf_counter() - t0 > budget_s * 0.5 or k >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} complete FP64 solve(s) of the 1600x1600 workload on one core",
+            "status": r.status}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    qp = gi.single_large()
+    import oracle
+    oracle.build()
+    times = []
+    for _ in range(args.warmup):
+        oracle.solve(qp, tau_rel=TAU_REL)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.solve(qp, tau_rel=TAU_REL)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": qp.n, "tau_rel": TAU_REL},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": "one complete FP64 solve of the 1600x1600 workload "
+                                       "per step, one core"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "status": r.status}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    import paper_cs_0101018_gb300 as g
+    g.load()
+    qp = gi.single_large()
+    stream = torch.cuda.Stream()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_in = {k: dev(getattr(qp, k)) for k in ("diag", "cx", "cy", "b", "l", "u")}
+    torch.cuda.synchronize()
+    prob = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, **d_in)
+    hbm_peak, peak_kind = _peaks()
+
+    def timed(precision, steps, warmup):
+        opts = g.default_options(tau_rel=TAU_REL, precision=precision, stream=stream)
+        for _ in range(warmup):
+            g.gpcg_solve(prob, opts)
+        torch.cuda.synchronize()
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        with Clocks(local) as clk:
+            t_wall = time.perf_counter()
+            for e0, e1 in ev:
+                e0.record(stream)
+                g.gpcg_solve(prob, opts)
+                e1.record(stream)
+                e1.synchronize()
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall
+        _barrier(ws)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        _, st = g.gpcg_result(prob)
+        return ms, st, clk.summary(), t_wall
+
+    # mixed precision (headline) and plain FP64
+    ms_mx, st_mx, clk_mx, wall_mx = timed(g.MIXED, args.steps, args.warmup)
+    ms_64, st_64, clk_64, wall_64 = timed(g.FP64, args.steps, args.warmup)
+
+    tot_mx = _max_over_ranks(ws, sum(ms_mx) / 1000.0)
+    tot_64 = _max_over_ranks(ws, sum(ms_64) / 1000.0)
+    value = ws * args.steps / tot_mx
+    value_64 = ws * args.steps / tot_64
+
+    def roof(ms, st):
+        t = (sum(ms) / len(ms)) / 1000.0
+        per_launch_t = t / max(1, st["launches"])
+        per_launch_b = st["alg_bytes"] / max(1, st["passes"])
+        ach = st["alg_bytes"] / t / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "gpcg::pass_kernel", "alg_bytes_per_launch": per_launch_b,
+                "launch_ms": 1000 * per_launch_t}
+
+    roof_mx, roof_64 = roof(ms_mx, st_mx), roof(ms_64, st_64)
+
+    # masked product alone (the CG matrix-vector kernel), on the final free set
+    spmv = {}
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        g.gpcg_solve(prob, g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream))
+        ms1, by = g.gpcg_time_masked_spmv(prob, prec, reps=50, stream=stream)
+        gbs = by / (ms1 / 1000.0) / 1e9
+        spmv[name] = {"GB/s": gbs, "frac": gbs / hbm_peak, "ms_per_launch": ms1,
+                      "alg_bytes_per_launch": by}
+
+    # end to end through the C ABI from pinned host buffers
+    pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(qp, k))).pin_memory()
+           for k in ("diag", "cx", "cy", "b", "l", "u")}
+    xh = torch.empty(qp.n, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 8 for t in pin.values())
+    d2h = xh.numel() * 8
+    opts = g.default_options(tau_rel=TAU_REL, precision=g.MIXED, stream=stream)
+    for _ in range(1):
+        p2 = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, **pin)
+        g.gpcg_solve(p2, opts)
+        g.gpcg_result(p2, xh)
+        del p2
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        p2 = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, **pin)
+        g.gpcg_solve(p2, opts)
+        g.gpcg_result(p2, xh)
+        del p2
+    torch.cuda.synchronize()
+    e2e_t = _max_over_ranks(ws, time.perf_counter() - t0)
+    e2e = {"value": ws * e_steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline(qp) if ws == 1 else None
+    lat = sorted(ms_mx)
+    p = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(ms_mx) / len(ms_mx), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-stream/f64-reduce", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": qp.n, "grid": [qp.nx, qp.ny], "tau_rel": TAU_REL,
+                   "parallelism": f"replicas{ws}",
+                   "l2": "working set 0.43 GB > 129 MB L2 (inputs larger than L2)"},
+        "p50_ms": p(0.5), "p99_ms": p(0.99),
+        "fp64": {"value": value_64, "unit": "solves/s",
+                 "ms_per_step": sum(ms_64) / len(ms_64), "roofline": roof_64,
+                 "clocks": clk_64,
+                 "solve": {k: st_64[k] for k in ("outer_iters", "gp_iters", "cg_iters",
+                                                 "ls_trials", "passes", "pg_norm", "tau")}},
+        "mixed_over_fp64": value / value_64,
+        "roofline": roof_mx,
+        "spmv": spmv,
+        "solve": {k: st_mx[k] for k in ("outer_iters", "gp_iters", "cg_iters", "ls_trials",
+                                        "refine_cg_iters", "passes", "pg_norm", "tau",
+                                        "n_active", "n_free")},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * st_mx["launches"]),
+        "clocks": clk_mx,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

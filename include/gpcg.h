@@ -1,0 +1,218 @@
+/*
+ * gpcg.h -- C ABI of the GB300 GPCG library (libgpcg.so).
+ *
+ * GPCG solves the bound-constrained strictly convex quadratic program
+ *
+ *     min { q(x) = 1/2 x'Ax + b'x + c  :  l <= x <= u }
+ *
+ * (Benson, McInnes & More, "GPCG: a case study in the performance and
+ * scalability of optimization algorithms", Sec. 2, Eq. def_bqp, def_bounds,
+ * def-quadratic) by alternating gradient projection with conjugate gradients
+ * on the face of the current iterate (Sec. 3, Algorithm GPCG).  A is a
+ * symmetric positive definite 2-D 5-point or 3-D 7-point stencil.  Every
+ * numerical step runs in the library's own CUDA kernels on the current
+ * device; the library never falls back to the CPU.
+ *
+ * Conventions for every entry point:
+ *   - Pointers to arrays may be host or device pointers (the library asks the
+ *     CUDA runtime which); arrays are dense, contiguous, FP64, indexed
+ *     i = ix + nx*(iy + ny*iz) with ix fastest.  Input arrays are only read,
+ *     and only during the call; the library keeps its own device copies.
+ *   - Every call returns a gpcg_status; nothing is thrown across the ABI.
+ *     gpcg_last_error() gives a one-line description of the latest failure
+ *     on the calling thread.
+ *   - Handles are owned by the library and released only by the matching
+ *     _destroy call.  A handle must not be used from two threads at once;
+ *     distinct handles may be used concurrently.
+ *   - Infinite bounds are written as -INFINITY / +INFINITY.
+ *   - n = nx*ny*nz must be below 2^31 and each of nx, ny, nz below 2^31.
+ */
+#ifndef GPCG_H
+#define GPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPCG_OK = 0,
+    GPCG_ERR_ARG = 1,         /* invalid argument (NULL, bad size, NaN, diag <= 0, ...) */
+    GPCG_ERR_INFEASIBLE = 2,  /* some l_i > u_i, l_i = +inf or u_i = -inf: Omega is empty */
+    GPCG_ERR_NUMERIC = 3,     /* a curvature <p,Ap> <= 0 (A not SPD) or a non-finite value */
+    GPCG_ERR_OOM = 4,         /* device allocation failed */
+    GPCG_ERR_BUDGET = 5,      /* request larger than the server's HBM budget */
+    GPCG_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+    GPCG_ERR_MAXIT = 7,       /* max_outer iterates without ||grad_Omega q|| <= tau */
+    GPCG_ERR_LINESEARCH = 8,  /* max_ls halvings without sufficient decrease */
+    GPCG_ERR_TIMEOUT = 9,     /* the host-side pass cap was reached */
+    GPCG_ERR_PENDING = 10,    /* result not available yet (solve not run / still running) */
+    GPCG_ERR_CANCELLED = 11   /* request cancelled before it finished */
+} gpcg_status;
+
+typedef enum {
+    GPCG_FP64 = 0,   /* every vector, coefficient and reduction in FP64 */
+    GPCG_MIXED = 1   /* CG streams FP32 coefficients and vectors with FP64
+                        reductions; gradient projection, projected search,
+                        q(x), the active/binding sets and the termination test
+                        stay FP64; a closing FP64 CG phase refines the result */
+} gpcg_precision;
+
+/* The Hessian as stencil bands (Sec. 2: A symmetric positive definite).
+ * diag[i] = A(i,i); cx[i] = A(i,i+1); cy[i] = A(i,i+nx); cz[i] = A(i,i+nx*ny)
+ * (dim == 3 only).  The entry of the last point along an axis (ix = nx-1 for
+ * cx, ...) is ignored.  Each array holds n values. */
+typedef struct {
+    int dim;               /* 2 or 3 */
+    int64_t nx, ny, nz;    /* grid size; nz must be 1 when dim == 2 */
+    const double* diag;
+    const double* cx;
+    const double* cy;
+    const double* cz;      /* NULL when dim == 2 */
+} gpcg_stencil;
+
+typedef struct gpcg_problem gpcg_problem;
+
+/* Create a problem (Sec. 4: the TaoSetQuadraticFunction / TaoSetVariableBounds
+ * pair).  Copies A, b, l, u to library-owned device memory and checks them:
+ * sizes, no NaN, finite couplings, diag > 0, l <= u, l < +inf, u > -inf.
+ * l == NULL means l = -inf everywhere, u == NULL means u = +inf everywhere.
+ * On success *out receives the handle; on failure *out is set to NULL.
+ * Errors: GPCG_ERR_ARG, GPCG_ERR_INFEASIBLE, GPCG_ERR_OOM, GPCG_ERR_CUDA. */
+gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b, const double* l,
+                                const double* u, double c, gpcg_problem** out);
+
+/* Release every resource of the handle (NULL is allowed). */
+void gpcg_problem_destroy(gpcg_problem* p);
+
+/* Problem size n = nx*ny*nz (0 for NULL). */
+int64_t gpcg_problem_size(const gpcg_problem* p);
+
+/* Solver options.  Defaults come from gpcg_default_options():
+ * tau_abs 0, tau_rel 1e-8 (stop when ||grad_Omega q(x)|| <= max(tau_abs,
+ * tau_rel*||grad_Omega q(x0)||), Eq. bqp_approximate_sol, 2-norm);
+ * eta1 0.1 (Eq. pgstop2), eta2 0.05 (Eq. cgstop1) -- the values of Sec. 5;
+ * mu 0.01 (Eq. gplsstop / cglsstop2, the paper only asks mu in (0,1/2));
+ * eta2_shrink 0.1 and eta2_floor 1e-12 (the reduction of eta2 when Eq.
+ * cgstop3 holds, unspecified in the paper); max_outer 10000, max_gp 50,
+ * max_cg 10000, max_ls 60; precision GPCG_FP64; refine 1; x0 NULL (start at
+ * P[l], falling back to u then 0 where a bound is infinite: Sec. 5 uses
+ * x0 = l); cuda_stream NULL (the legacy default stream); lambda_min 0. */
+typedef struct {
+    double tau_abs, tau_rel;
+    double eta1, eta2, mu, eta2_shrink, eta2_floor;
+    int max_outer, max_gp, max_cg, max_ls;
+    int precision;          /* gpcg_precision */
+    int refine;             /* GPCG_MIXED: run the closing FP64 CG phase */
+    const double* x0;       /* optional start (host or device, n values), projected onto Omega */
+    void* cuda_stream;      /* cudaStream_t the solve is ordered on */
+    double lambda_min;      /* optional lower bound on lambda_min(A), for err_bound */
+} gpcg_options;
+
+void gpcg_default_options(gpcg_options* o);
+
+/* Run GPCG (Sec. 3, Algorithm GPCG) on one problem; blocks until it ends.
+ * Returns the solve's status (GPCG_OK when the tolerance was met). */
+gpcg_status gpcg_solve(gpcg_problem* p, const gpcg_options* opt);
+
+/* Run GPCG on `count` independent problems at once: every pass of the engine
+ * advances all of them in one kernel launch (per-instance tile table).  The
+ * result of each problem is bit-identical to solving it alone with the same
+ * options.  Returns GPCG_OK if every solve met its tolerance, else the first
+ * failing status; per-problem statuses are in gpcg_result(). */
+gpcg_status gpcg_solve_batch(gpcg_problem* const* probs, int count, const gpcg_options* opt);
+
+typedef struct {
+    double q;               /* q(x) */
+    double pg_norm;         /* ||grad_Omega q(x)||_2 (Eq. proj-gradient) */
+    double pg_norm0;        /* ||grad_Omega q(x0)||_2 */
+    double tau;             /* the tolerance in force */
+    int64_t n_active, n_binding, n_free;   /* |A(x)|, |B(x)|, n - |A(x)| (Sec. 2) */
+    int outer_iters, gp_iters, cg_iters, ls_trials;
+    int refine_cg_iters;    /* CG iterations of the closing FP64 phase (GPCG_MIXED) */
+    int passes;             /* engine passes (one HBM sweep each) */
+    int status;             /* gpcg_status of the solve */
+    double err_bound;       /* ||x - x*|| <= pg_norm / lambda_min when lambda_min > 0, else -1 */
+    double alg_bytes;       /* algorithmic HBM bytes of all passes of the solve (the bytes
+                               each pass must read and write once, summed) */
+    int64_t launches;       /* kernel launches of the engine for the latest solve (passes
+                               plus the empty launches of the final loop iteration); for a
+                               batch, the launches of the whole batch */
+} gpcg_stats;
+
+/* Copy the latest solution (n values, host or device x_out; NULL skips it)
+ * and statistics (NULL skips them).  GPCG_ERR_PENDING before the first
+ * solve. */
+gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats);
+
+/* y = Z Z' A Z Z' p on the free set given by free_mask (one byte per point,
+ * nonzero = free): the reduced Hessian A_k = Z_k' A Z_k of Eq. cg2 applied in
+ * place, without extracting A_k (the "alternative technique" of Sec. 4).  This
+ * runs the same kernel as the CG phase's matrix-vector product.  precision
+ * GPCG_MIXED streams FP32 coefficients and vectors (p is rounded to FP32,
+ * y is FP32 widened to FP64).  *pAp (optional) receives <p_F, (A_k p)_F>
+ * accumulated in FP64.  Arrays: n values each, host or device. */
+gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask, const double* pv,
+                             double* y, double* pAp, int precision, void* cuda_stream);
+
+/* Time `reps` back-to-back launches of the masked matrix-vector kernel on
+ * the problem's free set after the latest solve (or all points free before
+ * any solve), with CUDA events on the given stream.  *ms_per_launch receives
+ * the mean launch duration and *bytes_per_launch the algorithmic bytes moved
+ * per launch (bands + p read once + Ap written once + mask bits). */
+gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, void* cuda_stream,
+                                  double* ms_per_launch, double* bytes_per_launch);
+
+/* ---- continuous-batching server --------------------------------------- */
+
+typedef struct gpcg_server gpcg_server;
+
+/* A server owns one engine whose passes advance every admitted solve in one
+ * kernel launch.  Requests are admitted when their device footprint fits in
+ * hbm_budget bytes (and fewer than max_live are running); finished solves are
+ * retired and their memory released while others keep running.
+ * Errors: GPCG_ERR_ARG, GPCG_ERR_OOM, GPCG_ERR_CUDA. */
+gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const gpcg_options* opt,
+                               gpcg_server** out);
+
+/* Queue one request.  The arrays (host pointers) must stay valid until the
+ * request completes; x_out (host, n values) receives the solution.  *ticket
+ * identifies the request.  Errors: GPCG_ERR_ARG, GPCG_ERR_BUDGET (the request
+ * alone exceeds the budget). */
+gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A, const double* b,
+                               const double* l, const double* u, double c, double* x_out,
+                               int64_t* ticket);
+
+/* Advance the server: admit what fits, run up to `passes` engine passes,
+ * retire what finished.  Returns after the passes (non-blocking w.r.t. new
+ * submissions). */
+gpcg_status gpcg_server_step(gpcg_server* s, int passes);
+
+/* 1 if the ticket finished (its x_out and stats are final), else 0. */
+int gpcg_server_done(gpcg_server* s, int64_t ticket);
+
+/* Statistics of a finished ticket, plus its latency (submit to retirement,
+ * seconds).  GPCG_ERR_PENDING while it runs. */
+gpcg_status gpcg_server_stats(gpcg_server* s, int64_t ticket, gpcg_stats* st,
+                              double* latency_s);
+
+/* Cancel a queued or running request (its x_out is not written). */
+gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket);
+
+/* Counts of queued, running and finished requests. */
+void gpcg_server_counts(gpcg_server* s, int* queued, int* running, int* finished);
+
+void gpcg_server_destroy(gpcg_server* s);
+
+/* One-line description of the latest error on the calling thread. */
+const char* gpcg_last_error(void);
+
+/* Library version string. */
+const char* gpcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,96 @@
+// engine.h -- data shared by the host driver and the device passes of the
+// GPCG engine.  Internal to libgpcg.so (the public ABI is include/gpcg.h).
+//
+// Layout in device memory (one problem):
+//   every per-point array is stored with a padded row pitch px (a multiple of
+//   8 elements, so each row starts on a 64-byte boundary for FP64 and 32-byte
+//   for FP32); point (ix, iy, iz) lives at ix + px*(iy + ny*iz).  Pad columns
+//   ix >= nx hold zeros and are never read as neighbours.
+//   The free set is a bitmask: bit (ix & 31) of word (iy + ny*iz)*mw + ix/32
+//   is 1 when the point is free, mw = ceil(px/32).
+//
+// One engine pass = one launch of the pass kernel over the tile table of all
+// live instances.  Each CTA processes one 64 x 32 tile of one instance, writes
+// its partial sums to a fixed slot, and the last CTA of an instance to finish
+// reduces that instance's partials in a fixed order and advances the
+// instance's GPCG state machine (Sec. 3, Algorithm GPCG).  Results therefore
+// depend only on the instance itself, never on what else shares the launch.
+#pragma once
+
+#include <cstdint>
+
+namespace gpcg {
+
+constexpr int kTX = 64;          // tile width (columns): 32 lanes x 2 points
+constexpr int kRY = 4;           // rows per warp
+constexpr int kWarps = 8;        // warps per CTA
+constexpr int kTY = kRY * kWarps;  // tile height (rows)
+constexpr int kThreads = 32 * kWarps;
+constexpr int kNRed = 8;         // partial sums per tile
+
+enum Pass : int {
+  P_NONE = 0,
+  P_START = 1,     // x = P[x0]
+  P_CENSUS = 2,    // g = Ax + b, free mask, |A|, |B|, ||pg||^2, q
+  P_GP_ALPHA = 3,  // <pg,pg>, <pg, A pg> for alpha0 (Eq. bqpls)
+  P_TRIAL = 4,     // trial point P[x + alpha*dir] with gradient and census
+  P_CG_B = 5,      // p = -r + beta p; Ap = A_FF p; <p, Ap>
+  P_CG_A = 6,      // w += alpha p; r += alpha Ap; ||r||^2
+};
+
+enum Dir : int { D_NEG_G = 0, D_W64 = 1, D_W32 = 2, D_ZERO = 3 };
+
+// Status values mirror gpcg_status.
+enum Status : int {
+  S_OK = 0,
+  S_NUMERIC = 3,
+  S_MAXIT = 7,
+  S_LINESEARCH = 8,
+  S_TIMEOUT = 9,
+  S_RUNNING = 10,
+};
+
+struct Opts {
+  double tau_abs, tau_rel, eta1, eta2, mu, eta2_shrink, eta2_floor, eta2_refine;
+  double c;
+  int max_outer, max_gp, max_cg, max_ls;
+  int mixed, refine, use_x0, pad;
+};
+
+// Mutable per-instance state, owned by the finalizer of each pass.
+struct Ctl {
+  int pass, status, done, cur, pcur, cg32, first_cg, dir;
+  int trial_gp, refining, refined, continue_cg, hold, pad0;
+  int outer_iters, gp_j, ls_i, cg_j, gp_iters, cg_iters, ls_trials, refine_cg_iters;
+  int passes, pad1;
+  unsigned arrive, pad2;
+  double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
+  double pg2, nA, nB, xgb, gF2;  // census of the current iterate
+  double alg_bytes;              // algorithmic HBM bytes of all passes so far
+  double red[kNRed];             // reduced sums of the latest pass
+};
+
+struct DevInst {
+  int dim, nx, ny, nz, px, mw, tiles_x, tiles_y, n_tiles, kc;
+  long long n, plane;
+  double* part;            // [n_tiles][kNRed] tile partial sums of this instance
+  const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
+  const float *diag32, *cx32, *cy32, *cz32;
+  double *x[2], *g[2];
+  unsigned* mask[2];
+  double *r64, *w64, *p64[2], *Ap64;
+  float *r32, *w32, *p32[2], *Ap32;
+  Opts opt;
+};
+
+struct EngineArgs {
+  const DevInst* insts;
+  Ctl* ctl;
+  const int2* tiles;      // (instance slot, tile) per CTA
+  int* live;              // instances not yet done
+  unsigned* npass;        // launches so far (block 0 increments)
+  unsigned pass_cap;      // launches after which the loop condition is cleared
+  unsigned long long cond;  // cudaGraphConditionalHandle, 0 when not in a WHILE graph
+};
+
+}  // namespace gpcg

@@ -1,0 +1,1074 @@
+// gpcg_api.cu -- host side of libgpcg.so: the C ABI of include/gpcg.h, device
+// memory of each problem, the engine driver (CUDA graphs) and the
+// continuous-batching server.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gpcg.h"
+#include "engine.h"
+
+namespace gpcg {
+const void* pass_kernel_ptr();
+cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s);
+cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
+                        int fill_l, int fill_u, int* flags, cudaStream_t s);
+cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
+cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
+                              unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s);
+cudaError_t launch_unpad(const DevInst& I, const void* src, bool f32, double* dst,
+                         cudaStream_t s);
+}  // namespace gpcg
+
+using namespace gpcg;
+
+// ------------------------------------------------------------------ errors --
+
+static thread_local char g_err[512] = "";
+
+static gpcg_status fail(gpcg_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,      \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                    \
+  } while (0)
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static unsigned env_pass_cap() {
+  const char* s = getenv("GPCG_PASS_CAP");
+  if (s && *s) return (unsigned)strtoul(s, nullptr, 10);
+  return 4u * 1024u * 1024u;
+}
+
+static int env_engine_mode() {
+  // 0: one WHILE-conditional CUDA graph per solve (default); 1: host-driven
+  // loop of fixed-length graphs.
+  const char* s = getenv("GPCG_ENGINE_MODE");
+  return (s && *s) ? atoi(s) : 0;
+}
+
+// ------------------------------------------------------------ problem --
+
+struct Scratch {
+  DevInst* d_insts = nullptr;
+  Ctl* d_ctl = nullptr;
+  int2* d_tiles = nullptr;
+  int* d_live = nullptr;
+  unsigned* d_npass = nullptr;
+  int* h_pin = nullptr;  // pinned: [0] live, [1] npass
+  int cap_inst = 0;
+  long long cap_tiles = 0;
+  cudaGraphExec_t gexec = nullptr;
+  long long g_tiles = -1;
+  int g_mode = -1;
+  int g_steps = 0;
+  ~Scratch() { release(); }
+  void release() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    cudaFree(d_insts);
+    cudaFree(d_ctl);
+    cudaFree(d_tiles);
+    cudaFree(d_live);
+    cudaFree(d_npass);
+    if (h_pin) cudaFreeHost(h_pin);
+    d_insts = nullptr;
+    d_ctl = nullptr;
+    d_tiles = nullptr;
+    d_live = nullptr;
+    d_npass = nullptr;
+    h_pin = nullptr;
+    cap_inst = 0;
+    cap_tiles = 0;
+    g_tiles = -1;
+  }
+  gpcg_status ensure(int n_inst, long long n_tiles) {
+    if (!h_pin) {
+      CK(cudaMallocHost(&h_pin, 4 * sizeof(int)));
+      CK(cudaMalloc(&d_live, sizeof(int)));
+      CK(cudaMalloc(&d_npass, sizeof(unsigned)));
+    }
+    if (n_inst > cap_inst) {
+      cudaFree(d_insts);
+      cudaFree(d_ctl);
+      d_insts = nullptr;
+      d_ctl = nullptr;
+      CK(cudaMalloc(&d_insts, sizeof(DevInst) * n_inst));
+      CK(cudaMalloc(&d_ctl, sizeof(Ctl) * n_inst));
+      cap_inst = n_inst;
+      invalidate();
+    }
+    if (n_tiles > cap_tiles) {
+      cudaFree(d_tiles);
+      d_tiles = nullptr;
+      CK(cudaMalloc(&d_tiles, sizeof(int2) * n_tiles));
+      cap_tiles = n_tiles;
+      invalidate();
+    }
+    return GPCG_OK;
+  }
+  void invalidate() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    g_tiles = -1;
+  }
+};
+
+struct gpcg_problem {
+  int dim = 2, nx = 0, ny = 0, nz = 1, px = 0, mw = 0, kc = 3;
+  long long n = 0, plane = 0, pn = 0, mwords = 0;
+  int tiles_x = 0, tiles_y = 0, n_tiles = 0;
+  double c = 0.0;
+  void* arena64 = nullptr;
+  size_t bytes64 = 0;
+  void* arena32 = nullptr;
+  size_t bytes32 = 0;
+  DevInst inst{};
+  Scratch sc;
+  Ctl last{};
+  bool have = false;
+  double lambda_min = 0.0;
+  long long launches = 0;
+  ~gpcg_problem() {
+    sc.release();
+    cudaFree(arena64);
+    cudaFree(arena32);
+  }
+};
+
+static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_problem* p) {
+  p->dim = dim;
+  p->nx = (int)nx;
+  p->ny = (int)ny;
+  p->nz = (int)nz;
+  p->px = (int)((nx + 7) / 8 * 8);
+  p->mw = (p->px + 31) / 32;
+  p->kc = dim == 3 ? 4 : 3;
+  p->n = nx * ny * nz;
+  p->plane = (long long)p->px * ny;
+  p->pn = p->plane * nz;
+  p->mwords = (long long)p->mw * ny * nz;
+  p->tiles_x = (int)((nx + kTX - 1) / kTX);
+  p->tiles_y = (int)((ny + kTY - 1) / kTY);
+  p->n_tiles = p->tiles_x * p->tiles_y * (int)nz;
+}
+
+// Bytes of the FP64 arena: kc bands, b, l, u, x[2], g[2], r, w, p[2], Ap,
+// two masks and the tile partials.
+static size_t arena64_bytes(const gpcg_problem* p) {
+  const size_t vec = align256(sizeof(double) * (size_t)p->pn);
+  const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
+  const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_tiles);
+  return (size_t)(p->kc + 12) * vec + 2 * msk + part;
+}
+
+static size_t arena32_bytes(const gpcg_problem* p) {
+  const size_t vec = align256(sizeof(float) * (size_t)p->pn);
+  return (size_t)(p->kc + 5) * vec;
+}
+
+static void carve64(gpcg_problem* p) {
+  char* a = (char*)p->arena64;
+  const size_t vec = align256(sizeof(double) * (size_t)p->pn);
+  const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
+  auto take = [&](size_t b) {
+    char* r = a;
+    a += b;
+    return r;
+  };
+  DevInst& I = p->inst;
+  I.dim = p->dim;
+  I.nx = p->nx;
+  I.ny = p->ny;
+  I.nz = p->nz;
+  I.px = p->px;
+  I.mw = p->mw;
+  I.tiles_x = p->tiles_x;
+  I.tiles_y = p->tiles_y;
+  I.n_tiles = p->n_tiles;
+  I.kc = p->kc;
+  I.n = p->n;
+  I.plane = p->plane;
+  I.diag = (double*)take(vec);
+  I.cx = (double*)take(vec);
+  I.cy = (double*)take(vec);
+  I.cz = p->dim == 3 ? (double*)take(vec) : nullptr;
+  I.b = (double*)take(vec);
+  I.l = (double*)take(vec);
+  I.u = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.x[k] = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.g[k] = (double*)take(vec);
+  I.r64 = (double*)take(vec);
+  I.w64 = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.p64[k] = (double*)take(vec);
+  I.Ap64 = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.mask[k] = (unsigned*)take(msk);
+  I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_tiles));
+  I.x0 = I.r64;  // a given start point is staged in r (unused until CG starts)
+}
+
+static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
+  if (p->arena32) return GPCG_OK;
+  const size_t bytes = arena32_bytes(p);
+  CK(cudaMalloc(&p->arena32, bytes));
+  CK(cudaMemsetAsync(p->arena32, 0, bytes, s));
+  p->bytes32 = bytes;
+  char* a = (char*)p->arena32;
+  const size_t vec = align256(sizeof(float) * (size_t)p->pn);
+  auto take = [&]() {
+    char* r = a;
+    a += vec;
+    return (float*)r;
+  };
+  DevInst& I = p->inst;
+  float* d32 = take();
+  float* x32 = take();
+  float* y32 = take();
+  float* z32 = p->dim == 3 ? take() : nullptr;
+  I.r32 = take();
+  I.w32 = take();
+  I.p32[0] = take();
+  I.p32[1] = take();
+  I.Ap32 = take();
+  CK(launch_to_float(I.diag, d32, p->pn, s));
+  CK(launch_to_float(I.cx, x32, p->pn, s));
+  CK(launch_to_float(I.cy, y32, p->pn, s));
+  if (z32) CK(launch_to_float(I.cz, z32, p->pn, s));
+  I.diag32 = d32;
+  I.cx32 = x32;
+  I.cy32 = y32;
+  I.cz32 = z32;
+  return GPCG_OK;
+}
+
+static gpcg_status copy_in(const gpcg_problem* p, double* dst, const double* src, cudaStream_t s) {
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * p->px, src, sizeof(double) * p->nx,
+                       sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault, s));
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b,
+                                           const double* l, const double* u, double c,
+                                           gpcg_problem** out) {
+  if (!out) return fail(GPCG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A || !b) return fail(GPCG_ERR_ARG, "A or b is NULL");
+  if (A->dim != 2 && A->dim != 3) return fail(GPCG_ERR_ARG, "dim must be 2 or 3");
+  if (A->nx < 1 || A->ny < 1 || A->nz < 1) return fail(GPCG_ERR_ARG, "grid sizes must be >= 1");
+  if (A->dim == 2 && A->nz != 1) return fail(GPCG_ERR_ARG, "nz must be 1 when dim == 2");
+  if (!A->diag || !A->cx || !A->cy || (A->dim == 3 && !A->cz))
+    return fail(GPCG_ERR_ARG, "missing stencil band");
+  if (A->nx >= (1LL << 31) || A->ny >= (1LL << 31) || A->nz >= (1LL << 31) ||
+      A->nx * A->ny * A->nz >= (1LL << 31))
+    return fail(GPCG_ERR_ARG, "problem too large (n must be below 2^31)");
+  if (!std::isfinite(c)) return fail(GPCG_ERR_ARG, "c is not finite");
+
+  gpcg_problem* p = new gpcg_problem();
+  geometry(A->dim, A->nx, A->ny, A->nz, p);
+  p->c = c;
+  p->bytes64 = arena64_bytes(p);
+  cudaError_t e = cudaMalloc(&p->arena64, p->bytes64);
+  if (e != cudaSuccess) {
+    const size_t bytes = p->bytes64;
+    delete p;
+    return fail(e == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
+                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  carve64(p);
+  cudaStream_t s = 0;
+  gpcg_status st = GPCG_OK;
+  int* d_flags = nullptr;
+  int h_flags = 0;
+  DevInst& I = p->inst;
+  do {
+    if ((e = cudaMemsetAsync(p->arena64, 0, p->bytes64, s)) != cudaSuccess) break;
+    if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) break;
+    if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) break;
+    if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) break;
+    if (A->dim == 3 && (st = copy_in(p, (double*)I.cz, A->cz, s)) != GPCG_OK) break;
+    if ((st = copy_in(p, (double*)I.b, b, s)) != GPCG_OK) break;
+    if (l && (st = copy_in(p, (double*)I.l, l, s)) != GPCG_OK) break;
+    if (u && (st = copy_in(p, (double*)I.u, u, s)) != GPCG_OK) break;
+    if ((e = cudaMalloc(&d_flags, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(d_flags, 0, sizeof(int), s)) != cudaSuccess) break;
+    if ((e = launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l,
+                         (double*)I.u, l == nullptr, u == nullptr, d_flags, s)) != cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+      break;
+    e = cudaStreamSynchronize(s);
+  } while (0);
+  cudaFree(d_flags);
+  if (st == GPCG_OK && e != cudaSuccess)
+    st = fail(GPCG_ERR_CUDA, "problem set-up failed: %s", cudaGetErrorString(e));
+  if (st == GPCG_OK && h_flags) {
+    if (h_flags & 1) st = fail(GPCG_ERR_ARG, "non-finite b, coupling or NaN bound");
+    else if (h_flags & 2) st = fail(GPCG_ERR_ARG, "diagonal entry <= 0 or not finite");
+    else st = fail(GPCG_ERR_INFEASIBLE, "empty box: some l > u, l = +inf or u = -inf");
+  }
+  if (st != GPCG_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return GPCG_OK;
+}
+
+extern "C" void gpcg_problem_destroy(gpcg_problem* p) { delete p; }
+
+extern "C" int64_t gpcg_problem_size(const gpcg_problem* p) { return p ? p->n : 0; }
+
+extern "C" void gpcg_default_options(gpcg_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tau_abs = 0.0;
+  o->tau_rel = 1e-8;
+  o->eta1 = 0.1;
+  o->eta2 = 0.05;
+  o->mu = 0.01;
+  o->eta2_shrink = 0.1;
+  o->eta2_floor = 1e-12;
+  o->max_outer = 10000;
+  o->max_gp = 50;
+  o->max_cg = 10000;
+  o->max_ls = 60;
+  o->precision = GPCG_FP64;
+  o->refine = 1;
+  o->x0 = nullptr;
+  o->cuda_stream = nullptr;
+  o->lambda_min = 0.0;
+}
+
+static gpcg_status check_options(const gpcg_options* o) {
+  if (!o) return fail(GPCG_ERR_ARG, "options are NULL");
+  if (!(o->tau_abs >= 0.0) || !(o->tau_rel >= 0.0)) return fail(GPCG_ERR_ARG, "bad tolerance");
+  if (!(o->eta1 > 0.0 && o->eta1 < 1.0) || !(o->eta2 > 0.0 && o->eta2 < 1.0))
+    return fail(GPCG_ERR_ARG, "eta1 and eta2 must lie in (0,1)");
+  if (!(o->mu > 0.0 && o->mu < 0.5)) return fail(GPCG_ERR_ARG, "mu must lie in (0,1/2)");
+  if (!(o->eta2_shrink > 0.0 && o->eta2_shrink <= 1.0) || !(o->eta2_floor >= 0.0))
+    return fail(GPCG_ERR_ARG, "bad eta2_shrink / eta2_floor");
+  if (o->max_outer < 1 || o->max_gp < 1 || o->max_cg < 0 || o->max_ls < 0)
+    return fail(GPCG_ERR_ARG, "bad iteration caps");
+  if (o->precision != GPCG_FP64 && o->precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  return GPCG_OK;
+}
+
+static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
+  Opts r{};
+  r.tau_abs = o->tau_abs;
+  r.tau_rel = o->tau_rel;
+  r.eta1 = o->eta1;
+  r.eta2 = o->eta2;
+  r.mu = o->mu;
+  r.eta2_shrink = o->eta2_shrink;
+  r.eta2_floor = o->eta2_floor;
+  r.eta2_refine = std::max(o->eta2 * o->eta2_shrink, o->eta2_floor);
+  r.c = c;
+  r.max_outer = o->max_outer;
+  r.max_gp = o->max_gp;
+  r.max_cg = o->max_cg;
+  r.max_ls = o->max_ls;
+  r.mixed = o->precision == GPCG_MIXED;
+  r.refine = o->refine ? 1 : 0;
+  r.use_x0 = use_x0 ? 1 : 0;
+  return r;
+}
+
+static Ctl fresh_ctl() {
+  Ctl C;
+  memset(&C, 0, sizeof(C));
+  C.pass = P_START;
+  C.status = S_RUNNING;
+  return C;
+}
+
+// ------------------------------------------------------------- engine --
+
+// Build (or reuse) the executable graph for `tiles` CTAs per pass.
+// mode 0: WHILE-conditional graph whose body is kBody passes; the pass kernel
+// clears the condition once every instance is done or the pass cap is hit.
+// mode 1: a plain graph of `steps` passes replayed by the host.
+static constexpr int kBody = 4;
+
+static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap) {
+  if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps))
+    return GPCG_OK;
+  sc.invalidate();
+  EngineArgs args{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, cap, 0ull};
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraph_t body = g;
+  int count = steps;
+  gpcg_status st = GPCG_OK;
+  if (mode == 0) {
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      alignas(cudaGraphNodeParams) unsigned char cp_buf[sizeof(cudaGraphNodeParams)];
+      memset(cp_buf, 0, sizeof(cp_buf));
+      cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_buf);
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t cn;
+      e = cudaGraphAddNode(&cn, g, nullptr, nullptr, 0, &cp);
+      if (e == cudaSuccess) {
+        body = cp.conditional.phGraph_out[0];
+        args.cond = (unsigned long long)h;
+        count = kBody;
+      }
+    }
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(GPCG_ERR_CUDA, "conditional graph set-up failed: %s", cudaGetErrorString(e));
+    }
+  }
+  void* kp[] = {&args};
+  cudaKernelNodeParams k;
+  memset(&k, 0, sizeof(k));
+  k.func = const_cast<void*>(pass_kernel_ptr());
+  k.gridDim = dim3((unsigned)tiles);
+  k.blockDim = dim3(kThreads);
+  k.sharedMemBytes = 0;
+  k.kernelParams = kp;
+  cudaGraphNode_t prev = nullptr;
+  for (int i = 0; i < count; ++i) {
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &k);
+    if (e != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "cudaGraphAddKernelNode: %s", cudaGetErrorString(e));
+      break;
+    }
+    prev = node;
+  }
+  if (st == GPCG_OK) {
+    cudaError_t e = cudaGraphInstantiate(&sc.gexec, g, 0);
+    if (e != cudaSuccess) st = fail(GPCG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(g);
+  if (st != GPCG_OK) {
+    sc.gexec = nullptr;
+    return st;
+  }
+  sc.g_tiles = tiles;
+  sc.g_mode = mode;
+  sc.g_steps = steps;
+  return GPCG_OK;
+}
+
+// Run the engine until every instance in the scratch tables is done.
+static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStream_t s) {
+  const unsigned cap = env_pass_cap();
+  const int mode = env_engine_mode();
+  sc.h_pin[0] = n_live;
+  sc.h_pin[1] = 0;
+  CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
+  if (mode == 0) {
+    gpcg_status st = get_graph(sc, tiles, 0, kBody, cap);
+    if (st != GPCG_OK) return st;
+    CK(cudaGraphLaunch(sc.gexec, s));
+    CK(cudaMemcpyAsync(&sc.h_pin[0], sc.d_live, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&sc.h_pin[1], sc.d_npass, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    int steps = 8;
+    unsigned done_passes = 0;
+    for (;;) {
+      gpcg_status st = get_graph(sc, tiles, 1, steps, cap);
+      if (st != GPCG_OK) return st;
+      CK(cudaGraphLaunch(sc.gexec, s));
+      CK(cudaMemcpyAsync(&sc.h_pin[0], sc.d_live, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&sc.h_pin[1], sc.d_npass, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      done_passes += steps;
+      if (sc.h_pin[0] == 0 || done_passes >= cap) break;
+      steps = std::min(steps * 2, 256);
+    }
+  }
+  if (sc.h_pin[0] != 0) return fail(GPCG_ERR_TIMEOUT, "pass cap reached with live solves");
+  return GPCG_OK;
+}
+
+static gpcg_status prepare_instance(gpcg_problem* p, const gpcg_options* o, cudaStream_t s,
+                                    DevInst* out) {
+  gpcg_status st;
+  if (o->precision == GPCG_MIXED && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  const bool use_x0 = o->x0 != nullptr;
+  if (use_x0 && (st = copy_in(p, (double*)p->inst.x0, o->x0, s)) != GPCG_OK) return st;
+  *out = p->inst;
+  out->opt = make_opts(o, p->c, use_x0);
+  return GPCG_OK;
+}
+
+static int to_status(int s) {
+  switch (s) {
+    case S_OK: return GPCG_OK;
+    case S_NUMERIC: return GPCG_ERR_NUMERIC;
+    case S_MAXIT: return GPCG_ERR_MAXIT;
+    case S_LINESEARCH: return GPCG_ERR_LINESEARCH;
+    case S_TIMEOUT: return GPCG_ERR_TIMEOUT;
+    default: return GPCG_ERR_PENDING;
+  }
+}
+
+static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_options* o,
+                             Scratch& sc) {
+  cudaStream_t s = (cudaStream_t)o->cuda_stream;
+  long long tiles = 0;
+  for (int k = 0; k < count; ++k) tiles += probs[k]->n_tiles;
+  gpcg_status st = sc.ensure(count, tiles);
+  if (st != GPCG_OK) return st;
+  std::vector<DevInst> insts(count);
+  std::vector<Ctl> ctl(count, fresh_ctl());
+  std::vector<int2> table((size_t)tiles);
+  long long t = 0;
+  for (int k = 0; k < count; ++k) {
+    if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
+    for (int j = 0; j < probs[k]->n_tiles; ++j) table[(size_t)t++] = make_int2(k, j);
+  }
+  CK(cudaMemcpyAsync(sc.d_insts, insts.data(), sizeof(DevInst) * count, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_ctl, ctl.data(), sizeof(Ctl) * count, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_tiles, table.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice, s));
+  gpcg_status run = run_engine(sc, count, tiles, s);
+  if (run != GPCG_OK && run != GPCG_ERR_TIMEOUT) return run;
+  CK(cudaMemcpyAsync(ctl.data(), sc.d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  gpcg_status first_bad = GPCG_OK;
+  for (int k = 0; k < count; ++k) {
+    if (!ctl[k].done) ctl[k].status = S_TIMEOUT;
+    probs[k]->launches = (unsigned)sc.h_pin[1];
+    probs[k]->last = ctl[k];
+    probs[k]->have = true;
+    probs[k]->lambda_min = o->lambda_min;
+    const gpcg_status sk = (gpcg_status)to_status(ctl[k].status);
+    if (sk != GPCG_OK && first_bad == GPCG_OK) first_bad = sk;
+  }
+  if (first_bad != GPCG_OK)
+    return fail(first_bad, "solve ended with status %d", (int)first_bad);
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_solve(gpcg_problem* p, const gpcg_options* opt) {
+  if (!p) return fail(GPCG_ERR_ARG, "problem is NULL");
+  gpcg_status st = check_options(opt);
+  if (st != GPCG_OK) return st;
+  gpcg_problem* one[1] = {p};
+  return solve_set(one, 1, opt, p->sc);
+}
+
+extern "C" gpcg_status gpcg_solve_batch(gpcg_problem* const* probs, int count,
+                                        const gpcg_options* opt) {
+  if (!probs || count < 1) return fail(GPCG_ERR_ARG, "empty batch");
+  for (int k = 0; k < count; ++k)
+    if (!probs[k]) return fail(GPCG_ERR_ARG, "problem %d is NULL", k);
+  gpcg_status st = check_options(opt);
+  if (st != GPCG_OK) return st;
+  Scratch sc;
+  return solve_set(probs, count, opt, sc);
+}
+
+static void fill_stats(const gpcg_problem* p, gpcg_stats* s) {
+  const Ctl& C = p->last;
+  memset(s, 0, sizeof(*s));
+  s->q = 0.5 * C.xgb + p->c;
+  s->pg_norm = std::sqrt(C.pg2);
+  s->pg_norm0 = C.pg0;
+  s->tau = C.tau;
+  s->n_active = (int64_t)C.nA;
+  s->n_binding = (int64_t)C.nB;
+  s->n_free = p->n - (int64_t)C.nA;
+  s->outer_iters = C.outer_iters;
+  s->gp_iters = C.gp_iters;
+  s->cg_iters = C.cg_iters;
+  s->ls_trials = C.ls_trials;
+  s->refine_cg_iters = C.refine_cg_iters;
+  s->passes = C.passes;
+  s->status = to_status(C.status);
+  s->err_bound = p->lambda_min > 0.0 ? s->pg_norm / p->lambda_min : -1.0;
+  s->alg_bytes = C.alg_bytes;
+  s->launches = p->launches;
+}
+
+extern "C" gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats) {
+  if (!p) return fail(GPCG_ERR_ARG, "problem is NULL");
+  if (!p->have) return fail(GPCG_ERR_PENDING, "no solve has run on this problem");
+  if (x_out) {
+    const double* x = p->inst.x[p->last.cur];
+    CK(cudaMemcpy2D(x_out, sizeof(double) * p->nx, x, sizeof(double) * p->px,
+                    sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault));
+  }
+  if (stats) fill_stats(p, stats);
+  return GPCG_OK;
+}
+
+// ------------------------------------------- masked product entry points --
+
+static bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
+  Scratch& sc = p->sc;
+  gpcg_status st = sc.ensure(1, p->n_tiles);
+  if (st != GPCG_OK) return st;
+  std::vector<int2> table((size_t)p->n_tiles);
+  for (int j = 0; j < p->n_tiles; ++j) table[(size_t)j] = make_int2(0, j);
+  DevInst I = p->inst;
+  I.opt = Opts{};
+  CK(cudaMemcpyAsync(sc.d_insts, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_ctl, &C, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_tiles, table.data(), sizeof(int2) * table.size(),
+                     cudaMemcpyHostToDevice, s));
+  sc.h_pin[0] = 1;
+  sc.h_pin[1] = 0;
+  CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
+  EngineArgs E{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, 0xffffffffu, 0ull};
+  CK(launch_pass(E, p->n_tiles, s));
+  if (out) {
+    CK(cudaMemcpyAsync(out, sc.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return GPCG_OK;
+}
+
+static Ctl spmv_ctl(bool f32, int cur, int pcur) {
+  Ctl C = fresh_ctl();
+  C.pass = P_CG_B;
+  C.first_cg = 0;
+  C.beta = 0.0;
+  C.cur = cur;
+  C.pcur = pcur;
+  C.cg32 = f32 ? 1 : 0;
+  C.hold = 1;
+  return C;
+}
+
+extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask,
+                                        const double* pv, double* y, double* pAp, int precision,
+                                        void* cuda_stream) {
+  if (!p || !free_mask || !pv || !y) return fail(GPCG_ERR_ARG, "NULL argument");
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f32 = precision == GPCG_MIXED;
+  gpcg_status st;
+  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  uint8_t* dm = nullptr;
+  double* dp = nullptr;
+  double* dy = nullptr;
+  const bool m_dev = is_device_ptr(free_mask), p_dev = is_device_ptr(pv), y_dev = is_device_ptr(y);
+  std::vector<void*> temps;
+  auto cleanup = [&]() {
+    for (void* t : temps) cudaFree(t);
+  };
+  st = GPCG_OK;
+  do {
+    if (m_dev) {
+      dm = const_cast<uint8_t*>(free_mask);
+    } else {
+      if (cudaMalloc(&dm, p->n) != cudaSuccess) { st = fail(GPCG_ERR_OOM, "temp alloc"); break; }
+      temps.push_back(dm);
+      if (cudaMemcpyAsync(dm, free_mask, p->n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "copy mask");
+        break;
+      }
+    }
+    if (p_dev) {
+      dp = const_cast<double*>(pv);
+    } else {
+      if (cudaMalloc(&dp, sizeof(double) * p->n) != cudaSuccess) { st = fail(GPCG_ERR_OOM, "temp alloc"); break; }
+      temps.push_back(dp);
+      if (cudaMemcpyAsync(dp, pv, sizeof(double) * p->n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "copy p");
+        break;
+      }
+    }
+    if (y_dev) {
+      dy = y;
+    } else {
+      if (cudaMalloc(&dy, sizeof(double) * p->n) != cudaSuccess) { st = fail(GPCG_ERR_OOM, "temp alloc"); break; }
+      temps.push_back(dy);
+    }
+    DevInst& I = p->inst;
+    void* r = f32 ? (void*)I.r32 : (void*)I.r64;
+    void* p0 = f32 ? (void*)I.p32[0] : (void*)I.p64[0];
+    if (launch_spmv_setup(I, dm, dp, I.mask[0], r, p0, f32, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "spmv set-up launch");
+      break;
+    }
+    Ctl out;
+    if ((st = one_pass(p, spmv_ctl(f32, 0, 0), s, &out)) != GPCG_OK) break;
+    const void* ap = f32 ? (const void*)I.Ap32 : (const void*)I.Ap64;
+    if (launch_unpad(I, ap, f32, dy, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "unpad launch");
+      break;
+    }
+    if (!y_dev &&
+        cudaMemcpyAsync(y, dy, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "copy y");
+      break;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "synchronize: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (pAp) *pAp = out.red[0];
+    p->have = false;  // the solve's vectors were overwritten
+  } while (0);
+  cleanup();
+  return st;
+}
+
+extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps,
+                                             void* cuda_stream, double* ms_per_launch,
+                                             double* bytes_per_launch) {
+  if (!p || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f32 = precision == GPCG_MIXED;
+  gpcg_status st;
+  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  int cur = p->have ? p->last.cur : 0;
+  if (!p->have) {
+    // all points free, p = 1
+    uint8_t* dm = nullptr;
+    double* dp = nullptr;
+    CK(cudaMalloc(&dm, p->n));
+    CK(cudaMalloc(&dp, sizeof(double) * p->n));
+    CK(cudaMemsetAsync(dm, 1, p->n, s));
+    std::vector<double> ones((size_t)p->n, 1.0);
+    CK(cudaMemcpyAsync(dp, ones.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, s));
+    DevInst& I = p->inst;
+    CK(launch_spmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.r32 : (void*)I.r64,
+                         f32 ? (void*)I.p32[0] : (void*)I.p64[0], f32, s));
+    CK(cudaStreamSynchronize(s));
+    cudaFree(dm);
+    cudaFree(dp);
+    cur = 0;
+  }
+  // one untimed launch sets up the tables, then `reps` timed launches
+  if ((st = one_pass(p, spmv_ctl(f32, cur, 0), s, nullptr)) != GPCG_OK) return st;
+  Scratch& sc = p->sc;
+  EngineArgs E{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, 0xffffffffu, 0ull};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  for (int k = 0; k < reps; ++k) CK(launch_pass(E, p->n_tiles, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_per_launch) *ms_per_launch = ms / reps;
+  const double sv = f32 ? 4.0 : 8.0;
+  if (bytes_per_launch) *bytes_per_launch = (double)p->n * (sv * p->kc + 4.0 * sv + 0.125);
+  return GPCG_OK;
+}
+
+// -------------------------------------------------------------- server --
+
+namespace {
+enum ReqState { R_QUEUED = 0, R_RUNNING = 1, R_DONE = 2, R_CANCELLED = 3 };
+
+struct Req {
+  int64_t ticket = 0;
+  gpcg_stencil A{};
+  const double *b = nullptr, *l = nullptr, *u = nullptr;
+  double c = 0.0;
+  double* x_out = nullptr;
+  int state = R_QUEUED;
+  gpcg_problem* prob = nullptr;
+  size_t bytes = 0;
+  int slot = -1;
+  double t_submit = 0.0, t_done = 0.0;
+  gpcg_stats st{};
+};
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct gpcg_server {
+  size_t budget = 0, used = 0;
+  int max_live = 0;
+  gpcg_options opt{};
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::deque<Req*> queue;
+  std::vector<Req*> slots;  // running request per slot (nullptr = free)
+  std::map<int64_t, Req*> all;
+  int64_t next_ticket = 1;
+  int finished = 0;
+  Scratch sc;
+  bool dirty = true;
+  long long tiles = 0;
+  ~gpcg_server() {
+    for (auto& kv : all) {
+      delete kv.second->prob;
+      delete kv.second;
+    }
+    sc.release();
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+static size_t footprint(const gpcg_stencil* A, bool mixed) {
+  gpcg_problem tmp;
+  geometry(A->dim, A->nx, A->ny, A->nz, &tmp);
+  size_t b = arena64_bytes(&tmp);
+  if (mixed) b += arena32_bytes(&tmp);
+  return b + 4096;
+}
+
+extern "C" gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const gpcg_options* opt,
+                                          gpcg_server** out) {
+  if (!out) return fail(GPCG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (hbm_budget == 0 || max_live < 1) return fail(GPCG_ERR_ARG, "bad budget or slot count");
+  gpcg_status st = check_options(opt);
+  if (st != GPCG_OK) return st;
+  gpcg_server* s = new gpcg_server();
+  s->budget = hbm_budget;
+  s->max_live = max_live;
+  s->opt = *opt;
+  s->opt.x0 = nullptr;
+  s->slots.assign(max_live, nullptr);
+  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && (st = s->sc.ensure(max_live, 1)) != GPCG_OK) {
+    delete s;
+    return st;
+  }
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(GPCG_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A, const double* b,
+                                          const double* l, const double* u, double c,
+                                          double* x_out, int64_t* ticket) {
+  if (!s || !A || !b || !x_out || !ticket) return fail(GPCG_ERR_ARG, "NULL argument");
+  if (A->dim != 2 && A->dim != 3) return fail(GPCG_ERR_ARG, "dim must be 2 or 3");
+  if (A->nx < 1 || A->ny < 1 || A->nz < 1 || (A->dim == 2 && A->nz != 1))
+    return fail(GPCG_ERR_ARG, "bad grid size");
+  const size_t bytes = footprint(A, s->opt.precision == GPCG_MIXED);
+  if (bytes > s->budget) return fail(GPCG_ERR_BUDGET, "request needs %zu bytes, budget %zu",
+                                     bytes, s->budget);
+  Req* r = new Req();
+  r->A = *A;
+  r->b = b;
+  r->l = l;
+  r->u = u;
+  r->c = c;
+  r->x_out = x_out;
+  r->bytes = bytes;
+  r->t_submit = now_s();
+  std::lock_guard<std::mutex> g(s->mu);
+  r->ticket = s->next_ticket++;
+  s->queue.push_back(r);
+  s->all[r->ticket] = r;
+  *ticket = r->ticket;
+  return GPCG_OK;
+}
+
+static gpcg_status server_upload_table(gpcg_server* s) {
+  std::vector<int2> table;
+  for (int k = 0; k < s->max_live; ++k) {
+    Req* r = s->slots[k];
+    if (!r) continue;
+    for (int j = 0; j < r->prob->n_tiles; ++j) table.push_back(make_int2(k, j));
+  }
+  s->tiles = (long long)table.size();
+  if (s->tiles == 0) return GPCG_OK;
+  gpcg_status st = s->sc.ensure(s->max_live, s->tiles);
+  if (st != GPCG_OK) return st;
+  CK(cudaMemcpyAsync(s->sc.d_tiles, table.data(), sizeof(int2) * table.size(),
+                     cudaMemcpyHostToDevice, s->stream));
+  s->sc.invalidate();
+  s->dirty = false;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_server_step(gpcg_server* s, int passes) {
+  if (!s || passes < 1) return fail(GPCG_ERR_ARG, "bad argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  cudaStream_t st_ = s->stream;
+  // admit what fits
+  while (!s->queue.empty()) {
+    Req* r = s->queue.front();
+    if (r->state == R_CANCELLED) {
+      s->queue.pop_front();
+      continue;
+    }
+    int slot = -1;
+    for (int k = 0; k < s->max_live; ++k)
+      if (!s->slots[k]) {
+        slot = k;
+        break;
+      }
+    if (slot < 0 || s->used + r->bytes > s->budget) break;
+    s->queue.pop_front();
+    gpcg_status st = gpcg_problem_create(&r->A, r->b, r->l, r->u, r->c, &r->prob);
+    if (st != GPCG_OK) {
+      r->state = R_DONE;
+      r->st.status = st;
+      r->t_done = now_s();
+      s->finished++;
+      continue;
+    }
+    DevInst I;
+    if ((st = prepare_instance(r->prob, &s->opt, st_, &I)) != GPCG_OK) return st;
+    Ctl C = fresh_ctl();
+    CK(cudaMemcpyAsync(s->sc.d_insts + slot, &I, sizeof(DevInst), cudaMemcpyHostToDevice, st_));
+    CK(cudaMemcpyAsync(s->sc.d_ctl + slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice, st_));
+    r->slot = slot;
+    r->state = R_RUNNING;
+    s->slots[slot] = r;
+    s->used += r->bytes;
+    s->dirty = true;
+  }
+  int live = 0;
+  for (Req* r : s->slots)
+    if (r) live++;
+  if (live == 0) return GPCG_OK;
+  if (s->dirty) {
+    gpcg_status st = server_upload_table(s);
+    if (st != GPCG_OK) return st;
+  }
+  s->sc.h_pin[0] = live;
+  CK(cudaMemcpyAsync(s->sc.d_live, &s->sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, st_));
+  gpcg_status st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu);
+  if (st != GPCG_OK) return st;
+  CK(cudaGraphLaunch(s->sc.gexec, st_));
+  std::vector<Ctl> ctl(s->max_live);
+  CK(cudaMemcpyAsync(ctl.data(), s->sc.d_ctl, sizeof(Ctl) * s->max_live, cudaMemcpyDeviceToHost,
+                     st_));
+  CK(cudaStreamSynchronize(st_));
+  for (int k = 0; k < s->max_live; ++k) {
+    Req* r = s->slots[k];
+    if (!r || !ctl[k].done) continue;
+    r->prob->last = ctl[k];
+    r->prob->have = true;
+    r->prob->lambda_min = s->opt.lambda_min;
+    gpcg_result(r->prob, r->x_out, &r->st);
+    delete r->prob;
+    r->prob = nullptr;
+    s->used -= r->bytes;
+    s->slots[k] = nullptr;
+    r->state = R_DONE;
+    r->t_done = now_s();
+    s->finished++;
+    s->dirty = true;
+  }
+  return GPCG_OK;
+}
+
+extern "C" int gpcg_server_done(gpcg_server* s, int64_t ticket) {
+  if (!s) return 0;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->all.find(ticket);
+  return it != s->all.end() && it->second->state == R_DONE;
+}
+
+extern "C" gpcg_status gpcg_server_stats(gpcg_server* s, int64_t ticket, gpcg_stats* st,
+                                         double* latency_s) {
+  if (!s) return fail(GPCG_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return fail(GPCG_ERR_ARG, "unknown ticket");
+  Req* r = it->second;
+  if (r->state == R_CANCELLED) return fail(GPCG_ERR_CANCELLED, "ticket cancelled");
+  if (r->state != R_DONE) return fail(GPCG_ERR_PENDING, "ticket still running");
+  if (st) *st = r->st;
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket) {
+  if (!s) return fail(GPCG_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return fail(GPCG_ERR_ARG, "unknown ticket");
+  Req* r = it->second;
+  if (r->state == R_DONE) return fail(GPCG_ERR_ARG, "ticket already finished");
+  if (r->state == R_RUNNING) {
+    // the slot is released between passes: no kernel of this request is in
+    // flight while the host holds the lock
+    Ctl C = fresh_ctl();
+    C.pass = P_NONE;
+    C.done = 1;
+    C.status = S_OK;
+    CK(cudaMemcpyAsync(s->sc.d_ctl + r->slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->slots[r->slot] = nullptr;
+    s->used -= r->bytes;
+    delete r->prob;
+    r->prob = nullptr;
+    s->dirty = true;
+  }
+  r->state = R_CANCELLED;
+  s->finished++;
+  return GPCG_OK;
+}
+
+extern "C" void gpcg_server_counts(gpcg_server* s, int* queued, int* running, int* finished) {
+  if (!s) return;
+  std::lock_guard<std::mutex> g(s->mu);
+  int q = 0, run = 0;
+  for (Req* r : s->queue)
+    if (r->state == R_QUEUED) q++;
+  for (Req* r : s->slots)
+    if (r) run++;
+  if (queued) *queued = q;
+  if (running) *running = run;
+  if (finished) *finished = s->finished;
+}
+
+extern "C" void gpcg_server_destroy(gpcg_server* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  delete s;
+}
+
+extern "C" const char* gpcg_last_error(void) { return g_err; }
+
+extern "C" const char* gpcg_version(void) { return "gpcg-gb300 0.1 (sm_103a)"; }

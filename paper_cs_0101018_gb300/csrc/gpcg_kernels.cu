@@ -1,0 +1,1074 @@
+// gpcg_kernels.cu -- device side of the GB300 GPCG engine.
+//
+// One kernel, pass_kernel, runs every pass of Algorithm GPCG (Sec. 3 of
+// Benson, McInnes & More) for every live instance: each CTA takes one 64x32
+// tile (one plane of a 3-D grid) of one instance, performs the pass the
+// instance's state machine asks for, and deposits its partial sums in a fixed
+// slot.  The last CTA of an instance reduces those slots in a fixed order and
+// runs the state-machine transition (finalize below), so the arithmetic of an
+// instance does not depend on the other instances in the launch.
+//
+// The stencil passes stream each operand once: a warp walks down its 64-column
+// strip keeping the operand of rows y-1, y, y+1 in registers; east/west
+// neighbours come from the adjacent lane by shuffle (lanes 0 and 31 load the
+// one point beyond the strip), and the up/down planes of a 3-D grid are
+// loaded directly.  The operand of a pass is computed from its inputs on the
+// fly (for example p = -r + beta*p in the CG pass, or P[x + alpha*d] in a
+// trial), so no pass writes a vector that another CTA of the same launch reads.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "engine.h"
+
+namespace gpcg {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ double mid3(double l, double u, double x) {
+  // median of {l, u, x} for l <= u: the projection P of Sec. 3
+  return x < l ? l : (x > u ? u : x);
+}
+
+// Projected gradient component, Eq. proj-gradient; a fixed variable
+// (l == u) has component 0.
+__device__ __forceinline__ double pg_comp(double x, double g, double l, double u) {
+  const bool al = (x == l), au = (x == u);
+  if (al && au) return 0.0;
+  if (al) return g < 0.0 ? g : 0.0;
+  if (au) return g > 0.0 ? g : 0.0;
+  return g;
+}
+
+__device__ __forceinline__ void ld2(const double* __restrict__ p, long long i, bool v0, bool v1,
+                                    double o[2]) {
+  if (v1) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p + i));
+    o[0] = t.x;
+    o[1] = t.y;
+  } else {
+    o[0] = v0 ? __ldg(p + i) : 0.0;
+    o[1] = 0.0;
+  }
+}
+
+__device__ __forceinline__ void ld2(const float* __restrict__ p, long long i, bool v0, bool v1,
+                                    float o[2]) {
+  if (v1) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p + i));
+    o[0] = t.x;
+    o[1] = t.y;
+  } else {
+    o[0] = v0 ? __ldg(p + i) : 0.0f;
+    o[1] = 0.0f;
+  }
+}
+
+__device__ __forceinline__ void st2(double* p, long long i, bool v0, bool v1, double a, double b) {
+  if (v1) {
+    *reinterpret_cast<double2*>(p + i) = make_double2(a, b);
+  } else if (v0) {
+    p[i] = a;
+  }
+}
+
+__device__ __forceinline__ void st2(float* p, long long i, bool v0, bool v1, float a, float b) {
+  if (v1) {
+    *reinterpret_cast<float2*>(p + i) = make_float2(a, b);
+  } else if (v0) {
+    p[i] = a;
+  }
+}
+
+// Spread the low 16 bits of v to the even bit positions of a 32-bit word.
+__device__ __forceinline__ unsigned spread16(unsigned v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+struct Acc {
+  double s[5];
+  int c[3];
+};
+
+__device__ __forceinline__ long long row_index(const DevInst& I, int y, int z) {
+  return (long long)z * I.ny + y;
+}
+
+// The two free bits of this lane's points (e0, e0+1) in row (y, z).
+__device__ __forceinline__ unsigned my_free_bits(const DevInst& I, const unsigned* __restrict__ m,
+                                                 int y, int z, int e0) {
+  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (e0 >> 5));
+  return (w >> (e0 & 31)) & 3u;
+}
+
+__device__ __forceinline__ bool free_bit(const DevInst& I, const unsigned* __restrict__ m, int y,
+                                         int z, int col) {
+  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (col >> 5));
+  return (w >> (col & 31)) & 1u;
+}
+
+// Write the free bits of a warp's 64-column strip (two words) for row (y,z);
+// returns, for lanes 0 and 16, the number of bits that differ from `old`
+// (nullptr: 0).
+__device__ __forceinline__ int write_mask(const DevInst& I, unsigned* m, const unsigned* old,
+                                          int y, int z, int x0, int lane, bool f0, bool f1) {
+  const unsigned b0 = __ballot_sync(FULL_MASK, f0);
+  const unsigned b1 = __ballot_sync(FULL_MASK, f1);
+  int diff = 0;
+  if ((lane & 15) == 0) {
+    const int h = lane >> 4;
+    const int wcol = (x0 >> 5) + h;
+    if (wcol < I.mw) {
+      const unsigned word = spread16(b0 >> (16 * h)) | (spread16(b1 >> (16 * h)) << 1);
+      const long long wi = row_index(I, y, z) * I.mw + wcol;
+      m[wi] = word;
+      if (old) diff = __popc(word ^ __ldg(old + wi));
+    }
+  }
+  return diff;
+}
+
+// ---------------------------------------------------------- stencil sweep --
+//
+// Op supplies the operand v of the pass at any point (operand_row for the
+// lane's two points of a row, operand_at for one point) and consumes, for
+// each row of the strip, v and (A v) at the lane's two points (output).
+
+template <class Op>
+__device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int x0, int y0, int z,
+                                             Acc& acc) {
+  using T = typename Op::T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;  // warp-uniform
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const long long zb = (long long)z * I.plane;
+  const T* __restrict__ diag = op.diag();
+  const T* __restrict__ cx = op.cx();
+  const T* __restrict__ cy = op.cy();
+  const T* __restrict__ cz = op.cz();
+
+  T vm[2], vc[2], vn[2], cs[2];
+  op.operand_row(ya - 1, z, e0, v0, v1, vm);
+  op.operand_row(ya, z, e0, v0, v1, vc);
+  if (ya > 0) {
+    ld2(cy, zb + (long long)(ya - 1) * I.px + e0, v0, v1, cs);
+  } else {
+    cs[0] = cs[1] = T(0);
+  }
+  for (int y = ya; y < yb; ++y) {
+    op.operand_row(y + 1, z, e0, v0, v1, vn);
+    const long long i = zb + (long long)y * I.px + e0;
+    T d[2], ce[2], cn[2];
+    ld2(diag, i, v0, v1, d);
+    ld2(cx, i, v0, v1, ce);
+    ld2(cy, i, v0, v1, cn);
+    T vw = __shfl_up_sync(FULL_MASK, vc[1], 1);
+    T cw = __shfl_up_sync(FULL_MASK, ce[1], 1);
+    T ve = __shfl_down_sync(FULL_MASK, vc[0], 1);
+    if (lane == 0) {
+      const bool has = v0 && e0 > 0;
+      vw = has ? op.operand_at(i - 1, y, z, e0 - 1) : T(0);
+      cw = has ? __ldg(cx + i - 1) : T(0);
+    }
+    if (lane == 31) ve = (e0 + 2 < I.nx) ? op.operand_at(i + 2, y, z, e0 + 2) : T(0);
+    T av[2];
+    // row sums in the order diag, west, east, south, north (, down, up)
+    av[0] = d[0] * vc[0];
+    av[0] = fma(cw, vw, av[0]);
+    av[0] = fma(ce[0], vc[1], av[0]);
+    av[0] = fma(cs[0], vm[0], av[0]);
+    av[0] = fma(cn[0], vn[0], av[0]);
+    av[1] = d[1] * vc[1];
+    av[1] = fma(ce[0], vc[0], av[1]);
+    av[1] = fma(ce[1], ve, av[1]);
+    av[1] = fma(cs[1], vm[1], av[1]);
+    av[1] = fma(cn[1], vn[1], av[1]);
+    if (I.dim == 3) {
+      T vd[2], vu[2], czd[2], czu[2];
+      op.operand_row(y, z - 1, e0, v0, v1, vd);
+      op.operand_row(y, z + 1, e0, v0, v1, vu);
+      if (z > 0) {
+        ld2(cz, i - I.plane, v0, v1, czd);
+      } else {
+        czd[0] = czd[1] = T(0);
+      }
+      ld2(cz, i, v0, v1, czu);
+      av[0] = fma(czd[0], vd[0], av[0]);
+      av[0] = fma(czu[0], vu[0], av[0]);
+      av[1] = fma(czd[1], vd[1], av[1]);
+      av[1] = fma(czu[1], vu[1], av[1]);
+    }
+    op.output(y, z, i, x0, e0, lane, v0, v1, vc, av, acc);
+    vm[0] = vc[0];
+    vm[1] = vc[1];
+    vc[0] = vn[0];
+    vc[1] = vn[1];
+    cs[0] = cn[0];
+    cs[1] = cn[1];
+  }
+}
+
+__device__ __forceinline__ bool row_ok(const DevInst& I, int y, int z) {
+  return y >= 0 && y < I.ny && z >= 0 && z < I.nz;
+}
+
+__device__ __forceinline__ long long pidx(const DevInst& I, int y, int z, int col) {
+  return (long long)z * I.plane + (long long)y * I.px + col;
+}
+
+// P_CENSUS: operand x; g = Ax + b and everything Sec. 2 defines at x.
+struct OpCensus {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  double* g_out;
+  unsigned* m_out;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    ld2(x, pidx(I, y, z, e0), v0, v1, o);
+  }
+  __device__ double operand_at(long long i, int, int, int) const { return __ldg(x + i); }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const double v[2], const double av[2], Acc& acc) const {
+    double b[2], l[2], u[2], g[2];
+    ld2(I.b, i, v0, v1, b);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      g[k] = av[k] + b[k];
+      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool act = al || au;
+      const bool bind = (al && g[k] >= 0.0) || (au && g[k] <= 0.0);
+      fr[k] = ok && !act;
+      if (ok) {
+        const double pg = pg_comp(v[k], g[k], l[k], u[k]);
+        acc.s[0] = fma(pg, pg, acc.s[0]);
+        acc.s[1] = fma(v[k], g[k] + b[k], acc.s[1]);
+        if (!act) acc.s[2] = fma(g[k], g[k], acc.s[2]);
+        acc.c[0] += act;
+        acc.c[1] += bind;
+      }
+    }
+    st2(g_out, i, v0, v1, g[0], g[1]);
+    write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// P_GP_ALPHA: operand pg = grad_Omega q(x); sums <pg,pg> and <pg, A pg>.
+struct OpGpAlpha {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const double* __restrict__ g;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    double xv[2], gv[2], l[2], u[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(g, i, v0, v1, gv);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    o[0] = v0 ? pg_comp(xv[0], gv[0], l[0], u[0]) : 0.0;
+    o[1] = v1 ? pg_comp(xv[1], gv[1], l[1], u[1]) : 0.0;
+  }
+  __device__ double operand_at(long long i, int, int, int) const {
+    return pg_comp(__ldg(x + i), __ldg(g + i), __ldg(I.l + i), __ldg(I.u + i));
+  }
+  __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const double v[2],
+                         const double av[2], Acc& acc) const {
+    if (v0) {
+      acc.s[0] = fma(v[0], v[0], acc.s[0]);
+      acc.s[1] = fma(v[0], av[0], acc.s[1]);
+    }
+    if (v1) {
+      acc.s[0] = fma(v[1], v[1], acc.s[0]);
+      acc.s[1] = fma(v[1], av[1], acc.s[1]);
+    }
+  }
+};
+
+// P_TRIAL: operand xt = P[x + alpha*dir] (Eq. next-y with dir = -grad q, or
+// the projected search along d with dir = w); gt = A xt + b, the
+// sufficient-decrease terms <g, s> and <s, g + gt> (s = xt - x) and the
+// census of xt.
+template <int DK>
+struct OpTrial {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const double* __restrict__ g;
+  const double* __restrict__ w64;
+  const float* __restrict__ w32;
+  double alpha;
+  double* xt_out;
+  double* gt_out;
+  unsigned* m_out;
+  const unsigned* __restrict__ m_old;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ double trial(double xv, double dv, double l, double u) const {
+    return mid3(l, u, fma(alpha, dv, xv));
+  }
+  __device__ void dir2(long long i, bool v0, bool v1, double d[2]) const {
+    if (DK == D_NEG_G) {
+      ld2(g, i, v0, v1, d);
+      d[0] = -d[0];
+      d[1] = -d[1];
+    } else if (DK == D_W64) {
+      ld2(w64, i, v0, v1, d);
+    } else {
+      float f[2];
+      ld2(w32, i, v0, v1, f);
+      d[0] = (double)f[0];
+      d[1] = (double)f[1];
+    }
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    double xv[2], d[2], l[2], u[2];
+    ld2(x, i, v0, v1, xv);
+    dir2(i, v0, v1, d);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    o[0] = v0 ? trial(xv[0], d[0], l[0], u[0]) : 0.0;
+    o[1] = v1 ? trial(xv[1], d[1], l[1], u[1]) : 0.0;
+  }
+  __device__ double operand_at(long long i, int, int, int) const {
+    double dv;
+    if (DK == D_NEG_G) dv = -__ldg(g + i);
+    else if (DK == D_W64) dv = __ldg(w64 + i);
+    else dv = (double)__ldg(w32 + i);
+    return trial(__ldg(x + i), dv, __ldg(I.l + i), __ldg(I.u + i));
+  }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const double v[2], const double av[2], Acc& acc) const {
+    double xv[2], gv[2], b[2], l[2], u[2], gt[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(g, i, v0, v1, gv);
+    ld2(I.b, i, v0, v1, b);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      gt[k] = av[k] + b[k];
+      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool act = al || au;
+      const bool bind = (al && gt[k] >= 0.0) || (au && gt[k] <= 0.0);
+      fr[k] = ok && !act;
+      if (ok) {
+        const double s = v[k] - xv[k];
+        acc.s[3] = fma(gv[k], s, acc.s[3]);
+        acc.s[4] = fma(s, gv[k] + gt[k], acc.s[4]);
+        const double pg = pg_comp(v[k], gt[k], l[k], u[k]);
+        acc.s[0] = fma(pg, pg, acc.s[0]);
+        acc.s[1] = fma(v[k], gt[k] + b[k], acc.s[1]);
+        if (!act) acc.s[2] = fma(gt[k], gt[k], acc.s[2]);
+        acc.c[0] += act;
+        acc.c[1] += bind;
+      }
+    }
+    st2(xt_out, i, v0, v1, v[0], v[1]);
+    st2(gt_out, i, v0, v1, gt[0], gt[1]);
+    acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// P_CG_B: operand p = -r + beta*p_old (FIRST: p = -g on the free set), the
+// masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap>.  T is the
+// streamed precision (double, or float in the mixed CG).
+template <class TV, bool FIRST>
+struct OpCgB {
+  using T = TV;
+  const DevInst& I;
+  const T* __restrict__ r;
+  const T* __restrict__ p_old;
+  const double* __restrict__ g;
+  const unsigned* __restrict__ m;
+  T beta;
+  T* p_out;
+  T* ap_out;
+  T* r_out;
+  T* w_out;
+  const T* bd;
+  const T* bx;
+  const T* by;
+  const T* bz;
+  __device__ const T* diag() const { return bd; }
+  __device__ const T* cx() const { return bx; }
+  __device__ const T* cy() const { return by; }
+  __device__ const T* cz() const { return bz; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, T o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = T(0);
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    if (FIRST) {
+      double gv[2];
+      ld2(g, i, v0, v1, gv);
+      const unsigned fb = (v0 ? my_free_bits(I, m, y, z, e0) : 0u);
+      o[0] = (fb & 1u) ? (T)(-gv[0]) : T(0);
+      o[1] = (fb & 2u) ? (T)(-gv[1]) : T(0);
+    } else {
+      T rv[2], pv[2];
+      ld2(r, i, v0, v1, rv);
+      ld2(p_old, i, v0, v1, pv);
+      o[0] = fma(beta, pv[0], -rv[0]);
+      o[1] = fma(beta, pv[1], -rv[1]);
+    }
+  }
+  __device__ T operand_at(long long i, int y, int z, int col) const {
+    if (FIRST) {
+      return free_bit(I, m, y, z, col) ? (T)(-__ldg(g + i)) : T(0);
+    } else {
+      return fma(beta, __ldg(p_old + i), -__ldg(r + i));
+    }
+  }
+  __device__ void output(int y, int z, long long i, int, int e0, int, bool v0, bool v1,
+                         const T v[2], const T av[2], Acc& acc) const {
+    const unsigned fb = v0 ? my_free_bits(I, m, y, z, e0) : 0u;
+    const T a0 = (fb & 1u) ? av[0] : T(0);
+    const T a1 = (fb & 2u) ? av[1] : T(0);
+    st2(ap_out, i, v0, v1, a0, a1);
+    st2(p_out, i, v0, v1, v[0], v[1]);
+    acc.s[0] = fma((double)v[0], (double)a0, acc.s[0]);
+    acc.s[0] = fma((double)v[1], (double)a1, acc.s[0]);
+    if (FIRST) {
+      st2(r_out, i, v0, v1, -v[0], -v[1]);
+      st2(w_out, i, v0, v1, T(0), T(0));
+      acc.s[1] = fma((double)v[0], (double)v[0], acc.s[1]);
+      acc.s[1] = fma((double)v[1], (double)v[1], acc.s[1]);
+    }
+  }
+};
+
+// ---------------------------------------------------------- pointwise passes
+
+// P_CG_A: w += alpha p, r += alpha Ap, ||r||^2.
+template <class T>
+__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T* __restrict__ p,
+                                          const T* __restrict__ ap, double alpha, int x0, int y0,
+                                          int z, Acc& acc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (!v0) return;
+  const T a = (T)alpha;
+  for (int y = ya; y < yb; ++y) {
+    const long long i = pidx(I, y, z, e0);
+    T wv[2], rv[2], pv[2], av[2];
+    ld2(w, i, v0, v1, wv);
+    ld2(r, i, v0, v1, rv);
+    ld2(p, i, v0, v1, pv);
+    ld2(ap, i, v0, v1, av);
+    wv[0] = fma(a, pv[0], wv[0]);
+    wv[1] = fma(a, pv[1], wv[1]);
+    rv[0] = fma(a, av[0], rv[0]);
+    rv[1] = fma(a, av[1], rv[1]);
+    st2(w, i, v0, v1, wv[0], wv[1]);
+    st2(r, i, v0, v1, rv[0], rv[1]);
+    acc.s[0] = fma((double)rv[0], (double)rv[0], acc.s[0]);
+    acc.s[0] = fma((double)rv[1], (double)rv[1], acc.s[0]);
+  }
+}
+
+// P_START: x = P[x0], x0 the given start or the default l -> u -> 0.
+__device__ __forceinline__ void start_tile(const DevInst& I, double* x, int x0, int y0, int z) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (!v0) return;
+  for (int y = ya; y < yb; ++y) {
+    const long long i = pidx(I, y, z, e0);
+    double l[2], u[2], s[2];
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    if (I.opt.use_x0) {
+      ld2(I.x0, i, v0, v1, s);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) s[k] = isfinite(l[k]) ? l[k] : (isfinite(u[k]) ? u[k] : 0.0);
+    }
+    st2(x, i, v0, v1, mid3(l[0], u[0], s[0]), mid3(l[1], u[1], s[1]));
+  }
+}
+
+// ---------------------------------------------------------------- control --
+
+__device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
+  // algorithmic HBM bytes of one pass per valid point (documented per pass)
+  const double kc = (double)I.kc;
+  const double sv = C.cg32 ? 4.0 : 8.0;
+  double per = 0.0;
+  switch (pass) {
+    case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0); break;
+    case P_CENSUS: per = 8.0 * kc + 40.0 + 0.125; break;
+    case P_GP_ALPHA: per = 8.0 * kc + 32.0; break;
+    case P_TRIAL:
+      per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
+      break;
+    case P_CG_B: per = sv * kc + (C.first_cg ? 8.0 + 4.0 * sv : 4.0 * sv) + 0.125; break;
+    case P_CG_A: per = 6.0 * sv; break;
+    default: break;
+  }
+  return per * (double)I.n;
+}
+
+__device__ void set_done(Ctl& C, int status, int* live) {
+  C.status = status;
+  C.pass = P_NONE;
+  C.done = 1;
+  atomicSub(live, 1);
+}
+
+__device__ void start_search(Ctl& C, int dir) {
+  C.dir = dir;
+  C.alpha = dir == D_ZERO ? 0.0 : 1.0;
+  C.ls_i = 0;
+  C.trial_gp = 0;
+  C.pass = P_TRIAL;
+}
+
+// Start a CG phase on the face of the current iterate (Eq. cg, cg2), w0 = 0.
+__device__ void begin_cg(const DevInst& I, Ctl& C) {
+  C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
+  C.cg_j = 0;
+  C.cdmax = 0.0;
+  if (C.gF2 > 0.0 && I.opt.max_cg >= 1) {
+    C.first_cg = 1;
+    C.beta = 0.0;
+    C.pass = P_CG_B;
+  } else {
+    start_search(C, D_ZERO);
+  }
+}
+
+// Start outer iterate k (Algorithm GPCG): gradient projection unless the
+// previous iterate satisfied Eq. cgstop3.
+__device__ void begin_outer(const DevInst& I, Ctl& C, int* live) {
+  if (C.outer_iters >= I.opt.max_outer) {
+    set_done(C, S_MAXIT, live);
+    return;
+  }
+  C.outer_iters++;
+  if (!C.continue_cg) {
+    C.gp_j = 0;
+    C.dmax = 0.0;
+    C.pass = P_GP_ALPHA;
+  } else {
+    begin_cg(I, C);
+  }
+}
+
+// ||grad_Omega q|| <= tau held.  In mixed precision the first time this
+// happens starts the closing FP64 CG phase on the identified face.
+__device__ void on_converged(const DevInst& I, Ctl& C, int* live) {
+  if (I.opt.mixed && I.opt.refine && !C.refined) {
+    C.refined = 1;
+    C.refining = 1;
+    C.continue_cg = 1;
+    C.eta2 = I.opt.eta2_refine;
+    C.outer_iters++;
+    begin_cg(I, C);
+  } else {
+    set_done(C, S_OK, live);
+  }
+}
+
+__device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live) {
+  for (int k = 0; k < kNRed; ++k) C.red[k] = red[k];
+  if (C.hold) return;  // standalone timing/test launch: leave the state alone
+  const Opts& o = I.opt;
+  C.passes++;
+  C.alg_bytes += pass_bytes(I, C, C.pass);
+  switch (C.pass) {
+    case P_START:
+      C.pass = P_CENSUS;
+      break;
+    case P_CENSUS: {
+      C.pg2 = red[0];
+      C.xgb = red[1];
+      C.gF2 = red[2];
+      C.nA = red[5];
+      C.nB = red[6];
+      C.pg0 = sqrt(C.pg2);
+      C.tau = fmax(o.tau_abs, o.tau_rel * C.pg0);
+      C.eta2 = o.eta2;
+      C.continue_cg = 0;
+      if (!isfinite(C.pg2) || !isfinite(C.xgb)) {
+        set_done(C, S_NUMERIC, live);
+      } else if (C.pg0 <= C.tau) {
+        set_done(C, S_OK, live);
+      } else {
+        begin_outer(I, C, live);
+      }
+      break;
+    }
+    case P_GP_ALPHA: {
+      const double gg = red[0], gAg = red[1];
+      if (!(gAg > 0.0) || !isfinite(gg)) {
+        set_done(C, S_NUMERIC, live);
+        break;
+      }
+      C.alpha0 = gg / gAg;  // Eq. bqpls: exact minimiser along -grad_Omega q
+      C.alpha = C.alpha0;
+      C.ls_i = 0;
+      C.dir = D_NEG_G;
+      C.trial_gp = 1;
+      C.pass = P_TRIAL;
+      break;
+    }
+    case P_TRIAL: {
+      C.ls_trials++;
+      const double gs = red[3];
+      const double dq = 0.5 * red[4];  // q(xt) - q(x)
+      if (dq <= o.mu * gs) {           // Eq. gplsstop / cglsstop2
+        C.cur ^= 1;
+        C.pg2 = red[0];
+        C.xgb = red[1];
+        C.gF2 = red[2];
+        C.nA = red[5];
+        C.nB = red[6];
+        const double pgn = sqrt(C.pg2);
+        if (C.trial_gp) {
+          C.gp_iters++;
+          C.gp_j++;
+          const double dec = -dq;
+          const bool same = red[7] == 0.0;  // Eq. pgstop1
+          if (pgn <= C.tau) {
+            on_converged(I, C, live);
+            break;
+          }
+          const bool stop = same || (C.gp_j >= 2 && dec <= o.eta1 * C.dmax) ||  // Eq. pgstop2
+                            (C.gp_j >= o.max_gp);
+          if (dec > C.dmax) C.dmax = dec;
+          if (stop) {
+            begin_cg(I, C);
+          } else {
+            C.pass = P_GP_ALPHA;
+          }
+        } else {
+          C.refining = 0;
+          if (pgn <= C.tau) {
+            on_converged(I, C, live);
+            break;
+          }
+          if (C.nB == C.nA) {  // Eq. cgstop3: B(x) = A(x)
+            C.eta2 = fmax(C.eta2 * o.eta2_shrink, o.eta2_floor);
+            C.continue_cg = 1;
+          } else {
+            C.eta2 = o.eta2;
+            C.continue_cg = 0;
+          }
+          begin_outer(I, C, live);
+        }
+      } else {
+        C.ls_i++;
+        if (C.ls_i > o.max_ls) {
+          set_done(C, S_LINESEARCH, live);
+          break;
+        }
+        if (C.dir != D_ZERO) C.alpha = ldexp(C.trial_gp ? C.alpha0 : 1.0, -C.ls_i);
+      }
+      break;
+    }
+    case P_CG_B: {
+      if (C.first_cg) {
+        C.rr = red[1];
+        C.first_cg = 0;
+        if (!(C.rr > 0.0)) {  // the rounded free gradient vanished
+          C.pcur ^= 1;
+          start_search(C, D_ZERO);
+          break;
+        }
+      }
+      const double pAp = red[0];
+      if (!(pAp > 0.0)) {
+        set_done(C, S_NUMERIC, live);
+        break;
+      }
+      C.alpha = C.rr / pAp;
+      C.pcur ^= 1;
+      C.pass = P_CG_A;
+      break;
+    }
+    case P_CG_A: {
+      const double rr_new = red[0];
+      C.cg_j++;
+      C.cg_iters++;
+      if (C.refining) C.refine_cg_iters++;
+      const double delta = 0.5 * C.alpha * C.rr;  // q_k(w_{j-1}) - q_k(w_j)
+      const bool stop = (C.cg_j >= 2 && delta <= C.eta2 * C.cdmax) ||  // Eq. cgstop1
+                        rr_new == 0.0 || C.cg_j >= o.max_cg;
+      if (delta > C.cdmax) C.cdmax = delta;
+      if (stop) {
+        start_search(C, C.cg32 ? D_W32 : D_W64);
+      } else {
+        C.beta = rr_new / C.rr;
+        C.rr = rr_new;
+        C.pass = P_CG_B;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------ kernel --
+
+__device__ __forceinline__ void warp_sum(Acc& a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) a.s[k] += __shfl_xor_sync(FULL_MASK, a.s[k], off);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) a.c[k] = __reduce_add_sync(FULL_MASK, a.c[k]);
+}
+
+__global__ void __launch_bounds__(kThreads) pass_kernel(EngineArgs E) {
+  __shared__ double sred[kWarps][kNRed];
+  __shared__ int s_last;
+  __shared__ DevInst sI;
+  static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned np = atomicAdd(E.npass, 1u) + 1u;
+    if (E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
+      cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
+    }
+  }
+  const int2 tr = E.tiles[blockIdx.x];
+  Ctl& C = E.ctl[tr.x];
+  const int pass = C.pass;
+  if (pass == P_NONE) return;
+  if (threadIdx.x < sizeof(DevInst) / 8)
+    reinterpret_cast<long long*>(&sI)[threadIdx.x] =
+        reinterpret_cast<const long long*>(E.insts + tr.x)[threadIdx.x];
+  __syncthreads();
+  const DevInst& I = sI;
+
+  const int tile = tr.y;
+  const int tx = tile % I.tiles_x;
+  const int rest = tile / I.tiles_x;
+  const int x0 = tx * kTX;
+  const int y0 = (rest % I.tiles_y) * kTY;
+  const int z = rest / I.tiles_y;
+
+  Acc acc;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) acc.s[k] = 0.0;
+  acc.c[0] = acc.c[1] = acc.c[2] = 0;
+
+  const int cur = C.cur, pcur = C.pcur;
+  switch (pass) {
+    case P_START:
+      start_tile(I, I.x[cur], x0, y0, z);
+      break;
+    case P_CENSUS: {
+      OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur]};
+      stencil_tile(I, op, x0, y0, z, acc);
+      break;
+    }
+    case P_GP_ALPHA: {
+      OpGpAlpha op{I, I.x[cur], I.g[cur]};
+      stencil_tile(I, op, x0, y0, z, acc);
+      break;
+    }
+    case P_TRIAL: {
+      const int dir = C.dir;
+      const double alpha = dir == D_ZERO ? 0.0 : C.alpha;
+      if (dir == D_W64) {
+        OpTrial<D_W64> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                          I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else if (dir == D_W32) {
+        OpTrial<D_W32> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                          I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        OpTrial<D_NEG_G> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                            I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
+      break;
+    }
+    case P_CG_B: {
+      const bool first = C.first_cg;
+      if (C.cg32) {
+        if (first) {
+          OpCgB<float, true> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], 0.0f,
+                                I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
+                                I.diag32, I.cx32, I.cy32, I.cz32};
+          stencil_tile(I, op, x0, y0, z, acc);
+        } else {
+          OpCgB<float, false> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], (float)C.beta,
+                                 I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
+                                 I.diag32, I.cx32, I.cy32, I.cz32};
+          stencil_tile(I, op, x0, y0, z, acc);
+        }
+      } else {
+        if (first) {
+          OpCgB<double, true> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], 0.0,
+                                 I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
+                                 I.diag, I.cx, I.cy, I.cz};
+          stencil_tile(I, op, x0, y0, z, acc);
+        } else {
+          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], C.beta,
+                                  I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
+                                  I.diag, I.cx, I.cy, I.cz};
+          stencil_tile(I, op, x0, y0, z, acc);
+        }
+      }
+      break;
+    }
+    case P_CG_A:
+      if (C.cg32) {
+        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, C.alpha, x0, y0, z, acc);
+      } else {
+        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, C.alpha, x0, y0, z, acc);
+      }
+      break;
+    default:
+      break;
+  }
+
+  // fixed-order block reduction: lanes by xor butterfly, warps in order
+  warp_sum(acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sred[warp][k] = acc.s[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sred[warp][5 + k] = (double)acc.c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* P = I.part + (long long)tile * kNRed;
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += sred[w][k];
+      P[k] = v;
+    }
+    __threadfence();
+    const unsigned prev = atomicAdd(&C.arrive, 1u);
+    s_last = (prev == (unsigned)(I.n_tiles - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+
+  // last CTA of this instance: reduce the tile partials in a fixed order
+  __threadfence();
+  const double* P0 = I.part;
+  double part[kNRed];
+#pragma unroll
+  for (int k = 0; k < kNRed; ++k) part[k] = 0.0;
+  for (int t = threadIdx.x; t < I.n_tiles; t += kThreads) {
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) part[k] += __ldcg(P0 + (long long)t * kNRed + k);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) part[k] += __shfl_xor_sync(FULL_MASK, part[k], off);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) sred[warp][k] = part[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double red[kNRed];
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += sred[w][k];
+      red[k] = v;
+    }
+    C.arrive = 0u;
+    finalize(I, C, red, E.live);
+  }
+}
+
+// ------------------------------------------------------- set-up kernels --
+
+// Zero the couplings of the last point along each axis, fill missing bounds
+// and check the input; flags: 1 = non-finite b / coupling / NaN bound,
+// 2 = diag <= 0 or non-finite, 4 = empty box (l > u, l = +inf, u = -inf).
+__global__ void prep_kernel(DevInst I, double* cx, double* cy, double* cz, double* l, double* u,
+                            int fill_l, int fill_u, int* flags) {
+  const long long total = (long long)I.nx * I.ny * I.nz;
+  int f = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(t % I.nx);
+    const long long r = t / I.nx;
+    const int iy = (int)(r % I.ny);
+    const int iz = (int)(r / I.ny);
+    const long long i = pidx(I, iy, iz, ix);
+    if (fill_l) l[i] = -INFINITY;
+    if (fill_u) u[i] = INFINITY;
+    if (ix == I.nx - 1) cx[i] = 0.0;
+    if (iy == I.ny - 1) cy[i] = 0.0;
+    if (I.dim == 3 && iz == I.nz - 1) cz[i] = 0.0;
+    const double d = I.diag[i], b = I.b[i], lv = l[i], uv = u[i];
+    if (!isfinite(b) || !isfinite(cx[i]) || !isfinite(cy[i]) ||
+        (I.dim == 3 && !isfinite(cz[i])) || isnan(lv) || isnan(uv))
+      f |= 1;
+    if (!(d > 0.0) || !isfinite(d)) f |= 2;
+    if (lv > uv || lv == INFINITY || uv == -INFINITY) f |= 4;
+  }
+  if (f) atomicOr(flags, f);
+}
+
+__global__ void to_float_kernel(const double* __restrict__ src, float* dst, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = (float)src[t];
+}
+
+// Byte mask (unpadded, one byte per point) -> bit mask; and a value array
+// (unpadded FP64) -> -value on the free set in T (used by the masked
+// product entry point: p = -r + 0 * p_old with r = -p_F).
+template <class T>
+__global__ void spmv_setup_kernel(DevInst I, const uint8_t* __restrict__ fm,
+                                  const double* __restrict__ pv, unsigned* mask, T* r, T* pold) {
+  const long long rows = (long long)I.ny * I.nz;
+  const long long total = rows * I.mw;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / I.mw;
+    const int wcol = (int)(t % I.mw);
+    const int iy = (int)(row % I.ny), iz = (int)(row / I.ny);
+    unsigned word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int ix = wcol * 32 + b;
+      if (ix >= I.px) break;
+      const long long i = pidx(I, iy, iz, ix);
+      T rv = T(0);
+      if (ix < I.nx) {
+        const long long j = ((long long)iz * I.ny + iy) * I.nx + ix;
+        if (fm[j]) {
+          word |= 1u << b;
+          rv = (T)(-pv[j]);
+        }
+      }
+      r[i] = rv;
+      pold[i] = T(0);
+    }
+    mask[t] = word;
+  }
+}
+
+template __global__ void spmv_setup_kernel<double>(DevInst, const uint8_t*, const double*,
+                                                   unsigned*, double*, double*);
+template __global__ void spmv_setup_kernel<float>(DevInst, const uint8_t*, const double*,
+                                                  unsigned*, float*, float*);
+
+// Padded T array -> unpadded FP64 array.
+template <class T>
+__global__ void unpad_kernel(DevInst I, const T* __restrict__ src, double* dst) {
+  const long long total = (long long)I.nx * I.ny * I.nz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(t % I.nx);
+    const long long r = t / I.nx;
+    dst[t] = (double)src[pidx(I, (int)(r % I.ny), (int)(r / I.ny), ix)];
+  }
+}
+
+template __global__ void unpad_kernel<double>(DevInst, const double*, double*);
+template __global__ void unpad_kernel<float>(DevInst, const float*, double*);
+
+// ---------------------------------------------------------- host wrappers --
+
+const void* pass_kernel_ptr() { return (const void*)pass_kernel; }
+
+cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s) {
+  pass_kernel<<<n_blocks, kThreads, 0, s>>>(E);
+  return cudaGetLastError();
+}
+
+static int grid_for(long long work) {
+  long long b = (work + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 8192) b = 8192;
+  return (int)b;
+}
+
+cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
+                        int fill_l, int fill_u, int* flags, cudaStream_t s) {
+  prep_kernel<<<grid_for(I.n), 256, 0, s>>>(I, cx, cy, cz, l, u, fill_l, fill_u, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s) {
+  to_float_kernel<<<grid_for(count), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
+                              unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s) {
+  const long long work = (long long)I.ny * I.nz * I.mw;
+  if (f32)
+    spmv_setup_kernel<float><<<grid_for(work), 256, 0, s>>>(I, fm, pv, mask, (float*)r,
+                                                            (float*)pold);
+  else
+    spmv_setup_kernel<double><<<grid_for(work), 256, 0, s>>>(I, fm, pv, mask, (double*)r,
+                                                             (double*)pold);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpad(const DevInst& I, const void* src, bool f32, double* dst,
+                         cudaStream_t s) {
+  if (f32)
+    unpad_kernel<float><<<grid_for(I.n), 256, 0, s>>>(I, (const float*)src, dst);
+  else
+    unpad_kernel<double><<<grid_for(I.n), 256, 0, s>>>(I, (const double*)src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace gpcg

@@ -7,6 +7,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# bound every engine run in the test suite (a solve that needed more passes
+# than this would report GPCG_ERR_TIMEOUT instead of running on)
+os.environ.setdefault("GPCG_PASS_CAP", "400000")
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")

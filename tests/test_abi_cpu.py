@@ -1,0 +1,78 @@
+"""CPU-only checks of the C ABI: the library builds, loads, exports every
+symbol include/gpcg.h declares, and rejects bad arguments before touching the
+GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "gpcg.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpcg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("gpcg_problem_create", "gpcg_solve", "gpcg_result", "gpcg_solve_batch",
+                 "gpcg_masked_spmv", "gpcg_server_create", "gpcg_server_submit"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_cs_0101018_gb300 as g
+    L = g.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert b"sm_103a" in L.gpcg_version()
+
+
+def test_python_binding_covers_every_symbol():
+    from paper_cs_0101018_gb300 import gpcg
+    bound = {n for n, _, _ in gpcg._SIGNATURES}
+    assert set(_declared()) <= bound
+
+
+def test_default_options_are_the_papers():
+    import paper_cs_0101018_gb300 as g
+    o = g.default_options()
+    assert (o.eta1, o.eta2) == (0.1, 0.05)     # Sec. 5
+    assert 0 < o.mu < 0.5                      # Eq. gplsstop asks mu in (0, 1/2)
+    assert o.precision == g.FP64 and o.refine == 1
+
+
+def test_argument_checks_need_no_gpu():
+    import paper_cs_0101018_gb300 as g
+    L = g.load()
+    from paper_cs_0101018_gb300.gpcg import gpcg_stencil, gpcg_options
+    out = C.c_void_p()
+    # NULL stencil / bad dimensions are rejected before any CUDA call
+    assert L.gpcg_problem_create(None, None, None, None, 0.0, C.byref(out)) == g.ERR_ARG
+    st = gpcg_stencil(4, 2, 2, 1, None, None, None, None)
+    assert L.gpcg_problem_create(C.byref(st), None, None, None, 0.0, C.byref(out)) == g.ERR_ARG
+    st = gpcg_stencil(2, 2, 2, 3, None, None, None, None)
+    assert L.gpcg_problem_create(C.byref(st), None, None, None, 0.0, C.byref(out)) == g.ERR_ARG
+    assert b"" != L.gpcg_last_error()
+    o = g.default_options(mu=0.7)
+    assert L.gpcg_solve(None, C.byref(o)) == g.ERR_ARG
+    srv = C.c_void_p()
+    assert L.gpcg_server_create(0, 4, C.byref(o), C.byref(srv)) == g.ERR_ARG
+    o = g.default_options(mu=0.7)
+    assert L.gpcg_server_create(1 << 30, 4, C.byref(o), C.byref(srv)) == g.ERR_ARG
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle (C, gcc) and the CUDA library must not include each other."""
+    csrc = os.path.join(ROOT, "paper_cs_0101018_gb300", "csrc")
+    for fn in os.listdir(csrc):
+        with open(os.path.join(csrc, fn)) as f:
+            assert "oracle" not in f.read().lower(), fn
+    for fn in ("gpcg_oracle.c", "gpcg_oracle.h", "__init__.py", "brute_force.py"):
+        with open(os.path.join(ROOT, "oracle", fn)) as f:
+            txt = f.read()
+        assert "paper_cs_0101018_gb300" not in txt and "csrc" not in txt, fn

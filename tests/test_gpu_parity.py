@@ -1,0 +1,216 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (stated once, used everywhere below):
+  * FP64 mode: max_i |x_gpu - x_oracle| <= 1e-9 * max(1, ||x_oracle||_inf);
+    path parity (same GP / CG / search counts) on the same inputs.
+  * mixed mode: the same with 1e-5.
+  * active sets identical except for points whose oracle value lies within
+    1e-8 of a bound.
+  * masked product, FP64: |y_gpu - y_oracle|_i <= 8 eps64 (|A| |p|)_i (forward
+    error of a dot product of at most 7 terms, with margin); mixed (FP32
+    streams): <= 8 eps32 (|A| |p|)_i + the error of rounding A and p to FP32.
+"""
+import numpy as np
+import pytest
+
+import gpcg_inputs as gi
+import oracle
+
+g = pytest.importorskip("paper_cs_0101018_gb300")
+
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+def _solve(qp, **opts):
+    prob = g.gpcg_problem_create(qp)
+    status = g.gpcg_solve(prob, g.default_options(**opts), check=False)
+    x, st = g.gpcg_result(prob)
+    return status, x, st
+
+
+def _rel_err(x, ref):
+    return float(np.max(np.abs(x - ref)) / max(1.0, float(np.max(np.abs(ref)))))
+
+
+def _active_sets_agree(qp, x, ref, band=1e-8):
+    act_g = (x == qp.l) | (x == qp.u)
+    act_o = (ref == qp.l) | (ref == qp.u)
+    near = (np.abs(ref - qp.l) <= band) | (np.abs(ref - qp.u) <= band)
+    return bool(np.all((act_g == act_o) | near))
+
+
+def _problems():
+    out = [gi.single_small()]
+    for k, (nx, ny) in enumerate([(1, 1), (1, 37), (37, 1), (65, 33), (100, 70), (64, 32),
+                                  (129, 5), (3, 200)]):
+        for bounds in ("lower0", "two_sided", "box1"):
+            out.append(gi.grid_qp_2d(nx, ny, seed=200 + k, shift=0.02, bounds=bounds))
+    for k, (nx, ny, nz) in enumerate([(1, 1, 1), (5, 4, 3), (17, 9, 6), (70, 33, 4)]):
+        out.append(gi.grid_qp_3d(nx, ny, nz, seed=300 + k, shift=0.02, sigma=0.5,
+                                 axis_scale=(1.0, 3.0, 9.0), bounds="box1"))
+    qp = gi.grid_qp_2d(50, 41, seed=400, shift=0.02, bounds="two_sided")
+    qp.l[::7] = -np.inf
+    qp.u[::11] = np.inf
+    qp.l[3::13] = qp.u[3::13]
+    out.append(qp)
+    out.append(gi.grid_qp_2d(40, 30, seed=401, shift=0.05, bounds="none"))
+    return out
+
+
+PROBLEMS = _problems()
+
+
+@pytest.mark.parametrize("k", range(len(PROBLEMS)))
+def test_fp64_matches_oracle(k):
+    qp = PROBLEMS[k]
+    ref = oracle.solve(qp, tau_rel=1e-10)
+    status, x, st = _solve(qp, tau_rel=1e-10)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= 1e-9
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    # path parity: the same decisions give the same counts
+    for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
+        assert st[key] == ref.stats[key], (key, st[key], ref.stats[key])
+    assert st["n_active"] == ref.stats["n_active"]
+    assert st["n_binding"] == ref.stats["n_binding"]
+    assert st["pg_norm"] <= st["tau"]
+    assert np.isclose(st["q"], ref.stats["q"], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", range(len(PROBLEMS)))
+def test_mixed_matches_oracle(k):
+    qp = PROBLEMS[k]
+    ref = oracle.solve(qp, tau_rel=1e-10)
+    status, x, st = _solve(qp, tau_rel=1e-10, precision=g.MIXED)
+    assert status == 0
+    assert _rel_err(x, ref.x) <= 1e-5
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    # the termination test is evaluated in FP64 on the returned point
+    c = oracle.census(qp, x)
+    assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
+
+
+def test_single_small_workload_fp64_and_mixed():
+    qp = gi.single_small()
+    ref = oracle.solve(qp, tau_rel=1e-8)
+    for prec, tol in ((g.FP64, 1e-9), (g.MIXED, 1e-5)):
+        status, x, st = _solve(qp, tau_rel=1e-8, precision=prec)
+        assert status == 0 and _rel_err(x, ref.x) <= tol
+        assert _active_sets_agree(qp, x, ref.x)
+
+
+def _abs_a_abs_p(qp, fm, p):
+    """(|A_FF| |p_F|) through the oracle's masked product on |bands|."""
+    aq = gi.QP(qp.dim, qp.nx, qp.ny, qp.nz, np.abs(qp.diag), np.abs(qp.cx), np.abs(qp.cy),
+               None if qp.cz is None else np.abs(qp.cz), qp.b, qp.l, qp.u)
+    return oracle.masked_matvec(aq, fm, np.abs(p))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 3, 1), (65, 33, 1), (200, 97, 1),
+                                   (33, 17, 5)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_masked_spmv_matches_oracle(shape, prec):
+    nx, ny, nz = shape
+    qp = (gi.grid_qp_2d(nx, ny, seed=7, shift=0.1) if nz == 1 else
+          gi.grid_qp_3d(nx, ny, nz, seed=7, shift=0.1, axis_scale=(1, 10, 100)))
+    fm = gi.uniform(8, 1, qp.n) < 0.6
+    p = gi.normal(8, 2, qp.n)
+    prob = g.gpcg_problem_create(qp)
+    y, pap = g.gpcg_masked_spmv(prob, fm, p, precision=prec)
+    ref = oracle.masked_matvec(qp, fm, p)
+    bound = _abs_a_abs_p(qp, fm, p)
+    if prec == g.FP64:
+        assert np.all(np.abs(y - ref) <= 8 * EPS64 * bound + 1e-300)
+        assert np.isclose(pap, float(np.dot(p * fm, ref)), rtol=1e-12, atol=1e-12)
+    else:
+        # FP32 bands and p: each product carries <= 3 eps32 relative error
+        assert np.all(np.abs(y - ref) <= 12 * EPS32 * bound + 1e-30)
+        assert np.isclose(pap, float(np.dot(p * fm, ref)), rtol=1e-5)
+    assert np.all(y[~fm] == 0.0)
+
+
+def test_batch_is_bitwise_identical_to_alone():
+    qps = [gi.grid_qp_2d(s, s + 3, seed=500 + s, shift=0.01,
+                         bounds="two_sided" if s % 2 else "lower0") for s in (8, 33, 64, 97)]
+    qps.append(gi.grid_qp_3d(9, 8, 7, seed=599, shift=0.02, bounds="box1"))
+    for prec in (g.FP64, g.MIXED):
+        opts = g.default_options(tau_rel=1e-9, precision=prec)
+        alone = []
+        for qp in qps:
+            prob = g.gpcg_problem_create(qp)
+            g.gpcg_solve(prob, opts)
+            alone.append(g.gpcg_result(prob))
+        probs = [g.gpcg_problem_create(qp) for qp in qps]
+        g.gpcg_solve_batch(probs, opts)
+        for prob, (xa, sa) in zip(probs, alone):
+            xb, sb = g.gpcg_result(prob)
+            assert np.array_equal(xa, xb)
+            assert sa["cg_iters"] == sb["cg_iters"] and sa["passes"] == sb["passes"]
+
+
+def test_engine_modes_agree(monkeypatch):
+    qp = gi.grid_qp_2d(90, 70, seed=610, shift=0.01, bounds="two_sided")
+    res = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("GPCG_ENGINE_MODE", mode)
+        status, x, st = _solve(qp, tau_rel=1e-9)
+        assert status == 0
+        res.append((x, st))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1]["passes"] == res[1][1]["passes"]
+
+
+def test_x0_and_device_arrays():
+    import torch
+    qp = gi.grid_qp_2d(48, 40, seed=620, shift=0.02, bounds="box1")
+    x0 = gi.uniform(620, 9, qp.n, -2, 2)
+    ref = oracle.solve(qp, x0=x0, tau_rel=1e-10)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prob = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, diag=dev(qp.diag), cx=dev(qp.cx),
+                                 cy=dev(qp.cy), b=dev(qp.b), l=dev(qp.l), u=dev(qp.u))
+    g.gpcg_solve(prob, g.default_options(tau_rel=1e-10, x0=dev(x0)))
+    xd = torch.empty(qp.n, dtype=torch.float64, device="cuda")
+    g.gpcg_result(prob, xd)
+    assert _rel_err(xd.cpu().numpy(), ref.x) <= 1e-9
+
+
+def test_argument_errors():
+    qp = gi.grid_qp_2d(10, 10, seed=630, shift=0.1, bounds="two_sided")
+    bad = gi.grid_qp_2d(10, 10, seed=630, shift=0.1, bounds="two_sided")
+    bad.l[5] = bad.u[5] + 1.0
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_problem_create(bad)
+    assert e.value.status == g.ERR_INFEASIBLE
+    bad = gi.grid_qp_2d(10, 10, seed=630, shift=0.1)
+    bad.b[3] = np.nan
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_problem_create(bad)
+    assert e.value.status == g.ERR_ARG
+    bad = gi.grid_qp_2d(10, 10, seed=630, shift=0.1)
+    bad.diag[0] = 0.0
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_problem_create(bad)
+    assert e.value.status == g.ERR_ARG
+    # indefinite A (diag > 0 but not positive definite) is caught lazily
+    ind = gi.grid_qp_2d(10, 10, seed=631, shift=0.1, bounds="none")
+    ind.diag[:] = 0.5
+    prob = g.gpcg_problem_create(ind)
+    assert g.gpcg_solve(prob, g.default_options(), check=False) == g.ERR_NUMERIC
+    prob = g.gpcg_problem_create(qp)
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_result(prob)
+    assert e.value.status == g.ERR_PENDING
+
+
+def test_caps_give_distinct_statuses():
+    qp = gi.grid_qp_2d(60, 60, seed=640, shift=0.001, bounds="two_sided")
+    prob = g.gpcg_problem_create(qp)
+    s = g.gpcg_solve(prob, g.default_options(tau_rel=1e-12, max_outer=1), check=False)
+    assert s == g.ERR_MAXIT
+    _, st = g.gpcg_result(prob)
+    assert st["outer_iters"] == 1 and st["status"] == g.ERR_MAXIT
