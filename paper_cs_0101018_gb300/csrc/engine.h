@@ -26,7 +26,8 @@ constexpr int kRY = 4;           // rows per warp
 constexpr int kWarps = 8;        // warps per CTA
 constexpr int kTY = kRY * kWarps;  // tile height (rows)
 constexpr int kThreads = 32 * kWarps;
-constexpr int kNRed = 8;         // partial sums per tile
+constexpr int kNRed = 8;         // partial sums per tile: 4 FP64 sums, 3 counts, 1 spare
+constexpr int kMinBlocks = 3;    // resident CTAs per SM the pass kernel is compiled for
 
 enum Pass : int {
   P_NONE = 0,
@@ -60,7 +61,7 @@ struct Opts {
 // Mutable per-instance state, owned by the finalizer of each pass.
 struct Ctl {
   int pass, status, done, cur, pcur, cg32, first_cg, dir;
-  int trial_gp, refining, refined, continue_cg, hold, pad0;
+  int trial_gp, refining, refined, continue_cg, hold, final_census;
   int outer_iters, gp_j, ls_i, cg_j, gp_iters, cg_iters, ls_trials, refine_cg_iters;
   int passes, pad1;
   unsigned arrive, pad2;
@@ -86,7 +87,10 @@ struct DevInst {
 struct EngineArgs {
   const DevInst* insts;
   Ctl* ctl;
-  const int2* tiles;      // (instance slot, tile) per CTA
+  const int2* tiles;      // (instance slot, tile) work items of the launch
+  int n_work;             // number of work items
+  int* queue;             // next work item (dynamic scheduling; reset by the last CTA)
+  unsigned* exits;        // CTAs that found the queue empty
   int* live;              // instances not yet done
   unsigned* npass;        // launches so far (block 0 increments)
   unsigned pass_cap;      // launches after which the loop condition is cleared

@@ -21,6 +21,7 @@
 
 namespace gpcg {
 const void* pass_kernel_ptr();
+int pass_grid(int n_work);
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s);
 cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
                         int fill_l, int fill_u, int* flags, cudaStream_t s);
@@ -76,6 +77,7 @@ struct Scratch {
   int2* d_tiles = nullptr;
   int* d_live = nullptr;
   unsigned* d_npass = nullptr;
+  int* d_queue = nullptr;     // [0] work queue head, [1] exit counter (zero between launches)
   int* h_pin = nullptr;  // pinned: [0] live, [1] npass
   int cap_inst = 0;
   long long cap_tiles = 0;
@@ -92,7 +94,9 @@ struct Scratch {
     cudaFree(d_tiles);
     cudaFree(d_live);
     cudaFree(d_npass);
+    cudaFree(d_queue);
     if (h_pin) cudaFreeHost(h_pin);
+    d_queue = nullptr;
     d_insts = nullptr;
     d_ctl = nullptr;
     d_tiles = nullptr;
@@ -108,6 +112,8 @@ struct Scratch {
       CK(cudaMallocHost(&h_pin, 4 * sizeof(int)));
       CK(cudaMalloc(&d_live, sizeof(int)));
       CK(cudaMalloc(&d_npass, sizeof(unsigned)));
+      CK(cudaMalloc(&d_queue, 2 * sizeof(int)));
+      CK(cudaMemset(d_queue, 0, 2 * sizeof(int)));
     }
     if (n_inst > cap_inst) {
       cudaFree(d_insts);
@@ -417,7 +423,8 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps))
     return GPCG_OK;
   sc.invalidate();
-  EngineArgs args{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, cap, 0ull};
+  EngineArgs args{sc.d_insts, sc.d_ctl,     sc.d_tiles, (int)tiles, sc.d_queue,
+                  (unsigned*)(sc.d_queue + 1), sc.d_live, sc.d_npass, cap, 0ull};
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   cudaGraph_t body = g;
@@ -451,7 +458,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   cudaKernelNodeParams k;
   memset(&k, 0, sizeof(k));
   k.func = const_cast<void*>(pass_kernel_ptr());
-  k.gridDim = dim3((unsigned)tiles);
+  k.gridDim = dim3((unsigned)pass_grid((int)tiles));
   k.blockDim = dim3(kThreads);
   k.sharedMemBytes = 0;
   k.kernelParams = kp;
@@ -653,8 +660,9 @@ static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
   sc.h_pin[1] = 0;
   CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
-  EngineArgs E{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, 0xffffffffu, 0ull};
-  CK(launch_pass(E, p->n_tiles, s));
+  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles, p->n_tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+               sc.d_live,   sc.d_npass, 0xffffffffu, 0ull};
+  CK(launch_pass(E, pass_grid(p->n_tiles), s));
   if (out) {
     CK(cudaMemcpyAsync(out, sc.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -781,12 +789,14 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
   // one untimed launch sets up the tables, then `reps` timed launches
   if ((st = one_pass(p, spmv_ctl(f32, cur, 0), s, nullptr)) != GPCG_OK) return st;
   Scratch& sc = p->sc;
-  EngineArgs E{sc.d_insts, sc.d_ctl, sc.d_tiles, sc.d_live, sc.d_npass, 0xffffffffu, 0ull};
+  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles, p->n_tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+               sc.d_live,   sc.d_npass, 0xffffffffu, 0ull};
+  const int grid = pass_grid(p->n_tiles);
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
-  for (int k = 0; k < reps; ++k) CK(launch_pass(E, p->n_tiles, s));
+  for (int k = 0; k < reps; ++k) CK(launch_pass(E, grid, s));
   CK(cudaEventRecord(e1, s));
   CK(cudaEventSynchronize(e1));
   float ms = 0.f;

@@ -1,20 +1,30 @@
 // gpcg_kernels.cu -- device side of the GB300 GPCG engine.
 //
 // One kernel, pass_kernel, runs every pass of Algorithm GPCG (Sec. 3 of
-// Benson, McInnes & More) for every live instance: each CTA takes one 64x32
-// tile (one plane of a 3-D grid) of one instance, performs the pass the
-// instance's state machine asks for, and deposits its partial sums in a fixed
-// slot.  The last CTA of an instance reduces those slots in a fixed order and
-// runs the state-machine transition (finalize below), so the arithmetic of an
-// instance does not depend on the other instances in the launch.
+// Benson, McInnes & More) for every live instance.  The grid is persistent
+// (a few CTAs per SM); CTAs pull work items -- one 64x32 tile of one plane of
+// one instance -- from a queue, perform the pass the instance's state machine
+// asks for, and deposit the tile's partial sums in the tile's own slot.  The
+// last CTA to finish a tile of an instance reduces that instance's slots in a
+// fixed order and runs the state-machine transition (finalize below), so an
+// instance's arithmetic depends only on the instance, never on the schedule or
+// on the other instances in the launch.
 //
-// The stencil passes stream each operand once: a warp walks down its 64-column
+// Stencil passes stream each operand once: a warp walks down its 64-column
 // strip keeping the operand of rows y-1, y, y+1 in registers; east/west
 // neighbours come from the adjacent lane by shuffle (lanes 0 and 31 load the
-// one point beyond the strip), and the up/down planes of a 3-D grid are
-// loaded directly.  The operand of a pass is computed from its inputs on the
-// fly (for example p = -r + beta*p in the CG pass, or P[x + alpha*d] in a
-// trial), so no pass writes a vector that another CTA of the same launch reads.
+// point beyond the strip), and the planes above/below of a 3-D grid are
+// loaded directly.  The operand is computed from its inputs on the fly (for
+// example p = -r + beta*p in the CG pass, or P[x + alpha*d] in a trial), so no
+// pass writes a vector that another CTA of the same launch reads.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 work is
+// kept to the arithmetic the method needs: comparisons against the bounds and
+// sign tests are done on the IEEE bit patterns with integer instructions, the
+// FP32 passes accumulate their dot products with error-free transformations
+// in FP32 (Ogita, Rump & Oishi, "Accurate sum and dot product", SISC 2005,
+// algorithm Dot2) and convert to FP64 once per thread and tile, and the
+// per-tile reduction runs through shared memory with one warp.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,22 +35,76 @@ namespace gpcg {
 
 #define FULL_MASK 0xffffffffu
 
-// ---------------------------------------------------------------- helpers --
+// ------------------------------------------------- FP64 tests on the bits --
+// Inputs are checked to be NaN-free when a problem is created, so every value
+// reaching these helpers is a number.
 
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Integer key with the order of the doubles (-0 sorts just below +0).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// a == b as numbers (+0 == -0).
+__device__ __forceinline__ bool deq(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  return x == y || ((x | y) << 1) == 0;
+}
+
+constexpr long long kNegZero = (long long)0x8000000000000000ULL;
+__device__ __forceinline__ bool dge0(double a) {
+  const long long x = dbits(a);
+  return x >= 0 || x == kNegZero;
+}
+__device__ __forceinline__ bool dle0(double a) { return dbits(a) <= 0; }
+__device__ __forceinline__ bool dlt0(double a) {
+  const long long x = dbits(a);
+  return x < 0 && x != kNegZero;
+}
+__device__ __forceinline__ bool dgt0(double a) { return dbits(a) > 0; }
+
+// median of {l, u, x} for l <= u: the projection P of Sec. 3; returns l or u
+// bit for bit when x lies outside [l, u]
 __device__ __forceinline__ double mid3(double l, double u, double x) {
-  // median of {l, u, x} for l <= u: the projection P of Sec. 3
-  return x < l ? l : (x > u ? u : x);
+  const long long kx = dkey(x);
+  if (kx < dkey(l)) return l;
+  if (kx > dkey(u)) return u;
+  return x;
 }
 
 // Projected gradient component, Eq. proj-gradient; a fixed variable
 // (l == u) has component 0.
 __device__ __forceinline__ double pg_comp(double x, double g, double l, double u) {
-  const bool al = (x == l), au = (x == u);
+  const bool al = deq(x, l), au = deq(x, u);
   if (al && au) return 0.0;
-  if (al) return g < 0.0 ? g : 0.0;
-  if (au) return g > 0.0 ? g : 0.0;
+  if (al) return dlt0(g) ? g : 0.0;
+  if (au) return dgt0(g) ? g : 0.0;
   return g;
 }
+
+// ---------------------------------------------- FP32 compensated dot (Dot2) --
+
+struct FF {
+  float hi, lo;
+};
+
+// s += a*b with the product error (TwoProduct by FMA) and the addition error
+// (TwoSum) accumulated in s.lo.
+__device__ __forceinline__ void ff_fma(FF& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s.hi, p);
+  const float z = __fsub_rn(t, s.hi);
+  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(pe, e));
+}
+
+__device__ __forceinline__ double ff_val(const FF& s) { return (double)s.hi + (double)s.lo; }
+
+// --------------------------------------------------------- memory helpers --
 
 __device__ __forceinline__ void ld2(const double* __restrict__ p, long long i, bool v0, bool v1,
                                     double o[2]) {
@@ -92,13 +156,28 @@ __device__ __forceinline__ unsigned spread16(unsigned v) {
   return v;
 }
 
+// Per-thread partial results of a pass: up to 4 FP64 sums and 3 counts.
 struct Acc {
-  double s[5];
+  double s[4];
   int c[3];
+};
+
+// What a tile needs from the instance's control block (read once per tile).
+struct Snap {
+  int pass, cur, pcur, cg32, first_cg, dir;
+  double alpha, beta;
 };
 
 __device__ __forceinline__ long long row_index(const DevInst& I, int y, int z) {
   return (long long)z * I.ny + y;
+}
+
+__device__ __forceinline__ bool row_ok(const DevInst& I, int y, int z) {
+  return y >= 0 && y < I.ny && z >= 0 && z < I.nz;
+}
+
+__device__ __forceinline__ long long pidx(const DevInst& I, int y, int z, int col) {
+  return (long long)z * I.plane + (long long)y * I.px + col;
 }
 
 // The two free bits of this lane's points (e0, e0+1) in row (y, z).
@@ -165,6 +244,7 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
   } else {
     cs[0] = cs[1] = T(0);
   }
+#pragma unroll 1
   for (int y = ya; y < yb; ++y) {
     op.operand_row(y + 1, z, e0, v0, v1, vn);
     const long long i = zb + (long long)y * I.px + e0;
@@ -218,15 +298,8 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
   }
 }
 
-__device__ __forceinline__ bool row_ok(const DevInst& I, int y, int z) {
-  return y >= 0 && y < I.ny && z >= 0 && z < I.nz;
-}
-
-__device__ __forceinline__ long long pidx(const DevInst& I, int y, int z, int col) {
-  return (long long)z * I.plane + (long long)y * I.px + col;
-}
-
-// P_CENSUS: operand x; g = Ax + b and everything Sec. 2 defines at x.
+// P_CENSUS: operand x; g = Ax + b and everything Sec. 2 defines at x:
+// sums ||pg||^2 and <x, g + b> (= 2 (q - c)), counts |A(x)| and |B(x)|.
 struct OpCensus {
   using T = double;
   const DevInst& I;
@@ -256,15 +329,14 @@ struct OpCensus {
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
       g[k] = av[k] + b[k];
-      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool al = deq(v[k], l[k]), au = deq(v[k], u[k]);
       const bool act = al || au;
-      const bool bind = (al && g[k] >= 0.0) || (au && g[k] <= 0.0);
+      const bool bind = (al && dge0(g[k])) || (au && dle0(g[k]));
       fr[k] = ok && !act;
       if (ok) {
         const double pg = pg_comp(v[k], g[k], l[k], u[k]);
         acc.s[0] = fma(pg, pg, acc.s[0]);
         acc.s[1] = fma(v[k], g[k] + b[k], acc.s[1]);
-        if (!act) acc.s[2] = fma(g[k], g[k], acc.s[2]);
         acc.c[0] += act;
         acc.c[1] += bind;
       }
@@ -315,9 +387,10 @@ struct OpGpAlpha {
 };
 
 // P_TRIAL: operand xt = P[x + alpha*dir] (Eq. next-y with dir = -grad q, or
-// the projected search along d with dir = w); gt = A xt + b, the
-// sufficient-decrease terms <g, s> and <s, g + gt> (s = xt - x) and the
-// census of xt.
+// the projected search along d with dir = w); gt = A xt + b; sums <g, s> and
+// <s, gt> with s = xt - x (q(xt) - q(x) = 1/2 (<g,s> + <s,gt>) exactly for a
+// quadratic) and ||grad_Omega q(xt)||^2; counts |A(xt)|, |B(xt)| and the
+// number of points whose active/free status changed (Eq. pgstop1).
 template <int DK>
 struct OpTrial {
   using T = double;
@@ -335,9 +408,6 @@ struct OpTrial {
   __device__ const double* cx() const { return I.cx; }
   __device__ const double* cy() const { return I.cy; }
   __device__ const double* cz() const { return I.cz; }
-  __device__ double trial(double xv, double dv, double l, double u) const {
-    return mid3(l, u, fma(alpha, dv, xv));
-  }
   __device__ void dir2(long long i, bool v0, bool v1, double d[2]) const {
     if (DK == D_NEG_G) {
       ld2(g, i, v0, v1, d);
@@ -363,15 +433,15 @@ struct OpTrial {
     dir2(i, v0, v1, d);
     ld2(I.l, i, v0, v1, l);
     ld2(I.u, i, v0, v1, u);
-    o[0] = v0 ? trial(xv[0], d[0], l[0], u[0]) : 0.0;
-    o[1] = v1 ? trial(xv[1], d[1], l[1], u[1]) : 0.0;
+    o[0] = v0 ? mid3(l[0], u[0], fma(alpha, d[0], xv[0])) : 0.0;
+    o[1] = v1 ? mid3(l[1], u[1], fma(alpha, d[1], xv[1])) : 0.0;
   }
   __device__ double operand_at(long long i, int, int, int) const {
     double dv;
     if (DK == D_NEG_G) dv = -__ldg(g + i);
     else if (DK == D_W64) dv = __ldg(w64 + i);
     else dv = (double)__ldg(w32 + i);
-    return trial(__ldg(x + i), dv, __ldg(I.l + i), __ldg(I.u + i));
+    return mid3(__ldg(I.l + i), __ldg(I.u + i), fma(alpha, dv, __ldg(x + i)));
   }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const double v[2], const double av[2], Acc& acc) const {
@@ -386,18 +456,16 @@ struct OpTrial {
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
       gt[k] = av[k] + b[k];
-      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool al = deq(v[k], l[k]), au = deq(v[k], u[k]);
       const bool act = al || au;
-      const bool bind = (al && gt[k] >= 0.0) || (au && gt[k] <= 0.0);
+      const bool bind = (al && dge0(gt[k])) || (au && dle0(gt[k]));
       fr[k] = ok && !act;
       if (ok) {
         const double s = v[k] - xv[k];
-        acc.s[3] = fma(gv[k], s, acc.s[3]);
-        acc.s[4] = fma(s, gv[k] + gt[k], acc.s[4]);
+        acc.s[0] = fma(gv[k], s, acc.s[0]);
+        acc.s[1] = fma(s, gt[k], acc.s[1]);
         const double pg = pg_comp(v[k], gt[k], l[k], u[k]);
-        acc.s[0] = fma(pg, pg, acc.s[0]);
-        acc.s[1] = fma(v[k], gt[k] + b[k], acc.s[1]);
-        if (!act) acc.s[2] = fma(gt[k], gt[k], acc.s[2]);
+        acc.s[2] = fma(pg, pg, acc.s[2]);
         acc.c[0] += act;
         acc.c[1] += bind;
       }
@@ -409,11 +477,13 @@ struct OpTrial {
 };
 
 // P_CG_B: operand p = -r + beta*p_old (FIRST: p = -g on the free set), the
-// masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap>.  T is the
-// streamed precision (double, or float in the mixed CG).
+// masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap> (FIRST: also
+// ||r||^2 for r = g_F).  TV is the streamed precision (double, or float in the
+// mixed CG, whose sums use the compensated FP32 accumulator).
 template <class TV, bool FIRST>
 struct OpCgB {
   using T = TV;
+  static constexpr bool kF32 = sizeof(TV) == 4;
   const DevInst& I;
   const T* __restrict__ r;
   const T* __restrict__ p_old;
@@ -428,6 +498,7 @@ struct OpCgB {
   const T* bx;
   const T* by;
   const T* bz;
+  FF* ff;  // [2] FP32 accumulators (kF32)
   __device__ const T* diag() const { return bd; }
   __device__ const T* cx() const { return bx; }
   __device__ const T* cy() const { return by; }
@@ -466,13 +537,23 @@ struct OpCgB {
     const T a1 = (fb & 2u) ? av[1] : T(0);
     st2(ap_out, i, v0, v1, a0, a1);
     st2(p_out, i, v0, v1, v[0], v[1]);
-    acc.s[0] = fma((double)v[0], (double)a0, acc.s[0]);
-    acc.s[0] = fma((double)v[1], (double)a1, acc.s[0]);
+    if (kF32) {
+      ff_fma(ff[0], (float)v[0], (float)a0);
+      ff_fma(ff[0], (float)v[1], (float)a1);
+    } else {
+      acc.s[0] = fma((double)v[0], (double)a0, acc.s[0]);
+      acc.s[0] = fma((double)v[1], (double)a1, acc.s[0]);
+    }
     if (FIRST) {
       st2(r_out, i, v0, v1, -v[0], -v[1]);
       st2(w_out, i, v0, v1, T(0), T(0));
-      acc.s[1] = fma((double)v[0], (double)v[0], acc.s[1]);
-      acc.s[1] = fma((double)v[1], (double)v[1], acc.s[1]);
+      if (kF32) {
+        ff_fma(ff[1], (float)v[0], (float)v[0]);
+        ff_fma(ff[1], (float)v[1], (float)v[1]);
+      } else {
+        acc.s[1] = fma((double)v[0], (double)v[0], acc.s[1]);
+        acc.s[1] = fma((double)v[1], (double)v[1], acc.s[1]);
+      }
     }
   }
 };
@@ -492,6 +573,7 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T*
   const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
   if (!v0) return;
   const T a = (T)alpha;
+  FF ff{0.f, 0.f};
   for (int y = ya; y < yb; ++y) {
     const long long i = pidx(I, y, z, e0);
     T wv[2], rv[2], pv[2], av[2];
@@ -505,9 +587,15 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T*
     rv[1] = fma(a, av[1], rv[1]);
     st2(w, i, v0, v1, wv[0], wv[1]);
     st2(r, i, v0, v1, rv[0], rv[1]);
-    acc.s[0] = fma((double)rv[0], (double)rv[0], acc.s[0]);
-    acc.s[0] = fma((double)rv[1], (double)rv[1], acc.s[0]);
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)rv[0], (float)rv[0]);
+      ff_fma(ff, (float)rv[1], (float)rv[1]);
+    } else {
+      acc.s[0] = fma((double)rv[0], (double)rv[0], acc.s[0]);
+      acc.s[0] = fma((double)rv[1], (double)rv[1], acc.s[0]);
+    }
   }
+  if (sizeof(T) == 4) acc.s[0] += ff_val(ff);
 }
 
 // P_START: x = P[x0], x0 the given start or the default l -> u -> 0.
@@ -537,7 +625,8 @@ __device__ __forceinline__ void start_tile(const DevInst& I, double* x, int x0, 
 // ---------------------------------------------------------------- control --
 
 __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
-  // algorithmic HBM bytes of one pass per valid point (documented per pass)
+  // algorithmic HBM bytes of one pass per valid point: every array the pass
+  // must read or write, once (documented per pass in the design notes)
   const double kc = (double)I.kc;
   const double sv = C.cg32 ? 4.0 : 8.0;
   double per = 0.0;
@@ -555,11 +644,12 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   return per * (double)I.n;
 }
 
-__device__ void set_done(Ctl& C, int status, int* live) {
+// End the solve with `status`: one final census pass refreshes g, the active
+// and binding counts, ||pg|| and q at the returned point.
+__device__ void set_done(Ctl& C, int status) {
   C.status = status;
-  C.pass = P_NONE;
-  C.done = 1;
-  atomicSub(live, 1);
+  C.final_census = 1;
+  C.pass = P_CENSUS;
 }
 
 __device__ void start_search(Ctl& C, int dir) {
@@ -575,7 +665,7 @@ __device__ void begin_cg(const DevInst& I, Ctl& C) {
   C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
   C.cg_j = 0;
   C.cdmax = 0.0;
-  if (C.gF2 > 0.0 && I.opt.max_cg >= 1) {
+  if (I.opt.max_cg >= 1) {
     C.first_cg = 1;
     C.beta = 0.0;
     C.pass = P_CG_B;
@@ -586,9 +676,9 @@ __device__ void begin_cg(const DevInst& I, Ctl& C) {
 
 // Start outer iterate k (Algorithm GPCG): gradient projection unless the
 // previous iterate satisfied Eq. cgstop3.
-__device__ void begin_outer(const DevInst& I, Ctl& C, int* live) {
+__device__ void begin_outer(const DevInst& I, Ctl& C) {
   if (C.outer_iters >= I.opt.max_outer) {
-    set_done(C, S_MAXIT, live);
+    set_done(C, S_MAXIT);
     return;
   }
   C.outer_iters++;
@@ -603,7 +693,7 @@ __device__ void begin_outer(const DevInst& I, Ctl& C, int* live) {
 
 // ||grad_Omega q|| <= tau held.  In mixed precision the first time this
 // happens starts the closing FP64 CG phase on the identified face.
-__device__ void on_converged(const DevInst& I, Ctl& C, int* live) {
+__device__ void on_converged(const DevInst& I, Ctl& C) {
   if (I.opt.mixed && I.opt.refine && !C.refined) {
     C.refined = 1;
     C.refining = 1;
@@ -612,7 +702,7 @@ __device__ void on_converged(const DevInst& I, Ctl& C, int* live) {
     C.outer_iters++;
     begin_cg(I, C);
   } else {
-    set_done(C, S_OK, live);
+    set_done(C, S_OK);
   }
 }
 
@@ -629,26 +719,31 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
     case P_CENSUS: {
       C.pg2 = red[0];
       C.xgb = red[1];
-      C.gF2 = red[2];
-      C.nA = red[5];
-      C.nB = red[6];
+      C.nA = red[4];
+      C.nB = red[5];
+      if (C.final_census) {
+        C.pass = P_NONE;
+        C.done = 1;
+        atomicSub(live, 1);
+        break;
+      }
       C.pg0 = sqrt(C.pg2);
       C.tau = fmax(o.tau_abs, o.tau_rel * C.pg0);
       C.eta2 = o.eta2;
       C.continue_cg = 0;
-      if (!isfinite(C.pg2) || !isfinite(C.xgb)) {
-        set_done(C, S_NUMERIC, live);
+      if (!isfinite(C.pg2)) {
+        set_done(C, S_NUMERIC);
       } else if (C.pg0 <= C.tau) {
-        set_done(C, S_OK, live);
+        set_done(C, S_OK);
       } else {
-        begin_outer(I, C, live);
+        begin_outer(I, C);
       }
       break;
     }
     case P_GP_ALPHA: {
       const double gg = red[0], gAg = red[1];
       if (!(gAg > 0.0) || !isfinite(gg)) {
-        set_done(C, S_NUMERIC, live);
+        set_done(C, S_NUMERIC);
         break;
       }
       C.alpha0 = gg / gAg;  // Eq. bqpls: exact minimiser along -grad_Omega q
@@ -661,23 +756,21 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
     }
     case P_TRIAL: {
       C.ls_trials++;
-      const double gs = red[3];
-      const double dq = 0.5 * red[4];  // q(xt) - q(x)
-      if (dq <= o.mu * gs) {           // Eq. gplsstop / cglsstop2
+      const double gs = red[0];
+      const double dq = 0.5 * (red[0] + red[1]);  // q(xt) - q(x)
+      if (dq <= o.mu * gs) {                     // Eq. gplsstop / cglsstop2
         C.cur ^= 1;
-        C.pg2 = red[0];
-        C.xgb = red[1];
-        C.gF2 = red[2];
-        C.nA = red[5];
-        C.nB = red[6];
+        C.pg2 = red[2];
+        C.nA = red[4];
+        C.nB = red[5];
         const double pgn = sqrt(C.pg2);
         if (C.trial_gp) {
           C.gp_iters++;
           C.gp_j++;
           const double dec = -dq;
-          const bool same = red[7] == 0.0;  // Eq. pgstop1
+          const bool same = red[6] == 0.0;  // Eq. pgstop1
           if (pgn <= C.tau) {
-            on_converged(I, C, live);
+            on_converged(I, C);
             break;
           }
           const bool stop = same || (C.gp_j >= 2 && dec <= o.eta1 * C.dmax) ||  // Eq. pgstop2
@@ -691,7 +784,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         } else {
           C.refining = 0;
           if (pgn <= C.tau) {
-            on_converged(I, C, live);
+            on_converged(I, C);
             break;
           }
           if (C.nB == C.nA) {  // Eq. cgstop3: B(x) = A(x)
@@ -701,12 +794,12 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
             C.eta2 = o.eta2;
             C.continue_cg = 0;
           }
-          begin_outer(I, C, live);
+          begin_outer(I, C);
         }
       } else {
         C.ls_i++;
         if (C.ls_i > o.max_ls) {
-          set_done(C, S_LINESEARCH, live);
+          set_done(C, S_LINESEARCH);
           break;
         }
         if (C.dir != D_ZERO) C.alpha = ldexp(C.trial_gp ? C.alpha0 : 1.0, -C.ls_i);
@@ -717,7 +810,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       if (C.first_cg) {
         C.rr = red[1];
         C.first_cg = 0;
-        if (!(C.rr > 0.0)) {  // the rounded free gradient vanished
+        if (!(C.rr > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
           C.pcur ^= 1;
           start_search(C, D_ZERO);
           break;
@@ -725,7 +818,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       }
       const double pAp = red[0];
       if (!(pAp > 0.0)) {
-        set_done(C, S_NUMERIC, live);
+        set_done(C, S_NUMERIC);
         break;
       }
       C.alpha = C.rr / pAp;
@@ -758,51 +851,22 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
 
 // ------------------------------------------------------------------ kernel --
 
-__device__ __forceinline__ void warp_sum(Acc& a) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) a.s[k] += __shfl_xor_sync(FULL_MASK, a.s[k], off);
+// Number of FP64 sums each pass reduces.
+__device__ __forceinline__ int n_sums(int pass, int first) {
+  switch (pass) {
+    case P_CENSUS: return 2;
+    case P_GP_ALPHA: return 2;
+    case P_TRIAL: return 3;
+    case P_CG_B: return first ? 2 : 1;
+    case P_CG_A: return 1;
+    default: return 0;
   }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) a.c[k] = __reduce_add_sync(FULL_MASK, a.c[k]);
 }
 
-__global__ void __launch_bounds__(kThreads) pass_kernel(EngineArgs E) {
-  __shared__ double sred[kWarps][kNRed];
-  __shared__ int s_last;
-  __shared__ DevInst sI;
-  static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const unsigned np = atomicAdd(E.npass, 1u) + 1u;
-    if (E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
-      cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
-    }
-  }
-  const int2 tr = E.tiles[blockIdx.x];
-  Ctl& C = E.ctl[tr.x];
-  const int pass = C.pass;
-  if (pass == P_NONE) return;
-  if (threadIdx.x < sizeof(DevInst) / 8)
-    reinterpret_cast<long long*>(&sI)[threadIdx.x] =
-        reinterpret_cast<const long long*>(E.insts + tr.x)[threadIdx.x];
-  __syncthreads();
-  const DevInst& I = sI;
-
-  const int tile = tr.y;
-  const int tx = tile % I.tiles_x;
-  const int rest = tile / I.tiles_x;
-  const int x0 = tx * kTX;
-  const int y0 = (rest % I.tiles_y) * kTY;
-  const int z = rest / I.tiles_y;
-
-  Acc acc;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) acc.s[k] = 0.0;
-  acc.c[0] = acc.c[1] = acc.c[2] = 0;
-
-  const int cur = C.cur, pcur = C.pcur;
-  switch (pass) {
+__device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
+                                         Acc& acc) {
+  const int cur = S.cur, pcur = S.pcur;
+  switch (S.pass) {
     case P_START:
       start_tile(I, I.x[cur], x0, y0, z);
       break;
@@ -817,13 +881,12 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(EngineArgs E) {
       break;
     }
     case P_TRIAL: {
-      const int dir = C.dir;
-      const double alpha = dir == D_ZERO ? 0.0 : C.alpha;
-      if (dir == D_W64) {
+      const double alpha = S.dir == D_ZERO ? 0.0 : S.alpha;
+      if (S.dir == D_W64) {
         OpTrial<D_W64> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
                           I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
         stencil_tile(I, op, x0, y0, z, acc);
-      } else if (dir == D_W32) {
+      } else if (S.dir == D_W32) {
         OpTrial<D_W32> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
                           I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
         stencil_tile(I, op, x0, y0, z, acc);
@@ -835,101 +898,179 @@ __global__ void __launch_bounds__(kThreads) pass_kernel(EngineArgs E) {
       break;
     }
     case P_CG_B: {
-      const bool first = C.first_cg;
-      if (C.cg32) {
-        if (first) {
+      if (S.cg32) {
+        FF ff[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        if (S.first_cg) {
           OpCgB<float, true> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], 0.0f,
                                 I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
-                                I.diag32, I.cx32, I.cy32, I.cz32};
+                                I.diag32, I.cx32, I.cy32, I.cz32, ff};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpCgB<float, false> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], (float)C.beta,
+          OpCgB<float, false> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], (float)S.beta,
                                  I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
-                                 I.diag32, I.cx32, I.cy32, I.cz32};
+                                 I.diag32, I.cx32, I.cy32, I.cz32, ff};
           stencil_tile(I, op, x0, y0, z, acc);
         }
+        acc.s[0] += ff_val(ff[0]);
+        acc.s[1] += ff_val(ff[1]);
       } else {
-        if (first) {
+        if (S.first_cg) {
           OpCgB<double, true> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], 0.0,
                                  I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
-                                 I.diag, I.cx, I.cy, I.cz};
+                                 I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], C.beta,
+          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], S.beta,
                                   I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
-                                  I.diag, I.cx, I.cy, I.cz};
+                                  I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
         }
       }
       break;
     }
     case P_CG_A:
-      if (C.cg32) {
-        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, C.alpha, x0, y0, z, acc);
+      if (S.cg32) {
+        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, S.alpha, x0, y0, z, acc);
       } else {
-        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, C.alpha, x0, y0, z, acc);
+        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, S.alpha, x0, y0, z, acc);
       }
       break;
     default:
       break;
   }
+}
 
-  // fixed-order block reduction: lanes by xor butterfly, warps in order
-  warp_sum(acc);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) sred[warp][k] = acc.s[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sred[warp][5 + k] = (double)acc.c[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double* P = I.part + (long long)tile * kNRed;
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; ++w) v += sred[w][k];
-      P[k] = v;
+__global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
+  __shared__ DevInst sI;
+  __shared__ Snap sS;
+  __shared__ double s_sum[4][kThreads];
+  __shared__ int s_cnt[3][kWarps];
+  __shared__ double s_red[kNRed];
+  __shared__ int s_t, s_inst, s_last;
+  static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (blockIdx.x == 0 && tid == 0) {
+    const unsigned np = atomicAdd(E.npass, 1u) + 1u;
+    if (E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
+      cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
     }
+  }
+  if (tid == 0) s_inst = -1;
+
+  for (;;) {
+    __syncthreads();  // the previous item's shared state is no longer read
+    if (tid == 0) s_t = atomicAdd(E.queue, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= E.n_work) break;
+    const int2 tr = __ldg(E.tiles + t);
+    if (tr.x != s_inst) {
+      __syncthreads();  // everyone compared against the old s_inst
+      if (tid < (int)(sizeof(DevInst) / 8))
+        reinterpret_cast<long long*>(&sI)[tid] =
+            __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
+      if (tid == 0) {
+        const Ctl& C = E.ctl[tr.x];
+        sS.pass = C.pass;
+        sS.cur = C.cur;
+        sS.pcur = C.pcur;
+        sS.cg32 = C.cg32;
+        sS.first_cg = C.first_cg;
+        sS.dir = C.dir;
+        sS.alpha = C.alpha;
+        sS.beta = C.beta;
+        s_inst = tr.x;
+      }
+      __syncthreads();
+    }
+    const DevInst& I = sI;
+    const Snap& S = sS;
+    if (S.pass == P_NONE) continue;
+
+    const int tile = tr.y;
+    const int tx = tile % I.tiles_x;
+    const int rest = tile / I.tiles_x;
+    const int x0 = tx * kTX;
+    const int y0 = (rest % I.tiles_y) * kTY;
+    const int z = rest / I.tiles_y;
+
+    Acc acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
+    acc.c[0] = acc.c[1] = acc.c[2] = 0;
+    run_tile(I, S, x0, y0, z, acc);
+
+    // fixed-order tile reduction: every thread's sums go to shared memory and
+    // warp 0 adds them up (lane j sums threads j, j+32, ..., then a butterfly)
+    const int ns = n_sums(S.pass, S.first_cg);
+    for (int k = 0; k < ns; ++k) s_sum[k][tid] = acc.s[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
+      if (lane == 0) s_cnt[k][warp] = c;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double part[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < ns; ++k) {
+        double v = s_sum[k][lane];
+        for (int j = 1; j < kWarps; ++j) v += s_sum[k][lane + 32 * j];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+        part[k] = v;
+      }
+      if (lane == 0) {
+        double* P = I.part + (long long)tile * kNRed;
+        for (int k = 0; k < 4; ++k) P[k] = part[k];
+        for (int k = 0; k < 3; ++k) {
+          int c = 0;
+          for (int w = 0; w < kWarps; ++w) c += s_cnt[k][w];
+          P[4 + k] = (double)c;
+        }
+        __threadfence();
+        const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, 1u);
+        s_last = (prev == (unsigned)(I.n_tiles - 1));
+      }
+    }
+    __syncthreads();
+    if (!s_last) continue;
+
+    // last tile of this instance: reduce the tile slots in a fixed order
     __threadfence();
-    const unsigned prev = atomicAdd(&C.arrive, 1u);
-    s_last = (prev == (unsigned)(I.n_tiles - 1));
-  }
-  __syncthreads();
-  if (!s_last) return;
-
-  // last CTA of this instance: reduce the tile partials in a fixed order
-  __threadfence();
-  const double* P0 = I.part;
-  double part[kNRed];
+    const double* P0 = I.part;
+    double part[kNRed];
 #pragma unroll
-  for (int k = 0; k < kNRed; ++k) part[k] = 0.0;
-  for (int t = threadIdx.x; t < I.n_tiles; t += kThreads) {
+    for (int k = 0; k < kNRed; ++k) part[k] = 0.0;
+    for (int j = tid; j < I.n_tiles; j += kThreads) {
 #pragma unroll
-    for (int k = 0; k < kNRed; ++k) part[k] += __ldcg(P0 + (long long)t * kNRed + k);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) part[k] += __shfl_xor_sync(FULL_MASK, part[k], off);
-  }
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) sred[warp][k] = part[k];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double red[kNRed];
+      for (int k = 0; k < kNRed; ++k) part[k] += __ldcg(P0 + (long long)j * kNRed + k);
+    }
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; ++w) v += sred[w][k];
-      red[k] = v;
+      double v = part[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+      if (lane == 0) s_sum[0][k * kWarps + warp] = v;
     }
-    C.arrive = 0u;
-    finalize(I, C, red, E.live);
+    __syncthreads();
+    if (tid == 0) {
+      for (int k = 0; k < kNRed; ++k) {
+        double v = 0.0;
+        for (int w = 0; w < kWarps; ++w) v += s_sum[0][k * kWarps + w];
+        s_red[k] = v;
+      }
+      Ctl& C = E.ctl[tr.x];
+      C.arrive = 0u;
+      finalize(I, C, s_red, E.live);
+    }
+  }
+
+  // the last CTA to leave resets the queue for the next launch
+  if (tid == 0) {
+    if (atomicAdd(E.exits, 1u) == gridDim.x - 1) {
+      *E.queue = 0;
+      *E.exits = 0u;
+      __threadfence();
+    }
   }
 }
 
@@ -1026,6 +1167,19 @@ template __global__ void unpad_kernel<float>(DevInst, const float*, double*);
 // ---------------------------------------------------------- host wrappers --
 
 const void* pass_kernel_ptr() { return (const void*)pass_kernel; }
+
+int pass_grid(int n_work) {
+  // persistent grid: the resident CTAs of the whole GPU, at most one per item
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel, kThreads, 0);
+    cached = sms * (per > 0 ? per : 1);
+  }
+  return n_work < cached ? (n_work > 0 ? n_work : 1) : cached;
+}
 
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s) {
   pass_kernel<<<n_blocks, kThreads, 0, s>>>(E);
