@@ -157,13 +157,17 @@ gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats)
 gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask, const double* pv,
                              double* y, double* pAp, int precision, void* cuda_stream);
 
-/* Time `reps` back-to-back launches of the masked matrix-vector kernel on
- * the problem's free set after the latest solve (or all points free before
- * any solve), with CUDA events on the given stream.  *ms_per_launch receives
- * the mean launch duration and *bytes_per_launch the algorithmic bytes moved
- * per launch (bands + p read once + Ap written once + mask bits). */
-gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, void* cuda_stream,
-                                  double* ms_per_launch, double* bytes_per_launch);
+/* Time `reps` launches of the masked matrix-vector kernel (the CG pass that
+ * forms p and A_k p) on the problem's free set after the latest solve (or all
+ * points free before any solve), with CUDA events on the given stream.  With
+ * flush_l2 != 0 every launch is preceded by a write of 256 MiB (twice the L2
+ * cache) so that each launch streams its operands from HBM, and only the
+ * launches are timed.  *ms_per_launch receives the mean launch duration and
+ * *bytes_per_launch the algorithmic bytes moved per launch (bands, r and p
+ * read once, p and A_k p written once, the mask bits). */
+gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int flush_l2,
+                                  void* cuda_stream, double* ms_per_launch,
+                                  double* bytes_per_launch);
 
 /* ---- continuous-batching server --------------------------------------- */
 

@@ -27,7 +27,28 @@ constexpr int kWarps = 8;        // warps per CTA
 constexpr int kTY = kRY * kWarps;  // tile height (rows)
 constexpr int kThreads = 32 * kWarps;
 constexpr int kNRed = 8;         // partial sums per tile: 4 FP64 sums, 3 counts, 1 spare
-constexpr int kMinBlocks = 3;    // resident CTAs per SM the pass kernel is compiled for
+constexpr int kMinBlocks = 2;    // resident CTAs per SM the pass kernel is compiled for
+
+// A work item is a group of consecutive tiles of one instance; the groups of
+// an instance depend only on its shape (about kGroupTiles tiles each, at most
+// kMaxGroups groups), and each group has one partial-sum slot.
+constexpr int kGroupTiles = 4;
+constexpr int kMaxGroups = 304;
+
+// TMA staging of the CG passes: a work item (64x32 tile) is streamed through
+// shared memory in chunks of 64 x kChunk rows, two stages deep.
+constexpr int kStageBytes = 45056;   // one stage (see the stage layout in the kernels)
+constexpr int kDynSmem = 2 * kStageBytes + 256;
+
+// Tensor maps of an instance (one CUtensorMap, 128 bytes, each).  H = halo
+// box (64+2h) x (chunk+2) starting at (x0-h, y0-1); D = 64 x chunk;
+// CX = (64+h) x chunk from x0-h; CY = 64 x (chunk+1) from y0-1; the rest are
+// 64 x chunk boxes over the (nx, ny*nz) row space.
+enum TMap : int {
+  M32_RH = 0, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R, M32_P0, M32_P1, M32_AP,
+  M64_RH, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R, M64_P0, M64_P1, M64_AP,
+  M_COUNT
+};
 
 enum Pass : int {
   P_NONE = 0,
@@ -73,8 +94,11 @@ struct Ctl {
 
 struct DevInst {
   int dim, nx, ny, nz, px, mw, tiles_x, tiles_y, n_tiles, kc;
+  int n_groups, pad_g;
   long long n, plane;
-  double* part;            // [n_tiles][kNRed] tile partial sums of this instance
+  double* part;            // [n_groups][kNRed] group partial sums of this instance
+  const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
+  int tma64, tma32;        // the FP64 / FP32 maps are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   double *x[2], *g[2];
@@ -87,12 +111,13 @@ struct DevInst {
 struct EngineArgs {
   const DevInst* insts;
   Ctl* ctl;
-  const int2* tiles;      // (instance slot, tile) work items of the launch
+  const int2* tiles;      // (instance slot, group) work items of the launch
   int n_work;             // number of work items
   int* queue;             // next work item (dynamic scheduling; reset by the last CTA)
   unsigned* exits;        // CTAs that found the queue empty
   int* live;              // instances not yet done
   unsigned* npass;        // launches so far (block 0 increments)
+  int* err;               // set when a bounded wait gave up
   unsigned pass_cap;      // launches after which the loop condition is cleared
   unsigned long long cond;  // cudaGraphConditionalHandle, 0 when not in a WHILE graph
 };

@@ -1,6 +1,8 @@
 // gpcg_api.cu -- host side of libgpcg.so: the C ABI of include/gpcg.h, device
 // memory of each problem, the engine driver (CUDA graphs) and the
 // continuous-batching server.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -77,7 +79,8 @@ struct Scratch {
   int2* d_tiles = nullptr;
   int* d_live = nullptr;
   unsigned* d_npass = nullptr;
-  int* d_queue = nullptr;     // [0] work queue head, [1] exit counter (zero between launches)
+  int* d_queue = nullptr;  // [0] work queue head, [1] exit counter (zero between launches),
+                           // [2] error flag of the bounded waits
   int* h_pin = nullptr;  // pinned: [0] live, [1] npass
   int cap_inst = 0;
   long long cap_tiles = 0;
@@ -112,8 +115,8 @@ struct Scratch {
       CK(cudaMallocHost(&h_pin, 4 * sizeof(int)));
       CK(cudaMalloc(&d_live, sizeof(int)));
       CK(cudaMalloc(&d_npass, sizeof(unsigned)));
-      CK(cudaMalloc(&d_queue, 2 * sizeof(int)));
-      CK(cudaMemset(d_queue, 0, 2 * sizeof(int)));
+      CK(cudaMalloc(&d_queue, 4 * sizeof(int)));
+      CK(cudaMemset(d_queue, 0, 4 * sizeof(int)));
     }
     if (n_inst > cap_inst) {
       cudaFree(d_insts);
@@ -144,7 +147,7 @@ struct Scratch {
 struct gpcg_problem {
   int dim = 2, nx = 0, ny = 0, nz = 1, px = 0, mw = 0, kc = 3;
   long long n = 0, plane = 0, pn = 0, mwords = 0;
-  int tiles_x = 0, tiles_y = 0, n_tiles = 0;
+  int tiles_x = 0, tiles_y = 0, n_tiles = 0, n_groups = 0;
   double c = 0.0;
   void* arena64 = nullptr;
   size_t bytes64 = 0;
@@ -178,6 +181,7 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
   p->tiles_x = (int)((nx + kTX - 1) / kTX);
   p->tiles_y = (int)((ny + kTY - 1) / kTY);
   p->n_tiles = p->tiles_x * p->tiles_y * (int)nz;
+  p->n_groups = std::min((p->n_tiles + kGroupTiles - 1) / kGroupTiles, kMaxGroups);
 }
 
 // Bytes of the FP64 arena: kc bands, b, l, u, x[2], g[2], r, w, p[2], Ap,
@@ -185,8 +189,9 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
 static size_t arena64_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(double) * (size_t)p->pn);
   const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
-  const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_tiles);
-  return (size_t)(p->kc + 12) * vec + 2 * msk + part;
+  const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_groups);
+  const size_t maps = align256(sizeof(CUtensorMap) * M_COUNT);
+  return (size_t)(p->kc + 12) * vec + 2 * msk + part + maps;
 }
 
 static size_t arena32_bytes(const gpcg_problem* p) {
@@ -213,6 +218,7 @@ static void carve64(gpcg_problem* p) {
   I.tiles_x = p->tiles_x;
   I.tiles_y = p->tiles_y;
   I.n_tiles = p->n_tiles;
+  I.n_groups = p->n_groups;
   I.kc = p->kc;
   I.n = p->n;
   I.plane = p->plane;
@@ -230,8 +236,82 @@ static void carve64(gpcg_problem* p) {
   for (int k = 0; k < 2; ++k) I.p64[k] = (double*)take(vec);
   I.Ap64 = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.mask[k] = (unsigned*)take(msk);
-  I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_tiles));
+  I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_groups));
+  I.tmaps = take(align256(sizeof(CUtensorMap) * M_COUNT));
+  I.tma64 = 0;
+  I.tma32 = 0;
   I.x0 = I.r64;  // a given start point is staged in r (unused until CG starts)
+}
+
+// ----------------------------------------------------------- tensor maps --
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool have_encode() {
+  static std::once_flag once;
+  std::call_once(once, []() {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    else
+      cudaGetLastError();
+  });
+  return g_encode != nullptr;
+}
+
+// One 2-D map over the padded array `base` seen as (nx columns, rows rows,
+// row pitch px elements), with a bw x bh box; out-of-range boxes fill zeros.
+static bool encode_map(CUtensorMap* m, bool f32, const void* base, const gpcg_problem* p, int bw,
+                       int bh) {
+  const size_t es = f32 ? 4 : 8;
+  cuuint64_t dims[2] = {(cuuint64_t)p->nx, (cuuint64_t)p->ny * (cuuint64_t)p->nz};
+  cuuint64_t strides[1] = {(cuuint64_t)p->px * es};
+  cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  cuuint32_t estr[2] = {1, 1};
+  return g_encode(m, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Encode the maps of one precision (the box shapes of the CG stages, see the
+// kernels) and copy them to the problem's device area.  Returns false (and
+// leaves the TMA path off) when the driver cannot encode them.
+static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
+  if (!have_encode()) return false;
+  DevInst& I = p->inst;
+  const int h = f32 ? 4 : 2, ch = f32 ? 32 : 16;
+  const int b0 = f32 ? M32_RH : M64_RH;
+  CUtensorMap m[11];
+  const void* r = f32 ? (const void*)I.r32 : (const void*)I.r64;
+  const void* p0 = f32 ? (const void*)I.p32[0] : (const void*)I.p64[0];
+  const void* p1 = f32 ? (const void*)I.p32[1] : (const void*)I.p64[1];
+  const void* d = f32 ? (const void*)I.diag32 : (const void*)I.diag;
+  const void* cx = f32 ? (const void*)I.cx32 : (const void*)I.cx;
+  const void* cy = f32 ? (const void*)I.cy32 : (const void*)I.cy;
+  const void* w = f32 ? (const void*)I.w32 : (const void*)I.w64;
+  const void* ap = f32 ? (const void*)I.Ap32 : (const void*)I.Ap64;
+  bool ok = encode_map(&m[0], f32, r, p, 64 + 2 * h, ch + 2) &&
+            encode_map(&m[1], f32, p0, p, 64 + 2 * h, ch + 2) &&
+            encode_map(&m[2], f32, p1, p, 64 + 2 * h, ch + 2) &&
+            encode_map(&m[3], f32, d, p, 64, ch) && encode_map(&m[4], f32, cx, p, 64 + h, ch) &&
+            encode_map(&m[5], f32, cy, p, 64, ch + 1) && encode_map(&m[6], f32, w, p, 64, ch) &&
+            encode_map(&m[7], f32, r, p, 64, ch) && encode_map(&m[8], f32, p0, p, 64, ch) &&
+            encode_map(&m[9], f32, p1, p, 64, ch) && encode_map(&m[10], f32, ap, p, 64, ch);
+  if (!ok) return false;
+  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
+  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return true;
+}
+
+static bool tma_disabled() {
+  const char* e = getenv("GPCG_NO_TMA");
+  return e && *e && *e != '0';
 }
 
 static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
@@ -265,6 +345,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.cx32 = x32;
   I.cy32 = y32;
   I.cz32 = z32;
+  I.tma32 = (!tma_disabled() && make_maps(p, true, s)) ? 1 : 0;
   return GPCG_OK;
 }
 
@@ -338,6 +419,7 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
     delete p;
     return st;
   }
+  p->inst.tma64 = (!tma_disabled() && make_maps(p, false, s)) ? 1 : 0;
   *out = p;
   return GPCG_OK;
 }
@@ -423,8 +505,8 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps))
     return GPCG_OK;
   sc.invalidate();
-  EngineArgs args{sc.d_insts, sc.d_ctl,     sc.d_tiles, (int)tiles, sc.d_queue,
-                  (unsigned*)(sc.d_queue + 1), sc.d_live, sc.d_npass, cap, 0ull};
+  EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+                  sc.d_live,   sc.d_npass, sc.d_queue + 2, cap, 0ull};
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   cudaGraph_t body = g;
@@ -460,7 +542,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   k.func = const_cast<void*>(pass_kernel_ptr());
   k.gridDim = dim3((unsigned)pass_grid((int)tiles));
   k.blockDim = dim3(kThreads);
-  k.sharedMemBytes = 0;
+  k.sharedMemBytes = kDynSmem;
   k.kernelParams = kp;
   cudaGraphNode_t prev = nullptr;
   for (int i = 0; i < count; ++i) {
@@ -517,6 +599,13 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
       steps = std::min(steps * 2, 256);
     }
   }
+  CK(cudaMemcpyAsync(&sc.h_pin[2], sc.d_queue + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (sc.h_pin[2] != 0) {
+    const int zero = 0;
+    cudaMemcpy(sc.d_queue + 2, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(GPCG_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
+  }
   if (sc.h_pin[0] != 0) return fail(GPCG_ERR_TIMEOUT, "pass cap reached with live solves");
   return GPCG_OK;
 }
@@ -547,7 +636,7 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
                              Scratch& sc) {
   cudaStream_t s = (cudaStream_t)o->cuda_stream;
   long long tiles = 0;
-  for (int k = 0; k < count; ++k) tiles += probs[k]->n_tiles;
+  for (int k = 0; k < count; ++k) tiles += probs[k]->n_groups;
   gpcg_status st = sc.ensure(count, tiles);
   if (st != GPCG_OK) return st;
   std::vector<DevInst> insts(count);
@@ -556,7 +645,7 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   long long t = 0;
   for (int k = 0; k < count; ++k) {
     if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
-    for (int j = 0; j < probs[k]->n_tiles; ++j) table[(size_t)t++] = make_int2(k, j);
+    for (int j = 0; j < probs[k]->n_groups; ++j) table[(size_t)t++] = make_int2(k, j);
   }
   CK(cudaMemcpyAsync(sc.d_insts, insts.data(), sizeof(DevInst) * count, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_ctl, ctl.data(), sizeof(Ctl) * count, cudaMemcpyHostToDevice, s));
@@ -646,10 +735,10 @@ static bool is_device_ptr(const void* ptr) {
 
 static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
   Scratch& sc = p->sc;
-  gpcg_status st = sc.ensure(1, p->n_tiles);
+  gpcg_status st = sc.ensure(1, p->n_groups);
   if (st != GPCG_OK) return st;
-  std::vector<int2> table((size_t)p->n_tiles);
-  for (int j = 0; j < p->n_tiles; ++j) table[(size_t)j] = make_int2(0, j);
+  std::vector<int2> table((size_t)p->n_groups);
+  for (int j = 0; j < p->n_groups; ++j) table[(size_t)j] = make_int2(0, j);
   DevInst I = p->inst;
   I.opt = Opts{};
   CK(cudaMemcpyAsync(sc.d_insts, &I, sizeof(DevInst), cudaMemcpyHostToDevice, s));
@@ -660,9 +749,9 @@ static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
   sc.h_pin[1] = 0;
   CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
-  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles, p->n_tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
-               sc.d_live,   sc.d_npass, 0xffffffffu, 0ull};
-  CK(launch_pass(E, pass_grid(p->n_tiles), s));
+  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles,    p->n_groups, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+               sc.d_live,   sc.d_npass, sc.d_queue + 2, 0xffffffffu, 0ull};
+  CK(launch_pass(E, pass_grid(p->n_groups), s));
   if (out) {
     CK(cudaMemcpyAsync(out, sc.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -759,8 +848,8 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
 }
 
 extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps,
-                                             void* cuda_stream, double* ms_per_launch,
-                                             double* bytes_per_launch) {
+                                             int flush_l2, void* cuda_stream,
+                                             double* ms_per_launch, double* bytes_per_launch) {
   if (!p || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
   if (precision != GPCG_FP64 && precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
@@ -789,21 +878,30 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
   // one untimed launch sets up the tables, then `reps` timed launches
   if ((st = one_pass(p, spmv_ctl(f32, cur, 0), s, nullptr)) != GPCG_OK) return st;
   Scratch& sc = p->sc;
-  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles, p->n_tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
-               sc.d_live,   sc.d_npass, 0xffffffffu, 0ull};
-  const int grid = pass_grid(p->n_tiles);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, s));
-  for (int k = 0; k < reps; ++k) CK(launch_pass(E, grid, s));
-  CK(cudaEventRecord(e1, s));
-  CK(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  CK(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (ms_per_launch) *ms_per_launch = ms / reps;
+  EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles,    p->n_groups, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+               sc.d_live,   sc.d_npass, sc.d_queue + 2, 0xffffffffu, 0ull};
+  const int grid = pass_grid(p->n_groups);
+  const size_t flush_bytes = (size_t)256 << 20;
+  void* flush = nullptr;
+  if (flush_l2) CK(cudaMalloc(&flush, flush_bytes));
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int k = 0; k < reps; ++k) {
+    if (flush) CK(cudaMemsetAsync(flush, k & 0xff, flush_bytes, s));
+    CK(cudaEventRecord(ev[2 * k], s));
+    CK(launch_pass(E, grid, s));
+    CK(cudaEventRecord(ev[2 * k + 1], s));
+  }
+  CK(cudaStreamSynchronize(s));
+  double total = 0.0;
+  for (int k = 0; k < reps; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    total += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (flush) cudaFree(flush);
+  if (ms_per_launch) *ms_per_launch = total / reps;
   const double sv = f32 ? 4.0 : 8.0;
   if (bytes_per_launch) *bytes_per_launch = (double)p->n * (sv * p->kc + 4.0 * sv + 0.125);
   return GPCG_OK;
@@ -924,7 +1022,7 @@ static gpcg_status server_upload_table(gpcg_server* s) {
   for (int k = 0; k < s->max_live; ++k) {
     Req* r = s->slots[k];
     if (!r) continue;
-    for (int j = 0; j < r->prob->n_tiles; ++j) table.push_back(make_int2(k, j));
+    for (int j = 0; j < r->prob->n_groups; ++j) table.push_back(make_int2(k, j));
   }
   s->tiles = (long long)table.size();
   if (s->tiles == 0) return GPCG_OK;

@@ -25,6 +25,7 @@
 // in FP32 (Ogita, Rump & Oishi, "Accurate sum and dot product", SISC 2005,
 // algorithm Dot2) and convert to FP64 once per thread and tile, and the
 // per-tile reduction runs through shared memory with one warp.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -103,6 +104,67 @@ __device__ __forceinline__ void ff_fma(FF& s, float a, float b) {
 }
 
 __device__ __forceinline__ double ff_val(const FF& s) { return (double)s.hi + (double)s.lo; }
+
+// a + b in float-float arithmetic (TwoSum of the high parts, then a fast
+// renormalisation).
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+  const float hi = __fadd_rn(s, lo);
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+// ------------------------------------------------------- TMA and mbarrier --
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after a bounded number of
+// polls (returns false) so that a lost copy can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 2-D tiled bulk tensor copy global -> shared, completing on `bar`.  The x
+// coordinate is always a multiple of 16 bytes; y may be -1 or beyond the
+// last row (the unit fills zeros there).
+__device__ __forceinline__ void tma_load2d(unsigned dst, const void* map, int x, int y,
+                                           unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// The tensor maps live in global memory written by the host; make the TMA
+// unit's view of them current before first use in this CTA.
+__device__ __forceinline__ void tmap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   (unsigned long long)map)
+               : "memory");
+}
 
 // --------------------------------------------------------- memory helpers --
 
@@ -849,6 +911,207 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
   }
 }
 
+
+// ------------------------------------------------------- TMA-staged CG --
+//
+// The two CG passes of a 2-D instance (and the pointwise CG pass of any
+// instance) stream a work item through shared memory with the tensor memory
+// accelerator: chunk k+1 is in flight while chunk k is computed.  Stage
+// layout (each array 128-byte aligned), T = float (32-row chunks, h = 4) or
+// double (16-row chunks, h = 2) -- both come to the same byte sizes:
+//   P_CG_B: R (64+2h)x(c+2) from (x0-h, y-1) | P likewise | D 64xc |
+//           CX (64+h)xc from x0-h | CY 64x(c+1) from y-1
+//   P_CG_A: W | R | P | AP, 64xc each
+// Out-of-range rows and columns arrive as zeros, which is exactly the
+// operand and coupling outside the grid.
+
+__host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+
+template <class T>
+struct ChunkGeo {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = sizeof(T) == 4 ? 32 : 16;
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int OFF_R = 0;
+  static constexpr int OFF_P = SZ_H;
+  static constexpr int OFF_D = 2 * SZ_H;
+  static constexpr int OFF_CX = OFF_D + 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END_B = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX_B =
+      (2 * (CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int SZ_A = 64 * CH * (int)sizeof(T);
+  static constexpr unsigned TX_A = 4 * SZ_A;
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH : M64_RH;  // first map of the precision
+};
+static_assert(ChunkGeo<float>::END_B <= kStageBytes && ChunkGeo<double>::END_B <= kStageBytes,
+              "stage layout");
+static_assert(4 * ChunkGeo<float>::SZ_A <= kStageBytes, "stage layout");
+
+__device__ __forceinline__ const void* tmap(const DevInst& I, int k) {
+  return reinterpret_cast<const char*>(I.tmaps) + 128 * k;
+}
+
+template <class T>
+__device__ __forceinline__ void issue_cgb(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = ChunkGeo<T>;
+  mbar_expect(bar, G::TX_B);
+  tma_load2d(st + G::OFF_R, tmap(I, G::MB + 0), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, G::MB + 1 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, G::MB + 3), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, G::MB + 4), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, G::MB + 5), x0, yc - 1, bar);
+}
+
+template <class T>
+__device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, int row,
+                                          unsigned st, unsigned bar) {
+  using G = ChunkGeo<T>;
+  mbar_expect(bar, G::TX_A);
+  tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + 6), x0, row, bar);
+  tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + 7), x0, row, bar);
+  tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + 8 + pcur), x0, row, bar);
+  tma_load2d(st + 3 * G::SZ_A, tmap(I, G::MB + 10), x0, row, bar);
+}
+
+// P_CG_B (not the first step of a phase) on one staged chunk of a 2-D grid:
+// p = -r + beta p_old over the halo'd box (in place), then Ap = Z Z' A Z Z' p
+// and <p, Ap> for the chunk's interior.
+template <class T>
+__device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                          T beta, const unsigned* fbits, T* p_out, T* ap_out,
+                                          Acc& acc, FF& ff) {
+  using G = ChunkGeo<T>;
+  T* R = reinterpret_cast<T*>(st + G::OFF_R);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) R[e] = fma(beta, P[e], -R[e]);
+  __syncthreads();
+  constexpr int RPW = G::CH / kWarps;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = warp * RPW + k;
+    const int y = yc + ry;
+    if (y >= I.ny || !v0) break;
+    const T* Rr = R + (ry + 1) * G::BW + G::H + c;
+    const T vc0 = Rr[0], vc1 = Rr[1];
+    const T vw = Rr[-1], ve = Rr[2];
+    const T vs0 = Rr[-G::BW], vs1 = Rr[1 - G::BW];
+    const T vn0 = Rr[G::BW], vn1 = Rr[G::BW + 1];
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    T a0 = Dr[0] * vc0;
+    a0 = fma(Xr[-1], vw, a0);
+    a0 = fma(Xr[0], vc1, a0);
+    a0 = fma(Ys[0], vs0, a0);
+    a0 = fma(Yn[0], vn0, a0);
+    T a1 = Dr[1] * vc1;
+    a1 = fma(Xr[0], vc0, a1);
+    a1 = fma(Xr[1], ve, a1);
+    a1 = fma(Ys[1], vs1, a1);
+    a1 = fma(Yn[1], vn1, a1);
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    const long long i = (long long)y * I.px + e0;
+    st2(ap_out, i, v0, v1, a0, a1);
+    st2(p_out, i, v0, v1, vc0, vc1);
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)vc0, (float)a0);
+      ff_fma(ff, (float)vc1, (float)a1);
+    } else {
+      acc.s[0] = fma((double)vc0, (double)a0, acc.s[0]);
+      acc.s[0] = fma((double)vc1, (double)a1, acc.s[0]);
+    }
+  }
+}
+
+// The free bits of this lane's two points in each of its rows of a chunk,
+// loaded before the chunk's data arrive.
+template <class T>
+__device__ __forceinline__ void load_chunk_bits(const DevInst& I, const unsigned* __restrict__ m,
+                                                int x0, int yc, unsigned fbits[4]) {
+  // the loads are unconditional (rows past the grid read the last row and
+  // are never used) so that nothing waits for them before the chunk's data
+  constexpr int RPW = ChunkGeo<T>::CH / kWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e0 = min(x0 + 2 * lane, I.nx - 1) & ~1;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int y = min(yc + warp * RPW + k, I.ny - 1);
+    fbits[k] = __ldg(m + row_index(I, y, 0) * I.mw + (e0 >> 5)) >> (e0 & 31);
+  }
+}
+
+// P_CG_A on one staged chunk: w += alpha p, r += alpha Ap, ||r||^2.  `row` is
+// the chunk's first row in the (ny*nz) row space, `ylim` the number of rows
+// of the chunk that lie inside the plane.
+template <class T>
+__device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                          int row, int ylim, T alpha, T* w, T* r, Acc& acc,
+                                          FF& ff) {
+  using G = ChunkGeo<T>;
+  const T* W = reinterpret_cast<const T*>(st + 0 * G::SZ_A);
+  const T* R = reinterpret_cast<const T*>(st + 1 * G::SZ_A);
+  const T* P = reinterpret_cast<const T*>(st + 2 * G::SZ_A);
+  const T* AP = reinterpret_cast<const T*>(st + 3 * G::SZ_A);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int RPW = G::CH / kWarps;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = warp * RPW + k;
+    if (ry >= ylim || !v0) break;
+    const int o = ry * 64 + c;
+    const T w0 = fma(alpha, P[o], W[o]), w1 = fma(alpha, P[o + 1], W[o + 1]);
+    const T r0 = fma(alpha, AP[o], R[o]), r1 = fma(alpha, AP[o + 1], R[o + 1]);
+    const long long i = (long long)(row + ry) * I.px + e0;
+    st2(w, i, v0, v1, w0, w1);
+    st2(r, i, v0, v1, r0, r1);
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)r0, (float)r0);
+      ff_fma(ff, (float)r1, (float)r1);
+    } else {
+      acc.s[0] = fma((double)r0, (double)r0, acc.s[0]);
+      acc.s[0] = fma((double)r1, (double)r1, acc.s[0]);
+    }
+  }
+}
+
+// Whether the item's pass runs through the TMA pipeline.
+__device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
+  const int ok = S.cg32 ? I.tma32 : I.tma64;
+  if (!ok) return false;
+  if (S.pass == P_CG_A) return true;
+  return S.pass == P_CG_B && !S.first_cg && I.dim == 2;
+}
+
+// Issue chunk `c` of tile (x0, y0, z) of the item's pass into a stage.
+__device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, int x0, int y0, int z,
+                                            int c, unsigned st, unsigned bar) {
+  if (S.cg32) {
+    const int yc = y0 + c * ChunkGeo<float>::CH;
+    if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, x0, yc, st, bar);
+    else issue_cga<float>(I, S.pcur, x0, z * I.ny + yc, st, bar);
+  } else {
+    const int yc = y0 + c * ChunkGeo<double>::CH;
+    if (S.pass == P_CG_B) issue_cgb<double>(I, S.pcur, x0, yc, st, bar);
+    else issue_cga<double>(I, S.pcur, x0, z * I.ny + yc, st, bar);
+  }
+}
+
 // ------------------------------------------------------------------ kernel --
 
 // Number of FP64 sums each pass reduces.
@@ -944,11 +1207,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ DevInst sI;
   __shared__ Snap sS;
   __shared__ double s_sum[4][kThreads];
+  __shared__ float s_ffh[kThreads], s_ffl[kThreads];
   __shared__ int s_cnt[3][kWarps];
   __shared__ double s_red[kNRed];
   __shared__ int s_t, s_inst, s_last;
+  extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // two TMA stages and their barriers, 128-byte aligned
+  unsigned char* stage0 =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~uintptr_t(127));
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + 2 * kStageBytes);
 
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned np = atomicAdd(E.npass, 1u) + 1u;
@@ -956,7 +1225,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
     }
   }
-  if (tid == 0) s_inst = -1;
+  if (tid == 0) {
+    s_inst = -1;
+    mbar_init(smem_u32(&bars[0]));
+    mbar_init(smem_u32(&bars[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  int seq = 0;   // next chunk of the TMA pipeline to consume (same in all threads)
+  int pend = 0;  // chunk `seq` has already been issued
 
   for (;;) {
     __syncthreads();  // the previous item's shared state is no longer read
@@ -983,81 +1259,199 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         s_inst = tr.x;
       }
       __syncthreads();
+      if (tid == 0 && sI.tmaps && (sS.pass == P_CG_A || sS.pass == P_CG_B)) {
+        const bool f32 = sS.cg32 != 0;
+        if (f32 ? sI.tma32 : sI.tma64) {
+          const int lo = f32 ? M32_RH : M64_RH;
+          for (int k = lo; k < lo + (M64_RH - M32_RH); ++k) tmap_acquire(tmap(sI, k));
+        }
+      }
     }
     const DevInst& I = sI;
     const Snap& S = sS;
     if (S.pass == P_NONE) continue;
 
-    const int tile = tr.y;
-    const int tx = tile % I.tiles_x;
-    const int rest = tile / I.tiles_x;
-    const int x0 = tx * kTX;
-    const int y0 = (rest % I.tiles_y) * kTY;
-    const int z = rest / I.tiles_y;
-
+    // the group's tiles
+    const int grp = tr.y;
+    const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+    const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
     Acc acc;
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
-    run_tile(I, S, x0, y0, z, acc);
-
-    // fixed-order tile reduction: every thread's sums go to shared memory and
-    // warp 0 adds them up (lane j sums threads j, j+32, ..., then a butterfly)
-    const int ns = n_sums(S.pass, S.first_cg);
-    for (int k = 0; k < ns; ++k) s_sum[k][tid] = acc.s[k];
+    FF ff{0.f, 0.f};
+    const bool tma = tma_pass(I, S);
+    unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
+    int pend_bits = 0;
+    for (int tile = t_lo; tile < t_hi; ++tile) {
+      const int tx = tile % I.tiles_x;
+      const int rest = tile / I.tiles_x;
+      const int x0 = tx * kTX;
+      const int y0 = (rest % I.tiles_y) * kTY;
+      const int z = rest / I.tiles_y;
+      if (!tma) {
+        run_tile(I, S, x0, y0, z, acc);
+        continue;
+      }
+      // TMA pipeline: chunk k+1 (of this tile or the next tile of the group)
+      // is in flight while chunk k is computed
+      const int ch = S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
+      const int nch = kTY / ch;
+      const bool more = tile + 1 < t_hi;
+      int nx0 = 0, ny0 = 0, nz0 = 0;
+      if (more) {
+        const int rn = (tile + 1) / I.tiles_x;
+        nx0 = ((tile + 1) % I.tiles_x) * kTX;
+        ny0 = (rn % I.tiles_y) * kTY;
+        nz0 = rn / I.tiles_y;
+      }
+      for (int c = 0; c < nch; ++c) {
+        const int sg = seq & 1;
+        unsigned char* st = stage0 + sg * kStageBytes;
+        const bool nxt = (c + 1 < nch) || more;
+        if (tid == 0) {
+          if (!pend) issue_chunk(I, S, x0, y0, z, c, smem_u32(st), smem_u32(&bars[sg]));
+          unsigned char* st2_ = stage0 + (sg ^ 1) * kStageBytes;
+          const unsigned b2 = smem_u32(&bars[sg ^ 1]);
+          if (c + 1 < nch) issue_chunk(I, S, x0, y0, z, c + 1, smem_u32(st2_), b2);
+          else if (more) issue_chunk(I, S, nx0, ny0, nz0, 0, smem_u32(st2_), b2);
+        }
+        // free bits of this chunk (prefetched with the previous chunk when
+        // possible) and of the next one
+        if (S.pass == P_CG_B) {
+          if (!pend_bits) {
+            if (S.cg32) load_chunk_bits<float>(I, I.mask[S.cur], x0, y0 + c * ch, fbits);
+            else load_chunk_bits<double>(I, I.mask[S.cur], x0, y0 + c * ch, fbits);
+          }
+          const int bx = c + 1 < nch ? x0 : nx0;
+          const int by = c + 1 < nch ? y0 + (c + 1) * ch : ny0;
+          if (nxt) {
+            if (S.cg32) load_chunk_bits<float>(I, I.mask[S.cur], bx, by, fbits_n);
+            else load_chunk_bits<double>(I, I.mask[S.cur], bx, by, fbits_n);
+          }
+        }
+        const bool ok = mbar_wait(smem_u32(&bars[sg]), (seq >> 1) & 1);
+        if (__syncthreads_or(!ok)) {
+          // a copy never completed: record it, give the other stage's copy (if
+          // one was issued) a bounded chance to land, and leave; the engine's
+          // loop then ends on its pass cap and the host reports the error
+          if (tid == 0) {
+            atomicOr(E.err, 1);
+            if (nxt) mbar_wait(smem_u32(&bars[sg ^ 1]), ((seq + 1) >> 1) & 1);
+          }
+          return;
+        }
+        if (S.pass == P_CG_B) {
+          if (S.cg32)
+            cgb_chunk<float>(I, st, x0, y0 + c * ch, (float)S.beta, fbits, I.p32[S.pcur ^ 1],
+                             I.Ap32, acc, ff);
+          else
+            cgb_chunk<double>(I, st, x0, y0 + c * ch, S.beta, fbits, I.p64[S.pcur ^ 1], I.Ap64,
+                              acc, ff);
+        } else {
+          const int ylim = min(ch, I.ny - (y0 + c * ch));
+          if (S.cg32)
+            cga_chunk<float>(I, st, x0, z * I.ny + y0 + c * ch, ylim, (float)S.alpha, I.w32,
+                             I.r32, acc, ff);
+          else
+            cga_chunk<double>(I, st, x0, z * I.ny + y0 + c * ch, ylim, S.alpha, I.w64, I.r64,
+                              acc, ff);
+        }
+        __syncthreads();  // the stage may be refilled
+        seq++;
+        pend = nxt;
+        pend_bits = nxt;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fbits[k] = fbits_n[k];
+      }
+    }
+    // fixed-order group reduction: every thread's sums go to shared memory;
+    // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
+    // butterfly).  The FP32 passes reduce their float-float accumulators in
+    // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
+    const bool ffred = tma && S.cg32;
+    const int ns = ffred ? 1 : n_sums(S.pass, S.first_cg);
+    if (ffred) {
+      s_ffh[tid] = ff.hi;
+      s_ffl[tid] = ff.lo;
+    } else {
+      for (int k = 0; k < ns; ++k) s_sum[k][tid] = acc.s[k];
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
       if (lane == 0) s_cnt[k][warp] = c;
     }
     __syncthreads();
-    if (warp == 0) {
-      double part[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int k = 0; k < ns; ++k) {
-        double v = s_sum[k][lane];
-        for (int j = 1; j < kWarps; ++j) v += s_sum[k][lane + 32 * j];
+    if (warp < ns) {
+      double v;
+      if (ffred) {
+        FF a{s_ffh[lane], s_ffl[lane]};
+        for (int j = 1; j < kWarps; ++j) a = ff_add(a, FF{s_ffh[lane + 32 * j], s_ffl[lane + 32 * j]});
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+          a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off), __shfl_xor_sync(FULL_MASK, a.lo, off)});
+        v = ff_val(a);
+      } else {
+        v = s_sum[warp][lane];
+        for (int j = 1; j < kWarps; ++j) v += s_sum[warp][lane + 32 * j];
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
-        part[k] = v;
       }
-      if (lane == 0) {
-        double* P = I.part + (long long)tile * kNRed;
-        for (int k = 0; k < 4; ++k) P[k] = part[k];
-        for (int k = 0; k < 3; ++k) {
-          int c = 0;
-          for (int w = 0; w < kWarps; ++w) c += s_cnt[k][w];
-          P[4 + k] = (double)c;
-        }
-        __threadfence();
-        const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, 1u);
-        s_last = (prev == (unsigned)(I.n_tiles - 1));
+      if (lane == 0) s_red[warp] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double* P = I.part + (long long)grp * kNRed;
+      for (int k = 0; k < 4; ++k) P[k] = k < ns ? s_red[k] : 0.0;
+      for (int k = 0; k < 3; ++k) {
+        int c = 0;
+        for (int w = 0; w < kWarps; ++w) c += s_cnt[k][w];
+        P[4 + k] = (double)c;
       }
+      __threadfence();
+      const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, 1u);
+      s_last = (prev == (unsigned)(I.n_groups - 1));
     }
     __syncthreads();
     if (!s_last) continue;
 
-    // last tile of this instance: reduce the tile slots in a fixed order
-    __threadfence();
-    const double* P0 = I.part;
-    double part[kNRed];
+    // last group of this instance: reduce the group slots in a fixed order.
+    // Thread j loads the 7 sums of groups j and j+256 (independent loads, all
+    // in flight at once), warps reduce by butterfly, and thread k adds the 8
+    // warp results of sum k.
+    if (tid == 0) __threadfence();
+    __syncthreads();
+    {
+      static_assert(kMaxGroups <= 2 * kThreads, "finalizer covers two groups per thread");
+      double v[kNRed - 1];
+      const double* P0 = I.part;
 #pragma unroll
-    for (int k = 0; k < kNRed; ++k) part[k] = 0.0;
-    for (int j = tid; j < I.n_tiles; j += kThreads) {
+      for (int k = 0; k < kNRed - 1; ++k) {
+        const double a = tid < I.n_groups ? __ldcg(P0 + (long long)tid * kNRed + k) : 0.0;
+        const double b =
+            tid + kThreads < I.n_groups ? __ldcg(P0 + (long long)(tid + kThreads) * kNRed + k) : 0.0;
+        v[k] = a + b;
+      }
 #pragma unroll
-      for (int k = 0; k < kNRed; ++k) part[k] += __ldcg(P0 + (long long)j * kNRed + k);
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < kNRed - 1; ++k) v[k] += __shfl_xor_sync(FULL_MASK, v[k], off);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kNRed - 1; ++k) s_sum[0][k * kWarps + warp] = v[k];
+      }
     }
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) {
-      double v = part[k];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
-      if (lane == 0) s_sum[0][k * kWarps + warp] = v;
+    __syncthreads();
+    if (tid < kNRed - 1) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += s_sum[0][tid * kWarps + w];
+      s_red[tid] = v;
     }
     __syncthreads();
     if (tid == 0) {
-      for (int k = 0; k < kNRed; ++k) {
-        double v = 0.0;
-        for (int w = 0; w < kWarps; ++w) v += s_sum[0][k * kWarps + w];
-        s_red[k] = v;
-      }
+      s_red[kNRed - 1] = 0.0;
       Ctl& C = E.ctl[tr.x];
       C.arrive = 0u;
       finalize(I, C, s_red, E.live);
@@ -1175,14 +1569,16 @@ int pass_grid(int n_work) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel, kThreads, 0);
+    cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel, kThreads, kDynSmem);
     cached = sms * (per > 0 ? per : 1);
   }
   return n_work < cached ? (n_work > 0 ? n_work : 1) : cached;
 }
 
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s) {
-  pass_kernel<<<n_blocks, kThreads, 0, s>>>(E);
+  pass_grid(1);  // sets the shared-memory attribute once
+  pass_kernel<<<n_blocks, kThreads, kDynSmem, s>>>(E);
   return cudaGetLastError();
 }
 

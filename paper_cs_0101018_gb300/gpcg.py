@@ -71,7 +71,7 @@ _SIGNATURES = [
     ("gpcg_result", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(gpcg_stats)]),
     ("gpcg_masked_spmv", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_double), C.c_int, C.c_void_p]),
-    ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+    ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("gpcg_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(gpcg_options),
                                      C.POINTER(C.c_void_p)]),
@@ -224,12 +224,12 @@ def gpcg_masked_spmv(prob: Problem, free_mask, p, precision=FP64, stream=None):
     return y, pap.value
 
 
-def gpcg_time_masked_spmv(prob: Problem, precision=FP64, reps=20, stream=None):
+def gpcg_time_masked_spmv(prob: Problem, precision=FP64, reps=20, flush_l2=True, stream=None):
     """(ms per launch, algorithmic bytes per launch) of the masked product."""
     ms, by = C.c_double(), C.c_double()
     sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-    _check(load().gpcg_time_masked_spmv(prob.handle, precision, reps, sp, C.byref(ms),
-                                        C.byref(by)))
+    _check(load().gpcg_time_masked_spmv(prob.handle, precision, reps, int(bool(flush_l2)), sp,
+                                        C.byref(ms), C.byref(by)))
     return ms.value, by.value
 
 
