@@ -169,6 +169,29 @@ gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int 
                                   void* cuda_stream, double* ms_per_launch,
                                   double* bytes_per_launch);
 
+/* The product of gpcg_masked_spmv (FP64) for callers that cannot allocate
+ * device memory: processes whose device memory belongs entirely to their own
+ * pool allocator, and latency-critical loops that cannot take the device-wide
+ * synchronisation that cudaMalloc / cudaFree may cause.  The paper has no
+ * counterpart; this is a deployment variant of the reduced-Hessian product.
+ *
+ * Computes y = Z Z' A Z Z' p and, if pAp != NULL, writes <p_F, y_F> to the
+ * host or device address pAp (the call then waits for the stream).  A's
+ * bands, free_mask (one byte per point, nonzero = free), p and y must be
+ * device pointers owned by the caller; nothing is copied or allocated.  The
+ * only scratch is a fixed array of about 33 KB in device memory, held by every
+ * GPU that loads the library until the process exits; it allows at most 4096
+ * tiles of 64x32 points (for example 8.4e6 points on a 2-D grid), and larger
+ * problems are rejected with GPCG_ERR_ARG.  The first call on a device looks
+ * up that array's device address, so make the first call on each device
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose kernels overlap on the GPU (different streams, other host threads)
+ * race and must be serialised by the caller.
+ * Errors: GPCG_ERR_ARG (NULL, host pointer, bad size, too large), GPCG_ERR_CUDA. */
+gpcg_status gpcg_masked_spmv_noalloc(const gpcg_stencil* A, const uint8_t* free_mask,
+                                     const double* p, double* y, double* pAp,
+                                     void* cuda_stream);
+
 /* ---- continuous-batching server --------------------------------------- */
 
 typedef struct gpcg_server gpcg_server;

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpcg.so")
-SOURCES = ["gpcg_kernels.cu", "gpcg_api.cu"]
+SOURCES = ["gpcg_kernels.cu", "gpcg_api.cu", "gpcg_noalloc.cu"]
 HEADERS = ["engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

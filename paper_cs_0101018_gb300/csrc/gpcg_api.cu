@@ -1179,4 +1179,10 @@ extern "C" void gpcg_server_destroy(gpcg_server* s) {
 
 extern "C" const char* gpcg_last_error(void) { return g_err; }
 
+namespace gpcg {
+// Lets the other translation units of the library report through
+// gpcg_last_error().
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace gpcg
+
 extern "C" const char* gpcg_version(void) { return "gpcg-gb300 0.1 (sm_103a)"; }

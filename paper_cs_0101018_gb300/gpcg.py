@@ -73,6 +73,8 @@ _SIGNATURES = [
                                    C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("gpcg_masked_spmv_noalloc", C.c_int, [C.POINTER(gpcg_stencil), C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     ("gpcg_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(gpcg_options),
                                      C.POINTER(C.c_void_p)]),
     ("gpcg_server_submit", C.c_int, [C.c_void_p, C.POINTER(gpcg_stencil), C.c_void_p,
