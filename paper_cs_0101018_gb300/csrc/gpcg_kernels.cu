@@ -1210,7 +1210,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ float s_ffh[kThreads], s_ffl[kThreads];
   __shared__ int s_cnt[3][kWarps];
   __shared__ double s_red[kNRed];
-  __shared__ int s_t, s_inst, s_last;
+  __shared__ int s_t, s_inst, s_last, s_skip;
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1243,7 +1243,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     const int2 tr = __ldg(E.tiles + t);
     if (tr.x != s_inst) {
       __syncthreads();  // everyone compared against the old s_inst
-      if (tid < (int)(sizeof(DevInst) / 8))
+      if (tid == 0) s_skip = E.ctl[tr.x].pass == P_NONE;
+      __syncthreads();
+      // a finished instance's groups are skipped without loading its descriptor
+      if (!s_skip && tid < (int)(sizeof(DevInst) / 8))
         reinterpret_cast<long long*>(&sI)[tid] =
             __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
       if (tid == 0) {
@@ -1259,7 +1262,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         s_inst = tr.x;
       }
       __syncthreads();
-      if (tid == 0 && sI.tmaps && (sS.pass == P_CG_A || sS.pass == P_CG_B)) {
+      if (tid == 0 && !s_skip && sI.tmaps && (sS.pass == P_CG_A || sS.pass == P_CG_B)) {
         const bool f32 = sS.cg32 != 0;
         if (f32 ? sI.tma32 : sI.tma64) {
           const int lo = f32 ? M32_RH : M64_RH;

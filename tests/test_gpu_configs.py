@@ -1,0 +1,181 @@
+"""The five workloads at their full sizes, through the C ABI, in the launch
+configuration the benchmark uses.
+
+Where the oracle finishes in seconds (the 1600x1600 QP, small batch members,
+reduced 3-D grids) the result is compared with it element by element;
+otherwise the properties that hold at any size are checked with the oracle's
+own census of the returned point (||grad_Omega q|| <= tau in FP64, x in the box
+bit for bit, active/binding counts), plus the agreement of the FP64 and mixed
+GPU results within the tolerance implied by the termination test.
+Tolerances are those of test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import gpcg_inputs as gi
+import oracle
+
+g = pytest.importorskip("paper_cs_0101018_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_err(x, ref):
+    return float(np.max(np.abs(x - ref)) / max(1.0, float(np.max(np.abs(ref)))))
+
+
+def _active_sets_agree(qp, x, ref, band=1e-8):
+    act_g = (x == qp.l) | (x == qp.u)
+    act_o = (ref == qp.l) | (ref == qp.u)
+    near = (np.abs(ref - qp.l) <= band) | (np.abs(ref - qp.u) <= band)
+    return bool(np.all((act_g == act_o) | near))
+
+
+def _check_properties(qp, x, st):
+    """Certified at any size: x in Omega exactly and the FP64 census of x (by
+    the oracle) meets the tolerance the GPU reported."""
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    c = oracle.census(qp, x)
+    assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9)
+    assert c.n_active == st["n_active"]
+    assert c.n_binding == st["n_binding"]
+    assert np.isclose(c.q, st["q"], rtol=1e-10, atol=1e-10)
+
+
+@pytest.fixture(scope="module")
+def large():
+    qp = gi.single_large()
+    ref = oracle.solve(qp, tau_rel=1e-8)
+    assert ref.status == 0
+    return qp, ref
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-5)])
+def test_single_large_matches_oracle(large, prec, tol):
+    qp, ref = large
+    prob = g.gpcg_problem_create(qp)
+    g.gpcg_solve(prob, g.default_options(tau_rel=1e-8, precision=prec))
+    x, st = g.gpcg_result(prob)
+    assert _rel_err(x, ref.x) <= tol
+    assert _active_sets_agree(qp, x, ref.x)
+    _check_properties(qp, x, st)
+
+
+def test_single_large_bench_tolerance_properties():
+    """The benchmark's own setting (tau_rel 1e-6, mixed and FP64)."""
+    qp = gi.single_large()
+    for prec in (g.MIXED, g.FP64):
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, g.default_options(tau_rel=1e-6, precision=prec))
+        x, st = g.gpcg_result(prob)
+        assert st["status"] == 0
+        _check_properties(qp, x, st)
+
+
+def test_precision_stress_3d():
+    """128^3 7-point, condition ~1e5: FP64 and mixed (FP32 coefficients with
+    the FP64 refinement) both certified by the FP64 census; their distance is
+    within what the two termination tests allow (||x - x*|| <= ||pg|| /
+    lambda_min for each)."""
+    qp = gi.precision_stress()
+    res = {}
+    for prec in (g.FP64, g.MIXED):
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, g.default_options(tau_rel=1e-8, precision=prec))
+        x, st = g.gpcg_result(prob)
+        assert st["status"] == 0
+        _check_properties(qp, x, st)
+        res[prec] = (x, st)
+    (x64, s64), (x32, s32) = res[g.FP64], res[g.MIXED]
+    bound = (s64["pg_norm"] + s32["pg_norm"]) / qp.shift
+    assert np.linalg.norm(x64 - x32) <= bound * (1 + 1e-6)
+    assert _rel_err(x32, x64) <= 1e-5
+
+
+def test_precision_stress_reduced_matches_oracle():
+    """The same generator on a 24^3 grid, where the oracle runs in seconds."""
+    qp = gi.precision_stress(24)
+    ref = oracle.solve(qp, tau_rel=1e-10)
+    for prec, tol in ((g.FP64, 1e-9), (g.MIXED, 1e-5)):
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, g.default_options(tau_rel=1e-10, precision=prec))
+        x, st = g.gpcg_result(prob)
+        assert _rel_err(x, ref.x) <= tol
+        assert _active_sets_agree(qp, x, ref.x)
+
+
+def test_batched_512():
+    """512 instances, sides uniform in [64, 512], one engine run (mixed): every
+    result is certified; the smallest ones match the oracle; a sample is
+    bit-identical to the same instance solved alone."""
+    sides = gi.batch_sides()
+    qps = [gi.batch_instance(k, s) for k, s in enumerate(sides)]
+    opts = g.default_options(tau_rel=1e-6, precision=g.MIXED)
+    probs = [g.gpcg_problem_create(qp) for qp in qps]
+    assert g.gpcg_solve_batch(probs, opts, check=False) == 0
+    results = [g.gpcg_result(p) for p in probs]
+    for qp, (x, st) in zip(qps, results):
+        assert st["status"] == 0
+        _check_properties(qp, x, st)
+    order = np.argsort(sides)
+    for k in list(order[:4]):
+        ref = oracle.solve(qps[k], tau_rel=1e-6)
+        assert _rel_err(results[k][0], ref.x) <= 1e-4  # both only certified to tau_rel 1e-6
+    for k in list(order[:2]) + [int(order[len(order) // 2])]:
+        prob = g.gpcg_problem_create(qps[k])
+        g.gpcg_solve(prob, opts)
+        xa, _ = g.gpcg_result(prob)
+        assert np.array_equal(xa, results[k][0])
+
+
+def test_serving_same_alone_and_in_the_mix():
+    """Continuous batching: requests of different sizes and dimensions arrive
+    while others run; each result equals the same QP solved alone, bit for
+    bit, and latencies are recorded."""
+    reqs = [r for r in gi.serving_trace(rate=200.0, duration=2.0) if
+            (r.side ** r.dim) <= 300_000][:24]
+    assert len(reqs) >= 12 and any(r.dim == 3 for r in reqs)
+    qps = [gi.serving_instance(r) for r in reqs]
+    opts = g.default_options(tau_rel=1e-6, precision=g.MIXED)
+    srv = g.Server(hbm_budget=2 << 30, max_live=8, opts=opts)
+    tickets = []
+    pending = list(qps)
+    # submit in waves so that new requests join while earlier ones are live
+    while pending or any(not srv.done(t) for t in tickets):
+        for _ in range(3):
+            if pending:
+                tickets.append(srv.submit(pending.pop(0)))
+        srv.step(16)
+    lat = []
+    for qp, tk in zip(qps, tickets):
+        st, latency = srv.stats(tk)
+        assert st["status"] == 0
+        lat.append(latency)
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, opts)
+        xa, _ = g.gpcg_result(prob)
+        assert np.array_equal(xa, tk.x)
+    q, r, f = srv.counts()
+    assert (q, r, f) == (0, 0, len(qps))
+    assert all(l > 0 for l in lat)
+    srv.close()
+
+
+def test_serving_budget_and_cancel():
+    qp_big = gi.grid_qp_2d(400, 400, seed=9, shift=1e-2)
+    qp_small = gi.grid_qp_2d(50, 50, seed=10, shift=1e-2)
+    opts = g.default_options(tau_rel=1e-6, precision=g.FP64)
+    srv = g.Server(hbm_budget=8 << 20, max_live=4, opts=opts)
+    with pytest.raises(g.GpcgError) as e:
+        srv.submit(qp_big)  # 160k points do not fit an 8 MB budget at all
+    assert e.value.status == g.ERR_BUDGET
+    t1 = srv.submit(qp_small)
+    t2 = srv.submit(qp_small)
+    srv.cancel(t2)
+    while not srv.done(t1):
+        srv.step(16)
+    st, _ = srv.stats(t1)
+    assert st["status"] == 0
+    with pytest.raises(g.GpcgError) as e:
+        srv.stats(t2)
+    assert e.value.status == g.ERR_CANCELLED
+    srv.close()
