@@ -308,14 +308,41 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Small fixed workloads for profiler captures: `solve` runs `--steps`
+    solves of the benchmark QP, `spmv` a few launches of the masked product
+    alone (L2 flushed before each)."""
+    import torch
+    import paper_cs_0101018_gb300 as g
+    prec = g.MIXED if args.precision == "mixed" else g.FP64
+    qp = gi.single_large()
+    prob = g.gpcg_problem_create(qp)
+    if args.profile == "solve":
+        for _ in range(args.steps):
+            g.gpcg_solve(prob, g.default_options(tau_rel=TAU_REL, precision=prec))
+        _, st = g.gpcg_result(prob)
+        print(json.dumps({"profile": "solve", "precision": args.precision, "passes": st["passes"],
+                          "launches": st["launches"]}))
+    else:
+        ms, by = g.gpcg_time_masked_spmv(prob, prec, reps=args.steps, flush_l2=True)
+        print(json.dumps({"profile": "spmv", "precision": args.precision, "us": 1000 * ms,
+                          "GB/s": by / ms / 1e6}))
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", choices=["solve", "spmv"], default=None,
+                    help="run a small fixed workload for a profiler capture instead")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -62,6 +62,14 @@ enum Pass : int {
 
 enum Dir : int { D_NEG_G = 0, D_W64 = 1, D_W32 = 2, D_ZERO = 3 };
 
+// Purpose of a P_CENSUS pass.
+enum CensusMode : int {
+  CM_INIT = 0,    // at x0: sets tau
+  CM_FINAL = 1,   // at the returned point: refreshes the statistics, ends the solve
+  CM_REFINE = 2,  // first FP64 census after the mixed phase met tau: closing FP64 CG
+  CM_RESUME = 3,  // first FP64 census after the mixed phase stalled: continue in FP64
+};
+
 // Status values mirror gpcg_status.
 enum Status : int {
   S_OK = 0,
@@ -84,8 +92,12 @@ struct Ctl {
   int pass, status, done, cur, pcur, cg32, first_cg, dir;
   int trial_gp, refining, refined, continue_cg, hold, final_census;
   int outer_iters, gp_j, ls_i, cg_j, gp_iters, cg_iters, ls_trials, refine_cg_iters;
-  int passes, pad1;
-  unsigned arrive, pad2;
+  int passes;
+  int gp32;          // mixed phase: census / GP / search passes stream FP32 (see kernels)
+  unsigned arrive;
+  int census_mode;   // CM_* : what the next P_CENSUS is for
+  int stall, pad3;   // mixed phase: outer iterates without progress of ||pg||
+  double best_pg2;   // mixed phase: smallest ||pg||^2 seen
   double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
   double pg2, nA, nB, xgb, gF2;  // census of the current iterate
   double alg_bytes;              // algorithmic HBM bytes of all passes so far
@@ -105,6 +117,7 @@ struct DevInst {
   unsigned* mask[2];
   double *r64, *w64, *p64[2], *Ap64;
   float *r32, *w32, *p32[2], *Ap32;
+  float *x32[2], *g32[2], *b32, *l32, *u32;  // FP32 copies streamed in the mixed phase
   Opts opt;
 };
 

@@ -194,9 +194,11 @@ static size_t arena64_bytes(const gpcg_problem* p) {
   return (size_t)(p->kc + 12) * vec + 2 * msk + part + maps;
 }
 
+// FP32 bands, the FP32 CG vectors r, w, p[2], Ap, and the FP32 copies of the
+// mixed phase x[2], g[2], b, l, u.
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
-  return (size_t)(p->kc + 5) * vec;
+  return (size_t)(p->kc + 5 + 7) * vec;
 }
 
 static void carve64(gpcg_problem* p) {
@@ -337,6 +339,17 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.p32[0] = take();
   I.p32[1] = take();
   I.Ap32 = take();
+  for (int k = 0; k < 2; ++k) I.x32[k] = take();
+  for (int k = 0; k < 2; ++k) I.g32[k] = take();
+  float* b32 = take();
+  float* l32 = take();
+  float* u32 = take();
+  CK(launch_to_float(I.b, b32, p->pn, s));
+  CK(launch_to_float(I.l, l32, p->pn, s));
+  CK(launch_to_float(I.u, u32, p->pn, s));
+  I.b32 = b32;
+  I.l32 = l32;
+  I.u32 = u32;
   CK(launch_to_float(I.diag, d32, p->pn, s));
   CK(launch_to_float(I.cx, x32, p->pn, s));
   CK(launch_to_float(I.cy, y32, p->pn, s));
@@ -640,7 +653,9 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   gpcg_status st = sc.ensure(count, tiles);
   if (st != GPCG_OK) return st;
   std::vector<DevInst> insts(count);
-  std::vector<Ctl> ctl(count, fresh_ctl());
+  Ctl c0 = fresh_ctl();
+  c0.gp32 = o->precision == GPCG_MIXED ? 1 : 0;  // the mixed phase streams FP32
+  std::vector<Ctl> ctl(count, c0);
   std::vector<int2> table((size_t)tiles);
   long long t = 0;
   for (int k = 0; k < count; ++k) {
@@ -1065,6 +1080,7 @@ extern "C" gpcg_status gpcg_server_step(gpcg_server* s, int passes) {
     DevInst I;
     if ((st = prepare_instance(r->prob, &s->opt, st_, &I)) != GPCG_OK) return st;
     Ctl C = fresh_ctl();
+    C.gp32 = s->opt.precision == GPCG_MIXED ? 1 : 0;
     CK(cudaMemcpyAsync(s->sc.d_insts + slot, &I, sizeof(DevInst), cudaMemcpyHostToDevice, st_));
     CK(cudaMemcpyAsync(s->sc.d_ctl + slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice, st_));
     r->slot = slot;

@@ -85,6 +85,17 @@ __device__ __forceinline__ double pg_comp(double x, double g, double l, double u
   return g;
 }
 
+// FP32 projection and projected gradient of the mixed phase (the exact FP64
+// versions above decide the active set; these only feed FP32 products).
+__device__ __forceinline__ float mid3f(float l, float u, float x) { return fminf(fmaxf(x, l), u); }
+
+__device__ __forceinline__ float pg_compf(bool al, bool au, float g) {
+  if (al && au) return 0.0f;
+  if (al) return g < 0.0f ? g : 0.0f;
+  if (au) return g > 0.0f ? g : 0.0f;
+  return g;
+}
+
 // ---------------------------------------------- FP32 compensated dot (Dot2) --
 
 struct FF {
@@ -226,7 +237,7 @@ struct Acc {
 
 // What a tile needs from the instance's control block (read once per tile).
 struct Snap {
-  int pass, cur, pcur, cg32, first_cg, dir;
+  int pass, cur, pcur, cg32, first_cg, dir, gp32, pad;
   double alpha, beta;
 };
 
@@ -538,6 +549,198 @@ struct OpTrial {
   }
 };
 
+
+// ------------------------------------------------- mixed-phase FP32 passes --
+//
+// In the mixed phase the census, the alpha0 pass and the trials apply the FP32
+// stencil to FP32 operands and keep the gradient in FP32, but the iterate,
+// the projection onto the box and the active/binding sets stay exact FP64:
+// every point's new x is P[x + alpha d] in FP64 and its status is decided by
+// exact comparisons with l and u.  Sums use the compensated FP32 accumulator.
+
+// P_CENSUS (mixed): operand x32; g32 = A32 x32 + b32; |A|, |B|, ||pg||^2.
+struct OpCensus32 {
+  using T = float;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const float* __restrict__ x32;
+  float* g_out;
+  unsigned* m_out;
+  FF* ff;  // [1]: ||pg||^2
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    ld2(x32, pidx(I, y, z, e0), v0, v1, o);
+  }
+  __device__ float operand_at(long long i, int, int, int) const { return __ldg(x32 + i); }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const float[2], const float av[2], Acc& acc) const {
+    double xv[2], l[2], u[2];
+    float b[2], g[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    ld2(I.b32, i, v0, v1, b);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      g[k] = av[k] + b[k];
+      const bool al = deq(xv[k], l[k]), au = deq(xv[k], u[k]);
+      const bool act = al || au;
+      fr[k] = ok && !act;
+      if (ok) {
+        const float pg = pg_compf(al, au, g[k]);
+        ff_fma(ff[0], pg, pg);
+        acc.c[0] += act;
+        acc.c[1] += (al && g[k] >= 0.0f) || (au && g[k] <= 0.0f);
+      }
+    }
+    st2(g_out, i, v0, v1, g[0], g[1]);
+    write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// P_GP_ALPHA (mixed): operand pg from g32 and the free bits (an active point
+// sits at l or u: the FP32 copies tell which); <pg,pg>, <pg, A32 pg>.
+struct OpGpAlpha32 {
+  using T = float;
+  const DevInst& I;
+  const float* __restrict__ x32;
+  const float* __restrict__ g32;
+  const unsigned* __restrict__ m;
+  FF* ff;  // [2]
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ float pg_at(long long i, bool fr) const {
+    const float g = __ldg(g32 + i);
+    if (fr) return g;
+    const float xv = __ldg(x32 + i);
+    return pg_compf(xv == __ldg(I.l32 + i), xv == __ldg(I.u32 + i), g);
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    const unsigned fb = v0 ? my_free_bits(I, m, y, z, e0) : 0u;
+    o[0] = v0 ? pg_at(i, fb & 1u) : 0.0f;
+    o[1] = v1 ? pg_at(i + 1, fb & 2u) : 0.0f;
+  }
+  __device__ float operand_at(long long i, int y, int z, int col) const {
+    return pg_at(i, free_bit(I, m, y, z, col));
+  }
+  __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const float v[2],
+                         const float av[2], Acc&) const {
+    if (v0) {
+      ff_fma(ff[0], v[0], v[0]);
+      ff_fma(ff[1], v[0], av[0]);
+    }
+    if (v1) {
+      ff_fma(ff[0], v[1], v[1]);
+      ff_fma(ff[1], v[1], av[1]);
+    }
+  }
+};
+
+// P_TRIAL (mixed): operand P[x32 + alpha d] in FP32 for the product; the new
+// iterate P[x + alpha d] in FP64 with its exact status; g32t = A32 xt32 + b32;
+// <g, s>, <s, gt>, ||pg||^2; s is alpha d where the point stays free and
+// exact otherwise.
+template <int DK>
+struct OpTrial32 {
+  using T = float;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const float* __restrict__ x32;
+  const float* __restrict__ g32;
+  const float* __restrict__ w32;
+  float alpha;
+  double alpha_d;
+  double* xt_out;
+  float* xt32_out;
+  float* gt_out;
+  unsigned* m_out;
+  const unsigned* __restrict__ m_old;
+  FF* ff;  // [3]: <g,s>, <s,gt>, ||pg||^2
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ float dir_at(long long i) const {
+    return DK == D_NEG_G ? -__ldg(g32 + i) : __ldg(w32 + i);
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    float xv[2], l[2], u[2], d[2];
+    ld2(x32, i, v0, v1, xv);
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
+    if (DK == D_NEG_G) {
+      ld2(g32, i, v0, v1, d);
+      d[0] = -d[0];
+      d[1] = -d[1];
+    } else {
+      ld2(w32, i, v0, v1, d);
+    }
+    o[0] = v0 ? mid3f(l[0], u[0], fmaf(alpha, d[0], xv[0])) : 0.0f;
+    o[1] = v1 ? mid3f(l[1], u[1], fmaf(alpha, d[1], xv[1])) : 0.0f;
+  }
+  __device__ float operand_at(long long i, int, int, int) const {
+    return mid3f(__ldg(I.l32 + i), __ldg(I.u32 + i), fmaf(alpha, dir_at(i), __ldg(x32 + i)));
+  }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const float v[2], const float av[2], Acc& acc) const {
+    double xv[2], l[2], u[2], xt[2];
+    float g[2], b[2], gt[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    ld2(g32, i, v0, v1, g);
+    ld2(I.b32, i, v0, v1, b);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      const float d = DK == D_NEG_G ? -g[k] : (ok ? __ldg(w32 + i + k) : 0.0f);
+      xt[k] = ok ? mid3(l[k], u[k], fma(alpha_d, (double)d, xv[k])) : 0.0;
+      gt[k] = av[k] + b[k];
+      const bool al = deq(xt[k], l[k]), au = deq(xt[k], u[k]);
+      const bool act = al || au;
+      fr[k] = ok && !act;
+      if (ok) {
+        float sk;
+        if (!act) sk = alpha * d;
+        else if (deq(xt[k], xv[k])) sk = 0.0f;
+        else sk = (float)(xt[k] - xv[k]);
+        ff_fma(ff[0], g[k], sk);
+        ff_fma(ff[1], sk, gt[k]);
+        const float pg = pg_compf(al, au, gt[k]);
+        ff_fma(ff[2], pg, pg);
+        acc.c[0] += act;
+        acc.c[1] += (al && gt[k] >= 0.0f) || (au && gt[k] <= 0.0f);
+      }
+    }
+    st2(xt_out, i, v0, v1, xt[0], xt[1]);
+    st2(xt32_out, i, v0, v1, v[0], v[1]);
+    st2(gt_out, i, v0, v1, gt[0], gt[1]);
+    acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
 // P_CG_B: operand p = -r + beta*p_old (FIRST: p = -g on the free set), the
 // masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap> (FIRST: also
 // ||r||^2 for r = g_F).  TV is the streamed precision (double, or float in the
@@ -552,6 +755,7 @@ struct OpCgB {
   const double* __restrict__ g;
   const unsigned* __restrict__ m;
   T beta;
+  const float* __restrict__ g32;  // mixed phase: the gradient is FP32 (FIRST)
   T* p_out;
   T* ap_out;
   T* r_out;
@@ -573,7 +777,14 @@ struct OpCgB {
     const long long i = pidx(I, y, z, e0);
     if (FIRST) {
       double gv[2];
-      ld2(g, i, v0, v1, gv);
+      if (g32) {
+        float gf[2];
+        ld2(g32, i, v0, v1, gf);
+        gv[0] = gf[0];
+        gv[1] = gf[1];
+      } else {
+        ld2(g, i, v0, v1, gv);
+      }
       const unsigned fb = (v0 ? my_free_bits(I, m, y, z, e0) : 0u);
       o[0] = (fb & 1u) ? (T)(-gv[0]) : T(0);
       o[1] = (fb & 2u) ? (T)(-gv[1]) : T(0);
@@ -587,7 +798,8 @@ struct OpCgB {
   }
   __device__ T operand_at(long long i, int y, int z, int col) const {
     if (FIRST) {
-      return free_bit(I, m, y, z, col) ? (T)(-__ldg(g + i)) : T(0);
+      if (!free_bit(I, m, y, z, col)) return T(0);
+      return g32 ? (T)(-__ldg(g32 + i)) : (T)(-__ldg(g + i));
     } else {
       return fma(beta, __ldg(p_old + i), -__ldg(r + i));
     }
@@ -626,7 +838,7 @@ struct OpCgB {
 template <class T>
 __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T* __restrict__ p,
                                           const T* __restrict__ ap, double alpha, int x0, int y0,
-                                          int z, Acc& acc) {
+                                          int z, Acc& acc, FF* ffs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ya = y0 + warp * kRY;
   if (ya >= I.ny) return;
@@ -635,7 +847,7 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T*
   const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
   if (!v0) return;
   const T a = (T)alpha;
-  FF ff{0.f, 0.f};
+  FF& ff = ffs[0];
   for (int y = ya; y < yb; ++y) {
     const long long i = pidx(I, y, z, e0);
     T wv[2], rv[2], pv[2], av[2];
@@ -657,11 +869,11 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T*
       acc.s[0] = fma((double)rv[1], (double)rv[1], acc.s[0]);
     }
   }
-  if (sizeof(T) == 4) acc.s[0] += ff_val(ff);
 }
 
 // P_START: x = P[x0], x0 the given start or the default l -> u -> 0.
-__device__ __forceinline__ void start_tile(const DevInst& I, double* x, int x0, int y0, int z) {
+__device__ __forceinline__ void start_tile(const DevInst& I, double* x, float* x32, int x0, int y0,
+                                           int z) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ya = y0 + warp * kRY;
   if (ya >= I.ny) return;
@@ -680,7 +892,9 @@ __device__ __forceinline__ void start_tile(const DevInst& I, double* x, int x0, 
 #pragma unroll
       for (int k = 0; k < 2; ++k) s[k] = isfinite(l[k]) ? l[k] : (isfinite(u[k]) ? u[k] : 0.0);
     }
-    st2(x, i, v0, v1, mid3(l[0], u[0], s[0]), mid3(l[1], u[1], s[1]));
+    const double a = mid3(l[0], u[0], s[0]), b = mid3(l[1], u[1], s[1]);
+    st2(x, i, v0, v1, a, b);
+    if (x32) st2(x32, i, v0, v1, (float)a, (float)b);
   }
 }
 
@@ -693,11 +907,14 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   const double sv = C.cg32 ? 4.0 : 8.0;
   double per = 0.0;
   switch (pass) {
-    case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0); break;
-    case P_CENSUS: per = 8.0 * kc + 40.0 + 0.125; break;
-    case P_GP_ALPHA: per = 8.0 * kc + 32.0; break;
+    case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
+    case P_CENSUS: per = C.gp32 ? 4.0 * kc + 36.125 : 8.0 * kc + 40.0 + 0.125; break;
+    case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 16.125 : 8.0 * kc + 32.0; break;
     case P_TRIAL:
-      per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
+      if (C.gp32)
+        per = 4.0 * kc + 64.25 + (C.dir == D_W32 ? 4.0 : 0.0);
+      else
+        per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
       break;
     case P_CG_B: per = sv * kc + (C.first_cg ? 8.0 + 4.0 * sv : 4.0 * sv) + 0.125; break;
     case P_CG_A: per = 6.0 * sv; break;
@@ -710,7 +927,17 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
 // and binding counts, ||pg|| and q at the returned point.
 __device__ void set_done(Ctl& C, int status) {
   C.status = status;
-  C.final_census = 1;
+  C.census_mode = CM_FINAL;
+  C.gp32 = 0;
+  C.pass = P_CENSUS;
+}
+
+// Leave the mixed phase: everything from here on is FP64, starting with an
+// FP64 census of the current iterate.
+__device__ void switch_fp64(Ctl& C, int mode) {
+  C.gp32 = 0;
+  C.refined = 1;
+  C.census_mode = mode;
   C.pass = P_CENSUS;
 }
 
@@ -756,7 +983,11 @@ __device__ void begin_outer(const DevInst& I, Ctl& C) {
 // ||grad_Omega q|| <= tau held.  In mixed precision the first time this
 // happens starts the closing FP64 CG phase on the identified face.
 __device__ void on_converged(const DevInst& I, Ctl& C) {
-  if (I.opt.mixed && I.opt.refine && !C.refined) {
+  if (C.gp32) {
+    // the FP32-streamed estimate met tau: certify in FP64 and, with refine,
+    // run the closing FP64 CG phase on the identified face
+    switch_fp64(C, I.opt.refine ? CM_REFINE : CM_RESUME);
+  } else if (I.opt.mixed && I.opt.refine && !C.refined) {
     C.refined = 1;
     C.refining = 1;
     C.continue_cg = 1;
@@ -783,12 +1014,36 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       C.xgb = red[1];
       C.nA = red[4];
       C.nB = red[5];
-      if (C.final_census) {
+      if (C.census_mode == CM_FINAL) {
         C.pass = P_NONE;
         C.done = 1;
         atomicSub(live, 1);
         break;
       }
+      if (C.census_mode == CM_REFINE) {  // closing FP64 CG phase on this face
+        C.census_mode = CM_INIT;
+        C.refining = 1;
+        C.continue_cg = 1;
+        C.eta2 = o.eta2_refine;
+        C.outer_iters++;
+        begin_cg(I, C);
+        break;
+      }
+      if (C.census_mode == CM_RESUME) {  // continue GPCG in FP64
+        C.census_mode = CM_INIT;
+        if (!isfinite(C.pg2)) {
+          set_done(C, S_NUMERIC);
+        } else if (sqrt(C.pg2) <= C.tau) {
+          set_done(C, S_OK);
+        } else {
+          C.eta2 = o.eta2;
+          C.continue_cg = 0;
+          begin_outer(I, C);
+        }
+        break;
+      }
+      C.best_pg2 = C.pg2;
+      C.stall = 0;
       C.pg0 = sqrt(C.pg2);
       C.tau = fmax(o.tau_abs, o.tau_rel * C.pg0);
       C.eta2 = o.eta2;
@@ -849,6 +1104,15 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
             on_converged(I, C);
             break;
           }
+          if (C.gp32) {  // mixed phase: leave it when ||pg|| stops improving
+            if (C.pg2 < 0.98 * C.best_pg2) {
+              C.best_pg2 = C.pg2;
+              C.stall = 0;
+            } else if (++C.stall >= 5) {
+              switch_fp64(C, CM_RESUME);
+              break;
+            }
+          }
           if (C.nB == C.nA) {  // Eq. cgstop3: B(x) = A(x)
             C.eta2 = fmax(C.eta2 * o.eta2_shrink, o.eta2_floor);
             C.continue_cg = 1;
@@ -861,7 +1125,10 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       } else {
         C.ls_i++;
         if (C.ls_i > o.max_ls) {
-          set_done(C, S_LINESEARCH);
+          // in the mixed phase the FP32 gradient may be too coarse for the
+          // sufficient-decrease test: continue in FP64 instead of failing
+          if (C.gp32) switch_fp64(C, CM_RESUME);
+          else set_done(C, S_LINESEARCH);
           break;
         }
         if (C.dir != D_ZERO) C.alpha = ldexp(C.trial_gp ? C.alpha0 : 1.0, -C.ls_i);
@@ -1115,9 +1382,9 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, int
 // ------------------------------------------------------------------ kernel --
 
 // Number of FP64 sums each pass reduces.
-__device__ __forceinline__ int n_sums(int pass, int first) {
+__device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
   switch (pass) {
-    case P_CENSUS: return 2;
+    case P_CENSUS: return gp32 ? 1 : 2;
     case P_GP_ALPHA: return 2;
     case P_TRIAL: return 3;
     case P_CG_B: return first ? 2 : 1;
@@ -1127,25 +1394,47 @@ __device__ __forceinline__ int n_sums(int pass, int first) {
 }
 
 __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
-                                         Acc& acc) {
+                                         Acc& acc, FF* ffs) {
   const int cur = S.cur, pcur = S.pcur;
   switch (S.pass) {
     case P_START:
-      start_tile(I, I.x[cur], x0, y0, z);
+      start_tile(I, I.x[cur], I.x32[cur], x0, y0, z);
       break;
     case P_CENSUS: {
-      OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur]};
-      stencil_tile(I, op, x0, y0, z, acc);
+      if (S.gp32) {
+        OpCensus32 op{I, I.x[cur], I.x32[cur], I.g32[cur], I.mask[cur], ffs};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
       break;
     }
     case P_GP_ALPHA: {
-      OpGpAlpha op{I, I.x[cur], I.g[cur]};
-      stencil_tile(I, op, x0, y0, z, acc);
+      if (S.gp32) {
+        OpGpAlpha32 op{I, I.x32[cur], I.g32[cur], I.mask[cur], ffs};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        OpGpAlpha op{I, I.x[cur], I.g[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
       break;
     }
     case P_TRIAL: {
       const double alpha = S.dir == D_ZERO ? 0.0 : S.alpha;
-      if (S.dir == D_W64) {
+      if (S.gp32) {
+        if (S.dir == D_W32) {
+          OpTrial32<D_W32> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
+                              I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.mask[cur ^ 1],
+                              I.mask[cur], ffs};
+          stencil_tile(I, op, x0, y0, z, acc);
+        } else {
+          OpTrial32<D_NEG_G> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
+                                I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.mask[cur ^ 1],
+                                I.mask[cur], ffs};
+          stencil_tile(I, op, x0, y0, z, acc);
+        }
+      } else if (S.dir == D_W64) {
         OpTrial<D_W64> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
                           I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
         stencil_tile(I, op, x0, y0, z, acc);
@@ -1161,29 +1450,27 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       break;
     }
     case P_CG_B: {
+      const float* g32 = S.gp32 ? I.g32[cur] : nullptr;
       if (S.cg32) {
-        FF ff[2] = {{0.f, 0.f}, {0.f, 0.f}};
         if (S.first_cg) {
-          OpCgB<float, true> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], 0.0f,
+          OpCgB<float, true> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], 0.0f, g32,
                                 I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
-                                I.diag32, I.cx32, I.cy32, I.cz32, ff};
+                                I.diag32, I.cx32, I.cy32, I.cz32, ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
           OpCgB<float, false> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], (float)S.beta,
-                                 I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
-                                 I.diag32, I.cx32, I.cy32, I.cz32, ff};
+                                 g32, I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
+                                 I.diag32, I.cx32, I.cy32, I.cz32, ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         }
-        acc.s[0] += ff_val(ff[0]);
-        acc.s[1] += ff_val(ff[1]);
       } else {
         if (S.first_cg) {
-          OpCgB<double, true> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], 0.0,
+          OpCgB<double, true> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], 0.0, nullptr,
                                  I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
                                  I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], S.beta,
+          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], S.beta, nullptr,
                                   I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
                                   I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
@@ -1193,9 +1480,9 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
     }
     case P_CG_A:
       if (S.cg32) {
-        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, S.alpha, x0, y0, z, acc);
+        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, S.alpha, x0, y0, z, acc, ffs);
       } else {
-        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, S.alpha, x0, y0, z, acc);
+        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, S.alpha, x0, y0, z, acc, ffs);
       }
       break;
     default:
@@ -1207,7 +1494,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ DevInst sI;
   __shared__ Snap sS;
   __shared__ double s_sum[4][kThreads];
-  __shared__ float s_ffh[kThreads], s_ffl[kThreads];
+  __shared__ float s_ffh[3][kThreads], s_ffl[3][kThreads];
   __shared__ int s_cnt[3][kWarps];
   __shared__ double s_red[kNRed];
   __shared__ int s_t, s_inst, s_last, s_skip;
@@ -1257,6 +1544,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         sS.cg32 = C.cg32;
         sS.first_cg = C.first_cg;
         sS.dir = C.dir;
+        sS.gp32 = C.gp32;
         sS.alpha = C.alpha;
         sS.beta = C.beta;
         s_inst = tr.x;
@@ -1282,7 +1570,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
-    FF ff{0.f, 0.f};
+    FF ffs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const bool tma = tma_pass(I, S);
     unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
     int pend_bits = 0;
@@ -1293,7 +1581,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       const int y0 = (rest % I.tiles_y) * kTY;
       const int z = rest / I.tiles_y;
       if (!tma) {
-        run_tile(I, S, x0, y0, z, acc);
+        run_tile(I, S, x0, y0, z, acc, ffs);
         continue;
       }
       // TMA pipeline: chunk k+1 (of this tile or the next tile of the group)
@@ -1347,18 +1635,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (S.pass == P_CG_B) {
           if (S.cg32)
             cgb_chunk<float>(I, st, x0, y0 + c * ch, (float)S.beta, fbits, I.p32[S.pcur ^ 1],
-                             I.Ap32, acc, ff);
+                             I.Ap32, acc, ffs[0]);
           else
             cgb_chunk<double>(I, st, x0, y0 + c * ch, S.beta, fbits, I.p64[S.pcur ^ 1], I.Ap64,
-                              acc, ff);
+                              acc, ffs[0]);
         } else {
           const int ylim = min(ch, I.ny - (y0 + c * ch));
           if (S.cg32)
             cga_chunk<float>(I, st, x0, z * I.ny + y0 + c * ch, ylim, (float)S.alpha, I.w32,
-                             I.r32, acc, ff);
+                             I.r32, acc, ffs[0]);
           else
             cga_chunk<double>(I, st, x0, z * I.ny + y0 + c * ch, ylim, S.alpha, I.w64, I.r64,
-                              acc, ff);
+                              acc, ffs[0]);
         }
         __syncthreads();  // the stage may be refilled
         seq++;
@@ -1370,15 +1658,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     }
     // fixed-order group reduction: every thread's sums go to shared memory;
     // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
-    // butterfly).  The FP32 passes reduce their float-float accumulators in
+    // butterfly).  FP32 passes reduce their float-float accumulators in
     // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
-    const bool ffred = tma && S.cg32;
-    const int ns = ffred ? 1 : n_sums(S.pass, S.first_cg);
-    if (ffred) {
-      s_ffh[tid] = ff.hi;
-      s_ffl[tid] = ff.lo;
-    } else {
-      for (int k = 0; k < ns; ++k) s_sum[k][tid] = acc.s[k];
+    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B) ? S.cg32 != 0
+                                                              : (S.pass != P_START && S.gp32 != 0);
+    const int ns = n_sums(S.pass, S.first_cg, S.gp32);
+    for (int k = 0; k < ns; ++k) {
+      if (ffred) {
+        s_ffh[k][tid] = ffs[k].hi;
+        s_ffl[k][tid] = ffs[k].lo;
+      } else {
+        s_sum[k][tid] = acc.s[k];
+      }
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -1389,8 +1680,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     if (warp < ns) {
       double v;
       if (ffred) {
-        FF a{s_ffh[lane], s_ffl[lane]};
-        for (int j = 1; j < kWarps; ++j) a = ff_add(a, FF{s_ffh[lane + 32 * j], s_ffl[lane + 32 * j]});
+        FF a{s_ffh[warp][lane], s_ffl[warp][lane]};
+        for (int j = 1; j < kWarps; ++j)
+          a = ff_add(a, FF{s_ffh[warp][lane + 32 * j], s_ffl[warp][lane + 32 * j]});
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
           a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off), __shfl_xor_sync(FULL_MASK, a.lo, off)});
