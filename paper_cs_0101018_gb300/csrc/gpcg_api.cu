@@ -22,7 +22,7 @@
 #include "engine.h"
 
 namespace gpcg {
-const void* pass_kernel_ptr();
+const void* pass_kernel_ptr(bool cond);
 int pass_grid(int n_work);
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s);
 cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
@@ -552,7 +552,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   void* kp[] = {&args};
   cudaKernelNodeParams k;
   memset(&k, 0, sizeof(k));
-  k.func = const_cast<void*>(pass_kernel_ptr());
+  k.func = const_cast<void*>(pass_kernel_ptr(mode == 0));
   k.gridDim = dim3((unsigned)pass_grid((int)tiles));
   k.blockDim = dim3(kThreads);
   k.sharedMemBytes = kDynSmem;

@@ -1490,6 +1490,10 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
   }
 }
 
+// kCond: the launch belongs to a WHILE-conditional graph whose condition this
+// kernel clears (a separate instantiation, because profilers cannot capture
+// graph nodes able to set a condition).
+template <bool kCond>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
   __shared__ DevInst sI;
   __shared__ Snap sS;
@@ -1508,7 +1512,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
 
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned np = atomicAdd(E.npass, 1u) + 1u;
-    if (E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
+    if (kCond && E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
       cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
     }
   }
@@ -1855,7 +1859,12 @@ template __global__ void unpad_kernel<float>(DevInst, const float*, double*);
 
 // ---------------------------------------------------------- host wrappers --
 
-const void* pass_kernel_ptr() { return (const void*)pass_kernel; }
+template __global__ void pass_kernel<true>(EngineArgs);
+template __global__ void pass_kernel<false>(EngineArgs);
+
+const void* pass_kernel_ptr(bool cond) {
+  return cond ? (const void*)pass_kernel<true> : (const void*)pass_kernel<false>;
+}
 
 int pass_grid(int n_work) {
   // persistent grid: the resident CTAs of the whole GPU, at most one per item
@@ -1864,8 +1873,9 @@ int pass_grid(int n_work) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel, kThreads, kDynSmem);
+    cudaFuncSetAttribute(pass_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    cudaFuncSetAttribute(pass_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel<false>, kThreads, kDynSmem);
     cached = sms * (per > 0 ? per : 1);
   }
   return n_work < cached ? (n_work > 0 ? n_work : 1) : cached;
@@ -1873,7 +1883,7 @@ int pass_grid(int n_work) {
 
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s) {
   pass_grid(1);  // sets the shared-memory attribute once
-  pass_kernel<<<n_blocks, kThreads, kDynSmem, s>>>(E);
+  pass_kernel<false><<<n_blocks, kThreads, kDynSmem, s>>>(E);
   return cudaGetLastError();
 }
 
