@@ -44,11 +44,21 @@ constexpr int kDynSmem = 2 * kStageBytes + 256;
 // box (64+2h) x (chunk+2) starting at (x0-h, y0-1); D = 64 x chunk;
 // CX = (64+h) x chunk from x0-h; CY = 64 x (chunk+1) from y0-1; the rest are
 // 64 x chunk boxes over the (nx, ny*nz) row space.
+//
+// The mixed-phase gradient-projection passes of a 2-D instance stage 8-row
+// chunks (census, trial) and 32-row chunks (alpha0): G8 = FP32 halo box
+// 72 x 10 from (x0-4, y0-1); G34 = FP32 halo box 72 x 34; the FP64 and FP32
+// interior boxes are 64 x 8; GCX = 68 x 8 from x0-4; GCY = 64 x 9 from y0-1.
 enum TMap : int {
   M32_RH = 0, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R, M32_P0, M32_P1, M32_AP,
   M64_RH, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R, M64_P0, M64_P1, M64_AP,
+  MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G8
+  MG_PGH0, MG_PGH1,                                                  // G34
+  MG_X0, MG_X1, MG_L, MG_U,                                          // FP64 64 x 8
+  MG_B32, MG_D32, MG_CX32, MG_CY32,                                  // FP32 64 x 8, GCX, GCY
   M_COUNT
 };
+constexpr int kGpMaps = M_COUNT - MG_X32H0;
 
 enum Pass : int {
   P_NONE = 0,
@@ -110,7 +120,8 @@ struct DevInst {
   long long n, plane;
   double* part;            // [n_groups][kNRed] group partial sums of this instance
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
-  int tma64, tma32;        // the FP64 / FP32 maps are valid
+  int tma64, tma32;        // the FP64 / FP32 CG maps are valid
+  int tma_gp, pad_t;       // the mixed-phase GP maps are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   double *x[2], *g[2];
@@ -118,6 +129,7 @@ struct DevInst {
   double *r64, *w64, *p64[2], *Ap64;
   float *r32, *w32, *p32[2], *Ap32;
   float *x32[2], *g32[2], *b32, *l32, *u32;  // FP32 copies streamed in the mixed phase
+  float* pg32[2];          // mixed phase: grad_Omega q at x[k] (FP32), read by alpha0
   Opts opt;
 };
 

@@ -194,11 +194,11 @@ static size_t arena64_bytes(const gpcg_problem* p) {
   return (size_t)(p->kc + 12) * vec + 2 * msk + part + maps;
 }
 
-// FP32 bands, the FP32 CG vectors r, w, p[2], Ap, and the FP32 copies of the
-// mixed phase x[2], g[2], b, l, u.
+// FP32 bands, the FP32 CG vectors r, w, p[2], Ap, and the FP32 arrays of the
+// mixed phase x[2], g[2], b, l, u, pg[2].
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
-  return (size_t)(p->kc + 5 + 7) * vec;
+  return (size_t)(p->kc + 5 + 9) * vec;
 }
 
 static void carve64(gpcg_problem* p) {
@@ -242,6 +242,7 @@ static void carve64(gpcg_problem* p) {
   I.tmaps = take(align256(sizeof(CUtensorMap) * M_COUNT));
   I.tma64 = 0;
   I.tma32 = 0;
+  I.tma_gp = 0;
   I.x0 = I.r64;  // a given start point is staged in r (unused until CG starts)
 }
 
@@ -311,6 +312,28 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   return true;
 }
 
+// Encode the maps of the mixed-phase gradient-projection passes (2-D only:
+// their chunks take halo rows from the same plane).
+static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
+  if (!have_encode() || p->dim != 2) return false;
+  DevInst& I = p->inst;
+  CUtensorMap m[kGpMaps];
+  CUtensorMap* q = m;
+  auto f32 = [&](const float* a, int bw, int bh) { return encode_map(q++, true, a, p, bw, bh); };
+  auto f64 = [&](const double* a) { return encode_map(q++, false, a, p, 64, 8); };
+  bool ok = f32(I.x32[0], 72, 10) && f32(I.x32[1], 72, 10) && f32(I.l32, 72, 10) &&
+            f32(I.u32, 72, 10) && f32(I.g32[0], 72, 10) && f32(I.g32[1], 72, 10) &&
+            f32(I.w32, 72, 10) && f32(I.pg32[0], 72, 34) && f32(I.pg32[1], 72, 34) &&
+            f64(I.x[0]) && f64(I.x[1]) && f64(I.l) && f64(I.u) && f32(I.b32, 64, 8) &&
+            f32(I.diag32, 64, 8) && f32(I.cx32, 68, 8) && f32(I.cy32, 64, 9);
+  if (!ok || q != m + kGpMaps) return false;
+  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MG_X32H0;
+  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return true;
+}
+
 static bool tma_disabled() {
   const char* e = getenv("GPCG_NO_TMA");
   return e && *e && *e != '0';
@@ -344,6 +367,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   float* b32 = take();
   float* l32 = take();
   float* u32 = take();
+  for (int k = 0; k < 2; ++k) I.pg32[k] = take();
   CK(launch_to_float(I.b, b32, p->pn, s));
   CK(launch_to_float(I.l, l32, p->pn, s));
   CK(launch_to_float(I.u, u32, p->pn, s));
@@ -359,6 +383,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.cy32 = y32;
   I.cz32 = z32;
   I.tma32 = (!tma_disabled() && make_maps(p, true, s)) ? 1 : 0;
+  I.tma_gp = (!tma_disabled() && make_gp_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
 }
 

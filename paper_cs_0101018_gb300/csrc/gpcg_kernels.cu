@@ -558,13 +558,15 @@ struct OpTrial {
 // every point's new x is P[x + alpha d] in FP64 and its status is decided by
 // exact comparisons with l and u.  Sums use the compensated FP32 accumulator.
 
-// P_CENSUS (mixed): operand x32; g32 = A32 x32 + b32; |A|, |B|, ||pg||^2.
+// P_CENSUS (mixed): operand x32; g32 = A32 x32 + b32, pg32; |A|, |B|,
+// ||pg||^2.
 struct OpCensus32 {
   using T = float;
   const DevInst& I;
   const double* __restrict__ x;
   const float* __restrict__ x32;
   float* g_out;
+  float* pg_out;
   unsigned* m_out;
   FF* ff;  // [1]: ||pg||^2
   __device__ const float* diag() const { return I.diag32; }
@@ -588,6 +590,7 @@ struct OpCensus32 {
     ld2(I.u, i, v0, v1, u);
     ld2(I.b32, i, v0, v1, b);
     bool fr[2];
+    float pg[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
@@ -595,50 +598,38 @@ struct OpCensus32 {
       const bool al = deq(xv[k], l[k]), au = deq(xv[k], u[k]);
       const bool act = al || au;
       fr[k] = ok && !act;
+      pg[k] = pg_compf(al, au, g[k]);
       if (ok) {
-        const float pg = pg_compf(al, au, g[k]);
-        ff_fma(ff[0], pg, pg);
+        ff_fma(ff[0], pg[k], pg[k]);
         acc.c[0] += act;
         acc.c[1] += (al && g[k] >= 0.0f) || (au && g[k] <= 0.0f);
       }
     }
     st2(g_out, i, v0, v1, g[0], g[1]);
+    st2(pg_out, i, v0, v1, pg[0], pg[1]);
     write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
   }
 };
 
-// P_GP_ALPHA (mixed): operand pg from g32 and the free bits (an active point
-// sits at l or u: the FP32 copies tell which); <pg,pg>, <pg, A32 pg>.
+// P_GP_ALPHA (mixed): operand pg32 (written by the census or the accepted
+// trial at x); <pg,pg>, <pg, A32 pg>.
 struct OpGpAlpha32 {
   using T = float;
   const DevInst& I;
-  const float* __restrict__ x32;
-  const float* __restrict__ g32;
-  const unsigned* __restrict__ m;
+  const float* __restrict__ pg32;
   FF* ff;  // [2]
   __device__ const float* diag() const { return I.diag32; }
   __device__ const float* cx() const { return I.cx32; }
   __device__ const float* cy() const { return I.cy32; }
   __device__ const float* cz() const { return I.cz32; }
-  __device__ float pg_at(long long i, bool fr) const {
-    const float g = __ldg(g32 + i);
-    if (fr) return g;
-    const float xv = __ldg(x32 + i);
-    return pg_compf(xv == __ldg(I.l32 + i), xv == __ldg(I.u32 + i), g);
-  }
   __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
     if (!row_ok(I, y, z)) {
       o[0] = o[1] = 0.0f;
       return;
     }
-    const long long i = pidx(I, y, z, e0);
-    const unsigned fb = v0 ? my_free_bits(I, m, y, z, e0) : 0u;
-    o[0] = v0 ? pg_at(i, fb & 1u) : 0.0f;
-    o[1] = v1 ? pg_at(i + 1, fb & 2u) : 0.0f;
+    ld2(pg32, pidx(I, y, z, e0), v0, v1, o);
   }
-  __device__ float operand_at(long long i, int y, int z, int col) const {
-    return pg_at(i, free_bit(I, m, y, z, col));
-  }
+  __device__ float operand_at(long long i, int, int, int) const { return __ldg(pg32 + i); }
   __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const float v[2],
                          const float av[2], Acc&) const {
     if (v0) {
@@ -669,6 +660,7 @@ struct OpTrial32 {
   double* xt_out;
   float* xt32_out;
   float* gt_out;
+  float* pg_out;
   unsigned* m_out;
   const unsigned* __restrict__ m_old;
   FF* ff;  // [3]: <g,s>, <s,gt>, ||pg||^2
@@ -712,6 +704,7 @@ struct OpTrial32 {
     ld2(g32, i, v0, v1, g);
     ld2(I.b32, i, v0, v1, b);
     bool fr[2];
+    float pgv[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
@@ -721,6 +714,7 @@ struct OpTrial32 {
       const bool al = deq(xt[k], l[k]), au = deq(xt[k], u[k]);
       const bool act = al || au;
       fr[k] = ok && !act;
+      pgv[k] = pg_compf(al, au, gt[k]);
       if (ok) {
         float sk;
         if (!act) sk = alpha * d;
@@ -728,8 +722,7 @@ struct OpTrial32 {
         else sk = (float)(xt[k] - xv[k]);
         ff_fma(ff[0], g[k], sk);
         ff_fma(ff[1], sk, gt[k]);
-        const float pg = pg_compf(al, au, gt[k]);
-        ff_fma(ff[2], pg, pg);
+        ff_fma(ff[2], pgv[k], pgv[k]);
         acc.c[0] += act;
         acc.c[1] += (al && gt[k] >= 0.0f) || (au && gt[k] <= 0.0f);
       }
@@ -737,6 +730,7 @@ struct OpTrial32 {
     st2(xt_out, i, v0, v1, xt[0], xt[1]);
     st2(xt32_out, i, v0, v1, v[0], v[1]);
     st2(gt_out, i, v0, v1, gt[0], gt[1]);
+    st2(pg_out, i, v0, v1, pgv[0], pgv[1]);
     acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
   }
 };
@@ -908,11 +902,11 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   double per = 0.0;
   switch (pass) {
     case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
-    case P_CENSUS: per = C.gp32 ? 4.0 * kc + 36.125 : 8.0 * kc + 40.0 + 0.125; break;
-    case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 16.125 : 8.0 * kc + 32.0; break;
+    case P_CENSUS: per = C.gp32 ? 4.0 * kc + 40.125 : 8.0 * kc + 40.0 + 0.125; break;
+    case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 4.0 : 8.0 * kc + 32.0; break;
     case P_TRIAL:
       if (C.gp32)
-        per = 4.0 * kc + 64.25 + (C.dir == D_W32 ? 4.0 : 0.0);
+        per = 4.0 * kc + 68.25 + (C.dir == D_W32 ? 4.0 : 0.0);
       else
         per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
       break;
@@ -1248,8 +1242,8 @@ __device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, in
 // and <p, Ap> for the chunk's interior.
 template <class T>
 __device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
-                                          T beta, const unsigned* fbits, T* p_out, T* ap_out,
-                                          Acc& acc, FF& ff) {
+                                          int rows, T beta, const unsigned* fbits, T* p_out,
+                                          T* ap_out, Acc& acc, FF& ff) {
   using G = ChunkGeo<T>;
   T* R = reinterpret_cast<T*>(st + G::OFF_R);
   const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
@@ -1267,7 +1261,7 @@ __device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, i
   for (int k = 0; k < RPW; ++k) {
     const int ry = warp * RPW + k;
     const int y = yc + ry;
-    if (y >= I.ny || !v0) break;
+    if (ry >= rows || y >= I.ny || !v0) break;
     const T* Rr = R + (ry + 1) * G::BW + G::H + c;
     const T vc0 = Rr[0], vc1 = Rr[1];
     const T vw = Rr[-1], ve = Rr[2];
@@ -1305,12 +1299,11 @@ __device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, i
 
 // The free bits of this lane's two points in each of its rows of a chunk,
 // loaded before the chunk's data arrive.
-template <class T>
+template <int RPW>
 __device__ __forceinline__ void load_chunk_bits(const DevInst& I, const unsigned* __restrict__ m,
                                                 int x0, int yc, unsigned fbits[4]) {
   // the loads are unconditional (rows past the grid read the last row and
   // are never used) so that nothing waits for them before the chunk's data
-  constexpr int RPW = ChunkGeo<T>::CH / kWarps;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e0 = min(x0 + 2 * lane, I.nx - 1) & ~1;
 #pragma unroll
@@ -1357,25 +1350,363 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
   }
 }
 
+// ------------------------------------ TMA-staged mixed-phase GP passes --
+//
+// In the mixed phase the census and the trial passes of a 2-D instance stream
+// 8-row chunks (one row per warp).  Stage layout (boxes 128-byte aligned):
+//   XH | LH | UH | DH | GH : FP32 72 x 10 from (x0-4, y-1): x32, l32, u32,
+//                            the direction (g32 or w32), g32 (trial along w)
+//   X | L | U : FP64 64 x 8 (x, l, u)    B : FP32 64 x 8 (b32)
+//   D : 64 x 8    CX : 68 x 8 from x0-4    CY : 64 x 9 from y-1
+// The census loads XH and the interior boxes only.  The alpha0 pass streams
+// 32-row chunks of pg32 through the R slot of the FP32 CG_B layout, with its
+// D, CX and CY boxes.
+struct GeoGP {
+  static constexpr int CH = 8, H = 4, BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * 4);
+  static constexpr int SZ_64 = 64 * CH * 8, SZ_32 = 64 * CH * 4;
+  static constexpr int OFF_XH = 0, OFF_LH = SZ_H, OFF_UH = 2 * SZ_H, OFF_DH = 3 * SZ_H;
+  static constexpr int OFF_GH = 4 * SZ_H;
+  static constexpr int OFF_X = 5 * SZ_H, OFF_L = OFF_X + SZ_64, OFF_U = OFF_L + SZ_64;
+  static constexpr int OFF_B = OFF_U + SZ_64, OFF_D = OFF_B + SZ_32;
+  static constexpr int OFF_CX = OFF_D + SZ_32;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr unsigned TX_H = (CH + 2) * BW * 4;  // one halo box
+  static constexpr unsigned TX_INT =
+      3 * SZ_64 + 2 * SZ_32 + (64 + H) * CH * 4 + 64 * (CH + 1) * 4;
+};
+static_assert(GeoGP::END <= kStageBytes, "stage layout");
+static_assert(GeoGP::CH == kWarps, "one row per warp");
+
+// Whether the item's pass is a mixed-phase GP pass on the TMA path.
+__device__ __forceinline__ bool gp_tma(const DevInst& I, const Snap& S) {
+  return S.gp32 && I.dim == 2 && I.tma_gp && I.tma32 &&
+         (S.pass == P_CENSUS || S.pass == P_GP_ALPHA || S.pass == P_TRIAL);
+}
+
+// Issue the chunk at rows yc.. of a mixed-phase GP pass.
+__device__ __forceinline__ void issue_gp(const DevInst& I, const Snap& S, int x0, int yc,
+                                         unsigned st, unsigned bar) {
+  using G = GeoGP;
+  const int cur = S.cur;
+  if (S.pass == P_GP_ALPHA) {
+    using F = ChunkGeo<float>;
+    mbar_expect(bar, ((F::CH + 2) * F::BW + 64 * F::CH + (64 + F::H) * F::CH +
+                      64 * (F::CH + 1)) * 4);
+    tma_load2d(st + F::OFF_R, tmap(I, MG_PGH0 + cur), x0 - F::H, yc - 1, bar);
+    tma_load2d(st + F::OFF_D, tmap(I, M32_D), x0, yc, bar);
+    tma_load2d(st + F::OFF_CX, tmap(I, M32_CX), x0 - F::H, yc, bar);
+    tma_load2d(st + F::OFF_CY, tmap(I, M32_CY), x0, yc - 1, bar);
+    return;
+  }
+  const bool trial = S.pass == P_TRIAL;
+  const bool along_w = trial && S.dir == D_W32;
+  const unsigned n_halo = trial ? (along_w ? 5u : 4u) : 1u;
+  mbar_expect(bar, n_halo * G::TX_H + G::TX_INT);
+  tma_load2d(st + G::OFF_XH, tmap(I, MG_X32H0 + cur), x0 - G::H, yc - 1, bar);
+  if (trial) {
+    tma_load2d(st + G::OFF_LH, tmap(I, MG_L32H), x0 - G::H, yc - 1, bar);
+    tma_load2d(st + G::OFF_UH, tmap(I, MG_U32H), x0 - G::H, yc - 1, bar);
+    tma_load2d(st + G::OFF_DH, tmap(I, along_w ? MG_W32H : MG_G32H0 + cur), x0 - G::H, yc - 1,
+               bar);
+    if (along_w) tma_load2d(st + G::OFF_GH, tmap(I, MG_G32H0 + cur), x0 - G::H, yc - 1, bar);
+  }
+  tma_load2d(st + G::OFF_X, tmap(I, MG_X0 + cur), x0, yc, bar);
+  tma_load2d(st + G::OFF_L, tmap(I, MG_L), x0, yc, bar);
+  tma_load2d(st + G::OFF_U, tmap(I, MG_U), x0, yc, bar);
+  tma_load2d(st + G::OFF_B, tmap(I, MG_B32), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, MG_D32), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, MG_CX32), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, MG_CY32), x0, yc - 1, bar);
+}
+
+// In the staged GP passes lane `lane` of warp w owns columns lane and lane+32
+// of row w of the chunk, so that shared-memory reads are unit-stride and a
+// warp ballot is one word of the free-set bitmask.
+
+// P_CENSUS (mixed) on one staged 8-row chunk: g32 = A32 x32 + b32, pg32, the
+// exact free set and |A|, |B|, ||pg||^2 (as OpCensus32).  Points past nx
+// arrive as zeros and contribute nothing.
+__device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                               int yc, float* g_out, float* pg_out,
+                                               unsigned* m_out, Acc& acc, FF& ff) {
+  using G = GeoGP;
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = yc + r;
+  if (y >= I.ny) return;  // warp-uniform
+  const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
+  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
+  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
+  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
+  const long long row = (long long)y * I.px + x0;
+  bool fr[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    const bool ok = x0 + j < I.nx;
+    const float* V = XH + (r + 1) * G::BW + G::H + j;
+    const float* cx = CX + r * (64 + G::H) + G::H + j;
+    // diag, west, east, south, north (the order of the register sweep)
+    float a = D[r * 64 + j] * V[0];
+    a = fmaf(cx[-1], V[-1], a);
+    a = fmaf(cx[0], V[1], a);
+    a = fmaf(CY[r * 64 + j], V[-G::BW], a);
+    a = fmaf(CY[(r + 1) * 64 + j], V[G::BW], a);
+    const float g = a + B[r * 64 + j];
+    const double xv = X[r * 64 + j];
+    const bool al = deq(xv, L[r * 64 + j]), au = deq(xv, U[r * 64 + j]);
+    const bool act = al || au;
+    fr[h] = ok && !act;
+    const float pg = pg_compf(al, au, g);
+    ff_fma(ff, pg, pg);
+    acc.c[0] += ok && act;
+    acc.c[1] += ok && ((al && g >= 0.0f) || (au && g <= 0.0f));
+    if (ok) {
+      g_out[row + j] = g;
+      pg_out[row + j] = pg;
+    }
+  }
+  const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+  const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+  const int wc = (x0 >> 5) + lane;
+  if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
+}
+
+// P_GP_ALPHA (mixed) on one staged chunk of up to 32 rows: <pg,pg>,
+// <pg, A32 pg> over its first `rows` rows.
+__device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned char* st, int yc,
+                                              int rows, FF* ff) {
+  using F = ChunkGeo<float>;
+  constexpr int RPW = F::CH / kWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* PH = reinterpret_cast<const float*>(st + F::OFF_R);
+  const float* D = reinterpret_cast<const float*>(st + F::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + F::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + F::OFF_CY);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = warp * RPW + k;
+    if (r >= rows || yc + r >= I.ny) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const float* V = PH + (r + 1) * F::BW + F::H + j;
+      const float* cx = CX + r * (64 + F::H) + F::H + j;
+      float a = D[r * 64 + j] * V[0];
+      a = fmaf(cx[-1], V[-1], a);
+      a = fmaf(cx[0], V[1], a);
+      a = fmaf(CY[r * 64 + j], V[-F::BW], a);
+      a = fmaf(CY[(r + 1) * 64 + j], V[F::BW], a);
+      ff_fma(ff[0], V[0], V[0]);
+      ff_fma(ff[1], V[0], a);
+    }
+  }
+}
+
+// The two words of the current free set covering row y, columns x0..x0+63,
+// reduced to this lane's bits (bit h: column lane + 32h), loaded ahead of the
+// chunk's data.
+__device__ __forceinline__ unsigned load_gp_bits(const DevInst& I, const unsigned* __restrict__ m,
+                                                 int x0, int yc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = min(yc + warp, I.ny - 1);
+  const int wc = x0 >> 5;
+  const unsigned* p = m + (long long)y * I.mw + wc;
+  const unsigned w0 = __ldg(p);
+  const unsigned w1 = wc + 1 < I.mw ? __ldg(p + 1) : 0u;
+  return ((w0 >> lane) & 1u) | (((w1 >> lane) & 1u) << 1);
+}
+
+// P_TRIAL (mixed) on one staged 8-row chunk (as OpTrial32).  Each warp forms
+// the FP32 operand P[x32 + alpha d] for its own row and the rows above and
+// below, takes the west and east neighbours by shuffles, then gives every
+// point its exact FP64 iterate and status, g32t, pg32 and the sums.  `fb_old`
+// holds the lane's two bits of the current free set (see load_gp_bits).
+template <int DK>
+__device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                              int yc, float alpha, double alpha_d,
+                                              unsigned fb_old, double* xt_out, float* xt32_out,
+                                              float* gt_out, float* pg_out, unsigned* m_out,
+                                              Acc& acc, FF* ff) {
+  using G = GeoGP;
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y = yc + r;
+  if (y >= I.ny) return;  // warp-uniform
+  const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
+  const float* LH = reinterpret_cast<const float*>(st + G::OFF_LH);
+  const float* UH = reinterpret_cast<const float*>(st + G::OFF_UH);
+  const float* DH = reinterpret_cast<const float*>(st + G::OFF_DH);
+  const float* GH = reinterpret_cast<const float*>(st + (DK == D_W32 ? G::OFF_GH : G::OFF_DH));
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
+  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
+  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
+  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
+  auto opnd = [&](int e) {
+    const float d = DK == D_NEG_G ? -DH[e] : DH[e];
+    return mid3f(LH[e], UH[e], fmaf(alpha, d, XH[e]));
+  };
+  const int b = (r + 1) * G::BW + G::H + lane;  // box index of column `lane` of this row
+  float vc[2], vs[2], vn[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    vc[h] = opnd(b + 32 * h);
+    vs[h] = opnd(b + 32 * h - G::BW);
+    vn[h] = opnd(b + 32 * h + G::BW);
+  }
+  float vw[2], ve[2];
+  vw[0] = __shfl_up_sync(FULL_MASK, vc[0], 1);
+  vw[1] = __shfl_up_sync(FULL_MASK, vc[1], 1);
+  ve[0] = __shfl_down_sync(FULL_MASK, vc[0], 1);
+  ve[1] = __shfl_down_sync(FULL_MASK, vc[1], 1);
+  const float col31 = __shfl_sync(FULL_MASK, vc[0], 31);
+  const float col32 = __shfl_sync(FULL_MASK, vc[1], 0);
+  if (lane == 0) {
+    vw[0] = opnd(b - 1);
+    vw[1] = col31;
+  }
+  if (lane == 31) {
+    ve[0] = col32;
+    ve[1] = opnd(b + 33);
+  }
+  const long long row = (long long)y * I.px + x0;
+  bool fr[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = lane + 32 * h;
+    const bool ok = x0 + j < I.nx;
+    const float* cx = CX + r * (64 + G::H) + G::H + j;
+    float a = D[r * 64 + j] * vc[h];
+    a = fmaf(cx[-1], vw[h], a);
+    a = fmaf(cx[0], ve[h], a);
+    a = fmaf(CY[r * 64 + j], vs[h], a);
+    a = fmaf(CY[(r + 1) * 64 + j], vn[h], a);
+    const float gt = a + B[r * 64 + j];
+    const float g = GH[b + 32 * h];
+    const float d = DK == D_NEG_G ? -g : DH[b + 32 * h];
+    const double xv = X[r * 64 + j], l = L[r * 64 + j], u = U[r * 64 + j];
+    const double xt = mid3(l, u, fma(alpha_d, (double)d, xv));
+    const bool al = deq(xt, l), au = deq(xt, u);
+    const bool act = al || au;
+    fr[h] = ok && !act;
+    const float pg = pg_compf(al, au, gt);
+    float sk = alpha * d;
+    if (act) sk = deq(xt, xv) ? 0.0f : (float)(xt - xv);
+    ff_fma(ff[0], g, sk);
+    ff_fma(ff[1], sk, gt);
+    ff_fma(ff[2], pg, pg);
+    acc.c[0] += ok && act;
+    acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
+    acc.c[2] += ok && (((fb_old >> h) & 1u) != (fr[h] ? 1u : 0u));
+    if (ok) {
+      xt_out[row + j] = xt;
+      xt32_out[row + j] = vc[h];
+      gt_out[row + j] = gt;
+      pg_out[row + j] = pg;
+    }
+  }
+  const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+  const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+  const int wc = (x0 >> 5) + lane;
+  if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
+}
+
 // Whether the item's pass runs through the TMA pipeline.
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
+  if (gp_tma(I, S)) return true;
+  if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
   const int ok = S.cg32 ? I.tma32 : I.tma64;
   if (!ok) return false;
   if (S.pass == P_CG_A) return true;
   return S.pass == P_CG_B && !S.first_cg && I.dim == 2;
 }
 
-// Issue chunk `c` of tile (x0, y0, z) of the item's pass into a stage.
-__device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, int x0, int y0, int z,
-                                            int c, unsigned st, unsigned bar) {
-  if (S.cg32) {
-    const int yc = y0 + c * ChunkGeo<float>::CH;
-    if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, x0, yc, st, bar);
-    else issue_cga<float>(I, S.pcur, x0, z * I.ny + yc, st, bar);
+// Rows per chunk of the item's TMA pass.
+__device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
+  if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
+  return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
+}
+
+// The free bits (rows per warp rpw) of the chunk at (x0, yc).
+__device__ __forceinline__ void load_bits(const DevInst& I, const unsigned* __restrict__ m, int rpw,
+                                          int x0, int yc, unsigned fbits[4]) {
+  if (rpw == 4) load_chunk_bits<4>(I, m, x0, yc, fbits);
+  else if (rpw == 2) load_chunk_bits<2>(I, m, x0, yc, fbits);
+  else load_chunk_bits<1>(I, m, x0, yc, fbits);
+}
+
+// A chunk of a TMA pass: rows yc .. yc+rows-1 (rows a multiple of 8, at most
+// the pass's chunk height) of the tile at column x0 of plane z.
+struct Chunk {
+  int x0, yc, z, rows;
+};
+
+// The chunk starting at 8-row strip u (tile u/4, strip u%4) of a group that
+// ends before strip u_hi.
+__device__ __forceinline__ Chunk make_chunk(const DevInst& I, int u, int u_hi, int ch) {
+  const int t = u >> 2, s = u & 3;
+  const int k = min(min(ch >> 3, 4 - s), max(u_hi - u, 1));
+  const int rest = t / I.tiles_x;
+  return Chunk{(t % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY + 8 * s, rest / I.tiles_y, 8 * k};
+}
+
+// Issue a chunk of the item's pass into a stage.
+__device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, bool gp,
+                                            const Chunk& c, unsigned st, unsigned bar) {
+  if (gp) {
+    issue_gp(I, S, c.x0, c.yc, st, bar);
+  } else if (S.cg32) {
+    if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cga<float>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
   } else {
-    const int yc = y0 + c * ChunkGeo<double>::CH;
-    if (S.pass == P_CG_B) issue_cgb<double>(I, S.pcur, x0, yc, st, bar);
-    else issue_cga<double>(I, S.pcur, x0, z * I.ny + yc, st, bar);
+    if (S.pass == P_CG_B) issue_cgb<double>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cga<double>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
+  }
+}
+
+// Compute a staged chunk of the item's pass.
+__device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool gp,
+                                          unsigned char* st, const Chunk& c,
+                                          const unsigned* fbits, Acc& acc, FF* ffs) {
+  const int cur = S.cur;
+  if (gp) {
+    if (S.pass == P_CENSUS) {
+      census32_chunk(I, st, c.x0, c.yc, I.g32[cur], I.pg32[cur], I.mask[cur], acc, ffs[0]);
+    } else if (S.pass == P_GP_ALPHA) {
+      alpha32_chunk(I, st, c.yc, c.rows, ffs);
+    } else {
+      const double al = S.dir == D_ZERO ? 0.0 : S.alpha;
+      if (S.dir == D_W32)
+        trial32_chunk<D_W32>(I, st, c.x0, c.yc, (float)al, al, fbits[0], I.x[cur ^ 1],
+                             I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1],
+                             acc, ffs);
+      else
+        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, (float)al, al, fbits[0], I.x[cur ^ 1],
+                               I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
+                               I.mask[cur ^ 1], acc, ffs);
+    }
+  } else if (S.pass == P_CG_B) {
+    if (S.cg32)
+      cgb_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.beta, fbits, I.p32[S.pcur ^ 1],
+                       I.Ap32, acc, ffs[0]);
+    else
+      cgb_chunk<double>(I, st, c.x0, c.yc, c.rows, S.beta, fbits, I.p64[S.pcur ^ 1], I.Ap64,
+                        acc, ffs[0]);
+  } else {
+    const int ylim = min(c.rows, I.ny - c.yc);
+    if (S.cg32)
+      cga_chunk<float>(I, st, c.x0, c.z * I.ny + c.yc, ylim, (float)S.alpha, I.w32, I.r32, acc,
+                       ffs[0]);
+    else
+      cga_chunk<double>(I, st, c.x0, c.z * I.ny + c.yc, ylim, S.alpha, I.w64, I.r64, acc,
+                        ffs[0]);
   }
 }
 
@@ -1402,7 +1733,7 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       break;
     case P_CENSUS: {
       if (S.gp32) {
-        OpCensus32 op{I, I.x[cur], I.x32[cur], I.g32[cur], I.mask[cur], ffs};
+        OpCensus32 op{I, I.x[cur], I.x32[cur], I.g32[cur], I.pg32[cur], I.mask[cur], ffs};
         stencil_tile(I, op, x0, y0, z, acc);
       } else {
         OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur]};
@@ -1412,7 +1743,7 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
     }
     case P_GP_ALPHA: {
       if (S.gp32) {
-        OpGpAlpha32 op{I, I.x32[cur], I.g32[cur], I.mask[cur], ffs};
+        OpGpAlpha32 op{I, I.pg32[cur], ffs};
         stencil_tile(I, op, x0, y0, z, acc);
       } else {
         OpGpAlpha op{I, I.x[cur], I.g[cur]};
@@ -1425,13 +1756,13 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       if (S.gp32) {
         if (S.dir == D_W32) {
           OpTrial32<D_W32> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
-                              I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.mask[cur ^ 1],
-                              I.mask[cur], ffs};
+                              I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
+                              I.mask[cur ^ 1], I.mask[cur], ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
           OpTrial32<D_NEG_G> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
-                                I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.mask[cur ^ 1],
-                                I.mask[cur], ffs};
+                                I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
+                                I.mask[cur ^ 1], I.mask[cur], ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         }
       } else if (S.dir == D_W64) {
@@ -1506,8 +1837,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // two TMA stages and their barriers, 128-byte aligned
-  unsigned char* stage0 =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dyn_smem) + 127) & ~uintptr_t(127));
+  // (offset from the array itself, so that the compiler keeps every stage
+  // access in the shared address space)
+  unsigned char* stage0 = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + 2 * kStageBytes);
 
   if (blockIdx.x == 0 && tid == 0) {
@@ -1554,6 +1886,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         s_inst = tr.x;
       }
       __syncthreads();
+      if (tid == 0 && !s_skip && sI.tmaps && sS.gp32 && sI.tma_gp && sI.tma32) {
+        for (int k = M32_RH; k < M32_RH + (M64_RH - M32_RH); ++k) tmap_acquire(tmap(sI, k));
+        for (int k = MG_X32H0; k < M_COUNT; ++k) tmap_acquire(tmap(sI, k));
+      }
       if (tid == 0 && !s_skip && sI.tmaps && (sS.pass == P_CG_A || sS.pass == P_CG_B)) {
         const bool f32 = sS.cg32 != 0;
         if (f32 ? sI.tma32 : sI.tma64) {
@@ -1566,67 +1902,73 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     const Snap& S = sS;
     if (S.pass == P_NONE) continue;
 
-    // the group's tiles
-    const int grp = tr.y;
-    const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
-    const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
     Acc acc;
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
     FF ffs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const int grp = tr.y;
     const bool tma = tma_pass(I, S);
-    unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
-    int pend_bits = 0;
-    for (int tile = t_lo; tile < t_hi; ++tile) {
-      const int tx = tile % I.tiles_x;
-      const int rest = tile / I.tiles_x;
-      const int x0 = tx * kTX;
-      const int y0 = (rest % I.tiles_y) * kTY;
-      const int z = rest / I.tiles_y;
-      if (!tma) {
-        run_tile(I, S, x0, y0, z, acc, ffs);
-        continue;
+    if (!tma) {
+      // register sweep: the group is a range of whole tiles
+      const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+      const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
+      for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int rest = tile / I.tiles_x;
+        run_tile(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY, rest / I.tiles_y, acc,
+                 ffs);
       }
-      // TMA pipeline: chunk k+1 (of this tile or the next tile of the group)
-      // is in flight while chunk k is computed
-      const int ch = S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
-      const int nch = kTY / ch;
-      const bool more = tile + 1 < t_hi;
-      int nx0 = 0, ny0 = 0, nz0 = 0;
-      if (more) {
-        const int rn = (tile + 1) / I.tiles_x;
-        nx0 = ((tile + 1) % I.tiles_x) * kTX;
-        ny0 = (rn % I.tiles_y) * kTY;
-        nz0 = rn / I.tiles_y;
-      }
-      for (int c = 0; c < nch; ++c) {
+    } else {
+      // TMA pipeline: the group is a range of 8-row strips (4 per tile), cut
+      // into chunks of up to `ch` rows that stay inside one tile; chunk k+1 is
+      // in flight while chunk k is computed
+      const bool gp = gp_tma(I, S);
+      const bool want_bits = S.pass == P_CG_B || (gp && S.pass == P_TRIAL);
+      const int ch = chunk_rows(S, gp);
+      const int rpw = ch / kWarps;
+      const long long n_strips = (long long)I.n_tiles * (kTY / 8);
+      const int u_hi = (int)((grp + 1) * n_strips / I.n_groups);
+      int u = (int)(grp * n_strips / I.n_groups);
+      Chunk cc = make_chunk(I, u, u_hi, ch);
+      unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
+      int pend_bits = 0;
+      while (u < u_hi) {
+        const int u_n = u + cc.rows / 8;
+        const bool nxt = u_n < u_hi;
+        const Chunk cn = make_chunk(I, u_n, u_hi, ch);
         const int sg = seq & 1;
         unsigned char* st = stage0 + sg * kStageBytes;
-        const bool nxt = (c + 1 < nch) || more;
         if (tid == 0) {
-          if (!pend) issue_chunk(I, S, x0, y0, z, c, smem_u32(st), smem_u32(&bars[sg]));
-          unsigned char* st2_ = stage0 + (sg ^ 1) * kStageBytes;
-          const unsigned b2 = smem_u32(&bars[sg ^ 1]);
-          if (c + 1 < nch) issue_chunk(I, S, x0, y0, z, c + 1, smem_u32(st2_), b2);
-          else if (more) issue_chunk(I, S, nx0, ny0, nz0, 0, smem_u32(st2_), b2);
+          if (!pend) issue_chunk(I, S, gp, cc, smem_u32(st), smem_u32(&bars[sg]));
+          if (nxt)
+            issue_chunk(I, S, gp, cn, smem_u32(stage0 + (sg ^ 1) * kStageBytes),
+                        smem_u32(&bars[sg ^ 1]));
         }
         // free bits of this chunk (prefetched with the previous chunk when
         // possible) and of the next one
-        if (S.pass == P_CG_B) {
-          if (!pend_bits) {
-            if (S.cg32) load_chunk_bits<float>(I, I.mask[S.cur], x0, y0 + c * ch, fbits);
-            else load_chunk_bits<double>(I, I.mask[S.cur], x0, y0 + c * ch, fbits);
-          }
-          const int bx = c + 1 < nch ? x0 : nx0;
-          const int by = c + 1 < nch ? y0 + (c + 1) * ch : ny0;
-          if (nxt) {
-            if (S.cg32) load_chunk_bits<float>(I, I.mask[S.cur], bx, by, fbits_n);
-            else load_chunk_bits<double>(I, I.mask[S.cur], bx, by, fbits_n);
+        if (want_bits) {
+          if (gp) {
+            if (!pend_bits) fbits[0] = load_gp_bits(I, I.mask[S.cur], cc.x0, cc.yc);
+            if (nxt) fbits_n[0] = load_gp_bits(I, I.mask[S.cur], cn.x0, cn.yc);
+          } else {
+            if (!pend_bits) load_bits(I, I.mask[S.cur], rpw, cc.x0, cc.yc, fbits);
+            if (nxt) load_bits(I, I.mask[S.cur], rpw, cn.x0, cn.yc, fbits_n);
           }
         }
         const bool ok = mbar_wait(smem_u32(&bars[sg]), (seq >> 1) & 1);
-        if (__syncthreads_or(!ok)) {
+        bool failed;
+        if (S.pass == P_CG_B && !gp) {
+          // the CG_B chunk has a barrier inside: agree on the wait first
+          failed = __syncthreads_or(!ok);
+          if (!failed) run_chunk(I, S, gp, st, cc, fbits, acc, ffs);
+          __syncthreads();  // the stage may be refilled
+        } else {
+          // one barrier per chunk: every thread is done with the stage (which
+          // may then be refilled) and no bounded wait gave up
+          if (ok) run_chunk(I, S, gp, st, cc, fbits, acc, ffs);
+          failed = __syncthreads_or(!ok);
+        }
+        if (failed) {
           // a copy never completed: record it, give the other stage's copy (if
           // one was issued) a bounded chance to land, and leave; the engine's
           // loop then ends on its pass cap and the host reports the error
@@ -1636,28 +1978,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           }
           return;
         }
-        if (S.pass == P_CG_B) {
-          if (S.cg32)
-            cgb_chunk<float>(I, st, x0, y0 + c * ch, (float)S.beta, fbits, I.p32[S.pcur ^ 1],
-                             I.Ap32, acc, ffs[0]);
-          else
-            cgb_chunk<double>(I, st, x0, y0 + c * ch, S.beta, fbits, I.p64[S.pcur ^ 1], I.Ap64,
-                              acc, ffs[0]);
-        } else {
-          const int ylim = min(ch, I.ny - (y0 + c * ch));
-          if (S.cg32)
-            cga_chunk<float>(I, st, x0, z * I.ny + y0 + c * ch, ylim, (float)S.alpha, I.w32,
-                             I.r32, acc, ffs[0]);
-          else
-            cga_chunk<double>(I, st, x0, z * I.ny + y0 + c * ch, ylim, S.alpha, I.w64, I.r64,
-                              acc, ffs[0]);
-        }
-        __syncthreads();  // the stage may be refilled
         seq++;
         pend = nxt;
         pend_bits = nxt;
 #pragma unroll
         for (int k = 0; k < 4; ++k) fbits[k] = fbits_n[k];
+        u = u_n;
+        cc = cn;
       }
     }
     // fixed-order group reduction: every thread's sums go to shared memory;

@@ -170,6 +170,24 @@ def test_engine_modes_agree(monkeypatch):
     assert res[0][1]["passes"] == res[1][1]["passes"]
 
 
+@pytest.mark.parametrize("shape,bounds", [((65, 33), "two_sided"), ((100, 70), "box1"),
+                                          ((129, 5), "lower0"), ((200, 131), "two_sided")])
+def test_mixed_staged_and_register_paths(monkeypatch, shape, bounds):
+    """The mixed-phase GP passes of a 2-D instance run TMA-staged by default
+    and through the register sweep with GPCG_NO_TMA=1 (read when a problem is
+    created); both paths meet the mixed tolerance against the oracle."""
+    qp = gi.grid_qp_2d(*shape, seed=640 + shape[0], shift=0.02, bounds=bounds)
+    ref = oracle.solve(qp, tau_rel=1e-10)
+    for off in ("1", "0"):
+        monkeypatch.setenv("GPCG_NO_TMA", off)
+        status, x, st = _solve(qp, tau_rel=1e-10, precision=g.MIXED)
+        assert status == 0
+        assert _rel_err(x, ref.x) <= 1e-5
+        assert _active_sets_agree(qp, x, ref.x)
+        c = oracle.census(qp, x)
+        assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
+
+
 def test_x0_and_device_arrays():
     import torch
     qp = gi.grid_qp_2d(48, 40, seed=620, shift=0.02, bounds="box1")
