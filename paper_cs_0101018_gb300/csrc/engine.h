@@ -35,15 +35,18 @@ constexpr int kMinBlocks = 2;    // resident CTAs per SM the pass kernel is comp
 constexpr int kGroupTiles = 4;
 constexpr int kMaxGroups = 304;
 
-// TMA staging of the CG passes: a work item (64x32 tile) is streamed through
-// shared memory in chunks of 64 x kChunk rows, two stages deep.
-constexpr int kStageBytes = 45056;   // one stage (see the stage layout in the kernels)
-constexpr int kDynSmem = 2 * kStageBytes + 256;
+// TMA staging: a work item is streamed through shared memory in chunks of
+// 64 columns by 8-32 rows, kStages stages deep (the next chunk is in flight
+// while one is computed).  Two CTAs of the pass kernel fit on one SM.
+constexpr int kStages = 2;
+constexpr int kStageBytes = 45056;   // one stage (the largest stage layout in the kernels)
+constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 
-// Tensor maps of an instance (one CUtensorMap, 128 bytes, each).  H = halo
-// box (64+2h) x (chunk+2) starting at (x0-h, y0-1); D = 64 x chunk;
-// CX = (64+h) x chunk from x0-h; CY = 64 x (chunk+1) from y0-1; the rest are
-// 64 x chunk boxes over the (nx, ny*nz) row space.
+// Tensor maps of an instance (one CUtensorMap, 128 bytes, each).  With c the
+// CG_B chunk (32 rows FP32, 16 FP64) and a the CG_A chunk (32 / 16 rows):
+// H = halo box (64+2h) x (c+2) starting at (x0-h, y0-1); D = 64 x c;
+// CX = (64+h) x c from x0-h; CY = 64 x (c+1) from y0-1; W, R, P, AP are
+// 64 x a boxes over the (nx, ny*nz) row space.
 //
 // The mixed-phase gradient-projection passes of a 2-D instance stage 8-row
 // chunks (census, trial) and 32-row chunks (alpha0): G8 = FP32 halo box

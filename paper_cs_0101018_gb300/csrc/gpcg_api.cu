@@ -286,7 +286,7 @@ static bool encode_map(CUtensorMap* m, bool f32, const void* base, const gpcg_pr
 static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   if (!have_encode()) return false;
   DevInst& I = p->inst;
-  const int h = f32 ? 4 : 2, ch = f32 ? 32 : 16;
+  const int h = f32 ? 4 : 2, ch = f32 ? 32 : 16, cha = f32 ? 32 : 16;
   const int b0 = f32 ? M32_RH : M64_RH;
   CUtensorMap m[11];
   const void* r = f32 ? (const void*)I.r32 : (const void*)I.r64;
@@ -301,9 +301,9 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
             encode_map(&m[1], f32, p0, p, 64 + 2 * h, ch + 2) &&
             encode_map(&m[2], f32, p1, p, 64 + 2 * h, ch + 2) &&
             encode_map(&m[3], f32, d, p, 64, ch) && encode_map(&m[4], f32, cx, p, 64 + h, ch) &&
-            encode_map(&m[5], f32, cy, p, 64, ch + 1) && encode_map(&m[6], f32, w, p, 64, ch) &&
-            encode_map(&m[7], f32, r, p, 64, ch) && encode_map(&m[8], f32, p0, p, 64, ch) &&
-            encode_map(&m[9], f32, p1, p, 64, ch) && encode_map(&m[10], f32, ap, p, 64, ch);
+            encode_map(&m[5], f32, cy, p, 64, ch + 1) && encode_map(&m[6], f32, w, p, 64, cha) &&
+            encode_map(&m[7], f32, r, p, 64, cha) && encode_map(&m[8], f32, p0, p, 64, cha) &&
+            encode_map(&m[9], f32, p1, p, 64, cha) && encode_map(&m[10], f32, ap, p, 64, cha);
   if (!ok) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -1177,12 +1177,12 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
 //
 // The two CG passes of a 2-D instance (and the pointwise CG pass of any
 // instance) stream a work item through shared memory with the tensor memory
-// accelerator: chunk k+1 is in flight while chunk k is computed.  Stage
-// layout (each array 128-byte aligned), T = float (32-row chunks, h = 4) or
-// double (16-row chunks, h = 2) -- both come to the same byte sizes:
-//   P_CG_B: R (64+2h)x(c+2) from (x0-h, y-1) | P likewise | D 64xc |
-//           CX (64+h)xc from x0-h | CY 64x(c+1) from y-1
-//   P_CG_A: W | R | P | AP, 64xc each
+// accelerator, kStages stages deep: the next kStages-1 chunks are in flight
+// while chunk k is computed.  Stage layout (each array 128-byte aligned),
+// T = float (h = 4) or double (h = 2):
+//   P_CG_B (c = 32 rows FP32, 16 FP64): R (64+2h)x(c+2) from (x0-h, y-1) |
+//           P likewise | D 64xc | CX (64+h)xc from x0-h | CY 64x(c+1) from y-1
+//   P_CG_A (a = 32 rows FP32, 16 FP64): W | R | P | AP, 64xa each
 // Out-of-range rows and columns arrive as zeros, which is exactly the
 // operand and coupling outside the grid.
 
@@ -1191,7 +1191,8 @@ __host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128
 template <class T>
 struct ChunkGeo {
   static constexpr int H = 16 / (int)sizeof(T);
-  static constexpr int CH = sizeof(T) == 4 ? 32 : 16;
+  static constexpr int CH = sizeof(T) == 4 ? 32 : 16;     // CG_B rows per chunk
+  static constexpr int CH_A = sizeof(T) == 4 ? 32 : 16;  // CG_A rows per chunk
   static constexpr int BW = 64 + 2 * H;
   static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
   static constexpr int OFF_R = 0;
@@ -1202,13 +1203,15 @@ struct ChunkGeo {
   static constexpr int END_B = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
   static constexpr unsigned TX_B =
       (2 * (CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
-  static constexpr int SZ_A = 64 * CH * (int)sizeof(T);
+  static constexpr int SZ_A = 64 * CH_A * (int)sizeof(T);
   static constexpr unsigned TX_A = 4 * SZ_A;
   static constexpr int MB = sizeof(T) == 4 ? M32_RH : M64_RH;  // first map of the precision
 };
 static_assert(ChunkGeo<float>::END_B <= kStageBytes && ChunkGeo<double>::END_B <= kStageBytes,
               "stage layout");
-static_assert(4 * ChunkGeo<float>::SZ_A <= kStageBytes, "stage layout");
+static_assert(4 * ChunkGeo<float>::SZ_A <= kStageBytes &&
+                  4 * ChunkGeo<double>::SZ_A <= kStageBytes,
+              "stage layout");
 
 __device__ __forceinline__ const void* tmap(const DevInst& I, int k) {
   return reinterpret_cast<const char*>(I.tmaps) + 128 * k;
@@ -1326,7 +1329,7 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
   const T* P = reinterpret_cast<const T*>(st + 2 * G::SZ_A);
   const T* AP = reinterpret_cast<const T*>(st + 3 * G::SZ_A);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int RPW = G::CH / kWarps;
+  constexpr int RPW = G::CH_A / kWarps;
   const int c = 2 * lane;
   const int e0 = x0 + c;
   const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
@@ -1631,6 +1634,7 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
 // Rows per chunk of the item's TMA pass.
 __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
+  if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
 }
 
@@ -1828,19 +1832,25 @@ template <bool kCond>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
   __shared__ DevInst sI;
   __shared__ Snap sS;
-  __shared__ double s_sum[4][kThreads];
-  __shared__ float s_ffh[3][kThreads], s_ffl[3][kThreads];
+  __shared__ Ctl sC;
   __shared__ int s_cnt[3][kWarps];
   __shared__ double s_red[kNRed];
   __shared__ int s_t, s_inst, s_last, s_skip;
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
+  static_assert(sizeof(Ctl) % 8 == 0 && sizeof(Ctl) / 8 <= kThreads, "control block copy");
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // two TMA stages and their barriers, 128-byte aligned
-  // (offset from the array itself, so that the compiler keeps every stage
-  // access in the shared address space)
+  // kStages TMA stages and their barriers, 128-byte aligned (offset from the
+  // array itself, so that the compiler keeps every stage access in the
+  // shared address space)
   unsigned char* stage0 = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + 2 * kStageBytes);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + kStages * kStageBytes);
+  // the group reduction's scratch lives in the first stage (no copy is in
+  // flight between groups)
+  double(*s_sum)[kThreads] = reinterpret_cast<double(*)[kThreads]>(stage0);
+  float(*s_ffh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + 4 * 8 * kThreads);
+  float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 12) * kThreads);
+  static_assert((32 + 24) * kThreads <= kStageBytes, "reduction scratch");
 
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned np = atomicAdd(E.npass, 1u) + 1u;
@@ -1850,16 +1860,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   }
   if (tid == 0) {
     s_inst = -1;
-    mbar_init(smem_u32(&bars[0]));
-    mbar_init(smem_u32(&bars[1]));
+    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  int seq = 0;   // next chunk of the TMA pipeline to consume (same in all threads)
-  int pend = 0;  // chunk `seq` has already been issued
+  int seq = 0;  // chunks of the TMA pipeline consumed so far (same in all threads)
 
-  for (;;) {
+  for (int first = 1;; first = 0) {
     __syncthreads();  // the previous item's shared state is no longer read
-    if (tid == 0) s_t = atomicAdd(E.queue, 1);
+    // the first item of a CTA is its own index; later ones are claimed
+    if (tid == 0) s_t = first ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(E.queue, 1);
     __syncthreads();
     const int t = s_t;
     if (t >= E.n_work) break;
@@ -1920,71 +1929,87 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       }
     } else {
       // TMA pipeline: the group is a range of 8-row strips (4 per tile), cut
-      // into chunks of up to `ch` rows that stay inside one tile; chunk k+1 is
-      // in flight while chunk k is computed
+      // into chunks of up to `ch` rows that stay inside one tile; the next
+      // kStages-1 chunks are in flight while chunk k is computed (the stage
+      // refilled at the top of an iteration is the one computed in the
+      // previous iteration).  Nothing is in flight between groups.
+      constexpr int kDepth = kStages - 1;
+      static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
       const bool gp = gp_tma(I, S);
       const bool want_bits = S.pass == P_CG_B || (gp && S.pass == P_TRIAL);
       const int ch = chunk_rows(S, gp);
       const int rpw = ch / kWarps;
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
       const int u_hi = (int)((grp + 1) * n_strips / I.n_groups);
-      int u = (int)(grp * n_strips / I.n_groups);
-      Chunk cc = make_chunk(I, u, u_hi, ch);
+      const int u0 = (int)(grp * n_strips / I.n_groups);
+      // the current chunk and the next two (h1, h2: they exist)
+      Chunk c0 = make_chunk(I, u0, u_hi, ch);
+      int u1 = u0 + c0.rows / 8;
+      bool h1 = u1 < u_hi;
+      Chunk c1 = make_chunk(I, u1, u_hi, ch);
+      int u2 = u1 + c1.rows / 8;
+      bool h2 = h1 && u2 < u_hi;
+      Chunk c2 = make_chunk(I, u2, u_hi, ch);
+      auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
+      auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
+      if (tid == 0) {
+        // order earlier generic writes to the stages before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_chunk(I, S, gp, c0, smem_u32(stage(seq)), bar(seq));
+        if (kDepth == 2 && h1) issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1));
+      }
       unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
-      int pend_bits = 0;
-      while (u < u_hi) {
-        const int u_n = u + cc.rows / 8;
-        const bool nxt = u_n < u_hi;
-        const Chunk cn = make_chunk(I, u_n, u_hi, ch);
-        const int sg = seq & 1;
-        unsigned char* st = stage0 + sg * kStageBytes;
-        if (tid == 0) {
-          if (!pend) issue_chunk(I, S, gp, cc, smem_u32(st), smem_u32(&bars[sg]));
-          if (nxt)
-            issue_chunk(I, S, gp, cn, smem_u32(stage0 + (sg ^ 1) * kStageBytes),
-                        smem_u32(&bars[sg ^ 1]));
+      if (want_bits) {
+        if (gp) fbits[0] = load_gp_bits(I, I.mask[S.cur], c0.x0, c0.yc);
+        else load_bits(I, I.mask[S.cur], rpw, c0.x0, c0.yc, fbits);
+      }
+      for (;;) {
+        if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
+          if (S.pass == P_CG_B && !gp) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (kDepth == 2) issue_chunk(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2));
+          else issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1));
         }
-        // free bits of this chunk (prefetched with the previous chunk when
-        // possible) and of the next one
-        if (want_bits) {
-          if (gp) {
-            if (!pend_bits) fbits[0] = load_gp_bits(I, I.mask[S.cur], cc.x0, cc.yc);
-            if (nxt) fbits_n[0] = load_gp_bits(I, I.mask[S.cur], cn.x0, cn.yc);
-          } else {
-            if (!pend_bits) load_bits(I, I.mask[S.cur], rpw, cc.x0, cc.yc, fbits);
-            if (nxt) load_bits(I, I.mask[S.cur], rpw, cn.x0, cn.yc, fbits_n);
-          }
+        // the next chunk's free bits, loaded while this chunk's data arrive
+        if (want_bits && h1) {
+          if (gp) fbits_n[0] = load_gp_bits(I, I.mask[S.cur], c1.x0, c1.yc);
+          else load_bits(I, I.mask[S.cur], rpw, c1.x0, c1.yc, fbits_n);
         }
-        const bool ok = mbar_wait(smem_u32(&bars[sg]), (seq >> 1) & 1);
+        unsigned char* st = stage(seq);
+        const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
         bool failed;
         if (S.pass == P_CG_B && !gp) {
           // the CG_B chunk has a barrier inside: agree on the wait first
           failed = __syncthreads_or(!ok);
-          if (!failed) run_chunk(I, S, gp, st, cc, fbits, acc, ffs);
+          if (!failed) run_chunk(I, S, gp, st, c0, fbits, acc, ffs);
           __syncthreads();  // the stage may be refilled
         } else {
           // one barrier per chunk: every thread is done with the stage (which
           // may then be refilled) and no bounded wait gave up
-          if (ok) run_chunk(I, S, gp, st, cc, fbits, acc, ffs);
+          if (ok) run_chunk(I, S, gp, st, c0, fbits, acc, ffs);
           failed = __syncthreads_or(!ok);
         }
         if (failed) {
-          // a copy never completed: record it, give the other stage's copy (if
-          // one was issued) a bounded chance to land, and leave; the engine's
-          // loop then ends on its pass cap and the host reports the error
+          // a copy never completed: record it, give the copies still in
+          // flight a bounded chance to land, and leave; the engine's loop
+          // then ends on its pass cap and the host reports the error
           if (tid == 0) {
             atomicOr(E.err, 1);
-            if (nxt) mbar_wait(smem_u32(&bars[sg ^ 1]), ((seq + 1) >> 1) & 1);
+            if (h1) mbar_wait(bar(seq + 1), ((seq + 1) / kStages) & 1);
+            if (kDepth == 2 && h2) mbar_wait(bar(seq + 2), ((seq + 2) / kStages) & 1);
           }
           return;
         }
         seq++;
-        pend = nxt;
-        pend_bits = nxt;
+        if (!h1) break;
 #pragma unroll
         for (int k = 0; k < 4; ++k) fbits[k] = fbits_n[k];
-        u = u_n;
-        cc = cn;
+        c0 = c1;
+        c1 = c2;
+        u1 = u2;
+        h1 = h2;
+        u2 = u1 + c1.rows / 8;
+        h2 = h1 && u2 < u_hi;
+        c2 = make_chunk(I, u2, u_hi, ch);
       }
     }
     // fixed-order group reduction: every thread's sums go to shared memory;
@@ -2076,12 +2101,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       s_red[tid] = v;
     }
     __syncthreads();
+    // the state machine runs on a shared copy of the control block (one
+    // round trip in, one out, instead of dependent global accesses)
+    long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
+    long long* cs = reinterpret_cast<long long*>(&sC);
+    if (tid < (int)(sizeof(Ctl) / 8)) cs[tid] = __ldcg(cg + tid);
+    __syncthreads();
     if (tid == 0) {
       s_red[kNRed - 1] = 0.0;
-      Ctl& C = E.ctl[tr.x];
-      C.arrive = 0u;
-      finalize(I, C, s_red, E.live);
+      sC.arrive = 0u;
+      finalize(I, sC, s_red, E.live);
     }
+    __syncthreads();
+    if (tid < (int)(sizeof(Ctl) / 8)) __stcg(cg + tid, cs[tid]);
   }
 
   // the last CTA to leave resets the queue for the next launch
