@@ -71,6 +71,12 @@ static int env_engine_mode() {
   return (s && *s) ? atoi(s) : 0;
 }
 
+static bool env_no_pdl() {
+  // GPCG_NO_PDL=1: plain edges between the passes of a graph
+  const char* s = getenv("GPCG_NO_PDL");
+  return s && *s && *s != '0';
+}
+
 // ------------------------------------------------------------ problem --
 
 struct Scratch {
@@ -88,6 +94,8 @@ struct Scratch {
   long long g_tiles = -1;
   int g_mode = -1;
   int g_steps = 0;
+  bool g_pdl = false;      // the cached graph joins its passes by programmatic edges
+  bool g_no_pdl = false;   // GPCG_NO_PDL when it was built
   ~Scratch() { release(); }
   void release() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -540,7 +548,8 @@ static Ctl fresh_ctl() {
 static constexpr int kBody = 4;
 
 static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap) {
-  if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps))
+  if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps) &&
+      sc.g_no_pdl == env_no_pdl())
     return GPCG_OK;
   sc.invalidate();
   EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
@@ -582,10 +591,37 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   k.blockDim = dim3(kThreads);
   k.sharedMemBytes = kDynSmem;
   k.kernelParams = kp;
+  // consecutive passes are joined by programmatic edges: the next pass's CTAs
+  // start (and load their static descriptors) while the previous pass's
+  // finalizer runs, and wait for its results in the kernel.  Plain edges are
+  // used where the driver does not accept them.
+  bool pdl = !env_no_pdl();
   cudaGraphNode_t prev = nullptr;
   for (int i = 0; i < count; ++i) {
     cudaGraphNode_t node;
-    cudaError_t e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &k);
+    cudaError_t e = cudaErrorUnknown;
+    if (prev && pdl) {
+      alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+      memset(np_buf, 0, sizeof(np_buf));
+      cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+      np.type = cudaGraphNodeTypeKernel;
+      np.kernel.func = k.func;
+      np.kernel.gridDim = k.gridDim;
+      np.kernel.blockDim = k.blockDim;
+      np.kernel.sharedMemBytes = k.sharedMemBytes;
+      np.kernel.kernelParams = k.kernelParams;
+      cudaGraphEdgeData ed;
+      memset(&ed, 0, sizeof(ed));
+      ed.from_port = cudaGraphKernelNodePortProgrammatic;
+      ed.type = cudaGraphDependencyTypeProgrammatic;
+      e = cudaGraphAddNode(&node, body, &prev, &ed, 1, &np);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        pdl = false;
+      }
+    }
+    if (e != cudaSuccess)
+      e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &k);
     if (e != cudaSuccess) {
       st = fail(GPCG_ERR_CUDA, "cudaGraphAddKernelNode: %s", cudaGetErrorString(e));
       break;
@@ -596,6 +632,8 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
     cudaError_t e = cudaGraphInstantiate(&sc.gexec, g, 0);
     if (e != cudaSuccess) st = fail(GPCG_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
   }
+  sc.g_pdl = pdl;
+  sc.g_no_pdl = env_no_pdl();
   cudaGraphDestroy(g);
   if (st != GPCG_OK) {
     sc.gexec = nullptr;

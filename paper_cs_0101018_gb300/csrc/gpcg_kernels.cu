@@ -1852,16 +1852,32 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 12) * kThreads);
   static_assert((32 + 24) * kThreads <= kStageBytes, "reduction scratch");
 
+  if (tid == 0) {
+    s_inst = -1;
+    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Static prologue, which may overlap the end of the previous pass (launched
+  // as a programmatic dependent): the descriptor and tensor maps of the
+  // first work item's instance.  Nothing the previous pass writes is read
+  // before griddepcontrol.wait.
+  if (blockIdx.x < (unsigned)E.n_work) {
+    const int inst = __ldg(E.tiles + blockIdx.x).x;
+    if (tid < (int)(sizeof(DevInst) / 8))
+      reinterpret_cast<long long*>(&sI)[tid] =
+          __ldg(reinterpret_cast<const long long*>(E.insts + inst) + tid);
+    __syncthreads();
+    if (tid == 0) s_inst = inst;
+    if (sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next pass may start its own prologue as soon as SMs free up
+  asm volatile("griddepcontrol.launch_dependents;" :::);
   if (blockIdx.x == 0 && tid == 0) {
     const unsigned np = atomicAdd(E.npass, 1u) + 1u;
     if (kCond && E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
       cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
     }
-  }
-  if (tid == 0) {
-    s_inst = -1;
-    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   int seq = 0;  // chunks of the TMA pipeline consumed so far (same in all threads)
 
@@ -1873,12 +1889,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     const int t = s_t;
     if (t >= E.n_work) break;
     const int2 tr = __ldg(E.tiles + t);
-    if (tr.x != s_inst) {
+    if (tr.x != s_inst || first) {
+      // a new instance (or the first item, whose descriptor the prologue
+      // loaded): read the snapshot of its state
+      const bool fresh = tr.x != s_inst;
       __syncthreads();  // everyone compared against the old s_inst
       if (tid == 0) s_skip = E.ctl[tr.x].pass == P_NONE;
       __syncthreads();
       // a finished instance's groups are skipped without loading its descriptor
-      if (!s_skip && tid < (int)(sizeof(DevInst) / 8))
+      if (fresh && !s_skip && tid < (int)(sizeof(DevInst) / 8))
         reinterpret_cast<long long*>(&sI)[tid] =
             __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
       if (tid == 0) {
@@ -1895,17 +1914,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         s_inst = tr.x;
       }
       __syncthreads();
-      if (tid == 0 && !s_skip && sI.tmaps && sS.gp32 && sI.tma_gp && sI.tma32) {
-        for (int k = M32_RH; k < M32_RH + (M64_RH - M32_RH); ++k) tmap_acquire(tmap(sI, k));
-        for (int k = MG_X32H0; k < M_COUNT; ++k) tmap_acquire(tmap(sI, k));
-      }
-      if (tid == 0 && !s_skip && sI.tmaps && (sS.pass == P_CG_A || sS.pass == P_CG_B)) {
-        const bool f32 = sS.cg32 != 0;
-        if (f32 ? sI.tma32 : sI.tma64) {
-          const int lo = f32 ? M32_RH : M64_RH;
-          for (int k = lo; k < lo + (M64_RH - M32_RH); ++k) tmap_acquire(tmap(sI, k));
-        }
-      }
+      if (fresh && !s_skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
     }
     const DevInst& I = sI;
     const Snap& S = sS;

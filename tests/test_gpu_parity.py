@@ -158,16 +158,22 @@ def test_batch_is_bitwise_identical_to_alone():
             assert sa["cg_iters"] == sb["cg_iters"] and sa["passes"] == sb["passes"]
 
 
-def test_engine_modes_agree(monkeypatch):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_engine_modes_agree(monkeypatch, prec):
+    """The WHILE-graph and host-loop engines, with and without programmatic
+    edges between passes, schedule the same passes: identical results."""
     qp = gi.grid_qp_2d(90, 70, seed=610, shift=0.01, bounds="two_sided")
     res = []
     for mode in ("0", "1"):
-        monkeypatch.setenv("GPCG_ENGINE_MODE", mode)
-        status, x, st = _solve(qp, tau_rel=1e-9)
-        assert status == 0
-        res.append((x, st))
-    assert np.array_equal(res[0][0], res[1][0])
-    assert res[0][1]["passes"] == res[1][1]["passes"]
+        for no_pdl in ("0", "1"):
+            monkeypatch.setenv("GPCG_ENGINE_MODE", mode)
+            monkeypatch.setenv("GPCG_NO_PDL", no_pdl)
+            status, x, st = _solve(qp, tau_rel=1e-9, precision=prec)
+            assert status == 0
+            res.append((x, st))
+    for x, st in res[1:]:
+        assert np.array_equal(res[0][0], x)
+        assert res[0][1]["passes"] == st["passes"]
 
 
 @pytest.mark.parametrize("shape,bounds", [((65, 33), "two_sided"), ((100, 70), "box1"),
