@@ -52,9 +52,18 @@ constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 // chunks (census, trial) and 32-row chunks (alpha0): G8 = FP32 halo box
 // 72 x 10 from (x0-4, y0-1); G34 = FP32 halo box 72 x 34; the FP64 and FP32
 // interior boxes are 64 x 8; GCX = 68 x 8 from x0-4; GCY = 64 x 9 from y0-1.
+//
+// The fused CG pass (2-D) stages f-row chunks (16 FP32, 8 FP64): FRH, FPH,
+// FAPH = halo boxes (64+2h) x (f+2) of r, p, Ap; FW, FD = 64 x f; FCX =
+// (64+h) x f; FCY = 64 x (f+1).  r, p and Ap are double-buffered (index
+// pcur: the current vectors), so each map of them comes in two.
 enum TMap : int {
-  M32_RH = 0, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R, M32_P0, M32_P1, M32_AP,
-  M64_RH, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R, M64_P0, M64_P1, M64_AP,
+  M32_RH0 = 0, M32_RH1, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R0, M32_R1, M32_P0,
+  M32_P1, M32_AP0, M32_AP1, M32_FRH0, M32_FRH1, M32_FPH0, M32_FPH1, M32_FAPH0, M32_FAPH1, M32_FW,
+  M32_FD, M32_FCX, M32_FCY,
+  M64_RH0, M64_RH1, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R0, M64_R1, M64_P0,
+  M64_P1, M64_AP0, M64_AP1, M64_FRH0, M64_FRH1, M64_FPH0, M64_FPH1, M64_FAPH0, M64_FAPH1, M64_FW,
+  M64_FD, M64_FCX, M64_FCY,
   MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G8
   MG_PGH0, MG_PGH1,                                                  // G34
   MG_X0, MG_X1, MG_L, MG_U,                                          // FP64 64 x 8
@@ -62,6 +71,7 @@ enum TMap : int {
   M_COUNT
 };
 constexpr int kGpMaps = M_COUNT - MG_X32H0;
+constexpr int kCgMaps = M64_RH0 - M32_RH0;  // maps of one precision's CG passes
 
 enum Pass : int {
   P_NONE = 0,
@@ -71,6 +81,8 @@ enum Pass : int {
   P_TRIAL = 4,     // trial point P[x + alpha*dir] with gradient and census
   P_CG_B = 5,      // p = -r + beta p; Ap = A_FF p; <p, Ap>
   P_CG_A = 6,      // w += alpha p; r += alpha Ap; ||r||^2
+  P_CG_F = 7,      // fused CG step (2-D, staged): r += alpha Ap, w += alpha p,
+                   // p = -r + beta p, Ap = A_FF p; ||r||^2, <p,Ap>, <r,Ap>, ||Ap||^2
 };
 
 enum Dir : int { D_NEG_G = 0, D_W64 = 1, D_W32 = 2, D_ZERO = 3 };
@@ -109,7 +121,8 @@ struct Ctl {
   int gp32;          // mixed phase: census / GP / search passes stream FP32 (see kernels)
   unsigned arrive;
   int census_mode;   // CM_* : what the next P_CENSUS is for
-  int stall, pad3;   // mixed phase: outer iterates without progress of ||pg||
+  int stall;         // mixed phase: outer iterates without progress of ||pg||
+  int cg_finish;     // the pending P_CG_A only completes w before the search
   double best_pg2;   // mixed phase: smallest ||pg||^2 seen
   double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
   double pg2, nA, nB, xgb, gF2;  // census of the current iterate
@@ -129,8 +142,8 @@ struct DevInst {
   const float *diag32, *cx32, *cy32, *cz32;
   double *x[2], *g[2];
   unsigned* mask[2];
-  double *r64, *w64, *p64[2], *Ap64;
-  float *r32, *w32, *p32[2], *Ap32;
+  double *r64[2], *w64, *p64[2], *Ap64[2];  // r, p, Ap double-buffered (index pcur)
+  float *r32[2], *w32, *p32[2], *Ap32[2];
   float *x32[2], *g32[2], *b32, *l32, *u32;  // FP32 copies streamed in the mixed phase
   float* pg32[2];          // mixed phase: grad_Omega q at x[k] (FP32), read by alpha0
   Opts opt;

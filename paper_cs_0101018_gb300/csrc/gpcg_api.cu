@@ -192,21 +192,21 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
   p->n_groups = std::min((p->n_tiles + kGroupTiles - 1) / kGroupTiles, kMaxGroups);
 }
 
-// Bytes of the FP64 arena: kc bands, b, l, u, x[2], g[2], r, w, p[2], Ap,
-// two masks and the tile partials.
+// Bytes of the FP64 arena: kc bands, b, l, u, x[2], g[2], r[2], w, p[2],
+// Ap[2], two masks and the tile partials.
 static size_t arena64_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(double) * (size_t)p->pn);
   const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
   const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_groups);
   const size_t maps = align256(sizeof(CUtensorMap) * M_COUNT);
-  return (size_t)(p->kc + 12) * vec + 2 * msk + part + maps;
+  return (size_t)(p->kc + 14) * vec + 2 * msk + part + maps;
 }
 
-// FP32 bands, the FP32 CG vectors r, w, p[2], Ap, and the FP32 arrays of the
-// mixed phase x[2], g[2], b, l, u, pg[2].
+// FP32 bands, the FP32 CG vectors r[2], w, p[2], Ap[2], and the FP32 arrays
+// of the mixed phase x[2], g[2], b, l, u, pg[2].
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
-  return (size_t)(p->kc + 5 + 9) * vec;
+  return (size_t)(p->kc + 7 + 9) * vec;
 }
 
 static void carve64(gpcg_problem* p) {
@@ -241,17 +241,17 @@ static void carve64(gpcg_problem* p) {
   I.u = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.x[k] = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.g[k] = (double*)take(vec);
-  I.r64 = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.r64[k] = (double*)take(vec);
   I.w64 = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.p64[k] = (double*)take(vec);
-  I.Ap64 = (double*)take(vec);
+  for (int k = 0; k < 2; ++k) I.Ap64[k] = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.mask[k] = (unsigned*)take(msk);
   I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_groups));
   I.tmaps = take(align256(sizeof(CUtensorMap) * M_COUNT));
   I.tma64 = 0;
   I.tma32 = 0;
   I.tma_gp = 0;
-  I.x0 = I.r64;  // a given start point is staged in r (unused until CG starts)
+  I.x0 = I.r64[0];  // a given start point is staged in r (unused until CG starts)
 }
 
 // ----------------------------------------------------------- tensor maps --
@@ -294,25 +294,35 @@ static bool encode_map(CUtensorMap* m, bool f32, const void* base, const gpcg_pr
 static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   if (!have_encode()) return false;
   DevInst& I = p->inst;
-  const int h = f32 ? 4 : 2, ch = f32 ? 32 : 16, cha = f32 ? 32 : 16;
-  const int b0 = f32 ? M32_RH : M64_RH;
-  CUtensorMap m[11];
-  const void* r = f32 ? (const void*)I.r32 : (const void*)I.r64;
-  const void* p0 = f32 ? (const void*)I.p32[0] : (const void*)I.p64[0];
-  const void* p1 = f32 ? (const void*)I.p32[1] : (const void*)I.p64[1];
+  // h: halo columns; c: CG_B chunk rows; a: CG_A chunk rows; f: fused chunk rows
+  const int h = f32 ? 4 : 2, c = f32 ? 32 : 16, a = f32 ? 32 : 16, f = f32 ? 16 : 8;
+  const int b0 = f32 ? M32_RH0 : M64_RH0;
+  auto v = [&](int k, const char* which) -> const void* {
+    if (which[0] == 'r') return f32 ? (const void*)I.r32[k] : (const void*)I.r64[k];
+    if (which[0] == 'p') return f32 ? (const void*)I.p32[k] : (const void*)I.p64[k];
+    return f32 ? (const void*)I.Ap32[k] : (const void*)I.Ap64[k];
+  };
   const void* d = f32 ? (const void*)I.diag32 : (const void*)I.diag;
   const void* cx = f32 ? (const void*)I.cx32 : (const void*)I.cx;
   const void* cy = f32 ? (const void*)I.cy32 : (const void*)I.cy;
   const void* w = f32 ? (const void*)I.w32 : (const void*)I.w64;
-  const void* ap = f32 ? (const void*)I.Ap32 : (const void*)I.Ap64;
-  bool ok = encode_map(&m[0], f32, r, p, 64 + 2 * h, ch + 2) &&
-            encode_map(&m[1], f32, p0, p, 64 + 2 * h, ch + 2) &&
-            encode_map(&m[2], f32, p1, p, 64 + 2 * h, ch + 2) &&
-            encode_map(&m[3], f32, d, p, 64, ch) && encode_map(&m[4], f32, cx, p, 64 + h, ch) &&
-            encode_map(&m[5], f32, cy, p, 64, ch + 1) && encode_map(&m[6], f32, w, p, 64, cha) &&
-            encode_map(&m[7], f32, r, p, 64, cha) && encode_map(&m[8], f32, p0, p, 64, cha) &&
-            encode_map(&m[9], f32, p1, p, 64, cha) && encode_map(&m[10], f32, ap, p, 64, cha);
-  if (!ok) return false;
+  CUtensorMap m[kCgMaps];
+  CUtensorMap* q = m;
+  auto e = [&](const void* base, int bw, int bh) { return encode_map(q++, f32, base, p, bw, bh); };
+  const bool ok =
+      // CG_B: RH[2], PH[2], D, CX, CY
+      e(v(0, "r"), 64 + 2 * h, c + 2) && e(v(1, "r"), 64 + 2 * h, c + 2) &&
+      e(v(0, "p"), 64 + 2 * h, c + 2) && e(v(1, "p"), 64 + 2 * h, c + 2) && e(d, 64, c) &&
+      e(cx, 64 + h, c) && e(cy, 64, c + 1) &&
+      // CG_A: W, R[2], P[2], AP[2]
+      e(w, 64, a) && e(v(0, "r"), 64, a) && e(v(1, "r"), 64, a) && e(v(0, "p"), 64, a) &&
+      e(v(1, "p"), 64, a) && e(v(0, "A"), 64, a) && e(v(1, "A"), 64, a) &&
+      // fused: FRH[2], FPH[2], FAPH[2], FW, FD, FCX, FCY
+      e(v(0, "r"), 64 + 2 * h, f + 2) && e(v(1, "r"), 64 + 2 * h, f + 2) &&
+      e(v(0, "p"), 64 + 2 * h, f + 2) && e(v(1, "p"), 64 + 2 * h, f + 2) &&
+      e(v(0, "A"), 64 + 2 * h, f + 2) && e(v(1, "A"), 64 + 2 * h, f + 2) && e(w, 64, f) &&
+      e(d, 64, f) && e(cx, 64 + h, f) && e(cy, 64, f + 1);
+  if (!ok || q != m + kCgMaps) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -365,11 +375,10 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   float* x32 = take();
   float* y32 = take();
   float* z32 = p->dim == 3 ? take() : nullptr;
-  I.r32 = take();
+  for (int k = 0; k < 2; ++k) I.r32[k] = take();
   I.w32 = take();
-  I.p32[0] = take();
-  I.p32[1] = take();
-  I.Ap32 = take();
+  for (int k = 0; k < 2; ++k) I.p32[k] = take();
+  for (int k = 0; k < 2; ++k) I.Ap32[k] = take();
   for (int k = 0; k < 2; ++k) I.x32[k] = take();
   for (int k = 0; k < 2; ++k) I.g32[k] = take();
   float* b32 = take();
@@ -896,7 +905,9 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
       temps.push_back(dy);
     }
     DevInst& I = p->inst;
-    void* r = f32 ? (void*)I.r32 : (void*)I.r64;
+    // the standalone pass is a CG_B step at pcur = 0 with beta = 0: it reads
+    // r[1] (p = -r) and writes p[1], Ap[1]
+    void* r = f32 ? (void*)I.r32[1] : (void*)I.r64[1];
     void* p0 = f32 ? (void*)I.p32[0] : (void*)I.p64[0];
     if (launch_spmv_setup(I, dm, dp, I.mask[0], r, p0, f32, s) != cudaSuccess) {
       st = fail(GPCG_ERR_CUDA, "spmv set-up launch");
@@ -904,7 +915,7 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
     }
     Ctl out;
     if ((st = one_pass(p, spmv_ctl(f32, 0, 0), s, &out)) != GPCG_OK) break;
-    const void* ap = f32 ? (const void*)I.Ap32 : (const void*)I.Ap64;
+    const void* ap = f32 ? (const void*)I.Ap32[1] : (const void*)I.Ap64[1];
     if (launch_unpad(I, ap, f32, dy, s) != cudaSuccess) {
       st = fail(GPCG_ERR_CUDA, "unpad launch");
       break;
@@ -946,7 +957,7 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
     std::vector<double> ones((size_t)p->n, 1.0);
     CK(cudaMemcpyAsync(dp, ones.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, s));
     DevInst& I = p->inst;
-    CK(launch_spmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.r32 : (void*)I.r64,
+    CK(launch_spmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.r32[1] : (void*)I.r64[1],
                          f32 ? (void*)I.p32[0] : (void*)I.p64[0], f32, s));
     CK(cudaStreamSynchronize(s));
     cudaFree(dm);

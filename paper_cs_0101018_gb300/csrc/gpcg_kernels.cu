@@ -758,7 +758,7 @@ struct OpCgB {
   const T* bx;
   const T* by;
   const T* bz;
-  FF* ff;  // [2] FP32 accumulators (kF32)
+  FF* ff;  // [3] FP32 accumulators (kF32)
   __device__ const T* diag() const { return bd; }
   __device__ const T* cx() const { return bx; }
   __device__ const T* cy() const { return by; }
@@ -815,12 +815,17 @@ struct OpCgB {
     if (FIRST) {
       st2(r_out, i, v0, v1, -v[0], -v[1]);
       st2(w_out, i, v0, v1, T(0), T(0));
+      // ||r||^2 and ||Ap||^2 (the fused steps predict ||r_1||^2 from them)
       if (kF32) {
         ff_fma(ff[1], (float)v[0], (float)v[0]);
         ff_fma(ff[1], (float)v[1], (float)v[1]);
+        ff_fma(ff[2], (float)a0, (float)a0);
+        ff_fma(ff[2], (float)a1, (float)a1);
       } else {
         acc.s[1] = fma((double)v[0], (double)v[0], acc.s[1]);
         acc.s[1] = fma((double)v[1], (double)v[1], acc.s[1]);
+        acc.s[2] = fma((double)a0, (double)a0, acc.s[2]);
+        acc.s[2] = fma((double)a1, (double)a1, acc.s[2]);
       }
     }
   }
@@ -828,9 +833,10 @@ struct OpCgB {
 
 // ---------------------------------------------------------- pointwise passes
 
-// P_CG_A: w += alpha p, r += alpha Ap, ||r||^2.
+// P_CG_A: w += alpha p, r_out = r + alpha Ap, ||r_out||^2.
 template <class T>
-__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T* __restrict__ p,
+__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* __restrict__ r,
+                                          T* r_out, const T* __restrict__ p,
                                           const T* __restrict__ ap, double alpha, int x0, int y0,
                                           int z, Acc& acc, FF* ffs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -854,7 +860,7 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, T* r, const T*
     rv[0] = fma(a, av[0], rv[0]);
     rv[1] = fma(a, av[1], rv[1]);
     st2(w, i, v0, v1, wv[0], wv[1]);
-    st2(r, i, v0, v1, rv[0], rv[1]);
+    st2(r_out, i, v0, v1, rv[0], rv[1]);
     if (sizeof(T) == 4) {
       ff_fma(ff, (float)rv[0], (float)rv[0]);
       ff_fma(ff, (float)rv[1], (float)rv[1]);
@@ -912,6 +918,7 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
       break;
     case P_CG_B: per = sv * kc + (C.first_cg ? 8.0 + 4.0 * sv : 4.0 * sv) + 0.125; break;
     case P_CG_A: per = 6.0 * sv; break;
+    case P_CG_F: per = sv * kc + 8.0 * sv + 0.125; break;
     default: break;
   }
   return per * (double)I.n;
@@ -948,6 +955,7 @@ __device__ void begin_cg(const DevInst& I, Ctl& C) {
   C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
   C.cg_j = 0;
   C.cdmax = 0.0;
+  C.cg_finish = 0;
   if (I.opt.max_cg >= 1) {
     C.first_cg = 1;
     C.beta = 0.0;
@@ -990,6 +998,37 @@ __device__ void on_converged(const DevInst& I, Ctl& C) {
     begin_cg(I, C);
   } else {
     set_done(C, S_OK);
+  }
+}
+
+// Whether the instance's CG phase runs fused steps (P_CG_F): 2-D grids whose
+// tensor maps of the CG precision are valid.
+__device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
+  return I.dim == 2 && I.tmaps != nullptr && (C.cg32 ? I.tma32 : I.tma64);
+}
+
+// After alpha_j of a fused phase is known (C.rr = ||r_j||^2): the CG
+// bookkeeping and Eq. cgstop1 of step j, with ||r_{j+1}||^2 taken from
+// ||r_j + alpha_j Ap_j||^2 = ||r_j||^2 + 2 alpha_j <r_j,Ap_j> + alpha_j^2 ||Ap_j||^2
+// (its sums come from the pass that formed Ap_j); then either the next fused
+// step or a last P_CG_A that completes w_{j+1} before the projected search.
+__device__ void cg_advance(const DevInst& I, Ctl& C, double rAp, double ApAp) {
+  const Opts& o = I.opt;
+  const double rr_next = C.rr + 2.0 * C.alpha * rAp + C.alpha * C.alpha * ApAp;
+  C.cg_j++;
+  C.cg_iters++;
+  if (C.refining) C.refine_cg_iters++;
+  const double delta = 0.5 * C.alpha * C.rr;  // q_k(w_j) - q_k(w_{j+1})
+  const bool stop = (C.cg_j >= 2 && delta <= C.eta2 * C.cdmax) ||  // Eq. cgstop1
+                    rr_next <= 0.0 || C.cg_j >= o.max_cg;
+  if (delta > C.cdmax) C.cdmax = delta;
+  if (stop) {
+    C.cg_finish = 1;
+    C.pass = P_CG_A;
+  } else {
+    C.beta = rr_next / C.rr;
+    C.rr = rr_next;
+    C.pass = P_CG_F;
   }
 }
 
@@ -1146,10 +1185,32 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       }
       C.alpha = C.rr / pAp;
       C.pcur ^= 1;
-      C.pass = P_CG_A;
+      if (cg_fused(I, C)) {
+        // first step of a fused phase: r_0 = -p_0, so <r_0, Ap_0> = -<p_0, Ap_0>
+        cg_advance(I, C, -pAp, red[2]);
+      } else {
+        C.pass = P_CG_A;
+      }
+      break;
+    }
+    case P_CG_F: {
+      C.rr = red[0];  // ||r_j||^2 of the stored r_j
+      const double pAp = red[1];
+      if (!(pAp > 0.0)) {
+        set_done(C, S_NUMERIC);
+        break;
+      }
+      C.alpha = C.rr / pAp;
+      C.pcur ^= 1;
+      cg_advance(I, C, red[2], red[3]);
       break;
     }
     case P_CG_A: {
+      if (C.cg_finish) {  // w of the last fused step is complete: search along it
+        C.cg_finish = 0;
+        start_search(C, C.cg32 ? D_W32 : D_W64);
+        break;
+      }
       const double rr_new = red[0];
       C.cg_j++;
       C.cg_iters++;
@@ -1205,7 +1266,7 @@ struct ChunkGeo {
       (2 * (CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
   static constexpr int SZ_A = 64 * CH_A * (int)sizeof(T);
   static constexpr unsigned TX_A = 4 * SZ_A;
-  static constexpr int MB = sizeof(T) == 4 ? M32_RH : M64_RH;  // first map of the precision
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;  // first map of the precision
 };
 static_assert(ChunkGeo<float>::END_B <= kStageBytes && ChunkGeo<double>::END_B <= kStageBytes,
               "stage layout");
@@ -1221,23 +1282,26 @@ template <class T>
 __device__ __forceinline__ void issue_cgb(const DevInst& I, int pcur, int x0, int yc,
                                           unsigned st, unsigned bar) {
   using G = ChunkGeo<T>;
+  constexpr int o = -M32_RH0;  // map offsets within a precision's block
   mbar_expect(bar, G::TX_B);
-  tma_load2d(st + G::OFF_R, tmap(I, G::MB + 0), x0 - G::H, yc - 1, bar);
-  tma_load2d(st + G::OFF_P, tmap(I, G::MB + 1 + pcur), x0 - G::H, yc - 1, bar);
-  tma_load2d(st + G::OFF_D, tmap(I, G::MB + 3), x0, yc, bar);
-  tma_load2d(st + G::OFF_CX, tmap(I, G::MB + 4), x0 - G::H, yc, bar);
-  tma_load2d(st + G::OFF_CY, tmap(I, G::MB + 5), x0, yc - 1, bar);
+  // r of this step was written by P_CG_A into r[pcur^1]
+  tma_load2d(st + G::OFF_R, tmap(I, G::MB + o + M32_RH0 + (pcur ^ 1)), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, G::MB + o + M32_PH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, G::MB + o + M32_D), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, G::MB + o + M32_CX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, G::MB + o + M32_CY), x0, yc - 1, bar);
 }
 
 template <class T>
 __device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, int row,
                                           unsigned st, unsigned bar) {
   using G = ChunkGeo<T>;
+  constexpr int o = -M32_RH0;
   mbar_expect(bar, G::TX_A);
-  tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + 6), x0, row, bar);
-  tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + 7), x0, row, bar);
-  tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + 8 + pcur), x0, row, bar);
-  tma_load2d(st + 3 * G::SZ_A, tmap(I, G::MB + 10), x0, row, bar);
+  tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + o + M32_W), x0, row, bar);
+  tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + o + M32_R0 + pcur), x0, row, bar);
+  tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + o + M32_P0 + pcur), x0, row, bar);
+  tma_load2d(st + 3 * G::SZ_A, tmap(I, G::MB + o + M32_AP0 + pcur), x0, row, bar);
 }
 
 // P_CG_B (not the first step of a phase) on one staged chunk of a 2-D grid:
@@ -1316,9 +1380,9 @@ __device__ __forceinline__ void load_chunk_bits(const DevInst& I, const unsigned
   }
 }
 
-// P_CG_A on one staged chunk: w += alpha p, r += alpha Ap, ||r||^2.  `row` is
-// the chunk's first row in the (ny*nz) row space, `ylim` the number of rows
-// of the chunk that lie inside the plane.
+// P_CG_A on one staged chunk: w += alpha p, r' = r + alpha Ap (into `r`, the
+// other buffer), ||r'||^2.  `row` is the chunk's first row in the (ny*nz) row
+// space, `ylim` the number of rows of the chunk that lie inside the plane.
 template <class T>
 __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char* st, int x0,
                                           int row, int ylim, T alpha, T* w, T* r, Acc& acc,
@@ -1350,6 +1414,241 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
       acc.s[0] = fma((double)r0, (double)r0, acc.s[0]);
       acc.s[0] = fma((double)r1, (double)r1, acc.s[0]);
     }
+  }
+}
+
+// ------------------------------------------------------- fused CG step --
+//
+// P_CG_F on a 2-D instance: one pass per CG step j >= 1 (Algorithm GPCG's
+// CG phase on the reduced system, Eq. cg2).  With alpha = alpha_{j-1} and
+// beta = beta_{j-1} over the halo box of the chunk, in place in the stage:
+//   r_j = r_{j-1} + alpha Ap_{j-1},   p_j = -r_j + beta p_{j-1},
+// at the chunk's points also w_j = w_{j-1} + alpha p_{j-1}; then
+// Ap_j = Z Z' A Z Z' p_j and the sums ||r_j||^2, <p_j,Ap_j>, <r_j,Ap_j>,
+// ||Ap_j||^2 (from which the finalizer takes alpha_j and ||r_{j+1}||^2).
+// r, p and Ap are read from buffer pcur and written to pcur^1.  Stage layout,
+// T = float (f = 16 rows, h = 4) or double (f = 8, h = 2): R | P | AP, each
+// (64+2h) x (f+2) from (x0-h, y-1) | W 64 x f | D 64 x f | CX (64+h) x f from
+// x0-h | CY 64 x (f+1) from y-1.
+template <class T>
+struct GeoF {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int SZ_I = 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_R = 0, OFF_P = SZ_H, OFF_AP = 2 * SZ_H, OFF_W = 3 * SZ_H;
+  static constexpr int OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX =
+      (3 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
+};
+static_assert(GeoF<float>::END <= kStageBytes && GeoF<double>::END <= kStageBytes,
+              "stage layout");
+
+template <class T>
+__device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = GeoF<T>;
+  constexpr int o = G::MB - M32_RH0;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_AP, tmap(I, o + M32_FAPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_W, tmap(I, o + M32_FW), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, o + M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, o + M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, o + M32_FCY), x0, yc - 1, bar);
+}
+
+// P_CG_F, FP64 (one row per warp): r_j and p_j are formed once per element
+// of the halo box, in place in the stage, then a block barrier; recomputing
+// them per warp would triple the FP64 work, the bound of this pass.
+__device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* st, int x0, int yc,
+                                              int rows, double alpha, double beta,
+                                              const unsigned* fbits, double* w, double* r_out,
+                                              double* p_out, double* ap_out, Acc& acc) {
+  using G = GeoF<double>;
+  double* R = reinterpret_cast<double*>(st + G::OFF_R);
+  double* P = reinterpret_cast<double*>(st + G::OFF_P);
+  const double* AP = reinterpret_cast<const double*>(st + G::OFF_AP);
+  const double* W = reinterpret_cast<const double*>(st + G::OFF_W);
+  const double* D = reinterpret_cast<const double*>(st + G::OFF_D);
+  const double* CX = reinterpret_cast<const double*>(st + G::OFF_CX);
+  const double* CY = reinterpret_cast<const double*>(st + G::OFF_CY);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ylim = min(rows, I.ny - yc);
+  double s_rr = 0.0;
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) {
+    const int br = e / G::BW, bc = e - br * G::BW;
+    const double pold = P[e];
+    const double rn = fma(alpha, AP[e], R[e]);
+    const double pn = fma(beta, pold, -rn);
+    R[e] = rn;
+    P[e] = pn;
+    const int ry = br - 1, col = bc - G::H;
+    if (ry >= 0 && ry < ylim && col >= 0 && col < 64 && x0 + col < I.nx) {
+      const long long i = (long long)(yc + ry) * I.px + x0 + col;
+      w[i] = fma(alpha, pold, W[ry * 64 + col]);
+      r_out[i] = rn;
+      p_out[i] = pn;
+      s_rr = fma(rn, rn, s_rr);
+    }
+  }
+  acc.s[0] += s_rr;
+  __syncthreads();
+  static_assert(G::CH == kWarps, "one row per warp");
+  const int ry = warp;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (ry >= ylim || !v0) return;
+  const double* Pr = P + (ry + 1) * G::BW + G::H + c;
+  const double* Rr = R + (ry + 1) * G::BW + G::H + c;
+  const double vc0 = Pr[0], vc1 = Pr[1];
+  const double* Dr = D + ry * 64 + c;
+  const double* Xr = CX + ry * (64 + G::H) + G::H + c;
+  const double* Ys = CY + ry * 64 + c;
+  const double* Yn = CY + (ry + 1) * 64 + c;
+  double a0 = Dr[0] * vc0;
+  a0 = fma(Xr[-1], Pr[-1], a0);
+  a0 = fma(Xr[0], vc1, a0);
+  a0 = fma(Ys[0], Pr[-G::BW], a0);
+  a0 = fma(Yn[0], Pr[G::BW], a0);
+  double a1 = Dr[1] * vc1;
+  a1 = fma(Xr[0], vc0, a1);
+  a1 = fma(Xr[1], Pr[2], a1);
+  a1 = fma(Ys[1], Pr[1 - G::BW], a1);
+  a1 = fma(Yn[1], Pr[G::BW + 1], a1);
+  const unsigned fb = fbits[0] & 3u;
+  a0 = (fb & 1u) ? a0 : 0.0;
+  a1 = (fb & 2u) ? a1 : 0.0;
+  st2(ap_out, (long long)(yc + ry) * I.px + e0, v0, v1, a0, a1);
+  const double r0 = Rr[0], r1 = Rr[1];
+  acc.s[1] = fma(vc0, a0, fma(vc1, a1, acc.s[1]));
+  acc.s[2] = fma(r0, a0, fma(r1, a1, acc.s[2]));
+  acc.s[3] = fma(a0, a0, fma(a1, a1, acc.s[3]));
+}
+
+template <class T>
+struct V2;
+template <>
+struct V2<float> {
+  using type = float2;
+};
+template <>
+struct V2<double> {
+  using type = double2;
+};
+
+// Add a thread's FP32 partial of one chunk to its float-float accumulator.
+__device__ __forceinline__ void ff_acc(FF& a, float v) { a = ff_add(a, FF{v, 0.0f}); }
+
+// P_CG_F on one staged chunk (rows yc .. yc+rows-1).  Sums: [0] ||r_j||^2,
+// [1] <p_j,Ap_j>, [2] <r_j,Ap_j>, [3] ||Ap_j||^2.  Each warp forms r_j and p_j
+// for its rows and the rows above and below from the staged r, p, Ap (west
+// and east neighbours by shuffles), so no block barrier is needed.  For
+// T = float a thread sums its few terms of the chunk in FP32 and adds that to
+// its float-float accumulator once per chunk.
+template <class T>
+__device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                          int yc, int rows, T alpha, T beta, const unsigned* fbits,
+                                          T* w, T* r_out, T* p_out, T* ap_out, Acc& acc, FF* ff) {
+  using G = GeoF<T>;
+  using T2 = typename V2<T>::type;
+  constexpr int RPW = G::CH / kWarps;
+  const T* R = reinterpret_cast<const T*>(st + G::OFF_R);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* AP = reinterpret_cast<const T*>(st + G::OFF_AP);
+  const T* W = reinterpret_cast<const T*>(st + G::OFF_W);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int r0 = warp * RPW;  // first chunk row of this warp
+  if (r0 >= ylim) return;     // warp-uniform
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q)
+  T pn[RPW + 2][2], rn[RPW][2], po[RPW][2], pw[RPW], pe[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + c;
+    const T2 rv = *reinterpret_cast<const T2*>(R + b);
+    const T2 pv = *reinterpret_cast<const T2*>(P + b);
+    const T2 av = *reinterpret_cast<const T2*>(AP + b);
+    const T ra = fma(alpha, av.x, rv.x), rb = fma(alpha, av.y, rv.y);
+    pn[q][0] = fma(beta, pv.x, -ra);
+    pn[q][1] = fma(beta, pv.y, -rb);
+    if (q >= 1 && q <= RPW) {
+      rn[q - 1][0] = ra;
+      rn[q - 1][1] = rb;
+      po[q - 1][0] = pv.x;
+      po[q - 1][1] = pv.y;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
+    pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
+    const int b = (r0 + k + 1) * G::BW + G::H + c;
+    if (lane == 0) pw[k] = fma(beta, P[b - 1], -fma(alpha, AP[b - 1], R[b - 1]));
+    if (lane == 31) pe[k] = fma(beta, P[b + 2], -fma(alpha, AP[b + 2], R[b + 2]));
+  }
+  T s_rr = T(0), s_pap = T(0), s_rap = T(0), s_apap = T(0);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    if (ry >= ylim) break;
+    const int q = k + 1;
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    // diag, west, east, south, north (the order of the register sweep)
+    T a0 = Dr[0] * pn[q][0];
+    a0 = fma(Xr[-1], pw[k], a0);
+    a0 = fma(Xr[0], pn[q][1], a0);
+    a0 = fma(Ys[0], pn[q - 1][0], a0);
+    a0 = fma(Yn[0], pn[q + 1][0], a0);
+    T a1 = Dr[1] * pn[q][1];
+    a1 = fma(Xr[0], pn[q][0], a1);
+    a1 = fma(Xr[1], pe[k], a1);
+    a1 = fma(Ys[1], pn[q - 1][1], a1);
+    a1 = fma(Yn[1], pn[q + 1][1], a1);
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    const T2 wv = *reinterpret_cast<const T2*>(W + ry * 64 + c);
+    const long long i = (long long)(yc + ry) * I.px + e0;
+    st2(w, i, v0, v1, fma(alpha, po[k][0], wv.x), fma(alpha, po[k][1], wv.y));
+    st2(r_out, i, v0, v1, rn[k][0], rn[k][1]);
+    st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
+    st2(ap_out, i, v0, v1, a0, a1);
+    // points past nx hold zeros (the boxes are zero-filled there)
+    s_rr = fma(rn[k][0], rn[k][0], s_rr);
+    s_rr = fma(rn[k][1], rn[k][1], s_rr);
+    s_pap = fma(pn[q][0], a0, s_pap);
+    s_pap = fma(pn[q][1], a1, s_pap);
+    s_rap = fma(rn[k][0], a0, s_rap);
+    s_rap = fma(rn[k][1], a1, s_rap);
+    s_apap = fma(a0, a0, s_apap);
+    s_apap = fma(a1, a1, s_apap);
+  }
+  if (sizeof(T) == 4) {
+    ff_acc(ff[0], (float)s_rr);
+    ff_acc(ff[1], (float)s_pap);
+    ff_acc(ff[2], (float)s_rap);
+    ff_acc(ff[3], (float)s_apap);
+  } else {
+    acc.s[0] += (double)s_rr;
+    acc.s[1] += (double)s_pap;
+    acc.s[2] += (double)s_rap;
+    acc.s[3] += (double)s_apap;
   }
 }
 
@@ -1448,6 +1747,7 @@ __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned 
   const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
   const long long row = (long long)y * I.px + x0;
   bool fr[2];
+  float s_pg = 0.0f;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int j = lane + 32 * h;
@@ -1466,7 +1766,7 @@ __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned 
     const bool act = al || au;
     fr[h] = ok && !act;
     const float pg = pg_compf(al, au, g);
-    ff_fma(ff, pg, pg);
+    s_pg = fmaf(pg, pg, s_pg);
     acc.c[0] += ok && act;
     acc.c[1] += ok && ((al && g >= 0.0f) || (au && g <= 0.0f));
     if (ok) {
@@ -1474,6 +1774,7 @@ __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned 
       pg_out[row + j] = pg;
     }
   }
+  ff_acc(ff, s_pg);
   const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
   const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
   const int wc = (x0 >> 5) + lane;
@@ -1491,6 +1792,7 @@ __device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned c
   const float* D = reinterpret_cast<const float*>(st + F::OFF_D);
   const float* CX = reinterpret_cast<const float*>(st + F::OFF_CX);
   const float* CY = reinterpret_cast<const float*>(st + F::OFF_CY);
+  float s_gg = 0.0f, s_gag = 0.0f;  // this chunk's terms, added once to ff
 #pragma unroll
   for (int k = 0; k < RPW; ++k) {
     const int r = warp * RPW + k;
@@ -1505,10 +1807,12 @@ __device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned c
       a = fmaf(cx[0], V[1], a);
       a = fmaf(CY[r * 64 + j], V[-F::BW], a);
       a = fmaf(CY[(r + 1) * 64 + j], V[F::BW], a);
-      ff_fma(ff[0], V[0], V[0]);
-      ff_fma(ff[1], V[0], a);
+      s_gg = fmaf(V[0], V[0], s_gg);
+      s_gag = fmaf(V[0], a, s_gag);
     }
   }
+  ff_acc(ff[0], s_gg);
+  ff_acc(ff[1], s_gag);
 }
 
 // The two words of the current free set covering row y, columns x0..x0+63,
@@ -1581,6 +1885,7 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
   }
   const long long row = (long long)y * I.px + x0;
   bool fr[2];
+  float s_gs = 0.0f, s_sgt = 0.0f, s_pg = 0.0f;  // this chunk's terms, added once to ff
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int j = lane + 32 * h;
@@ -1602,9 +1907,9 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
     const float pg = pg_compf(al, au, gt);
     float sk = alpha * d;
     if (act) sk = deq(xt, xv) ? 0.0f : (float)(xt - xv);
-    ff_fma(ff[0], g, sk);
-    ff_fma(ff[1], sk, gt);
-    ff_fma(ff[2], pg, pg);
+    s_gs = fmaf(g, sk, s_gs);
+    s_sgt = fmaf(sk, gt, s_sgt);
+    s_pg = fmaf(pg, pg, s_pg);
     acc.c[0] += ok && act;
     acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
     acc.c[2] += ok && (((fb_old >> h) & 1u) != (fr[h] ? 1u : 0u));
@@ -1615,6 +1920,9 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
       pg_out[row + j] = pg;
     }
   }
+  ff_acc(ff[0], s_gs);
+  ff_acc(ff[1], s_sgt);
+  ff_acc(ff[2], s_pg);
   const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
   const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
   const int wc = (x0 >> 5) + lane;
@@ -1624,6 +1932,7 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
 // Whether the item's pass runs through the TMA pipeline.
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
+  if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
   if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
   const int ok = S.cg32 ? I.tma32 : I.tma64;
   if (!ok) return false;
@@ -1635,6 +1944,7 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
 __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
+  if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
 }
 
@@ -1666,6 +1976,9 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
                                             const Chunk& c, unsigned st, unsigned bar) {
   if (gp) {
     issue_gp(I, S, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_CG_F) {
+    if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
   } else if (S.cg32) {
     if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cga<float>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
@@ -1696,20 +2009,30 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
                                I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
                                I.mask[cur ^ 1], acc, ffs);
     }
-  } else if (S.pass == P_CG_B) {
+  } else if (S.pass == P_CG_F) {
+    const int q = S.pcur ^ 1;
     if (S.cg32)
-      cgb_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.beta, fbits, I.p32[S.pcur ^ 1],
-                       I.Ap32, acc, ffs[0]);
+      cgf_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits, I.w32,
+                       I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
     else
-      cgb_chunk<double>(I, st, c.x0, c.yc, c.rows, S.beta, fbits, I.p64[S.pcur ^ 1], I.Ap64,
-                        acc, ffs[0]);
+      cgf_chunk_box(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q], I.p64[q],
+                    I.Ap64[q], acc);
+  } else if (S.pass == P_CG_B) {
+    const int q = S.pcur ^ 1;
+    if (S.cg32)
+      cgb_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.beta, fbits, I.p32[q], I.Ap32[q],
+                       acc, ffs[0]);
+    else
+      cgb_chunk<double>(I, st, c.x0, c.yc, c.rows, S.beta, fbits, I.p64[q], I.Ap64[q], acc,
+                        ffs[0]);
   } else {
     const int ylim = min(c.rows, I.ny - c.yc);
+    const int q = S.pcur ^ 1;
     if (S.cg32)
-      cga_chunk<float>(I, st, c.x0, c.z * I.ny + c.yc, ylim, (float)S.alpha, I.w32, I.r32, acc,
-                       ffs[0]);
+      cga_chunk<float>(I, st, c.x0, c.z * I.ny + c.yc, ylim, (float)S.alpha, I.w32, I.r32[q],
+                       acc, ffs[0]);
     else
-      cga_chunk<double>(I, st, c.x0, c.z * I.ny + c.yc, ylim, S.alpha, I.w64, I.r64, acc,
+      cga_chunk<double>(I, st, c.x0, c.z * I.ny + c.yc, ylim, S.alpha, I.w64, I.r64[q], acc,
                         ffs[0]);
   }
 }
@@ -1722,8 +2045,9 @@ __device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
     case P_CENSUS: return gp32 ? 1 : 2;
     case P_GP_ALPHA: return 2;
     case P_TRIAL: return 3;
-    case P_CG_B: return first ? 2 : 1;
+    case P_CG_B: return first ? 3 : 1;
     case P_CG_A: return 1;
+    case P_CG_F: return 4;
     default: return 0;
   }
 }
@@ -1788,25 +2112,28 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       const float* g32 = S.gp32 ? I.g32[cur] : nullptr;
       if (S.cg32) {
         if (S.first_cg) {
-          OpCgB<float, true> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], 0.0f, g32,
-                                I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
+          OpCgB<float, true> op{I, I.r32[pcur ^ 1], I.p32[pcur], I.g[cur], I.mask[cur], 0.0f, g32,
+                                I.p32[pcur ^ 1], I.Ap32[pcur ^ 1], I.r32[pcur ^ 1], I.w32,
                                 I.diag32, I.cx32, I.cy32, I.cz32, ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpCgB<float, false> op{I, I.r32, I.p32[pcur], I.g[cur], I.mask[cur], (float)S.beta,
-                                 g32, I.p32[pcur ^ 1], I.Ap32, I.r32, I.w32,
+          OpCgB<float, false> op{I, I.r32[pcur ^ 1], I.p32[pcur], I.g[cur], I.mask[cur],
+                                 (float)S.beta, g32, I.p32[pcur ^ 1], I.Ap32[pcur ^ 1],
+                                 I.r32[pcur ^ 1], I.w32,
                                  I.diag32, I.cx32, I.cy32, I.cz32, ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         }
       } else {
         if (S.first_cg) {
-          OpCgB<double, true> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], 0.0, nullptr,
-                                 I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
+          OpCgB<double, true> op{I, I.r64[pcur ^ 1], I.p64[pcur], I.g[cur], I.mask[cur], 0.0,
+                                 nullptr, I.p64[pcur ^ 1], I.Ap64[pcur ^ 1], I.r64[pcur ^ 1],
+                                 I.w64,
                                  I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpCgB<double, false> op{I, I.r64, I.p64[pcur], I.g[cur], I.mask[cur], S.beta, nullptr,
-                                  I.p64[pcur ^ 1], I.Ap64, I.r64, I.w64,
+          OpCgB<double, false> op{I, I.r64[pcur ^ 1], I.p64[pcur], I.g[cur], I.mask[cur], S.beta,
+                                  nullptr, I.p64[pcur ^ 1], I.Ap64[pcur ^ 1], I.r64[pcur ^ 1],
+                                  I.w64,
                                   I.diag, I.cx, I.cy, I.cz, nullptr};
           stencil_tile(I, op, x0, y0, z, acc);
         }
@@ -1815,9 +2142,11 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
     }
     case P_CG_A:
       if (S.cg32) {
-        cg_a_tile<float>(I, I.w32, I.r32, I.p32[pcur], I.Ap32, S.alpha, x0, y0, z, acc, ffs);
+        cg_a_tile<float>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur], I.Ap32[pcur],
+                         S.alpha, x0, y0, z, acc, ffs);
       } else {
-        cg_a_tile<double>(I, I.w64, I.r64, I.p64[pcur], I.Ap64, S.alpha, x0, y0, z, acc, ffs);
+        cg_a_tile<double>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur], I.Ap64[pcur],
+                          S.alpha, x0, y0, z, acc, ffs);
       }
       break;
     default:
@@ -1849,8 +2178,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   // flight between groups)
   double(*s_sum)[kThreads] = reinterpret_cast<double(*)[kThreads]>(stage0);
   float(*s_ffh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + 4 * 8 * kThreads);
-  float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 12) * kThreads);
-  static_assert((32 + 24) * kThreads <= kStageBytes, "reduction scratch");
+  float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 16) * kThreads);
+  static_assert((32 + 32) * kThreads <= kStageBytes, "reduction scratch");
 
   if (tid == 0) {
     s_inst = -1;
@@ -1924,7 +2253,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
-    FF ffs[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const int grp = tr.y;
     const bool tma = tma_pass(I, S);
     if (!tma) {
@@ -1945,7 +2274,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       constexpr int kDepth = kStages - 1;
       static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
       const bool gp = gp_tma(I, S);
-      const bool want_bits = S.pass == P_CG_B || (gp && S.pass == P_TRIAL);
+      const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
       const int ch = chunk_rows(S, gp);
       const int rpw = ch / kWarps;
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
@@ -1974,7 +2303,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       }
       for (;;) {
         if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
-          if (S.pass == P_CG_B && !gp) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           if (kDepth == 2) issue_chunk(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2));
           else issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1));
         }
@@ -1986,8 +2316,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         unsigned char* st = stage(seq);
         const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
         bool failed;
-        if (S.pass == P_CG_B && !gp) {
-          // the CG_B chunk has a barrier inside: agree on the wait first
+        if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp) {
+          // the chunk has a barrier inside: agree on the wait first
           failed = __syncthreads_or(!ok);
           if (!failed) run_chunk(I, S, gp, st, c0, fbits, acc, ffs);
           __syncthreads();  // the stage may be refilled
@@ -2025,7 +2355,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
     // butterfly).  FP32 passes reduce their float-float accumulators in
     // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
-    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B) ? S.cg32 != 0
+    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F) ? S.cg32 != 0
                                                               : (S.pass != P_START && S.gp32 != 0);
     const int ns = n_sums(S.pass, S.first_cg, S.gp32);
     for (int k = 0; k < ns; ++k) {
