@@ -48,10 +48,10 @@ constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 // CX = (64+h) x c from x0-h; CY = 64 x (c+1) from y0-1; W, R, P, AP are
 // 64 x a boxes over the (nx, ny*nz) row space.
 //
-// The mixed-phase gradient-projection passes of a 2-D instance stage 8-row
-// chunks (census, trial) and 32-row chunks (alpha0): G8 = FP32 halo box
-// 72 x 10 from (x0-4, y0-1); G34 = FP32 halo box 72 x 34; the FP64 and FP32
-// interior boxes are 64 x 8; GCX = 68 x 8 from x0-4; GCY = 64 x 9 from y0-1.
+// The mixed-phase gradient-projection passes of a 2-D instance stage 16-row
+// chunks (census, trial; their band boxes are the fused pass's FD, FCX, FCY)
+// and 32-row chunks (alpha0): G18 = FP32 halo box 72 x 18 from (x0-4, y0-1);
+// G34 = FP32 halo box 72 x 34; the interior boxes are 64 x 16.
 //
 // The fused CG pass (2-D) stages f-row chunks (16 FP32, 8 FP64): FRH, FPH,
 // FAPH = halo boxes (64+2h) x (f+2) of r, p, Ap; FW, FD = 64 x f; FCX =
@@ -64,10 +64,9 @@ enum TMap : int {
   M64_RH0, M64_RH1, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R0, M64_R1, M64_P0,
   M64_P1, M64_AP0, M64_AP1, M64_FRH0, M64_FRH1, M64_FPH0, M64_FPH1, M64_FAPH0, M64_FAPH1, M64_FW,
   M64_FD, M64_FCX, M64_FCY,
-  MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G8
+  MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G18
   MG_PGH0, MG_PGH1,                                                  // G34
-  MG_X0, MG_X1, MG_L, MG_U,                                          // FP64 64 x 8
-  MG_B32, MG_D32, MG_CX32, MG_CY32,                                  // FP32 64 x 8, GCX, GCY
+  MG_L32, MG_U32, MG_B32,                                            // 64 x 16
   M_COUNT
 };
 constexpr int kGpMaps = M_COUNT - MG_X32H0;
@@ -115,7 +114,8 @@ struct Opts {
 // Mutable per-instance state, owned by the finalizer of each pass.
 struct Ctl {
   int pass, status, done, cur, pcur, cg32, first_cg, dir;
-  int trial_gp, refining, refined, continue_cg, hold, final_census;
+  int trial_gp, refining, refined, continue_cg, hold;
+  int x32_live;      // mixed phase: the iterate lives in x32; the next FP64 census rebuilds x
   int outer_iters, gp_j, ls_i, cg_j, gp_iters, cg_iters, ls_trials, refine_cg_iters;
   int passes;
   int gp32;          // mixed phase: census / GP / search passes stream FP32 (see kernels)
@@ -144,7 +144,7 @@ struct DevInst {
   unsigned* mask[2];
   double *r64[2], *w64, *p64[2], *Ap64[2];  // r, p, Ap double-buffered (index pcur)
   float *r32[2], *w32, *p32[2], *Ap32[2];
-  float *x32[2], *g32[2], *b32, *l32, *u32;  // FP32 copies streamed in the mixed phase
+  float *x32[2], *g32[2], *b32, *l32, *u32;  // FP32 iterate and copies of the mixed phase
   float* pg32[2];          // mixed phase: grad_Omega q at x[k] (FP32), read by alpha0
   Opts opt;
 };

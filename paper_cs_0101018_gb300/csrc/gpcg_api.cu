@@ -338,12 +338,10 @@ static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
   CUtensorMap m[kGpMaps];
   CUtensorMap* q = m;
   auto f32 = [&](const float* a, int bw, int bh) { return encode_map(q++, true, a, p, bw, bh); };
-  auto f64 = [&](const double* a) { return encode_map(q++, false, a, p, 64, 8); };
-  bool ok = f32(I.x32[0], 72, 10) && f32(I.x32[1], 72, 10) && f32(I.l32, 72, 10) &&
-            f32(I.u32, 72, 10) && f32(I.g32[0], 72, 10) && f32(I.g32[1], 72, 10) &&
-            f32(I.w32, 72, 10) && f32(I.pg32[0], 72, 34) && f32(I.pg32[1], 72, 34) &&
-            f64(I.x[0]) && f64(I.x[1]) && f64(I.l) && f64(I.u) && f32(I.b32, 64, 8) &&
-            f32(I.diag32, 64, 8) && f32(I.cx32, 68, 8) && f32(I.cy32, 64, 9);
+  bool ok = f32(I.x32[0], 72, 18) && f32(I.x32[1], 72, 18) && f32(I.l32, 72, 18) &&
+            f32(I.u32, 72, 18) && f32(I.g32[0], 72, 18) && f32(I.g32[1], 72, 18) &&
+            f32(I.w32, 72, 18) && f32(I.pg32[0], 72, 34) && f32(I.pg32[1], 72, 34) &&
+            f32(I.l32, 64, 16) && f32(I.u32, 64, 16) && f32(I.b32, 64, 16);
   if (!ok || q != m + kGpMaps) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MG_X32H0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -237,7 +237,7 @@ struct Acc {
 
 // What a tile needs from the instance's control block (read once per tile).
 struct Snap {
-  int pass, cur, pcur, cg32, first_cg, dir, gp32, pad;
+  int pass, cur, pcur, cg32, first_cg, dir, gp32, x32_live;
   double alpha, beta;
 };
 
@@ -373,24 +373,53 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
 
 // P_CENSUS: operand x; g = Ax + b and everything Sec. 2 defines at x:
 // sums ||pg||^2 and <x, g + b> (= 2 (q - c)), counts |A(x)| and |B(x)|.
+//
+// After the mixed phase (x32 != nullptr) the iterate is rebuilt from the
+// FP32 one first: a point on an FP32 bound goes to the FP64 bound, any other
+// to P[x32] (the projection of Sec. 3 onto the FP64 box); x_out receives it.
 struct OpCensus {
   using T = double;
   const DevInst& I;
   const double* __restrict__ x;
   double* g_out;
   unsigned* m_out;
+  const float* __restrict__ x32;
+  double* x_out;
   __device__ const double* diag() const { return I.diag; }
   __device__ const double* cx() const { return I.cx; }
   __device__ const double* cy() const { return I.cy; }
   __device__ const double* cz() const { return I.cz; }
+  __device__ double rebuild(float xf, double l, double u, float lf, float uf) const {
+    if (xf == lf) return l;
+    if (xf == uf) return u;
+    return mid3(l, u, (double)xf);
+  }
   __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
     if (!row_ok(I, y, z)) {
       o[0] = o[1] = 0.0;
       return;
     }
-    ld2(x, pidx(I, y, z, e0), v0, v1, o);
+    const long long i = pidx(I, y, z, e0);
+    if (x32) {
+      float xf[2], lf[2], uf[2];
+      double l[2], u[2];
+      ld2(x32, i, v0, v1, xf);
+      ld2(I.l32, i, v0, v1, lf);
+      ld2(I.u32, i, v0, v1, uf);
+      ld2(I.l, i, v0, v1, l);
+      ld2(I.u, i, v0, v1, u);
+      o[0] = v0 ? rebuild(xf[0], l[0], u[0], lf[0], uf[0]) : 0.0;
+      o[1] = v1 ? rebuild(xf[1], l[1], u[1], lf[1], uf[1]) : 0.0;
+    } else {
+      ld2(x, i, v0, v1, o);
+    }
   }
-  __device__ double operand_at(long long i, int, int, int) const { return __ldg(x + i); }
+  __device__ double operand_at(long long i, int, int, int) const {
+    if (x32)
+      return rebuild(__ldg(x32 + i), __ldg(I.l + i), __ldg(I.u + i), __ldg(I.l32 + i),
+                     __ldg(I.u32 + i));
+    return __ldg(x + i);
+  }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const double v[2], const double av[2], Acc& acc) const {
     double b[2], l[2], u[2], g[2];
@@ -415,6 +444,7 @@ struct OpCensus {
       }
     }
     st2(g_out, i, v0, v1, g[0], g[1]);
+    if (x32) st2(x_out, i, v0, v1, v[0], v[1]);
     write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
   }
 };
@@ -552,18 +582,18 @@ struct OpTrial {
 
 // ------------------------------------------------- mixed-phase FP32 passes --
 //
-// In the mixed phase the census, the alpha0 pass and the trials apply the FP32
-// stencil to FP32 operands and keep the gradient in FP32, but the iterate,
-// the projection onto the box and the active/binding sets stay exact FP64:
-// every point's new x is P[x + alpha d] in FP64 and its status is decided by
-// exact comparisons with l and u.  Sums use the compensated FP32 accumulator.
+// In the mixed phase the census, the alpha0 pass and the trials work on the
+// FP32 iterate x32, kept on the FP32 box [l32, u32] by the FP32 projection
+// (which returns the bound itself when it clamps): a point is active when x32
+// equals l32 or u32.  The FP32 stencil is applied to FP32 operands and the
+// gradient is kept in FP32; sums use the compensated FP32 accumulator.  The
+// first FP64 census after the phase rebuilds the FP64 iterate (OpCensus).
 
 // P_CENSUS (mixed): operand x32; g32 = A32 x32 + b32, pg32; |A|, |B|,
 // ||pg||^2.
 struct OpCensus32 {
   using T = float;
   const DevInst& I;
-  const double* __restrict__ x;
   const float* __restrict__ x32;
   float* g_out;
   float* pg_out;
@@ -582,20 +612,17 @@ struct OpCensus32 {
   }
   __device__ float operand_at(long long i, int, int, int) const { return __ldg(x32 + i); }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
-                         const float[2], const float av[2], Acc& acc) const {
-    double xv[2], l[2], u[2];
-    float b[2], g[2];
-    ld2(x, i, v0, v1, xv);
-    ld2(I.l, i, v0, v1, l);
-    ld2(I.u, i, v0, v1, u);
+                         const float v[2], const float av[2], Acc& acc) const {
+    float l[2], u[2], b[2], g[2], pg[2];
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
     ld2(I.b32, i, v0, v1, b);
     bool fr[2];
-    float pg[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
       g[k] = av[k] + b[k];
-      const bool al = deq(xv[k], l[k]), au = deq(xv[k], u[k]);
+      const bool al = v[k] == l[k], au = v[k] == u[k];
       const bool act = al || au;
       fr[k] = ok && !act;
       pg[k] = pg_compf(al, au, g[k]);
@@ -643,21 +670,17 @@ struct OpGpAlpha32 {
   }
 };
 
-// P_TRIAL (mixed): operand P[x32 + alpha d] in FP32 for the product; the new
-// iterate P[x + alpha d] in FP64 with its exact status; g32t = A32 xt32 + b32;
-// <g, s>, <s, gt>, ||pg||^2; s is alpha d where the point stays free and
-// exact otherwise.
+// P_TRIAL (mixed): operand xt32 = P[x32 + alpha d] on the FP32 box;
+// g32t = A32 xt32 + b32, the status of xt32, pg32; <g, s>, <s, gt>,
+// ||pg||^2 with s = xt32 - x32.
 template <int DK>
 struct OpTrial32 {
   using T = float;
   const DevInst& I;
-  const double* __restrict__ x;
   const float* __restrict__ x32;
   const float* __restrict__ g32;
   const float* __restrict__ w32;
   float alpha;
-  double alpha_d;
-  double* xt_out;
   float* xt32_out;
   float* gt_out;
   float* pg_out;
@@ -696,41 +719,33 @@ struct OpTrial32 {
   }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const float v[2], const float av[2], Acc& acc) const {
-    double xv[2], l[2], u[2], xt[2];
-    float g[2], b[2], gt[2];
-    ld2(x, i, v0, v1, xv);
-    ld2(I.l, i, v0, v1, l);
-    ld2(I.u, i, v0, v1, u);
+    float xv[2], l[2], u[2], g[2], b[2], gt[2], pg[2];
+    ld2(x32, i, v0, v1, xv);
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
     ld2(g32, i, v0, v1, g);
     ld2(I.b32, i, v0, v1, b);
     bool fr[2];
-    float pgv[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const bool ok = k == 0 ? v0 : v1;
-      const float d = DK == D_NEG_G ? -g[k] : (ok ? __ldg(w32 + i + k) : 0.0f);
-      xt[k] = ok ? mid3(l[k], u[k], fma(alpha_d, (double)d, xv[k])) : 0.0;
       gt[k] = av[k] + b[k];
-      const bool al = deq(xt[k], l[k]), au = deq(xt[k], u[k]);
+      const bool al = v[k] == l[k], au = v[k] == u[k];
       const bool act = al || au;
       fr[k] = ok && !act;
-      pgv[k] = pg_compf(al, au, gt[k]);
+      pg[k] = pg_compf(al, au, gt[k]);
       if (ok) {
-        float sk;
-        if (!act) sk = alpha * d;
-        else if (deq(xt[k], xv[k])) sk = 0.0f;
-        else sk = (float)(xt[k] - xv[k]);
+        const float sk = v[k] - xv[k];
         ff_fma(ff[0], g[k], sk);
         ff_fma(ff[1], sk, gt[k]);
-        ff_fma(ff[2], pgv[k], pgv[k]);
+        ff_fma(ff[2], pg[k], pg[k]);
         acc.c[0] += act;
         acc.c[1] += (al && gt[k] >= 0.0f) || (au && gt[k] <= 0.0f);
       }
     }
-    st2(xt_out, i, v0, v1, xt[0], xt[1]);
     st2(xt32_out, i, v0, v1, v[0], v[1]);
     st2(gt_out, i, v0, v1, gt[0], gt[1]);
-    st2(pg_out, i, v0, v1, pgv[0], pgv[1]);
+    st2(pg_out, i, v0, v1, pg[0], pg[1]);
     acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
   }
 };
@@ -908,11 +923,13 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   double per = 0.0;
   switch (pass) {
     case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
-    case P_CENSUS: per = C.gp32 ? 4.0 * kc + 40.125 : 8.0 * kc + 40.0 + 0.125; break;
+    case P_CENSUS:
+      per = C.gp32 ? 4.0 * kc + 24.125 : 8.0 * kc + 40.0 + 0.125 + (C.x32_live ? 20.0 : 0.0);
+      break;
     case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 4.0 : 8.0 * kc + 32.0; break;
     case P_TRIAL:
       if (C.gp32)
-        per = 4.0 * kc + 68.25 + (C.dir == D_W32 ? 4.0 : 0.0);
+        per = 4.0 * kc + 36.25 + (C.dir == D_W32 ? 4.0 : 0.0);
       else
         per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
       break;
@@ -1040,9 +1057,11 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
   C.alg_bytes += pass_bytes(I, C, C.pass);
   switch (C.pass) {
     case P_START:
+      C.x32_live = C.gp32;  // the mixed phase moves the FP32 iterate only
       C.pass = P_CENSUS;
       break;
     case P_CENSUS: {
+      if (!C.gp32) C.x32_live = 0;  // an FP64 census rebuilt x from x32
       C.pg2 = red[0];
       C.xgb = red[1];
       C.nA = red[4];
@@ -1654,32 +1673,34 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
 
 // ------------------------------------ TMA-staged mixed-phase GP passes --
 //
-// In the mixed phase the census and the trial passes of a 2-D instance stream
-// 8-row chunks (one row per warp).  Stage layout (boxes 128-byte aligned):
-//   XH | LH | UH | DH | GH : FP32 72 x 10 from (x0-4, y-1): x32, l32, u32,
+// In the mixed phase the iterate is x32, kept on the FP32 box [l32, u32]: a
+// point is active when x32 equals l32 or u32 (bit for bit; the FP32
+// projection returns the bound itself), and the first FP64 census after the
+// phase rebuilds the FP64 iterate from it (see OpCensus).  The census and the
+// trial of a 2-D instance stream 16-row chunks (two rows per warp).  Stage
+// layout (boxes 128-byte aligned):
+//   XH | LH | UH | DH | GH : FP32 72 x 18 from (x0-4, y-1): x32, l32, u32,
 //                            the direction (g32 or w32), g32 (trial along w)
-//   X | L | U : FP64 64 x 8 (x, l, u)    B : FP32 64 x 8 (b32)
-//   D : 64 x 8    CX : 68 x 8 from x0-4    CY : 64 x 9 from y-1
-// The census loads XH and the interior boxes only.  The alpha0 pass streams
-// 32-row chunks of pg32 through the R slot of the FP32 CG_B layout, with its
-// D, CX and CY boxes.
+//   B : 64 x 16 (b32)   D : 64 x 16   CX : 68 x 16 from x0-4   CY : 64 x 17 from y-1
+// The census loads XH, l32 and u32 as 64 x 16 boxes in the LH and UH slots,
+// B and the bands.  The alpha0 pass streams 32-row chunks of pg32 through the
+// R slot of the FP32 CG_B layout, with its D, CX and CY boxes.
 struct GeoGP {
-  static constexpr int CH = 8, H = 4, BW = 64 + 2 * H;
+  static constexpr int CH = 16, H = 4, BW = 64 + 2 * H;
+  static constexpr int RPW = CH / kWarps;
   static constexpr int SZ_H = align128((CH + 2) * BW * 4);
-  static constexpr int SZ_64 = 64 * CH * 8, SZ_32 = 64 * CH * 4;
+  static constexpr int SZ_32 = 64 * CH * 4;
   static constexpr int OFF_XH = 0, OFF_LH = SZ_H, OFF_UH = 2 * SZ_H, OFF_DH = 3 * SZ_H;
   static constexpr int OFF_GH = 4 * SZ_H;
-  static constexpr int OFF_X = 5 * SZ_H, OFF_L = OFF_X + SZ_64, OFF_U = OFF_L + SZ_64;
-  static constexpr int OFF_B = OFF_U + SZ_64, OFF_D = OFF_B + SZ_32;
+  static constexpr int OFF_B = 5 * SZ_H, OFF_D = OFF_B + SZ_32;
   static constexpr int OFF_CX = OFF_D + SZ_32;
   static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
   static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 4);
   static constexpr unsigned TX_H = (CH + 2) * BW * 4;  // one halo box
-  static constexpr unsigned TX_INT =
-      3 * SZ_64 + 2 * SZ_32 + (64 + H) * CH * 4 + 64 * (CH + 1) * 4;
+  static constexpr unsigned TX_BANDS = SZ_32 + SZ_32 + (64 + H) * CH * 4 + 64 * (CH + 1) * 4;
 };
 static_assert(GeoGP::END <= kStageBytes, "stage layout");
-static_assert(GeoGP::CH == kWarps, "one row per warp");
+static_assert(GeoGP::CH == GeoF<float>::CH, "the GP passes use the fused pass's band maps");
 
 // Whether the item's pass is a mixed-phase GP pass on the TMA path.
 __device__ __forceinline__ bool gp_tma(const DevInst& I, const Snap& S) {
@@ -1702,83 +1723,84 @@ __device__ __forceinline__ void issue_gp(const DevInst& I, const Snap& S, int x0
     tma_load2d(st + F::OFF_CY, tmap(I, M32_CY), x0, yc - 1, bar);
     return;
   }
-  const bool trial = S.pass == P_TRIAL;
-  const bool along_w = trial && S.dir == D_W32;
-  const unsigned n_halo = trial ? (along_w ? 5u : 4u) : 1u;
-  mbar_expect(bar, n_halo * G::TX_H + G::TX_INT);
+  const bool along_w = S.pass == P_TRIAL && S.dir == D_W32;
+  mbar_expect(bar, S.pass == P_TRIAL ? (along_w ? 5u : 4u) * G::TX_H + G::TX_BANDS
+                                     : G::TX_H + 2 * G::SZ_32 + G::TX_BANDS);
   tma_load2d(st + G::OFF_XH, tmap(I, MG_X32H0 + cur), x0 - G::H, yc - 1, bar);
-  if (trial) {
+  if (S.pass == P_TRIAL) {
     tma_load2d(st + G::OFF_LH, tmap(I, MG_L32H), x0 - G::H, yc - 1, bar);
     tma_load2d(st + G::OFF_UH, tmap(I, MG_U32H), x0 - G::H, yc - 1, bar);
     tma_load2d(st + G::OFF_DH, tmap(I, along_w ? MG_W32H : MG_G32H0 + cur), x0 - G::H, yc - 1,
                bar);
     if (along_w) tma_load2d(st + G::OFF_GH, tmap(I, MG_G32H0 + cur), x0 - G::H, yc - 1, bar);
+  } else {
+    tma_load2d(st + G::OFF_LH, tmap(I, MG_L32), x0, yc, bar);
+    tma_load2d(st + G::OFF_UH, tmap(I, MG_U32), x0, yc, bar);
   }
-  tma_load2d(st + G::OFF_X, tmap(I, MG_X0 + cur), x0, yc, bar);
-  tma_load2d(st + G::OFF_L, tmap(I, MG_L), x0, yc, bar);
-  tma_load2d(st + G::OFF_U, tmap(I, MG_U), x0, yc, bar);
   tma_load2d(st + G::OFF_B, tmap(I, MG_B32), x0, yc, bar);
-  tma_load2d(st + G::OFF_D, tmap(I, MG_D32), x0, yc, bar);
-  tma_load2d(st + G::OFF_CX, tmap(I, MG_CX32), x0 - G::H, yc, bar);
-  tma_load2d(st + G::OFF_CY, tmap(I, MG_CY32), x0, yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M32_FCY), x0, yc - 1, bar);
 }
 
-// In the staged GP passes lane `lane` of warp w owns columns lane and lane+32
-// of row w of the chunk, so that shared-memory reads are unit-stride and a
+// In the staged GP passes lane `lane` of a warp owns columns lane and lane+32
+// of each of its rows, so that shared-memory reads are unit-stride and a
 // warp ballot is one word of the free-set bitmask.
 
-// P_CENSUS (mixed) on one staged 8-row chunk: g32 = A32 x32 + b32, pg32, the
-// exact free set and |A|, |B|, ||pg||^2 (as OpCensus32).  Points past nx
+// P_CENSUS (mixed) on one staged 16-row chunk: g32 = A32 x32 + b32, pg32,
+// the free set and |A|, |B|, ||pg||^2 (as OpCensus32).  Points past nx
 // arrive as zeros and contribute nothing.
 __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned char* st, int x0,
                                                int yc, float* g_out, float* pg_out,
                                                unsigned* m_out, Acc& acc, FF& ff) {
   using G = GeoGP;
-  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = yc + r;
-  if (y >= I.ny) return;  // warp-uniform
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
+  const float* L = reinterpret_cast<const float*>(st + G::OFF_LH);  // 64 x 16
+  const float* U = reinterpret_cast<const float*>(st + G::OFF_UH);
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
   const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
   const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
   const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
-  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
-  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
-  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
-  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
-  const long long row = (long long)y * I.px + x0;
-  bool fr[2];
   float s_pg = 0.0f;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int j = lane + 32 * h;
-    const bool ok = x0 + j < I.nx;
-    const float* V = XH + (r + 1) * G::BW + G::H + j;
-    const float* cx = CX + r * (64 + G::H) + G::H + j;
-    // diag, west, east, south, north (the order of the register sweep)
-    float a = D[r * 64 + j] * V[0];
-    a = fmaf(cx[-1], V[-1], a);
-    a = fmaf(cx[0], V[1], a);
-    a = fmaf(CY[r * 64 + j], V[-G::BW], a);
-    a = fmaf(CY[(r + 1) * 64 + j], V[G::BW], a);
-    const float g = a + B[r * 64 + j];
-    const double xv = X[r * 64 + j];
-    const bool al = deq(xv, L[r * 64 + j]), au = deq(xv, U[r * 64 + j]);
-    const bool act = al || au;
-    fr[h] = ok && !act;
-    const float pg = pg_compf(al, au, g);
-    s_pg = fmaf(pg, pg, s_pg);
-    acc.c[0] += ok && act;
-    acc.c[1] += ok && ((al && g >= 0.0f) || (au && g <= 0.0f));
-    if (ok) {
-      g_out[row + j] = g;
-      pg_out[row + j] = pg;
+  for (int k = 0; k < G::RPW; ++k) {
+    const int r = warp * G::RPW + k;
+    const int y = yc + r;
+    if (y >= I.ny) break;  // warp-uniform
+    const long long row = (long long)y * I.px + x0;
+    bool fr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const bool ok = x0 + j < I.nx;
+      const float* V = XH + (r + 1) * G::BW + G::H + j;
+      const float* cx = CX + r * (64 + G::H) + G::H + j;
+      // diag, west, east, south, north (the order of the register sweep)
+      float a = D[r * 64 + j] * V[0];
+      a = fmaf(cx[-1], V[-1], a);
+      a = fmaf(cx[0], V[1], a);
+      a = fmaf(CY[r * 64 + j], V[-G::BW], a);
+      a = fmaf(CY[(r + 1) * 64 + j], V[G::BW], a);
+      const float g = a + B[r * 64 + j];
+      const bool al = V[0] == L[r * 64 + j], au = V[0] == U[r * 64 + j];
+      const bool act = al || au;
+      fr[h] = ok && !act;
+      const float pg = pg_compf(al, au, g);
+      s_pg = fmaf(pg, pg, s_pg);
+      acc.c[0] += ok && act;
+      acc.c[1] += ok && ((al && g >= 0.0f) || (au && g <= 0.0f));
+      if (ok) {
+        g_out[row + j] = g;
+        pg_out[row + j] = pg;
+      }
     }
+    const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+    const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+    const int wc = (x0 >> 5) + lane;
+    if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
   }
   ff_acc(ff, s_pg);
-  const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
-  const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
-  const int wc = (x0 >> 5) + lane;
-  if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
 }
 
 // P_GP_ALPHA (mixed) on one staged chunk of up to 32 rows: <pg,pg>,
@@ -1815,118 +1837,123 @@ __device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned c
   ff_acc(ff[1], s_gag);
 }
 
-// The two words of the current free set covering row y, columns x0..x0+63,
-// reduced to this lane's bits (bit h: column lane + 32h), loaded ahead of the
-// chunk's data.
-__device__ __forceinline__ unsigned load_gp_bits(const DevInst& I, const unsigned* __restrict__ m,
-                                                 int x0, int yc) {
+// This lane's bits of the current free set for each of its rows of a staged
+// GP chunk (bit h: column lane + 32h), loaded ahead of the chunk's data.
+__device__ __forceinline__ void load_gp_bits(const DevInst& I, const unsigned* __restrict__ m,
+                                             int x0, int yc, unsigned fbits[4]) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = min(yc + warp, I.ny - 1);
   const int wc = x0 >> 5;
-  const unsigned* p = m + (long long)y * I.mw + wc;
-  const unsigned w0 = __ldg(p);
-  const unsigned w1 = wc + 1 < I.mw ? __ldg(p + 1) : 0u;
-  return ((w0 >> lane) & 1u) | (((w1 >> lane) & 1u) << 1);
+#pragma unroll
+  for (int k = 0; k < GeoGP::RPW; ++k) {
+    const int y = min(yc + warp * GeoGP::RPW + k, I.ny - 1);
+    const unsigned* p = m + (long long)y * I.mw + wc;
+    const unsigned w0 = __ldg(p);
+    const unsigned w1 = wc + 1 < I.mw ? __ldg(p + 1) : 0u;
+    fbits[k] = ((w0 >> lane) & 1u) | (((w1 >> lane) & 1u) << 1);
+  }
 }
 
-// P_TRIAL (mixed) on one staged 8-row chunk (as OpTrial32).  Each warp forms
-// the FP32 operand P[x32 + alpha d] for its own row and the rows above and
-// below, takes the west and east neighbours by shuffles, then gives every
-// point its exact FP64 iterate and status, g32t, pg32 and the sums.  `fb_old`
-// holds the lane's two bits of the current free set (see load_gp_bits).
+// P_TRIAL (mixed) on one staged 16-row chunk (as OpTrial32): each warp forms
+// xt32 = P[x32 + alpha d] on the FP32 box for its rows and the rows above and
+// below (west and east neighbours by shuffles), then g32t = A32 xt32 + b32,
+// the status of xt32, pg32 and the sums <g,s>, <s,gt>, ||pg||^2 with
+// s = xt32 - x32.  `fbits` holds the lane's bits of the current free set.
 template <int DK>
 __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned char* st, int x0,
-                                              int yc, float alpha, double alpha_d,
-                                              unsigned fb_old, double* xt_out, float* xt32_out,
-                                              float* gt_out, float* pg_out, unsigned* m_out,
-                                              Acc& acc, FF* ff) {
+                                              int yc, float alpha, const unsigned* fbits,
+                                              float* xt_out, float* gt_out, float* pg_out,
+                                              unsigned* m_out, Acc& acc, FF* ff) {
   using G = GeoGP;
-  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y = yc + r;
-  if (y >= I.ny) return;  // warp-uniform
+  constexpr int RPW = G::RPW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = warp * RPW;
+  if (yc + r0 >= I.ny) return;  // warp-uniform
   const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
   const float* LH = reinterpret_cast<const float*>(st + G::OFF_LH);
   const float* UH = reinterpret_cast<const float*>(st + G::OFF_UH);
   const float* DH = reinterpret_cast<const float*>(st + G::OFF_DH);
   const float* GH = reinterpret_cast<const float*>(st + (DK == D_W32 ? G::OFF_GH : G::OFF_DH));
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
   const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
   const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
   const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
-  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
-  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
-  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
-  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
   auto opnd = [&](int e) {
     const float d = DK == D_NEG_G ? -DH[e] : DH[e];
     return mid3f(LH[e], UH[e], fmaf(alpha, d, XH[e]));
   };
-  const int b = (r + 1) * G::BW + G::H + lane;  // box index of column `lane` of this row
-  float vc[2], vs[2], vn[2];
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q)
+  float v[RPW + 2][2];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    vc[h] = opnd(b + 32 * h);
-    vs[h] = opnd(b + 32 * h - G::BW);
-    vn[h] = opnd(b + 32 * h + G::BW);
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + lane;
+    v[q][0] = opnd(b);
+    v[q][1] = opnd(b + 32);
   }
-  float vw[2], ve[2];
-  vw[0] = __shfl_up_sync(FULL_MASK, vc[0], 1);
-  vw[1] = __shfl_up_sync(FULL_MASK, vc[1], 1);
-  ve[0] = __shfl_down_sync(FULL_MASK, vc[0], 1);
-  ve[1] = __shfl_down_sync(FULL_MASK, vc[1], 1);
-  const float col31 = __shfl_sync(FULL_MASK, vc[0], 31);
-  const float col32 = __shfl_sync(FULL_MASK, vc[1], 0);
-  if (lane == 0) {
-    vw[0] = opnd(b - 1);
-    vw[1] = col31;
-  }
-  if (lane == 31) {
-    ve[0] = col32;
-    ve[1] = opnd(b + 33);
-  }
-  const long long row = (long long)y * I.px + x0;
-  bool fr[2];
   float s_gs = 0.0f, s_sgt = 0.0f, s_pg = 0.0f;  // this chunk's terms, added once to ff
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int j = lane + 32 * h;
-    const bool ok = x0 + j < I.nx;
-    const float* cx = CX + r * (64 + G::H) + G::H + j;
-    float a = D[r * 64 + j] * vc[h];
-    a = fmaf(cx[-1], vw[h], a);
-    a = fmaf(cx[0], ve[h], a);
-    a = fmaf(CY[r * 64 + j], vs[h], a);
-    a = fmaf(CY[(r + 1) * 64 + j], vn[h], a);
-    const float gt = a + B[r * 64 + j];
-    const float g = GH[b + 32 * h];
-    const float d = DK == D_NEG_G ? -g : DH[b + 32 * h];
-    const double xv = X[r * 64 + j], l = L[r * 64 + j], u = U[r * 64 + j];
-    const double xt = mid3(l, u, fma(alpha_d, (double)d, xv));
-    const bool al = deq(xt, l), au = deq(xt, u);
-    const bool act = al || au;
-    fr[h] = ok && !act;
-    const float pg = pg_compf(al, au, gt);
-    float sk = alpha * d;
-    if (act) sk = deq(xt, xv) ? 0.0f : (float)(xt - xv);
-    s_gs = fmaf(g, sk, s_gs);
-    s_sgt = fmaf(sk, gt, s_sgt);
-    s_pg = fmaf(pg, pg, s_pg);
-    acc.c[0] += ok && act;
-    acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
-    acc.c[2] += ok && (((fb_old >> h) & 1u) != (fr[h] ? 1u : 0u));
-    if (ok) {
-      xt_out[row + j] = xt;
-      xt32_out[row + j] = vc[h];
-      gt_out[row + j] = gt;
-      pg_out[row + j] = pg;
+  for (int k = 0; k < RPW; ++k) {
+    const int r = r0 + k;
+    const int y = yc + r;
+    if (y >= I.ny) break;  // warp-uniform
+    const int q = k + 1;
+    const int b = (r + 1) * G::BW + G::H + lane;  // box index of column `lane` of row r
+    // west and east neighbours across the 64 columns
+    float vw[2], ve[2];
+    vw[0] = __shfl_up_sync(FULL_MASK, v[q][0], 1);
+    vw[1] = __shfl_up_sync(FULL_MASK, v[q][1], 1);
+    ve[0] = __shfl_down_sync(FULL_MASK, v[q][0], 1);
+    ve[1] = __shfl_down_sync(FULL_MASK, v[q][1], 1);
+    const float col31 = __shfl_sync(FULL_MASK, v[q][0], 31);
+    const float col32 = __shfl_sync(FULL_MASK, v[q][1], 0);
+    if (lane == 0) {
+      vw[0] = opnd(b - 1);
+      vw[1] = col31;
     }
+    if (lane == 31) {
+      ve[0] = col32;
+      ve[1] = opnd(b + 33);
+    }
+    const long long row = (long long)y * I.px + x0;
+    bool fr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const int e = b + 32 * h;
+      const bool ok = x0 + j < I.nx;
+      const float* cx = CX + r * (64 + G::H) + G::H + j;
+      float a = D[r * 64 + j] * v[q][h];
+      a = fmaf(cx[-1], vw[h], a);
+      a = fmaf(cx[0], ve[h], a);
+      a = fmaf(CY[r * 64 + j], v[q - 1][h], a);
+      a = fmaf(CY[(r + 1) * 64 + j], v[q + 1][h], a);
+      const float gt = a + B[r * 64 + j];
+      const float xt = v[q][h];
+      const float sk = xt - XH[e];
+      const float g = GH[e];
+      const bool al = xt == LH[e], au = xt == UH[e];
+      const bool act = al || au;
+      fr[h] = ok && !act;
+      const float pg = pg_compf(al, au, gt);
+      s_gs = fmaf(g, sk, s_gs);
+      s_sgt = fmaf(sk, gt, s_sgt);
+      s_pg = fmaf(pg, pg, s_pg);
+      acc.c[0] += ok && act;
+      acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
+      acc.c[2] += ok && (((fbits[k] >> h) & 1u) != (fr[h] ? 1u : 0u));
+      if (ok) {
+        xt_out[row + j] = xt;
+        gt_out[row + j] = gt;
+        pg_out[row + j] = pg;
+      }
+    }
+    const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+    const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+    const int wc = (x0 >> 5) + lane;
+    if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
   }
   ff_acc(ff[0], s_gs);
   ff_acc(ff[1], s_sgt);
   ff_acc(ff[2], s_pg);
-  const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
-  const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
-  const int wc = (x0 >> 5) + lane;
-  if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
 }
 
 // Whether the item's pass runs through the TMA pipeline.
@@ -1999,15 +2026,13 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
     } else if (S.pass == P_GP_ALPHA) {
       alpha32_chunk(I, st, c.yc, c.rows, ffs);
     } else {
-      const double al = S.dir == D_ZERO ? 0.0 : S.alpha;
+      const float al = S.dir == D_ZERO ? 0.0f : (float)S.alpha;
       if (S.dir == D_W32)
-        trial32_chunk<D_W32>(I, st, c.x0, c.yc, (float)al, al, fbits[0], I.x[cur ^ 1],
-                             I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1],
-                             acc, ffs);
+        trial32_chunk<D_W32>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
+                             I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
       else
-        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, (float)al, al, fbits[0], I.x[cur ^ 1],
-                               I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
-                               I.mask[cur ^ 1], acc, ffs);
+        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
+                               I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
     }
   } else if (S.pass == P_CG_F) {
     const int q = S.pcur ^ 1;
@@ -2061,10 +2086,12 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       break;
     case P_CENSUS: {
       if (S.gp32) {
-        OpCensus32 op{I, I.x[cur], I.x32[cur], I.g32[cur], I.pg32[cur], I.mask[cur], ffs};
+        OpCensus32 op{I, I.x32[cur], I.g32[cur], I.pg32[cur], I.mask[cur], ffs};
         stencil_tile(I, op, x0, y0, z, acc);
       } else {
-        OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur]};
+        // the first FP64 census after the mixed phase rebuilds x from x32
+        OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur], S.x32_live ? I.x32[cur] : nullptr,
+                    I.x[cur]};
         stencil_tile(I, op, x0, y0, z, acc);
       }
       break;
@@ -2083,14 +2110,14 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       const double alpha = S.dir == D_ZERO ? 0.0 : S.alpha;
       if (S.gp32) {
         if (S.dir == D_W32) {
-          OpTrial32<D_W32> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
-                              I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
-                              I.mask[cur ^ 1], I.mask[cur], ffs};
+          OpTrial32<D_W32> op{I, I.x32[cur], I.g32[cur], I.w32, (float)alpha, I.x32[cur ^ 1],
+                              I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], I.mask[cur],
+                              ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         } else {
-          OpTrial32<D_NEG_G> op{I, I.x[cur], I.x32[cur], I.g32[cur], I.w32, (float)alpha, alpha,
-                                I.x[cur ^ 1], I.x32[cur ^ 1], I.g32[cur ^ 1], I.pg32[cur ^ 1],
-                                I.mask[cur ^ 1], I.mask[cur], ffs};
+          OpTrial32<D_NEG_G> op{I, I.x32[cur], I.g32[cur], I.w32, (float)alpha, I.x32[cur ^ 1],
+                                I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], I.mask[cur],
+                                ffs};
           stencil_tile(I, op, x0, y0, z, acc);
         }
       } else if (S.dir == D_W64) {
@@ -2238,6 +2265,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         sS.first_cg = C.first_cg;
         sS.dir = C.dir;
         sS.gp32 = C.gp32;
+        sS.x32_live = C.x32_live;
         sS.alpha = C.alpha;
         sS.beta = C.beta;
         s_inst = tr.x;
@@ -2298,7 +2326,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       }
       unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
       if (want_bits) {
-        if (gp) fbits[0] = load_gp_bits(I, I.mask[S.cur], c0.x0, c0.yc);
+        if (gp) load_gp_bits(I, I.mask[S.cur], c0.x0, c0.yc, fbits);
         else load_bits(I, I.mask[S.cur], rpw, c0.x0, c0.yc, fbits);
       }
       for (;;) {
@@ -2310,7 +2338,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         }
         // the next chunk's free bits, loaded while this chunk's data arrive
         if (want_bits && h1) {
-          if (gp) fbits_n[0] = load_gp_bits(I, I.mask[S.cur], c1.x0, c1.yc);
+          if (gp) load_gp_bits(I, I.mask[S.cur], c1.x0, c1.yc, fbits_n);
           else load_bits(I, I.mask[S.cur], rpw, c1.x0, c1.yc, fbits_n);
         }
         unsigned char* st = stage(seq);
