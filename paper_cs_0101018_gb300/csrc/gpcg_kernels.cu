@@ -929,11 +929,13 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
     case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 4.0 : 8.0 * kc + 32.0; break;
     case P_TRIAL:
       if (C.gp32)
-        per = 4.0 * kc + 36.25 + (C.dir == D_W32 ? 4.0 : 0.0);
+        per = 4.0 * kc + 32.25 + (C.dir == D_W32 ? 4.0 : 0.0);
       else
         per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
       break;
-    case P_CG_B: per = sv * kc + (C.first_cg ? 8.0 + 4.0 * sv : 4.0 * sv) + 0.125; break;
+    case P_CG_B:
+      per = sv * kc + (C.first_cg ? (C.gp32 ? 4.0 : 8.0) + 4.0 * sv : 4.0 * sv) + 0.125;
+      break;
     case P_CG_A: per = 6.0 * sv; break;
     case P_CG_F: per = sv * kc + 8.0 * sv + 0.125; break;
     default: break;
@@ -1989,14 +1991,37 @@ struct Chunk {
   int x0, yc, z, rows;
 };
 
-// The chunk starting at 8-row strip u (tile u/4, strip u%4) of a group that
-// ends before strip u_hi.
-__device__ __forceinline__ Chunk make_chunk(const DevInst& I, int u, int u_hi, int ch) {
-  const int t = u >> 2, s = u & 3;
-  const int k = min(min(ch >> 3, 4 - s), max(u_hi - u, 1));
-  const int rest = t / I.tiles_x;
-  return Chunk{(t % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY + 8 * s, rest / I.tiles_y, 8 * k};
-}
+// Walks a group's strips [u, u_hi) in chunks: a chunk starts at the current
+// strip and takes up to ch/8 strips without leaving its tile or the group.
+// Tile coordinates are divided out once, at the group's first strip.
+struct Walk {
+  int u, u_hi, ch8, tx, ty, z, s;
+  __device__ Walk(const DevInst& I, int u0, int hi, int ch) : u(u0), u_hi(hi), ch8(ch >> 3) {
+    const int t = u0 >> 2, rest = t / I.tiles_x;
+    s = u0 & 3;
+    tx = t - rest * I.tiles_x;
+    ty = rest % I.tiles_y;
+    z = rest / I.tiles_y;
+  }
+  __device__ bool done() const { return u >= u_hi; }
+  __device__ Chunk take(const DevInst& I) {
+    const int k = min(min(ch8, 4 - s), u_hi - u);
+    const Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k};
+    u += k;
+    s += k;
+    if (s == 4) {
+      s = 0;
+      if (++tx == I.tiles_x) {
+        tx = 0;
+        if (++ty == I.tiles_y) {
+          ty = 0;
+          ++z;
+        }
+      }
+    }
+    return c;
+  }
+};
 
 // Issue a chunk of the item's pass into a stage.
 __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, bool gp,
@@ -2191,7 +2216,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ Ctl sC;
   __shared__ int s_cnt[3][kWarps];
   __shared__ double s_red[kNRed];
-  __shared__ int s_t, s_inst, s_last, s_skip;
+  __shared__ int s_t, s_inst, s_last;
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   static_assert(sizeof(Ctl) % 8 == 0 && sizeof(Ctl) / 8 <= kThreads, "control block copy");
@@ -2247,31 +2272,34 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     const int2 tr = __ldg(E.tiles + t);
     if (tr.x != s_inst || first) {
       // a new instance (or the first item, whose descriptor the prologue
-      // loaded): read the snapshot of its state
+      // loaded): read the snapshot of its state, the control block in one
+      // round trip (the finalizer's shared copy sC is free here)
       const bool fresh = tr.x != s_inst;
       __syncthreads();  // everyone compared against the old s_inst
-      if (tid == 0) s_skip = E.ctl[tr.x].pass == P_NONE;
+      if (tid < (int)(sizeof(Ctl) / 8))
+        reinterpret_cast<long long*>(&sC)[tid] =
+            __ldcg(reinterpret_cast<const long long*>(E.ctl + tr.x) + tid);
       __syncthreads();
+      const bool skip = sC.pass == P_NONE;
       // a finished instance's groups are skipped without loading its descriptor
-      if (fresh && !s_skip && tid < (int)(sizeof(DevInst) / 8))
+      if (fresh && !skip && tid < (int)(sizeof(DevInst) / 8))
         reinterpret_cast<long long*>(&sI)[tid] =
             __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
       if (tid == 0) {
-        const Ctl& C = E.ctl[tr.x];
-        sS.pass = C.pass;
-        sS.cur = C.cur;
-        sS.pcur = C.pcur;
-        sS.cg32 = C.cg32;
-        sS.first_cg = C.first_cg;
-        sS.dir = C.dir;
-        sS.gp32 = C.gp32;
-        sS.x32_live = C.x32_live;
-        sS.alpha = C.alpha;
-        sS.beta = C.beta;
+        sS.pass = sC.pass;
+        sS.cur = sC.cur;
+        sS.pcur = sC.pcur;
+        sS.cg32 = sC.cg32;
+        sS.first_cg = sC.first_cg;
+        sS.dir = sC.dir;
+        sS.gp32 = sC.gp32;
+        sS.x32_live = sC.x32_live;
+        sS.alpha = sC.alpha;
+        sS.beta = sC.beta;
         s_inst = tr.x;
       }
       __syncthreads();
-      if (fresh && !s_skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
+      if (fresh && !skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
     }
     const DevInst& I = sI;
     const Snap& S = sS;
@@ -2306,16 +2334,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       const int ch = chunk_rows(S, gp);
       const int rpw = ch / kWarps;
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
-      const int u_hi = (int)((grp + 1) * n_strips / I.n_groups);
-      const int u0 = (int)(grp * n_strips / I.n_groups);
+      Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
       // the current chunk and the next two (h1, h2: they exist)
-      Chunk c0 = make_chunk(I, u0, u_hi, ch);
-      int u1 = u0 + c0.rows / 8;
-      bool h1 = u1 < u_hi;
-      Chunk c1 = make_chunk(I, u1, u_hi, ch);
-      int u2 = u1 + c1.rows / 8;
-      bool h2 = h1 && u2 < u_hi;
-      Chunk c2 = make_chunk(I, u2, u_hi, ch);
+      Chunk c0 = wk.take(I);
+      const bool hh1 = !wk.done();
+      Chunk c1 = hh1 ? wk.take(I) : c0;
+      const bool hh2 = !wk.done();
+      Chunk c2 = hh2 ? wk.take(I) : c0;
+      bool h1 = hh1, h2 = hh2;
       auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
       auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
       if (tid == 0) {
@@ -2372,11 +2398,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         for (int k = 0; k < 4; ++k) fbits[k] = fbits_n[k];
         c0 = c1;
         c1 = c2;
-        u1 = u2;
         h1 = h2;
-        u2 = u1 + c1.rows / 8;
-        h2 = h1 && u2 < u_hi;
-        c2 = make_chunk(I, u2, u_hi, ch);
+        h2 = !wk.done();
+        if (h2) c2 = wk.take(I);
       }
     }
     // fixed-order group reduction: every thread's sums go to shared memory;
