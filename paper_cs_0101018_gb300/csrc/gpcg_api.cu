@@ -30,6 +30,11 @@ cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, do
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
 cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
                               unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s);
+cudaError_t launch_mspmv(const DevInst& I, bool f32, const unsigned* mask, void* y, double* part,
+                         unsigned* counter, double* result, int* err, cudaStream_t s);
+int ms_max_ctas();
+cudaError_t launch_mspmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
+                               unsigned* mask, void* pm, bool f32, cudaStream_t s);
 cudaError_t launch_unpad(const DevInst& I, const void* src, bool f32, double* dst,
                          cudaStream_t s);
 }  // namespace gpcg
@@ -161,6 +166,7 @@ struct gpcg_problem {
   size_t bytes64 = 0;
   void* arena32 = nullptr;
   size_t bytes32 = 0;
+  double* ms_buf = nullptr;  // standalone masked product: CTA partials, result, counter, flag
   DevInst inst{};
   Scratch sc;
   Ctl last{};
@@ -171,6 +177,7 @@ struct gpcg_problem {
     sc.release();
     cudaFree(arena64);
     cudaFree(arena32);
+    cudaFree(ms_buf);
   }
 };
 
@@ -856,6 +863,49 @@ static Ctl spmv_ctl(bool f32, int cur, int pcur) {
   return C;
 }
 
+// The standalone masked product runs its own kernel on 2-D instances whose
+// maps of the precision are valid (the generic engine pass otherwise).
+static bool lean_spmv(const gpcg_problem* p, bool f32) {
+  return p->dim == 2 && (f32 ? p->inst.tma32 : p->inst.tma64) != 0;
+}
+
+static gpcg_status ms_scratch(gpcg_problem* p, cudaStream_t s) {
+  if (p->ms_buf) return GPCG_OK;
+  const size_t n = (size_t)ms_max_ctas() + 8;
+  CK(cudaMalloc(&p->ms_buf, n * sizeof(double)));
+  CK(cudaMemsetAsync(p->ms_buf, 0, n * sizeof(double), s));
+  return GPCG_OK;
+}
+
+// One launch of the standalone kernel on the problem's p[0] (operand) and
+// Ap[1] (result) with free-set words `mask`.
+static gpcg_status ms_launch(gpcg_problem* p, bool f32, const unsigned* mask, cudaStream_t s) {
+  const size_t c = (size_t)ms_max_ctas();
+  double* part = p->ms_buf;
+  DevInst& I = p->inst;
+  void* y = f32 ? (void*)I.Ap32[1] : (void*)I.Ap64[1];
+  CK(launch_mspmv(I, f32, mask, y, part, (unsigned*)(part + c + 1), part + c, (int*)(part + c + 2),
+                  s));
+  return GPCG_OK;
+}
+
+static gpcg_status ms_check(gpcg_problem* p, cudaStream_t s, double* result) {
+  const size_t c = (size_t)ms_max_ctas();
+  double r = 0.0;
+  int err = 0;
+  CK(cudaMemcpyAsync(&r, p->ms_buf + c, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&err, (int*)(p->ms_buf + c + 2), sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err) {
+    // the CTAs that gave up never counted themselves: reset flag and counter
+    cudaMemsetAsync(p->ms_buf + c + 1, 0, 2 * sizeof(double), s);
+    cudaStreamSynchronize(s);
+    return fail(GPCG_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
+  }
+  if (result) *result = r;
+  return GPCG_OK;
+}
+
 extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask,
                                         const double* pv, double* y, double* pAp, int precision,
                                         void* cuda_stream) {
@@ -903,6 +953,30 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
       temps.push_back(dy);
     }
     DevInst& I = p->inst;
+    if (lean_spmv(p, f32)) {
+      void* pm = f32 ? (void*)I.p32[0] : (void*)I.p64[0];
+      double r = 0.0;
+      if ((st = ms_scratch(p, s)) != GPCG_OK) break;
+      if (launch_mspmv_setup(I, dm, dp, I.mask[0], pm, f32, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "spmv set-up launch");
+        break;
+      }
+      if ((st = ms_launch(p, f32, I.mask[0], s)) != GPCG_OK) break;
+      const void* yb = f32 ? (const void*)I.Ap32[1] : (const void*)I.Ap64[1];
+      if (launch_unpad(I, yb, f32, dy, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "unpad launch");
+        break;
+      }
+      if (!y_dev &&
+          cudaMemcpyAsync(y, dy, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "copy y");
+        break;
+      }
+      if ((st = ms_check(p, s, &r)) != GPCG_OK) break;
+      if (pAp) *pAp = r;
+      p->have = false;  // the solve's vectors were overwritten
+      break;
+    }
     // the standalone pass is a CG_B step at pcur = 0 with beta = 0: it reads
     // r[1] (p = -r) and writes p[1], Ap[1]
     void* r = f32 ? (void*)I.r32[1] : (void*)I.r64[1];
@@ -955,12 +1029,48 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
     std::vector<double> ones((size_t)p->n, 1.0);
     CK(cudaMemcpyAsync(dp, ones.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, s));
     DevInst& I = p->inst;
-    CK(launch_spmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.r32[1] : (void*)I.r64[1],
-                         f32 ? (void*)I.p32[0] : (void*)I.p64[0], f32, s));
+    if (lean_spmv(p, f32))
+      CK(launch_mspmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.p32[0] : (void*)I.p64[0], f32,
+                            s));
+    else
+      CK(launch_spmv_setup(I, dm, dp, I.mask[0], f32 ? (void*)I.r32[1] : (void*)I.r64[1],
+                           f32 ? (void*)I.p32[0] : (void*)I.p64[0], f32, s));
     CK(cudaStreamSynchronize(s));
     cudaFree(dm);
     cudaFree(dp);
     cur = 0;
+  }
+  if (lean_spmv(p, f32)) {
+    DevInst& I = p->inst;
+    const unsigned* mask = I.mask[cur];
+    if ((st = ms_scratch(p, s)) != GPCG_OK) return st;
+    if ((st = ms_launch(p, f32, mask, s)) != GPCG_OK) return st;  // untimed
+    const size_t flush_bytes = (size_t)256 << 20;
+    void* flush = nullptr;
+    if (flush_l2) CK(cudaMalloc(&flush, flush_bytes));
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    for (int k = 0; k < reps; ++k) {
+      if (flush) CK(cudaMemsetAsync(flush, k & 0xff, flush_bytes, s));
+      CK(cudaEventRecord(ev[2 * k], s));
+      if ((st = ms_launch(p, f32, mask, s)) != GPCG_OK) return st;
+      CK(cudaEventRecord(ev[2 * k + 1], s));
+    }
+    CK(cudaStreamSynchronize(s));
+    double total = 0.0;
+    for (int k = 0; k < reps; ++k) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+      total += ms;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (flush) cudaFree(flush);
+    if ((st = ms_check(p, s, nullptr)) != GPCG_OK) return st;
+    if (ms_per_launch) *ms_per_launch = total / reps;
+    // p and y, the bands and the mask words
+    const double sv = f32 ? 4.0 : 8.0;
+    if (bytes_per_launch) *bytes_per_launch = (double)p->n * (sv * p->kc + 2.0 * sv + 0.125);
+    return GPCG_OK;
   }
   // one untimed launch sets up the tables, then `reps` timed launches
   if ((st = one_pass(p, spmv_ctl(f32, cur, 0), s, nullptr)) != GPCG_OK) return st;

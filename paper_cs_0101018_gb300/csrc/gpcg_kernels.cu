@@ -2517,6 +2517,247 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   }
 }
 
+// -------------------------------------------- standalone masked product --
+//
+// y = Z Z' A Z Z' p and <p_F, y> (Eq. cg2) for one 2-D instance, the
+// operation of gpcg_masked_spmv: p (zero outside the free set) and the bands
+// stream through shared memory with TMA in 64 x c chunks (c = 16 rows FP32,
+// 8 FP64), four stages deep, three CTAs per SM; CTAs take chunks
+// round-robin.  Each CTA adds its terms in a fixed order; the last CTA to
+// finish adds the CTA partials in index order, so the sum does not depend on
+// the schedule.  Stage layout: P (64+2h) x (c+2) from (x0-h, y-1) | D 64 x c |
+// CX (64+h) x c from x0-h | CY 64 x (c+1) from y-1 -- the boxes of the fused
+// CG pass's maps (p[0]).
+constexpr int kMsStages = 4;
+template <class T>
+struct GeoMS {
+  using G = GeoF<T>;
+  static constexpr int H = G::H, CH = G::CH, BW = G::BW;
+  static constexpr int OFF_P = 0, OFF_D = G::SZ_H;
+  static constexpr int OFF_CX = OFF_D + 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX = ((CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+};
+constexpr int kMsStage = GeoMS<float>::END > GeoMS<double>::END ? GeoMS<float>::END : GeoMS<double>::END;
+constexpr int kMsSmem = kMsStages * kMsStage + 128 + 8 * kMsStages;
+
+struct MsArgs {
+  const void* tmaps;       // the instance's maps (CG_B boxes of p[0] and the bands)
+  const unsigned* mask;    // free-set bitmask
+  void* y;                 // output, padded layout
+  double* part;            // [gridDim.x] CTA partials
+  unsigned* counter;       // CTAs done (the last one resets it)
+  double* result;          // <p_F, y>
+  int* err;                // a bounded wait gave up
+  int nx, ny, px, mw, tiles_x, n_chunks;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
+  using G = GeoMS<T>;
+  constexpr int RPW = G::CH / kWarps;
+  extern __shared__ unsigned char dyn_smem[];
+  __shared__ double s_part[kWarps];
+  __shared__ int s_last;
+  unsigned char* st0 = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(st0 + kMsStages * kMsStage);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const char* maps = reinterpret_cast<const char*>(A.tmaps);
+  constexpr int mb = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
+  const void* mP = maps + 128 * (mb + (M32_FPH0 - M32_RH0));
+  const void* mD = maps + 128 * (mb + (M32_FD - M32_RH0));
+  const void* mX = maps + 128 * (mb + (M32_FCX - M32_RH0));
+  const void* mY = maps + 128 * (mb + (M32_FCY - M32_RH0));
+  if (tid == 0) {
+    for (int k = 0; k < kMsStages; ++k) mbar_init(smem_u32(&bars[k]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tmap_acquire(mP);
+    tmap_acquire(mD);
+    tmap_acquire(mX);
+    tmap_acquire(mY);
+  }
+  __syncthreads();
+  const int G0 = (int)gridDim.x;
+  const int my = (A.n_chunks - (int)blockIdx.x + G0 - 1) / G0;  // chunks of this CTA
+  auto coords = [&](int k, int& x0, int& yc) {
+    const int c = (int)blockIdx.x + k * G0;
+    const int cy = c / A.tiles_x;
+    x0 = (c - cy * A.tiles_x) * kTX;
+    yc = cy * G::CH;
+  };
+  auto issue = [&](int k) {
+    int x0, yc;
+    coords(k, x0, yc);
+    const unsigned st = smem_u32(st0 + (k % kMsStages) * kMsStage);
+    const unsigned bar = smem_u32(&bars[k % kMsStages]);
+    mbar_expect(bar, G::TX);
+    tma_load2d(st + G::OFF_P, mP, x0 - G::H, yc - 1, bar);
+    tma_load2d(st + G::OFF_D, mD, x0, yc, bar);
+    tma_load2d(st + G::OFF_CX, mX, x0 - G::H, yc, bar);
+    tma_load2d(st + G::OFF_CY, mY, x0, yc - 1, bar);
+  };
+  auto bits = [&](int k, unsigned fb[4]) {
+    int x0, yc;
+    coords(k, x0, yc);
+    const int e0 = min(x0 + 2 * lane, A.nx - 1) & ~1;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const int y = min(yc + warp * RPW + q, A.ny - 1);
+      fb[q] = __ldg(A.mask + (long long)y * A.mw + (e0 >> 5)) >> (e0 & 31);
+    }
+  };
+  if (tid == 0)
+    for (int k = 0; k < kMsStages - 1 && k < my; ++k) issue(k);
+  unsigned fb[4] = {0u, 0u, 0u, 0u}, fbn[4] = {0u, 0u, 0u, 0u};
+  if (my > 0) bits(0, fb);
+  T sum = T(0);  // this thread's terms of the current chunk
+  FF ffs{0.f, 0.f};
+  double dsum = 0.0;
+  T* y = reinterpret_cast<T*>(A.y);
+  for (int k = 0; k < my; ++k) {
+    if (tid == 0 && k + kMsStages - 1 < my) issue(k + kMsStages - 1);
+    if (k + 1 < my) bits(k + 1, fbn);
+    const unsigned char* st = st0 + (k % kMsStages) * kMsStage;
+    const bool ok = mbar_wait(smem_u32(&bars[k % kMsStages]), (k / kMsStages) & 1);
+    if (ok) {
+      int x0, yc;
+      coords(k, x0, yc);
+      const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+      const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+      const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+      const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+      const int c = 2 * lane, e0 = x0 + c;
+      const bool v0 = e0 < A.nx, v1 = e0 + 1 < A.nx;
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int ry = warp * RPW + q;
+        if (yc + ry >= A.ny || !v0) break;
+        const T* Pr = P + (ry + 1) * G::BW + G::H + c;
+        const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+        const T vc0 = Pr[0], vc1 = Pr[1];
+        // diag, west, east, south, north (the order of the register sweep)
+        T a0 = D[ry * 64 + c] * vc0;
+        a0 = fma(Xr[-1], Pr[-1], a0);
+        a0 = fma(Xr[0], vc1, a0);
+        a0 = fma(CY[ry * 64 + c], Pr[-G::BW], a0);
+        a0 = fma(CY[(ry + 1) * 64 + c], Pr[G::BW], a0);
+        T a1 = D[ry * 64 + c + 1] * vc1;
+        a1 = fma(Xr[0], vc0, a1);
+        a1 = fma(Xr[1], Pr[2], a1);
+        a1 = fma(CY[ry * 64 + c + 1], Pr[1 - G::BW], a1);
+        a1 = fma(CY[(ry + 1) * 64 + c + 1], Pr[G::BW + 1], a1);
+        a0 = (fb[q] & 1u) ? a0 : T(0);
+        a1 = (fb[q] & 2u) ? a1 : T(0);
+        st2(y, (long long)(yc + ry) * A.px + e0, v0, v1, a0, a1);
+        sum = fma(vc0, a0, fma(vc1, a1, sum));
+      }
+      if (sizeof(T) == 4) ff_acc(ffs, (float)sum);
+      else dsum += (double)sum;
+      sum = T(0);
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(A.err, 1);
+        for (int j = 1; j < kMsStages && k + j < my; ++j)
+          mbar_wait(smem_u32(&bars[(k + j) % kMsStages]), ((k + j) / kMsStages) & 1);
+      }
+      return;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) fb[q] = fbn[q];
+  }
+  // fixed-order CTA sum, then the last CTA adds the CTA partials in order
+  double v = sizeof(T) == 4 ? ff_val(ffs) : dsum;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+  if (lane == 0) s_part[warp] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s_part[w];
+    A.part[blockIdx.x] = t;
+    __threadfence();
+    s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid == 0) __threadfence();
+  __syncthreads();
+  double t = 0.0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(A.part + b);
+  if (warp == 0) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL_MASK, t, off);
+    if (lane == 0) {
+      *A.result = t;
+      *A.counter = 0u;
+    }
+  }
+}
+
+// Grid of the standalone masked product: the resident CTAs of the GPU, at
+// most one per chunk.
+static int ms_grid(int n_chunks) {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(mspmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMsSmem);
+    cudaFuncSetAttribute(mspmv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMsSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mspmv_kernel<float>, kThreads, kMsSmem);
+    cached = sms * (per > 0 ? per : 1);
+  }
+  return n_chunks < cached ? (n_chunks > 0 ? n_chunks : 1) : cached;
+}
+
+// Launch the standalone masked product of a 2-D instance whose CG maps are
+// valid, with free-set words `mask`; `part` holds at least ms_max_ctas()
+// doubles.
+cudaError_t launch_mspmv(const DevInst& I, bool f32, const unsigned* mask, void* y, double* part,
+                         unsigned* counter, double* result, int* err, cudaStream_t s) {
+  const int ch = f32 ? GeoMS<float>::CH : GeoMS<double>::CH;
+  MsArgs A{I.tmaps, mask, y, part, counter, result, err,
+           I.nx, I.ny, I.px, I.mw, I.tiles_x, I.tiles_x * ((I.ny + ch - 1) / ch)};
+  const int grid = ms_grid(A.n_chunks);
+  if (f32) mspmv_kernel<float><<<grid, kThreads, kMsSmem, s>>>(A);
+  else mspmv_kernel<double><<<grid, kThreads, kMsSmem, s>>>(A);
+  return cudaGetLastError();
+}
+
+int ms_max_ctas() { return ms_grid(1 << 30); }
+
+// p restricted to the free set into pm (padded layout) and the free-set words.
+template <class T>
+__global__ void mspmv_setup_kernel(DevInst I, const uint8_t* __restrict__ fm,
+                                   const double* __restrict__ pv, unsigned* mask, T* pm) {
+  const long long rows = (long long)I.ny * I.nz;
+  const long long total = rows * I.mw;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / I.mw;
+    const int wcol = (int)(t % I.mw);
+    const int iy = (int)(row % I.ny), iz = (int)(row / I.ny);
+    unsigned word = 0;
+    for (int b = 0; b < 32; ++b) {
+      const int ix = wcol * 32 + b;
+      if (ix >= I.px) break;
+      const long long i = pidx(I, iy, iz, ix);
+      T v = T(0);
+      if (ix < I.nx) {
+        const long long j = ((long long)iz * I.ny + iy) * I.nx + ix;
+        if (fm[j]) {
+          word |= 1u << b;
+          v = (T)pv[j];
+        }
+      }
+      pm[i] = v;
+    }
+    mask[t] = word;
+  }
+}
+
 // ------------------------------------------------------- set-up kernels --
 
 // Zero the couplings of the last point along each axis, fill missing bounds
@@ -2664,6 +2905,15 @@ cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double*
   else
     spmv_setup_kernel<double><<<grid_for(work), 256, 0, s>>>(I, fm, pv, mask, (double*)r,
                                                              (double*)pold);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mspmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
+                               unsigned* mask, void* pm, bool f32, cudaStream_t s) {
+  const long long words = (long long)I.ny * I.nz * I.mw;
+  const int grid = (int)std::min<long long>((words + 255) / 256, 4096);
+  if (f32) mspmv_setup_kernel<float><<<grid, 256, 0, s>>>(I, fm, pv, mask, (float*)pm);
+  else mspmv_setup_kernel<double><<<grid, 256, 0, s>>>(I, fm, pv, mask, (double*)pm);
   return cudaGetLastError();
 }
 
