@@ -140,6 +140,11 @@ typedef struct {
     int64_t launches;       /* kernel launches of the engine for the latest solve (passes
                                plus the empty launches of the final loop iteration); for a
                                batch, the launches of the whole batch */
+    int staged;             /* the shared-memory (TMA) staged paths available to the problem:
+                               1 free-set words, 2 FP64 CG passes, 4 FP32 CG passes,
+                               8 mixed-precision gradient-projection passes (2-D only; the
+                               other passes and 3-D problems use the register sweep) */
+    int reserved;
 } gpcg_stats;
 
 /* Copy the latest solution (n values, host or device x_out; NULL skips it)

@@ -7,7 +7,8 @@
 //   for FP32); point (ix, iy, iz) lives at ix + px*(iy + ny*iz).  Pad columns
 //   ix >= nx hold zeros and are never read as neighbours.
 //   The free set is a bitmask: bit (ix & 31) of word (iy + ny*iz)*mw + ix/32
-//   is 1 when the point is free, mw = ceil(px/32).
+//   is 1 when the point is free; mw = ceil(px/32) rounded up to a multiple of
+//   4 words, so that mask rows are 16-byte strides TMA can stage.
 //
 // One engine pass = one launch of the pass kernel over the tile table of all
 // live instances.  Each CTA processes one 64 x 32 tile of one instance, writes
@@ -39,7 +40,9 @@ constexpr int kMaxGroups = 304;
 // 64 columns by 8-32 rows, kStages stages deep (the next chunk is in flight
 // while one is computed).  Two CTAs of the pass kernel fit on one SM.
 constexpr int kStages = 2;
-constexpr int kStageBytes = 45056;   // one stage (the largest stage layout in the kernels)
+constexpr int kStageBytes = 45568;   // one stage: the largest layout (45056) + the mask box
+constexpr int kMaskBox = 512;        // 4 words x 32 rows, at the end of every stage
+constexpr int kOffMask = kStageBytes - kMaskBox;
 constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 
 // Tensor maps of an instance (one CUtensorMap, 128 bytes, each).  With c the
@@ -67,9 +70,10 @@ enum TMap : int {
   MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G18
   MG_PGH0, MG_PGH1,                                                  // G34
   MG_L32, MG_U32, MG_B32,                                            // 64 x 16
+  M_MASK0, M_MASK1,  // free-set words of mask[0], mask[1]: box 4 words x 32 rows
   M_COUNT
 };
-constexpr int kGpMaps = M_COUNT - MG_X32H0;
+constexpr int kGpMaps = M_MASK0 - MG_X32H0;  // the GP maps (make_gp_maps encodes them)
 constexpr int kCgMaps = M64_RH0 - M32_RH0;  // maps of one precision's CG passes
 
 enum Pass : int {
@@ -137,7 +141,7 @@ struct DevInst {
   double* part;            // [n_groups][kNRed] group partial sums of this instance
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
   int tma64, tma32;        // the FP64 / FP32 CG maps are valid
-  int tma_gp, pad_t;       // the mixed-phase GP maps are valid
+  int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   double *x[2], *g[2];

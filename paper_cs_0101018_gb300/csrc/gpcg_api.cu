@@ -30,7 +30,7 @@ cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, do
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
 cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
                               unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s);
-cudaError_t launch_mspmv(const DevInst& I, bool f32, const unsigned* mask, void* y, double* part,
+cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* part,
                          unsigned* counter, double* result, int* err, cudaStream_t s);
 int ms_max_ctas();
 cudaError_t launch_mspmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
@@ -187,7 +187,7 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
   p->ny = (int)ny;
   p->nz = (int)nz;
   p->px = (int)((nx + 7) / 8 * 8);
-  p->mw = (p->px + 31) / 32;
+  p->mw = ((p->px + 31) / 32 + 3) / 4 * 4;
   p->kc = dim == 3 ? 4 : 3;
   p->n = nx * ny * nz;
   p->plane = (long long)p->px * ny;
@@ -258,6 +258,7 @@ static void carve64(gpcg_problem* p) {
   I.tma64 = 0;
   I.tma32 = 0;
   I.tma_gp = 0;
+  I.tma_mask = 0;
   I.x0 = I.r64[0];  // a given start point is staged in r (unused until CG starts)
 }
 
@@ -357,6 +358,29 @@ static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
   return true;
 }
 
+// The free-set words as a 2-D u32 tensor (mw words x ny*nz rows), box 4 x 32.
+static bool make_mask_maps(gpcg_problem* p, cudaStream_t s) {
+  if (!have_encode()) return false;
+  DevInst& I = p->inst;
+  CUtensorMap m[2];
+  for (int k = 0; k < 2; ++k) {
+    cuuint64_t dims[2] = {(cuuint64_t)p->mw, (cuuint64_t)p->ny * (cuuint64_t)p->nz};
+    cuuint64_t strides[1] = {(cuuint64_t)p->mw * 4};
+    cuuint32_t box[2] = {4, 32};
+    cuuint32_t estr[2] = {1, 1};
+    if (g_encode(&m[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, I.mask[k], dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * M_MASK0;
+  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return true;
+}
+
 static bool tma_disabled() {
   const char* e = getenv("GPCG_NO_TMA");
   return e && *e && *e != '0';
@@ -404,8 +428,8 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.cx32 = x32;
   I.cy32 = y32;
   I.cz32 = z32;
-  I.tma32 = (!tma_disabled() && make_maps(p, true, s)) ? 1 : 0;
-  I.tma_gp = (!tma_disabled() && make_gp_maps(p, s)) ? 1 : 0;
+  I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
+  I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
 }
 
@@ -479,7 +503,8 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
     delete p;
     return st;
   }
-  p->inst.tma64 = (!tma_disabled() && make_maps(p, false, s)) ? 1 : 0;
+  p->inst.tma_mask = (!tma_disabled() && make_mask_maps(p, s)) ? 1 : 0;
+  p->inst.tma64 = (p->inst.tma_mask && make_maps(p, false, s)) ? 1 : 0;
   *out = p;
   return GPCG_OK;
 }
@@ -800,6 +825,9 @@ static void fill_stats(const gpcg_problem* p, gpcg_stats* s) {
   s->err_bound = p->lambda_min > 0.0 ? s->pg_norm / p->lambda_min : -1.0;
   s->alg_bytes = C.alg_bytes;
   s->launches = p->launches;
+  const DevInst& I = p->inst;
+  s->staged = (I.tma_mask ? 1 : 0) | (I.tma64 ? 2 : 0) | (I.tma32 ? 4 : 0) | (I.tma_gp ? 8 : 0);
+  s->reserved = 0;
 }
 
 extern "C" gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats) {
@@ -866,7 +894,7 @@ static Ctl spmv_ctl(bool f32, int cur, int pcur) {
 // The standalone masked product runs its own kernel on 2-D instances whose
 // maps of the precision are valid (the generic engine pass otherwise).
 static bool lean_spmv(const gpcg_problem* p, bool f32) {
-  return p->dim == 2 && (f32 ? p->inst.tma32 : p->inst.tma64) != 0;
+  return p->dim == 2 && p->inst.tma_mask && (f32 ? p->inst.tma32 : p->inst.tma64) != 0;
 }
 
 static gpcg_status ms_scratch(gpcg_problem* p, cudaStream_t s) {
@@ -879,7 +907,7 @@ static gpcg_status ms_scratch(gpcg_problem* p, cudaStream_t s) {
 
 // One launch of the standalone kernel on the problem's p[0] (operand) and
 // Ap[1] (result) with free-set words `mask`.
-static gpcg_status ms_launch(gpcg_problem* p, bool f32, const unsigned* mask, cudaStream_t s) {
+static gpcg_status ms_launch(gpcg_problem* p, bool f32, int mask, cudaStream_t s) {
   const size_t c = (size_t)ms_max_ctas();
   double* part = p->ms_buf;
   DevInst& I = p->inst;
@@ -961,7 +989,7 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
         st = fail(GPCG_ERR_CUDA, "spmv set-up launch");
         break;
       }
-      if ((st = ms_launch(p, f32, I.mask[0], s)) != GPCG_OK) break;
+      if ((st = ms_launch(p, f32, 0, s)) != GPCG_OK) break;
       const void* yb = f32 ? (const void*)I.Ap32[1] : (const void*)I.Ap64[1];
       if (launch_unpad(I, yb, f32, dy, s) != cudaSuccess) {
         st = fail(GPCG_ERR_CUDA, "unpad launch");
@@ -1042,7 +1070,8 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
   }
   if (lean_spmv(p, f32)) {
     DevInst& I = p->inst;
-    const unsigned* mask = I.mask[cur];
+    const int mask = cur;
+    (void)I;
     if ((st = ms_scratch(p, s)) != GPCG_OK) return st;
     if ((st = ms_launch(p, f32, mask, s)) != GPCG_OK) return st;  // untimed
     const size_t flush_bytes = (size_t)256 << 20;

@@ -142,6 +142,12 @@ __device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
                : "memory");
 }
 
+// Add `bytes` to the transaction count of the barrier's current phase
+// without arriving (for copies issued beside an arrive.expect_tx).
+__device__ __forceinline__ void mbar_expect_only(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 // Wait for phase `parity` of the barrier; gives up after a bounded number of
 // polls (returns false) so that a lost copy can never hang the GPU.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
@@ -1289,10 +1295,10 @@ struct ChunkGeo {
   static constexpr unsigned TX_A = 4 * SZ_A;
   static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;  // first map of the precision
 };
-static_assert(ChunkGeo<float>::END_B <= kStageBytes && ChunkGeo<double>::END_B <= kStageBytes,
+static_assert(ChunkGeo<float>::END_B <= kOffMask && ChunkGeo<double>::END_B <= kOffMask,
               "stage layout");
-static_assert(4 * ChunkGeo<float>::SZ_A <= kStageBytes &&
-                  4 * ChunkGeo<double>::SZ_A <= kStageBytes,
+static_assert(4 * ChunkGeo<float>::SZ_A <= kOffMask &&
+                  4 * ChunkGeo<double>::SZ_A <= kOffMask,
               "stage layout");
 
 __device__ __forceinline__ const void* tmap(const DevInst& I, int k) {
@@ -1385,22 +1391,6 @@ __device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, i
   }
 }
 
-// The free bits of this lane's two points in each of its rows of a chunk,
-// loaded before the chunk's data arrive.
-template <int RPW>
-__device__ __forceinline__ void load_chunk_bits(const DevInst& I, const unsigned* __restrict__ m,
-                                                int x0, int yc, unsigned fbits[4]) {
-  // the loads are unconditional (rows past the grid read the last row and
-  // are never used) so that nothing waits for them before the chunk's data
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e0 = min(x0 + 2 * lane, I.nx - 1) & ~1;
-#pragma unroll
-  for (int k = 0; k < RPW; ++k) {
-    const int y = min(yc + warp * RPW + k, I.ny - 1);
-    fbits[k] = __ldg(m + row_index(I, y, 0) * I.mw + (e0 >> 5)) >> (e0 & 31);
-  }
-}
-
 // P_CG_A on one staged chunk: w += alpha p, r' = r + alpha Ap (into `r`, the
 // other buffer), ||r'||^2.  `row` is the chunk's first row in the (ny*nz) row
 // space, `ylim` the number of rows of the chunk that lie inside the plane.
@@ -1466,7 +1456,7 @@ struct GeoF {
       (3 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
   static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
 };
-static_assert(GeoF<float>::END <= kStageBytes && GeoF<double>::END <= kStageBytes,
+static_assert(GeoF<float>::END <= kOffMask && GeoF<double>::END <= kOffMask,
               "stage layout");
 
 template <class T>
@@ -1701,12 +1691,12 @@ struct GeoGP {
   static constexpr unsigned TX_H = (CH + 2) * BW * 4;  // one halo box
   static constexpr unsigned TX_BANDS = SZ_32 + SZ_32 + (64 + H) * CH * 4 + 64 * (CH + 1) * 4;
 };
-static_assert(GeoGP::END <= kStageBytes, "stage layout");
+static_assert(GeoGP::END <= kOffMask, "stage layout");
 static_assert(GeoGP::CH == GeoF<float>::CH, "the GP passes use the fused pass's band maps");
 
 // Whether the item's pass is a mixed-phase GP pass on the TMA path.
 __device__ __forceinline__ bool gp_tma(const DevInst& I, const Snap& S) {
-  return S.gp32 && I.dim == 2 && I.tma_gp && I.tma32 &&
+  return S.gp32 && I.dim == 2 && I.tma_gp && I.tma32 && I.tma_mask &&
          (S.pass == P_CENSUS || S.pass == P_GP_ALPHA || S.pass == P_TRIAL);
 }
 
@@ -1839,22 +1829,6 @@ __device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned c
   ff_acc(ff[1], s_gag);
 }
 
-// This lane's bits of the current free set for each of its rows of a staged
-// GP chunk (bit h: column lane + 32h), loaded ahead of the chunk's data.
-__device__ __forceinline__ void load_gp_bits(const DevInst& I, const unsigned* __restrict__ m,
-                                             int x0, int yc, unsigned fbits[4]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wc = x0 >> 5;
-#pragma unroll
-  for (int k = 0; k < GeoGP::RPW; ++k) {
-    const int y = min(yc + warp * GeoGP::RPW + k, I.ny - 1);
-    const unsigned* p = m + (long long)y * I.mw + wc;
-    const unsigned w0 = __ldg(p);
-    const unsigned w1 = wc + 1 < I.mw ? __ldg(p + 1) : 0u;
-    fbits[k] = ((w0 >> lane) & 1u) | (((w1 >> lane) & 1u) << 1);
-  }
-}
-
 // P_TRIAL (mixed) on one staged 16-row chunk (as OpTrial32): each warp forms
 // xt32 = P[x32 + alpha d] on the FP32 box for its rows and the rows above and
 // below (west and east neighbours by shuffles), then g32t = A32 xt32 + b32,
@@ -1963,6 +1937,7 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
   if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
   if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
+  if (!I.tma_mask) return false;
   const int ok = S.cg32 ? I.tma32 : I.tma64;
   if (!ok) return false;
   if (S.pass == P_CG_A) return true;
@@ -1975,14 +1950,6 @@ __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
   if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
-}
-
-// The free bits (rows per warp rpw) of the chunk at (x0, yc).
-__device__ __forceinline__ void load_bits(const DevInst& I, const unsigned* __restrict__ m, int rpw,
-                                          int x0, int yc, unsigned fbits[4]) {
-  if (rpw == 4) load_chunk_bits<4>(I, m, x0, yc, fbits);
-  else if (rpw == 2) load_chunk_bits<2>(I, m, x0, yc, fbits);
-  else load_chunk_bits<1>(I, m, x0, yc, fbits);
 }
 
 // A chunk of a TMA pass: rows yc .. yc+rows-1 (rows a multiple of 8, at most
@@ -2023,9 +1990,36 @@ struct Walk {
   }
 };
 
-// Issue a chunk of the item's pass into a stage.
+// The free-set bits of this lane for each of its rows of a chunk, read from
+// the staged mask box (4 words x 32 rows from word (x0/32) rounded down to a
+// multiple of 4).  `gp`: bit h is column lane+32h (the GP passes); otherwise
+// bits 0 and 1 are columns 2*lane and 2*lane+1.
+__device__ __forceinline__ void stage_bits(const unsigned char* st, int x0, int rpw, bool gp,
+                                           unsigned fbits[4]) {
+  const unsigned* M = reinterpret_cast<const unsigned*>(st + kOffMask);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int off = (x0 >> 5) & 3;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= rpw) break;
+    const unsigned* row = M + (warp * rpw + k) * 4 + off;
+    if (gp) {
+      fbits[k] = ((row[0] >> lane) & 1u) | (((row[1] >> lane) & 1u) << 1);
+    } else {
+      fbits[k] = row[lane >> 4] >> ((2 * lane) & 31);
+    }
+  }
+}
+
+// Issue a chunk of the item's pass into a stage; `mask`: also the chunk's
+// free-set words of mask[S.cur].
 __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, bool gp,
-                                            const Chunk& c, unsigned st, unsigned bar) {
+                                            const Chunk& c, unsigned st, unsigned bar,
+                                            bool mask) {
+  if (mask) {
+    mbar_expect_only(bar, kMaskBox);
+    tma_load2d(st + kOffMask, tmap(I, M_MASK0 + S.cur), (c.x0 >> 5) & ~3, c.z * I.ny + c.yc, bar);
+  }
   if (gp) {
     issue_gp(I, S, c.x0, c.yc, st, bar);
   } else if (S.pass == P_CG_F) {
@@ -2347,29 +2341,24 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       if (tid == 0) {
         // order earlier generic writes to the stages before the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_chunk(I, S, gp, c0, smem_u32(stage(seq)), bar(seq));
-        if (kDepth == 2 && h1) issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1));
+        issue_chunk(I, S, gp, c0, smem_u32(stage(seq)), bar(seq), want_bits);
+        if (kDepth == 2 && h1)
+          issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
       }
-      unsigned fbits[4] = {0u, 0u, 0u, 0u}, fbits_n[4] = {0u, 0u, 0u, 0u};
-      if (want_bits) {
-        if (gp) load_gp_bits(I, I.mask[S.cur], c0.x0, c0.yc, fbits);
-        else load_bits(I, I.mask[S.cur], rpw, c0.x0, c0.yc, fbits);
-      }
+      unsigned fbits[4] = {0u, 0u, 0u, 0u};
       for (;;) {
         if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
           if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (kDepth == 2) issue_chunk(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2));
-          else issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1));
-        }
-        // the next chunk's free bits, loaded while this chunk's data arrive
-        if (want_bits && h1) {
-          if (gp) load_gp_bits(I, I.mask[S.cur], c1.x0, c1.yc, fbits_n);
-          else load_bits(I, I.mask[S.cur], rpw, c1.x0, c1.yc, fbits_n);
+          if (kDepth == 2)
+            issue_chunk(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2), want_bits);
+          else
+            issue_chunk(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
         }
         unsigned char* st = stage(seq);
         const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
         bool failed;
+        if (ok && want_bits) stage_bits(st, c0.x0, rpw, gp, fbits);
         if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp) {
           // the chunk has a barrier inside: agree on the wait first
           failed = __syncthreads_or(!ok);
@@ -2394,8 +2383,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         }
         seq++;
         if (!h1) break;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) fbits[k] = fbits_n[k];
         c0 = c1;
         c1 = c2;
         h1 = h2;
@@ -2536,15 +2523,17 @@ struct GeoMS {
   static constexpr int OFF_P = 0, OFF_D = G::SZ_H;
   static constexpr int OFF_CX = OFF_D + 64 * CH * (int)sizeof(T);
   static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
-  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
-  static constexpr unsigned TX = ((CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int OFF_M = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));  // mask box
+  static constexpr int END = OFF_M + kMaskBox;
+  static constexpr unsigned TX =
+      ((CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T) + kMaskBox;
 };
 constexpr int kMsStage = GeoMS<float>::END > GeoMS<double>::END ? GeoMS<float>::END : GeoMS<double>::END;
 constexpr int kMsSmem = kMsStages * kMsStage + 128 + 8 * kMsStages;
 
 struct MsArgs {
   const void* tmaps;       // the instance's maps (CG_B boxes of p[0] and the bands)
-  const unsigned* mask;    // free-set bitmask
+  int mask;                // free-set words: mask[0] or mask[1] (map M_MASK0 + mask)
   void* y;                 // output, padded layout
   double* part;            // [gridDim.x] CTA partials
   unsigned* counter;       // CTAs done (the last one resets it)
@@ -2569,6 +2558,7 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
   const void* mD = maps + 128 * (mb + (M32_FD - M32_RH0));
   const void* mX = maps + 128 * (mb + (M32_FCX - M32_RH0));
   const void* mY = maps + 128 * (mb + (M32_FCY - M32_RH0));
+  const void* mM = maps + 128 * (M_MASK0 + A.mask);
   if (tid == 0) {
     for (int k = 0; k < kMsStages; ++k) mbar_init(smem_u32(&bars[k]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -2576,6 +2566,7 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
     tmap_acquire(mD);
     tmap_acquire(mX);
     tmap_acquire(mY);
+    tmap_acquire(mM);
   }
   __syncthreads();
   const int G0 = (int)gridDim.x;
@@ -2596,28 +2587,16 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
     tma_load2d(st + G::OFF_D, mD, x0, yc, bar);
     tma_load2d(st + G::OFF_CX, mX, x0 - G::H, yc, bar);
     tma_load2d(st + G::OFF_CY, mY, x0, yc - 1, bar);
-  };
-  auto bits = [&](int k, unsigned fb[4]) {
-    int x0, yc;
-    coords(k, x0, yc);
-    const int e0 = min(x0 + 2 * lane, A.nx - 1) & ~1;
-#pragma unroll
-    for (int q = 0; q < RPW; ++q) {
-      const int y = min(yc + warp * RPW + q, A.ny - 1);
-      fb[q] = __ldg(A.mask + (long long)y * A.mw + (e0 >> 5)) >> (e0 & 31);
-    }
+    tma_load2d(st + G::OFF_M, mM, (x0 >> 5) & ~3, yc, bar);
   };
   if (tid == 0)
     for (int k = 0; k < kMsStages - 1 && k < my; ++k) issue(k);
-  unsigned fb[4] = {0u, 0u, 0u, 0u}, fbn[4] = {0u, 0u, 0u, 0u};
-  if (my > 0) bits(0, fb);
   T sum = T(0);  // this thread's terms of the current chunk
   FF ffs{0.f, 0.f};
   double dsum = 0.0;
   T* y = reinterpret_cast<T*>(A.y);
   for (int k = 0; k < my; ++k) {
     if (tid == 0 && k + kMsStages - 1 < my) issue(k + kMsStages - 1);
-    if (k + 1 < my) bits(k + 1, fbn);
     const unsigned char* st = st0 + (k % kMsStages) * kMsStage;
     const bool ok = mbar_wait(smem_u32(&bars[k % kMsStages]), (k / kMsStages) & 1);
     if (ok) {
@@ -2629,6 +2608,10 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
       const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
       const int c = 2 * lane, e0 = x0 + c;
       const bool v0 = e0 < A.nx, v1 = e0 + 1 < A.nx;
+      const unsigned* M = reinterpret_cast<const unsigned*>(st + G::OFF_M) + ((x0 >> 5) & 3);
+      unsigned fb[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) fb[q] = M[(warp * RPW + q) * 4 + (lane >> 4)] >> (c & 31);
 #pragma unroll
       for (int q = 0; q < RPW; ++q) {
         const int ry = warp * RPW + q;
@@ -2664,8 +2647,6 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
       }
       return;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) fb[q] = fbn[q];
   }
   // fixed-order CTA sum, then the last CTA adds the CTA partials in order
   double v = sizeof(T) == 4 ? ff_val(ffs) : dsum;
@@ -2713,9 +2694,9 @@ static int ms_grid(int n_chunks) {
 }
 
 // Launch the standalone masked product of a 2-D instance whose CG maps are
-// valid, with free-set words `mask`; `part` holds at least ms_max_ctas()
+// valid, with free-set words mask[mask]; `part` holds at least ms_max_ctas()
 // doubles.
-cudaError_t launch_mspmv(const DevInst& I, bool f32, const unsigned* mask, void* y, double* part,
+cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* part,
                          unsigned* counter, double* result, int* err, cudaStream_t s) {
   const int ch = f32 ? GeoMS<float>::CH : GeoMS<double>::CH;
   MsArgs A{I.tmaps, mask, y, part, counter, result, err,

@@ -51,7 +51,8 @@ class gpcg_stats(C.Structure):
                 ("n_free", C.c_int64), ("outer_iters", C.c_int), ("gp_iters", C.c_int),
                 ("cg_iters", C.c_int), ("ls_trials", C.c_int), ("refine_cg_iters", C.c_int),
                 ("passes", C.c_int), ("status", C.c_int), ("err_bound", C.c_double),
-                ("alg_bytes", C.c_double), ("launches", C.c_int64)]
+                ("alg_bytes", C.c_double), ("launches", C.c_int64), ("staged", C.c_int),
+                ("reserved", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -194,6 +194,20 @@ def test_mixed_staged_and_register_paths(monkeypatch, shape, bounds):
         assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
 
+def test_staged_paths_enabled(monkeypatch):
+    """The TMA-staged paths are in use where they apply (a silent fall-back to
+    the register sweep would still pass parity, only slower)."""
+    monkeypatch.delenv("GPCG_NO_TMA", raising=False)
+    qp2 = gi.grid_qp_2d(100, 70, seed=650, shift=0.02, bounds="two_sided")
+    qp3 = gi.grid_qp_3d(17, 9, 6, seed=651, shift=0.02, bounds="box1")
+    for qp, want in ((qp2, 15), (qp3, 7)):
+        status, x, st = _solve(qp, tau_rel=1e-8, precision=g.MIXED)
+        assert status == 0 and st["staged"] == want, (qp.dim, st["staged"])
+    monkeypatch.setenv("GPCG_NO_TMA", "1")
+    status, x, st = _solve(qp2, tau_rel=1e-8, precision=g.MIXED)
+    assert status == 0 and st["staged"] == 0
+
+
 def test_x0_and_device_arrays():
     import torch
     qp = gi.grid_qp_2d(48, 40, seed=620, shift=0.02, bounds="box1")
