@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("tau_abs", C.c_double), ("tau_rel", C.c_double), ("eta1", C.c_double),
                 ("eta2", C.c_double), ("mu", C.c_double), ("eta2_shrink", C.c_double),
                 ("eta2_floor", C.c_double), ("max_outer", C.c_int), ("max_gp", C.c_int),
-                ("max_cg", C.c_int), ("max_ls", C.c_int)]
+                ("max_cg", C.c_int), ("max_ls", C.c_int), ("precond", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -96,7 +96,7 @@ def lib():
                                   C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl),
                                   C.POINTER(ci)]
         L.ora_gp_step.restype = ci
-        L.ora_reduced_cg.argtypes = [C.POINTER(_Stencil), vp, vp, dbl, ci, vp,
+        L.ora_reduced_cg.argtypes = [C.POINTER(_Stencil), vp, vp, dbl, ci, ci, vp,
                                      C.POINTER(ci), C.POINTER(ci), vp, i64, C.POINTER(i64)]
         L.ora_reduced_cg.restype = ci
         L.ora_projected_search.argtypes = [C.POINTER(_Stencil), vp, vp, vp, dbl, ci, vp, vp,
@@ -207,15 +207,21 @@ def gp_step(qp, y, g, mu=0.01, max_ls=60):
     return s, y, g, a0.value, a.value, dec.value, tr.value
 
 
-def reduced_cg(qp, free_mask, g, eta2, max_cg, trace_cap=100000):
-    """CG on the reduced system from w0 = 0; returns (status, w, iters, reason, events)."""
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+
+
+def reduced_cg(qp, free_mask, g, eta2, max_cg, trace_cap=100000, precond=PRECOND_NONE):
+    """(Preconditioned) CG on the reduced system from w0 = 0; returns (status, w,
+    iters, reason, events); event c is <r_j, z_j> (= ||r_j||^2 without a
+    preconditioner)."""
     st = Stencil(qp)
     fm = np.ascontiguousarray(free_mask, dtype=np.uint8)
     g = _f64(g)
     w = np.zeros_like(g)
     it, rs, ln = C.c_int(), C.c_int(), C.c_int64()
     ev = (Event * trace_cap)()
-    s = lib().ora_reduced_cg(st.ref, _ptr(fm), _ptr(g), eta2, max_cg, _ptr(w), C.byref(it),
+    s = lib().ora_reduced_cg(st.ref, _ptr(fm), _ptr(g), eta2, max_cg, precond, _ptr(w),
+                             C.byref(it),
                              C.byref(rs), C.cast(ev, C.c_void_p), trace_cap, C.byref(ln))
     return s, w, it.value, rs.value, _events(ev, ln.value, trace_cap)
 

@@ -307,22 +307,43 @@ done:
  * with Delta_j <= eta2 * max_{l<j} Delta_l (cgstop1), when r vanishes, or at
  * max_cg; the step of the stopping iteration is kept, so w = w_{j_k}.
  * Returns ORA_OK or ORA_ERR_NUMERIC (<p, A_k p> <= 0). */
+/* z = M^{-1} r on the free set: the identity, or the diagonal of the reduced
+ * Hessian A_k (point Jacobi, Sec. 6). */
+static void precondition(const ora_stencil* A, const uint8_t* free_mask, int precond,
+                         const double* r, double* z)
+{
+    const int64_t n = ora_n(A);
+    for (int64_t i = 0; i < n; i++) {
+        if (!free_mask[i]) z[i] = 0.0;
+        else if (precond == ORA_PRECOND_JACOBI) z[i] = r[i] / A->diag[i];
+        else z[i] = r[i];
+    }
+}
+
+/* Preconditioned conjugate gradients on subproblem (cg2) from w_0 = 0, in
+ * the textbook recurrences with rho_j = <r_j, z_j>, z_j = M^{-1} r_j:
+ * alpha_j = rho_j / <p_j, A_k p_j>, w += alpha p, r += alpha A_k p,
+ * beta = rho_{j+1} / rho_j, p = -z + beta p.  The decrease of q_k in step j
+ * is alpha_j rho_j - alpha_j^2 <p_j, A_k p_j> / 2 = alpha_j rho_j / 2, which
+ * feeds the test (cgstop1).  With M = I this is plain CG. */
 static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const double* g,
-                      double eta2, int max_cg, double* w, int* iters, int* reason,
-                      trace_t* tr, int outer)
+                      double eta2, int max_cg, int precond, double* w, int* iters,
+                      int* reason, trace_t* tr, int outer)
 {
     const int64_t n = ora_n(A);
     const size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
     double* r = (double*)malloc(bytes);
+    double* z = (double*)malloc(bytes);
     double* p = (double*)malloc(bytes);
     double* Ap = (double*)malloc(bytes);
     int status = ORA_OK;
     for (int64_t i = 0; i < n; i++) {
         r[i] = free_mask[i] ? g[i] : 0.0;
-        p[i] = -r[i];
         w[i] = 0.0;
     }
-    double rr = dot(n, r, r);
+    precondition(A, free_mask, precond, r, z);
+    for (int64_t i = 0; i < n; i++) p[i] = -z[i];
+    double rr = dot(n, r, z);
     double dmax = 0.0;
     *iters = 0;
     *reason = ORA_CG_EMPTY;
@@ -339,7 +360,8 @@ static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const doub
             r[i] += alpha * Ap[i];
         }
         const double delta = 0.5 * alpha * rr;
-        const double rr_new = dot(n, r, r);
+        precondition(A, free_mask, precond, r, z);
+        const double rr_new = dot(n, r, z);
         *iters = j;
         if (tr) emit(tr, ORA_EV_CG_ITER, outer, j, 0, alpha, delta, rr_new, pAp);
         if (j >= 2 && delta <= eta2 * dmax) {
@@ -356,21 +378,22 @@ static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const doub
         }
         if (delta > dmax) dmax = delta;
         const double beta = rr_new / rr;
-        for (int64_t i = 0; i < n; i++) p[i] = -r[i] + beta * p[i];
+        for (int64_t i = 0; i < n; i++) p[i] = -z[i] + beta * p[i];
         rr = rr_new;
     }
     free(r);
+    free(z);
     free(p);
     free(Ap);
     return status;
 }
 
 int ora_reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const double* g,
-                   double eta2, int max_cg, double* w, int* iters, int* reason,
+                   double eta2, int max_cg, int precond, double* w, int* iters, int* reason,
                    ora_event* events, int64_t event_cap, int64_t* event_len)
 {
     trace_t tr = {events, event_cap, 0};
-    const int s = reduced_cg(A, free_mask, g, eta2, max_cg, w, iters, reason, &tr, 0);
+    const int s = reduced_cg(A, free_mask, g, eta2, max_cg, precond, w, iters, reason, &tr, 0);
     if (event_len) *event_len = tr.len;
     return s;
 }
@@ -420,6 +443,7 @@ void ora_default_options(ora_options* o)
     o->max_gp = 50;
     o->max_cg = 10000;
     o->max_ls = 60;
+    o->precond = ORA_PRECOND_NONE;
 }
 
 /* Algorithm GPCG (Sec. 3): gradient projection until (pgstop1) or (pgstop2),
@@ -504,7 +528,8 @@ int ora_gpcg(const ora_stencil* A, const double* b, double c, const double* l,
         /* conjugate gradient phase on the face of x_k */
         for (int64_t i = 0; i < n; i++) fr[i] = (uint8_t)!act[i];
         int iters = 0, reason = 0;
-        int s = reduced_cg(A, fr, g, eta2, opt->max_cg, w, &iters, &reason, &tr, k);
+        int s = reduced_cg(A, fr, g, eta2, opt->max_cg, opt->precond, w, &iters, &reason, &tr,
+                           k);
         st->cg_iters += iters;
         emit(&tr, ORA_EV_CG_END, k, iters, 0, reason, eta2, 0.0, 0.0);
         if (s != ORA_OK) {

@@ -32,7 +32,7 @@ enum {
     ORA_EV_START = 1,   /* a = q(x0), b = ||pg(x0)||, c = tau */
     ORA_EV_GP_STEP = 2, /* inner = j, trials, a = alpha, b = q(y_{j-1}) - q(y_j), c = same face, d = ||pg|| */
     ORA_EV_GP_END = 3,  /* inner = j, a = reason, b = alpha0 of the last step */
-    ORA_EV_CG_ITER = 4, /* inner = j, a = alpha, b = Delta_j, c = ||r_j||^2, d = <p, A p> */
+    ORA_EV_CG_ITER = 4, /* inner = j, a = alpha, b = Delta_j, c = <r_j, z_j>, d = <p, A p> */
     ORA_EV_CG_END = 5,  /* inner = iterations, a = reason, b = eta2 in force */
     ORA_EV_SEARCH = 6,  /* trials, a = alpha, b = q(x_{k+1}) - q(x_k), c = ||pg||, d = (B == A) */
     ORA_EV_DONE = 7     /* outer = iterations, a = status, b = ||pg||, c = q */
@@ -47,10 +47,14 @@ typedef struct {
     const double* cz;     /* A(i,i+nx*ny), dim == 3 only */
 } ora_stencil;
 
+/* Preconditioners of the reduced CG (Sec. 6 compares them). */
+enum { ORA_PRECOND_NONE = 0, ORA_PRECOND_JACOBI = 1 /* M = diag(A_k) */ };
+
 typedef struct {
     double tau_abs, tau_rel;
     double eta1, eta2, mu, eta2_shrink, eta2_floor;
     int max_outer, max_gp, max_cg, max_ls;
+    int precond;          /* ORA_PRECOND_* */
 } ora_options;
 
 typedef struct {
@@ -85,7 +89,7 @@ int ora_gp_step(const ora_stencil* A, const double* b, const double* l, const do
                 double mu, int max_ls, double* y, double* g, double* alpha0,
                 double* alpha, double* decrease, int* trials);
 int ora_reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const double* g,
-                   double eta2, int max_cg, double* w, int* iters, int* reason,
+                   double eta2, int max_cg, int precond, double* w, int* iters, int* reason,
                    ora_event* events, int64_t event_cap, int64_t* event_len);
 int ora_projected_search(const ora_stencil* A, const double* b, const double* l,
                          const double* u, double mu, int max_ls, const double* d,

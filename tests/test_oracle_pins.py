@@ -233,6 +233,98 @@ def test_reduced_cg_exact_solve_and_closed_form_decrease():
     assert all(e["d"] > 0 for e in ev if e["kind"] == oracle.EV_CG_ITER)
 
 
+def _scaled_qp(qp):
+    """The symmetrically scaled problem D^-1/2 A D^-1/2 (unit diagonal), built
+    band by band: the couplings of points i and j divide by sqrt(d_i d_j)."""
+    d = np.sqrt(qp.diag).reshape(qp.nz, qp.ny, qp.nx)
+    cx = qp.cx.reshape(d.shape).copy()
+    cy = qp.cy.reshape(d.shape).copy()
+    cx[:, :, :-1] /= d[:, :, :-1] * d[:, :, 1:]
+    cy[:, :-1, :] /= d[:, :-1, :] * d[:, 1:, :]
+    return gi.QP(qp.dim, qp.nx, qp.ny, qp.nz, np.ones(qp.n), cx.ravel(), cy.ravel(), None,
+                 qp.b, qp.l, qp.u)
+
+
+def test_pcg_jacobi_exact_solve_and_closed_form_decrease():
+    """Point-Jacobi PCG (Sec. 6) with eta2 = 0 reaches the solution of
+    A_FF w = -g_F, and its closed-form decreases alpha_j rho_j / 2 telescope to
+    q_k(0) - q_k(w)."""
+    qp = gi.grid_qp_2d(9, 8, seed=56, shift=0.05, sigma=1.0)
+    A = bf.dense_matrix(qp)
+    free = gi.uniform(56, 2, qp.n) < 0.7
+    g = gi.normal(56, 3, qp.n)
+    s, w, iters, reason, ev = oracle.reduced_cg(qp, free, g, eta2=0.0, max_cg=4 * qp.n,
+                                                precond=oracle.PRECOND_JACOBI)
+    assert s == oracle.OK
+    F = np.flatnonzero(free)
+    AF = A[np.ix_(F, F)]
+    wF = np.linalg.solve(AF, -g[F])
+    assert np.allclose(w[F], wF, rtol=1e-9, atol=1e-10)
+    assert np.all(w[~free] == 0)
+    qk = 0.5 * w[F] @ AF @ w[F] + g[F] @ w[F]
+    deltas = [e["b"] for e in ev if e["kind"] == oracle.EV_CG_ITER]
+    assert math.isclose(sum(deltas), -qk, rel_tol=1e-10)
+
+
+def test_pcg_jacobi_is_cg_on_the_scaled_system():
+    """Jacobi PCG on A equals plain CG on D^-1/2 A D^-1/2 in the variables
+    D^1/2 w: after any number of steps w = D^-1/2 w_hat, with the same alpha
+    and the same rho (= ||r_hat||^2)."""
+    qp = gi.grid_qp_2d(13, 11, seed=57, shift=0.02, sigma=1.0)
+    sq = _scaled_qp(qp)
+    free = gi.uniform(57, 2, qp.n) < 0.75
+    g = gi.normal(57, 3, qp.n)
+    dh = np.sqrt(qp.diag)
+    for k in (1, 3, 7):
+        s1, w, it1, _, ev1 = oracle.reduced_cg(qp, free, g, eta2=0.0, max_cg=k,
+                                               precond=oracle.PRECOND_JACOBI)
+        s2, wh, it2, _, ev2 = oracle.reduced_cg(sq, free, g / dh, eta2=0.0, max_cg=k)
+        assert s1 == s2 == oracle.OK and it1 == it2 == k
+        assert np.allclose(w, wh / dh, rtol=1e-10, atol=1e-13)
+        a1 = [e["a"] for e in ev1 if e["kind"] == oracle.EV_CG_ITER]
+        a2 = [e["a"] for e in ev2 if e["kind"] == oracle.EV_CG_ITER]
+        c1 = [e["c"] for e in ev1 if e["kind"] == oracle.EV_CG_ITER]
+        c2 = [e["c"] for e in ev2 if e["kind"] == oracle.EV_CG_ITER]
+        assert np.allclose(a1, a2, rtol=1e-10) and np.allclose(c1, c2, rtol=1e-9)
+
+
+def test_pcg_jacobi_special_cases():
+    """Constant diagonal: Jacobi PCG takes exactly the CG steps (M is a
+    multiple of I).  No couplings: the first step (alpha = 1) solves the
+    diagonal system."""
+    qp = gi.grid_qp_2d(10, 9, seed=58, shift=0.05)
+    qp.diag[:] = 1.0 + float(np.max(qp.diag))  # constant, still diagonally dominant
+    free = gi.uniform(58, 2, qp.n) < 0.8
+    g = gi.normal(58, 3, qp.n)
+    s1, w1, it1, r1, _ = oracle.reduced_cg(qp, free, g, eta2=0.05, max_cg=1000)
+    s2, w2, it2, r2, _ = oracle.reduced_cg(qp, free, g, eta2=0.05, max_cg=1000,
+                                           precond=oracle.PRECOND_JACOBI)
+    assert (s1, it1, r1) == (s2, it2, r2)
+    assert np.allclose(w1, w2, rtol=1e-12, atol=1e-15)
+    qp.cx[:] = 0.0
+    qp.cy[:] = 0.0
+    # the first step is the solution (alpha = 1; the residual left is rounding)
+    s, w, it, reason, ev = oracle.reduced_cg(qp, free, g, eta2=0.0, max_cg=1,
+                                             precond=oracle.PRECOND_JACOBI)
+    assert s == oracle.OK and it == 1
+    assert math.isclose(ev[0]["a"], 1.0, rel_tol=1e-14)
+    assert np.allclose(w[free], -g[free] / qp.diag[free], rtol=1e-14)
+    assert ev[0]["c"] <= 1e-28 * np.sum(g[free] ** 2 / qp.diag[free])
+
+
+def test_gpcg_with_jacobi_meets_the_same_tolerance():
+    """GPCG with the Jacobi-preconditioned CG phase converges to the same
+    minimiser (the KKT point is unique; only the path changes)."""
+    qp = gi.grid_qp_2d(24, 20, seed=59, shift=0.02, bounds="two_sided", sigma=1.0)
+    r0 = oracle.solve(qp, tau_rel=1e-11)
+    r1 = oracle.solve(qp, tau_rel=1e-11, precond=oracle.PRECOND_JACOBI)
+    assert r0.status == r1.status == oracle.OK
+    assert r1.stats["pg_norm"] <= 1e-11 * r1.stats["pg_norm0"] * (1 + 1e-9)
+    A = bf.dense_matrix(qp)
+    assert bf.kkt_residual(A, qp.b, qp.l, qp.u, r1.x) < 1e-8
+    assert np.allclose(r0.x, r1.x, rtol=1e-7, atol=1e-9)
+
+
 def test_reduced_cg_progress_stop():
     """(cgstop1): stop at the first j >= 2 with Delta_j <= eta2 max_{l<j} Delta_l
     and never earlier; the stopping step is included in w."""
