@@ -99,7 +99,8 @@ int64_t gpcg_problem_size(const gpcg_problem* p);
  * cgstop3 holds, unspecified in the paper); max_outer 10000, max_gp 50,
  * max_cg 10000, max_ls 60; precision GPCG_FP64; refine 1; x0 NULL (start at
  * P[l], falling back to u then 0 where a bound is infinite: Sec. 5 uses
- * x0 = l); cuda_stream NULL (the legacy default stream); lambda_min 0. */
+ * x0 = l); cuda_stream NULL (the legacy default stream); lambda_min 0;
+ * precond GPCG_PRECOND_NONE. */
 typedef struct {
     double tau_abs, tau_rel;
     double eta1, eta2, mu, eta2_shrink, eta2_floor;
@@ -109,7 +110,15 @@ typedef struct {
     const double* x0;       /* optional start (host or device, n values), projected onto Omega */
     void* cuda_stream;      /* cudaStream_t the solve is ordered on */
     double lambda_min;      /* optional lower bound on lambda_min(A), for err_bound */
+    int precond;            /* gpcg_precond: preconditioner of the CG phase (Sec. 6) */
+    int reserved;
 } gpcg_options;
+
+/* Preconditioners of the CG phase on the reduced system (Sec. 6 compares the
+ * diagonal one with block Jacobi).  GPCG_PRECOND_JACOBI: M = diag(A_k), the
+ * diagonal of the reduced Hessian; the decrease of Eq. cgstop1 is then
+ * alpha_j <r_j, M^-1 r_j> / 2. */
+typedef enum { GPCG_PRECOND_NONE = 0, GPCG_PRECOND_JACOBI = 1 } gpcg_precond;
 
 void gpcg_default_options(gpcg_options* o);
 

@@ -58,15 +58,16 @@ constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 //
 // The fused CG pass (2-D) stages f-row chunks (16 FP32, 8 FP64): FRH, FPH,
 // FAPH = halo boxes (64+2h) x (f+2) of r, p, Ap; FW, FD = 64 x f; FCX =
-// (64+h) x f; FCY = 64 x (f+1).  r, p and Ap are double-buffered (index
-// pcur: the current vectors), so each map of them comes in two.
+// (64+h) x f; FCY = 64 x (f+1); FDIH = halo box of 1/diag (Jacobi).  r, p
+// and Ap are double-buffered (index pcur: the current vectors), so each map
+// of them comes in two.  ADI = 64 x a box of 1/diag for P_CG_A.
 enum TMap : int {
   M32_RH0 = 0, M32_RH1, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R0, M32_R1, M32_P0,
   M32_P1, M32_AP0, M32_AP1, M32_FRH0, M32_FRH1, M32_FPH0, M32_FPH1, M32_FAPH0, M32_FAPH1, M32_FW,
-  M32_FD, M32_FCX, M32_FCY,
+  M32_FD, M32_FCX, M32_FCY, M32_FDIH, M32_ADI,
   M64_RH0, M64_RH1, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R0, M64_R1, M64_P0,
   M64_P1, M64_AP0, M64_AP1, M64_FRH0, M64_FRH1, M64_FPH0, M64_FPH1, M64_FAPH0, M64_FAPH1, M64_FW,
-  M64_FD, M64_FCX, M64_FCY,
+  M64_FD, M64_FCX, M64_FCY, M64_FDIH, M64_ADI,
   MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G18
   MG_PGH0, MG_PGH1,                                                  // G34
   MG_L32, MG_U32, MG_B32,                                            // 64 x 16
@@ -112,7 +113,7 @@ struct Opts {
   double tau_abs, tau_rel, eta1, eta2, mu, eta2_shrink, eta2_floor, eta2_refine;
   double c;
   int max_outer, max_gp, max_cg, max_ls;
-  int mixed, refine, use_x0, pad;
+  int mixed, refine, use_x0, precond;  // precond: 1 = point Jacobi in the CG phase
 };
 
 // Mutable per-instance state, owned by the finalizer of each pass.
@@ -144,6 +145,8 @@ struct DevInst {
   int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
+  const double* dinv;      // 1/diag (0 in pad columns): the point-Jacobi preconditioner
+  const float* dinv32;
   double *x[2], *g[2];
   unsigned* mask[2];
   double *r64[2], *w64, *p64[2], *Ap64[2];  // r, p, Ap double-buffered (index pcur)

@@ -28,6 +28,8 @@ cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s);
 cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
                         int fill_l, int fill_u, int* flags, cudaStream_t s);
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
+cudaError_t launch_recip(const double* d, double* out64, float* out32, long long count,
+                         cudaStream_t s);
 cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
                               unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s);
 cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* part,
@@ -199,21 +201,21 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
   p->n_groups = std::min((p->n_tiles + kGroupTiles - 1) / kGroupTiles, kMaxGroups);
 }
 
-// Bytes of the FP64 arena: kc bands, b, l, u, x[2], g[2], r[2], w, p[2],
-// Ap[2], two masks and the tile partials.
+// Bytes of the FP64 arena: kc bands, 1/diag, b, l, u, x[2], g[2], r[2], w,
+// p[2], Ap[2], two masks and the tile partials.
 static size_t arena64_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(double) * (size_t)p->pn);
   const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
   const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_groups);
   const size_t maps = align256(sizeof(CUtensorMap) * M_COUNT);
-  return (size_t)(p->kc + 14) * vec + 2 * msk + part + maps;
+  return (size_t)(p->kc + 15) * vec + 2 * msk + part + maps;
 }
 
-// FP32 bands, the FP32 CG vectors r[2], w, p[2], Ap[2], and the FP32 arrays
-// of the mixed phase x[2], g[2], b, l, u, pg[2].
+// FP32 bands and 1/diag, the FP32 CG vectors r[2], w, p[2], Ap[2], and the
+// FP32 arrays of the mixed phase x[2], g[2], b, l, u, pg[2].
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
-  return (size_t)(p->kc + 7 + 9) * vec;
+  return (size_t)(p->kc + 1 + 7 + 9) * vec;
 }
 
 static void carve64(gpcg_problem* p) {
@@ -243,6 +245,7 @@ static void carve64(gpcg_problem* p) {
   I.cx = (double*)take(vec);
   I.cy = (double*)take(vec);
   I.cz = p->dim == 3 ? (double*)take(vec) : nullptr;
+  I.dinv = (double*)take(vec);
   I.b = (double*)take(vec);
   I.l = (double*)take(vec);
   I.u = (double*)take(vec);
@@ -314,6 +317,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   const void* cx = f32 ? (const void*)I.cx32 : (const void*)I.cx;
   const void* cy = f32 ? (const void*)I.cy32 : (const void*)I.cy;
   const void* w = f32 ? (const void*)I.w32 : (const void*)I.w64;
+  const void* di = f32 ? (const void*)I.dinv32 : (const void*)I.dinv;
   CUtensorMap m[kCgMaps];
   CUtensorMap* q = m;
   auto e = [&](const void* base, int bw, int bh) { return encode_map(q++, f32, base, p, bw, bh); };
@@ -329,7 +333,9 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
       e(v(0, "r"), 64 + 2 * h, f + 2) && e(v(1, "r"), 64 + 2 * h, f + 2) &&
       e(v(0, "p"), 64 + 2 * h, f + 2) && e(v(1, "p"), 64 + 2 * h, f + 2) &&
       e(v(0, "A"), 64 + 2 * h, f + 2) && e(v(1, "A"), 64 + 2 * h, f + 2) && e(w, 64, f) &&
-      e(d, 64, f) && e(cx, 64 + h, f) && e(cy, 64, f + 1);
+      e(d, 64, f) && e(cx, 64 + h, f) && e(cy, 64, f + 1) &&
+      // 1/diag: FDIH, ADI
+      e(di, 64 + 2 * h, f + 2) && e(di, 64, a);
   if (!ok || q != m + kCgMaps) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -401,6 +407,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   };
   DevInst& I = p->inst;
   float* d32 = take();
+  float* dinv32 = take();
   float* x32 = take();
   float* y32 = take();
   float* z32 = p->dim == 3 ? take() : nullptr;
@@ -428,6 +435,8 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.cx32 = x32;
   I.cy32 = y32;
   I.cz32 = z32;
+  CK(launch_recip(I.diag, nullptr, dinv32, p->pn, s));
+  I.dinv32 = dinv32;
   I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
   I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
@@ -486,6 +495,7 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
     if ((e = launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l,
                          (double*)I.u, l == nullptr, u == nullptr, d_flags, s)) != cudaSuccess)
       break;
+    if ((e = launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
       break;
@@ -532,6 +542,8 @@ extern "C" void gpcg_default_options(gpcg_options* o) {
   o->x0 = nullptr;
   o->cuda_stream = nullptr;
   o->lambda_min = 0.0;
+  o->precond = GPCG_PRECOND_NONE;
+  o->reserved = 0;
 }
 
 static gpcg_status check_options(const gpcg_options* o) {
@@ -546,6 +558,8 @@ static gpcg_status check_options(const gpcg_options* o) {
     return fail(GPCG_ERR_ARG, "bad iteration caps");
   if (o->precision != GPCG_FP64 && o->precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
+  if (o->precond != GPCG_PRECOND_NONE && o->precond != GPCG_PRECOND_JACOBI)
+    return fail(GPCG_ERR_ARG, "unknown preconditioner");
   return GPCG_OK;
 }
 
@@ -567,6 +581,7 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   r.mixed = o->precision == GPCG_MIXED;
   r.refine = o->refine ? 1 : 0;
   r.use_x0 = use_x0 ? 1 : 0;
+  r.precond = o->precond == GPCG_PRECOND_JACOBI ? 1 : 0;
   return r;
 }
 

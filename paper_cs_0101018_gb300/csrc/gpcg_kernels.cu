@@ -756,11 +756,36 @@ struct OpTrial32 {
   }
 };
 
+// The first CG step's r_0 = g_F and M^-1 Ap under point Jacobi, out of line:
+// it runs once per CG phase and, inlined, raises the register pressure of the
+// whole sweep.
+template <class T>
+__device__ __noinline__ void first_step_jacobi(const float* __restrict__ g32,
+                                               const double* __restrict__ g,
+                                               const T* __restrict__ dinv, long long i, bool v0,
+                                               bool v1, unsigned fb, T* rv, T* da) {
+  T di[2];
+  ld2(dinv, i, v0, v1, di);
+  double gv[2];
+  if (g32) {
+    float gf[2];
+    ld2(g32, i, v0, v1, gf);
+    gv[0] = gf[0];
+    gv[1] = gf[1];
+  } else {
+    ld2(g, i, v0, v1, gv);
+  }
+  rv[0] = (fb & 1u) ? (T)gv[0] : T(0);
+  rv[1] = (fb & 2u) ? (T)gv[1] : T(0);
+  da[0] *= di[0];
+  da[1] *= di[1];
+}
+
 // P_CG_B: operand p = -r + beta*p_old (FIRST: p = -g on the free set), the
 // masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap> (FIRST: also
 // ||r||^2 for r = g_F).  TV is the streamed precision (double, or float in the
 // mixed CG, whose sums use the compensated FP32 accumulator).
-template <class TV, bool FIRST>
+template <class TV, bool FIRST, bool JAC = false>
 struct OpCgB {
   using T = TV;
   static constexpr bool kF32 = sizeof(TV) == 4;
@@ -780,6 +805,7 @@ struct OpCgB {
   const T* by;
   const T* bz;
   FF* ff;  // [3] FP32 accumulators (kF32)
+  const T* __restrict__ dinv;  // 1/diag (point Jacobi, z = r / diag), or nullptr
   __device__ const T* diag() const { return bd; }
   __device__ const T* cx() const { return bx; }
   __device__ const T* cy() const { return by; }
@@ -801,22 +827,36 @@ struct OpCgB {
         ld2(g, i, v0, v1, gv);
       }
       const unsigned fb = (v0 ? my_free_bits(I, m, y, z, e0) : 0u);
-      o[0] = (fb & 1u) ? (T)(-gv[0]) : T(0);
-      o[1] = (fb & 2u) ? (T)(-gv[1]) : T(0);
+      T zv[2] = {(T)gv[0], (T)gv[1]};
+      if (JAC) {
+        T di[2];
+        ld2(dinv, i, v0, v1, di);
+        zv[0] *= di[0];
+        zv[1] *= di[1];
+      }
+      o[0] = (fb & 1u) ? -zv[0] : T(0);
+      o[1] = (fb & 2u) ? -zv[1] : T(0);
     } else {
       T rv[2], pv[2];
       ld2(r, i, v0, v1, rv);
       ld2(p_old, i, v0, v1, pv);
+      if (JAC) {
+        T di[2];
+        ld2(dinv, i, v0, v1, di);
+        rv[0] *= di[0];
+        rv[1] *= di[1];
+      }
       o[0] = fma(beta, pv[0], -rv[0]);
       o[1] = fma(beta, pv[1], -rv[1]);
     }
   }
   __device__ T operand_at(long long i, int y, int z, int col) const {
+    const T di = JAC ? __ldg(dinv + i) : T(1);
     if (FIRST) {
       if (!free_bit(I, m, y, z, col)) return T(0);
-      return g32 ? (T)(-__ldg(g32 + i)) : (T)(-__ldg(g + i));
+      return -(g32 ? (T)__ldg(g32 + i) : (T)__ldg(g + i)) * di;
     } else {
-      return fma(beta, __ldg(p_old + i), -__ldg(r + i));
+      return fma(beta, __ldg(p_old + i), -__ldg(r + i) * di);
     }
   }
   __device__ void output(int y, int z, long long i, int, int e0, int, bool v0, bool v1,
@@ -834,19 +874,22 @@ struct OpCgB {
       acc.s[0] = fma((double)v[1], (double)a1, acc.s[0]);
     }
     if (FIRST) {
-      st2(r_out, i, v0, v1, -v[0], -v[1]);
+      // r = g_F (v = -z = -M^-1 r); rho = <r, z>; <Ap, M^-1 Ap> (the fused
+      // steps predict rho_1 from them)
+      T rv[2] = {-v[0], -v[1]}, da[2] = {a0, a1};
+      if (JAC) first_step_jacobi<T>(g32, g, dinv, i, v0, v1, fb, rv, da);
+      st2(r_out, i, v0, v1, rv[0], rv[1]);
       st2(w_out, i, v0, v1, T(0), T(0));
-      // ||r||^2 and ||Ap||^2 (the fused steps predict ||r_1||^2 from them)
       if (kF32) {
-        ff_fma(ff[1], (float)v[0], (float)v[0]);
-        ff_fma(ff[1], (float)v[1], (float)v[1]);
-        ff_fma(ff[2], (float)a0, (float)a0);
-        ff_fma(ff[2], (float)a1, (float)a1);
+        ff_fma(ff[1], (float)rv[0], -(float)v[0]);
+        ff_fma(ff[1], (float)rv[1], -(float)v[1]);
+        ff_fma(ff[2], (float)a0, (float)da[0]);
+        ff_fma(ff[2], (float)a1, (float)da[1]);
       } else {
-        acc.s[1] = fma((double)v[0], (double)v[0], acc.s[1]);
-        acc.s[1] = fma((double)v[1], (double)v[1], acc.s[1]);
-        acc.s[2] = fma((double)a0, (double)a0, acc.s[2]);
-        acc.s[2] = fma((double)a1, (double)a1, acc.s[2]);
+        acc.s[1] = fma((double)rv[0], -(double)v[0], acc.s[1]);
+        acc.s[1] = fma((double)rv[1], -(double)v[1], acc.s[1]);
+        acc.s[2] = fma((double)a0, (double)da[0], acc.s[2]);
+        acc.s[2] = fma((double)a1, (double)da[1], acc.s[2]);
       }
     }
   }
@@ -854,12 +897,14 @@ struct OpCgB {
 
 // ---------------------------------------------------------- pointwise passes
 
-// P_CG_A: w += alpha p, r_out = r + alpha Ap, ||r_out||^2.
-template <class T>
+// P_CG_A: w += alpha p, r_out = r + alpha Ap, <r_out, M^-1 r_out> (M = I or
+// diag(A) with dinv).
+template <class T, bool JAC>
 __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* __restrict__ r,
                                           T* r_out, const T* __restrict__ p,
-                                          const T* __restrict__ ap, double alpha, int x0, int y0,
-                                          int z, Acc& acc, FF* ffs) {
+                                          const T* __restrict__ ap, const T* __restrict__ dinv,
+                                          double alpha, int x0, int y0, int z, Acc& acc,
+                                          FF* ffs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ya = y0 + warp * kRY;
   if (ya >= I.ny) return;
@@ -882,12 +927,19 @@ __device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* __res
     rv[1] = fma(a, av[1], rv[1]);
     st2(w, i, v0, v1, wv[0], wv[1]);
     st2(r_out, i, v0, v1, rv[0], rv[1]);
+    T zv[2] = {rv[0], rv[1]};  // z = M^-1 r (point Jacobi) or r
+    if (JAC) {
+      T di[2];
+      ld2(dinv, i, v0, v1, di);
+      zv[0] *= di[0];
+      zv[1] *= di[1];
+    }
     if (sizeof(T) == 4) {
-      ff_fma(ff, (float)rv[0], (float)rv[0]);
-      ff_fma(ff, (float)rv[1], (float)rv[1]);
+      ff_fma(ff, (float)rv[0], (float)zv[0]);
+      ff_fma(ff, (float)rv[1], (float)zv[1]);
     } else {
-      acc.s[0] = fma((double)rv[0], (double)rv[0], acc.s[0]);
-      acc.s[0] = fma((double)rv[1], (double)rv[1], acc.s[0]);
+      acc.s[0] = fma((double)rv[0], (double)zv[0], acc.s[0]);
+      acc.s[0] = fma((double)rv[1], (double)zv[1], acc.s[0]);
     }
   }
 }
@@ -926,6 +978,7 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   // must read or write, once (documented per pass in the design notes)
   const double kc = (double)I.kc;
   const double sv = C.cg32 ? 4.0 : 8.0;
+  const double pj = I.opt.precond ? sv : 0.0;
   double per = 0.0;
   switch (pass) {
     case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
@@ -939,11 +992,11 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
       else
         per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
       break;
-    case P_CG_B:
-      per = sv * kc + (C.first_cg ? (C.gp32 ? 4.0 : 8.0) + 4.0 * sv : 4.0 * sv) + 0.125;
+    case P_CG_B:  // (+ 1/diag with point Jacobi)
+      per = sv * kc + (C.first_cg ? (C.gp32 ? 4.0 : 8.0) + 4.0 * sv : 4.0 * sv) + 0.125 + pj;
       break;
-    case P_CG_A: per = 6.0 * sv; break;
-    case P_CG_F: per = sv * kc + 8.0 * sv + 0.125; break;
+    case P_CG_A: per = 6.0 * sv + pj; break;
+    case P_CG_F: per = sv * kc + 8.0 * sv + 0.125 + pj; break;
     default: break;
   }
   return per * (double)I.n;
@@ -1032,14 +1085,15 @@ __device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
   return I.dim == 2 && I.tmaps != nullptr && (C.cg32 ? I.tma32 : I.tma64);
 }
 
-// After alpha_j of a fused phase is known (C.rr = ||r_j||^2): the CG
-// bookkeeping and Eq. cgstop1 of step j, with ||r_{j+1}||^2 taken from
-// ||r_j + alpha_j Ap_j||^2 = ||r_j||^2 + 2 alpha_j <r_j,Ap_j> + alpha_j^2 ||Ap_j||^2
-// (its sums come from the pass that formed Ap_j); then either the next fused
-// step or a last P_CG_A that completes w_{j+1} before the projected search.
-__device__ void cg_advance(const DevInst& I, Ctl& C, double rAp, double ApAp) {
+// After alpha_j of a fused phase is known (C.rr = rho_j = <r_j, z_j>, z =
+// M^-1 r): the CG bookkeeping and Eq. cgstop1 of step j (decrease
+// alpha_j rho_j / 2), with rho_{j+1} = <r_j + alpha Ap_j, M^-1 (r_j + alpha Ap_j)>
+// = rho_j + 2 alpha_j <z_j,Ap_j> + alpha_j^2 <Ap_j,M^-1 Ap_j> (its sums come
+// from the pass that formed Ap_j); then either the next fused step or a last
+// P_CG_A that completes w_{j+1} before the projected search.
+__device__ void cg_advance(const DevInst& I, Ctl& C, double zAp, double ApMAp) {
   const Opts& o = I.opt;
-  const double rr_next = C.rr + 2.0 * C.alpha * rAp + C.alpha * C.alpha * ApAp;
+  const double rr_next = C.rr + 2.0 * C.alpha * zAp + C.alpha * C.alpha * ApMAp;
   C.cg_j++;
   C.cg_iters++;
   if (C.refining) C.refine_cg_iters++;
@@ -1213,7 +1267,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       C.alpha = C.rr / pAp;
       C.pcur ^= 1;
       if (cg_fused(I, C)) {
-        // first step of a fused phase: r_0 = -p_0, so <r_0, Ap_0> = -<p_0, Ap_0>
+        // first step of a fused phase: z_0 = -p_0, so <z_0, Ap_0> = -<p_0, Ap_0>
         cg_advance(I, C, -pAp, red[2]);
       } else {
         C.pass = P_CG_A;
@@ -1297,9 +1351,9 @@ struct ChunkGeo {
 };
 static_assert(ChunkGeo<float>::END_B <= kOffMask && ChunkGeo<double>::END_B <= kOffMask,
               "stage layout");
-static_assert(4 * ChunkGeo<float>::SZ_A <= kOffMask &&
-                  4 * ChunkGeo<double>::SZ_A <= kOffMask,
-              "stage layout");
+static_assert(5 * ChunkGeo<float>::SZ_A <= kOffMask &&
+                  5 * ChunkGeo<double>::SZ_A <= kOffMask,
+              "stage layout (W, R, P, AP and, with point Jacobi, 1/diag)");
 
 __device__ __forceinline__ const void* tmap(const DevInst& I, int k) {
   return reinterpret_cast<const char*>(I.tmaps) + 128 * k;
@@ -1324,7 +1378,8 @@ __device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, in
                                           unsigned st, unsigned bar) {
   using G = ChunkGeo<T>;
   constexpr int o = -M32_RH0;
-  mbar_expect(bar, G::TX_A);
+  mbar_expect(bar, G::TX_A + (I.opt.precond ? G::SZ_A : 0));
+  if (I.opt.precond) tma_load2d(st + 4 * G::SZ_A, tmap(I, G::MB + o + M32_ADI), x0, row, bar);
   tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + o + M32_W), x0, row, bar);
   tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + o + M32_R0 + pcur), x0, row, bar);
   tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + o + M32_P0 + pcur), x0, row, bar);
@@ -1392,9 +1447,9 @@ __device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, i
 }
 
 // P_CG_A on one staged chunk: w += alpha p, r' = r + alpha Ap (into `r`, the
-// other buffer), ||r'||^2.  `row` is the chunk's first row in the (ny*nz) row
+// other buffer), <r', M^-1 r'> (M = I, or diag(A) from the staged 1/diag).  `row` is the chunk's first row in the (ny*nz) row
 // space, `ylim` the number of rows of the chunk that lie inside the plane.
-template <class T>
+template <class T, bool JAC>
 __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char* st, int x0,
                                           int row, int ylim, T alpha, T* w, T* r, Acc& acc,
                                           FF& ff) {
@@ -1403,6 +1458,8 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
   const T* R = reinterpret_cast<const T*>(st + 1 * G::SZ_A);
   const T* P = reinterpret_cast<const T*>(st + 2 * G::SZ_A);
   const T* AP = reinterpret_cast<const T*>(st + 3 * G::SZ_A);
+  const T* DI = reinterpret_cast<const T*>(st + 4 * G::SZ_A);  // 1/diag (point Jacobi)
+  constexpr bool jac = JAC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int RPW = G::CH_A / kWarps;
   const int c = 2 * lane;
@@ -1415,15 +1472,16 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
     const int o = ry * 64 + c;
     const T w0 = fma(alpha, P[o], W[o]), w1 = fma(alpha, P[o + 1], W[o + 1]);
     const T r0 = fma(alpha, AP[o], R[o]), r1 = fma(alpha, AP[o + 1], R[o + 1]);
+    const T z0 = jac ? r0 * DI[o] : r0, z1 = jac ? r1 * DI[o + 1] : r1;
     const long long i = (long long)(row + ry) * I.px + e0;
     st2(w, i, v0, v1, w0, w1);
     st2(r, i, v0, v1, r0, r1);
     if (sizeof(T) == 4) {
-      ff_fma(ff, (float)r0, (float)r0);
-      ff_fma(ff, (float)r1, (float)r1);
+      ff_fma(ff, (float)r0, (float)z0);
+      ff_fma(ff, (float)r1, (float)z1);
     } else {
-      acc.s[0] = fma((double)r0, (double)r0, acc.s[0]);
-      acc.s[0] = fma((double)r1, (double)r1, acc.s[0]);
+      acc.s[0] = fma((double)r0, (double)z0, acc.s[0]);
+      acc.s[0] = fma((double)r1, (double)z1, acc.s[0]);
     }
   }
 }
@@ -1433,10 +1491,11 @@ __device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char*
 // P_CG_F on a 2-D instance: one pass per CG step j >= 1 (Algorithm GPCG's
 // CG phase on the reduced system, Eq. cg2).  With alpha = alpha_{j-1} and
 // beta = beta_{j-1} over the halo box of the chunk, in place in the stage:
-//   r_j = r_{j-1} + alpha Ap_{j-1},   p_j = -r_j + beta p_{j-1},
-// at the chunk's points also w_j = w_{j-1} + alpha p_{j-1}; then
-// Ap_j = Z Z' A Z Z' p_j and the sums ||r_j||^2, <p_j,Ap_j>, <r_j,Ap_j>,
-// ||Ap_j||^2 (from which the finalizer takes alpha_j and ||r_{j+1}||^2).
+//   r_j = r_{j-1} + alpha Ap_{j-1},  z_j = M^-1 r_j,  p_j = -z_j + beta p_{j-1}
+// (M = I, or diag(A) for point Jacobi, Sec. 6), at the chunk's points also
+// w_j = w_{j-1} + alpha p_{j-1}; then Ap_j = Z Z' A Z Z' p_j and the sums
+// rho_j = <r_j,z_j>, <p_j,Ap_j>, <z_j,Ap_j>, <Ap_j,M^-1 Ap_j> (from which the
+// finalizer takes alpha_j and rho_{j+1}).
 // r, p and Ap are read from buffer pcur and written to pcur^1.  Stage layout,
 // T = float (f = 16 rows, h = 4) or double (f = 8, h = 2): R | P | AP, each
 // (64+2h) x (f+2) from (x0-h, y-1) | W 64 x f | D 64 x f | CX (64+h) x f from
@@ -1451,9 +1510,11 @@ struct GeoF {
   static constexpr int OFF_R = 0, OFF_P = SZ_H, OFF_AP = 2 * SZ_H, OFF_W = 3 * SZ_H;
   static constexpr int OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
   static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
-  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr int OFF_DI = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));  // 1/diag
+  static constexpr int END = OFF_DI + SZ_H;
   static constexpr unsigned TX =
       (3 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr unsigned TX_DI = (CH + 2) * BW * sizeof(T);
   static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
 };
 static_assert(GeoF<float>::END <= kOffMask && GeoF<double>::END <= kOffMask,
@@ -1464,7 +1525,9 @@ __device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, in
                                           unsigned st, unsigned bar) {
   using G = GeoF<T>;
   constexpr int o = G::MB - M32_RH0;
-  mbar_expect(bar, G::TX);
+  mbar_expect(bar, G::TX + (I.opt.precond ? G::TX_DI : 0u));
+  if (I.opt.precond)
+    tma_load2d(st + G::OFF_DI, tmap(I, o + M32_FDIH), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_AP, tmap(I, o + M32_FAPH0 + pcur), x0 - G::H, yc - 1, bar);
@@ -1477,6 +1540,7 @@ __device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, in
 // P_CG_F, FP64 (one row per warp): r_j and p_j are formed once per element
 // of the halo box, in place in the stage, then a block barrier; recomputing
 // them per warp would triple the FP64 work, the bound of this pass.
+template <bool JAC>
 __device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* st, int x0, int yc,
                                               int rows, double alpha, double beta,
                                               const unsigned* fbits, double* w, double* r_out,
@@ -1489,6 +1553,8 @@ __device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* s
   const double* D = reinterpret_cast<const double*>(st + G::OFF_D);
   const double* CX = reinterpret_cast<const double*>(st + G::OFF_CX);
   const double* CY = reinterpret_cast<const double*>(st + G::OFF_CY);
+  const double* DI = reinterpret_cast<const double*>(st + G::OFF_DI);
+  constexpr bool jac = JAC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ylim = min(rows, I.ny - yc);
   double s_rr = 0.0;
@@ -1496,8 +1562,9 @@ __device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* s
     const int br = e / G::BW, bc = e - br * G::BW;
     const double pold = P[e];
     const double rn = fma(alpha, AP[e], R[e]);
-    const double pn = fma(beta, pold, -rn);
-    R[e] = rn;
+    const double zn = jac ? rn * DI[e] : rn;  // z = M^-1 r
+    const double pn = fma(beta, pold, -zn);
+    R[e] = zn;  // the stage keeps z for <z, Ap>
     P[e] = pn;
     const int ry = br - 1, col = bc - G::H;
     if (ry >= 0 && ry < ylim && col >= 0 && col < 64 && x0 + col < I.nx) {
@@ -1505,7 +1572,7 @@ __device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* s
       w[i] = fma(alpha, pold, W[ry * 64 + col]);
       r_out[i] = rn;
       p_out[i] = pn;
-      s_rr = fma(rn, rn, s_rr);
+      s_rr = fma(rn, zn, s_rr);
     }
   }
   acc.s[0] += s_rr;
@@ -1537,10 +1604,12 @@ __device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* s
   a0 = (fb & 1u) ? a0 : 0.0;
   a1 = (fb & 2u) ? a1 : 0.0;
   st2(ap_out, (long long)(yc + ry) * I.px + e0, v0, v1, a0, a1);
-  const double r0 = Rr[0], r1 = Rr[1];
+  const double z0 = Rr[0], z1 = Rr[1];
+  const double* Dr2 = DI + (ry + 1) * G::BW + G::H + c;
+  const double da0 = jac ? a0 * Dr2[0] : a0, da1 = jac ? a1 * Dr2[1] : a1;
   acc.s[1] = fma(vc0, a0, fma(vc1, a1, acc.s[1]));
-  acc.s[2] = fma(r0, a0, fma(r1, a1, acc.s[2]));
-  acc.s[3] = fma(a0, a0, fma(a1, a1, acc.s[3]));
+  acc.s[2] = fma(z0, a0, fma(z1, a1, acc.s[2]));
+  acc.s[3] = fma(a0, da0, fma(a1, da1, acc.s[3]));
 }
 
 template <class T>
@@ -1563,7 +1632,7 @@ __device__ __forceinline__ void ff_acc(FF& a, float v) { a = ff_add(a, FF{v, 0.0
 // and east neighbours by shuffles), so no block barrier is needed.  For
 // T = float a thread sums its few terms of the chunk in FP32 and adds that to
 // its float-float accumulator once per chunk.
-template <class T>
+template <class T, bool JAC>
 __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char* st, int x0,
                                           int yc, int rows, T alpha, T beta, const unsigned* fbits,
                                           T* w, T* r_out, T* p_out, T* ap_out, Acc& acc, FF* ff) {
@@ -1577,6 +1646,8 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
   const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
   const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
   const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const T* DI = reinterpret_cast<const T*>(st + G::OFF_DI);  // 1/diag (point Jacobi)
+  constexpr bool jac = JAC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ylim = min(rows, I.ny - yc);
   const int r0 = warp * RPW;  // first chunk row of this warp
@@ -1584,7 +1655,7 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
   const int c = 2 * lane;
   const int e0 = x0 + c;
   const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
-  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q)
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q); z = M^-1 r
   T pn[RPW + 2][2], rn[RPW][2], po[RPW][2], pw[RPW], pe[RPW];
 #pragma unroll
   for (int q = 0; q < RPW + 2; ++q) {
@@ -1592,9 +1663,14 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
     const T2 rv = *reinterpret_cast<const T2*>(R + b);
     const T2 pv = *reinterpret_cast<const T2*>(P + b);
     const T2 av = *reinterpret_cast<const T2*>(AP + b);
+    T2 dv;
+    dv.x = T(1);
+    dv.y = T(1);
+    if (jac) dv = *reinterpret_cast<const T2*>(DI + b);
     const T ra = fma(alpha, av.x, rv.x), rb = fma(alpha, av.y, rv.y);
-    pn[q][0] = fma(beta, pv.x, -ra);
-    pn[q][1] = fma(beta, pv.y, -rb);
+    const T za = ra * dv.x, zb = rb * dv.y;
+    pn[q][0] = fma(beta, pv.x, -za);
+    pn[q][1] = fma(beta, pv.y, -zb);
     if (q >= 1 && q <= RPW) {
       rn[q - 1][0] = ra;
       rn[q - 1][1] = rb;
@@ -1607,8 +1683,10 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
     pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
     pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
     const int b = (r0 + k + 1) * G::BW + G::H + c;
-    if (lane == 0) pw[k] = fma(beta, P[b - 1], -fma(alpha, AP[b - 1], R[b - 1]));
-    if (lane == 31) pe[k] = fma(beta, P[b + 2], -fma(alpha, AP[b + 2], R[b + 2]));
+    if (lane == 0)
+      pw[k] = fma(beta, P[b - 1], -fma(alpha, AP[b - 1], R[b - 1]) * (jac ? DI[b - 1] : T(1)));
+    if (lane == 31)
+      pe[k] = fma(beta, P[b + 2], -fma(alpha, AP[b + 2], R[b + 2]) * (jac ? DI[b + 2] : T(1)));
   }
   T s_rr = T(0), s_pap = T(0), s_rap = T(0), s_apap = T(0);
 #pragma unroll
@@ -1641,14 +1719,21 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
     st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
     st2(ap_out, i, v0, v1, a0, a1);
     // points past nx hold zeros (the boxes are zero-filled there)
-    s_rr = fma(rn[k][0], rn[k][0], s_rr);
-    s_rr = fma(rn[k][1], rn[k][1], s_rr);
+    T d0 = T(1), d1 = T(1);
+    if (jac) {
+      const T2 dv = *reinterpret_cast<const T2*>(DI + (ry + 1) * G::BW + G::H + c);
+      d0 = dv.x;
+      d1 = dv.y;
+    }
+    const T z0 = rn[k][0] * d0, z1 = rn[k][1] * d1;
+    s_rr = fma(rn[k][0], z0, s_rr);
+    s_rr = fma(rn[k][1], z1, s_rr);
     s_pap = fma(pn[q][0], a0, s_pap);
     s_pap = fma(pn[q][1], a1, s_pap);
-    s_rap = fma(rn[k][0], a0, s_rap);
-    s_rap = fma(rn[k][1], a1, s_rap);
-    s_apap = fma(a0, a0, s_apap);
-    s_apap = fma(a1, a1, s_apap);
+    s_rap = fma(z0, a0, s_rap);
+    s_rap = fma(z1, a1, s_rap);
+    s_apap = fma(a0, a0 * d0, s_apap);
+    s_apap = fma(a1, a1 * d1, s_apap);
   }
   if (sizeof(T) == 4) {
     ff_acc(ff[0], (float)s_rr);
@@ -2055,12 +2140,19 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
     }
   } else if (S.pass == P_CG_F) {
     const int q = S.pcur ^ 1;
-    if (S.cg32)
-      cgf_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits, I.w32,
-                       I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
+    const bool jac = I.opt.precond != 0;
+    if (S.cg32 && jac)
+      cgf_chunk<float, true>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits,
+                             I.w32, I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
+    else if (S.cg32)
+      cgf_chunk<float, false>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits,
+                              I.w32, I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
+    else if (jac)
+      cgf_chunk_box<true>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                          I.p64[q], I.Ap64[q], acc);
     else
-      cgf_chunk_box(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q], I.p64[q],
-                    I.Ap64[q], acc);
+      cgf_chunk_box<false>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                           I.p64[q], I.Ap64[q], acc);
   } else if (S.pass == P_CG_B) {
     const int q = S.pcur ^ 1;
     if (S.cg32)
@@ -2072,12 +2164,17 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
   } else {
     const int ylim = min(c.rows, I.ny - c.yc);
     const int q = S.pcur ^ 1;
-    if (S.cg32)
-      cga_chunk<float>(I, st, c.x0, c.z * I.ny + c.yc, ylim, (float)S.alpha, I.w32, I.r32[q],
-                       acc, ffs[0]);
+    const int row = c.z * I.ny + c.yc;
+    if (S.cg32 && I.opt.precond)
+      cga_chunk<float, true>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
+                             ffs[0]);
+    else if (S.cg32)
+      cga_chunk<float, false>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
+                              ffs[0]);
+    else if (I.opt.precond)
+      cga_chunk<double, true>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
     else
-      cga_chunk<double>(I, st, c.x0, c.z * I.ny + c.yc, ylim, S.alpha, I.w64, I.r64[q], acc,
-                        ffs[0]);
+      cga_chunk<double, false>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
   }
 }
 
@@ -2156,44 +2253,56 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
     }
     case P_CG_B: {
       const float* g32 = S.gp32 ? I.g32[cur] : nullptr;
+      // point Jacobi (z = r / diag) runs in its own instantiations
+      const bool jac = I.opt.precond != 0;
       if (S.cg32) {
-        if (S.first_cg) {
-          OpCgB<float, true> op{I, I.r32[pcur ^ 1], I.p32[pcur], I.g[cur], I.mask[cur], 0.0f, g32,
-                                I.p32[pcur ^ 1], I.Ap32[pcur ^ 1], I.r32[pcur ^ 1], I.w32,
-                                I.diag32, I.cx32, I.cy32, I.cz32, ffs};
-          stencil_tile(I, op, x0, y0, z, acc);
-        } else {
-          OpCgB<float, false> op{I, I.r32[pcur ^ 1], I.p32[pcur], I.g[cur], I.mask[cur],
-                                 (float)S.beta, g32, I.p32[pcur ^ 1], I.Ap32[pcur ^ 1],
-                                 I.r32[pcur ^ 1], I.w32,
-                                 I.diag32, I.cx32, I.cy32, I.cz32, ffs};
-          stencil_tile(I, op, x0, y0, z, acc);
-        }
+        float* p_new = I.p32[pcur ^ 1];
+        float* ap = I.Ap32[pcur ^ 1];
+        float* r1 = I.r32[pcur ^ 1];
+#define GPCG_CGB32(FIRST, JAC, BETA)                                                          \
+  {                                                                                          \
+    OpCgB<float, FIRST, JAC> op{I, r1, I.p32[pcur], I.g[cur], I.mask[cur], BETA, g32, p_new, \
+                                ap, r1, I.w32, I.diag32, I.cx32, I.cy32, I.cz32, ffs,         \
+                                I.dinv32};                                                   \
+    stencil_tile(I, op, x0, y0, z, acc);                                                      \
+  }
+        if (S.first_cg && jac) GPCG_CGB32(true, true, 0.0f)
+        else if (S.first_cg) GPCG_CGB32(true, false, 0.0f)
+        else if (jac) GPCG_CGB32(false, true, (float)S.beta)
+        else GPCG_CGB32(false, false, (float)S.beta)
+#undef GPCG_CGB32
       } else {
-        if (S.first_cg) {
-          OpCgB<double, true> op{I, I.r64[pcur ^ 1], I.p64[pcur], I.g[cur], I.mask[cur], 0.0,
-                                 nullptr, I.p64[pcur ^ 1], I.Ap64[pcur ^ 1], I.r64[pcur ^ 1],
-                                 I.w64,
-                                 I.diag, I.cx, I.cy, I.cz, nullptr};
-          stencil_tile(I, op, x0, y0, z, acc);
-        } else {
-          OpCgB<double, false> op{I, I.r64[pcur ^ 1], I.p64[pcur], I.g[cur], I.mask[cur], S.beta,
-                                  nullptr, I.p64[pcur ^ 1], I.Ap64[pcur ^ 1], I.r64[pcur ^ 1],
-                                  I.w64,
-                                  I.diag, I.cx, I.cy, I.cz, nullptr};
-          stencil_tile(I, op, x0, y0, z, acc);
-        }
+        double* p_new = I.p64[pcur ^ 1];
+        double* ap = I.Ap64[pcur ^ 1];
+        double* r1 = I.r64[pcur ^ 1];
+#define GPCG_CGB64(FIRST, JAC, BETA)                                                           \
+  {                                                                                           \
+    OpCgB<double, FIRST, JAC> op{I, r1, I.p64[pcur], I.g[cur], I.mask[cur], BETA, nullptr,     \
+                                 p_new, ap, r1, I.w64, I.diag, I.cx, I.cy, I.cz, nullptr,     \
+                                 I.dinv};                                                     \
+    stencil_tile(I, op, x0, y0, z, acc);                                                       \
+  }
+        if (S.first_cg && jac) GPCG_CGB64(true, true, 0.0)
+        else if (S.first_cg) GPCG_CGB64(true, false, 0.0)
+        else if (jac) GPCG_CGB64(false, true, S.beta)
+        else GPCG_CGB64(false, false, S.beta)
+#undef GPCG_CGB64
       }
       break;
     }
     case P_CG_A:
-      if (S.cg32) {
-        cg_a_tile<float>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur], I.Ap32[pcur],
-                         S.alpha, x0, y0, z, acc, ffs);
-      } else {
-        cg_a_tile<double>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur], I.Ap64[pcur],
-                          S.alpha, x0, y0, z, acc, ffs);
-      }
+      if (S.cg32 && I.opt.precond)
+        cg_a_tile<float, true>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
+                               I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
+      else if (S.cg32)
+        cg_a_tile<float, false>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
+                                I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
+      else if (I.opt.precond)
+        cg_a_tile<double, true>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur],
+                                I.Ap64[pcur], I.dinv, S.alpha, x0, y0, z, acc, ffs);
+      else
+        cg_a_tile<double, false>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur],
+                                 I.Ap64[pcur], I.dinv, S.alpha, x0, y0, z, acc, ffs);
       break;
     default:
       break;
@@ -2776,6 +2885,17 @@ __global__ void to_float_kernel(const double* __restrict__ src, float* dst, long
     dst[t] = (float)src[t];
 }
 
+// 1/diag in FP64 and (rounded from it) FP32; pad columns (diag 0) get 0.
+__global__ void recip_kernel(const double* __restrict__ d, double* out64, float* out32,
+                             long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double v = d[t] != 0.0 ? 1.0 / d[t] : 0.0;
+    if (out64) out64[t] = v;
+    if (out32) out32[t] = (float)v;
+  }
+}
+
 // Byte mask (unpadded, one byte per point) -> bit mask; and a value array
 // (unpadded FP64) -> -value on the free set in T (used by the masked
 // product entry point: p = -r + 0 * p_old with r = -p_F).
@@ -2874,6 +2994,12 @@ cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, do
 
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s) {
   to_float_kernel<<<grid_for(count), 256, 0, s>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recip(const double* d, double* out64, float* out32, long long count,
+                         cudaStream_t s) {
+  recip_kernel<<<grid_for(count), 256, 0, s>>>(d, out64, out32, count);
   return cudaGetLastError();
 }
 

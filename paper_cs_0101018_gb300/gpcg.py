@@ -18,6 +18,7 @@ from . import _build
 OK, ERR_ARG, ERR_INFEASIBLE, ERR_NUMERIC, ERR_OOM, ERR_BUDGET, ERR_CUDA = 0, 1, 2, 3, 4, 5, 6
 ERR_MAXIT, ERR_LINESEARCH, ERR_TIMEOUT, ERR_PENDING, ERR_CANCELLED = 7, 8, 9, 10, 11
 FP64, MIXED = 0, 1
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_INFEASIBLE", 3: "ERR_NUMERIC", 4: "ERR_OOM",
                 5: "ERR_BUDGET", 6: "ERR_CUDA", 7: "ERR_MAXIT", 8: "ERR_LINESEARCH",
@@ -42,7 +43,7 @@ class gpcg_options(C.Structure):
                 ("eta2_floor", C.c_double), ("max_outer", C.c_int), ("max_gp", C.c_int),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("precision", C.c_int),
                 ("refine", C.c_int), ("x0", C.c_void_p), ("cuda_stream", C.c_void_p),
-                ("lambda_min", C.c_double)]
+                ("lambda_min", C.c_double), ("precond", C.c_int), ("reserved", C.c_int)]
 
 
 class gpcg_stats(C.Structure):

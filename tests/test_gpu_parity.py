@@ -100,6 +100,30 @@ def test_mixed_matches_oracle(k):
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
 
+JACOBI = [PROBLEMS[k] for k in (0, 2, 5, 10, 14, 20, 24, 26, 28, 29, 30)]
+
+
+@pytest.mark.parametrize("k", range(len(JACOBI)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_jacobi_pcg_matches_oracle(k, prec):
+    """Point-Jacobi preconditioned CG phase (Sec. 6, M = diag of the reduced
+    Hessian): the same tolerances as the plain CG phase, against the oracle
+    running the same preconditioner; FP64 also follows the oracle's path."""
+    qp = JACOBI[k]
+    ref = oracle.solve(qp, tau_rel=1e-10, precond=oracle.PRECOND_JACOBI)
+    status, x, st = _solve(qp, tau_rel=1e-10, precision=prec, precond=g.PRECOND_JACOBI)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    if prec == g.FP64:
+        for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
+            a, b = st[key], ref.stats[key]
+            assert abs(a - b) <= 3 + 0.10 * b, (key, a, b)
+    c = oracle.census(qp, x)
+    assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
+
+
 def test_single_small_workload_fp64_and_mixed():
     qp = gi.single_small()
     ref = oracle.solve(qp, tau_rel=1e-8)
