@@ -224,8 +224,9 @@ def run_ours(args):
     prob = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, **d_in)
     hbm_peak, peak_kind = _peaks()
 
-    def timed(precision, steps, warmup):
-        opts = g.default_options(tau_rel=TAU_REL, precision=precision, stream=stream)
+    def timed(precision, steps, warmup, precond=0):
+        opts = g.default_options(tau_rel=TAU_REL, precision=precision, stream=stream,
+                                 precond=precond)
         for _ in range(warmup):
             g.gpcg_solve(prob, opts)
         torch.cuda.synchronize()
@@ -251,6 +252,15 @@ def run_ours(args):
     # mixed precision (headline) and plain FP64
     ms_mx, st_mx, clk_mx, wall_mx = timed(g.MIXED, args.steps, args.warmup)
     ms_64, st_64, clk_64, wall_64 = timed(g.FP64, args.steps, args.warmup)
+    # the point-Jacobi preconditioned CG phase (Sec. 6) on the same workload
+    jac = {}
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        msj, stj, _, _ = timed(prec, max(1, min(args.steps, 5)), 1, precond=g.PRECOND_JACOBI)
+        tj = _max_over_ranks(ws, sum(msj) / 1000.0)
+        jac[name] = {"value": ws * len(msj) / tj, "unit": "solves/s",
+                     "ms_per_step": sum(msj) / len(msj),
+                     "solve": {k: stj[k] for k in ("outer_iters", "gp_iters", "cg_iters",
+                                                   "passes", "pg_norm", "tau")}}
 
     tot_mx = _max_over_ranks(ws, sum(ms_mx) / 1000.0)
     tot_64 = _max_over_ranks(ws, sum(ms_64) / 1000.0)
@@ -346,6 +356,7 @@ def run_ours(args):
                  "solve": {k: st_64[k] for k in ("outer_iters", "gp_iters", "cg_iters",
                                                  "ls_trials", "passes", "pg_norm", "tau")}},
         "mixed_over_fp64": value / value_64,
+        "jacobi": jac,
         "roofline": roof_mx,
         "spmv": spmv,
         "solve": {k: st_mx[k] for k in ("outer_iters", "gp_iters", "cg_iters", "ls_trials",
