@@ -266,3 +266,36 @@ def serving_instance(r: Request) -> QP:
                           name=f"req{r.seed}")
     return grid_qp_3d(r.side, r.side, r.side, seed=r.seed, shift=1e-2, sigma=0.5,
                       bounds=r.bounds, b_dist="uniform", name=f"req{r.seed}")
+
+
+def journal_bearing(nx: int, ny: int, eps: float, half_width: float = 10.0) -> QP:
+    """The journal bearing problem of Sec. 5 as a finite-difference QP: minimise
+    the integral of w_q |grad v|^2 / 2 - w_l v over D = (0, 2 pi) x (0, 2 b),
+    w_q = (1 + eps cos xi_1)^3, w_l = eps sin xi_1, with v >= 0 and v = 0 on the
+    boundary, on nx x ny interior points (h1 = 2 pi / (nx + 1), h2 = 2 b / (ny + 1),
+    b = half_width).
+
+    Each grid edge contributes w (v_i - v_j)^2 / 2 with w = w_q at the edge
+    midpoint times h2/h1 (xi_1 edges) or h1/h2 (xi_2 edges); an edge to the
+    boundary adds its w to the diagonal only (v = 0 there).  The linear term
+    is b_i = -w_l(xi_1) h1 h2.  l = 0, u = +inf.  (The paper uses finite
+    elements from a reference that is not at hand; this discretisation is
+    for qualitative comparison only.)"""
+    h1 = 2.0 * np.pi / (nx + 1)
+    h2 = 2.0 * half_width / (ny + 1)
+    wq = lambda t: (1.0 + eps * np.cos(t)) ** 3
+    i = np.arange(1, nx + 1, dtype=np.float64)
+    ax = wq((np.arange(0, nx + 1) + 0.5) * h1) * (h2 / h1)  # edge i+1/2, i = 0..nx
+    cyw = wq(i * h1) * (h1 / h2)                            # xi_2 edges at column i
+    diag_row = ax[:-1] + ax[1:] + 2.0 * cyw
+    cx_row = np.zeros(nx)
+    cx_row[:-1] = -ax[1:-1]
+    diag = np.tile(diag_row, ny)
+    cx = np.tile(cx_row, ny)
+    cy = np.tile(-cyw, ny)
+    cy[(ny - 1) * nx:] = 0.0
+    b = np.tile(-eps * np.sin(i * h1) * h1 * h2, ny)
+    n = nx * ny
+    return QP(2, nx, ny, 1, diag, cx, cy, None, b, np.zeros(n), np.full(n, np.inf),
+              shift=0.0, name=f"journal_bearing_{nx}x{ny}_eps{eps}",
+              meta={"eps": eps, "half_width": half_width, "h1": h1, "h2": h2})

@@ -124,6 +124,21 @@ def test_jacobi_pcg_matches_oracle(k, prec):
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
 
+@pytest.mark.parametrize("shape", [(64, 48), (130, 70)])
+@pytest.mark.parametrize("eps", [0.1, 0.9])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_journal_bearing_matches_oracle(shape, eps, prec):
+    """The journal bearing workload (Sec. 5, finite differences): l = 0,
+    u = +inf, x0 = l, absolute tolerance."""
+    qp = gi.journal_bearing(*shape, eps)
+    ref = oracle.solve(qp, tau_abs=1e-10, tau_rel=0.0)
+    status, x, st = _solve(qp, tau_abs=1e-10, tau_rel=0.0, precision=prec)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all(x >= 0)
+
+
 def test_single_small_workload_fp64_and_mixed():
     qp = gi.single_small()
     ref = oracle.solve(qp, tau_rel=1e-8)
