@@ -310,6 +310,30 @@ def run_ours(args):
                       "kernel": "gpcg::mspmv_kernel"}
     del pbig, big
 
+    # the journal bearing problem of Sec. 5 (finite differences, 1600^2 like
+    # the paper's n = 2.56e6; tau = 1e-4 absolute, x0 = l), with the
+    # point-Jacobi preconditioned CG phase
+    jb = {}
+    for eps in (0.1, 0.9):
+        jqp = gi.journal_bearing(1600, 1600, eps)
+        jp = g.gpcg_problem_create(jqp)
+        for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+            jo = g.default_options(tau_abs=1e-4, tau_rel=0.0, precision=prec,
+                                   precond=g.PRECOND_JACOBI, stream=stream)
+            g.gpcg_solve(jp, jo)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gpcg_solve(jp, jo)
+            e1.record(stream)
+            e1.synchronize()
+            xj, sj = g.gpcg_result(jp)
+            jb[f"eps{eps}_{name}"] = {
+                "solves/s": 1000.0 / e0.elapsed_time(e1), "ms": e0.elapsed_time(e1),
+                "outer_iters": sj["outer_iters"], "gp_iters": sj["gp_iters"],
+                "cg_iters": sj["cg_iters"], "free_fraction": float(np.mean(xj > 0)),
+                "pg_norm": sj["pg_norm"], "status": sj["status"]}
+        del jp, jqp
+
     # end to end through the C ABI from pinned host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(qp, k))).pin_memory()
            for k in ("diag", "cx", "cy", "b", "l", "u")}
@@ -357,6 +381,7 @@ def run_ours(args):
                                                  "ls_trials", "passes", "pg_norm", "tau")}},
         "mixed_over_fp64": value / value_64,
         "jacobi": jac,
+        "journal_bearing_1600": jb,
         "roofline": roof_mx,
         "spmv": spmv,
         "solve": {k: st_mx[k] for k in ("outer_iters", "gp_iters", "cg_iters", "ls_trials",

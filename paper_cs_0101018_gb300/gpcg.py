@@ -46,6 +46,9 @@ class gpcg_options(C.Structure):
                 ("lambda_min", C.c_double), ("precond", C.c_int), ("reserved", C.c_int)]
 
 
+_OPTION_FIELDS = frozenset(f for f, _ in gpcg_options._fields_)
+
+
 class gpcg_stats(C.Structure):
     _fields_ = [("q", C.c_double), ("pg_norm", C.c_double), ("pg_norm0", C.c_double),
                 ("tau", C.c_double), ("n_active", C.c_int64), ("n_binding", C.c_int64),
@@ -153,6 +156,8 @@ def default_options(**kw) -> gpcg_options:
             k, v = "cuda_stream", (v.cuda_stream if hasattr(v, "cuda_stream") else v)
         if k == "x0":
             v = _ptr(v)
+        if k not in _OPTION_FIELDS:
+            raise TypeError(f"unknown gpcg option {k!r}")
         setattr(o, k, v)
     return o
 
