@@ -99,6 +99,8 @@ def lib():
         L.ora_reduced_cg.argtypes = [C.POINTER(_Stencil), vp, vp, dbl, ci, ci, vp,
                                      C.POINTER(ci), C.POINTER(ci), vp, i64, C.POINTER(i64)]
         L.ora_reduced_cg.restype = ci
+        L.ora_precondition.argtypes = [C.POINTER(_Stencil), vp, ci, vp, vp]
+        L.ora_precondition.restype = None
         L.ora_projected_search.argtypes = [C.POINTER(_Stencil), vp, vp, vp, dbl, ci, vp, vp,
                                            vp, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(ci)]
         L.ora_projected_search.restype = ci
@@ -207,7 +209,18 @@ def gp_step(qp, y, g, mu=0.01, max_ls=60):
     return s, y, g, a0.value, a.value, dec.value, tr.value
 
 
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_TILE = 0, 1, 2
+TILE_X, TILE_Y = 64, 8  # the blocks of PRECOND_TILE
+
+
+def precondition(qp, free_mask, r, precond):
+    """z = M^-1 r on the free set (zero elsewhere)."""
+    st = Stencil(qp)
+    fm = np.ascontiguousarray(free_mask, dtype=np.uint8)
+    r = _f64(r)
+    z = np.zeros_like(r)
+    lib().ora_precondition(st.ref, _ptr(fm), precond, _ptr(r), _ptr(z))
+    return z
 
 
 def reduced_cg(qp, free_mask, g, eta2, max_cg, trace_cap=100000, precond=PRECOND_NONE):

@@ -307,17 +307,91 @@ done:
  * with Delta_j <= eta2 * max_{l<j} Delta_l (cgstop1), when r vanishes, or at
  * max_cg; the step of the stopping iteration is kept, so w = w_{j_k}.
  * Returns ORA_OK or ORA_ERR_NUMERIC (<p, A_k p> <= 0). */
-/* z = M^{-1} r on the free set: the identity, or the diagonal of the reduced
- * Hessian A_k (point Jacobi, Sec. 6). */
+/* Solve the tridiagonal system of the reduced Hessian along one x-line
+ * segment: points i0 .. i0+len-1 of one row, couplings A(i,i+1) = cx[i]
+ * between consecutive points that are both free, nothing outside the
+ * segment.  A point off the free set gets the equation z_i = 0.  Thomas
+ * algorithm (forward elimination, back substitution); cp and dp are scratch
+ * of length len. */
+static void line_solve(const ora_stencil* A, const uint8_t* fm, int64_t i0, int64_t len,
+                       const double* rhs, double* z, double* cp, double* dp)
+{
+    for (int64_t k = 0; k < len; k++) {
+        const int64_t i = i0 + k;
+        const double a = (k > 0 && fm[i] && fm[i - 1]) ? A->cx[i - 1] : 0.0;
+        const double c = (k + 1 < len && fm[i] && fm[i + 1]) ? A->cx[i] : 0.0;
+        const double b = fm[i] ? A->diag[i] : 1.0;
+        const double d = fm[i] ? rhs[k] : 0.0;
+        const double den = k > 0 ? b - a * cp[k - 1] : b;
+        cp[k] = c / den;
+        dp[k] = k > 0 ? (d - a * dp[k - 1]) / den : d / den;
+    }
+    for (int64_t k = len - 1; k >= 0; k--) {
+        z[i0 + k] = k + 1 < len ? dp[k] - cp[k] * z[i0 + k + 1] : dp[k];
+    }
+}
+
+/* The tile preconditioner (ORA_PRECOND_TILE): in every 64 x 8 tile of every
+ * xy-plane, z starts at 0 and the lines of the even rows, then the odd rows,
+ * then the even rows are solved exactly with the couplings A(i, i +- nx) to
+ * the rows above and below inside the tile moved to the right-hand side with
+ * the current z there. */
+static void tile_sweep(const ora_stencil* A, const uint8_t* fm, const double* r, double* z)
+{
+    const int64_t nx = A->nx, ny = A->ny, nz = A->nz;
+    double* rhs = (double*)malloc(sizeof(double) * ORA_TILE_X);
+    double* cp = (double*)malloc(sizeof(double) * ORA_TILE_X);
+    double* dp = (double*)malloc(sizeof(double) * ORA_TILE_X);
+    for (int64_t i = 0; i < nx * ny * nz; i++) z[i] = 0.0;
+    for (int64_t iz = 0; iz < nz; iz++) {
+        for (int64_t y0 = 0; y0 < ny; y0 += ORA_TILE_Y) {
+            const int64_t y1 = y0 + ORA_TILE_Y < ny ? y0 + ORA_TILE_Y : ny;
+            for (int64_t x0 = 0; x0 < nx; x0 += ORA_TILE_X) {
+                const int64_t len = x0 + ORA_TILE_X < nx ? ORA_TILE_X : nx - x0;
+                static const int parity[3] = {0, 1, 0};
+                for (int h = 0; h < 3; h++) {
+                    for (int64_t iy = y0 + parity[h]; iy < y1; iy += 2) {
+                        const int64_t i0 = x0 + nx * (iy + ny * iz);
+                        for (int64_t k = 0; k < len; k++) {
+                            const int64_t i = i0 + k;
+                            double v = r[i];
+                            if (iy > y0 && fm[i] && fm[i - nx]) v -= A->cy[i - nx] * z[i - nx];
+                            if (iy + 1 < y1 && fm[i] && fm[i + nx]) v -= A->cy[i] * z[i + nx];
+                            rhs[k] = v;
+                        }
+                        line_solve(A, fm, i0, len, rhs, z, cp, dp);
+                    }
+                }
+            }
+        }
+    }
+    free(rhs);
+    free(cp);
+    free(dp);
+}
+
+/* z = M^{-1} r on the free set: the identity, the diagonal of the reduced
+ * Hessian A_k (point Jacobi, Sec. 6), or the tile block Jacobi above (the
+ * analogue of the paper's block Jacobi with one block per processor). */
 static void precondition(const ora_stencil* A, const uint8_t* free_mask, int precond,
                          const double* r, double* z)
 {
     const int64_t n = ora_n(A);
+    if (precond == ORA_PRECOND_TILE) {
+        tile_sweep(A, free_mask, r, z);
+        return;
+    }
     for (int64_t i = 0; i < n; i++) {
         if (!free_mask[i]) z[i] = 0.0;
         else if (precond == ORA_PRECOND_JACOBI) z[i] = r[i] / A->diag[i];
         else z[i] = r[i];
     }
+}
+
+void ora_precondition(const ora_stencil* A, const uint8_t* free_mask, int precond,
+                      const double* r, double* z)
+{
+    precondition(A, free_mask, precond, r, z);
 }
 
 /* Preconditioned conjugate gradients on subproblem (cg2) from w_0 = 0, in

@@ -47,8 +47,21 @@ typedef struct {
     const double* cz;     /* A(i,i+nx*ny), dim == 3 only */
 } ora_stencil;
 
-/* Preconditioners of the reduced CG (Sec. 6 compares them). */
-enum { ORA_PRECOND_NONE = 0, ORA_PRECOND_JACOBI = 1 /* M = diag(A_k) */ };
+/* Preconditioners of the reduced CG (Sec. 6 compares them).  TILE: block
+ * Jacobi with one block per 64 x 8 tile of each xy-plane (tiles start at
+ * multiples of 64 in x and 8 in y; couplings between tiles and between planes
+ * are dropped), each block solved approximately by one symmetric zebra line
+ * Gauss-Seidel sweep: exact solves along the x-lines of the tile's even rows,
+ * then its odd rows, then its even rows again, each line with the current
+ * values of its neighbouring lines on the right-hand side.  That is
+ * M = (D + L) D^-1 (D + U) per tile, D the line tridiagonals, L/U the
+ * couplings between lines in the order (even rows, odd rows). */
+enum {
+    ORA_PRECOND_NONE = 0,
+    ORA_PRECOND_JACOBI = 1, /* M = diag(A_k) */
+    ORA_PRECOND_TILE = 2    /* tile block Jacobi, zebra line sweep */
+};
+enum { ORA_TILE_X = 64, ORA_TILE_Y = 8 };
 
 typedef struct {
     double tau_abs, tau_rel;
@@ -91,6 +104,9 @@ int ora_gp_step(const ora_stencil* A, const double* b, const double* l, const do
 int ora_reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const double* g,
                    double eta2, int max_cg, int precond, double* w, int* iters, int* reason,
                    ora_event* events, int64_t event_cap, int64_t* event_len);
+/* z = M^-1 r on the free set (zero elsewhere) for preconditioner `precond`. */
+void ora_precondition(const ora_stencil* A, const uint8_t* free_mask, int precond,
+                      const double* r, double* z);
 int ora_projected_search(const ora_stencil* A, const double* b, const double* l,
                          const double* u, double mu, int max_ls, const double* d,
                          double* x, double* g, double* alpha, double* dq, int* trials);

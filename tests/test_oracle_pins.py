@@ -325,6 +325,118 @@ def test_gpcg_with_jacobi_meets_the_same_tolerance():
     assert np.allclose(r0.x, r1.x, rtol=1e-7, atol=1e-9)
 
 
+def _tile_operator(qp, free):
+    """M of the tile preconditioner on the free set, assembled densely from its
+    definition: per 64 x 8 tile of each xy-plane, D = the couplings along x
+    inside one row (the line tridiagonals, with the diagonal), L = the
+    couplings from an odd row to an even row of the same tile, U = L',
+    M = (D + L) D^-1 (D + U); nothing couples two tiles."""
+    A = bf.dense_matrix(qp)
+    F = np.flatnonzero(free)
+    AF = A[np.ix_(F, F)]
+    ix = F % qp.nx
+    iy = (F // qp.nx) % qp.ny
+    iz = F // (qp.nx * qp.ny)
+    tile = (iz * 10**6 + (iy // oracle.TILE_Y)) * 10**6 + ix // oracle.TILE_X
+    same_tile = tile[:, None] == tile[None, :]
+    same_row = same_tile & (iy[:, None] == iy[None, :])
+    odd_even = same_tile & (iy[:, None] % 2 == 1) & (iy[None, :] % 2 == 0)
+    D = np.where(same_row, AF, 0.0)
+    L = np.where(odd_even, AF, 0.0)
+    return F, AF, (D + L) @ np.linalg.solve(D, D + L.T)
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "ragged"])
+def test_tile_preconditioner_is_the_zebra_operator(case):
+    """The oracle's line sweeps (Thomas algorithm) apply exactly the inverse
+    of the dense M = (D + L) D^-1 (D + U) of each tile."""
+    if case == "2d":
+        qp = gi.grid_qp_2d(70, 12, seed=60, shift=0.02, sigma=1.0)
+    elif case == "3d":
+        qp = gi.grid_qp_3d(66, 9, 3, seed=61, shift=0.02, sigma=0.5, bounds="two_sided",
+                           b_dist="uniform")
+    else:
+        qp = gi.grid_qp_2d(131, 17, seed=62, shift=0.02, sigma=1.0)
+    free = gi.uniform(60, 2, qp.n) < 0.7
+    r = gi.normal(60, 3, qp.n)
+    z = oracle.precondition(qp, free, r, oracle.PRECOND_TILE)
+    F, _, M = _tile_operator(qp, free)
+    assert np.all(z[~free] == 0.0)
+    assert np.allclose(z[F], np.linalg.solve(M, r[F]), rtol=1e-11, atol=1e-13)
+
+
+def test_tile_preconditioner_is_symmetric_positive_definite():
+    """M^-1 (columns by applying it to unit vectors) is symmetric and positive
+    definite, so PCG's theory holds."""
+    qp = gi.grid_qp_2d(67, 10, seed=63, shift=0.02, sigma=1.0)
+    free = gi.uniform(63, 2, qp.n) < 0.8
+    F = np.flatnonzero(free)
+    Z = np.empty((F.size, F.size))
+    for k, i in enumerate(F):
+        e = np.zeros(qp.n)
+        e[i] = 1.0
+        Z[:, k] = oracle.precondition(qp, free, e, oracle.PRECOND_TILE)[F]
+    assert np.allclose(Z, Z.T, rtol=0, atol=1e-13 * np.max(np.abs(Z)))
+    assert np.min(np.linalg.eigvalsh(0.5 * (Z + Z.T))) > 0.0
+
+
+def test_pcg_tile_special_cases():
+    """No couplings between rows and one tile column (nx <= 64): M = A_FF, so
+    the first PCG step (alpha = 1) is the solution.  No couplings at all: the
+    tile preconditioner is point Jacobi."""
+    qp = gi.grid_qp_2d(60, 13, seed=64, shift=0.05, sigma=1.0)
+    qp.cy[:] = 0.0
+    free = gi.uniform(64, 2, qp.n) < 0.8
+    g = gi.normal(64, 3, qp.n)
+    s, w, it, reason, ev = oracle.reduced_cg(qp, free, g, eta2=0.0, max_cg=1,
+                                             precond=oracle.PRECOND_TILE)
+    A = bf.dense_matrix(qp)
+    F = np.flatnonzero(free)
+    assert s == oracle.OK and it == 1
+    assert math.isclose(ev[0]["a"], 1.0, rel_tol=1e-13)
+    assert np.allclose(w[F], np.linalg.solve(A[np.ix_(F, F)], -g[F]), rtol=1e-12, atol=1e-14)
+    qp.cx[:] = 0.0
+    r = gi.normal(64, 4, qp.n)
+    zt = oracle.precondition(qp, free, r, oracle.PRECOND_TILE)
+    zj = oracle.precondition(qp, free, r, oracle.PRECOND_JACOBI)
+    assert np.array_equal(zt, zj)
+
+
+def test_pcg_tile_exact_solve_and_closed_form_decrease():
+    """Tile-preconditioned CG with eta2 = 0 reaches the solution of
+    A_FF w = -g_F; its closed-form decreases telescope to q_k(0) - q_k(w); it
+    needs fewer steps than point Jacobi on an anisotropic problem."""
+    qp = gi.journal_bearing(70, 20, 0.5)
+    A = bf.dense_matrix(qp)
+    free = gi.uniform(65, 2, qp.n) < 0.85
+    g = gi.normal(65, 3, qp.n)
+    res = {}
+    for pc in (oracle.PRECOND_JACOBI, oracle.PRECOND_TILE):
+        s, w, iters, reason, ev = oracle.reduced_cg(qp, free, g, eta2=0.0, max_cg=4 * qp.n,
+                                                    precond=pc)
+        assert s == oracle.OK
+        F = np.flatnonzero(free)
+        AF = A[np.ix_(F, F)]
+        assert np.allclose(w[F], np.linalg.solve(AF, -g[F]), rtol=1e-8, atol=1e-10)
+        qk = 0.5 * w[F] @ AF @ w[F] + g[F] @ w[F]
+        deltas = [e["b"] for e in ev if e["kind"] == oracle.EV_CG_ITER]
+        assert math.isclose(sum(deltas), -qk, rel_tol=1e-9)
+        res[pc] = iters
+    assert res[oracle.PRECOND_TILE] < res[oracle.PRECOND_JACOBI]
+
+
+def test_gpcg_with_tile_meets_the_same_tolerance():
+    """GPCG with the tile-preconditioned CG phase reaches the same minimiser."""
+    qp = gi.grid_qp_2d(90, 20, seed=66, shift=0.02, bounds="two_sided", sigma=1.0)
+    r0 = oracle.solve(qp, tau_rel=1e-11)
+    r1 = oracle.solve(qp, tau_rel=1e-11, precond=oracle.PRECOND_TILE)
+    assert r0.status == r1.status == oracle.OK
+    assert r1.stats["pg_norm"] <= 1e-11 * r1.stats["pg_norm0"] * (1 + 1e-9)
+    A = bf.dense_matrix(qp)
+    assert bf.kkt_residual(A, qp.b, qp.l, qp.u, r1.x) < 1e-8
+    assert np.allclose(r0.x, r1.x, rtol=1e-7, atol=1e-9)
+
+
 def test_reduced_cg_progress_stop():
     """(cgstop1): stop at the first j >= 2 with Delta_j <= eta2 max_{l<j} Delta_l
     and never earlier; the stopping step is included in w."""
