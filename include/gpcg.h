@@ -115,10 +115,25 @@ typedef struct {
 } gpcg_options;
 
 /* Preconditioners of the CG phase on the reduced system (Sec. 6 compares the
- * diagonal one with block Jacobi).  GPCG_PRECOND_JACOBI: M = diag(A_k), the
- * diagonal of the reduced Hessian; the decrease of Eq. cgstop1 is then
- * alpha_j <r_j, M^-1 r_j> / 2. */
-typedef enum { GPCG_PRECOND_NONE = 0, GPCG_PRECOND_JACOBI = 1 } gpcg_precond;
+ * diagonal one with block Jacobi); the decrease of Eq. cgstop1 is then
+ * alpha_j <r_j, M^-1 r_j> / 2.
+ *   GPCG_PRECOND_JACOBI: M = diag(A_k), the diagonal of the reduced Hessian.
+ *   GPCG_PRECOND_TILE: block Jacobi with one block per 64 x 8 tile of the grid
+ *     (tiles start at multiples of 64 in x and 8 in y; couplings between tiles
+ *     are dropped), the analogue of the paper's one block per processor; each
+ *     block is solved approximately by one symmetric zebra line Gauss-Seidel
+ *     sweep on the free set (exact solves along the x-lines of the tile's even
+ *     rows, then odd rows, then even rows), so M = (D + L) D^-1 (D + U) per
+ *     tile, which is symmetric positive definite.  M^-1 is applied in FP32
+ *     arithmetic in every precision mode.  2-D problems only, on the staged
+ *     path (not with GPCG_NO_TMA); otherwise gpcg_solve returns GPCG_ERR_ARG.
+ *     The first solve with it allocates 4 more vectors of the CG precision(s)
+ *     (z = M^-1 r and q = M^-1 Ap, double-buffered). */
+typedef enum {
+    GPCG_PRECOND_NONE = 0,
+    GPCG_PRECOND_JACOBI = 1,
+    GPCG_PRECOND_TILE = 2
+} gpcg_precond;
 
 void gpcg_default_options(gpcg_options* o);
 
@@ -170,6 +185,18 @@ gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats)
  * accumulated in FP64.  Arrays: n values each, host or device. */
 gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask, const double* pv,
                              double* y, double* pAp, int precision, void* cuda_stream);
+
+/* z = M^-1 r for the tile preconditioner (GPCG_PRECOND_TILE) on the free set
+ * given by free_mask (one byte per point, nonzero = free): the pass that
+ * starts a tile-preconditioned CG phase, run once on r in place of the
+ * gradient.  z is 0 off the free set.  precision GPCG_MIXED rounds r to FP32
+ * and returns FP32 values widened to FP64 (M^-1 itself is applied in FP32 in
+ * both modes).  *rz (optional) receives <r_F, z_F> accumulated in FP64.
+ * Arrays: n values each, host or device.  2-D problems on the staged path
+ * only (GPCG_ERR_ARG otherwise).  Overwrites the problem's CG vectors, so
+ * gpcg_result reports GPCG_ERR_PENDING until the next solve. */
+gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* free_mask, const double* r,
+                                   double* z, double* rz, int precision, void* cuda_stream);
 
 /* Time `reps` launches of the masked matrix-vector kernel (the CG pass that
  * forms p and A_k p) on the problem's free set after the latest solve (or all

@@ -60,14 +60,16 @@ constexpr int kDynSmem = kStages * kStageBytes + 128 + 8 * kStages;
 // FAPH = halo boxes (64+2h) x (f+2) of r, p, Ap; FW, FD = 64 x f; FCX =
 // (64+h) x f; FCY = 64 x (f+1); FDIH = halo box of 1/diag (Jacobi).  r, p
 // and Ap are double-buffered (index pcur: the current vectors), so each map
-// of them comes in two.  ADI = 64 x a box of 1/diag for P_CG_A.
+// of them comes in two.  ADI = 64 x a box of 1/diag for P_CG_A.  FZH, FQH:
+// halo boxes of z = M^-1 r and q = M^-1 Ap under the tile preconditioner
+// (encoded when its vectors are first needed).
 enum TMap : int {
   M32_RH0 = 0, M32_RH1, M32_PH0, M32_PH1, M32_D, M32_CX, M32_CY, M32_W, M32_R0, M32_R1, M32_P0,
   M32_P1, M32_AP0, M32_AP1, M32_FRH0, M32_FRH1, M32_FPH0, M32_FPH1, M32_FAPH0, M32_FAPH1, M32_FW,
-  M32_FD, M32_FCX, M32_FCY, M32_FDIH, M32_ADI,
+  M32_FD, M32_FCX, M32_FCY, M32_FDIH, M32_ADI, M32_FZH0, M32_FZH1, M32_FQH0, M32_FQH1,
   M64_RH0, M64_RH1, M64_PH0, M64_PH1, M64_D, M64_CX, M64_CY, M64_W, M64_R0, M64_R1, M64_P0,
   M64_P1, M64_AP0, M64_AP1, M64_FRH0, M64_FRH1, M64_FPH0, M64_FPH1, M64_FAPH0, M64_FAPH1, M64_FW,
-  M64_FD, M64_FCX, M64_FCY, M64_FDIH, M64_ADI,
+  M64_FD, M64_FCX, M64_FCY, M64_FDIH, M64_ADI, M64_FZH0, M64_FZH1, M64_FQH0, M64_FQH1,
   MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G18
   MG_PGH0, MG_PGH1,                                                  // G34
   MG_L32, MG_U32, MG_B32,                                            // 64 x 16
@@ -76,6 +78,8 @@ enum TMap : int {
 };
 constexpr int kGpMaps = M_MASK0 - MG_X32H0;  // the GP maps (make_gp_maps encodes them)
 constexpr int kCgMaps = M64_RH0 - M32_RH0;  // maps of one precision's CG passes
+constexpr int kCgBase = M32_FZH0 - M32_RH0;  // of which make_maps encodes the first kCgBase
+constexpr int kTileMaps = kCgMaps - kCgBase;  // and the tile preconditioner's the rest
 
 enum Pass : int {
   P_NONE = 0,
@@ -87,7 +91,17 @@ enum Pass : int {
   P_CG_A = 6,      // w += alpha p; r += alpha Ap; ||r||^2
   P_CG_F = 7,      // fused CG step (2-D, staged): r += alpha Ap, w += alpha p,
                    // p = -r + beta p, Ap = A_FF p; ||r||^2, <p,Ap>, <r,Ap>, ||Ap||^2
+  P_CG_Z = 8,      // first step of a tile-preconditioned CG phase: r = g_F,
+                   // z = M^-1 r, <r, z>; p, Ap, q = M^-1 Ap and w set to 0
 };
+
+// Preconditioners of the CG phase (Opts.precond; the public gpcg_precond).
+enum Precond : int { PC_NONE = 0, PC_JACOBI = 1, PC_TILE = 2 };
+
+// The tile preconditioner's blocks: 64 x 8 points of one xy-plane, starting
+// at multiples of 64 in x and 8 in y.
+constexpr int kBlkX = 64;
+constexpr int kBlkY = 8;
 
 enum Dir : int { D_NEG_G = 0, D_W64 = 1, D_W32 = 2, D_ZERO = 3 };
 
@@ -113,7 +127,7 @@ struct Opts {
   double tau_abs, tau_rel, eta1, eta2, mu, eta2_shrink, eta2_floor, eta2_refine;
   double c;
   int max_outer, max_gp, max_cg, max_ls;
-  int mixed, refine, use_x0, precond;  // precond: 1 = point Jacobi in the CG phase
+  int mixed, refine, use_x0, precond;  // precond: a Precond value
 };
 
 // Mutable per-instance state, owned by the finalizer of each pass.
@@ -127,8 +141,12 @@ struct Ctl {
   unsigned arrive;
   int census_mode;   // CM_* : what the next P_CENSUS is for
   int stall;         // mixed phase: outer iterates without progress of ||pg||
+  int slow;          // mixed phase: consecutive iterates on an unchanged face without
+                     // a halving of ||pg|| (the FP32 noise floor)
+  int pad_c;
   int cg_finish;     // the pending P_CG_A only completes w before the search
   double best_pg2;   // mixed phase: smallest ||pg||^2 seen
+  double search_pg2; // mixed phase: ||pg||^2 after the previous outer iterate
   double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
   double pg2, nA, nB, xgb, gF2;  // census of the current iterate
   double alg_bytes;              // algorithmic HBM bytes of all passes so far
@@ -147,6 +165,10 @@ struct DevInst {
   const float *diag32, *cx32, *cy32, *cz32;
   const double* dinv;      // 1/diag (0 in pad columns): the point-Jacobi preconditioner
   const float* dinv32;
+  int tma_tile;            // bit 0 / bit 1: the FP64 / FP32 tile-preconditioner maps are valid
+  int pad_t;
+  double *z64[2], *q64[2];  // tile preconditioner: z = M^-1 r, q = M^-1 Ap (index pcur)
+  float *z32[2], *q32[2];
   double *x[2], *g[2];
   unsigned* mask[2];
   double *r64[2], *w64, *p64[2], *Ap64[2];  // r, p, Ap double-buffered (index pcur)

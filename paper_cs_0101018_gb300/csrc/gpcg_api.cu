@@ -168,6 +168,8 @@ struct gpcg_problem {
   size_t bytes64 = 0;
   void* arena32 = nullptr;
   size_t bytes32 = 0;
+  void* arena_t64 = nullptr;  // tile preconditioner: z[2], q[2] in FP64, then in FP32
+  void* arena_t32 = nullptr;
   double* ms_buf = nullptr;  // standalone masked product: CTA partials, result, counter, flag
   DevInst inst{};
   Scratch sc;
@@ -179,6 +181,8 @@ struct gpcg_problem {
     sc.release();
     cudaFree(arena64);
     cudaFree(arena32);
+    cudaFree(arena_t64);
+    cudaFree(arena_t32);
     cudaFree(ms_buf);
   }
 };
@@ -216,6 +220,11 @@ static size_t arena64_bytes(const gpcg_problem* p) {
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
   return (size_t)(p->kc + 1 + 7 + 9) * vec;
+}
+
+// Bytes of the tile preconditioner's vectors of one precision: z[2], q[2].
+static size_t arena_tile_bytes(const gpcg_problem* p, bool f32) {
+  return 4 * align256((f32 ? sizeof(float) : sizeof(double)) * (size_t)p->pn);
 }
 
 static void carve64(gpcg_problem* p) {
@@ -318,7 +327,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   const void* cy = f32 ? (const void*)I.cy32 : (const void*)I.cy;
   const void* w = f32 ? (const void*)I.w32 : (const void*)I.w64;
   const void* di = f32 ? (const void*)I.dinv32 : (const void*)I.dinv;
-  CUtensorMap m[kCgMaps];
+  CUtensorMap m[kCgBase];
   CUtensorMap* q = m;
   auto e = [&](const void* base, int bw, int bh) { return encode_map(q++, f32, base, p, bw, bh); };
   const bool ok =
@@ -336,7 +345,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
       e(d, 64, f) && e(cx, 64 + h, f) && e(cy, 64, f + 1) &&
       // 1/diag: FDIH, ADI
       e(di, 64 + 2 * h, f + 2) && e(di, 64, a);
-  if (!ok || q != m + kCgMaps) return false;
+  if (!ok || q != m + kCgBase) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -381,6 +390,28 @@ static bool make_mask_maps(gpcg_problem* p, cudaStream_t s) {
       return false;
   }
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * M_MASK0;
+  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return true;
+}
+
+// Encode the tile preconditioner's maps of one precision: FZH[2], FQH[2],
+// halo boxes of z and q like the fused CG step's FRH.
+static bool make_tile_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
+  if (!have_encode()) return false;
+  DevInst& I = p->inst;
+  const int h = f32 ? 4 : 2, f = f32 ? 16 : 8;
+  const void* zq[4] = {f32 ? (const void*)I.z32[0] : (const void*)I.z64[0],
+                       f32 ? (const void*)I.z32[1] : (const void*)I.z64[1],
+                       f32 ? (const void*)I.q32[0] : (const void*)I.q64[0],
+                       f32 ? (const void*)I.q32[1] : (const void*)I.q64[1]};
+  CUtensorMap m[kTileMaps];
+  static_assert(kTileMaps == 4, "FZH[2], FQH[2]");
+  for (int k = 0; k < 4; ++k)
+    if (!encode_map(&m[k], f32, zq[k], p, 64 + 2 * h, f + 2)) return false;
+  const int b0 = (f32 ? M32_RH0 : M64_RH0) + kCgBase;
+  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return false;
@@ -439,6 +470,40 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.dinv32 = dinv32;
   I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
   I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
+  return GPCG_OK;
+}
+
+// The tile preconditioner's vectors and maps for the CG precisions of a
+// solve (FP64 always; FP32 too in mixed precision), made on first use.  The
+// vectors start at zero and stay finite: the first fused step of a phase
+// multiplies them by alpha = beta = 0.
+static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s) {
+  DevInst& I = p->inst;
+  if (p->dim != 2)
+    return fail(GPCG_ERR_ARG, "the tile preconditioner is for 2-D problems only");
+  if (!I.tma64 || (mixed && !I.tma32))
+    return fail(GPCG_ERR_ARG, "the tile preconditioner needs the TMA-staged path");
+  for (int f32 = 0; f32 <= (mixed ? 1 : 0); ++f32) {
+    void*& a = f32 ? p->arena_t32 : p->arena_t64;
+    if (a) continue;
+    const size_t bytes = arena_tile_bytes(p, f32);
+    CK(cudaMalloc(&a, bytes));
+    CK(cudaMemsetAsync(a, 0, bytes, s));
+    const size_t vec = bytes / 4;
+    char* c = (char*)a;
+    for (int k = 0; k < 2; ++k) {
+      if (f32) {
+        I.z32[k] = (float*)(c + k * vec);
+        I.q32[k] = (float*)(c + (2 + k) * vec);
+      } else {
+        I.z64[k] = (double*)(c + k * vec);
+        I.q64[k] = (double*)(c + (2 + k) * vec);
+      }
+    }
+    if (!make_tile_maps(p, f32, s))
+      return fail(GPCG_ERR_CUDA, "tensor maps of the tile preconditioner could not be encoded");
+    I.tma_tile |= f32 ? 2 : 1;
+  }
   return GPCG_OK;
 }
 
@@ -558,7 +623,8 @@ static gpcg_status check_options(const gpcg_options* o) {
     return fail(GPCG_ERR_ARG, "bad iteration caps");
   if (o->precision != GPCG_FP64 && o->precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
-  if (o->precond != GPCG_PRECOND_NONE && o->precond != GPCG_PRECOND_JACOBI)
+  if (o->precond != GPCG_PRECOND_NONE && o->precond != GPCG_PRECOND_JACOBI &&
+      o->precond != GPCG_PRECOND_TILE)
     return fail(GPCG_ERR_ARG, "unknown preconditioner");
   return GPCG_OK;
 }
@@ -581,7 +647,9 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   r.mixed = o->precision == GPCG_MIXED;
   r.refine = o->refine ? 1 : 0;
   r.use_x0 = use_x0 ? 1 : 0;
-  r.precond = o->precond == GPCG_PRECOND_JACOBI ? 1 : 0;
+  r.precond = o->precond == GPCG_PRECOND_JACOBI ? PC_JACOBI
+              : o->precond == GPCG_PRECOND_TILE  ? PC_TILE
+                                                 : PC_NONE;
   return r;
 }
 
@@ -744,6 +812,9 @@ static gpcg_status prepare_instance(gpcg_problem* p, const gpcg_options* o, cuda
                                     DevInst* out) {
   gpcg_status st;
   if (o->precision == GPCG_MIXED && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if (o->precond == GPCG_PRECOND_TILE &&
+      (st = ensure_tile(p, o->precision == GPCG_MIXED, s)) != GPCG_OK)
+    return st;
   const bool use_x0 = o->x0 != nullptr;
   if (use_x0 && (st = copy_in(p, (double*)p->inst.x0, o->x0, s)) != GPCG_OK) return st;
   *out = p->inst;
@@ -1051,6 +1122,80 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
   return st;
 }
 
+extern "C" gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* free_mask,
+                                              const double* r, double* z, double* rz,
+                                              int precision, void* cuda_stream) {
+  if (!p || !free_mask || !r || !z) return fail(GPCG_ERR_ARG, "NULL argument");
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f32 = precision == GPCG_MIXED;
+  gpcg_status st;
+  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if ((st = ensure_tile(p, f32, s)) != GPCG_OK) return st;
+  std::vector<void*> temps;
+  auto dev_copy = [&](const void* src, size_t bytes, void** out) -> gpcg_status {
+    if (is_device_ptr(src)) {
+      *out = const_cast<void*>(src);
+      return GPCG_OK;
+    }
+    CK(cudaMalloc(out, bytes));
+    temps.push_back(*out);
+    CK(cudaMemcpyAsync(*out, src, bytes, cudaMemcpyHostToDevice, s));
+    return GPCG_OK;
+  };
+  do {
+    void *dm = nullptr, *dr = nullptr, *dz = z;
+    if ((st = dev_copy(free_mask, (size_t)p->n, &dm)) != GPCG_OK) break;
+    if ((st = dev_copy(r, sizeof(double) * (size_t)p->n, &dr)) != GPCG_OK) break;
+    const bool z_dev = is_device_ptr(z);
+    if (!z_dev) {
+      if (cudaMalloc(&dz, sizeof(double) * (size_t)p->n) != cudaSuccess) {
+        st = fail(GPCG_ERR_OOM, "temp alloc");
+        break;
+      }
+      temps.push_back(dz);
+    }
+    DevInst& I = p->inst;
+    // free-set words into mask[0] (the set-up also fills two CG scratch
+    // vectors the pass overwrites), r into the FP64 gradient g[0]
+    if (launch_spmv_setup(I, (const uint8_t*)dm, (const double*)dr, I.mask[0], I.r64[1],
+                          I.p64[1], false, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "set-up launch");
+      break;
+    }
+    if ((st = copy_in(p, I.g[0], (const double*)dr, s)) != GPCG_OK) break;
+    Ctl C = fresh_ctl();
+    C.pass = P_CG_Z;
+    C.cur = 0;
+    C.pcur = 0;
+    C.cg32 = f32 ? 1 : 0;
+    C.gp32 = 0;
+    C.hold = 1;
+    Ctl out;
+    if ((st = one_pass(p, C, s, &out)) != GPCG_OK) break;
+    const void* zb = f32 ? (const void*)I.z32[0] : (const void*)I.z64[0];
+    if (launch_unpad(I, zb, f32, (double*)dz, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "unpad launch");
+      break;
+    }
+    if (!z_dev &&
+        cudaMemcpyAsync(z, dz, sizeof(double) * (size_t)p->n, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "copy z");
+      break;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "synchronize: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    if (rz) *rz = out.red[0];
+    p->have = false;  // the solve's vectors were overwritten
+  } while (0);
+  for (void* t : temps) cudaFree(t);
+  return st;
+}
+
 extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps,
                                              int flush_l2, void* cuda_stream,
                                              double* ms_per_launch, double* bytes_per_launch) {
@@ -1197,11 +1342,12 @@ struct gpcg_server {
   }
 };
 
-static size_t footprint(const gpcg_stencil* A, bool mixed) {
+static size_t footprint(const gpcg_stencil* A, bool mixed, bool tile) {
   gpcg_problem tmp;
   geometry(A->dim, A->nx, A->ny, A->nz, &tmp);
   size_t b = arena64_bytes(&tmp);
   if (mixed) b += arena32_bytes(&tmp);
+  if (tile) b += arena_tile_bytes(&tmp, false) + (mixed ? arena_tile_bytes(&tmp, true) : 0);
   return b + 4096;
 }
 
@@ -1238,7 +1384,10 @@ extern "C" gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A,
   if (A->dim != 2 && A->dim != 3) return fail(GPCG_ERR_ARG, "dim must be 2 or 3");
   if (A->nx < 1 || A->ny < 1 || A->nz < 1 || (A->dim == 2 && A->nz != 1))
     return fail(GPCG_ERR_ARG, "bad grid size");
-  const size_t bytes = footprint(A, s->opt.precision == GPCG_MIXED);
+  if (s->opt.precond == GPCG_PRECOND_TILE && A->dim != 2)
+    return fail(GPCG_ERR_ARG, "the tile preconditioner is for 2-D problems only");
+  const size_t bytes =
+      footprint(A, s->opt.precision == GPCG_MIXED, s->opt.precond == GPCG_PRECOND_TILE);
   if (bytes > s->budget) return fail(GPCG_ERR_BUDGET, "request needs %zu bytes, budget %zu",
                                      bytes, s->budget);
   Req* r = new Req();

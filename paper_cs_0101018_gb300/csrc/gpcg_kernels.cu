@@ -127,6 +127,9 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
 }
 
+// Add a thread's FP32 partial of one chunk to its float-float accumulator.
+__device__ __forceinline__ void ff_acc(FF& a, float v) { a = ff_add(a, FF{v, 0.0f}); }
+
 // ------------------------------------------------------- TMA and mbarrier --
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -971,6 +974,226 @@ __device__ __forceinline__ void start_tile(const DevInst& I, double* x, float* x
   }
 }
 
+// ------------------------------------------------- tile preconditioner --
+//
+// M of the tile preconditioner (the analogue of the block Jacobi with one
+// block per processor of Sec. 6): one block per 64 x 8 tile of an xy-plane,
+// couplings between tiles dropped; each block solved approximately by one
+// symmetric zebra line Gauss-Seidel sweep on the free set -- the x-lines of
+// the tile's even rows, then its odd rows, then its even rows, each solved
+// exactly with the current values of the lines above and below on the
+// right-hand side.  Per tile M = (D + L) D^-1 (D + U), D the line
+// tridiagonals, L and U the couplings between lines in the order (even
+// rows, odd rows); M is symmetric positive definite.  A warp holds a line
+// (lane l: columns 2l and 2l+1).  M^-1 is applied in FP32 in every phase: it
+// only shapes the search directions, which stay in the phase's precision.
+
+// One line of a tile: b0, b1 the diagonal of the lane's points (1 off the
+// free set), cw the coupling of column 2l-1 to 2l, cm of 2l to 2l+1 (0 unless
+// both points are free; cw = 0 on lane 0, the tile's edge), cn / cs the
+// couplings of the two points to the row above / below inside the tile.
+struct TileLine {
+  float b0, b1, cw, cm, cn0, cn1, cs0, cs1;
+};
+
+// Solve the warp's line system
+//   cw x[2l-1] + b0 x[2l] + cm x[2l+1] = d0,  cm x[2l] + b1 x[2l+1] + ce x[2l+2] = d1,
+// ce = the next lane's cw (0 on lane 31).  Each lane eliminates its even
+// point and its east neighbour's, which leaves one equation per lane in
+// u_l = x[2l+1]; parallel cyclic reduction (Hockney) then removes the
+// couplings at distance 1, 2, 4, 8, 16 by shuffles, after which each u_l
+// stands alone; last the even points are recovered.  The system is a
+// principal submatrix of A (symmetric positive definite), so no pivot vanishes.
+__device__ __forceinline__ void line_solve(float b0, float b1, float cw, float cm, float d0,
+                                           float d1, float& x0, float& x1) {
+  const int lane = threadIdx.x & 31;
+  const float ie = __frcp_rn(b0);
+  float ce = __shfl_down_sync(FULL_MASK, cw, 1);
+  const float ie_n = __shfl_down_sync(FULL_MASK, ie, 1);
+  const float d0_n = __shfl_down_sync(FULL_MASK, d0, 1);
+  const float cm_n = __shfl_down_sync(FULL_MASK, cm, 1);
+  if (lane == 31) ce = 0.0f;
+  float a = -cm * cw * ie;
+  float b = b1 - cm * cm * ie - ce * ce * ie_n;
+  float c = -ce * cm_n * ie_n;
+  float d = d1 - cm * d0 * ie - ce * d0_n * ie_n;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const float ib = __frcp_rn(b);
+    float am = __shfl_up_sync(FULL_MASK, a, s), cmm = __shfl_up_sync(FULL_MASK, c, s);
+    float dm = __shfl_up_sync(FULL_MASK, d, s), ibm = __shfl_up_sync(FULL_MASK, ib, s);
+    float ap = __shfl_down_sync(FULL_MASK, a, s), cp = __shfl_down_sync(FULL_MASK, c, s);
+    float dp = __shfl_down_sync(FULL_MASK, d, s), ibp = __shfl_down_sync(FULL_MASK, ib, s);
+    if (lane < s) am = cmm = dm = ibm = 0.0f;
+    if (lane + s >= 32) ap = cp = dp = ibp = 0.0f;
+    const float k1 = a * ibm, k2 = c * ibp;
+    a = -k1 * am;
+    c = -k2 * cp;
+    b = b - k1 * cmm - k2 * ap;
+    d = d - k1 * dm - k2 * dp;
+  }
+  const float u = __fdiv_rn(d, b);
+  float um = __shfl_up_sync(FULL_MASK, u, 1);
+  if (lane == 0) um = 0.0f;
+  x1 = u;
+  x0 = (d0 - cw * um - cm * u) * ie;
+}
+
+// The zebra sweep over the chunk rows r0 .. r0+RPW-1 a warp holds (all warps
+// of the CTA take part; the chunk starts on a multiple of 8 rows, so the
+// parity of a chunk row is that of the grid row).  `scr`: a CTA buffer of
+// (chunk rows) x `pitch` floats through which the lines see their
+// neighbours; each warp writes only the rows it holds.  d: the right-hand
+// side (0 off the free set); x: M^-1 d on the warp's rows.
+template <int RPW>
+__device__ __forceinline__ void zebra_sweep(const TileLine (&L)[RPW], const float (&d)[RPW][2],
+                                            int r0, float* scr, int pitch, float (&x)[RPW][2]) {
+  const int c = 2 * (threadIdx.x & 31);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    if (((r0 + k) & 1) == 0) {
+      line_solve(L[k].b0, L[k].b1, L[k].cw, L[k].cm, d[k][0], d[k][1], x[k][0], x[k][1]);
+      *reinterpret_cast<float2*>(scr + (r0 + k) * pitch + c) = make_float2(x[k][0], x[k][1]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int h = 1; h >= 0; --h) {  // odd rows, then even rows again
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int row = r0 + k;
+      if ((row & 1) != h) continue;
+      float e0 = d[k][0], e1 = d[k][1];
+      if ((row & (kBlkY - 1)) != 0) {
+        const float2 v = *reinterpret_cast<const float2*>(scr + (row - 1) * pitch + c);
+        e0 -= L[k].cn0 * v.x;
+        e1 -= L[k].cn1 * v.y;
+      }
+      if ((row & (kBlkY - 1)) != kBlkY - 1) {
+        const float2 v = *reinterpret_cast<const float2*>(scr + (row + 1) * pitch + c);
+        e0 -= L[k].cs0 * v.x;
+        e1 -= L[k].cs1 * v.y;
+      }
+      line_solve(L[k].b0, L[k].b1, L[k].cw, L[k].cm, e0, e1, x[k][0], x[k][1]);
+      if (h == 1)
+        *reinterpret_cast<float2*>(scr + row * pitch + c) = make_float2(x[k][0], x[k][1]);
+    }
+    if (h == 1) __syncthreads();
+  }
+}
+
+// The line of row `row` (a chunk row) from its coefficients: dg = the two
+// diagonal entries, xw / xm = the couplings of columns 2l-1|2l and 2l|2l+1,
+// yn / ys = the couplings to the rows above / below; f = the free bits of the
+// lane's points in this row, fa / fb in the rows above / below.
+__device__ __forceinline__ TileLine tile_line(int row, float dg0, float dg1, float xw, float xm,
+                                              float yn0, float yn1, float ys0, float ys1,
+                                              unsigned f, unsigned fa, unsigned fb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned fw = __shfl_up_sync(FULL_MASK, f >> 1, 1) & 1u;  // column 2l-1
+  const bool f0 = f & 1u, f1 = (f >> 1) & 1u;
+  const bool top = (row & (kBlkY - 1)) == 0, bot = (row & (kBlkY - 1)) == kBlkY - 1;
+  TileLine L;
+  L.b0 = f0 ? dg0 : 1.0f;
+  L.b1 = f1 ? dg1 : 1.0f;
+  L.cw = (lane > 0 && f0 && fw) ? xw : 0.0f;
+  L.cm = (f0 && f1) ? xm : 0.0f;
+  L.cn0 = (!top && f0 && (fa & 1u)) ? yn0 : 0.0f;
+  L.cn1 = (!top && f1 && (fa & 2u)) ? yn1 : 0.0f;
+  L.cs0 = (!bot && f0 && (fb & 1u)) ? ys0 : 0.0f;
+  L.cs1 = (!bot && f1 && (fb & 2u)) ? ys1 : 0.0f;
+  return L;
+}
+
+// P_CG_Z on one 64 x 32 tile (register path, four rows per warp): the first
+// step of a tile-preconditioned CG phase: r_0 = g_F, z_0 = M^-1 r_0 and
+// rho_0 = <r_0, z_0>; p, Ap, q (buffer pcur) and w are set to 0, so that the
+// first fused step, run with alpha = beta = 0, forms p_0 = -z_0 and Ap_0.
+// The exchange buffer is the first TMA stage (no copy is in flight in a
+// register pass).
+template <class T>
+__device__ void cg_z_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
+                          float* scr, Acc& acc, FF* ffs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = warp * kRY;
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const bool f32 = sizeof(T) == 4;
+  const T* bd = f32 ? (const T*)I.diag32 : (const T*)I.diag;
+  const T* bx = f32 ? (const T*)I.cx32 : (const T*)I.cx;
+  const T* by = f32 ? (const T*)I.cy32 : (const T*)I.cy;
+  const unsigned* m = I.mask[S.cur];
+  auto bits = [&](int y) -> unsigned {
+    return (v0 && y >= 0 && y < I.ny) ? my_free_bits(I, m, y, z, e0) : 0u;
+  };
+  TileLine L[kRY];
+  float d[kRY][2], x[kRY][2];
+  T rv[kRY][2];
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + r0 + k;
+    const bool ok = y < I.ny && v0;
+    const unsigned f = ok ? bits(y) : 0u;
+    T dg[2] = {T(1), T(1)}, xm[2] = {T(0), T(0)}, yn[2] = {T(0), T(0)}, ys[2] = {T(0), T(0)};
+    double gv[2] = {0.0, 0.0};
+    if (ok) {
+      const long long i = pidx(I, y, z, e0);
+      ld2(bd, i, v0, v1, dg);
+      ld2(bx, i, v0, v1, xm);
+      if (y > 0) ld2(by, i - I.px, v0, v1, yn);
+      ld2(by, i, v0, v1, ys);
+      if (S.gp32) {
+        float gf[2];
+        ld2(I.g32[S.cur], i, v0, v1, gf);
+        gv[0] = gf[0];
+        gv[1] = gf[1];
+      } else {
+        ld2(I.g[S.cur], i, v0, v1, gv);
+      }
+    }
+    // coupling of column 2l-1 to 2l: the west lane's cx of its second point
+    const float xw = __shfl_up_sync(FULL_MASK, (float)xm[1], 1);
+    L[k] = tile_line(r0 + k, (float)dg[0], (float)dg[1], xw, (float)xm[0], (float)yn[0],
+                     (float)yn[1], (float)ys[0], (float)ys[1], f, ok ? bits(y - 1) : 0u,
+                     ok ? bits(y + 1) : 0u);
+    rv[k][0] = (f & 1u) ? (T)gv[0] : T(0);
+    rv[k][1] = (f & 2u) ? (T)gv[1] : T(0);
+    d[k][0] = (float)rv[k][0];
+    d[k][1] = (float)rv[k][1];
+  }
+  zebra_sweep<kRY>(L, d, r0, scr, 64, x);
+  const int pc = S.pcur;
+  T* r_out = f32 ? (T*)I.r32[pc] : (T*)I.r64[pc];
+  T* z_out = f32 ? (T*)I.z32[pc] : (T*)I.z64[pc];
+  T* p_out = f32 ? (T*)I.p32[pc] : (T*)I.p64[pc];
+  T* ap_out = f32 ? (T*)I.Ap32[pc] : (T*)I.Ap64[pc];
+  T* q_out = f32 ? (T*)I.q32[pc] : (T*)I.q64[pc];
+  T* w_out = f32 ? (T*)I.w32 : (T*)I.w64;
+  float s32 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + r0 + k;
+    if (y >= I.ny || !v0) continue;
+    const long long i = pidx(I, y, z, e0);
+    const T z0 = (T)x[k][0], z1 = (T)x[k][1];
+    st2(r_out, i, v0, v1, rv[k][0], rv[k][1]);
+    st2(z_out, i, v0, v1, z0, z1);
+    st2(p_out, i, v0, v1, T(0), T(0));
+    st2(ap_out, i, v0, v1, T(0), T(0));
+    st2(q_out, i, v0, v1, T(0), T(0));
+    st2(w_out, i, v0, v1, T(0), T(0));
+    if (f32) {
+      s32 = fmaf((float)rv[k][0], (float)z0, s32);
+      s32 = fmaf((float)rv[k][1], (float)z1, s32);
+    } else {
+      acc.s[0] = fma((double)rv[k][0], (double)z0, acc.s[0]);
+      acc.s[0] = fma((double)rv[k][1], (double)z1, acc.s[0]);
+    }
+  }
+  if (f32) ff_acc(ffs[0], s32);
+  __syncthreads();  // the exchange buffer is free again
+}
+
 // ---------------------------------------------------------------- control --
 
 __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
@@ -978,7 +1201,7 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
   // must read or write, once (documented per pass in the design notes)
   const double kc = (double)I.kc;
   const double sv = C.cg32 ? 4.0 : 8.0;
-  const double pj = I.opt.precond ? sv : 0.0;
+  const double pj = I.opt.precond == PC_JACOBI ? sv : 0.0;
   double per = 0.0;
   switch (pass) {
     case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
@@ -996,7 +1219,10 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
       per = sv * kc + (C.first_cg ? (C.gp32 ? 4.0 : 8.0) + 4.0 * sv : 4.0 * sv) + 0.125 + pj;
       break;
     case P_CG_A: per = 6.0 * sv + pj; break;
-    case P_CG_F: per = sv * kc + 8.0 * sv + 0.125 + pj; break;
+    case P_CG_F:  // tile preconditioner: z, q, p, r, Ap, w read and written
+      per = sv * kc + (I.opt.precond == PC_TILE ? 12.0 * sv : 8.0 * sv + pj) + 0.125;
+      break;
+    case P_CG_Z: per = (C.gp32 ? 4.0 : 8.0) + 3.0 * sv + 6.0 * sv + 0.125; break;
     default: break;
   }
   return per * (double)I.n;
@@ -1028,13 +1254,24 @@ __device__ void start_search(Ctl& C, int dir) {
   C.pass = P_TRIAL;
 }
 
+// Whether the instance's CG phase runs fused steps (P_CG_F): 2-D grids whose
+// tensor maps of the CG precision are valid (and, under the tile preconditioner, its maps).
+__device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
+  if (I.dim != 2 || I.tmaps == nullptr || !(C.cg32 ? I.tma32 : I.tma64)) return false;
+  return I.opt.precond != PC_TILE || ((I.tma_tile >> (C.cg32 ? 1 : 0)) & 1);
+}
+
 // Start a CG phase on the face of the current iterate (Eq. cg, cg2), w0 = 0.
 __device__ void begin_cg(const DevInst& I, Ctl& C) {
   C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
   C.cg_j = 0;
   C.cdmax = 0.0;
   C.cg_finish = 0;
-  if (I.opt.max_cg >= 1) {
+  if (I.opt.max_cg >= 1 && I.opt.precond == PC_TILE && cg_fused(I, C)) {
+    C.first_cg = 0;
+    C.beta = 0.0;
+    C.pass = P_CG_Z;
+  } else if (I.opt.max_cg >= 1) {
     C.first_cg = 1;
     C.beta = 0.0;
     C.pass = P_CG_B;
@@ -1079,11 +1316,6 @@ __device__ void on_converged(const DevInst& I, Ctl& C) {
   }
 }
 
-// Whether the instance's CG phase runs fused steps (P_CG_F): 2-D grids whose
-// tensor maps of the CG precision are valid.
-__device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
-  return I.dim == 2 && I.tmaps != nullptr && (C.cg32 ? I.tma32 : I.tma64);
-}
 
 // After alpha_j of a fused phase is known (C.rr = rho_j = <r_j, z_j>, z =
 // M^-1 r): the CG bookkeeping and Eq. cgstop1 of step j (decrease
@@ -1157,7 +1389,9 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         break;
       }
       C.best_pg2 = C.pg2;
+      C.search_pg2 = C.pg2;
       C.stall = 0;
+      C.slow = 0;
       C.pg0 = sqrt(C.pg2);
       C.tau = fmax(o.tau_abs, o.tau_rel * C.pg0);
       C.eta2 = o.eta2;
@@ -1218,11 +1452,22 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
             on_converged(I, C);
             break;
           }
-          if (C.gp32) {  // mixed phase: leave it when ||pg|| stops improving
+          if (C.gp32) {
+            // mixed phase: leave it when ||pg|| stops improving -- five
+            // iterates without a 2 % decrease of ||pg||^2, or two in a row on
+            // an unchanged face (Eq. cgstop3 holds) that do not halve ||pg||:
+            // there CG runs on a fixed system and only FP32 noise stops it
+            const bool face_kept = C.nB == C.nA;
+            const bool halved = C.pg2 < 0.25 * C.search_pg2;
+            C.search_pg2 = C.pg2;
+            C.slow = (face_kept && !halved) ? C.slow + 1 : 0;
             if (C.pg2 < 0.98 * C.best_pg2) {
               C.best_pg2 = C.pg2;
               C.stall = 0;
-            } else if (++C.stall >= 5) {
+            } else {
+              ++C.stall;
+            }
+            if (C.stall >= 5 || C.slow >= 2) {
               switch_fp64(C, CM_RESUME);
               break;
             }
@@ -1271,6 +1516,21 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         cg_advance(I, C, -pAp, red[2]);
       } else {
         C.pass = P_CG_A;
+      }
+      break;
+    }
+    case P_CG_Z: {
+      const double rz = red[0];  // rho_0 = <r_0, M^-1 r_0>
+      if (!isfinite(rz)) {
+        set_done(C, S_NUMERIC);
+      } else if (!(rz > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
+        start_search(C, D_ZERO);
+      } else {
+        // the first fused step, with alpha = beta = 0, forms p_0 and Ap_0
+        C.rr = rz;
+        C.alpha = 0.0;
+        C.beta = 0.0;
+        C.pass = P_CG_F;
       }
       break;
     }
@@ -1378,8 +1638,9 @@ __device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, in
                                           unsigned st, unsigned bar) {
   using G = ChunkGeo<T>;
   constexpr int o = -M32_RH0;
-  mbar_expect(bar, G::TX_A + (I.opt.precond ? G::SZ_A : 0));
-  if (I.opt.precond) tma_load2d(st + 4 * G::SZ_A, tmap(I, G::MB + o + M32_ADI), x0, row, bar);
+  mbar_expect(bar, G::TX_A + (I.opt.precond == PC_JACOBI ? G::SZ_A : 0));
+  if (I.opt.precond == PC_JACOBI)
+    tma_load2d(st + 4 * G::SZ_A, tmap(I, G::MB + o + M32_ADI), x0, row, bar);
   tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + o + M32_W), x0, row, bar);
   tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + o + M32_R0 + pcur), x0, row, bar);
   tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + o + M32_P0 + pcur), x0, row, bar);
@@ -1525,8 +1786,8 @@ __device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, in
                                           unsigned st, unsigned bar) {
   using G = GeoF<T>;
   constexpr int o = G::MB - M32_RH0;
-  mbar_expect(bar, G::TX + (I.opt.precond ? G::TX_DI : 0u));
-  if (I.opt.precond)
+  mbar_expect(bar, G::TX + (I.opt.precond == PC_JACOBI ? G::TX_DI : 0u));
+  if (I.opt.precond == PC_JACOBI)
     tma_load2d(st + G::OFF_DI, tmap(I, o + M32_FDIH), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
@@ -1623,8 +1884,6 @@ struct V2<double> {
   using type = double2;
 };
 
-// Add a thread's FP32 partial of one chunk to its float-float accumulator.
-__device__ __forceinline__ void ff_acc(FF& a, float v) { a = ff_add(a, FF{v, 0.0f}); }
 
 // P_CG_F on one staged chunk (rows yc .. yc+rows-1).  Sums: [0] ||r_j||^2,
 // [1] <p_j,Ap_j>, [2] <r_j,Ap_j>, [3] ||Ap_j||^2.  Each warp forms r_j and p_j
@@ -1745,6 +2004,197 @@ __device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char*
     acc.s[1] += (double)s_pap;
     acc.s[2] += (double)s_rap;
     acc.s[3] += (double)s_apap;
+  }
+}
+
+// P_CG_F under the tile preconditioner (2-D): the same CG step with
+// z = M^-1 r carried by its own recurrence, so that M^-1 is applied once per
+// step, to Ap, inside the chunk:
+//   r_j = r_{j-1} + alpha Ap_{j-1},  z_j = z_{j-1} + alpha q_{j-1}  (q = M^-1 Ap),
+//   w_j = w_{j-1} + alpha p_{j-1},  p_j = -z_j + beta p_{j-1},
+//   Ap_j = Z Z' A Z Z' p_j,  q_j = M^-1 Ap_j  (the zebra sweep over the chunk's
+//   8-row tiles), sums <r_j,z_j>, <p_j,Ap_j>, <z_j,Ap_j>, <Ap_j,q_j>.
+// The first step of a phase runs with alpha = beta = 0 on the vectors P_CG_Z
+// left.  z, q, p, r, Ap are read from buffer pcur and written to pcur^1.
+// Stage layout (T = float: f = 16 rows, h = 4; double: f = 8, h = 2): ZH | QH
+// | PH | RH | APH, each (64+2h) x (f+2) from (x0-h, y-1) | W 64 x f | D 64 x f |
+// CX (64+h) x f from x0-h | CY 64 x (f+1) from y-1.  Once a warp has read its
+// rows of W, those rows of the W box become its rows of the sweep's exchange
+// buffer (no other warp reads them).
+template <class T>
+struct GeoT {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = GeoF<T>::CH;
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int SZ_I = 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_Z = 0, OFF_Q = SZ_H, OFF_P = 2 * SZ_H, OFF_R = 3 * SZ_H;
+  static constexpr int OFF_AP = 4 * SZ_H, OFF_W = 5 * SZ_H;
+  static constexpr int OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX =
+      (5 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int PITCH = 64 * (int)sizeof(T) / 4;  // exchange row pitch (floats)
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
+};
+static_assert(GeoT<float>::END <= kOffMask && GeoT<double>::END <= kOffMask, "stage layout");
+static_assert(GeoT<float>::CH % kBlkY == 0 && GeoT<double>::CH % kBlkY == 0 &&
+                  kTX == kBlkX && kTY % kBlkY == 0,
+              "chunks and tiles hold whole preconditioner blocks");
+
+template <class T>
+__device__ __forceinline__ void issue_cgt(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = GeoT<T>;
+  constexpr int o = G::MB - M32_RH0;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_Z, tmap(I, o + M32_FZH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_Q, tmap(I, o + M32_FQH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_AP, tmap(I, o + M32_FAPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_W, tmap(I, o + M32_FW), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, o + M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, o + M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, o + M32_FCY), x0, yc - 1, bar);
+}
+
+// The free bits of this lane's two columns in chunk row `row` of the staged
+// mask box (0 outside the box's rows).
+__device__ __forceinline__ unsigned stage_row_bits(const unsigned char* st, int x0, int row) {
+  if (row < 0 || row >= 32) return 0u;
+  const unsigned* M = reinterpret_cast<const unsigned*>(st + kOffMask);
+  const int lane = threadIdx.x & 31;
+  return (M[row * 4 + ((x0 >> 5) & 3) + (lane >> 4)] >> ((2 * lane) & 31)) & 3u;
+}
+
+template <class T>
+__device__ __forceinline__ void cgt_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                          int rows, T alpha, T beta, const unsigned* fbits,
+                                          T* w, T* r_out, T* z_out, T* p_out, T* ap_out,
+                                          T* q_out, Acc& acc, FF* ff) {
+  using G = GeoT<T>;
+  using T2 = typename V2<T>::type;
+  constexpr int RPW = G::CH / kWarps;
+  const T* Z = reinterpret_cast<const T*>(st + G::OFF_Z);
+  const T* Q = reinterpret_cast<const T*>(st + G::OFF_Q);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* R = reinterpret_cast<const T*>(st + G::OFF_R);
+  const T* AP = reinterpret_cast<const T*>(st + G::OFF_AP);
+  const T* W = reinterpret_cast<const T*>(st + G::OFF_W);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int r0 = warp * RPW;  // first chunk row of this warp
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q): z_j, p_j there
+  T pn[RPW + 2][2], zn[RPW][2], rn[RPW][2], pw[RPW], pe[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + c;
+    const T2 zv = *reinterpret_cast<const T2*>(Z + b);
+    const T2 qv = *reinterpret_cast<const T2*>(Q + b);
+    const T2 pv = *reinterpret_cast<const T2*>(P + b);
+    const T za = fma(alpha, qv.x, zv.x), zb = fma(alpha, qv.y, zv.y);
+    pn[q][0] = fma(beta, pv.x, -za);
+    pn[q][1] = fma(beta, pv.y, -zb);
+    if (q >= 1 && q <= RPW) {
+      const int k = q - 1, ry = r0 + k;
+      zn[k][0] = za;
+      zn[k][1] = zb;
+      const T2 rv = *reinterpret_cast<const T2*>(R + b);
+      const T2 av = *reinterpret_cast<const T2*>(AP + b);
+      rn[k][0] = fma(alpha, av.x, rv.x);
+      rn[k][1] = fma(alpha, av.y, rv.y);
+      const T2 wv = *reinterpret_cast<const T2*>(W + ry * 64 + c);
+      if (ry < ylim)
+        st2(w, (long long)(yc + ry) * I.px + e0, v0, v1, fma(alpha, pv.x, wv.x),
+            fma(alpha, pv.y, wv.y));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
+    pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
+    const int b = (r0 + k + 1) * G::BW + G::H + c;
+    if (lane == 0) pw[k] = fma(beta, P[b - 1], -fma(alpha, Q[b - 1], Z[b - 1]));
+    if (lane == 31) pe[k] = fma(beta, P[b + 2], -fma(alpha, Q[b + 2], Z[b + 2]));
+  }
+  TileLine L[RPW];
+  float d[RPW][2], x[RPW][2];
+  T ap[RPW][2];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    const int q = k + 1;
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    // diag, west, east, south, north (the order of the register sweep)
+    T a0 = Dr[0] * pn[q][0];
+    a0 = fma(Xr[-1], pw[k], a0);
+    a0 = fma(Xr[0], pn[q][1], a0);
+    a0 = fma(Ys[0], pn[q - 1][0], a0);
+    a0 = fma(Yn[0], pn[q + 1][0], a0);
+    T a1 = Dr[1] * pn[q][1];
+    a1 = fma(Xr[0], pn[q][0], a1);
+    a1 = fma(Xr[1], pe[k], a1);
+    a1 = fma(Ys[1], pn[q - 1][1], a1);
+    a1 = fma(Yn[1], pn[q + 1][1], a1);
+    // rows past the grid arrive as zeros in the mask box: no free point
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    ap[k][0] = a0;
+    ap[k][1] = a1;
+    const float xw = __shfl_up_sync(FULL_MASK, (float)Xr[1], 1);
+    L[k] = tile_line(ry, (float)Dr[0], (float)Dr[1], xw, (float)Xr[0], (float)Ys[0],
+                     (float)Ys[1], (float)Yn[0], (float)Yn[1], fb,
+                     stage_row_bits(st, x0, ry - 1), stage_row_bits(st, x0, ry + 1));
+    d[k][0] = (float)a0;
+    d[k][1] = (float)a1;
+  }
+  // every warp has read its rows of W (above): they now carry the sweep
+  zebra_sweep<RPW>(L, d, r0, reinterpret_cast<float*>(st + G::OFF_W), G::PITCH, x);
+  T s_rz = T(0), s_pap = T(0), s_zap = T(0), s_aq = T(0);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    if (ry >= ylim) break;
+    const int q = k + 1;
+    const T q0 = (T)x[k][0], q1 = (T)x[k][1];
+    const long long i = (long long)(yc + ry) * I.px + e0;
+    st2(r_out, i, v0, v1, rn[k][0], rn[k][1]);
+    st2(z_out, i, v0, v1, zn[k][0], zn[k][1]);
+    st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
+    st2(ap_out, i, v0, v1, ap[k][0], ap[k][1]);
+    st2(q_out, i, v0, v1, q0, q1);
+    // points past nx hold zeros (the boxes are zero-filled there)
+    s_rz = fma(rn[k][0], zn[k][0], s_rz);
+    s_rz = fma(rn[k][1], zn[k][1], s_rz);
+    s_pap = fma(pn[q][0], ap[k][0], s_pap);
+    s_pap = fma(pn[q][1], ap[k][1], s_pap);
+    s_zap = fma(zn[k][0], ap[k][0], s_zap);
+    s_zap = fma(zn[k][1], ap[k][1], s_zap);
+    s_aq = fma(ap[k][0], q0, s_aq);
+    s_aq = fma(ap[k][1], q1, s_aq);
+  }
+  if (sizeof(T) == 4) {
+    ff_acc(ff[0], (float)s_rz);
+    ff_acc(ff[1], (float)s_pap);
+    ff_acc(ff[2], (float)s_zap);
+    ff_acc(ff[3], (float)s_aq);
+  } else {
+    acc.s[0] += (double)s_rz;
+    acc.s[1] += (double)s_pap;
+    acc.s[2] += (double)s_zap;
+    acc.s[3] += (double)s_aq;
   }
 }
 
@@ -2107,6 +2557,9 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
   }
   if (gp) {
     issue_gp(I, S, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
+    if (S.cg32) issue_cgt<float>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cgt<double>(I, S.pcur, c.x0, c.yc, st, bar);
   } else if (S.pass == P_CG_F) {
     if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
@@ -2138,9 +2591,17 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
         trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
                                I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
     }
+  } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
+    const int q = S.pcur ^ 1;
+    if (S.cg32)
+      cgt_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits, I.w32,
+                       I.r32[q], I.z32[q], I.p32[q], I.Ap32[q], I.q32[q], acc, ffs);
+    else
+      cgt_chunk<double>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                        I.z64[q], I.p64[q], I.Ap64[q], I.q64[q], acc, ffs);
   } else if (S.pass == P_CG_F) {
     const int q = S.pcur ^ 1;
-    const bool jac = I.opt.precond != 0;
+    const bool jac = I.opt.precond == PC_JACOBI;
     if (S.cg32 && jac)
       cgf_chunk<float, true>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits,
                              I.w32, I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
@@ -2165,13 +2626,13 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
     const int ylim = min(c.rows, I.ny - c.yc);
     const int q = S.pcur ^ 1;
     const int row = c.z * I.ny + c.yc;
-    if (S.cg32 && I.opt.precond)
+    if (S.cg32 && I.opt.precond == PC_JACOBI)
       cga_chunk<float, true>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
                              ffs[0]);
     else if (S.cg32)
       cga_chunk<float, false>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
                               ffs[0]);
-    else if (I.opt.precond)
+    else if (I.opt.precond == PC_JACOBI)
       cga_chunk<double, true>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
     else
       cga_chunk<double, false>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
@@ -2189,12 +2650,13 @@ __device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
     case P_CG_B: return first ? 3 : 1;
     case P_CG_A: return 1;
     case P_CG_F: return 4;
+    case P_CG_Z: return 1;
     default: return 0;
   }
 }
 
 __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
-                                         Acc& acc, FF* ffs) {
+                                         Acc& acc, FF* ffs, float* scr) {
   const int cur = S.cur, pcur = S.pcur;
   switch (S.pass) {
     case P_START:
@@ -2254,7 +2716,7 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
     case P_CG_B: {
       const float* g32 = S.gp32 ? I.g32[cur] : nullptr;
       // point Jacobi (z = r / diag) runs in its own instantiations
-      const bool jac = I.opt.precond != 0;
+      const bool jac = I.opt.precond == PC_JACOBI;
       if (S.cg32) {
         float* p_new = I.p32[pcur ^ 1];
         float* ap = I.Ap32[pcur ^ 1];
@@ -2290,14 +2752,18 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       }
       break;
     }
+    case P_CG_Z:
+      if (S.cg32) cg_z_tile<float>(I, S, x0, y0, z, scr, acc, ffs);
+      else cg_z_tile<double>(I, S, x0, y0, z, scr, acc, ffs);
+      break;
     case P_CG_A:
-      if (S.cg32 && I.opt.precond)
+      if (S.cg32 && I.opt.precond == PC_JACOBI)
         cg_a_tile<float, true>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
                                I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
       else if (S.cg32)
         cg_a_tile<float, false>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
                                 I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
-      else if (I.opt.precond)
+      else if (I.opt.precond == PC_JACOBI)
         cg_a_tile<double, true>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur],
                                 I.Ap64[pcur], I.dinv, S.alpha, x0, y0, z, acc, ffs);
       else
@@ -2422,7 +2888,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       for (int tile = t_lo; tile < t_hi; ++tile) {
         const int rest = tile / I.tiles_x;
         run_tile(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY, rest / I.tiles_y, acc,
-                 ffs);
+                 ffs, reinterpret_cast<float*>(stage0));
       }
     } else {
       // TMA pipeline: the group is a range of 8-row strips (4 per tile), cut
@@ -2436,6 +2902,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
       const int ch = chunk_rows(S, gp);
       const int rpw = ch / kWarps;
+      // chunks that write to their stage (and have block barriers inside)
+      const bool writes_stage =
+          !gp && (S.pass == P_CG_B ||
+                  (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
       Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
       // the current chunk and the next two (h1, h2: they exist)
@@ -2457,7 +2927,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       unsigned fbits[4] = {0u, 0u, 0u, 0u};
       for (;;) {
         if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
-          if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp)
+          if (writes_stage)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           if (kDepth == 2)
             issue_chunk(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2), want_bits);
@@ -2468,7 +2938,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
         bool failed;
         if (ok && want_bits) stage_bits(st, c0.x0, rpw, gp, fbits);
-        if ((S.pass == P_CG_B || (S.pass == P_CG_F && !S.cg32)) && !gp) {
+        if (writes_stage) {
           // the chunk has a barrier inside: agree on the wait first
           failed = __syncthreads_or(!ok);
           if (!failed) run_chunk(I, S, gp, st, c0, fbits, acc, ffs);
@@ -2503,7 +2973,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
     // butterfly).  FP32 passes reduce their float-float accumulators in
     // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
-    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F) ? S.cg32 != 0
+    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
+                        S.pass == P_CG_Z)
+                           ? S.cg32 != 0
                                                               : (S.pass != P_START && S.gp32 != 0);
     const int ns = n_sums(S.pass, S.first_cg, S.gp32);
     for (int k = 0; k < ns; ++k) {

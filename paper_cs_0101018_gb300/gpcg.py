@@ -18,7 +18,7 @@ from . import _build
 OK, ERR_ARG, ERR_INFEASIBLE, ERR_NUMERIC, ERR_OOM, ERR_BUDGET, ERR_CUDA = 0, 1, 2, 3, 4, 5, 6
 ERR_MAXIT, ERR_LINESEARCH, ERR_TIMEOUT, ERR_PENDING, ERR_CANCELLED = 7, 8, 9, 10, 11
 FP64, MIXED = 0, 1
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_TILE = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_INFEASIBLE", 3: "ERR_NUMERIC", 4: "ERR_OOM",
                 5: "ERR_BUDGET", 6: "ERR_CUDA", 7: "ERR_MAXIT", 8: "ERR_LINESEARCH",
@@ -76,6 +76,8 @@ _SIGNATURES = [
     ("gpcg_result", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(gpcg_stats)]),
     ("gpcg_masked_spmv", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+    ("gpcg_tile_precondition", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("gpcg_masked_spmv_noalloc", C.c_int, [C.POINTER(gpcg_stencil), C.c_void_p, C.c_void_p,
@@ -231,6 +233,19 @@ def gpcg_masked_spmv(prob: Problem, free_mask, p, precision=FP64, stream=None):
     _check(load().gpcg_masked_spmv(prob.handle, _ptr(fm), _ptr(p), _ptr(y), C.byref(pap),
                                    precision, sp))
     return y, pap.value
+
+
+def gpcg_tile_precondition(prob: Problem, free_mask, r, precision=FP64, stream=None):
+    """z = M^-1 r of the tile preconditioner; returns (z, <r, z>)."""
+    fm = np.ascontiguousarray(free_mask, dtype=np.uint8) if isinstance(free_mask, np.ndarray) \
+        else free_mask
+    r = _f64(r)
+    z = np.empty(prob.n) if isinstance(r, np.ndarray) else r.new_empty(r.shape)
+    rz = C.c_double()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(load().gpcg_tile_precondition(prob.handle, _ptr(fm), _ptr(r), _ptr(z), C.byref(rz),
+                                         precision, sp))
+    return z, rz.value
 
 
 def gpcg_time_masked_spmv(prob: Problem, precision=FP64, reps=20, flush_l2=True, stream=None):

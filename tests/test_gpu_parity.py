@@ -124,6 +124,89 @@ def test_jacobi_pcg_matches_oracle(k, prec):
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
 
+@pytest.mark.parametrize("shape", [(64, 32), (130, 70), (200, 9), (1, 37), (37, 1), (65, 17),
+                                   (3, 200)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tile_precondition_matches_oracle(shape, prec):
+    """z = M^-1 r of the tile preconditioner (64 x 8 tiles, one symmetric zebra
+    line sweep on the free set) element by element against the oracle.  M^-1
+    is applied in FP32 on the GPU: each line solve and line update loses a few
+    FP32 roundings times the lines' condition (below 100 for these weights),
+    so |z - z_oracle| <= 1e-4 max|z_oracle|; exact zeros off the free set."""
+    qp = gi.grid_qp_2d(*shape, seed=500 + shape[0], shift=0.02, sigma=1.0)
+    free = gi.uniform(501, 2, qp.n) < 0.7
+    r = gi.normal(501, 3, qp.n)
+    ref = oracle.precondition(qp, free, r, oracle.PRECOND_TILE)
+    prob = g.gpcg_problem_create(qp)
+    z, rz = g.gpcg_tile_precondition(prob, free, r, precision=prec)
+    assert np.all(z[~free] == 0.0)
+    scale = max(float(np.max(np.abs(ref))), 1e-300)
+    assert float(np.max(np.abs(z - ref))) <= 1e-4 * scale
+    assert np.isclose(rz, float(r[free] @ ref[free]), rtol=1e-4)
+
+
+def test_tile_precondition_journal_bearing():
+    """The anisotropic journal bearing (x-couplings about 10x the y-couplings),
+    all points free and with a mask, against the oracle."""
+    qp = gi.journal_bearing(150, 40, 0.9)
+    r = gi.normal(502, 3, qp.n)
+    prob = g.gpcg_problem_create(qp)
+    for free in (np.ones(qp.n, bool), gi.uniform(502, 2, qp.n) < 0.6):
+        ref = oracle.precondition(qp, free, r, oracle.PRECOND_TILE)
+        z, _ = g.gpcg_tile_precondition(prob, free, r)
+        assert float(np.max(np.abs(z - ref))) <= 1e-4 * float(np.max(np.abs(ref)))
+
+
+TILE = [PROBLEMS[k] for k in (0, 2, 5, 8, 10, 14, 17, 20, 24, 29, 30)]
+
+
+@pytest.mark.parametrize("k", range(len(TILE)))
+@pytest.mark.parametrize("prec", [0, 1])
+def test_tile_pcg_matches_oracle(k, prec):
+    """CG phase under the tile preconditioner against the oracle running the
+    same preconditioner in FP64.  M^-1 is applied in FP32 on the GPU, so the
+    iteration paths may differ: both sides solve to ||pg|| <= 1e-12 ||pg(x0)||,
+    where differently preconditioned oracle runs agree to ~1e-12, and x must
+    agree to the usual 1e-9 (FP64) / 1e-5 (mixed)."""
+    qp = TILE[k]
+    ref = oracle.solve(qp, tau_rel=1e-12, precond=oracle.PRECOND_TILE)
+    status, x, st = _solve(qp, tau_rel=1e-12, precision=prec, precond=g.PRECOND_TILE)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    c = oracle.census(qp, x)
+    assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
+    # fewer CG steps than without a preconditioner on the larger grids (FP64;
+    # at this tolerance the mixed mode's step count is set by its FP32 phase)
+    if qp.n >= 2000 and prec == g.FP64:
+        plain = oracle.solve(qp, tau_rel=1e-12)
+        assert st["cg_iters"] < plain.stats["cg_iters"]
+
+
+def test_tile_preconditioner_needs_a_2d_staged_problem():
+    qp = gi.grid_qp_3d(17, 9, 6, seed=503, shift=0.02, sigma=0.5, bounds="box1")
+    prob = g.gpcg_problem_create(qp)
+    status = g.gpcg_solve(prob, g.default_options(precond=g.PRECOND_TILE), check=False)
+    assert status == g.ERR_ARG
+
+
+@pytest.mark.parametrize("shape", [(64, 48), (130, 70)])
+@pytest.mark.parametrize("eps", [0.1, 0.9])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_journal_bearing_tile_matches_oracle(shape, eps, prec):
+    """The journal bearing with the tile preconditioner (its intended use:
+    strong couplings along x)."""
+    qp = gi.journal_bearing(*shape, eps)
+    ref = oracle.solve(qp, tau_abs=1e-12, tau_rel=0.0)
+    status, x, st = _solve(qp, tau_abs=1e-12, tau_rel=0.0, precision=prec,
+                           precond=g.PRECOND_TILE)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all(x >= 0)
+
+
 @pytest.mark.parametrize("shape", [(64, 48), (130, 70)])
 @pytest.mark.parametrize("eps", [0.1, 0.9])
 @pytest.mark.parametrize("prec", [0, 1])
