@@ -252,15 +252,17 @@ def run_ours(args):
     # mixed precision (headline) and plain FP64
     ms_mx, st_mx, clk_mx, wall_mx = timed(g.MIXED, args.steps, args.warmup)
     ms_64, st_64, clk_64, wall_64 = timed(g.FP64, args.steps, args.warmup)
-    # the point-Jacobi preconditioned CG phase (Sec. 6) on the same workload
-    jac = {}
-    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
-        msj, stj, _, _ = timed(prec, max(1, min(args.steps, 5)), 1, precond=g.PRECOND_JACOBI)
-        tj = _max_over_ranks(ws, sum(msj) / 1000.0)
-        jac[name] = {"value": ws * len(msj) / tj, "unit": "solves/s",
-                     "ms_per_step": sum(msj) / len(msj),
-                     "solve": {k: stj[k] for k in ("outer_iters", "gp_iters", "cg_iters",
-                                                   "passes", "pg_norm", "tau")}}
+    # the preconditioned CG phases (Sec. 6) on the same workload: point
+    # Jacobi and the tile block Jacobi (zebra line sweep in 64 x 8 tiles)
+    jac, tile = {}, {}
+    for out, pc in ((jac, g.PRECOND_JACOBI), (tile, g.PRECOND_TILE)):
+        for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+            msj, stj, _, _ = timed(prec, max(1, min(args.steps, 5)), 1, precond=pc)
+            tj = _max_over_ranks(ws, sum(msj) / 1000.0)
+            out[name] = {"value": ws * len(msj) / tj, "unit": "solves/s",
+                         "ms_per_step": sum(msj) / len(msj),
+                         "solve": {k: stj[k] for k in ("outer_iters", "gp_iters", "cg_iters",
+                                                       "passes", "pg_norm", "tau")}}
 
     tot_mx = _max_over_ranks(ws, sum(ms_mx) / 1000.0)
     tot_64 = _max_over_ranks(ws, sum(ms_64) / 1000.0)
@@ -311,15 +313,18 @@ def run_ours(args):
     del pbig, big
 
     # the journal bearing problem of Sec. 5 (finite differences, 1600^2 like
-    # the paper's n = 2.56e6; tau = 1e-4 absolute, x0 = l), with the
-    # point-Jacobi preconditioned CG phase
+    # the paper's n = 2.56e6; tau = 1e-4 absolute, x0 = l), with the point-
+    # Jacobi and the tile preconditioned CG phases
     jb = {}
     for eps in (0.1, 0.9):
         jqp = gi.journal_bearing(1600, 1600, eps)
         jp = g.gpcg_problem_create(jqp)
-        for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
-            jo = g.default_options(tau_abs=1e-4, tau_rel=0.0, precision=prec,
-                                   precond=g.PRECOND_JACOBI, stream=stream)
+        for name, prec, pc in (("mixed_jacobi", g.MIXED, g.PRECOND_JACOBI),
+                               ("mixed_tile", g.MIXED, g.PRECOND_TILE),
+                               ("fp64_jacobi", g.FP64, g.PRECOND_JACOBI),
+                               ("fp64_tile", g.FP64, g.PRECOND_TILE)):
+            jo = g.default_options(tau_abs=1e-4, tau_rel=0.0, precision=prec, precond=pc,
+                                   stream=stream)
             g.gpcg_solve(jp, jo)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -381,6 +386,7 @@ def run_ours(args):
                                                  "ls_trials", "passes", "pg_norm", "tau")}},
         "mixed_over_fp64": value / value_64,
         "jacobi": jac,
+        "tile": tile,
         "journal_bearing_1600": jb,
         "roofline": roof_mx,
         "spmv": spmv,
