@@ -408,11 +408,12 @@ def run_profile(args):
     import torch
     import paper_cs_0101018_gb300 as g
     prec = g.MIXED if args.precision == "mixed" else g.FP64
-    qp = gi.single_large()
+    pc = {"none": g.PRECOND_NONE, "jacobi": g.PRECOND_JACOBI, "tile": g.PRECOND_TILE}[args.precond]
+    qp = gi.single_large(args.side)
     prob = g.gpcg_problem_create(qp)
     if args.profile == "solve":
         for _ in range(args.steps):
-            g.gpcg_solve(prob, g.default_options(tau_rel=TAU_REL, precision=prec))
+            g.gpcg_solve(prob, g.default_options(tau_rel=TAU_REL, precision=prec, precond=pc))
         _, st = g.gpcg_result(prob)
         print(json.dumps({"profile": "solve", "precision": args.precision, "passes": st["passes"],
                           "launches": st["launches"]}))
@@ -432,6 +433,10 @@ def main():
     ap.add_argument("--profile", choices=["solve", "spmv"], default=None,
                     help="run a small fixed workload for a profiler capture instead")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precond", choices=["none", "jacobi", "tile"], default="none",
+                    help="preconditioner of the CG phase (profile workloads only)")
+    ap.add_argument("--side", type=int, default=1600,
+                    help="grid side of the profile workloads (the benchmark QP at 1600)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
