@@ -345,6 +345,34 @@ def run_ours(args):
                 "pg_norm": sj["pg_norm"], "status": sj["status"]}
         del jp, jqp
 
+    # the reduced system applied through the bitmask (the default) or
+    # extracted into compact numbering (Sec. 4's A_k), on 1600^2 QPs whose
+    # solutions are free on a disc covering the given fraction of the grid
+    ablation = {}
+    for frac in (0.01, 0.1, 0.3, 0.9):
+        dqp = gi.disc_free_qp(1600, frac)
+        dp = g.gpcg_problem_create(dqp)
+        row = {}
+        for name, cs in (("masked", g.CG_MASKED), ("extracted", g.CG_EXTRACTED)):
+            do = g.default_options(tau_rel=TAU_REL, precision=g.MIXED, cg_system=cs,
+                                   stream=stream)
+            g.gpcg_solve(dp, do)
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.gpcg_solve(dp, do)
+                e1.record(stream)
+                e1.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            xd, sd = g.gpcg_result(dp)
+            row[name] = {"ms": best, "cg_iters": sd["cg_iters"], "passes": sd["passes"],
+                         "alg_GB": sd["alg_bytes"] / 1e9}
+        row["free_fraction"] = float(np.mean(xd > 0))
+        ablation[f"disc_{frac}"] = row
+        del dp, dqp
+
     # end to end through the C ABI from pinned host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(getattr(qp, k))).pin_memory()
            for k in ("diag", "cx", "cy", "b", "l", "u")}
@@ -394,6 +422,7 @@ def run_ours(args):
         "jacobi": jac,
         "tile": tile,
         "journal_bearing_1600": jb,
+        "cg_system_1600_mixed": ablation,
         "roofline": roof_mx,
         "spmv": spmv,
         "solve": {k: st_mx[k] for k in ("outer_iters", "gp_iters", "cg_iters", "ls_trials",

@@ -299,3 +299,21 @@ def journal_bearing(nx: int, ny: int, eps: float, half_width: float = 10.0) -> Q
     return QP(2, nx, ny, 1, diag, cx, cy, None, b, np.zeros(n), np.full(n, np.inf),
               shift=0.0, name=f"journal_bearing_{nx}x{ny}_eps{eps}",
               meta={"eps": eps, "half_width": half_width, "h1": h1, "h2": h2})
+
+
+def disc_free_qp(side: int, free_frac: float, seed: int = 7, shift: float = 1e-2) -> QP:
+    """A side x side QP whose solution is free on a disc covering about
+    `free_frac` of the grid and at its lower bound elsewhere: the 5-point
+    weighted Laplacian of grid_qp_2d, l = 0, u = +inf, b = -1 - |N(0,1)| / 4
+    inside the disc (pulling x above 0) and +1 + |N(0,1)| / 4 outside (pressing
+    it onto the bound).  For the masked-versus-extracted reduced system
+    comparison across free fractions."""
+    qp = grid_qp_2d(side, side, seed=seed, shift=shift, bounds="lower0",
+                    name=f"disc_{side}_{free_frac}")
+    iy, ix = np.divmod(np.arange(side * side), side)
+    c = (side - 1) / 2.0
+    rad = side * np.sqrt(free_frac / np.pi)
+    inside = (ix - c) ** 2 + (iy - c) ** 2 <= rad * rad
+    mag = 1.0 + np.abs(normal(seed, 11, side * side)) / 4.0
+    qp.b = np.where(inside, -mag, mag)
+    return qp

@@ -111,8 +111,22 @@ typedef struct {
     void* cuda_stream;      /* cudaStream_t the solve is ordered on */
     double lambda_min;      /* optional lower bound on lambda_min(A), for err_bound */
     int precond;            /* gpcg_precond: preconditioner of the CG phase (Sec. 6) */
-    int reserved;
+    int cg_system;          /* gpcg_cg_system: how the CG phase applies A_k (Sec. 4) */
 } gpcg_options;
+
+/* How the CG phase works on the reduced system A_k = Z_k' A Z_k (Sec. 4).
+ *   GPCG_CG_MASKED (default): full-length vectors, the free set a bitmask
+ *     applied inside the stencil product (the paper's alternative technique).
+ *   GPCG_CG_EXTRACTED: A_k is extracted, as the paper's design does: the free
+ *     points get a compact numbering (tiles in order, rows within a tile,
+ *     columns within a row), A_k is stored as rows of a diagonal and 2*dim
+ *     neighbour slots in that numbering, and CG runs on compact vectors; w is
+ *     scattered back before the projected search.  Three extra passes per CG
+ *     phase; pays when few points are free.  Not with GPCG_PRECOND_TILE
+ *     (GPCG_ERR_ARG).  The first solve with it allocates the compact arrays
+ *     (capacity n: 4 + 4 dim bytes per point plus (9 + 2 dim) values per
+ *     point of each CG precision). */
+typedef enum { GPCG_CG_MASKED = 0, GPCG_CG_EXTRACTED = 1 } gpcg_cg_system;
 
 /* Preconditioners of the CG phase on the reduced system (Sec. 6 compares the
  * diagonal one with block Jacobi); the decrease of Eq. cgstop1 is then
@@ -195,6 +209,21 @@ gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask, const do
  * Arrays: n values each, host or device.  2-D problems on the staged path
  * only (GPCG_ERR_ARG otherwise).  Overwrites the problem's CG vectors, so
  * gpcg_result reports GPCG_ERR_PENDING until the next solve. */
+/* The explicit reduced system of GPCG_CG_EXTRACTED for the free set given by
+ * free_mask (one byte per point, nonzero = free), built by the same passes
+ * as in a solve: *m receives the number of free points; fidx (m values) the
+ * point (row-major index ix + nx*(iy + ny*iz)) of each compact index; diag
+ * (m values) the diagonal; nb and val (2*dim*m values, slot-major: slot j of
+ * compact row k at j*m + k; slots x-1, x+1, y-1, y+1, z-1, z+1) the
+ * neighbours' compact indices and couplings, a slot outside the free set
+ * holding the row's own index and 0.  Host arrays of capacity n (fidx,
+ * diag) and 2*dim*n (nb, val).  precision GPCG_MIXED returns the FP32
+ * rows widened to FP64.  Overwrites the problem's CG vectors (gpcg_result
+ * reports GPCG_ERR_PENDING until the next solve). */
+gpcg_status gpcg_reduced_system(gpcg_problem* p, const uint8_t* free_mask, int precision,
+                                int64_t* m, int32_t* fidx, double* diag, int32_t* nb,
+                                double* val, void* cuda_stream);
+
 gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* free_mask, const double* r,
                                    double* z, double* rz, int precision, void* cuda_stream);
 

@@ -93,7 +93,18 @@ enum Pass : int {
                    // p = -r + beta p, Ap = A_FF p; ||r||^2, <p,Ap>, <r,Ap>, ||Ap||^2
   P_CG_Z = 8,      // first step of a tile-preconditioned CG phase: r = g_F,
                    // z = M^-1 r, <r, z>; p, Ap, q = M^-1 Ap and w set to 0
+  // explicit reduced system (option extract, Sec. 4's extraction of A_k):
+  P_RX_COUNT = 9,  // free points per group -> group offsets of the compact numbering
+  P_RX_MAP = 10,   // compact index of every free point, r_0 = g_F (compact), w = 0
+  P_RX_BUILD = 11, // rows of A_FF in compact numbering; z_0, rho_0; p, Ap, w = 0
+  P_RCG = 12,      // fused CG step on the compact system
+  P_RW = 13,       // w (full length) = the compact w_{j+1}, before the search
 };
+
+// Neighbour slots of a row of the explicit reduced system: x-1, x+1, y-1,
+// y+1 (, z-1, z+1); a slot whose neighbour is outside the free set holds the
+// row's own compact index and a zero coupling.
+constexpr int kMaxNb = 6;
 
 // Preconditioners of the CG phase (Opts.precond; the public gpcg_precond).
 enum Precond : int { PC_NONE = 0, PC_JACOBI = 1, PC_TILE = 2 };
@@ -128,6 +139,7 @@ struct Opts {
   double c;
   int max_outer, max_gp, max_cg, max_ls;
   int mixed, refine, use_x0, precond;  // precond: a Precond value
+  int extract, pad_o;  // extract: the CG phase runs on the explicit reduced system
 };
 
 // Mutable per-instance state, owned by the finalizer of each pass.
@@ -145,6 +157,8 @@ struct Ctl {
                      // a halving of ||pg|| (the FP32 noise floor)
   int pad_c;
   int cg_finish;     // the pending P_CG_A only completes w before the search
+  int m;             // explicit reduced system: free points of the current phase
+  int pad_m;
   double best_pg2;   // mixed phase: smallest ||pg||^2 seen
   double search_pg2; // mixed phase: ||pg||^2 after the previous outer iterate
   double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
@@ -169,6 +183,14 @@ struct DevInst {
   int pad_t;
   double *z64[2], *q64[2];  // tile preconditioner: z = M^-1 r, q = M^-1 Ap (index pcur)
   float *z32[2], *q32[2];
+  // explicit reduced system (capacity n): compact index of each point (padded
+  // layout, -1 off the free set), point of each compact index, group offsets,
+  // neighbour slots [kMaxNb][n]; per precision the rows (diagonal, couplings
+  // [kMaxNb][n], 1/diagonal) and the compact CG vectors (r, p, Ap by pcur)
+  int *cidx, *fidx, *goff, *rnb;
+  double *rd64, *rv64, *rdi64, *rc64[2], *pc64[2], *apc64[2], *wc64;
+  float *rd32, *rv32, *rdi32, *rc32[2], *pc32[2], *apc32[2], *wc32;
+  int rx64, rx32;          // the FP64 / FP32 compact arrays exist
   double *x[2], *g[2];
   unsigned* mask[2];
   double *r64[2], *w64, *p64[2], *Ap64[2];  // r, p, Ap double-buffered (index pcur)

@@ -170,6 +170,9 @@ struct gpcg_problem {
   size_t bytes32 = 0;
   void* arena_t64 = nullptr;  // tile preconditioner: z[2], q[2] in FP64, then in FP32
   void* arena_t32 = nullptr;
+  void* arena_xi = nullptr;   // explicit reduced system: index arrays, then values
+  void* arena_x64 = nullptr;
+  void* arena_x32 = nullptr;
   double* ms_buf = nullptr;  // standalone masked product: CTA partials, result, counter, flag
   DevInst inst{};
   Scratch sc;
@@ -183,6 +186,9 @@ struct gpcg_problem {
     cudaFree(arena32);
     cudaFree(arena_t64);
     cudaFree(arena_t32);
+    cudaFree(arena_xi);
+    cudaFree(arena_x64);
+    cudaFree(arena_x32);
     cudaFree(ms_buf);
   }
 };
@@ -220,6 +226,19 @@ static size_t arena64_bytes(const gpcg_problem* p) {
 static size_t arena32_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
   return (size_t)(p->kc + 1 + 7 + 9) * vec;
+}
+
+// Bytes of the explicit reduced system: the index arrays (cidx over the padded
+// layout, fidx, group offsets, 2*dim neighbour slots per point) and, per
+// precision, the rows (diagonal, 2*dim couplings, 1/diagonal) and the compact
+// vectors r[2], p[2], Ap[2], w.
+static size_t arena_rx_index_bytes(const gpcg_problem* p) {
+  return align256(sizeof(int) * (size_t)p->pn) + align256(sizeof(int) * (size_t)p->n) +
+         align256(sizeof(int) * kMaxGroups) + align256(sizeof(int) * 2 * p->dim * (size_t)p->n);
+}
+static size_t arena_rx_value_bytes(const gpcg_problem* p, bool f32) {
+  const size_t vec = align256((f32 ? sizeof(float) : sizeof(double)) * (size_t)p->n);
+  return (size_t)(9 + 2 * p->dim) * vec;
 }
 
 // Bytes of the tile preconditioner's vectors of one precision: z[2], q[2].
@@ -507,6 +526,61 @@ static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s) {
   return GPCG_OK;
 }
 
+// The explicit reduced system's arrays for the CG precisions of a solve,
+// made on first use.
+static gpcg_status ensure_extract(gpcg_problem* p, bool mixed, cudaStream_t s) {
+  DevInst& I = p->inst;
+  if (p->pn >= (1LL << 31))
+    return fail(GPCG_ERR_ARG, "the explicit reduced system needs fewer than 2^31 points");
+  if (!p->arena_xi) {
+    const size_t bytes = arena_rx_index_bytes(p);
+    CK(cudaMalloc(&p->arena_xi, bytes));
+    CK(cudaMemsetAsync(p->arena_xi, 0, bytes, s));
+    char* a = (char*)p->arena_xi;
+    I.cidx = (int*)a;
+    a += align256(sizeof(int) * (size_t)p->pn);
+    I.fidx = (int*)a;
+    a += align256(sizeof(int) * (size_t)p->n);
+    I.goff = (int*)a;
+    a += align256(sizeof(int) * kMaxGroups);
+    I.rnb = (int*)a;
+  }
+  for (int f32 = 0; f32 <= (mixed ? 1 : 0); ++f32) {
+    void*& arena = f32 ? p->arena_x32 : p->arena_x64;
+    if (arena) continue;
+    const size_t bytes = arena_rx_value_bytes(p, f32);
+    CK(cudaMalloc(&arena, bytes));
+    CK(cudaMemsetAsync(arena, 0, bytes, s));
+    const size_t vec = align256((f32 ? sizeof(float) : sizeof(double)) * (size_t)p->n);
+    char* a = (char*)arena;
+    auto take = [&](size_t k) {
+      char* r = a;
+      a += k * vec;
+      return r;
+    };
+    if (f32) {
+      I.rd32 = (float*)take(1);
+      I.rv32 = (float*)take(2 * p->dim);
+      I.rdi32 = (float*)take(1);
+      for (int k = 0; k < 2; ++k) I.rc32[k] = (float*)take(1);
+      for (int k = 0; k < 2; ++k) I.pc32[k] = (float*)take(1);
+      for (int k = 0; k < 2; ++k) I.apc32[k] = (float*)take(1);
+      I.wc32 = (float*)take(1);
+      I.rx32 = 1;
+    } else {
+      I.rd64 = (double*)take(1);
+      I.rv64 = (double*)take(2 * p->dim);
+      I.rdi64 = (double*)take(1);
+      for (int k = 0; k < 2; ++k) I.rc64[k] = (double*)take(1);
+      for (int k = 0; k < 2; ++k) I.pc64[k] = (double*)take(1);
+      for (int k = 0; k < 2; ++k) I.apc64[k] = (double*)take(1);
+      I.wc64 = (double*)take(1);
+      I.rx64 = 1;
+    }
+  }
+  return GPCG_OK;
+}
+
 static gpcg_status copy_in(const gpcg_problem* p, double* dst, const double* src, cudaStream_t s) {
   CK(cudaMemcpy2DAsync(dst, sizeof(double) * p->px, src, sizeof(double) * p->nx,
                        sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault, s));
@@ -608,7 +682,7 @@ extern "C" void gpcg_default_options(gpcg_options* o) {
   o->cuda_stream = nullptr;
   o->lambda_min = 0.0;
   o->precond = GPCG_PRECOND_NONE;
-  o->reserved = 0;
+  o->cg_system = GPCG_CG_MASKED;
 }
 
 static gpcg_status check_options(const gpcg_options* o) {
@@ -626,6 +700,10 @@ static gpcg_status check_options(const gpcg_options* o) {
   if (o->precond != GPCG_PRECOND_NONE && o->precond != GPCG_PRECOND_JACOBI &&
       o->precond != GPCG_PRECOND_TILE)
     return fail(GPCG_ERR_ARG, "unknown preconditioner");
+  if (o->cg_system != GPCG_CG_MASKED && o->cg_system != GPCG_CG_EXTRACTED)
+    return fail(GPCG_ERR_ARG, "unknown CG system");
+  if (o->cg_system == GPCG_CG_EXTRACTED && o->precond == GPCG_PRECOND_TILE)
+    return fail(GPCG_ERR_ARG, "the tile preconditioner works on the masked system only");
   return GPCG_OK;
 }
 
@@ -647,6 +725,7 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   r.mixed = o->precision == GPCG_MIXED;
   r.refine = o->refine ? 1 : 0;
   r.use_x0 = use_x0 ? 1 : 0;
+  r.extract = o->cg_system == GPCG_CG_EXTRACTED ? 1 : 0;
   r.precond = o->precond == GPCG_PRECOND_JACOBI ? PC_JACOBI
               : o->precond == GPCG_PRECOND_TILE  ? PC_TILE
                                                  : PC_NONE;
@@ -814,6 +893,9 @@ static gpcg_status prepare_instance(gpcg_problem* p, const gpcg_options* o, cuda
   if (o->precision == GPCG_MIXED && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
   if (o->precond == GPCG_PRECOND_TILE &&
       (st = ensure_tile(p, o->precision == GPCG_MIXED, s)) != GPCG_OK)
+    return st;
+  if (o->cg_system == GPCG_CG_EXTRACTED &&
+      (st = ensure_extract(p, o->precision == GPCG_MIXED, s)) != GPCG_OK)
     return st;
   const bool use_x0 = o->x0 != nullptr;
   if (use_x0 && (st = copy_in(p, (double*)p->inst.x0, o->x0, s)) != GPCG_OK) return st;
@@ -1122,6 +1204,101 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
   return st;
 }
 
+extern "C" gpcg_status gpcg_reduced_system(gpcg_problem* p, const uint8_t* free_mask,
+                                           int precision, int64_t* m, int32_t* fidx,
+                                           double* diag, int32_t* nb, double* val,
+                                           void* cuda_stream) {
+  if (!p || !free_mask || !m || !fidx || !diag || !nb || !val)
+    return fail(GPCG_ERR_ARG, "NULL argument");
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f32 = precision == GPCG_MIXED;
+  gpcg_status st;
+  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if ((st = ensure_extract(p, f32, s)) != GPCG_OK) return st;
+  DevInst& I = p->inst;
+  uint8_t* dm = nullptr;
+  CK(cudaMalloc(&dm, (size_t)p->n));
+  st = GPCG_OK;
+  do {
+    if (cudaMemcpyAsync(dm, free_mask, (size_t)p->n, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "copy mask");
+      break;
+    }
+    // free-set words into mask[0] (the set-up also fills two CG scratch
+    // vectors; its value operand is unused here)
+    if (launch_spmv_setup(I, dm, I.diag, I.mask[0], I.r64[1], I.p64[1], false, s) !=
+        cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "set-up launch");
+      break;
+    }
+    Ctl C = fresh_ctl();
+    C.cur = 0;
+    C.pcur = 0;
+    C.cg32 = f32 ? 1 : 0;
+    C.gp32 = 0;
+    C.hold = 1;
+    Ctl out;
+    C.pass = P_RX_COUNT;
+    if ((st = one_pass(p, C, s, &out)) != GPCG_OK) break;
+    const long long mm = (long long)out.red[4];
+    C.m = (int)mm;
+    C.pass = P_RX_MAP;
+    if ((st = one_pass(p, C, s, &out)) != GPCG_OK) break;
+    C.pass = P_RX_BUILD;
+    if ((st = one_pass(p, C, s, &out)) != GPCG_OK) break;
+    *m = mm;
+    const int nn = 2 * p->dim;
+    std::vector<int32_t> fx((size_t)mm);
+    if (mm > 0 &&
+        cudaMemcpyAsync(fx.data(), I.fidx, sizeof(int) * mm, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "copy fidx");
+      break;
+    }
+    for (int j = 0; j < nn && mm > 0; ++j)
+      if (cudaMemcpyAsync(nb + (size_t)j * mm, I.rnb + (size_t)j * p->n, sizeof(int) * mm,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "copy neighbours");
+        break;
+      }
+    if (st != GPCG_OK) break;
+    const size_t es = f32 ? sizeof(float) : sizeof(double);
+    std::vector<char> dv((size_t)mm * es), vv((size_t)mm * nn * es);
+    const char* rd = f32 ? (const char*)I.rd32 : (const char*)I.rd64;
+    const char* rv = f32 ? (const char*)I.rv32 : (const char*)I.rv64;
+    if (mm > 0 && cudaMemcpyAsync(dv.data(), rd, es * mm, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "copy diagonal");
+      break;
+    }
+    for (int j = 0; j < nn && mm > 0; ++j)
+      if (cudaMemcpyAsync(vv.data() + (size_t)j * mm * es, rv + (size_t)j * p->n * es, es * mm,
+                          cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        st = fail(GPCG_ERR_CUDA, "copy couplings");
+        break;
+      }
+    if (st != GPCG_OK) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      st = fail(GPCG_ERR_CUDA, "synchronize: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    // padded point index -> row-major index of the unpadded grid
+    for (long long k = 0; k < mm; ++k) {
+      const long long i = fx[(size_t)k];
+      const long long ix = i % p->px, row = i / p->px;
+      fidx[k] = (int32_t)(ix + (long long)p->nx * row);
+    }
+    for (size_t k = 0; k < (size_t)mm; ++k)
+      diag[k] = f32 ? (double)((const float*)dv.data())[k] : ((const double*)dv.data())[k];
+    for (size_t k = 0; k < (size_t)mm * nn; ++k)
+      val[k] = f32 ? (double)((const float*)vv.data())[k] : ((const double*)vv.data())[k];
+    p->have = false;  // the solve's vectors were overwritten
+  } while (0);
+  cudaFree(dm);
+  return st;
+}
+
 extern "C" gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* free_mask,
                                               const double* r, double* z, double* rz,
                                               int precision, void* cuda_stream) {
@@ -1342,12 +1519,15 @@ struct gpcg_server {
   }
 };
 
-static size_t footprint(const gpcg_stencil* A, bool mixed, bool tile) {
+static size_t footprint(const gpcg_stencil* A, bool mixed, bool tile, bool extract) {
   gpcg_problem tmp;
   geometry(A->dim, A->nx, A->ny, A->nz, &tmp);
   size_t b = arena64_bytes(&tmp);
   if (mixed) b += arena32_bytes(&tmp);
   if (tile) b += arena_tile_bytes(&tmp, false) + (mixed ? arena_tile_bytes(&tmp, true) : 0);
+  if (extract)
+    b += arena_rx_index_bytes(&tmp) + arena_rx_value_bytes(&tmp, false) +
+         (mixed ? arena_rx_value_bytes(&tmp, true) : 0);
   return b + 4096;
 }
 
@@ -1387,7 +1567,8 @@ extern "C" gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A,
   if (s->opt.precond == GPCG_PRECOND_TILE && A->dim != 2)
     return fail(GPCG_ERR_ARG, "the tile preconditioner is for 2-D problems only");
   const size_t bytes =
-      footprint(A, s->opt.precision == GPCG_MIXED, s->opt.precond == GPCG_PRECOND_TILE);
+      footprint(A, s->opt.precision == GPCG_MIXED, s->opt.precond == GPCG_PRECOND_TILE,
+                s->opt.cg_system == GPCG_CG_EXTRACTED);
   if (bytes > s->budget) return fail(GPCG_ERR_BUDGET, "request needs %zu bytes, budget %zu",
                                      bytes, s->budget);
   Req* r = new Req();

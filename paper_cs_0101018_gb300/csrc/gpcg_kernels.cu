@@ -247,6 +247,7 @@ struct Acc {
 // What a tile needs from the instance's control block (read once per tile).
 struct Snap {
   int pass, cur, pcur, cg32, first_cg, dir, gp32, x32_live;
+  int m, pad;  // explicit reduced system: free points of the phase
   double alpha, beta;
 };
 
@@ -1194,6 +1195,258 @@ __device__ void cg_z_tile(const DevInst& I, const Snap& S, int x0, int y0, int z
   __syncthreads();  // the exchange buffer is free again
 }
 
+// ----------------------------------------------- explicit reduced system --
+//
+// The paper's design extracts A_k = Z' A Z (Sec. 4) into its own matrix;
+// here that is an option beside the bitmask: the free points get a compact
+// numbering (tiles in order, rows within a tile, columns within a row, the
+// groups' ranges concatenated), A_FF is stored in that numbering as rows of
+// a diagonal and 2*dim neighbour slots (compact index and coupling), and the
+// CG phase runs on compact vectors.  It pays when few points are free: a CG
+// step then touches m entries instead of streaming all n.
+
+// Exclusive prefix sum of v over the CTA in thread order; `total` receives
+// the sum.  All threads must call it (two block barriers).
+__device__ __forceinline__ int cta_excl_scan(int v, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int t = s_warp[w];
+    before += w < warp ? t : 0;
+    all += t;
+  }
+  __syncthreads();
+  total = all;
+  return before + x - v;
+}
+
+// The free bits of the lane's two points of row (y, z) (0 past the grid).
+__device__ __forceinline__ unsigned rx_bits(const DevInst& I, const Snap& S, int y, int z,
+                                            int e0) {
+  if (y >= I.ny || e0 >= I.nx) return 0u;
+  const unsigned b = my_free_bits(I, I.mask[S.cur], y, z, e0);
+  return e0 + 1 < I.nx ? b : (b & 1u);
+}
+
+// P_RX_COUNT on one tile: the number of free points (a count of the pass).
+__device__ __forceinline__ void rx_count_tile(const DevInst& I, const Snap& S, int x0, int y0,
+                                              int z, Acc& acc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e0 = x0 + 2 * lane;
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) acc.c[0] += __popc(rx_bits(I, S, y0 + warp * kRY + k, z, e0));
+}
+
+// The passes of the explicit reduced system run out of line: they are not
+// the hot path of the default solve and, inlined, would raise the register
+// and stack use of the whole pass kernel.
+
+// P_RX_MAP over a group's tiles: compact indices from the group's offset
+// (written by P_RX_COUNT's last group), fidx, r_0 = g_F in compact order, and
+// the full-length w set to 0 (the search direction is scattered into it).
+template <class T>
+__device__ __noinline__ void rx_map_group(const DevInst& I, const Snap& S, int grp, int t_lo, int t_hi,
+                             int* s_warp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool f32 = sizeof(T) == 4;
+  T* rc = f32 ? (T*)I.rc32[S.pcur] : (T*)I.rc64[S.pcur];
+  T* wf = f32 ? (T*)I.w32 : (T*)I.w64;
+  const unsigned lt = (1u << lane) - 1u;
+  int base = __ldcg(I.goff + grp);
+  for (int tile = t_lo; tile < t_hi; ++tile) {
+    const int rest = tile / I.tiles_x;
+    const int x0 = (tile % I.tiles_x) * kTX, y0 = (rest % I.tiles_y) * kTY, z = rest / I.tiles_y;
+    const int e0 = x0 + 2 * lane;
+    const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+    const int ya = y0 + warp * kRY;
+    unsigned fb[kRY], b0[kRY], b1[kRY];
+    int wtot = 0;
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+      fb[k] = rx_bits(I, S, ya + k, z, e0);
+      b0[k] = __ballot_sync(FULL_MASK, fb[k] & 1u);
+      b1[k] = __ballot_sync(FULL_MASK, (fb[k] >> 1) & 1u);
+      wtot += __popc(b0[k]) + __popc(b1[k]);
+    }
+    int tile_tot;
+    const int wo = __shfl_sync(FULL_MASK, cta_excl_scan(lane == 0 ? wtot : 0, s_warp, tile_tot), 0);
+    int off = base + wo;
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+      const int y = ya + k;
+      const int k0 = off + __popc(b0[k] & lt) + __popc(b1[k] & lt);
+      const int k1 = k0 + (int)(fb[k] & 1u);
+      if (y < I.ny && v0) {
+        const long long i = pidx(I, y, z, e0);
+        I.cidx[i] = (fb[k] & 1u) ? k0 : -1;
+        if (v1) I.cidx[i + 1] = (fb[k] & 2u) ? k1 : -1;
+        st2(wf, i, v0, v1, T(0), T(0));
+        double gv[2] = {0.0, 0.0};
+        if (S.gp32) {
+          float gf[2];
+          ld2(I.g32[S.cur], i, v0, v1, gf);
+          gv[0] = gf[0];
+          gv[1] = gf[1];
+        } else {
+          ld2(I.g[S.cur], i, v0, v1, gv);
+        }
+        if (fb[k] & 1u) {
+          I.fidx[k0] = (int)i;
+          rc[k0] = (T)gv[0];
+        }
+        if (fb[k] & 2u) {
+          I.fidx[k1] = (int)(i + 1);
+          rc[k1] = (T)gv[1];
+        }
+      }
+      off += __popc(b0[k]) + __popc(b1[k]);
+    }
+    base += tile_tot;
+  }
+}
+
+// P_RX_BUILD on one tile: the rows of A_FF of its free points in compact
+// numbering, 1/diagonal, and the first CG step's state: z_0 = M^-1 r_0 (M = I
+// or the diagonal), rho_0 = <r_0, z_0> (sum 0); compact p, Ap, w = 0 so that
+// the first fused step, run with alpha = beta = 0, forms p_0 and Ap_0.
+template <class T, bool JAC>
+__device__ __noinline__ void rx_build_tile(const DevInst& I, const Snap& S, int x0, int y0, int z, Acc& acc,
+                              FF* ffs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool f32 = sizeof(T) == 4;
+  const T* bd = f32 ? (const T*)I.diag32 : (const T*)I.diag;
+  const T* bx = f32 ? (const T*)I.cx32 : (const T*)I.cx;
+  const T* by = f32 ? (const T*)I.cy32 : (const T*)I.cy;
+  const T* bz = f32 ? (const T*)I.cz32 : (const T*)I.cz;
+  const T* dv = f32 ? (const T*)I.dinv32 : (const T*)I.dinv;
+  T* rd = f32 ? (T*)I.rd32 : (T*)I.rd64;
+  T* rv = f32 ? (T*)I.rv32 : (T*)I.rv64;
+  T* rdi = f32 ? (T*)I.rdi32 : (T*)I.rdi64;
+  const T* rc = f32 ? (const T*)I.rc32[S.pcur] : (const T*)I.rc64[S.pcur];
+  T* pcv = f32 ? (T*)I.pc32[S.pcur] : (T*)I.pc64[S.pcur];
+  T* apc = f32 ? (T*)I.apc32[S.pcur] : (T*)I.apc64[S.pcur];
+  T* wc = f32 ? (T*)I.wc32 : (T*)I.wc64;
+  const long long st = I.n;
+  float s32 = 0.0f;
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + warp * kRY + k;
+    if (y >= I.ny) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int x = x0 + 2 * lane + h;
+      if (x >= I.nx) continue;
+      const long long i = pidx(I, y, z, x);
+      const int c = __ldcg(I.cidx + i);
+      if (c < 0) continue;
+      int nb[kMaxNb];
+      T val[kMaxNb];
+      auto slot = [&](int j, bool has, long long o, T cpl) {
+        const int q = has ? __ldcg(I.cidx + i + o) : -1;
+        nb[j] = q >= 0 ? q : c;
+        val[j] = q >= 0 ? cpl : T(0);
+      };
+      slot(0, x > 0, -1, x > 0 ? bx[i - 1] : T(0));
+      slot(1, x + 1 < I.nx, 1, bx[i]);
+      slot(2, y > 0, -(long long)I.px, y > 0 ? by[i - I.px] : T(0));
+      slot(3, y + 1 < I.ny, I.px, by[i]);
+      if (I.dim == 3) {
+        slot(4, z > 0, -I.plane, z > 0 ? bz[i - I.plane] : T(0));
+        slot(5, z + 1 < I.nz, I.plane, bz[i]);
+      }
+      const int nn = 2 * I.dim;
+      for (int j = 0; j < nn; ++j) {
+        I.rnb[j * st + c] = nb[j];
+        rv[j * st + c] = val[j];
+      }
+      rd[c] = bd[i];
+      const T di = dv[i];
+      rdi[c] = di;
+      pcv[c] = T(0);
+      apc[c] = T(0);
+      wc[c] = T(0);
+      const T r = rc[c];
+      const T zz = JAC ? r * di : r;
+      if (f32) s32 = fmaf((float)r, (float)zz, s32);
+      else acc.s[0] = fma((double)r, (double)zz, acc.s[0]);
+    }
+  }
+  if (f32) ff_acc(ffs[0], s32);
+}
+
+// P_RCG over compact indices [lo, hi): the fused CG step of P_CG_F on the
+// compact system, with the neighbours' p_j formed from their old r, Ap, p.
+template <class T, bool JAC>
+__device__ __noinline__ void rcg_range(const DevInst& I, const Snap& S, long long lo, long long hi, Acc& acc,
+                          FF* ffs) {
+  const bool f32 = sizeof(T) == 4;
+  const int pc = S.pcur;
+  const T* __restrict__ r = f32 ? (const T*)I.rc32[pc] : (const T*)I.rc64[pc];
+  const T* __restrict__ p = f32 ? (const T*)I.pc32[pc] : (const T*)I.pc64[pc];
+  const T* __restrict__ ap = f32 ? (const T*)I.apc32[pc] : (const T*)I.apc64[pc];
+  const T* __restrict__ rd = f32 ? (const T*)I.rd32 : (const T*)I.rd64;
+  const T* __restrict__ rv = f32 ? (const T*)I.rv32 : (const T*)I.rv64;
+  const T* __restrict__ di = f32 ? (const T*)I.rdi32 : (const T*)I.rdi64;
+  T* r_o = f32 ? (T*)I.rc32[pc ^ 1] : (T*)I.rc64[pc ^ 1];
+  T* p_o = f32 ? (T*)I.pc32[pc ^ 1] : (T*)I.pc64[pc ^ 1];
+  T* ap_o = f32 ? (T*)I.apc32[pc ^ 1] : (T*)I.apc64[pc ^ 1];
+  T* w = f32 ? (T*)I.wc32 : (T*)I.wc64;
+  const int* __restrict__ rnb = I.rnb;
+  const long long st = I.n;
+  const int nn = 2 * I.dim;
+  const T a = (T)S.alpha, b = (T)S.beta;
+  for (long long k = lo + threadIdx.x; k < hi; k += kThreads) {
+    const T pk = p[k];
+    const T rn = fma(a, ap[k], r[k]);
+    const T zn = JAC ? rn * di[k] : rn;
+    const T pn = fma(b, pk, -zn);
+    w[k] = fma(a, pk, w[k]);
+    T y = rd[k] * pn;
+    for (int j = 0; j < nn; ++j) {
+      const int q = __ldg(rnb + j * st + k);
+      const T rq = fma(a, ap[q], r[q]);
+      const T pq = fma(b, p[q], -(JAC ? rq * di[q] : rq));
+      y = fma(rv[j * st + k], pq, y);
+    }
+    r_o[k] = rn;
+    p_o[k] = pn;
+    ap_o[k] = y;
+    const T dy = JAC ? y * di[k] : y;
+    if (f32) {
+      ff_fma(ffs[0], (float)rn, (float)zn);
+      ff_fma(ffs[1], (float)pn, (float)y);
+      ff_fma(ffs[2], (float)zn, (float)y);
+      ff_fma(ffs[3], (float)y, (float)dy);
+    } else {
+      acc.s[0] = fma((double)rn, (double)zn, acc.s[0]);
+      acc.s[1] = fma((double)pn, (double)y, acc.s[1]);
+      acc.s[2] = fma((double)zn, (double)y, acc.s[2]);
+      acc.s[3] = fma((double)y, (double)dy, acc.s[3]);
+    }
+  }
+}
+
+// P_RW over compact indices [lo, hi): w_{j+1} = w_j + alpha_j p_j scattered
+// into the full-length w (zero elsewhere since P_RX_MAP).
+template <class T>
+__device__ __noinline__ void rw_range(const DevInst& I, const Snap& S, long long lo, long long hi) {
+  const bool f32 = sizeof(T) == 4;
+  const T* p = f32 ? (const T*)I.pc32[S.pcur] : (const T*)I.pc64[S.pcur];
+  const T* wc = f32 ? (const T*)I.wc32 : (const T*)I.wc64;
+  T* wf = f32 ? (T*)I.w32 : (T*)I.w64;
+  const T a = (T)S.alpha;
+  for (long long k = lo + threadIdx.x; k < hi; k += kThreads)
+    wf[__ldg(I.fidx + k)] = fma(a, p[k], wc[k]);
+}
+
 // ---------------------------------------------------------------- control --
 
 __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
@@ -1223,6 +1476,19 @@ __device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
       per = sv * kc + (I.opt.precond == PC_TILE ? 12.0 * sv : 8.0 * sv + pj) + 0.125;
       break;
     case P_CG_Z: per = (C.gp32 ? 4.0 : 8.0) + 3.0 * sv + 6.0 * sv + 0.125; break;
+    case P_RX_COUNT: per = 0.125; break;
+    case P_RX_MAP:  // mask, cidx and w for every point; g, fidx, r for the free ones
+      return (0.125 + 4.0 + sv) * (double)I.n + ((C.gp32 ? 4.0 : 8.0) + 4.0 + sv) * (double)C.m;
+    case P_RX_BUILD: {  // cidx of every point; bands, 1/diag, r in; rows, p, Ap, w out
+      const double nn = 2.0 * I.dim;
+      return 4.0 * (double)I.n +
+             (sv * kc + sv + sv + (1.0 + nn) * sv + 4.0 * nn + sv + 3.0 * sv) * (double)C.m;
+    }
+    case P_RCG: {  // r, p, Ap, w in and out; the row (and 1/diag)
+      const double nn = 2.0 * I.dim;
+      return (8.0 * sv + (1.0 + nn) * sv + 4.0 * nn + pj) * (double)C.m;
+    }
+    case P_RW: return (4.0 + 3.0 * sv) * (double)C.m;
     default: break;
   }
   return per * (double)I.n;
@@ -1267,7 +1533,11 @@ __device__ void begin_cg(const DevInst& I, Ctl& C) {
   C.cg_j = 0;
   C.cdmax = 0.0;
   C.cg_finish = 0;
-  if (I.opt.max_cg >= 1 && I.opt.precond == PC_TILE && cg_fused(I, C)) {
+  if (I.opt.max_cg >= 1 && I.opt.extract) {
+    C.first_cg = 0;
+    C.beta = 0.0;
+    C.pass = P_RX_COUNT;
+  } else if (I.opt.max_cg >= 1 && I.opt.precond == PC_TILE && cg_fused(I, C)) {
     C.first_cg = 0;
     C.beta = 0.0;
     C.pass = P_CG_Z;
@@ -1335,11 +1605,11 @@ __device__ void cg_advance(const DevInst& I, Ctl& C, double zAp, double ApMAp) {
   if (delta > C.cdmax) C.cdmax = delta;
   if (stop) {
     C.cg_finish = 1;
-    C.pass = P_CG_A;
+    C.pass = I.opt.extract ? P_RW : P_CG_A;
   } else {
     C.beta = rr_next / C.rr;
     C.rr = rr_next;
-    C.pass = P_CG_F;
+    C.pass = I.opt.extract ? P_RCG : P_CG_F;
   }
 }
 
@@ -1534,6 +1804,33 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       }
       break;
     }
+    case P_RX_COUNT:
+      C.m = (int)red[4];  // the group offsets were written by this pass's last group
+      if (C.m == 0) start_search(C, D_ZERO);  // no free variable: w = 0
+      else C.pass = P_RX_MAP;
+      break;
+    case P_RX_MAP:
+      C.pass = P_RX_BUILD;
+      break;
+    case P_RX_BUILD: {
+      const double rz = red[0];  // rho_0 = <r_0, M^-1 r_0>
+      if (!isfinite(rz)) {
+        set_done(C, S_NUMERIC);
+      } else if (!(rz > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
+        start_search(C, D_ZERO);
+      } else {
+        C.rr = rz;
+        C.alpha = 0.0;
+        C.beta = 0.0;
+        C.pass = P_RCG;
+      }
+      break;
+    }
+    case P_RW:
+      C.cg_finish = 0;
+      start_search(C, C.cg32 ? D_W32 : D_W64);
+      break;
+    case P_RCG:
     case P_CG_F: {
       C.rr = red[0];  // ||r_j||^2 of the stored r_j
       const double pAp = red[1];
@@ -2651,6 +2948,8 @@ __device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
     case P_CG_A: return 1;
     case P_CG_F: return 4;
     case P_CG_Z: return 1;
+    case P_RX_BUILD: return 1;
+    case P_RCG: return 4;
     default: return 0;
   }
 }
@@ -2752,6 +3051,15 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
       }
       break;
     }
+    case P_RX_COUNT:
+      rx_count_tile(I, S, x0, y0, z, acc);
+      break;
+    case P_RX_BUILD:
+      if (S.cg32 && I.opt.precond == PC_JACOBI) rx_build_tile<float, true>(I, S, x0, y0, z, acc, ffs);
+      else if (S.cg32) rx_build_tile<float, false>(I, S, x0, y0, z, acc, ffs);
+      else if (I.opt.precond == PC_JACOBI) rx_build_tile<double, true>(I, S, x0, y0, z, acc, ffs);
+      else rx_build_tile<double, false>(I, S, x0, y0, z, acc, ffs);
+      break;
     case P_CG_Z:
       if (S.cg32) cg_z_tile<float>(I, S, x0, y0, z, scr, acc, ffs);
       else cg_z_tile<double>(I, S, x0, y0, z, scr, acc, ffs);
@@ -2784,6 +3092,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ Snap sS;
   __shared__ Ctl sC;
   __shared__ int s_cnt[3][kWarps];
+  __shared__ int s_scan[kWarps];
   __shared__ double s_red[kNRed];
   __shared__ int s_t, s_inst, s_last;
   extern __shared__ unsigned char dyn_smem[];
@@ -2863,6 +3172,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         sS.dir = sC.dir;
         sS.gp32 = sC.gp32;
         sS.x32_live = sC.x32_live;
+        sS.m = sC.m;
         sS.alpha = sC.alpha;
         sS.beta = sC.beta;
         s_inst = tr.x;
@@ -2881,7 +3191,28 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const int grp = tr.y;
     const bool tma = tma_pass(I, S);
-    if (!tma) {
+    if (S.pass == P_RCG || S.pass == P_RW) {
+      // compact passes of the explicit reduced system: the group is a range
+      // of compact indices
+      const long long lo = (long long)grp * S.m / I.n_groups;
+      const long long hi = (long long)(grp + 1) * S.m / I.n_groups;
+      const bool jac = I.opt.precond == PC_JACOBI;
+      if (S.pass == P_RW) {
+        if (S.cg32) rw_range<float>(I, S, lo, hi);
+        else rw_range<double>(I, S, lo, hi);
+      } else if (S.cg32) {
+        if (jac) rcg_range<float, true>(I, S, lo, hi, acc, ffs);
+        else rcg_range<float, false>(I, S, lo, hi, acc, ffs);
+      } else {
+        if (jac) rcg_range<double, true>(I, S, lo, hi, acc, ffs);
+        else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
+      }
+    } else if (S.pass == P_RX_MAP) {
+      const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+      const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
+      if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
+      else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
+    } else if (!tma) {
       // register sweep: the group is a range of whole tiles
       const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
       const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
@@ -2974,7 +3305,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     // butterfly).  FP32 passes reduce their float-float accumulators in
     // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
     const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
-                        S.pass == P_CG_Z)
+                        S.pass == P_CG_Z || S.pass == P_RX_BUILD || S.pass == P_RCG)
                            ? S.cg32 != 0
                                                               : (S.pass != P_START && S.gp32 != 0);
     const int ns = n_sums(S.pass, S.first_cg, S.gp32);
@@ -3060,6 +3391,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       s_red[tid] = v;
     }
     __syncthreads();
+    if (S.pass == P_RX_COUNT) {
+      // the groups' offsets in the compact numbering (exclusive prefix sum
+      // of their free counts, two groups per thread)
+      int t0, t1;
+      const double* P0 = I.part;
+      const int c0 = tid < I.n_groups ? (int)__ldcg(P0 + (long long)tid * kNRed + 4) : 0;
+      const int o0 = cta_excl_scan(c0, s_scan, t0);
+      const int g1 = tid + kThreads;
+      const int c1 = g1 < I.n_groups ? (int)__ldcg(P0 + (long long)g1 * kNRed + 4) : 0;
+      const int o1 = cta_excl_scan(c1, s_scan, t1);
+      if (tid < I.n_groups) I.goff[tid] = o0;
+      if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
+    }
     // the state machine runs on a shared copy of the control block (one
     // round trip in, one out, instead of dependent global accesses)
     long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);

@@ -19,6 +19,7 @@ OK, ERR_ARG, ERR_INFEASIBLE, ERR_NUMERIC, ERR_OOM, ERR_BUDGET, ERR_CUDA = 0, 1, 
 ERR_MAXIT, ERR_LINESEARCH, ERR_TIMEOUT, ERR_PENDING, ERR_CANCELLED = 7, 8, 9, 10, 11
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_TILE = 0, 1, 2
+CG_MASKED, CG_EXTRACTED = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_INFEASIBLE", 3: "ERR_NUMERIC", 4: "ERR_OOM",
                 5: "ERR_BUDGET", 6: "ERR_CUDA", 7: "ERR_MAXIT", 8: "ERR_LINESEARCH",
@@ -43,7 +44,7 @@ class gpcg_options(C.Structure):
                 ("eta2_floor", C.c_double), ("max_outer", C.c_int), ("max_gp", C.c_int),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("precision", C.c_int),
                 ("refine", C.c_int), ("x0", C.c_void_p), ("cuda_stream", C.c_void_p),
-                ("lambda_min", C.c_double), ("precond", C.c_int), ("reserved", C.c_int)]
+                ("lambda_min", C.c_double), ("precond", C.c_int), ("cg_system", C.c_int)]
 
 
 _OPTION_FIELDS = frozenset(f for f, _ in gpcg_options._fields_)
@@ -76,6 +77,9 @@ _SIGNATURES = [
     ("gpcg_result", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(gpcg_stats)]),
     ("gpcg_masked_spmv", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+    ("gpcg_reduced_system", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int64),
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
     ("gpcg_tile_precondition", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
@@ -233,6 +237,24 @@ def gpcg_masked_spmv(prob: Problem, free_mask, p, precision=FP64, stream=None):
     _check(load().gpcg_masked_spmv(prob.handle, _ptr(fm), _ptr(p), _ptr(y), C.byref(pap),
                                    precision, sp))
     return y, pap.value
+
+
+def gpcg_reduced_system(prob: Problem, free_mask, dim=2, precision=FP64, stream=None):
+    """The explicit reduced system for a free set: (m, fidx, diag, nb, val) with
+    nb, val of shape (2*dim, m)."""
+    fm = np.ascontiguousarray(free_mask, dtype=np.uint8)
+    n = prob.n
+    fidx = np.empty(n, np.int32)
+    diag = np.empty(n)
+    nb = np.empty(2 * dim * n, np.int32)
+    val = np.empty(2 * dim * n)
+    m = C.c_int64()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(load().gpcg_reduced_system(prob.handle, _ptr(fm), precision, C.byref(m), _ptr(fidx),
+                                      _ptr(diag), _ptr(nb), _ptr(val), sp))
+    k = m.value
+    return (k, fidx[:k].copy(), diag[:k].copy(), nb[:2 * dim * k].reshape(2 * dim, k).copy(),
+            val[:2 * dim * k].reshape(2 * dim, k).copy())
 
 
 def gpcg_tile_precondition(prob: Problem, free_mask, r, precision=FP64, stream=None):

@@ -64,6 +64,18 @@ def test_argument_checks_need_no_gpu():
     assert L.gpcg_server_create(0, 4, C.byref(o), C.byref(srv)) == g.ERR_ARG
     o = g.default_options(mu=0.7)
     assert L.gpcg_server_create(1 << 30, 4, C.byref(o), C.byref(srv)) == g.ERR_ARG
+    # options are checked before any CUDA call: unknown preconditioner or CG
+    # system, and the tile preconditioner with the extracted reduced system
+    for bad in (dict(precond=3), dict(cg_system=2),
+                dict(precond=g.PRECOND_TILE, cg_system=g.CG_EXTRACTED)):
+        o = g.default_options(**bad)
+        assert L.gpcg_server_create(1 << 30, 4, C.byref(o), C.byref(srv)) == g.ERR_ARG
+
+
+def test_option_defaults_are_the_masked_unpreconditioned_cg():
+    import paper_cs_0101018_gb300 as g
+    o = g.default_options()
+    assert o.precond == g.PRECOND_NONE and o.cg_system == g.CG_MASKED
 
 
 def test_oracle_and_library_share_no_code():

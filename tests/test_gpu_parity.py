@@ -184,6 +184,98 @@ def test_tile_pcg_matches_oracle(k, prec):
         assert st["cg_iters"] < plain.stats["cg_iters"]
 
 
+def _reduced_reference(qp, free):
+    """The explicit reduced system from its definition: free points numbered
+    tile by tile (64 x 32 tiles of each xy-plane, in the order x, y, z of the
+    tiles), row by row, column by column; per row the neighbour slots x-1,
+    x+1, y-1, y+1 (, z-1, z+1) with their couplings, or the row itself and 0."""
+    nx, ny, nz = qp.nx, qp.ny, qp.nz
+    F = np.flatnonzero(free)
+    ix, iy, iz = F % nx, (F // nx) % ny, F // (nx * ny)
+    order = np.lexsort((ix, iy, ix // 64, iy // 32, iz))
+    fidx = F[order]
+    m = fidx.size
+    comp = np.full(qp.n, -1, np.int64)
+    comp[fidx] = np.arange(m)
+    ix, iy, iz = fidx % nx, (fidx // nx) % ny, fidx // (nx * ny)
+    slots = [(ix > 0, -1, lambda i: qp.cx[i - 1]), (ix + 1 < nx, 1, lambda i: qp.cx[i]),
+             (iy > 0, -nx, lambda i: qp.cy[i - nx]), (iy + 1 < ny, nx, lambda i: qp.cy[i])]
+    if qp.dim == 3:
+        slots += [(iz > 0, -nx * ny, lambda i: qp.cz[i - nx * ny]),
+                  (iz + 1 < nz, nx * ny, lambda i: qp.cz[i])]
+    nb = np.empty((len(slots), m), np.int64)
+    val = np.empty((len(slots), m))
+    for j, (has, off, cpl) in enumerate(slots):
+        q = np.where(has, comp[np.where(has, fidx + off, fidx)], -1)
+        ok = q >= 0
+        nb[j] = np.where(ok, q, np.arange(m))
+        val[j] = np.where(ok, cpl(np.where(has, fidx, 0)), 0.0)
+    return m, fidx, qp.diag[fidx], nb, val
+
+
+@pytest.mark.parametrize("case", ["2d", "ragged", "row", "column", "3d"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_reduced_system_matches_definition(case, prec):
+    """The compact numbering and the rows of A_FF built by the extraction
+    passes: indices bit for bit, values exact (FP32: the rounded values)."""
+    qp = {"2d": lambda: gi.grid_qp_2d(130, 70, seed=510, shift=0.02),
+          "ragged": lambda: gi.grid_qp_2d(65, 33, seed=511, shift=0.02),
+          "row": lambda: gi.grid_qp_2d(200, 1, seed=512, shift=0.02),
+          "column": lambda: gi.grid_qp_2d(1, 90, seed=513, shift=0.02),
+          "3d": lambda: gi.grid_qp_3d(70, 33, 4, seed=514, shift=0.02, sigma=0.5,
+                                      bounds="box1")}[case]()
+    free = gi.uniform(515, 2, qp.n) < 0.6
+    prob = g.gpcg_problem_create(qp)
+    m, fidx, diag, nb, val = g.gpcg_reduced_system(prob, free, dim=qp.dim, precision=prec)
+    rm, rfidx, rdiag, rnb, rval = _reduced_reference(qp, free)
+    cast = (lambda v: v.astype(np.float32).astype(np.float64)) if prec == g.MIXED else (lambda v: v)
+    assert m == rm
+    assert np.array_equal(fidx, rfidx)
+    assert np.array_equal(nb, rnb)
+    assert np.array_equal(diag, cast(rdiag))
+    assert np.array_equal(val, cast(rval))
+
+
+EXTRACT = [PROBLEMS[k] for k in (0, 2, 5, 8, 10, 14, 17, 20, 24, 26, 27, 29, 30)]
+
+
+@pytest.mark.parametrize("k", range(len(EXTRACT)))
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("pc", [0, 1])
+def test_extracted_cg_matches_oracle(k, prec, pc):
+    """CG on the explicitly extracted reduced system (Sec. 4's A_k) against
+    the oracle: the same arithmetic as the masked system up to the order of
+    the sums, so FP64 also follows the oracle's path."""
+    qp = EXTRACT[k]
+    ref = oracle.solve(qp, tau_rel=1e-10, precond=pc)
+    status, x, st = _solve(qp, tau_rel=1e-10, precision=prec, precond=pc,
+                           cg_system=g.CG_EXTRACTED)
+    assert status == ref.status == 0
+    assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
+    assert _active_sets_agree(qp, x, ref.x)
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    if prec == g.FP64:
+        for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
+            a, b = st[key], ref.stats[key]
+            assert abs(a - b) <= 3 + 0.10 * b, (key, a, b)
+    c = oracle.census(qp, x)
+    assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
+
+
+def test_extracted_and_masked_solves_agree_in_a_batch():
+    """Batched solve with the extracted system: each result equals the masked
+    solve of the same instance to the FP64 tolerance."""
+    qps = [gi.grid_qp_2d(nx, ny, seed=520 + nx, shift=0.02, bounds="two_sided")
+           for nx, ny in ((40, 30), (129, 5), (70, 70), (3, 200))]
+    probs = [g.gpcg_problem_create(qp) for qp in qps]
+    opts = g.default_options(tau_rel=1e-10, cg_system=g.CG_EXTRACTED)
+    assert g.gpcg_solve_batch(probs, opts, check=False) == 0
+    for qp, pr in zip(qps, probs):
+        x, _ = g.gpcg_result(pr)
+        _, xm, _ = _solve(qp, tau_rel=1e-10)
+        assert _rel_err(x, xm) <= 1e-9
+
+
 def test_tile_preconditioner_needs_a_2d_staged_problem():
     qp = gi.grid_qp_3d(17, 9, 6, seed=503, shift=0.02, sigma=0.5, bounds="box1")
     prob = g.gpcg_problem_create(qp)
