@@ -106,6 +106,10 @@ enum Pass : int {
 // row's own compact index and a zero coupling.
 constexpr int kMaxNb = 6;
 
+// Optional pass families, compiled into their own instantiations of the
+// pass kernel so that the default kernel carries none of their code.
+enum Feature : int { FEAT_TILE = 1, FEAT_EXT = 2 };
+
 // Preconditioners of the CG phase (Opts.precond; the public gpcg_precond).
 enum Precond : int { PC_NONE = 0, PC_JACOBI = 1, PC_TILE = 2 };
 

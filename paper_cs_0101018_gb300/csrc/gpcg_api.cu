@@ -22,9 +22,9 @@
 #include "engine.h"
 
 namespace gpcg {
-const void* pass_kernel_ptr(bool cond);
+const void* pass_kernel_ptr(bool cond, int feat);
 int pass_grid(int n_work);
-cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s);
+cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
 cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
                         int fill_l, int fill_u, int* flags, cudaStream_t s);
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
@@ -103,6 +103,7 @@ struct Scratch {
   int g_steps = 0;
   bool g_pdl = false;      // the cached graph joins its passes by programmatic edges
   bool g_no_pdl = false;   // GPCG_NO_PDL when it was built
+  int g_feat = -1;         // the feature set of its pass kernel (Feature bits)
   ~Scratch() { release(); }
   void release() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -732,6 +733,13 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   return r;
 }
 
+// The pass kernel instantiation a solve with these options needs.
+static int feature_set(const gpcg_options* o) {
+  if (o->precond == GPCG_PRECOND_TILE) return FEAT_TILE;
+  if (o->cg_system == GPCG_CG_EXTRACTED) return FEAT_EXT;
+  return 0;
+}
+
 static Ctl fresh_ctl() {
   Ctl C;
   memset(&C, 0, sizeof(C));
@@ -748,9 +756,10 @@ static Ctl fresh_ctl() {
 // mode 1: a plain graph of `steps` passes replayed by the host.
 static constexpr int kBody = 8;
 
-static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap) {
+static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap,
+                             int feat) {
   if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps) &&
-      sc.g_no_pdl == env_no_pdl())
+      sc.g_no_pdl == env_no_pdl() && sc.g_feat == feat)
     return GPCG_OK;
   sc.invalidate();
   EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
@@ -787,7 +796,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   void* kp[] = {&args};
   cudaKernelNodeParams k;
   memset(&k, 0, sizeof(k));
-  k.func = const_cast<void*>(pass_kernel_ptr(mode == 0));
+  k.func = const_cast<void*>(pass_kernel_ptr(mode == 0, feat));
   k.gridDim = dim3((unsigned)pass_grid((int)tiles));
   k.blockDim = dim3(kThreads);
   k.sharedMemBytes = kDynSmem;
@@ -835,6 +844,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   }
   sc.g_pdl = pdl;
   sc.g_no_pdl = env_no_pdl();
+  sc.g_feat = feat;
   cudaGraphDestroy(g);
   if (st != GPCG_OK) {
     sc.gexec = nullptr;
@@ -847,7 +857,8 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
 }
 
 // Run the engine until every instance in the scratch tables is done.
-static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStream_t s) {
+static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStream_t s,
+                              int feat) {
   const unsigned cap = env_pass_cap();
   const int mode = env_engine_mode();
   sc.h_pin[0] = n_live;
@@ -855,7 +866,7 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
   if (mode == 0) {
-    gpcg_status st = get_graph(sc, tiles, 0, kBody, cap);
+    gpcg_status st = get_graph(sc, tiles, 0, kBody, cap, feat);
     if (st != GPCG_OK) return st;
     CK(cudaGraphLaunch(sc.gexec, s));
     CK(cudaMemcpyAsync(&sc.h_pin[0], sc.d_live, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -865,7 +876,7 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
     int steps = 8;
     unsigned done_passes = 0;
     for (;;) {
-      gpcg_status st = get_graph(sc, tiles, 1, steps, cap);
+      gpcg_status st = get_graph(sc, tiles, 1, steps, cap, feat);
       if (st != GPCG_OK) return st;
       CK(cudaGraphLaunch(sc.gexec, s));
       CK(cudaMemcpyAsync(&sc.h_pin[0], sc.d_live, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -935,7 +946,7 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   CK(cudaMemcpyAsync(sc.d_insts, insts.data(), sizeof(DevInst) * count, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_ctl, ctl.data(), sizeof(Ctl) * count, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_tiles, table.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice, s));
-  gpcg_status run = run_engine(sc, count, tiles, s);
+  gpcg_status run = run_engine(sc, count, tiles, s, feature_set(o));
   if (run != GPCG_OK && run != GPCG_ERR_TIMEOUT) return run;
   CK(cudaMemcpyAsync(ctl.data(), sc.d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -1021,6 +1032,13 @@ static bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The pass kernel's feature set a pass needs.
+static int pass_feature(int pass) {
+  if (pass == P_CG_Z) return FEAT_TILE;
+  if (pass >= P_RX_COUNT && pass <= P_RW) return FEAT_EXT;
+  return 0;
+}
+
 static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
   Scratch& sc = p->sc;
   gpcg_status st = sc.ensure(1, p->n_groups);
@@ -1039,7 +1057,7 @@ static gpcg_status one_pass(gpcg_problem* p, Ctl C, cudaStream_t s, Ctl* out) {
   CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
   EngineArgs E{sc.d_insts, sc.d_ctl,  sc.d_tiles,    p->n_groups, sc.d_queue, (unsigned*)(sc.d_queue + 1),
                sc.d_live,   sc.d_npass, sc.d_queue + 2, 0xffffffffu, 0ull};
-  CK(launch_pass(E, pass_grid(p->n_groups), s));
+  CK(launch_pass(E, pass_grid(p->n_groups), s, pass_feature(C.pass)));
   if (out) {
     CK(cudaMemcpyAsync(out, sc.d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1452,7 +1470,7 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
   for (int k = 0; k < reps; ++k) {
     if (flush) CK(cudaMemsetAsync(flush, k & 0xff, flush_bytes, s));
     CK(cudaEventRecord(ev[2 * k], s));
-    CK(launch_pass(E, grid, s));
+    CK(launch_pass(E, grid, s, 0));
     CK(cudaEventRecord(ev[2 * k + 1], s));
   }
   CK(cudaStreamSynchronize(s));
@@ -1655,7 +1673,7 @@ extern "C" gpcg_status gpcg_server_step(gpcg_server* s, int passes) {
   }
   s->sc.h_pin[0] = live;
   CK(cudaMemcpyAsync(s->sc.d_live, &s->sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, st_));
-  gpcg_status st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu);
+  gpcg_status st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu, feature_set(&s->opt));
   if (st != GPCG_OK) return st;
   CK(cudaGraphLaunch(s->sc.gexec, st_));
   std::vector<Ctl> ctl(s->max_live);

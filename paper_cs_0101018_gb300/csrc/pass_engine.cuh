@@ -1,0 +1,3473 @@
+// pass_engine.cuh -- the GPCG engine's pass kernel and its device code.
+//
+// Included by the translation units that instantiate the pass kernel: one
+// per feature set (gpcg_kernels.cu: the default passes; gpcg_pass_tile.cu:
+// with the tile preconditioner; gpcg_pass_rx.cu: with the explicit reduced
+// system), so that the default kernel carries none of the optional code.
+//
+// One kernel, pass_kernel, runs every pass of Algorithm GPCG (Sec. 3 of
+// Benson, McInnes & More) for every live instance.  The grid is persistent
+// (a few CTAs per SM); CTAs pull work items -- one 64x32 tile of one plane of
+// one instance -- from a queue, perform the pass the instance's state machine
+// asks for, and deposit the tile's partial sums in the tile's own slot.  The
+// last CTA to finish a tile of an instance reduces that instance's slots in a
+// fixed order and runs the state-machine transition (finalize below), so an
+// instance's arithmetic depends only on the instance, never on the schedule or
+// on the other instances in the launch.
+//
+// Stencil passes stream each operand once: a warp walks down its 64-column
+// strip keeping the operand of rows y-1, y, y+1 in registers; east/west
+// neighbours come from the adjacent lane by shuffle (lanes 0 and 31 load the
+// point beyond the strip), and the planes above/below of a 3-D grid are
+// loaded directly.  The operand is computed from its inputs on the fly (for
+// example p = -r + beta*p in the CG pass, or P[x + alpha*d] in a trial), so no
+// pass writes a vector that another CTA of the same launch reads.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so FP64 work is
+// kept to the arithmetic the method needs: comparisons against the bounds and
+// sign tests are done on the IEEE bit patterns with integer instructions, the
+// FP32 passes accumulate their dot products with error-free transformations
+// in FP32 (Ogita, Rump & Oishi, "Accurate sum and dot product", SISC 2005,
+// algorithm Dot2) and convert to FP64 once per thread and tile, and the
+// per-tile reduction runs through shared memory with one warp.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "engine.h"
+
+namespace gpcg {
+// internal linkage: every translation unit that includes this header has its
+// own copy of the device code and instantiates the pass kernel it needs
+namespace {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------- FP64 tests on the bits --
+// Inputs are checked to be NaN-free when a problem is created, so every value
+// reaching these helpers is a number.
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Integer key with the order of the doubles (-0 sorts just below +0).
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// a == b as numbers (+0 == -0).
+__device__ __forceinline__ bool deq(double a, double b) {
+  const long long x = dbits(a), y = dbits(b);
+  return x == y || ((x | y) << 1) == 0;
+}
+
+constexpr long long kNegZero = (long long)0x8000000000000000ULL;
+__device__ __forceinline__ bool dge0(double a) {
+  const long long x = dbits(a);
+  return x >= 0 || x == kNegZero;
+}
+__device__ __forceinline__ bool dle0(double a) { return dbits(a) <= 0; }
+__device__ __forceinline__ bool dlt0(double a) {
+  const long long x = dbits(a);
+  return x < 0 && x != kNegZero;
+}
+__device__ __forceinline__ bool dgt0(double a) { return dbits(a) > 0; }
+
+// median of {l, u, x} for l <= u: the projection P of Sec. 3; returns l or u
+// bit for bit when x lies outside [l, u]
+__device__ __forceinline__ double mid3(double l, double u, double x) {
+  const long long kx = dkey(x);
+  if (kx < dkey(l)) return l;
+  if (kx > dkey(u)) return u;
+  return x;
+}
+
+// Projected gradient component, Eq. proj-gradient; a fixed variable
+// (l == u) has component 0.
+__device__ __forceinline__ double pg_comp(double x, double g, double l, double u) {
+  const bool al = deq(x, l), au = deq(x, u);
+  if (al && au) return 0.0;
+  if (al) return dlt0(g) ? g : 0.0;
+  if (au) return dgt0(g) ? g : 0.0;
+  return g;
+}
+
+// FP32 projection and projected gradient of the mixed phase (the exact FP64
+// versions above decide the active set; these only feed FP32 products).
+__device__ __forceinline__ float mid3f(float l, float u, float x) { return fminf(fmaxf(x, l), u); }
+
+__device__ __forceinline__ float pg_compf(bool al, bool au, float g) {
+  if (al && au) return 0.0f;
+  if (al) return g < 0.0f ? g : 0.0f;
+  if (au) return g > 0.0f ? g : 0.0f;
+  return g;
+}
+
+// ---------------------------------------------- FP32 compensated dot (Dot2) --
+
+struct FF {
+  float hi, lo;
+};
+
+// s += a*b with the product error (TwoProduct by FMA) and the addition error
+// (TwoSum) accumulated in s.lo.
+__device__ __forceinline__ void ff_fma(FF& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s.hi, p);
+  const float z = __fsub_rn(t, s.hi);
+  const float e = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(pe, e));
+}
+
+__device__ __forceinline__ double ff_val(const FF& s) { return (double)s.hi + (double)s.lo; }
+
+// a + b in float-float arithmetic (TwoSum of the high parts, then a fast
+// renormalisation).
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+  const float hi = __fadd_rn(s, lo);
+  return FF{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+
+// Add a thread's FP32 partial of one chunk to its float-float accumulator.
+__device__ __forceinline__ void ff_acc(FF& a, float v) { a = ff_add(a, FF{v, 0.0f}); }
+
+// ------------------------------------------------------- TMA and mbarrier --
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+// Add `bytes` to the transaction count of the barrier's current phase
+// without arriving (for copies issued beside an arrive.expect_tx).
+__device__ __forceinline__ void mbar_expect_only(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after a bounded number of
+// polls (returns false) so that a lost copy can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 2-D tiled bulk tensor copy global -> shared, completing on `bar`.  The x
+// coordinate is always a multiple of 16 bytes; y may be -1 or beyond the
+// last row (the unit fills zeros there).
+__device__ __forceinline__ void tma_load2d(unsigned dst, const void* map, int x, int y,
+                                           unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// The tensor maps live in global memory written by the host; make the TMA
+// unit's view of them current before first use in this CTA.
+__device__ __forceinline__ void tmap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   (unsigned long long)map)
+               : "memory");
+}
+
+// --------------------------------------------------------- memory helpers --
+
+__device__ __forceinline__ void ld2(const double* __restrict__ p, long long i, bool v0, bool v1,
+                                    double o[2]) {
+  if (v1) {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p + i));
+    o[0] = t.x;
+    o[1] = t.y;
+  } else {
+    o[0] = v0 ? __ldg(p + i) : 0.0;
+    o[1] = 0.0;
+  }
+}
+
+__device__ __forceinline__ void ld2(const float* __restrict__ p, long long i, bool v0, bool v1,
+                                    float o[2]) {
+  if (v1) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p + i));
+    o[0] = t.x;
+    o[1] = t.y;
+  } else {
+    o[0] = v0 ? __ldg(p + i) : 0.0f;
+    o[1] = 0.0f;
+  }
+}
+
+__device__ __forceinline__ void st2(double* p, long long i, bool v0, bool v1, double a, double b) {
+  if (v1) {
+    *reinterpret_cast<double2*>(p + i) = make_double2(a, b);
+  } else if (v0) {
+    p[i] = a;
+  }
+}
+
+__device__ __forceinline__ void st2(float* p, long long i, bool v0, bool v1, float a, float b) {
+  if (v1) {
+    *reinterpret_cast<float2*>(p + i) = make_float2(a, b);
+  } else if (v0) {
+    p[i] = a;
+  }
+}
+
+// Spread the low 16 bits of v to the even bit positions of a 32-bit word.
+__device__ __forceinline__ unsigned spread16(unsigned v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+// Per-thread partial results of a pass: up to 4 FP64 sums and 3 counts.
+struct Acc {
+  double s[4];
+  int c[3];
+};
+
+// What a tile needs from the instance's control block (read once per tile).
+struct Snap {
+  int pass, cur, pcur, cg32, first_cg, dir, gp32, x32_live;
+  int m, pad;  // explicit reduced system: free points of the phase
+  double alpha, beta;
+};
+
+__device__ __forceinline__ long long row_index(const DevInst& I, int y, int z) {
+  return (long long)z * I.ny + y;
+}
+
+__device__ __forceinline__ bool row_ok(const DevInst& I, int y, int z) {
+  return y >= 0 && y < I.ny && z >= 0 && z < I.nz;
+}
+
+__device__ __forceinline__ long long pidx(const DevInst& I, int y, int z, int col) {
+  return (long long)z * I.plane + (long long)y * I.px + col;
+}
+
+// The two free bits of this lane's points (e0, e0+1) in row (y, z).
+__device__ __forceinline__ unsigned my_free_bits(const DevInst& I, const unsigned* __restrict__ m,
+                                                 int y, int z, int e0) {
+  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (e0 >> 5));
+  return (w >> (e0 & 31)) & 3u;
+}
+
+__device__ __forceinline__ bool free_bit(const DevInst& I, const unsigned* __restrict__ m, int y,
+                                         int z, int col) {
+  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (col >> 5));
+  return (w >> (col & 31)) & 1u;
+}
+
+// Write the free bits of a warp's 64-column strip (two words) for row (y,z);
+// returns, for lanes 0 and 16, the number of bits that differ from `old`
+// (nullptr: 0).
+__device__ __forceinline__ int write_mask(const DevInst& I, unsigned* m, const unsigned* old,
+                                          int y, int z, int x0, int lane, bool f0, bool f1) {
+  const unsigned b0 = __ballot_sync(FULL_MASK, f0);
+  const unsigned b1 = __ballot_sync(FULL_MASK, f1);
+  int diff = 0;
+  if ((lane & 15) == 0) {
+    const int h = lane >> 4;
+    const int wcol = (x0 >> 5) + h;
+    if (wcol < I.mw) {
+      const unsigned word = spread16(b0 >> (16 * h)) | (spread16(b1 >> (16 * h)) << 1);
+      const long long wi = row_index(I, y, z) * I.mw + wcol;
+      m[wi] = word;
+      if (old) diff = __popc(word ^ __ldg(old + wi));
+    }
+  }
+  return diff;
+}
+
+// ---------------------------------------------------------- stencil sweep --
+//
+// Op supplies the operand v of the pass at any point (operand_row for the
+// lane's two points of a row, operand_at for one point) and consumes, for
+// each row of the strip, v and (A v) at the lane's two points (output).
+
+template <class Op>
+__device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int x0, int y0, int z,
+                                             Acc& acc) {
+  using T = typename Op::T;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;  // warp-uniform
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const long long zb = (long long)z * I.plane;
+  const T* __restrict__ diag = op.diag();
+  const T* __restrict__ cx = op.cx();
+  const T* __restrict__ cy = op.cy();
+  const T* __restrict__ cz = op.cz();
+
+  T vm[2], vc[2], vn[2], cs[2];
+  op.operand_row(ya - 1, z, e0, v0, v1, vm);
+  op.operand_row(ya, z, e0, v0, v1, vc);
+  if (ya > 0) {
+    ld2(cy, zb + (long long)(ya - 1) * I.px + e0, v0, v1, cs);
+  } else {
+    cs[0] = cs[1] = T(0);
+  }
+#pragma unroll 1
+  for (int y = ya; y < yb; ++y) {
+    op.operand_row(y + 1, z, e0, v0, v1, vn);
+    const long long i = zb + (long long)y * I.px + e0;
+    T d[2], ce[2], cn[2];
+    ld2(diag, i, v0, v1, d);
+    ld2(cx, i, v0, v1, ce);
+    ld2(cy, i, v0, v1, cn);
+    T vw = __shfl_up_sync(FULL_MASK, vc[1], 1);
+    T cw = __shfl_up_sync(FULL_MASK, ce[1], 1);
+    T ve = __shfl_down_sync(FULL_MASK, vc[0], 1);
+    if (lane == 0) {
+      const bool has = v0 && e0 > 0;
+      vw = has ? op.operand_at(i - 1, y, z, e0 - 1) : T(0);
+      cw = has ? __ldg(cx + i - 1) : T(0);
+    }
+    if (lane == 31) ve = (e0 + 2 < I.nx) ? op.operand_at(i + 2, y, z, e0 + 2) : T(0);
+    T av[2];
+    // row sums in the order diag, west, east, south, north (, down, up)
+    av[0] = d[0] * vc[0];
+    av[0] = fma(cw, vw, av[0]);
+    av[0] = fma(ce[0], vc[1], av[0]);
+    av[0] = fma(cs[0], vm[0], av[0]);
+    av[0] = fma(cn[0], vn[0], av[0]);
+    av[1] = d[1] * vc[1];
+    av[1] = fma(ce[0], vc[0], av[1]);
+    av[1] = fma(ce[1], ve, av[1]);
+    av[1] = fma(cs[1], vm[1], av[1]);
+    av[1] = fma(cn[1], vn[1], av[1]);
+    if (I.dim == 3) {
+      T vd[2], vu[2], czd[2], czu[2];
+      op.operand_row(y, z - 1, e0, v0, v1, vd);
+      op.operand_row(y, z + 1, e0, v0, v1, vu);
+      if (z > 0) {
+        ld2(cz, i - I.plane, v0, v1, czd);
+      } else {
+        czd[0] = czd[1] = T(0);
+      }
+      ld2(cz, i, v0, v1, czu);
+      av[0] = fma(czd[0], vd[0], av[0]);
+      av[0] = fma(czu[0], vu[0], av[0]);
+      av[1] = fma(czd[1], vd[1], av[1]);
+      av[1] = fma(czu[1], vu[1], av[1]);
+    }
+    op.output(y, z, i, x0, e0, lane, v0, v1, vc, av, acc);
+    vm[0] = vc[0];
+    vm[1] = vc[1];
+    vc[0] = vn[0];
+    vc[1] = vn[1];
+    cs[0] = cn[0];
+    cs[1] = cn[1];
+  }
+}
+
+// P_CENSUS: operand x; g = Ax + b and everything Sec. 2 defines at x:
+// sums ||pg||^2 and <x, g + b> (= 2 (q - c)), counts |A(x)| and |B(x)|.
+//
+// After the mixed phase (x32 != nullptr) the iterate is rebuilt from the
+// FP32 one first: a point on an FP32 bound goes to the FP64 bound, any other
+// to P[x32] (the projection of Sec. 3 onto the FP64 box); x_out receives it.
+struct OpCensus {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  double* g_out;
+  unsigned* m_out;
+  const float* __restrict__ x32;
+  double* x_out;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ double rebuild(float xf, double l, double u, float lf, float uf) const {
+    if (xf == lf) return l;
+    if (xf == uf) return u;
+    return mid3(l, u, (double)xf);
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    if (x32) {
+      float xf[2], lf[2], uf[2];
+      double l[2], u[2];
+      ld2(x32, i, v0, v1, xf);
+      ld2(I.l32, i, v0, v1, lf);
+      ld2(I.u32, i, v0, v1, uf);
+      ld2(I.l, i, v0, v1, l);
+      ld2(I.u, i, v0, v1, u);
+      o[0] = v0 ? rebuild(xf[0], l[0], u[0], lf[0], uf[0]) : 0.0;
+      o[1] = v1 ? rebuild(xf[1], l[1], u[1], lf[1], uf[1]) : 0.0;
+    } else {
+      ld2(x, i, v0, v1, o);
+    }
+  }
+  __device__ double operand_at(long long i, int, int, int) const {
+    if (x32)
+      return rebuild(__ldg(x32 + i), __ldg(I.l + i), __ldg(I.u + i), __ldg(I.l32 + i),
+                     __ldg(I.u32 + i));
+    return __ldg(x + i);
+  }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const double v[2], const double av[2], Acc& acc) const {
+    double b[2], l[2], u[2], g[2];
+    ld2(I.b, i, v0, v1, b);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      g[k] = av[k] + b[k];
+      const bool al = deq(v[k], l[k]), au = deq(v[k], u[k]);
+      const bool act = al || au;
+      const bool bind = (al && dge0(g[k])) || (au && dle0(g[k]));
+      fr[k] = ok && !act;
+      if (ok) {
+        const double pg = pg_comp(v[k], g[k], l[k], u[k]);
+        acc.s[0] = fma(pg, pg, acc.s[0]);
+        acc.s[1] = fma(v[k], g[k] + b[k], acc.s[1]);
+        acc.c[0] += act;
+        acc.c[1] += bind;
+      }
+    }
+    st2(g_out, i, v0, v1, g[0], g[1]);
+    if (x32) st2(x_out, i, v0, v1, v[0], v[1]);
+    write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// P_GP_ALPHA: operand pg = grad_Omega q(x); sums <pg,pg> and <pg, A pg>.
+struct OpGpAlpha {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const double* __restrict__ g;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    double xv[2], gv[2], l[2], u[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(g, i, v0, v1, gv);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    o[0] = v0 ? pg_comp(xv[0], gv[0], l[0], u[0]) : 0.0;
+    o[1] = v1 ? pg_comp(xv[1], gv[1], l[1], u[1]) : 0.0;
+  }
+  __device__ double operand_at(long long i, int, int, int) const {
+    return pg_comp(__ldg(x + i), __ldg(g + i), __ldg(I.l + i), __ldg(I.u + i));
+  }
+  __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const double v[2],
+                         const double av[2], Acc& acc) const {
+    if (v0) {
+      acc.s[0] = fma(v[0], v[0], acc.s[0]);
+      acc.s[1] = fma(v[0], av[0], acc.s[1]);
+    }
+    if (v1) {
+      acc.s[0] = fma(v[1], v[1], acc.s[0]);
+      acc.s[1] = fma(v[1], av[1], acc.s[1]);
+    }
+  }
+};
+
+// P_TRIAL: operand xt = P[x + alpha*dir] (Eq. next-y with dir = -grad q, or
+// the projected search along d with dir = w); gt = A xt + b; sums <g, s> and
+// <s, gt> with s = xt - x (q(xt) - q(x) = 1/2 (<g,s> + <s,gt>) exactly for a
+// quadratic) and ||grad_Omega q(xt)||^2; counts |A(xt)|, |B(xt)| and the
+// number of points whose active/free status changed (Eq. pgstop1).
+template <int DK>
+struct OpTrial {
+  using T = double;
+  const DevInst& I;
+  const double* __restrict__ x;
+  const double* __restrict__ g;
+  const double* __restrict__ w64;
+  const float* __restrict__ w32;
+  double alpha;
+  double* xt_out;
+  double* gt_out;
+  unsigned* m_out;
+  const unsigned* __restrict__ m_old;
+  __device__ const double* diag() const { return I.diag; }
+  __device__ const double* cx() const { return I.cx; }
+  __device__ const double* cy() const { return I.cy; }
+  __device__ const double* cz() const { return I.cz; }
+  __device__ void dir2(long long i, bool v0, bool v1, double d[2]) const {
+    if (DK == D_NEG_G) {
+      ld2(g, i, v0, v1, d);
+      d[0] = -d[0];
+      d[1] = -d[1];
+    } else if (DK == D_W64) {
+      ld2(w64, i, v0, v1, d);
+    } else {
+      float f[2];
+      ld2(w32, i, v0, v1, f);
+      d[0] = (double)f[0];
+      d[1] = (double)f[1];
+    }
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, double o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    double xv[2], d[2], l[2], u[2];
+    ld2(x, i, v0, v1, xv);
+    dir2(i, v0, v1, d);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    o[0] = v0 ? mid3(l[0], u[0], fma(alpha, d[0], xv[0])) : 0.0;
+    o[1] = v1 ? mid3(l[1], u[1], fma(alpha, d[1], xv[1])) : 0.0;
+  }
+  __device__ double operand_at(long long i, int, int, int) const {
+    double dv;
+    if (DK == D_NEG_G) dv = -__ldg(g + i);
+    else if (DK == D_W64) dv = __ldg(w64 + i);
+    else dv = (double)__ldg(w32 + i);
+    return mid3(__ldg(I.l + i), __ldg(I.u + i), fma(alpha, dv, __ldg(x + i)));
+  }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const double v[2], const double av[2], Acc& acc) const {
+    double xv[2], gv[2], b[2], l[2], u[2], gt[2];
+    ld2(x, i, v0, v1, xv);
+    ld2(g, i, v0, v1, gv);
+    ld2(I.b, i, v0, v1, b);
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      gt[k] = av[k] + b[k];
+      const bool al = deq(v[k], l[k]), au = deq(v[k], u[k]);
+      const bool act = al || au;
+      const bool bind = (al && dge0(gt[k])) || (au && dle0(gt[k]));
+      fr[k] = ok && !act;
+      if (ok) {
+        const double s = v[k] - xv[k];
+        acc.s[0] = fma(gv[k], s, acc.s[0]);
+        acc.s[1] = fma(s, gt[k], acc.s[1]);
+        const double pg = pg_comp(v[k], gt[k], l[k], u[k]);
+        acc.s[2] = fma(pg, pg, acc.s[2]);
+        acc.c[0] += act;
+        acc.c[1] += bind;
+      }
+    }
+    st2(xt_out, i, v0, v1, v[0], v[1]);
+    st2(gt_out, i, v0, v1, gt[0], gt[1]);
+    acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+
+// ------------------------------------------------- mixed-phase FP32 passes --
+//
+// In the mixed phase the census, the alpha0 pass and the trials work on the
+// FP32 iterate x32, kept on the FP32 box [l32, u32] by the FP32 projection
+// (which returns the bound itself when it clamps): a point is active when x32
+// equals l32 or u32.  The FP32 stencil is applied to FP32 operands and the
+// gradient is kept in FP32; sums use the compensated FP32 accumulator.  The
+// first FP64 census after the phase rebuilds the FP64 iterate (OpCensus).
+
+// P_CENSUS (mixed): operand x32; g32 = A32 x32 + b32, pg32; |A|, |B|,
+// ||pg||^2.
+struct OpCensus32 {
+  using T = float;
+  const DevInst& I;
+  const float* __restrict__ x32;
+  float* g_out;
+  float* pg_out;
+  unsigned* m_out;
+  FF* ff;  // [1]: ||pg||^2
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    ld2(x32, pidx(I, y, z, e0), v0, v1, o);
+  }
+  __device__ float operand_at(long long i, int, int, int) const { return __ldg(x32 + i); }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const float v[2], const float av[2], Acc& acc) const {
+    float l[2], u[2], b[2], g[2], pg[2];
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
+    ld2(I.b32, i, v0, v1, b);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      g[k] = av[k] + b[k];
+      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool act = al || au;
+      fr[k] = ok && !act;
+      pg[k] = pg_compf(al, au, g[k]);
+      if (ok) {
+        ff_fma(ff[0], pg[k], pg[k]);
+        acc.c[0] += act;
+        acc.c[1] += (al && g[k] >= 0.0f) || (au && g[k] <= 0.0f);
+      }
+    }
+    st2(g_out, i, v0, v1, g[0], g[1]);
+    st2(pg_out, i, v0, v1, pg[0], pg[1]);
+    write_mask(I, m_out, nullptr, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// P_GP_ALPHA (mixed): operand pg32 (written by the census or the accepted
+// trial at x); <pg,pg>, <pg, A32 pg>.
+struct OpGpAlpha32 {
+  using T = float;
+  const DevInst& I;
+  const float* __restrict__ pg32;
+  FF* ff;  // [2]
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    ld2(pg32, pidx(I, y, z, e0), v0, v1, o);
+  }
+  __device__ float operand_at(long long i, int, int, int) const { return __ldg(pg32 + i); }
+  __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const float v[2],
+                         const float av[2], Acc&) const {
+    if (v0) {
+      ff_fma(ff[0], v[0], v[0]);
+      ff_fma(ff[1], v[0], av[0]);
+    }
+    if (v1) {
+      ff_fma(ff[0], v[1], v[1]);
+      ff_fma(ff[1], v[1], av[1]);
+    }
+  }
+};
+
+// P_TRIAL (mixed): operand xt32 = P[x32 + alpha d] on the FP32 box;
+// g32t = A32 xt32 + b32, the status of xt32, pg32; <g, s>, <s, gt>,
+// ||pg||^2 with s = xt32 - x32.
+template <int DK>
+struct OpTrial32 {
+  using T = float;
+  const DevInst& I;
+  const float* __restrict__ x32;
+  const float* __restrict__ g32;
+  const float* __restrict__ w32;
+  float alpha;
+  float* xt32_out;
+  float* gt_out;
+  float* pg_out;
+  unsigned* m_out;
+  const unsigned* __restrict__ m_old;
+  FF* ff;  // [3]: <g,s>, <s,gt>, ||pg||^2
+  __device__ const float* diag() const { return I.diag32; }
+  __device__ const float* cx() const { return I.cx32; }
+  __device__ const float* cy() const { return I.cy32; }
+  __device__ const float* cz() const { return I.cz32; }
+  __device__ float dir_at(long long i) const {
+    return DK == D_NEG_G ? -__ldg(g32 + i) : __ldg(w32 + i);
+  }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = 0.0f;
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    float xv[2], l[2], u[2], d[2];
+    ld2(x32, i, v0, v1, xv);
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
+    if (DK == D_NEG_G) {
+      ld2(g32, i, v0, v1, d);
+      d[0] = -d[0];
+      d[1] = -d[1];
+    } else {
+      ld2(w32, i, v0, v1, d);
+    }
+    o[0] = v0 ? mid3f(l[0], u[0], fmaf(alpha, d[0], xv[0])) : 0.0f;
+    o[1] = v1 ? mid3f(l[1], u[1], fmaf(alpha, d[1], xv[1])) : 0.0f;
+  }
+  __device__ float operand_at(long long i, int, int, int) const {
+    return mid3f(__ldg(I.l32 + i), __ldg(I.u32 + i), fmaf(alpha, dir_at(i), __ldg(x32 + i)));
+  }
+  __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
+                         const float v[2], const float av[2], Acc& acc) const {
+    float xv[2], l[2], u[2], g[2], b[2], gt[2], pg[2];
+    ld2(x32, i, v0, v1, xv);
+    ld2(I.l32, i, v0, v1, l);
+    ld2(I.u32, i, v0, v1, u);
+    ld2(g32, i, v0, v1, g);
+    ld2(I.b32, i, v0, v1, b);
+    bool fr[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const bool ok = k == 0 ? v0 : v1;
+      gt[k] = av[k] + b[k];
+      const bool al = v[k] == l[k], au = v[k] == u[k];
+      const bool act = al || au;
+      fr[k] = ok && !act;
+      pg[k] = pg_compf(al, au, gt[k]);
+      if (ok) {
+        const float sk = v[k] - xv[k];
+        ff_fma(ff[0], g[k], sk);
+        ff_fma(ff[1], sk, gt[k]);
+        ff_fma(ff[2], pg[k], pg[k]);
+        acc.c[0] += act;
+        acc.c[1] += (al && gt[k] >= 0.0f) || (au && gt[k] <= 0.0f);
+      }
+    }
+    st2(xt32_out, i, v0, v1, v[0], v[1]);
+    st2(gt_out, i, v0, v1, gt[0], gt[1]);
+    st2(pg_out, i, v0, v1, pg[0], pg[1]);
+    acc.c[2] += write_mask(I, m_out, m_old, y, z, x0, lane, fr[0], fr[1]);
+  }
+};
+
+// The first CG step's r_0 = g_F and M^-1 Ap under point Jacobi, out of line:
+// it runs once per CG phase and, inlined, raises the register pressure of the
+// whole sweep.
+template <class T>
+__device__ __noinline__ void first_step_jacobi(const float* __restrict__ g32,
+                                               const double* __restrict__ g,
+                                               const T* __restrict__ dinv, long long i, bool v0,
+                                               bool v1, unsigned fb, T* rv, T* da) {
+  T di[2];
+  ld2(dinv, i, v0, v1, di);
+  double gv[2];
+  if (g32) {
+    float gf[2];
+    ld2(g32, i, v0, v1, gf);
+    gv[0] = gf[0];
+    gv[1] = gf[1];
+  } else {
+    ld2(g, i, v0, v1, gv);
+  }
+  rv[0] = (fb & 1u) ? (T)gv[0] : T(0);
+  rv[1] = (fb & 2u) ? (T)gv[1] : T(0);
+  da[0] *= di[0];
+  da[1] *= di[1];
+}
+
+// P_CG_B: operand p = -r + beta*p_old (FIRST: p = -g on the free set), the
+// masked product Ap = Z Z' A Z Z' p of Eq. cg2 and <p, Ap> (FIRST: also
+// ||r||^2 for r = g_F).  TV is the streamed precision (double, or float in the
+// mixed CG, whose sums use the compensated FP32 accumulator).
+template <class TV, bool FIRST, bool JAC = false>
+struct OpCgB {
+  using T = TV;
+  static constexpr bool kF32 = sizeof(TV) == 4;
+  const DevInst& I;
+  const T* __restrict__ r;
+  const T* __restrict__ p_old;
+  const double* __restrict__ g;
+  const unsigned* __restrict__ m;
+  T beta;
+  const float* __restrict__ g32;  // mixed phase: the gradient is FP32 (FIRST)
+  T* p_out;
+  T* ap_out;
+  T* r_out;
+  T* w_out;
+  const T* bd;
+  const T* bx;
+  const T* by;
+  const T* bz;
+  FF* ff;  // [3] FP32 accumulators (kF32)
+  const T* __restrict__ dinv;  // 1/diag (point Jacobi, z = r / diag), or nullptr
+  __device__ const T* diag() const { return bd; }
+  __device__ const T* cx() const { return bx; }
+  __device__ const T* cy() const { return by; }
+  __device__ const T* cz() const { return bz; }
+  __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, T o[2]) const {
+    if (!row_ok(I, y, z)) {
+      o[0] = o[1] = T(0);
+      return;
+    }
+    const long long i = pidx(I, y, z, e0);
+    if (FIRST) {
+      double gv[2];
+      if (g32) {
+        float gf[2];
+        ld2(g32, i, v0, v1, gf);
+        gv[0] = gf[0];
+        gv[1] = gf[1];
+      } else {
+        ld2(g, i, v0, v1, gv);
+      }
+      const unsigned fb = (v0 ? my_free_bits(I, m, y, z, e0) : 0u);
+      T zv[2] = {(T)gv[0], (T)gv[1]};
+      if (JAC) {
+        T di[2];
+        ld2(dinv, i, v0, v1, di);
+        zv[0] *= di[0];
+        zv[1] *= di[1];
+      }
+      o[0] = (fb & 1u) ? -zv[0] : T(0);
+      o[1] = (fb & 2u) ? -zv[1] : T(0);
+    } else {
+      T rv[2], pv[2];
+      ld2(r, i, v0, v1, rv);
+      ld2(p_old, i, v0, v1, pv);
+      if (JAC) {
+        T di[2];
+        ld2(dinv, i, v0, v1, di);
+        rv[0] *= di[0];
+        rv[1] *= di[1];
+      }
+      o[0] = fma(beta, pv[0], -rv[0]);
+      o[1] = fma(beta, pv[1], -rv[1]);
+    }
+  }
+  __device__ T operand_at(long long i, int y, int z, int col) const {
+    const T di = JAC ? __ldg(dinv + i) : T(1);
+    if (FIRST) {
+      if (!free_bit(I, m, y, z, col)) return T(0);
+      return -(g32 ? (T)__ldg(g32 + i) : (T)__ldg(g + i)) * di;
+    } else {
+      return fma(beta, __ldg(p_old + i), -__ldg(r + i) * di);
+    }
+  }
+  __device__ void output(int y, int z, long long i, int, int e0, int, bool v0, bool v1,
+                         const T v[2], const T av[2], Acc& acc) const {
+    const unsigned fb = v0 ? my_free_bits(I, m, y, z, e0) : 0u;
+    const T a0 = (fb & 1u) ? av[0] : T(0);
+    const T a1 = (fb & 2u) ? av[1] : T(0);
+    st2(ap_out, i, v0, v1, a0, a1);
+    st2(p_out, i, v0, v1, v[0], v[1]);
+    if (kF32) {
+      ff_fma(ff[0], (float)v[0], (float)a0);
+      ff_fma(ff[0], (float)v[1], (float)a1);
+    } else {
+      acc.s[0] = fma((double)v[0], (double)a0, acc.s[0]);
+      acc.s[0] = fma((double)v[1], (double)a1, acc.s[0]);
+    }
+    if (FIRST) {
+      // r = g_F (v = -z = -M^-1 r); rho = <r, z>; <Ap, M^-1 Ap> (the fused
+      // steps predict rho_1 from them)
+      T rv[2] = {-v[0], -v[1]}, da[2] = {a0, a1};
+      if (JAC) first_step_jacobi<T>(g32, g, dinv, i, v0, v1, fb, rv, da);
+      st2(r_out, i, v0, v1, rv[0], rv[1]);
+      st2(w_out, i, v0, v1, T(0), T(0));
+      if (kF32) {
+        ff_fma(ff[1], (float)rv[0], -(float)v[0]);
+        ff_fma(ff[1], (float)rv[1], -(float)v[1]);
+        ff_fma(ff[2], (float)a0, (float)da[0]);
+        ff_fma(ff[2], (float)a1, (float)da[1]);
+      } else {
+        acc.s[1] = fma((double)rv[0], -(double)v[0], acc.s[1]);
+        acc.s[1] = fma((double)rv[1], -(double)v[1], acc.s[1]);
+        acc.s[2] = fma((double)a0, (double)da[0], acc.s[2]);
+        acc.s[2] = fma((double)a1, (double)da[1], acc.s[2]);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------- pointwise passes
+
+// P_CG_A: w += alpha p, r_out = r + alpha Ap, <r_out, M^-1 r_out> (M = I or
+// diag(A) with dinv).
+template <class T, bool JAC>
+__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* __restrict__ r,
+                                          T* r_out, const T* __restrict__ p,
+                                          const T* __restrict__ ap, const T* __restrict__ dinv,
+                                          double alpha, int x0, int y0, int z, Acc& acc,
+                                          FF* ffs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (!v0) return;
+  const T a = (T)alpha;
+  FF& ff = ffs[0];
+  for (int y = ya; y < yb; ++y) {
+    const long long i = pidx(I, y, z, e0);
+    T wv[2], rv[2], pv[2], av[2];
+    ld2(w, i, v0, v1, wv);
+    ld2(r, i, v0, v1, rv);
+    ld2(p, i, v0, v1, pv);
+    ld2(ap, i, v0, v1, av);
+    wv[0] = fma(a, pv[0], wv[0]);
+    wv[1] = fma(a, pv[1], wv[1]);
+    rv[0] = fma(a, av[0], rv[0]);
+    rv[1] = fma(a, av[1], rv[1]);
+    st2(w, i, v0, v1, wv[0], wv[1]);
+    st2(r_out, i, v0, v1, rv[0], rv[1]);
+    T zv[2] = {rv[0], rv[1]};  // z = M^-1 r (point Jacobi) or r
+    if (JAC) {
+      T di[2];
+      ld2(dinv, i, v0, v1, di);
+      zv[0] *= di[0];
+      zv[1] *= di[1];
+    }
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)rv[0], (float)zv[0]);
+      ff_fma(ff, (float)rv[1], (float)zv[1]);
+    } else {
+      acc.s[0] = fma((double)rv[0], (double)zv[0], acc.s[0]);
+      acc.s[0] = fma((double)rv[1], (double)zv[1], acc.s[0]);
+    }
+  }
+}
+
+// P_START: x = P[x0], x0 the given start or the default l -> u -> 0.
+__device__ __forceinline__ void start_tile(const DevInst& I, double* x, float* x32, int x0, int y0,
+                                           int z) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ya = y0 + warp * kRY;
+  if (ya >= I.ny) return;
+  const int yb = min(ya + kRY, I.ny);
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (!v0) return;
+  for (int y = ya; y < yb; ++y) {
+    const long long i = pidx(I, y, z, e0);
+    double l[2], u[2], s[2];
+    ld2(I.l, i, v0, v1, l);
+    ld2(I.u, i, v0, v1, u);
+    if (I.opt.use_x0) {
+      ld2(I.x0, i, v0, v1, s);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) s[k] = isfinite(l[k]) ? l[k] : (isfinite(u[k]) ? u[k] : 0.0);
+    }
+    const double a = mid3(l[0], u[0], s[0]), b = mid3(l[1], u[1], s[1]);
+    st2(x, i, v0, v1, a, b);
+    if (x32) st2(x32, i, v0, v1, (float)a, (float)b);
+  }
+}
+
+// ------------------------------------------------- tile preconditioner --
+//
+// M of the tile preconditioner (the analogue of the block Jacobi with one
+// block per processor of Sec. 6): one block per 64 x 8 tile of an xy-plane,
+// couplings between tiles dropped; each block solved approximately by one
+// symmetric zebra line Gauss-Seidel sweep on the free set -- the x-lines of
+// the tile's even rows, then its odd rows, then its even rows, each solved
+// exactly with the current values of the lines above and below on the
+// right-hand side.  Per tile M = (D + L) D^-1 (D + U), D the line
+// tridiagonals, L and U the couplings between lines in the order (even
+// rows, odd rows); M is symmetric positive definite.  A warp holds a line
+// (lane l: columns 2l and 2l+1).  M^-1 is applied in FP32 in every phase: it
+// only shapes the search directions, which stay in the phase's precision.
+
+// One line of a tile: b0, b1 the diagonal of the lane's points (1 off the
+// free set), cw the coupling of column 2l-1 to 2l, cm of 2l to 2l+1 (0 unless
+// both points are free; cw = 0 on lane 0, the tile's edge), cn / cs the
+// couplings of the two points to the row above / below inside the tile.
+struct TileLine {
+  float b0, b1, cw, cm, cn0, cn1, cs0, cs1;
+};
+
+// Solve the warp's line system
+//   cw x[2l-1] + b0 x[2l] + cm x[2l+1] = d0,  cm x[2l] + b1 x[2l+1] + ce x[2l+2] = d1,
+// ce = the next lane's cw (0 on lane 31).  Each lane eliminates its even
+// point and its east neighbour's, which leaves one equation per lane in
+// u_l = x[2l+1]; parallel cyclic reduction (Hockney) then removes the
+// couplings at distance 1, 2, 4, 8, 16 by shuffles, after which each u_l
+// stands alone; last the even points are recovered.  The system is a
+// principal submatrix of A (symmetric positive definite), so no pivot vanishes.
+__device__ __forceinline__ void line_solve(float b0, float b1, float cw, float cm, float d0,
+                                           float d1, float& x0, float& x1) {
+  const int lane = threadIdx.x & 31;
+  const float ie = __frcp_rn(b0);
+  float ce = __shfl_down_sync(FULL_MASK, cw, 1);
+  const float ie_n = __shfl_down_sync(FULL_MASK, ie, 1);
+  const float d0_n = __shfl_down_sync(FULL_MASK, d0, 1);
+  const float cm_n = __shfl_down_sync(FULL_MASK, cm, 1);
+  if (lane == 31) ce = 0.0f;
+  float a = -cm * cw * ie;
+  float b = b1 - cm * cm * ie - ce * ce * ie_n;
+  float c = -ce * cm_n * ie_n;
+  float d = d1 - cm * d0 * ie - ce * d0_n * ie_n;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const float ib = __frcp_rn(b);
+    float am = __shfl_up_sync(FULL_MASK, a, s), cmm = __shfl_up_sync(FULL_MASK, c, s);
+    float dm = __shfl_up_sync(FULL_MASK, d, s), ibm = __shfl_up_sync(FULL_MASK, ib, s);
+    float ap = __shfl_down_sync(FULL_MASK, a, s), cp = __shfl_down_sync(FULL_MASK, c, s);
+    float dp = __shfl_down_sync(FULL_MASK, d, s), ibp = __shfl_down_sync(FULL_MASK, ib, s);
+    if (lane < s) am = cmm = dm = ibm = 0.0f;
+    if (lane + s >= 32) ap = cp = dp = ibp = 0.0f;
+    const float k1 = a * ibm, k2 = c * ibp;
+    a = -k1 * am;
+    c = -k2 * cp;
+    b = b - k1 * cmm - k2 * ap;
+    d = d - k1 * dm - k2 * dp;
+  }
+  const float u = __fdiv_rn(d, b);
+  float um = __shfl_up_sync(FULL_MASK, u, 1);
+  if (lane == 0) um = 0.0f;
+  x1 = u;
+  x0 = (d0 - cw * um - cm * u) * ie;
+}
+
+// The zebra sweep over the chunk rows r0 .. r0+RPW-1 a warp holds (all warps
+// of the CTA take part; the chunk starts on a multiple of 8 rows, so the
+// parity of a chunk row is that of the grid row).  `scr`: a CTA buffer of
+// (chunk rows) x `pitch` floats through which the lines see their
+// neighbours; each warp writes only the rows it holds.  d: the right-hand
+// side (0 off the free set); x: M^-1 d on the warp's rows.
+template <int RPW>
+__device__ __forceinline__ void zebra_sweep(const TileLine (&L)[RPW], const float (&d)[RPW][2],
+                                            int r0, float* scr, int pitch, float (&x)[RPW][2]) {
+  const int c = 2 * (threadIdx.x & 31);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    if (((r0 + k) & 1) == 0) {
+      line_solve(L[k].b0, L[k].b1, L[k].cw, L[k].cm, d[k][0], d[k][1], x[k][0], x[k][1]);
+      *reinterpret_cast<float2*>(scr + (r0 + k) * pitch + c) = make_float2(x[k][0], x[k][1]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int h = 1; h >= 0; --h) {  // odd rows, then even rows again
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      const int row = r0 + k;
+      if ((row & 1) != h) continue;
+      float e0 = d[k][0], e1 = d[k][1];
+      if ((row & (kBlkY - 1)) != 0) {
+        const float2 v = *reinterpret_cast<const float2*>(scr + (row - 1) * pitch + c);
+        e0 -= L[k].cn0 * v.x;
+        e1 -= L[k].cn1 * v.y;
+      }
+      if ((row & (kBlkY - 1)) != kBlkY - 1) {
+        const float2 v = *reinterpret_cast<const float2*>(scr + (row + 1) * pitch + c);
+        e0 -= L[k].cs0 * v.x;
+        e1 -= L[k].cs1 * v.y;
+      }
+      line_solve(L[k].b0, L[k].b1, L[k].cw, L[k].cm, e0, e1, x[k][0], x[k][1]);
+      if (h == 1)
+        *reinterpret_cast<float2*>(scr + row * pitch + c) = make_float2(x[k][0], x[k][1]);
+    }
+    if (h == 1) __syncthreads();
+  }
+}
+
+// The line of row `row` (a chunk row) from its coefficients: dg = the two
+// diagonal entries, xw / xm = the couplings of columns 2l-1|2l and 2l|2l+1,
+// yn / ys = the couplings to the rows above / below; f = the free bits of the
+// lane's points in this row, fa / fb in the rows above / below.
+__device__ __forceinline__ TileLine tile_line(int row, float dg0, float dg1, float xw, float xm,
+                                              float yn0, float yn1, float ys0, float ys1,
+                                              unsigned f, unsigned fa, unsigned fb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned fw = __shfl_up_sync(FULL_MASK, f >> 1, 1) & 1u;  // column 2l-1
+  const bool f0 = f & 1u, f1 = (f >> 1) & 1u;
+  const bool top = (row & (kBlkY - 1)) == 0, bot = (row & (kBlkY - 1)) == kBlkY - 1;
+  TileLine L;
+  L.b0 = f0 ? dg0 : 1.0f;
+  L.b1 = f1 ? dg1 : 1.0f;
+  L.cw = (lane > 0 && f0 && fw) ? xw : 0.0f;
+  L.cm = (f0 && f1) ? xm : 0.0f;
+  L.cn0 = (!top && f0 && (fa & 1u)) ? yn0 : 0.0f;
+  L.cn1 = (!top && f1 && (fa & 2u)) ? yn1 : 0.0f;
+  L.cs0 = (!bot && f0 && (fb & 1u)) ? ys0 : 0.0f;
+  L.cs1 = (!bot && f1 && (fb & 2u)) ? ys1 : 0.0f;
+  return L;
+}
+
+// P_CG_Z on one 64 x 32 tile (register path, four rows per warp): the first
+// step of a tile-preconditioned CG phase: r_0 = g_F, z_0 = M^-1 r_0 and
+// rho_0 = <r_0, z_0>; p, Ap, q (buffer pcur) and w are set to 0, so that the
+// first fused step, run with alpha = beta = 0, forms p_0 = -z_0 and Ap_0.
+// The exchange buffer is the first TMA stage (no copy is in flight in a
+// register pass).
+template <class T>
+__device__ void cg_z_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
+                          float* scr, Acc& acc, FF* ffs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = warp * kRY;
+  const int e0 = x0 + 2 * lane;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const bool f32 = sizeof(T) == 4;
+  const T* bd = f32 ? (const T*)I.diag32 : (const T*)I.diag;
+  const T* bx = f32 ? (const T*)I.cx32 : (const T*)I.cx;
+  const T* by = f32 ? (const T*)I.cy32 : (const T*)I.cy;
+  const unsigned* m = I.mask[S.cur];
+  auto bits = [&](int y) -> unsigned {
+    return (v0 && y >= 0 && y < I.ny) ? my_free_bits(I, m, y, z, e0) : 0u;
+  };
+  TileLine L[kRY];
+  float d[kRY][2], x[kRY][2];
+  T rv[kRY][2];
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + r0 + k;
+    const bool ok = y < I.ny && v0;
+    const unsigned f = ok ? bits(y) : 0u;
+    T dg[2] = {T(1), T(1)}, xm[2] = {T(0), T(0)}, yn[2] = {T(0), T(0)}, ys[2] = {T(0), T(0)};
+    double gv[2] = {0.0, 0.0};
+    if (ok) {
+      const long long i = pidx(I, y, z, e0);
+      ld2(bd, i, v0, v1, dg);
+      ld2(bx, i, v0, v1, xm);
+      if (y > 0) ld2(by, i - I.px, v0, v1, yn);
+      ld2(by, i, v0, v1, ys);
+      if (S.gp32) {
+        float gf[2];
+        ld2(I.g32[S.cur], i, v0, v1, gf);
+        gv[0] = gf[0];
+        gv[1] = gf[1];
+      } else {
+        ld2(I.g[S.cur], i, v0, v1, gv);
+      }
+    }
+    // coupling of column 2l-1 to 2l: the west lane's cx of its second point
+    const float xw = __shfl_up_sync(FULL_MASK, (float)xm[1], 1);
+    L[k] = tile_line(r0 + k, (float)dg[0], (float)dg[1], xw, (float)xm[0], (float)yn[0],
+                     (float)yn[1], (float)ys[0], (float)ys[1], f, ok ? bits(y - 1) : 0u,
+                     ok ? bits(y + 1) : 0u);
+    rv[k][0] = (f & 1u) ? (T)gv[0] : T(0);
+    rv[k][1] = (f & 2u) ? (T)gv[1] : T(0);
+    d[k][0] = (float)rv[k][0];
+    d[k][1] = (float)rv[k][1];
+  }
+  zebra_sweep<kRY>(L, d, r0, scr, 64, x);
+  const int pc = S.pcur;
+  T* r_out = f32 ? (T*)I.r32[pc] : (T*)I.r64[pc];
+  T* z_out = f32 ? (T*)I.z32[pc] : (T*)I.z64[pc];
+  T* p_out = f32 ? (T*)I.p32[pc] : (T*)I.p64[pc];
+  T* ap_out = f32 ? (T*)I.Ap32[pc] : (T*)I.Ap64[pc];
+  T* q_out = f32 ? (T*)I.q32[pc] : (T*)I.q64[pc];
+  T* w_out = f32 ? (T*)I.w32 : (T*)I.w64;
+  float s32 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + r0 + k;
+    if (y >= I.ny || !v0) continue;
+    const long long i = pidx(I, y, z, e0);
+    const T z0 = (T)x[k][0], z1 = (T)x[k][1];
+    st2(r_out, i, v0, v1, rv[k][0], rv[k][1]);
+    st2(z_out, i, v0, v1, z0, z1);
+    st2(p_out, i, v0, v1, T(0), T(0));
+    st2(ap_out, i, v0, v1, T(0), T(0));
+    st2(q_out, i, v0, v1, T(0), T(0));
+    st2(w_out, i, v0, v1, T(0), T(0));
+    if (f32) {
+      s32 = fmaf((float)rv[k][0], (float)z0, s32);
+      s32 = fmaf((float)rv[k][1], (float)z1, s32);
+    } else {
+      acc.s[0] = fma((double)rv[k][0], (double)z0, acc.s[0]);
+      acc.s[0] = fma((double)rv[k][1], (double)z1, acc.s[0]);
+    }
+  }
+  if (f32) ff_acc(ffs[0], s32);
+  __syncthreads();  // the exchange buffer is free again
+}
+
+// ----------------------------------------------- explicit reduced system --
+//
+// The paper's design extracts A_k = Z' A Z (Sec. 4) into its own matrix;
+// here that is an option beside the bitmask: the free points get a compact
+// numbering (tiles in order, rows within a tile, columns within a row, the
+// groups' ranges concatenated), A_FF is stored in that numbering as rows of
+// a diagonal and 2*dim neighbour slots (compact index and coupling), and the
+// CG phase runs on compact vectors.  It pays when few points are free: a CG
+// step then touches m entries instead of streaming all n.
+
+// Exclusive prefix sum of v over the CTA in thread order; `total` receives
+// the sum.  All threads must call it (two block barriers).
+__device__ __forceinline__ int cta_excl_scan(int v, int* s_warp, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL_MASK, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int t = s_warp[w];
+    before += w < warp ? t : 0;
+    all += t;
+  }
+  __syncthreads();
+  total = all;
+  return before + x - v;
+}
+
+// The free bits of the lane's two points of row (y, z) (0 past the grid).
+__device__ __forceinline__ unsigned rx_bits(const DevInst& I, const Snap& S, int y, int z,
+                                            int e0) {
+  if (y >= I.ny || e0 >= I.nx) return 0u;
+  const unsigned b = my_free_bits(I, I.mask[S.cur], y, z, e0);
+  return e0 + 1 < I.nx ? b : (b & 1u);
+}
+
+// P_RX_COUNT on one tile: the number of free points (a count of the pass).
+__device__ __forceinline__ void rx_count_tile(const DevInst& I, const Snap& S, int x0, int y0,
+                                              int z, Acc& acc) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e0 = x0 + 2 * lane;
+#pragma unroll
+  for (int k = 0; k < kRY; ++k) acc.c[0] += __popc(rx_bits(I, S, y0 + warp * kRY + k, z, e0));
+}
+
+// The passes of the explicit reduced system run out of line: they are not
+// the hot path of the default solve and, inlined, would raise the register
+// and stack use of the whole pass kernel.
+
+// P_RX_MAP over a group's tiles: compact indices from the group's offset
+// (written by P_RX_COUNT's last group), fidx, r_0 = g_F in compact order, and
+// the full-length w set to 0 (the search direction is scattered into it).
+template <class T>
+__device__ __noinline__ void rx_map_group(const DevInst& I, const Snap& S, int grp, int t_lo, int t_hi,
+                             int* s_warp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool f32 = sizeof(T) == 4;
+  T* rc = f32 ? (T*)I.rc32[S.pcur] : (T*)I.rc64[S.pcur];
+  T* wf = f32 ? (T*)I.w32 : (T*)I.w64;
+  const unsigned lt = (1u << lane) - 1u;
+  int base = __ldcg(I.goff + grp);
+  for (int tile = t_lo; tile < t_hi; ++tile) {
+    const int rest = tile / I.tiles_x;
+    const int x0 = (tile % I.tiles_x) * kTX, y0 = (rest % I.tiles_y) * kTY, z = rest / I.tiles_y;
+    const int e0 = x0 + 2 * lane;
+    const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+    const int ya = y0 + warp * kRY;
+    unsigned fb[kRY], b0[kRY], b1[kRY];
+    int wtot = 0;
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+      fb[k] = rx_bits(I, S, ya + k, z, e0);
+      b0[k] = __ballot_sync(FULL_MASK, fb[k] & 1u);
+      b1[k] = __ballot_sync(FULL_MASK, (fb[k] >> 1) & 1u);
+      wtot += __popc(b0[k]) + __popc(b1[k]);
+    }
+    int tile_tot;
+    const int wo = __shfl_sync(FULL_MASK, cta_excl_scan(lane == 0 ? wtot : 0, s_warp, tile_tot), 0);
+    int off = base + wo;
+#pragma unroll
+    for (int k = 0; k < kRY; ++k) {
+      const int y = ya + k;
+      const int k0 = off + __popc(b0[k] & lt) + __popc(b1[k] & lt);
+      const int k1 = k0 + (int)(fb[k] & 1u);
+      if (y < I.ny && v0) {
+        const long long i = pidx(I, y, z, e0);
+        I.cidx[i] = (fb[k] & 1u) ? k0 : -1;
+        if (v1) I.cidx[i + 1] = (fb[k] & 2u) ? k1 : -1;
+        st2(wf, i, v0, v1, T(0), T(0));
+        double gv[2] = {0.0, 0.0};
+        if (S.gp32) {
+          float gf[2];
+          ld2(I.g32[S.cur], i, v0, v1, gf);
+          gv[0] = gf[0];
+          gv[1] = gf[1];
+        } else {
+          ld2(I.g[S.cur], i, v0, v1, gv);
+        }
+        if (fb[k] & 1u) {
+          I.fidx[k0] = (int)i;
+          rc[k0] = (T)gv[0];
+        }
+        if (fb[k] & 2u) {
+          I.fidx[k1] = (int)(i + 1);
+          rc[k1] = (T)gv[1];
+        }
+      }
+      off += __popc(b0[k]) + __popc(b1[k]);
+    }
+    base += tile_tot;
+  }
+}
+
+// P_RX_BUILD on one tile: the rows of A_FF of its free points in compact
+// numbering, 1/diagonal, and the first CG step's state: z_0 = M^-1 r_0 (M = I
+// or the diagonal), rho_0 = <r_0, z_0> (sum 0); compact p, Ap, w = 0 so that
+// the first fused step, run with alpha = beta = 0, forms p_0 and Ap_0.
+template <class T, bool JAC>
+__device__ __noinline__ void rx_build_tile(const DevInst& I, const Snap& S, int x0, int y0, int z, Acc& acc,
+                              FF* ffs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool f32 = sizeof(T) == 4;
+  const T* bd = f32 ? (const T*)I.diag32 : (const T*)I.diag;
+  const T* bx = f32 ? (const T*)I.cx32 : (const T*)I.cx;
+  const T* by = f32 ? (const T*)I.cy32 : (const T*)I.cy;
+  const T* bz = f32 ? (const T*)I.cz32 : (const T*)I.cz;
+  const T* dv = f32 ? (const T*)I.dinv32 : (const T*)I.dinv;
+  T* rd = f32 ? (T*)I.rd32 : (T*)I.rd64;
+  T* rv = f32 ? (T*)I.rv32 : (T*)I.rv64;
+  T* rdi = f32 ? (T*)I.rdi32 : (T*)I.rdi64;
+  const T* rc = f32 ? (const T*)I.rc32[S.pcur] : (const T*)I.rc64[S.pcur];
+  T* pcv = f32 ? (T*)I.pc32[S.pcur] : (T*)I.pc64[S.pcur];
+  T* apc = f32 ? (T*)I.apc32[S.pcur] : (T*)I.apc64[S.pcur];
+  T* wc = f32 ? (T*)I.wc32 : (T*)I.wc64;
+  const long long st = I.n;
+  float s32 = 0.0f;
+  for (int k = 0; k < kRY; ++k) {
+    const int y = y0 + warp * kRY + k;
+    if (y >= I.ny) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int x = x0 + 2 * lane + h;
+      if (x >= I.nx) continue;
+      const long long i = pidx(I, y, z, x);
+      const int c = __ldcg(I.cidx + i);
+      if (c < 0) continue;
+      int nb[kMaxNb];
+      T val[kMaxNb];
+      auto slot = [&](int j, bool has, long long o, T cpl) {
+        const int q = has ? __ldcg(I.cidx + i + o) : -1;
+        nb[j] = q >= 0 ? q : c;
+        val[j] = q >= 0 ? cpl : T(0);
+      };
+      slot(0, x > 0, -1, x > 0 ? bx[i - 1] : T(0));
+      slot(1, x + 1 < I.nx, 1, bx[i]);
+      slot(2, y > 0, -(long long)I.px, y > 0 ? by[i - I.px] : T(0));
+      slot(3, y + 1 < I.ny, I.px, by[i]);
+      if (I.dim == 3) {
+        slot(4, z > 0, -I.plane, z > 0 ? bz[i - I.plane] : T(0));
+        slot(5, z + 1 < I.nz, I.plane, bz[i]);
+      }
+      const int nn = 2 * I.dim;
+      for (int j = 0; j < nn; ++j) {
+        I.rnb[j * st + c] = nb[j];
+        rv[j * st + c] = val[j];
+      }
+      rd[c] = bd[i];
+      const T di = dv[i];
+      rdi[c] = di;
+      pcv[c] = T(0);
+      apc[c] = T(0);
+      wc[c] = T(0);
+      const T r = rc[c];
+      const T zz = JAC ? r * di : r;
+      if (f32) s32 = fmaf((float)r, (float)zz, s32);
+      else acc.s[0] = fma((double)r, (double)zz, acc.s[0]);
+    }
+  }
+  if (f32) ff_acc(ffs[0], s32);
+}
+
+// P_RCG over compact indices [lo, hi): the fused CG step of P_CG_F on the
+// compact system, with the neighbours' p_j formed from their old r, Ap, p.
+template <class T, bool JAC>
+__device__ __noinline__ void rcg_range(const DevInst& I, const Snap& S, long long lo, long long hi, Acc& acc,
+                          FF* ffs) {
+  const bool f32 = sizeof(T) == 4;
+  const int pc = S.pcur;
+  const T* __restrict__ r = f32 ? (const T*)I.rc32[pc] : (const T*)I.rc64[pc];
+  const T* __restrict__ p = f32 ? (const T*)I.pc32[pc] : (const T*)I.pc64[pc];
+  const T* __restrict__ ap = f32 ? (const T*)I.apc32[pc] : (const T*)I.apc64[pc];
+  const T* __restrict__ rd = f32 ? (const T*)I.rd32 : (const T*)I.rd64;
+  const T* __restrict__ rv = f32 ? (const T*)I.rv32 : (const T*)I.rv64;
+  const T* __restrict__ di = f32 ? (const T*)I.rdi32 : (const T*)I.rdi64;
+  T* r_o = f32 ? (T*)I.rc32[pc ^ 1] : (T*)I.rc64[pc ^ 1];
+  T* p_o = f32 ? (T*)I.pc32[pc ^ 1] : (T*)I.pc64[pc ^ 1];
+  T* ap_o = f32 ? (T*)I.apc32[pc ^ 1] : (T*)I.apc64[pc ^ 1];
+  T* w = f32 ? (T*)I.wc32 : (T*)I.wc64;
+  const int* __restrict__ rnb = I.rnb;
+  const long long st = I.n;
+  const int nn = 2 * I.dim;
+  const T a = (T)S.alpha, b = (T)S.beta;
+  for (long long k = lo + threadIdx.x; k < hi; k += kThreads) {
+    const T pk = p[k];
+    const T rn = fma(a, ap[k], r[k]);
+    const T zn = JAC ? rn * di[k] : rn;
+    const T pn = fma(b, pk, -zn);
+    w[k] = fma(a, pk, w[k]);
+    T y = rd[k] * pn;
+    for (int j = 0; j < nn; ++j) {
+      const int q = __ldg(rnb + j * st + k);
+      const T rq = fma(a, ap[q], r[q]);
+      const T pq = fma(b, p[q], -(JAC ? rq * di[q] : rq));
+      y = fma(rv[j * st + k], pq, y);
+    }
+    r_o[k] = rn;
+    p_o[k] = pn;
+    ap_o[k] = y;
+    const T dy = JAC ? y * di[k] : y;
+    if (f32) {
+      ff_fma(ffs[0], (float)rn, (float)zn);
+      ff_fma(ffs[1], (float)pn, (float)y);
+      ff_fma(ffs[2], (float)zn, (float)y);
+      ff_fma(ffs[3], (float)y, (float)dy);
+    } else {
+      acc.s[0] = fma((double)rn, (double)zn, acc.s[0]);
+      acc.s[1] = fma((double)pn, (double)y, acc.s[1]);
+      acc.s[2] = fma((double)zn, (double)y, acc.s[2]);
+      acc.s[3] = fma((double)y, (double)dy, acc.s[3]);
+    }
+  }
+}
+
+// P_RW over compact indices [lo, hi): w_{j+1} = w_j + alpha_j p_j scattered
+// into the full-length w (zero elsewhere since P_RX_MAP).
+template <class T>
+__device__ __noinline__ void rw_range(const DevInst& I, const Snap& S, long long lo, long long hi) {
+  const bool f32 = sizeof(T) == 4;
+  const T* p = f32 ? (const T*)I.pc32[S.pcur] : (const T*)I.pc64[S.pcur];
+  const T* wc = f32 ? (const T*)I.wc32 : (const T*)I.wc64;
+  T* wf = f32 ? (T*)I.w32 : (T*)I.w64;
+  const T a = (T)S.alpha;
+  for (long long k = lo + threadIdx.x; k < hi; k += kThreads)
+    wf[__ldg(I.fidx + k)] = fma(a, p[k], wc[k]);
+}
+
+// ---------------------------------------------------------------- control --
+
+__device__ double pass_bytes(const DevInst& I, const Ctl& C, int pass) {
+  // algorithmic HBM bytes of one pass per valid point: every array the pass
+  // must read or write, once (documented per pass in the design notes)
+  const double kc = (double)I.kc;
+  const double sv = C.cg32 ? 4.0 : 8.0;
+  const double pj = I.opt.precond == PC_JACOBI ? sv : 0.0;
+  double per = 0.0;
+  switch (pass) {
+    case P_START: per = 24.0 + (I.opt.use_x0 ? 8.0 : 0.0) + (I.x32[0] ? 4.0 : 0.0); break;
+    case P_CENSUS:
+      per = C.gp32 ? 4.0 * kc + 24.125 : 8.0 * kc + 40.0 + 0.125 + (C.x32_live ? 20.0 : 0.0);
+      break;
+    case P_GP_ALPHA: per = C.gp32 ? 4.0 * kc + 4.0 : 8.0 * kc + 32.0; break;
+    case P_TRIAL:
+      if (C.gp32)
+        per = 4.0 * kc + 32.25 + (C.dir == D_W32 ? 4.0 : 0.0);
+      else
+        per = 8.0 * kc + 56.0 + 0.25 + (C.dir == D_W64 ? 8.0 : (C.dir == D_W32 ? 4.0 : 0.0));
+      break;
+    case P_CG_B:  // (+ 1/diag with point Jacobi)
+      per = sv * kc + (C.first_cg ? (C.gp32 ? 4.0 : 8.0) + 4.0 * sv : 4.0 * sv) + 0.125 + pj;
+      break;
+    case P_CG_A: per = 6.0 * sv + pj; break;
+    case P_CG_F:  // tile preconditioner: z, q, p, r, Ap, w read and written
+      per = sv * kc + (I.opt.precond == PC_TILE ? 12.0 * sv : 8.0 * sv + pj) + 0.125;
+      break;
+    case P_CG_Z: per = (C.gp32 ? 4.0 : 8.0) + 3.0 * sv + 6.0 * sv + 0.125; break;
+    case P_RX_COUNT: per = 0.125; break;
+    case P_RX_MAP:  // mask, cidx and w for every point; g, fidx, r for the free ones
+      return (0.125 + 4.0 + sv) * (double)I.n + ((C.gp32 ? 4.0 : 8.0) + 4.0 + sv) * (double)C.m;
+    case P_RX_BUILD: {  // cidx of every point; bands, 1/diag, r in; rows, p, Ap, w out
+      const double nn = 2.0 * I.dim;
+      return 4.0 * (double)I.n +
+             (sv * kc + sv + sv + (1.0 + nn) * sv + 4.0 * nn + sv + 3.0 * sv) * (double)C.m;
+    }
+    case P_RCG: {  // r, p, Ap, w in and out; the row (and 1/diag)
+      const double nn = 2.0 * I.dim;
+      return (8.0 * sv + (1.0 + nn) * sv + 4.0 * nn + pj) * (double)C.m;
+    }
+    case P_RW: return (4.0 + 3.0 * sv) * (double)C.m;
+    default: break;
+  }
+  return per * (double)I.n;
+}
+
+// End the solve with `status`: one final census pass refreshes g, the active
+// and binding counts, ||pg|| and q at the returned point.
+__device__ void set_done(Ctl& C, int status) {
+  C.status = status;
+  C.census_mode = CM_FINAL;
+  C.gp32 = 0;
+  C.pass = P_CENSUS;
+}
+
+// Leave the mixed phase: everything from here on is FP64, starting with an
+// FP64 census of the current iterate.
+__device__ void switch_fp64(Ctl& C, int mode) {
+  C.gp32 = 0;
+  C.refined = 1;
+  C.census_mode = mode;
+  C.pass = P_CENSUS;
+}
+
+__device__ void start_search(Ctl& C, int dir) {
+  C.dir = dir;
+  C.alpha = dir == D_ZERO ? 0.0 : 1.0;
+  C.ls_i = 0;
+  C.trial_gp = 0;
+  C.pass = P_TRIAL;
+}
+
+// Whether the instance's CG phase runs fused steps (P_CG_F): 2-D grids whose
+// tensor maps of the CG precision are valid (and, under the tile preconditioner, its maps).
+__device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
+  if (I.dim != 2 || I.tmaps == nullptr || !(C.cg32 ? I.tma32 : I.tma64)) return false;
+  return I.opt.precond != PC_TILE || ((I.tma_tile >> (C.cg32 ? 1 : 0)) & 1);
+}
+
+// Start a CG phase on the face of the current iterate (Eq. cg, cg2), w0 = 0.
+__device__ void begin_cg(const DevInst& I, Ctl& C) {
+  C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
+  C.cg_j = 0;
+  C.cdmax = 0.0;
+  C.cg_finish = 0;
+  if (I.opt.max_cg >= 1 && I.opt.extract) {
+    C.first_cg = 0;
+    C.beta = 0.0;
+    C.pass = P_RX_COUNT;
+  } else if (I.opt.max_cg >= 1 && I.opt.precond == PC_TILE && cg_fused(I, C)) {
+    C.first_cg = 0;
+    C.beta = 0.0;
+    C.pass = P_CG_Z;
+  } else if (I.opt.max_cg >= 1) {
+    C.first_cg = 1;
+    C.beta = 0.0;
+    C.pass = P_CG_B;
+  } else {
+    start_search(C, D_ZERO);
+  }
+}
+
+// Start outer iterate k (Algorithm GPCG): gradient projection unless the
+// previous iterate satisfied Eq. cgstop3.
+__device__ void begin_outer(const DevInst& I, Ctl& C) {
+  if (C.outer_iters >= I.opt.max_outer) {
+    set_done(C, S_MAXIT);
+    return;
+  }
+  C.outer_iters++;
+  if (!C.continue_cg) {
+    C.gp_j = 0;
+    C.dmax = 0.0;
+    C.pass = P_GP_ALPHA;
+  } else {
+    begin_cg(I, C);
+  }
+}
+
+// ||grad_Omega q|| <= tau held.  In mixed precision the first time this
+// happens starts the closing FP64 CG phase on the identified face.
+__device__ void on_converged(const DevInst& I, Ctl& C) {
+  if (C.gp32) {
+    // the FP32-streamed estimate met tau: certify in FP64 and, with refine,
+    // run the closing FP64 CG phase on the identified face
+    switch_fp64(C, I.opt.refine ? CM_REFINE : CM_RESUME);
+  } else if (I.opt.mixed && I.opt.refine && !C.refined) {
+    C.refined = 1;
+    C.refining = 1;
+    C.continue_cg = 1;
+    C.eta2 = I.opt.eta2_refine;
+    C.outer_iters++;
+    begin_cg(I, C);
+  } else {
+    set_done(C, S_OK);
+  }
+}
+
+
+// After alpha_j of a fused phase is known (C.rr = rho_j = <r_j, z_j>, z =
+// M^-1 r): the CG bookkeeping and Eq. cgstop1 of step j (decrease
+// alpha_j rho_j / 2), with rho_{j+1} = <r_j + alpha Ap_j, M^-1 (r_j + alpha Ap_j)>
+// = rho_j + 2 alpha_j <z_j,Ap_j> + alpha_j^2 <Ap_j,M^-1 Ap_j> (its sums come
+// from the pass that formed Ap_j); then either the next fused step or a last
+// P_CG_A that completes w_{j+1} before the projected search.
+__device__ void cg_advance(const DevInst& I, Ctl& C, double zAp, double ApMAp) {
+  const Opts& o = I.opt;
+  const double rr_next = C.rr + 2.0 * C.alpha * zAp + C.alpha * C.alpha * ApMAp;
+  C.cg_j++;
+  C.cg_iters++;
+  if (C.refining) C.refine_cg_iters++;
+  const double delta = 0.5 * C.alpha * C.rr;  // q_k(w_j) - q_k(w_{j+1})
+  const bool stop = (C.cg_j >= 2 && delta <= C.eta2 * C.cdmax) ||  // Eq. cgstop1
+                    rr_next <= 0.0 || C.cg_j >= o.max_cg;
+  if (delta > C.cdmax) C.cdmax = delta;
+  if (stop) {
+    C.cg_finish = 1;
+    C.pass = I.opt.extract ? P_RW : P_CG_A;
+  } else {
+    C.beta = rr_next / C.rr;
+    C.rr = rr_next;
+    C.pass = I.opt.extract ? P_RCG : P_CG_F;
+  }
+}
+
+__device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live) {
+  for (int k = 0; k < kNRed; ++k) C.red[k] = red[k];
+  if (C.hold) return;  // standalone timing/test launch: leave the state alone
+  const Opts& o = I.opt;
+  C.passes++;
+  C.alg_bytes += pass_bytes(I, C, C.pass);
+  switch (C.pass) {
+    case P_START:
+      C.x32_live = C.gp32;  // the mixed phase moves the FP32 iterate only
+      C.pass = P_CENSUS;
+      break;
+    case P_CENSUS: {
+      if (!C.gp32) C.x32_live = 0;  // an FP64 census rebuilt x from x32
+      C.pg2 = red[0];
+      C.xgb = red[1];
+      C.nA = red[4];
+      C.nB = red[5];
+      if (C.census_mode == CM_FINAL) {
+        C.pass = P_NONE;
+        C.done = 1;
+        atomicSub(live, 1);
+        break;
+      }
+      if (C.census_mode == CM_REFINE) {  // closing FP64 CG phase on this face
+        C.census_mode = CM_INIT;
+        C.refining = 1;
+        C.continue_cg = 1;
+        C.eta2 = o.eta2_refine;
+        C.outer_iters++;
+        begin_cg(I, C);
+        break;
+      }
+      if (C.census_mode == CM_RESUME) {  // continue GPCG in FP64
+        C.census_mode = CM_INIT;
+        if (!isfinite(C.pg2)) {
+          set_done(C, S_NUMERIC);
+        } else if (sqrt(C.pg2) <= C.tau) {
+          set_done(C, S_OK);
+        } else {
+          C.eta2 = o.eta2;
+          C.continue_cg = 0;
+          begin_outer(I, C);
+        }
+        break;
+      }
+      C.best_pg2 = C.pg2;
+      C.search_pg2 = C.pg2;
+      C.stall = 0;
+      C.slow = 0;
+      C.pg0 = sqrt(C.pg2);
+      C.tau = fmax(o.tau_abs, o.tau_rel * C.pg0);
+      C.eta2 = o.eta2;
+      C.continue_cg = 0;
+      if (!isfinite(C.pg2)) {
+        set_done(C, S_NUMERIC);
+      } else if (C.pg0 <= C.tau) {
+        set_done(C, S_OK);
+      } else {
+        begin_outer(I, C);
+      }
+      break;
+    }
+    case P_GP_ALPHA: {
+      const double gg = red[0], gAg = red[1];
+      if (!(gAg > 0.0) || !isfinite(gg)) {
+        set_done(C, S_NUMERIC);
+        break;
+      }
+      C.alpha0 = gg / gAg;  // Eq. bqpls: exact minimiser along -grad_Omega q
+      C.alpha = C.alpha0;
+      C.ls_i = 0;
+      C.dir = D_NEG_G;
+      C.trial_gp = 1;
+      C.pass = P_TRIAL;
+      break;
+    }
+    case P_TRIAL: {
+      C.ls_trials++;
+      const double gs = red[0];
+      const double dq = 0.5 * (red[0] + red[1]);  // q(xt) - q(x)
+      if (dq <= o.mu * gs) {                     // Eq. gplsstop / cglsstop2
+        C.cur ^= 1;
+        C.pg2 = red[2];
+        C.nA = red[4];
+        C.nB = red[5];
+        const double pgn = sqrt(C.pg2);
+        if (C.trial_gp) {
+          C.gp_iters++;
+          C.gp_j++;
+          const double dec = -dq;
+          const bool same = red[6] == 0.0;  // Eq. pgstop1
+          if (pgn <= C.tau) {
+            on_converged(I, C);
+            break;
+          }
+          const bool stop = same || (C.gp_j >= 2 && dec <= o.eta1 * C.dmax) ||  // Eq. pgstop2
+                            (C.gp_j >= o.max_gp);
+          if (dec > C.dmax) C.dmax = dec;
+          if (stop) {
+            begin_cg(I, C);
+          } else {
+            C.pass = P_GP_ALPHA;
+          }
+        } else {
+          C.refining = 0;
+          if (pgn <= C.tau) {
+            on_converged(I, C);
+            break;
+          }
+          if (C.gp32) {
+            // mixed phase: leave it when ||pg|| stops improving -- five
+            // iterates without a 2 % decrease of ||pg||^2, or two in a row on
+            // an unchanged face (Eq. cgstop3 holds) that do not halve ||pg||:
+            // there CG runs on a fixed system and only FP32 noise stops it
+            const bool face_kept = C.nB == C.nA;
+            const bool halved = C.pg2 < 0.25 * C.search_pg2;
+            C.search_pg2 = C.pg2;
+            C.slow = (face_kept && !halved) ? C.slow + 1 : 0;
+            if (C.pg2 < 0.98 * C.best_pg2) {
+              C.best_pg2 = C.pg2;
+              C.stall = 0;
+            } else {
+              ++C.stall;
+            }
+            if (C.stall >= 5 || C.slow >= 2) {
+              switch_fp64(C, CM_RESUME);
+              break;
+            }
+          }
+          if (C.nB == C.nA) {  // Eq. cgstop3: B(x) = A(x)
+            C.eta2 = fmax(C.eta2 * o.eta2_shrink, o.eta2_floor);
+            C.continue_cg = 1;
+          } else {
+            C.eta2 = o.eta2;
+            C.continue_cg = 0;
+          }
+          begin_outer(I, C);
+        }
+      } else {
+        C.ls_i++;
+        if (C.ls_i > o.max_ls) {
+          // in the mixed phase the FP32 gradient may be too coarse for the
+          // sufficient-decrease test: continue in FP64 instead of failing
+          if (C.gp32) switch_fp64(C, CM_RESUME);
+          else set_done(C, S_LINESEARCH);
+          break;
+        }
+        if (C.dir != D_ZERO) C.alpha = ldexp(C.trial_gp ? C.alpha0 : 1.0, -C.ls_i);
+      }
+      break;
+    }
+    case P_CG_B: {
+      if (C.first_cg) {
+        C.rr = red[1];
+        C.first_cg = 0;
+        if (!(C.rr > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
+          C.pcur ^= 1;
+          start_search(C, D_ZERO);
+          break;
+        }
+      }
+      const double pAp = red[0];
+      if (!(pAp > 0.0)) {
+        set_done(C, S_NUMERIC);
+        break;
+      }
+      C.alpha = C.rr / pAp;
+      C.pcur ^= 1;
+      if (cg_fused(I, C)) {
+        // first step of a fused phase: z_0 = -p_0, so <z_0, Ap_0> = -<p_0, Ap_0>
+        cg_advance(I, C, -pAp, red[2]);
+      } else {
+        C.pass = P_CG_A;
+      }
+      break;
+    }
+    case P_CG_Z: {
+      const double rz = red[0];  // rho_0 = <r_0, M^-1 r_0>
+      if (!isfinite(rz)) {
+        set_done(C, S_NUMERIC);
+      } else if (!(rz > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
+        start_search(C, D_ZERO);
+      } else {
+        // the first fused step, with alpha = beta = 0, forms p_0 and Ap_0
+        C.rr = rz;
+        C.alpha = 0.0;
+        C.beta = 0.0;
+        C.pass = P_CG_F;
+      }
+      break;
+    }
+    case P_RX_COUNT:
+      C.m = (int)red[4];  // the group offsets were written by this pass's last group
+      if (C.m == 0) start_search(C, D_ZERO);  // no free variable: w = 0
+      else C.pass = P_RX_MAP;
+      break;
+    case P_RX_MAP:
+      C.pass = P_RX_BUILD;
+      break;
+    case P_RX_BUILD: {
+      const double rz = red[0];  // rho_0 = <r_0, M^-1 r_0>
+      if (!isfinite(rz)) {
+        set_done(C, S_NUMERIC);
+      } else if (!(rz > 0.0)) {  // r = g_F vanished: no CG step (w stays 0)
+        start_search(C, D_ZERO);
+      } else {
+        C.rr = rz;
+        C.alpha = 0.0;
+        C.beta = 0.0;
+        C.pass = P_RCG;
+      }
+      break;
+    }
+    case P_RW:
+      C.cg_finish = 0;
+      start_search(C, C.cg32 ? D_W32 : D_W64);
+      break;
+    case P_RCG:
+    case P_CG_F: {
+      C.rr = red[0];  // ||r_j||^2 of the stored r_j
+      const double pAp = red[1];
+      if (!(pAp > 0.0)) {
+        set_done(C, S_NUMERIC);
+        break;
+      }
+      C.alpha = C.rr / pAp;
+      C.pcur ^= 1;
+      cg_advance(I, C, red[2], red[3]);
+      break;
+    }
+    case P_CG_A: {
+      if (C.cg_finish) {  // w of the last fused step is complete: search along it
+        C.cg_finish = 0;
+        start_search(C, C.cg32 ? D_W32 : D_W64);
+        break;
+      }
+      const double rr_new = red[0];
+      C.cg_j++;
+      C.cg_iters++;
+      if (C.refining) C.refine_cg_iters++;
+      const double delta = 0.5 * C.alpha * C.rr;  // q_k(w_{j-1}) - q_k(w_j)
+      const bool stop = (C.cg_j >= 2 && delta <= C.eta2 * C.cdmax) ||  // Eq. cgstop1
+                        rr_new == 0.0 || C.cg_j >= o.max_cg;
+      if (delta > C.cdmax) C.cdmax = delta;
+      if (stop) {
+        start_search(C, C.cg32 ? D_W32 : D_W64);
+      } else {
+        C.beta = rr_new / C.rr;
+        C.rr = rr_new;
+        C.pass = P_CG_B;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+
+// ------------------------------------------------------- TMA-staged CG --
+//
+// The two CG passes of a 2-D instance (and the pointwise CG pass of any
+// instance) stream a work item through shared memory with the tensor memory
+// accelerator, kStages stages deep: the next kStages-1 chunks are in flight
+// while chunk k is computed.  Stage layout (each array 128-byte aligned),
+// T = float (h = 4) or double (h = 2):
+//   P_CG_B (c = 32 rows FP32, 16 FP64): R (64+2h)x(c+2) from (x0-h, y-1) |
+//           P likewise | D 64xc | CX (64+h)xc from x0-h | CY 64x(c+1) from y-1
+//   P_CG_A (a = 32 rows FP32, 16 FP64): W | R | P | AP, 64xa each
+// Out-of-range rows and columns arrive as zeros, which is exactly the
+// operand and coupling outside the grid.
+
+__host__ __device__ constexpr int align128(int b) { return (b + 127) / 128 * 128; }
+
+template <class T>
+struct ChunkGeo {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = sizeof(T) == 4 ? 32 : 16;     // CG_B rows per chunk
+  static constexpr int CH_A = sizeof(T) == 4 ? 32 : 16;  // CG_A rows per chunk
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int OFF_R = 0;
+  static constexpr int OFF_P = SZ_H;
+  static constexpr int OFF_D = 2 * SZ_H;
+  static constexpr int OFF_CX = OFF_D + 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END_B = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX_B =
+      (2 * (CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int SZ_A = 64 * CH_A * (int)sizeof(T);
+  static constexpr unsigned TX_A = 4 * SZ_A;
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;  // first map of the precision
+};
+static_assert(ChunkGeo<float>::END_B <= kOffMask && ChunkGeo<double>::END_B <= kOffMask,
+              "stage layout");
+static_assert(5 * ChunkGeo<float>::SZ_A <= kOffMask &&
+                  5 * ChunkGeo<double>::SZ_A <= kOffMask,
+              "stage layout (W, R, P, AP and, with point Jacobi, 1/diag)");
+
+__device__ __forceinline__ const void* tmap(const DevInst& I, int k) {
+  return reinterpret_cast<const char*>(I.tmaps) + 128 * k;
+}
+
+template <class T>
+__device__ __forceinline__ void issue_cgb(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = ChunkGeo<T>;
+  constexpr int o = -M32_RH0;  // map offsets within a precision's block
+  mbar_expect(bar, G::TX_B);
+  // r of this step was written by P_CG_A into r[pcur^1]
+  tma_load2d(st + G::OFF_R, tmap(I, G::MB + o + M32_RH0 + (pcur ^ 1)), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, G::MB + o + M32_PH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, G::MB + o + M32_D), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, G::MB + o + M32_CX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, G::MB + o + M32_CY), x0, yc - 1, bar);
+}
+
+template <class T>
+__device__ __forceinline__ void issue_cga(const DevInst& I, int pcur, int x0, int row,
+                                          unsigned st, unsigned bar) {
+  using G = ChunkGeo<T>;
+  constexpr int o = -M32_RH0;
+  mbar_expect(bar, G::TX_A + (I.opt.precond == PC_JACOBI ? G::SZ_A : 0));
+  if (I.opt.precond == PC_JACOBI)
+    tma_load2d(st + 4 * G::SZ_A, tmap(I, G::MB + o + M32_ADI), x0, row, bar);
+  tma_load2d(st + 0 * G::SZ_A, tmap(I, G::MB + o + M32_W), x0, row, bar);
+  tma_load2d(st + 1 * G::SZ_A, tmap(I, G::MB + o + M32_R0 + pcur), x0, row, bar);
+  tma_load2d(st + 2 * G::SZ_A, tmap(I, G::MB + o + M32_P0 + pcur), x0, row, bar);
+  tma_load2d(st + 3 * G::SZ_A, tmap(I, G::MB + o + M32_AP0 + pcur), x0, row, bar);
+}
+
+// P_CG_B (not the first step of a phase) on one staged chunk of a 2-D grid:
+// p = -r + beta p_old over the halo'd box (in place), then Ap = Z Z' A Z Z' p
+// and <p, Ap> for the chunk's interior.
+template <class T>
+__device__ __forceinline__ void cgb_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                          int rows, T beta, const unsigned* fbits, T* p_out,
+                                          T* ap_out, Acc& acc, FF& ff) {
+  using G = ChunkGeo<T>;
+  T* R = reinterpret_cast<T*>(st + G::OFF_R);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) R[e] = fma(beta, P[e], -R[e]);
+  __syncthreads();
+  constexpr int RPW = G::CH / kWarps;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = warp * RPW + k;
+    const int y = yc + ry;
+    if (ry >= rows || y >= I.ny || !v0) break;
+    const T* Rr = R + (ry + 1) * G::BW + G::H + c;
+    const T vc0 = Rr[0], vc1 = Rr[1];
+    const T vw = Rr[-1], ve = Rr[2];
+    const T vs0 = Rr[-G::BW], vs1 = Rr[1 - G::BW];
+    const T vn0 = Rr[G::BW], vn1 = Rr[G::BW + 1];
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    T a0 = Dr[0] * vc0;
+    a0 = fma(Xr[-1], vw, a0);
+    a0 = fma(Xr[0], vc1, a0);
+    a0 = fma(Ys[0], vs0, a0);
+    a0 = fma(Yn[0], vn0, a0);
+    T a1 = Dr[1] * vc1;
+    a1 = fma(Xr[0], vc0, a1);
+    a1 = fma(Xr[1], ve, a1);
+    a1 = fma(Ys[1], vs1, a1);
+    a1 = fma(Yn[1], vn1, a1);
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    const long long i = (long long)y * I.px + e0;
+    st2(ap_out, i, v0, v1, a0, a1);
+    st2(p_out, i, v0, v1, vc0, vc1);
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)vc0, (float)a0);
+      ff_fma(ff, (float)vc1, (float)a1);
+    } else {
+      acc.s[0] = fma((double)vc0, (double)a0, acc.s[0]);
+      acc.s[0] = fma((double)vc1, (double)a1, acc.s[0]);
+    }
+  }
+}
+
+// P_CG_A on one staged chunk: w += alpha p, r' = r + alpha Ap (into `r`, the
+// other buffer), <r', M^-1 r'> (M = I, or diag(A) from the staged 1/diag).  `row` is the chunk's first row in the (ny*nz) row
+// space, `ylim` the number of rows of the chunk that lie inside the plane.
+template <class T, bool JAC>
+__device__ __forceinline__ void cga_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                          int row, int ylim, T alpha, T* w, T* r, Acc& acc,
+                                          FF& ff) {
+  using G = ChunkGeo<T>;
+  const T* W = reinterpret_cast<const T*>(st + 0 * G::SZ_A);
+  const T* R = reinterpret_cast<const T*>(st + 1 * G::SZ_A);
+  const T* P = reinterpret_cast<const T*>(st + 2 * G::SZ_A);
+  const T* AP = reinterpret_cast<const T*>(st + 3 * G::SZ_A);
+  const T* DI = reinterpret_cast<const T*>(st + 4 * G::SZ_A);  // 1/diag (point Jacobi)
+  constexpr bool jac = JAC;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int RPW = G::CH_A / kWarps;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = warp * RPW + k;
+    if (ry >= ylim || !v0) break;
+    const int o = ry * 64 + c;
+    const T w0 = fma(alpha, P[o], W[o]), w1 = fma(alpha, P[o + 1], W[o + 1]);
+    const T r0 = fma(alpha, AP[o], R[o]), r1 = fma(alpha, AP[o + 1], R[o + 1]);
+    const T z0 = jac ? r0 * DI[o] : r0, z1 = jac ? r1 * DI[o + 1] : r1;
+    const long long i = (long long)(row + ry) * I.px + e0;
+    st2(w, i, v0, v1, w0, w1);
+    st2(r, i, v0, v1, r0, r1);
+    if (sizeof(T) == 4) {
+      ff_fma(ff, (float)r0, (float)z0);
+      ff_fma(ff, (float)r1, (float)z1);
+    } else {
+      acc.s[0] = fma((double)r0, (double)z0, acc.s[0]);
+      acc.s[0] = fma((double)r1, (double)z1, acc.s[0]);
+    }
+  }
+}
+
+// ------------------------------------------------------- fused CG step --
+//
+// P_CG_F on a 2-D instance: one pass per CG step j >= 1 (Algorithm GPCG's
+// CG phase on the reduced system, Eq. cg2).  With alpha = alpha_{j-1} and
+// beta = beta_{j-1} over the halo box of the chunk, in place in the stage:
+//   r_j = r_{j-1} + alpha Ap_{j-1},  z_j = M^-1 r_j,  p_j = -z_j + beta p_{j-1}
+// (M = I, or diag(A) for point Jacobi, Sec. 6), at the chunk's points also
+// w_j = w_{j-1} + alpha p_{j-1}; then Ap_j = Z Z' A Z Z' p_j and the sums
+// rho_j = <r_j,z_j>, <p_j,Ap_j>, <z_j,Ap_j>, <Ap_j,M^-1 Ap_j> (from which the
+// finalizer takes alpha_j and rho_{j+1}).
+// r, p and Ap are read from buffer pcur and written to pcur^1.  Stage layout,
+// T = float (f = 16 rows, h = 4) or double (f = 8, h = 2): R | P | AP, each
+// (64+2h) x (f+2) from (x0-h, y-1) | W 64 x f | D 64 x f | CX (64+h) x f from
+// x0-h | CY 64 x (f+1) from y-1.
+template <class T>
+struct GeoF {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int SZ_I = 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_R = 0, OFF_P = SZ_H, OFF_AP = 2 * SZ_H, OFF_W = 3 * SZ_H;
+  static constexpr int OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int OFF_DI = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));  // 1/diag
+  static constexpr int END = OFF_DI + SZ_H;
+  static constexpr unsigned TX =
+      (3 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr unsigned TX_DI = (CH + 2) * BW * sizeof(T);
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
+};
+static_assert(GeoF<float>::END <= kOffMask && GeoF<double>::END <= kOffMask,
+              "stage layout");
+
+template <class T>
+__device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = GeoF<T>;
+  constexpr int o = G::MB - M32_RH0;
+  mbar_expect(bar, G::TX + (I.opt.precond == PC_JACOBI ? G::TX_DI : 0u));
+  if (I.opt.precond == PC_JACOBI)
+    tma_load2d(st + G::OFF_DI, tmap(I, o + M32_FDIH), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_AP, tmap(I, o + M32_FAPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_W, tmap(I, o + M32_FW), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, o + M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, o + M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, o + M32_FCY), x0, yc - 1, bar);
+}
+
+// P_CG_F, FP64 (one row per warp): r_j and p_j are formed once per element
+// of the halo box, in place in the stage, then a block barrier; recomputing
+// them per warp would triple the FP64 work, the bound of this pass.
+template <bool JAC>
+__device__ __forceinline__ void cgf_chunk_box(const DevInst& I, unsigned char* st, int x0, int yc,
+                                              int rows, double alpha, double beta,
+                                              const unsigned* fbits, double* w, double* r_out,
+                                              double* p_out, double* ap_out, Acc& acc) {
+  using G = GeoF<double>;
+  double* R = reinterpret_cast<double*>(st + G::OFF_R);
+  double* P = reinterpret_cast<double*>(st + G::OFF_P);
+  const double* AP = reinterpret_cast<const double*>(st + G::OFF_AP);
+  const double* W = reinterpret_cast<const double*>(st + G::OFF_W);
+  const double* D = reinterpret_cast<const double*>(st + G::OFF_D);
+  const double* CX = reinterpret_cast<const double*>(st + G::OFF_CX);
+  const double* CY = reinterpret_cast<const double*>(st + G::OFF_CY);
+  const double* DI = reinterpret_cast<const double*>(st + G::OFF_DI);
+  constexpr bool jac = JAC;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ylim = min(rows, I.ny - yc);
+  double s_rr = 0.0;
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) {
+    const int br = e / G::BW, bc = e - br * G::BW;
+    const double pold = P[e];
+    const double rn = fma(alpha, AP[e], R[e]);
+    const double zn = jac ? rn * DI[e] : rn;  // z = M^-1 r
+    const double pn = fma(beta, pold, -zn);
+    R[e] = zn;  // the stage keeps z for <z, Ap>
+    P[e] = pn;
+    const int ry = br - 1, col = bc - G::H;
+    if (ry >= 0 && ry < ylim && col >= 0 && col < 64 && x0 + col < I.nx) {
+      const long long i = (long long)(yc + ry) * I.px + x0 + col;
+      w[i] = fma(alpha, pold, W[ry * 64 + col]);
+      r_out[i] = rn;
+      p_out[i] = pn;
+      s_rr = fma(rn, zn, s_rr);
+    }
+  }
+  acc.s[0] += s_rr;
+  __syncthreads();
+  static_assert(G::CH == kWarps, "one row per warp");
+  const int ry = warp;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (ry >= ylim || !v0) return;
+  const double* Pr = P + (ry + 1) * G::BW + G::H + c;
+  const double* Rr = R + (ry + 1) * G::BW + G::H + c;
+  const double vc0 = Pr[0], vc1 = Pr[1];
+  const double* Dr = D + ry * 64 + c;
+  const double* Xr = CX + ry * (64 + G::H) + G::H + c;
+  const double* Ys = CY + ry * 64 + c;
+  const double* Yn = CY + (ry + 1) * 64 + c;
+  double a0 = Dr[0] * vc0;
+  a0 = fma(Xr[-1], Pr[-1], a0);
+  a0 = fma(Xr[0], vc1, a0);
+  a0 = fma(Ys[0], Pr[-G::BW], a0);
+  a0 = fma(Yn[0], Pr[G::BW], a0);
+  double a1 = Dr[1] * vc1;
+  a1 = fma(Xr[0], vc0, a1);
+  a1 = fma(Xr[1], Pr[2], a1);
+  a1 = fma(Ys[1], Pr[1 - G::BW], a1);
+  a1 = fma(Yn[1], Pr[G::BW + 1], a1);
+  const unsigned fb = fbits[0] & 3u;
+  a0 = (fb & 1u) ? a0 : 0.0;
+  a1 = (fb & 2u) ? a1 : 0.0;
+  st2(ap_out, (long long)(yc + ry) * I.px + e0, v0, v1, a0, a1);
+  const double z0 = Rr[0], z1 = Rr[1];
+  const double* Dr2 = DI + (ry + 1) * G::BW + G::H + c;
+  const double da0 = jac ? a0 * Dr2[0] : a0, da1 = jac ? a1 * Dr2[1] : a1;
+  acc.s[1] = fma(vc0, a0, fma(vc1, a1, acc.s[1]));
+  acc.s[2] = fma(z0, a0, fma(z1, a1, acc.s[2]));
+  acc.s[3] = fma(a0, da0, fma(a1, da1, acc.s[3]));
+}
+
+template <class T>
+struct V2;
+template <>
+struct V2<float> {
+  using type = float2;
+};
+template <>
+struct V2<double> {
+  using type = double2;
+};
+
+
+// P_CG_F on one staged chunk (rows yc .. yc+rows-1).  Sums: [0] ||r_j||^2,
+// [1] <p_j,Ap_j>, [2] <r_j,Ap_j>, [3] ||Ap_j||^2.  Each warp forms r_j and p_j
+// for its rows and the rows above and below from the staged r, p, Ap (west
+// and east neighbours by shuffles), so no block barrier is needed.  For
+// T = float a thread sums its few terms of the chunk in FP32 and adds that to
+// its float-float accumulator once per chunk.
+template <class T, bool JAC>
+__device__ __forceinline__ void cgf_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                          int yc, int rows, T alpha, T beta, const unsigned* fbits,
+                                          T* w, T* r_out, T* p_out, T* ap_out, Acc& acc, FF* ff) {
+  using G = GeoF<T>;
+  using T2 = typename V2<T>::type;
+  constexpr int RPW = G::CH / kWarps;
+  const T* R = reinterpret_cast<const T*>(st + G::OFF_R);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* AP = reinterpret_cast<const T*>(st + G::OFF_AP);
+  const T* W = reinterpret_cast<const T*>(st + G::OFF_W);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const T* DI = reinterpret_cast<const T*>(st + G::OFF_DI);  // 1/diag (point Jacobi)
+  constexpr bool jac = JAC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int r0 = warp * RPW;  // first chunk row of this warp
+  if (r0 >= ylim) return;     // warp-uniform
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q); z = M^-1 r
+  T pn[RPW + 2][2], rn[RPW][2], po[RPW][2], pw[RPW], pe[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + c;
+    const T2 rv = *reinterpret_cast<const T2*>(R + b);
+    const T2 pv = *reinterpret_cast<const T2*>(P + b);
+    const T2 av = *reinterpret_cast<const T2*>(AP + b);
+    T2 dv;
+    dv.x = T(1);
+    dv.y = T(1);
+    if (jac) dv = *reinterpret_cast<const T2*>(DI + b);
+    const T ra = fma(alpha, av.x, rv.x), rb = fma(alpha, av.y, rv.y);
+    const T za = ra * dv.x, zb = rb * dv.y;
+    pn[q][0] = fma(beta, pv.x, -za);
+    pn[q][1] = fma(beta, pv.y, -zb);
+    if (q >= 1 && q <= RPW) {
+      rn[q - 1][0] = ra;
+      rn[q - 1][1] = rb;
+      po[q - 1][0] = pv.x;
+      po[q - 1][1] = pv.y;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
+    pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
+    const int b = (r0 + k + 1) * G::BW + G::H + c;
+    if (lane == 0)
+      pw[k] = fma(beta, P[b - 1], -fma(alpha, AP[b - 1], R[b - 1]) * (jac ? DI[b - 1] : T(1)));
+    if (lane == 31)
+      pe[k] = fma(beta, P[b + 2], -fma(alpha, AP[b + 2], R[b + 2]) * (jac ? DI[b + 2] : T(1)));
+  }
+  T s_rr = T(0), s_pap = T(0), s_rap = T(0), s_apap = T(0);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    if (ry >= ylim) break;
+    const int q = k + 1;
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    // diag, west, east, south, north (the order of the register sweep)
+    T a0 = Dr[0] * pn[q][0];
+    a0 = fma(Xr[-1], pw[k], a0);
+    a0 = fma(Xr[0], pn[q][1], a0);
+    a0 = fma(Ys[0], pn[q - 1][0], a0);
+    a0 = fma(Yn[0], pn[q + 1][0], a0);
+    T a1 = Dr[1] * pn[q][1];
+    a1 = fma(Xr[0], pn[q][0], a1);
+    a1 = fma(Xr[1], pe[k], a1);
+    a1 = fma(Ys[1], pn[q - 1][1], a1);
+    a1 = fma(Yn[1], pn[q + 1][1], a1);
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    const T2 wv = *reinterpret_cast<const T2*>(W + ry * 64 + c);
+    const long long i = (long long)(yc + ry) * I.px + e0;
+    st2(w, i, v0, v1, fma(alpha, po[k][0], wv.x), fma(alpha, po[k][1], wv.y));
+    st2(r_out, i, v0, v1, rn[k][0], rn[k][1]);
+    st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
+    st2(ap_out, i, v0, v1, a0, a1);
+    // points past nx hold zeros (the boxes are zero-filled there)
+    T d0 = T(1), d1 = T(1);
+    if (jac) {
+      const T2 dv = *reinterpret_cast<const T2*>(DI + (ry + 1) * G::BW + G::H + c);
+      d0 = dv.x;
+      d1 = dv.y;
+    }
+    const T z0 = rn[k][0] * d0, z1 = rn[k][1] * d1;
+    s_rr = fma(rn[k][0], z0, s_rr);
+    s_rr = fma(rn[k][1], z1, s_rr);
+    s_pap = fma(pn[q][0], a0, s_pap);
+    s_pap = fma(pn[q][1], a1, s_pap);
+    s_rap = fma(z0, a0, s_rap);
+    s_rap = fma(z1, a1, s_rap);
+    s_apap = fma(a0, a0 * d0, s_apap);
+    s_apap = fma(a1, a1 * d1, s_apap);
+  }
+  if (sizeof(T) == 4) {
+    ff_acc(ff[0], (float)s_rr);
+    ff_acc(ff[1], (float)s_pap);
+    ff_acc(ff[2], (float)s_rap);
+    ff_acc(ff[3], (float)s_apap);
+  } else {
+    acc.s[0] += (double)s_rr;
+    acc.s[1] += (double)s_pap;
+    acc.s[2] += (double)s_rap;
+    acc.s[3] += (double)s_apap;
+  }
+}
+
+// P_CG_F under the tile preconditioner (2-D): the same CG step with
+// z = M^-1 r carried by its own recurrence, so that M^-1 is applied once per
+// step, to Ap, inside the chunk:
+//   r_j = r_{j-1} + alpha Ap_{j-1},  z_j = z_{j-1} + alpha q_{j-1}  (q = M^-1 Ap),
+//   w_j = w_{j-1} + alpha p_{j-1},  p_j = -z_j + beta p_{j-1},
+//   Ap_j = Z Z' A Z Z' p_j,  q_j = M^-1 Ap_j  (the zebra sweep over the chunk's
+//   8-row tiles), sums <r_j,z_j>, <p_j,Ap_j>, <z_j,Ap_j>, <Ap_j,q_j>.
+// The first step of a phase runs with alpha = beta = 0 on the vectors P_CG_Z
+// left.  z, q, p, r, Ap are read from buffer pcur and written to pcur^1.
+// Stage layout (T = float: f = 16 rows, h = 4; double: f = 8, h = 2): ZH | QH
+// | PH | RH | APH, each (64+2h) x (f+2) from (x0-h, y-1) | W 64 x f | D 64 x f |
+// CX (64+h) x f from x0-h | CY 64 x (f+1) from y-1.  Once a warp has read its
+// rows of W, those rows of the W box become its rows of the sweep's exchange
+// buffer (no other warp reads them).
+template <class T>
+struct GeoT {
+  static constexpr int H = 16 / (int)sizeof(T);
+  static constexpr int CH = GeoF<T>::CH;
+  static constexpr int BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * (int)sizeof(T));
+  static constexpr int SZ_I = 64 * CH * (int)sizeof(T);
+  static constexpr int OFF_Z = 0, OFF_Q = SZ_H, OFF_P = 2 * SZ_H, OFF_R = 3 * SZ_H;
+  static constexpr int OFF_AP = 4 * SZ_H, OFF_W = 5 * SZ_H;
+  static constexpr int OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * (int)sizeof(T));
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * (int)sizeof(T));
+  static constexpr unsigned TX =
+      (5 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T);
+  static constexpr int PITCH = 64 * (int)sizeof(T) / 4;  // exchange row pitch (floats)
+  static constexpr int MB = sizeof(T) == 4 ? M32_RH0 : M64_RH0;
+};
+static_assert(GeoT<float>::END <= kOffMask && GeoT<double>::END <= kOffMask, "stage layout");
+static_assert(GeoT<float>::CH % kBlkY == 0 && GeoT<double>::CH % kBlkY == 0 &&
+                  kTX == kBlkX && kTY % kBlkY == 0,
+              "chunks and tiles hold whole preconditioner blocks");
+
+template <class T>
+__device__ __forceinline__ void issue_cgt(const DevInst& I, int pcur, int x0, int yc,
+                                          unsigned st, unsigned bar) {
+  using G = GeoT<T>;
+  constexpr int o = G::MB - M32_RH0;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_Z, tmap(I, o + M32_FZH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_Q, tmap(I, o + M32_FQH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, o + M32_FPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_R, tmap(I, o + M32_FRH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_AP, tmap(I, o + M32_FAPH0 + pcur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_W, tmap(I, o + M32_FW), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, o + M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, o + M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, o + M32_FCY), x0, yc - 1, bar);
+}
+
+// The free bits of this lane's two columns in chunk row `row` of the staged
+// mask box (0 outside the box's rows).
+__device__ __forceinline__ unsigned stage_row_bits(const unsigned char* st, int x0, int row) {
+  if (row < 0 || row >= 32) return 0u;
+  const unsigned* M = reinterpret_cast<const unsigned*>(st + kOffMask);
+  const int lane = threadIdx.x & 31;
+  return (M[row * 4 + ((x0 >> 5) & 3) + (lane >> 4)] >> ((2 * lane) & 31)) & 3u;
+}
+
+template <class T>
+__device__ __forceinline__ void cgt_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                          int rows, T alpha, T beta, const unsigned* fbits,
+                                          T* w, T* r_out, T* z_out, T* p_out, T* ap_out,
+                                          T* q_out, Acc& acc, FF* ff) {
+  using G = GeoT<T>;
+  using T2 = typename V2<T>::type;
+  constexpr int RPW = G::CH / kWarps;
+  const T* Z = reinterpret_cast<const T*>(st + G::OFF_Z);
+  const T* Q = reinterpret_cast<const T*>(st + G::OFF_Q);
+  const T* P = reinterpret_cast<const T*>(st + G::OFF_P);
+  const T* R = reinterpret_cast<const T*>(st + G::OFF_R);
+  const T* AP = reinterpret_cast<const T*>(st + G::OFF_AP);
+  const T* W = reinterpret_cast<const T*>(st + G::OFF_W);
+  const T* D = reinterpret_cast<const T*>(st + G::OFF_D);
+  const T* CX = reinterpret_cast<const T*>(st + G::OFF_CX);
+  const T* CY = reinterpret_cast<const T*>(st + G::OFF_CY);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int r0 = warp * RPW;  // first chunk row of this warp
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q): z_j, p_j there
+  T pn[RPW + 2][2], zn[RPW][2], rn[RPW][2], pw[RPW], pe[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + c;
+    const T2 zv = *reinterpret_cast<const T2*>(Z + b);
+    const T2 qv = *reinterpret_cast<const T2*>(Q + b);
+    const T2 pv = *reinterpret_cast<const T2*>(P + b);
+    const T za = fma(alpha, qv.x, zv.x), zb = fma(alpha, qv.y, zv.y);
+    pn[q][0] = fma(beta, pv.x, -za);
+    pn[q][1] = fma(beta, pv.y, -zb);
+    if (q >= 1 && q <= RPW) {
+      const int k = q - 1, ry = r0 + k;
+      zn[k][0] = za;
+      zn[k][1] = zb;
+      const T2 rv = *reinterpret_cast<const T2*>(R + b);
+      const T2 av = *reinterpret_cast<const T2*>(AP + b);
+      rn[k][0] = fma(alpha, av.x, rv.x);
+      rn[k][1] = fma(alpha, av.y, rv.y);
+      const T2 wv = *reinterpret_cast<const T2*>(W + ry * 64 + c);
+      if (ry < ylim)
+        st2(w, (long long)(yc + ry) * I.px + e0, v0, v1, fma(alpha, pv.x, wv.x),
+            fma(alpha, pv.y, wv.y));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
+    pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
+    const int b = (r0 + k + 1) * G::BW + G::H + c;
+    if (lane == 0) pw[k] = fma(beta, P[b - 1], -fma(alpha, Q[b - 1], Z[b - 1]));
+    if (lane == 31) pe[k] = fma(beta, P[b + 2], -fma(alpha, Q[b + 2], Z[b + 2]));
+  }
+  TileLine L[RPW];
+  float d[RPW][2], x[RPW][2];
+  T ap[RPW][2];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    const int q = k + 1;
+    const T* Dr = D + ry * 64 + c;
+    const T* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const T* Ys = CY + ry * 64 + c;
+    const T* Yn = CY + (ry + 1) * 64 + c;
+    // diag, west, east, south, north (the order of the register sweep)
+    T a0 = Dr[0] * pn[q][0];
+    a0 = fma(Xr[-1], pw[k], a0);
+    a0 = fma(Xr[0], pn[q][1], a0);
+    a0 = fma(Ys[0], pn[q - 1][0], a0);
+    a0 = fma(Yn[0], pn[q + 1][0], a0);
+    T a1 = Dr[1] * pn[q][1];
+    a1 = fma(Xr[0], pn[q][0], a1);
+    a1 = fma(Xr[1], pe[k], a1);
+    a1 = fma(Ys[1], pn[q - 1][1], a1);
+    a1 = fma(Yn[1], pn[q + 1][1], a1);
+    // rows past the grid arrive as zeros in the mask box: no free point
+    const unsigned fb = fbits[k] & 3u;
+    a0 = (fb & 1u) ? a0 : T(0);
+    a1 = (fb & 2u) ? a1 : T(0);
+    ap[k][0] = a0;
+    ap[k][1] = a1;
+    const float xw = __shfl_up_sync(FULL_MASK, (float)Xr[1], 1);
+    L[k] = tile_line(ry, (float)Dr[0], (float)Dr[1], xw, (float)Xr[0], (float)Ys[0],
+                     (float)Ys[1], (float)Yn[0], (float)Yn[1], fb,
+                     stage_row_bits(st, x0, ry - 1), stage_row_bits(st, x0, ry + 1));
+    d[k][0] = (float)a0;
+    d[k][1] = (float)a1;
+  }
+  // every warp has read its rows of W (above): they now carry the sweep
+  zebra_sweep<RPW>(L, d, r0, reinterpret_cast<float*>(st + G::OFF_W), G::PITCH, x);
+  T s_rz = T(0), s_pap = T(0), s_zap = T(0), s_aq = T(0);
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    if (ry >= ylim) break;
+    const int q = k + 1;
+    const T q0 = (T)x[k][0], q1 = (T)x[k][1];
+    const long long i = (long long)(yc + ry) * I.px + e0;
+    st2(r_out, i, v0, v1, rn[k][0], rn[k][1]);
+    st2(z_out, i, v0, v1, zn[k][0], zn[k][1]);
+    st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
+    st2(ap_out, i, v0, v1, ap[k][0], ap[k][1]);
+    st2(q_out, i, v0, v1, q0, q1);
+    // points past nx hold zeros (the boxes are zero-filled there)
+    s_rz = fma(rn[k][0], zn[k][0], s_rz);
+    s_rz = fma(rn[k][1], zn[k][1], s_rz);
+    s_pap = fma(pn[q][0], ap[k][0], s_pap);
+    s_pap = fma(pn[q][1], ap[k][1], s_pap);
+    s_zap = fma(zn[k][0], ap[k][0], s_zap);
+    s_zap = fma(zn[k][1], ap[k][1], s_zap);
+    s_aq = fma(ap[k][0], q0, s_aq);
+    s_aq = fma(ap[k][1], q1, s_aq);
+  }
+  if (sizeof(T) == 4) {
+    ff_acc(ff[0], (float)s_rz);
+    ff_acc(ff[1], (float)s_pap);
+    ff_acc(ff[2], (float)s_zap);
+    ff_acc(ff[3], (float)s_aq);
+  } else {
+    acc.s[0] += (double)s_rz;
+    acc.s[1] += (double)s_pap;
+    acc.s[2] += (double)s_zap;
+    acc.s[3] += (double)s_aq;
+  }
+}
+
+// ------------------------------------ TMA-staged mixed-phase GP passes --
+//
+// In the mixed phase the iterate is x32, kept on the FP32 box [l32, u32]: a
+// point is active when x32 equals l32 or u32 (bit for bit; the FP32
+// projection returns the bound itself), and the first FP64 census after the
+// phase rebuilds the FP64 iterate from it (see OpCensus).  The census and the
+// trial of a 2-D instance stream 16-row chunks (two rows per warp).  Stage
+// layout (boxes 128-byte aligned):
+//   XH | LH | UH | DH | GH : FP32 72 x 18 from (x0-4, y-1): x32, l32, u32,
+//                            the direction (g32 or w32), g32 (trial along w)
+//   B : 64 x 16 (b32)   D : 64 x 16   CX : 68 x 16 from x0-4   CY : 64 x 17 from y-1
+// The census loads XH, l32 and u32 as 64 x 16 boxes in the LH and UH slots,
+// B and the bands.  The alpha0 pass streams 32-row chunks of pg32 through the
+// R slot of the FP32 CG_B layout, with its D, CX and CY boxes.
+struct GeoGP {
+  static constexpr int CH = 16, H = 4, BW = 64 + 2 * H;
+  static constexpr int RPW = CH / kWarps;
+  static constexpr int SZ_H = align128((CH + 2) * BW * 4);
+  static constexpr int SZ_32 = 64 * CH * 4;
+  static constexpr int OFF_XH = 0, OFF_LH = SZ_H, OFF_UH = 2 * SZ_H, OFF_DH = 3 * SZ_H;
+  static constexpr int OFF_GH = 4 * SZ_H;
+  static constexpr int OFF_B = 5 * SZ_H, OFF_D = OFF_B + SZ_32;
+  static constexpr int OFF_CX = OFF_D + SZ_32;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr unsigned TX_H = (CH + 2) * BW * 4;  // one halo box
+  static constexpr unsigned TX_BANDS = SZ_32 + SZ_32 + (64 + H) * CH * 4 + 64 * (CH + 1) * 4;
+};
+static_assert(GeoGP::END <= kOffMask, "stage layout");
+static_assert(GeoGP::CH == GeoF<float>::CH, "the GP passes use the fused pass's band maps");
+
+// Whether the item's pass is a mixed-phase GP pass on the TMA path.
+__device__ __forceinline__ bool gp_tma(const DevInst& I, const Snap& S) {
+  return S.gp32 && I.dim == 2 && I.tma_gp && I.tma32 && I.tma_mask &&
+         (S.pass == P_CENSUS || S.pass == P_GP_ALPHA || S.pass == P_TRIAL);
+}
+
+// Issue the chunk at rows yc.. of a mixed-phase GP pass.
+__device__ __forceinline__ void issue_gp(const DevInst& I, const Snap& S, int x0, int yc,
+                                         unsigned st, unsigned bar) {
+  using G = GeoGP;
+  const int cur = S.cur;
+  if (S.pass == P_GP_ALPHA) {
+    using F = ChunkGeo<float>;
+    mbar_expect(bar, ((F::CH + 2) * F::BW + 64 * F::CH + (64 + F::H) * F::CH +
+                      64 * (F::CH + 1)) * 4);
+    tma_load2d(st + F::OFF_R, tmap(I, MG_PGH0 + cur), x0 - F::H, yc - 1, bar);
+    tma_load2d(st + F::OFF_D, tmap(I, M32_D), x0, yc, bar);
+    tma_load2d(st + F::OFF_CX, tmap(I, M32_CX), x0 - F::H, yc, bar);
+    tma_load2d(st + F::OFF_CY, tmap(I, M32_CY), x0, yc - 1, bar);
+    return;
+  }
+  const bool along_w = S.pass == P_TRIAL && S.dir == D_W32;
+  mbar_expect(bar, S.pass == P_TRIAL ? (along_w ? 5u : 4u) * G::TX_H + G::TX_BANDS
+                                     : G::TX_H + 2 * G::SZ_32 + G::TX_BANDS);
+  tma_load2d(st + G::OFF_XH, tmap(I, MG_X32H0 + cur), x0 - G::H, yc - 1, bar);
+  if (S.pass == P_TRIAL) {
+    tma_load2d(st + G::OFF_LH, tmap(I, MG_L32H), x0 - G::H, yc - 1, bar);
+    tma_load2d(st + G::OFF_UH, tmap(I, MG_U32H), x0 - G::H, yc - 1, bar);
+    tma_load2d(st + G::OFF_DH, tmap(I, along_w ? MG_W32H : MG_G32H0 + cur), x0 - G::H, yc - 1,
+               bar);
+    if (along_w) tma_load2d(st + G::OFF_GH, tmap(I, MG_G32H0 + cur), x0 - G::H, yc - 1, bar);
+  } else {
+    tma_load2d(st + G::OFF_LH, tmap(I, MG_L32), x0, yc, bar);
+    tma_load2d(st + G::OFF_UH, tmap(I, MG_U32), x0, yc, bar);
+  }
+  tma_load2d(st + G::OFF_B, tmap(I, MG_B32), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M32_FCY), x0, yc - 1, bar);
+}
+
+// In the staged GP passes lane `lane` of a warp owns columns lane and lane+32
+// of each of its rows, so that shared-memory reads are unit-stride and a
+// warp ballot is one word of the free-set bitmask.
+
+// P_CENSUS (mixed) on one staged 16-row chunk: g32 = A32 x32 + b32, pg32,
+// the free set and |A|, |B|, ||pg||^2 (as OpCensus32).  Points past nx
+// arrive as zeros and contribute nothing.
+__device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                               int yc, float* g_out, float* pg_out,
+                                               unsigned* m_out, Acc& acc, FF& ff) {
+  using G = GeoGP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
+  const float* L = reinterpret_cast<const float*>(st + G::OFF_LH);  // 64 x 16
+  const float* U = reinterpret_cast<const float*>(st + G::OFF_UH);
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  float s_pg = 0.0f;
+#pragma unroll
+  for (int k = 0; k < G::RPW; ++k) {
+    const int r = warp * G::RPW + k;
+    const int y = yc + r;
+    if (y >= I.ny) break;  // warp-uniform
+    const long long row = (long long)y * I.px + x0;
+    bool fr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const bool ok = x0 + j < I.nx;
+      const float* V = XH + (r + 1) * G::BW + G::H + j;
+      const float* cx = CX + r * (64 + G::H) + G::H + j;
+      // diag, west, east, south, north (the order of the register sweep)
+      float a = D[r * 64 + j] * V[0];
+      a = fmaf(cx[-1], V[-1], a);
+      a = fmaf(cx[0], V[1], a);
+      a = fmaf(CY[r * 64 + j], V[-G::BW], a);
+      a = fmaf(CY[(r + 1) * 64 + j], V[G::BW], a);
+      const float g = a + B[r * 64 + j];
+      const bool al = V[0] == L[r * 64 + j], au = V[0] == U[r * 64 + j];
+      const bool act = al || au;
+      fr[h] = ok && !act;
+      const float pg = pg_compf(al, au, g);
+      s_pg = fmaf(pg, pg, s_pg);
+      acc.c[0] += ok && act;
+      acc.c[1] += ok && ((al && g >= 0.0f) || (au && g <= 0.0f));
+      if (ok) {
+        g_out[row + j] = g;
+        pg_out[row + j] = pg;
+      }
+    }
+    const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+    const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+    const int wc = (x0 >> 5) + lane;
+    if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
+  }
+  ff_acc(ff, s_pg);
+}
+
+// P_GP_ALPHA (mixed) on one staged chunk of up to 32 rows: <pg,pg>,
+// <pg, A32 pg> over its first `rows` rows.
+__device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned char* st, int yc,
+                                              int rows, FF* ff) {
+  using F = ChunkGeo<float>;
+  constexpr int RPW = F::CH / kWarps;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* PH = reinterpret_cast<const float*>(st + F::OFF_R);
+  const float* D = reinterpret_cast<const float*>(st + F::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + F::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + F::OFF_CY);
+  float s_gg = 0.0f, s_gag = 0.0f;  // this chunk's terms, added once to ff
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = warp * RPW + k;
+    if (r >= rows || yc + r >= I.ny) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const float* V = PH + (r + 1) * F::BW + F::H + j;
+      const float* cx = CX + r * (64 + F::H) + F::H + j;
+      float a = D[r * 64 + j] * V[0];
+      a = fmaf(cx[-1], V[-1], a);
+      a = fmaf(cx[0], V[1], a);
+      a = fmaf(CY[r * 64 + j], V[-F::BW], a);
+      a = fmaf(CY[(r + 1) * 64 + j], V[F::BW], a);
+      s_gg = fmaf(V[0], V[0], s_gg);
+      s_gag = fmaf(V[0], a, s_gag);
+    }
+  }
+  ff_acc(ff[0], s_gg);
+  ff_acc(ff[1], s_gag);
+}
+
+// P_TRIAL (mixed) on one staged 16-row chunk (as OpTrial32): each warp forms
+// xt32 = P[x32 + alpha d] on the FP32 box for its rows and the rows above and
+// below (west and east neighbours by shuffles), then g32t = A32 xt32 + b32,
+// the status of xt32, pg32 and the sums <g,s>, <s,gt>, ||pg||^2 with
+// s = xt32 - x32.  `fbits` holds the lane's bits of the current free set.
+template <int DK>
+__device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                              int yc, float alpha, const unsigned* fbits,
+                                              float* xt_out, float* gt_out, float* pg_out,
+                                              unsigned* m_out, Acc& acc, FF* ff) {
+  using G = GeoGP;
+  constexpr int RPW = G::RPW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = warp * RPW;
+  if (yc + r0 >= I.ny) return;  // warp-uniform
+  const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
+  const float* LH = reinterpret_cast<const float*>(st + G::OFF_LH);
+  const float* UH = reinterpret_cast<const float*>(st + G::OFF_UH);
+  const float* DH = reinterpret_cast<const float*>(st + G::OFF_DH);
+  const float* GH = reinterpret_cast<const float*>(st + (DK == D_W32 ? G::OFF_GH : G::OFF_DH));
+  const float* B = reinterpret_cast<const float*>(st + G::OFF_B);
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  auto opnd = [&](int e) {
+    const float d = DK == D_NEG_G ? -DH[e] : DH[e];
+    return mid3f(LH[e], UH[e], fmaf(alpha, d, XH[e]));
+  };
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q)
+  float v[RPW + 2][2];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int b = (r0 + q) * G::BW + G::H + lane;
+    v[q][0] = opnd(b);
+    v[q][1] = opnd(b + 32);
+  }
+  float s_gs = 0.0f, s_sgt = 0.0f, s_pg = 0.0f;  // this chunk's terms, added once to ff
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = r0 + k;
+    const int y = yc + r;
+    if (y >= I.ny) break;  // warp-uniform
+    const int q = k + 1;
+    const int b = (r + 1) * G::BW + G::H + lane;  // box index of column `lane` of row r
+    // west and east neighbours across the 64 columns
+    float vw[2], ve[2];
+    vw[0] = __shfl_up_sync(FULL_MASK, v[q][0], 1);
+    vw[1] = __shfl_up_sync(FULL_MASK, v[q][1], 1);
+    ve[0] = __shfl_down_sync(FULL_MASK, v[q][0], 1);
+    ve[1] = __shfl_down_sync(FULL_MASK, v[q][1], 1);
+    const float col31 = __shfl_sync(FULL_MASK, v[q][0], 31);
+    const float col32 = __shfl_sync(FULL_MASK, v[q][1], 0);
+    if (lane == 0) {
+      vw[0] = opnd(b - 1);
+      vw[1] = col31;
+    }
+    if (lane == 31) {
+      ve[0] = col32;
+      ve[1] = opnd(b + 33);
+    }
+    const long long row = (long long)y * I.px + x0;
+    bool fr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const int e = b + 32 * h;
+      const bool ok = x0 + j < I.nx;
+      const float* cx = CX + r * (64 + G::H) + G::H + j;
+      float a = D[r * 64 + j] * v[q][h];
+      a = fmaf(cx[-1], vw[h], a);
+      a = fmaf(cx[0], ve[h], a);
+      a = fmaf(CY[r * 64 + j], v[q - 1][h], a);
+      a = fmaf(CY[(r + 1) * 64 + j], v[q + 1][h], a);
+      const float gt = a + B[r * 64 + j];
+      const float xt = v[q][h];
+      const float sk = xt - XH[e];
+      const float g = GH[e];
+      const bool al = xt == LH[e], au = xt == UH[e];
+      const bool act = al || au;
+      fr[h] = ok && !act;
+      const float pg = pg_compf(al, au, gt);
+      s_gs = fmaf(g, sk, s_gs);
+      s_sgt = fmaf(sk, gt, s_sgt);
+      s_pg = fmaf(pg, pg, s_pg);
+      acc.c[0] += ok && act;
+      acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
+      acc.c[2] += ok && (((fbits[k] >> h) & 1u) != (fr[h] ? 1u : 0u));
+      if (ok) {
+        xt_out[row + j] = xt;
+        gt_out[row + j] = gt;
+        pg_out[row + j] = pg;
+      }
+    }
+    const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+    const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+    const int wc = (x0 >> 5) + lane;
+    if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
+  }
+  ff_acc(ff[0], s_gs);
+  ff_acc(ff[1], s_sgt);
+  ff_acc(ff[2], s_pg);
+}
+
+// Whether the item's pass runs through the TMA pipeline.
+__device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
+  if (gp_tma(I, S)) return true;
+  if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
+  if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
+  if (!I.tma_mask) return false;
+  const int ok = S.cg32 ? I.tma32 : I.tma64;
+  if (!ok) return false;
+  if (S.pass == P_CG_A) return true;
+  return S.pass == P_CG_B && !S.first_cg && I.dim == 2;
+}
+
+// Rows per chunk of the item's TMA pass.
+__device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
+  if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
+  if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
+  if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
+  return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
+}
+
+// A chunk of a TMA pass: rows yc .. yc+rows-1 (rows a multiple of 8, at most
+// the pass's chunk height) of the tile at column x0 of plane z.
+struct Chunk {
+  int x0, yc, z, rows;
+};
+
+// Walks a group's strips [u, u_hi) in chunks: a chunk starts at the current
+// strip and takes up to ch/8 strips without leaving its tile or the group.
+// Tile coordinates are divided out once, at the group's first strip.
+struct Walk {
+  int u, u_hi, ch8, tx, ty, z, s;
+  __device__ Walk(const DevInst& I, int u0, int hi, int ch) : u(u0), u_hi(hi), ch8(ch >> 3) {
+    const int t = u0 >> 2, rest = t / I.tiles_x;
+    s = u0 & 3;
+    tx = t - rest * I.tiles_x;
+    ty = rest % I.tiles_y;
+    z = rest / I.tiles_y;
+  }
+  __device__ bool done() const { return u >= u_hi; }
+  __device__ Chunk take(const DevInst& I) {
+    const int k = min(min(ch8, 4 - s), u_hi - u);
+    const Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k};
+    u += k;
+    s += k;
+    if (s == 4) {
+      s = 0;
+      if (++tx == I.tiles_x) {
+        tx = 0;
+        if (++ty == I.tiles_y) {
+          ty = 0;
+          ++z;
+        }
+      }
+    }
+    return c;
+  }
+};
+
+// The free-set bits of this lane for each of its rows of a chunk, read from
+// the staged mask box (4 words x 32 rows from word (x0/32) rounded down to a
+// multiple of 4).  `gp`: bit h is column lane+32h (the GP passes); otherwise
+// bits 0 and 1 are columns 2*lane and 2*lane+1.
+__device__ __forceinline__ void stage_bits(const unsigned char* st, int x0, int rpw, bool gp,
+                                           unsigned fbits[4]) {
+  const unsigned* M = reinterpret_cast<const unsigned*>(st + kOffMask);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int off = (x0 >> 5) & 3;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k >= rpw) break;
+    const unsigned* row = M + (warp * rpw + k) * 4 + off;
+    if (gp) {
+      fbits[k] = ((row[0] >> lane) & 1u) | (((row[1] >> lane) & 1u) << 1);
+    } else {
+      fbits[k] = row[lane >> 4] >> ((2 * lane) & 31);
+    }
+  }
+}
+
+// Issue a chunk of the item's pass into a stage; `mask`: also the chunk's
+// free-set words of mask[S.cur].
+template <int kFeat>
+__device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, bool gp,
+                                            const Chunk& c, unsigned st, unsigned bar,
+                                            bool mask) {
+  if (mask) {
+    mbar_expect_only(bar, kMaskBox);
+    tma_load2d(st + kOffMask, tmap(I, M_MASK0 + S.cur), (c.x0 >> 5) & ~3, c.z * I.ny + c.yc, bar);
+  }
+  if (gp) {
+    issue_gp(I, S, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
+    if constexpr ((kFeat & FEAT_TILE) != 0) {
+      if (S.cg32) issue_cgt<float>(I, S.pcur, c.x0, c.yc, st, bar);
+      else issue_cgt<double>(I, S.pcur, c.x0, c.yc, st, bar);
+    }
+  } else if (S.pass == P_CG_F) {
+    if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
+  } else if (S.cg32) {
+    if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cga<float>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
+  } else {
+    if (S.pass == P_CG_B) issue_cgb<double>(I, S.pcur, c.x0, c.yc, st, bar);
+    else issue_cga<double>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
+  }
+}
+
+// Compute a staged chunk of the item's pass.
+template <int kFeat>
+__device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool gp,
+                                          unsigned char* st, const Chunk& c,
+                                          const unsigned* fbits, Acc& acc, FF* ffs) {
+  const int cur = S.cur;
+  if (gp) {
+    if (S.pass == P_CENSUS) {
+      census32_chunk(I, st, c.x0, c.yc, I.g32[cur], I.pg32[cur], I.mask[cur], acc, ffs[0]);
+    } else if (S.pass == P_GP_ALPHA) {
+      alpha32_chunk(I, st, c.yc, c.rows, ffs);
+    } else {
+      const float al = S.dir == D_ZERO ? 0.0f : (float)S.alpha;
+      if (S.dir == D_W32)
+        trial32_chunk<D_W32>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
+                             I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
+      else
+        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
+                               I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
+    }
+  } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
+    if constexpr ((kFeat & FEAT_TILE) != 0) {
+      const int q = S.pcur ^ 1;
+      if (S.cg32)
+        cgt_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits, I.w32,
+                         I.r32[q], I.z32[q], I.p32[q], I.Ap32[q], I.q32[q], acc, ffs);
+      else
+        cgt_chunk<double>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                          I.z64[q], I.p64[q], I.Ap64[q], I.q64[q], acc, ffs);
+    }
+  } else if (S.pass == P_CG_F) {
+    const int q = S.pcur ^ 1;
+    const bool jac = I.opt.precond == PC_JACOBI;
+    if (S.cg32 && jac)
+      cgf_chunk<float, true>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits,
+                             I.w32, I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
+    else if (S.cg32)
+      cgf_chunk<float, false>(I, st, c.x0, c.yc, c.rows, (float)S.alpha, (float)S.beta, fbits,
+                              I.w32, I.r32[q], I.p32[q], I.Ap32[q], acc, ffs);
+    else if (jac)
+      cgf_chunk_box<true>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                          I.p64[q], I.Ap64[q], acc);
+    else
+      cgf_chunk_box<false>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
+                           I.p64[q], I.Ap64[q], acc);
+  } else if (S.pass == P_CG_B) {
+    const int q = S.pcur ^ 1;
+    if (S.cg32)
+      cgb_chunk<float>(I, st, c.x0, c.yc, c.rows, (float)S.beta, fbits, I.p32[q], I.Ap32[q],
+                       acc, ffs[0]);
+    else
+      cgb_chunk<double>(I, st, c.x0, c.yc, c.rows, S.beta, fbits, I.p64[q], I.Ap64[q], acc,
+                        ffs[0]);
+  } else {
+    const int ylim = min(c.rows, I.ny - c.yc);
+    const int q = S.pcur ^ 1;
+    const int row = c.z * I.ny + c.yc;
+    if (S.cg32 && I.opt.precond == PC_JACOBI)
+      cga_chunk<float, true>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
+                             ffs[0]);
+    else if (S.cg32)
+      cga_chunk<float, false>(I, st, c.x0, row, ylim, (float)S.alpha, I.w32, I.r32[q], acc,
+                              ffs[0]);
+    else if (I.opt.precond == PC_JACOBI)
+      cga_chunk<double, true>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
+    else
+      cga_chunk<double, false>(I, st, c.x0, row, ylim, S.alpha, I.w64, I.r64[q], acc, ffs[0]);
+  }
+}
+
+// ------------------------------------------------------------------ kernel --
+
+// Number of FP64 sums each pass reduces.
+__device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
+  switch (pass) {
+    case P_CENSUS: return gp32 ? 1 : 2;
+    case P_GP_ALPHA: return 2;
+    case P_TRIAL: return 3;
+    case P_CG_B: return first ? 3 : 1;
+    case P_CG_A: return 1;
+    case P_CG_F: return 4;
+    case P_CG_Z: return 1;
+    case P_RX_BUILD: return 1;
+    case P_RCG: return 4;
+    default: return 0;
+  }
+}
+
+template <int kFeat>
+__device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0, int y0, int z,
+                                         Acc& acc, FF* ffs, float* scr) {
+  const int cur = S.cur, pcur = S.pcur;
+  switch (S.pass) {
+    case P_START:
+      start_tile(I, I.x[cur], I.x32[cur], x0, y0, z);
+      break;
+    case P_CENSUS: {
+      if (S.gp32) {
+        OpCensus32 op{I, I.x32[cur], I.g32[cur], I.pg32[cur], I.mask[cur], ffs};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        // the first FP64 census after the mixed phase rebuilds x from x32
+        OpCensus op{I, I.x[cur], I.g[cur], I.mask[cur], S.x32_live ? I.x32[cur] : nullptr,
+                    I.x[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
+      break;
+    }
+    case P_GP_ALPHA: {
+      if (S.gp32) {
+        OpGpAlpha32 op{I, I.pg32[cur], ffs};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        OpGpAlpha op{I, I.x[cur], I.g[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
+      break;
+    }
+    case P_TRIAL: {
+      const double alpha = S.dir == D_ZERO ? 0.0 : S.alpha;
+      if (S.gp32) {
+        if (S.dir == D_W32) {
+          OpTrial32<D_W32> op{I, I.x32[cur], I.g32[cur], I.w32, (float)alpha, I.x32[cur ^ 1],
+                              I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], I.mask[cur],
+                              ffs};
+          stencil_tile(I, op, x0, y0, z, acc);
+        } else {
+          OpTrial32<D_NEG_G> op{I, I.x32[cur], I.g32[cur], I.w32, (float)alpha, I.x32[cur ^ 1],
+                                I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], I.mask[cur],
+                                ffs};
+          stencil_tile(I, op, x0, y0, z, acc);
+        }
+      } else if (S.dir == D_W64) {
+        OpTrial<D_W64> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                          I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else if (S.dir == D_W32) {
+        OpTrial<D_W32> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                          I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      } else {
+        OpTrial<D_NEG_G> op{I, I.x[cur], I.g[cur], I.w64, I.w32, alpha, I.x[cur ^ 1],
+                            I.g[cur ^ 1], I.mask[cur ^ 1], I.mask[cur]};
+        stencil_tile(I, op, x0, y0, z, acc);
+      }
+      break;
+    }
+    case P_CG_B: {
+      const float* g32 = S.gp32 ? I.g32[cur] : nullptr;
+      // point Jacobi (z = r / diag) runs in its own instantiations
+      const bool jac = I.opt.precond == PC_JACOBI;
+      if (S.cg32) {
+        float* p_new = I.p32[pcur ^ 1];
+        float* ap = I.Ap32[pcur ^ 1];
+        float* r1 = I.r32[pcur ^ 1];
+#define GPCG_CGB32(FIRST, JAC, BETA)                                                          \
+  {                                                                                          \
+    OpCgB<float, FIRST, JAC> op{I, r1, I.p32[pcur], I.g[cur], I.mask[cur], BETA, g32, p_new, \
+                                ap, r1, I.w32, I.diag32, I.cx32, I.cy32, I.cz32, ffs,         \
+                                I.dinv32};                                                   \
+    stencil_tile(I, op, x0, y0, z, acc);                                                      \
+  }
+        if (S.first_cg && jac) GPCG_CGB32(true, true, 0.0f)
+        else if (S.first_cg) GPCG_CGB32(true, false, 0.0f)
+        else if (jac) GPCG_CGB32(false, true, (float)S.beta)
+        else GPCG_CGB32(false, false, (float)S.beta)
+#undef GPCG_CGB32
+      } else {
+        double* p_new = I.p64[pcur ^ 1];
+        double* ap = I.Ap64[pcur ^ 1];
+        double* r1 = I.r64[pcur ^ 1];
+#define GPCG_CGB64(FIRST, JAC, BETA)                                                           \
+  {                                                                                           \
+    OpCgB<double, FIRST, JAC> op{I, r1, I.p64[pcur], I.g[cur], I.mask[cur], BETA, nullptr,     \
+                                 p_new, ap, r1, I.w64, I.diag, I.cx, I.cy, I.cz, nullptr,     \
+                                 I.dinv};                                                     \
+    stencil_tile(I, op, x0, y0, z, acc);                                                       \
+  }
+        if (S.first_cg && jac) GPCG_CGB64(true, true, 0.0)
+        else if (S.first_cg) GPCG_CGB64(true, false, 0.0)
+        else if (jac) GPCG_CGB64(false, true, S.beta)
+        else GPCG_CGB64(false, false, S.beta)
+#undef GPCG_CGB64
+      }
+      break;
+    }
+    case P_RX_COUNT:
+      if constexpr ((kFeat & FEAT_EXT) != 0) rx_count_tile(I, S, x0, y0, z, acc);
+      break;
+    case P_RX_BUILD:
+      if constexpr ((kFeat & FEAT_EXT) != 0) {
+        const bool jac = I.opt.precond == PC_JACOBI;
+        if (S.cg32 && jac) rx_build_tile<float, true>(I, S, x0, y0, z, acc, ffs);
+        else if (S.cg32) rx_build_tile<float, false>(I, S, x0, y0, z, acc, ffs);
+        else if (jac) rx_build_tile<double, true>(I, S, x0, y0, z, acc, ffs);
+        else rx_build_tile<double, false>(I, S, x0, y0, z, acc, ffs);
+      }
+      break;
+    case P_CG_Z:
+      if constexpr ((kFeat & FEAT_TILE) != 0) {
+        if (S.cg32) cg_z_tile<float>(I, S, x0, y0, z, scr, acc, ffs);
+        else cg_z_tile<double>(I, S, x0, y0, z, scr, acc, ffs);
+      }
+      break;
+    case P_CG_A:
+      if (S.cg32 && I.opt.precond == PC_JACOBI)
+        cg_a_tile<float, true>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
+                               I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
+      else if (S.cg32)
+        cg_a_tile<float, false>(I, I.w32, I.r32[pcur], I.r32[pcur ^ 1], I.p32[pcur],
+                                I.Ap32[pcur], I.dinv32, S.alpha, x0, y0, z, acc, ffs);
+      else if (I.opt.precond == PC_JACOBI)
+        cg_a_tile<double, true>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur],
+                                I.Ap64[pcur], I.dinv, S.alpha, x0, y0, z, acc, ffs);
+      else
+        cg_a_tile<double, false>(I, I.w64, I.r64[pcur], I.r64[pcur ^ 1], I.p64[pcur],
+                                 I.Ap64[pcur], I.dinv, S.alpha, x0, y0, z, acc, ffs);
+      break;
+    default:
+      break;
+  }
+}
+
+// kCond: the launch belongs to a WHILE-conditional graph whose condition this
+// kernel clears (a separate instantiation, because profilers cannot capture
+// graph nodes able to set a condition).
+// Whether this instantiation has the code of the item's pass.
+template <int kFeat>
+__device__ __forceinline__ bool pass_supported(const DevInst& I, const Snap& S) {
+  const bool tile = S.pass == P_CG_Z || (S.pass == P_CG_F && I.opt.precond == PC_TILE);
+  const bool ext = S.pass >= P_RX_COUNT && S.pass <= P_RW;
+  return (!tile || (kFeat & FEAT_TILE) != 0) && (!ext || (kFeat & FEAT_EXT) != 0);
+}
+
+template <bool kCond, int kFeat>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
+  __shared__ DevInst sI;
+  __shared__ Snap sS;
+  __shared__ Ctl sC;
+  __shared__ int s_cnt[3][kWarps];
+  __shared__ int s_scan[kWarps];
+  __shared__ double s_red[kNRed];
+  __shared__ int s_t, s_inst, s_last;
+  extern __shared__ unsigned char dyn_smem[];
+  static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
+  static_assert(sizeof(Ctl) % 8 == 0 && sizeof(Ctl) / 8 <= kThreads, "control block copy");
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // kStages TMA stages and their barriers, 128-byte aligned (offset from the
+  // array itself, so that the compiler keeps every stage access in the
+  // shared address space)
+  unsigned char* stage0 = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + kStages * kStageBytes);
+  // the group reduction's scratch lives in the first stage (no copy is in
+  // flight between groups)
+  double(*s_sum)[kThreads] = reinterpret_cast<double(*)[kThreads]>(stage0);
+  float(*s_ffh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + 4 * 8 * kThreads);
+  float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 16) * kThreads);
+  static_assert((32 + 32) * kThreads <= kStageBytes, "reduction scratch");
+
+  if (tid == 0) {
+    s_inst = -1;
+    for (int k = 0; k < kStages; ++k) mbar_init(smem_u32(&bars[k]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // Static prologue, which may overlap the end of the previous pass (launched
+  // as a programmatic dependent): the descriptor and tensor maps of the
+  // first work item's instance.  Nothing the previous pass writes is read
+  // before griddepcontrol.wait.
+  if (blockIdx.x < (unsigned)E.n_work) {
+    const int inst = __ldg(E.tiles + blockIdx.x).x;
+    if (tid < (int)(sizeof(DevInst) / 8))
+      reinterpret_cast<long long*>(&sI)[tid] =
+          __ldg(reinterpret_cast<const long long*>(E.insts + inst) + tid);
+    __syncthreads();
+    if (tid == 0) s_inst = inst;
+    if (sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the next pass may start its own prologue as soon as SMs free up
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+  if (blockIdx.x == 0 && tid == 0) {
+    const unsigned np = atomicAdd(E.npass, 1u) + 1u;
+    if (kCond && E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
+      cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
+    }
+  }
+  int seq = 0;  // chunks of the TMA pipeline consumed so far (same in all threads)
+
+  for (int first = 1;; first = 0) {
+    __syncthreads();  // the previous item's shared state is no longer read
+    // the first item of a CTA is its own index; later ones are claimed
+    if (tid == 0) s_t = first ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(E.queue, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= E.n_work) break;
+    const int2 tr = __ldg(E.tiles + t);
+    if (tr.x != s_inst || first) {
+      // a new instance (or the first item, whose descriptor the prologue
+      // loaded): read the snapshot of its state, the control block in one
+      // round trip (the finalizer's shared copy sC is free here)
+      const bool fresh = tr.x != s_inst;
+      __syncthreads();  // everyone compared against the old s_inst
+      if (tid < (int)(sizeof(Ctl) / 8))
+        reinterpret_cast<long long*>(&sC)[tid] =
+            __ldcg(reinterpret_cast<const long long*>(E.ctl + tr.x) + tid);
+      __syncthreads();
+      const bool skip = sC.pass == P_NONE;
+      // a finished instance's groups are skipped without loading its descriptor
+      if (fresh && !skip && tid < (int)(sizeof(DevInst) / 8))
+        reinterpret_cast<long long*>(&sI)[tid] =
+            __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
+      if (tid == 0) {
+        sS.pass = sC.pass;
+        sS.cur = sC.cur;
+        sS.pcur = sC.pcur;
+        sS.cg32 = sC.cg32;
+        sS.first_cg = sC.first_cg;
+        sS.dir = sC.dir;
+        sS.gp32 = sC.gp32;
+        sS.x32_live = sC.x32_live;
+        sS.m = sC.m;
+        sS.alpha = sC.alpha;
+        sS.beta = sC.beta;
+        s_inst = tr.x;
+      }
+      __syncthreads();
+      if (fresh && !skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
+    }
+    const DevInst& I = sI;
+    const Snap& S = sS;
+    if (S.pass == P_NONE) continue;
+    if (!pass_supported<kFeat>(I, S)) {
+      // launched with the wrong instantiation: report it and leave the
+      // instance unfinished (the engine stops at its pass cap)
+      if (tid == 0) atomicOr(E.err, 2);
+      continue;
+    }
+
+    Acc acc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
+    acc.c[0] = acc.c[1] = acc.c[2] = 0;
+    FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const int grp = tr.y;
+    const bool tma = tma_pass(I, S);
+    if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
+      if constexpr ((kFeat & FEAT_EXT) != 0) {
+        // compact passes of the explicit reduced system: the group is a
+        // range of compact indices
+        const long long lo = (long long)grp * S.m / I.n_groups;
+        const long long hi = (long long)(grp + 1) * S.m / I.n_groups;
+        const bool jac = I.opt.precond == PC_JACOBI;
+        if (S.pass == P_RW) {
+          if (S.cg32) rw_range<float>(I, S, lo, hi);
+          else rw_range<double>(I, S, lo, hi);
+        } else if (S.cg32) {
+          if (jac) rcg_range<float, true>(I, S, lo, hi, acc, ffs);
+          else rcg_range<float, false>(I, S, lo, hi, acc, ffs);
+        } else {
+          if (jac) rcg_range<double, true>(I, S, lo, hi, acc, ffs);
+          else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
+        }
+      }
+    } else if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_MAP) {
+      if constexpr ((kFeat & FEAT_EXT) != 0) {
+        const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+        const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
+        if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
+        else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
+      }
+    } else if (!tma) {
+      // register sweep: the group is a range of whole tiles
+      const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+      const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
+      for (int tile = t_lo; tile < t_hi; ++tile) {
+        const int rest = tile / I.tiles_x;
+        run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
+                        rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
+      }
+    } else {
+      // TMA pipeline: the group is a range of 8-row strips (4 per tile), cut
+      // into chunks of up to `ch` rows that stay inside one tile; the next
+      // kStages-1 chunks are in flight while chunk k is computed (the stage
+      // refilled at the top of an iteration is the one computed in the
+      // previous iteration).  Nothing is in flight between groups.
+      constexpr int kDepth = kStages - 1;
+      static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
+      const bool gp = gp_tma(I, S);
+      const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
+      const int ch = chunk_rows(S, gp);
+      const int rpw = ch / kWarps;
+      // chunks that write to their stage (and have block barriers inside)
+      const bool writes_stage =
+          !gp && (S.pass == P_CG_B ||
+                  (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
+      const long long n_strips = (long long)I.n_tiles * (kTY / 8);
+      Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
+      // the current chunk and the next two (h1, h2: they exist)
+      Chunk c0 = wk.take(I);
+      const bool hh1 = !wk.done();
+      Chunk c1 = hh1 ? wk.take(I) : c0;
+      const bool hh2 = !wk.done();
+      Chunk c2 = hh2 ? wk.take(I) : c0;
+      bool h1 = hh1, h2 = hh2;
+      auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
+      auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
+      if (tid == 0) {
+        // order earlier generic writes to the stages before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_chunk<kFeat>(I, S, gp, c0, smem_u32(stage(seq)), bar(seq), want_bits);
+        if (kDepth == 2 && h1)
+          issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
+      }
+      unsigned fbits[4] = {0u, 0u, 0u, 0u};
+      for (;;) {
+        if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
+          if (writes_stage)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (kDepth == 2)
+            issue_chunk<kFeat>(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2), want_bits);
+          else
+            issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
+        }
+        unsigned char* st = stage(seq);
+        const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
+        bool failed;
+        if (ok && want_bits) stage_bits(st, c0.x0, rpw, gp, fbits);
+        if (writes_stage) {
+          // the chunk has a barrier inside: agree on the wait first
+          failed = __syncthreads_or(!ok);
+          if (!failed) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
+          __syncthreads();  // the stage may be refilled
+        } else {
+          // one barrier per chunk: every thread is done with the stage (which
+          // may then be refilled) and no bounded wait gave up
+          if (ok) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
+          failed = __syncthreads_or(!ok);
+        }
+        if (failed) {
+          // a copy never completed: record it, give the copies still in
+          // flight a bounded chance to land, and leave; the engine's loop
+          // then ends on its pass cap and the host reports the error
+          if (tid == 0) {
+            atomicOr(E.err, 1);
+            if (h1) mbar_wait(bar(seq + 1), ((seq + 1) / kStages) & 1);
+            if (kDepth == 2 && h2) mbar_wait(bar(seq + 2), ((seq + 2) / kStages) & 1);
+          }
+          return;
+        }
+        seq++;
+        if (!h1) break;
+        c0 = c1;
+        c1 = c2;
+        h1 = h2;
+        h2 = !wk.done();
+        if (h2) c2 = wk.take(I);
+      }
+    }
+    // fixed-order group reduction: every thread's sums go to shared memory;
+    // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
+    // butterfly).  FP32 passes reduce their float-float accumulators in
+    // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
+    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
+                        S.pass == P_CG_Z || S.pass == P_RX_BUILD || S.pass == P_RCG)
+                           ? S.cg32 != 0
+                                                              : (S.pass != P_START && S.gp32 != 0);
+    const int ns = n_sums(S.pass, S.first_cg, S.gp32);
+    for (int k = 0; k < ns; ++k) {
+      if (ffred) {
+        s_ffh[k][tid] = ffs[k].hi;
+        s_ffl[k][tid] = ffs[k].lo;
+      } else {
+        s_sum[k][tid] = acc.s[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
+      if (lane == 0) s_cnt[k][warp] = c;
+    }
+    __syncthreads();
+    if (warp < ns) {
+      double v;
+      if (ffred) {
+        FF a{s_ffh[warp][lane], s_ffl[warp][lane]};
+        for (int j = 1; j < kWarps; ++j)
+          a = ff_add(a, FF{s_ffh[warp][lane + 32 * j], s_ffl[warp][lane + 32 * j]});
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+          a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off), __shfl_xor_sync(FULL_MASK, a.lo, off)});
+        v = ff_val(a);
+      } else {
+        v = s_sum[warp][lane];
+        for (int j = 1; j < kWarps; ++j) v += s_sum[warp][lane + 32 * j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+      }
+      if (lane == 0) s_red[warp] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double* P = I.part + (long long)grp * kNRed;
+      for (int k = 0; k < 4; ++k) P[k] = k < ns ? s_red[k] : 0.0;
+      for (int k = 0; k < 3; ++k) {
+        int c = 0;
+        for (int w = 0; w < kWarps; ++w) c += s_cnt[k][w];
+        P[4 + k] = (double)c;
+      }
+      __threadfence();
+      const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, 1u);
+      s_last = (prev == (unsigned)(I.n_groups - 1));
+    }
+    __syncthreads();
+    if (!s_last) continue;
+
+    // last group of this instance: reduce the group slots in a fixed order.
+    // Thread j loads the 7 sums of groups j and j+256 (independent loads, all
+    // in flight at once), warps reduce by butterfly, and thread k adds the 8
+    // warp results of sum k.
+    if (tid == 0) __threadfence();
+    __syncthreads();
+    {
+      static_assert(kMaxGroups <= 2 * kThreads, "finalizer covers two groups per thread");
+      double v[kNRed - 1];
+      const double* P0 = I.part;
+#pragma unroll
+      for (int k = 0; k < kNRed - 1; ++k) {
+        const double a = tid < I.n_groups ? __ldcg(P0 + (long long)tid * kNRed + k) : 0.0;
+        const double b =
+            tid + kThreads < I.n_groups ? __ldcg(P0 + (long long)(tid + kThreads) * kNRed + k) : 0.0;
+        v[k] = a + b;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < kNRed - 1; ++k) v[k] += __shfl_xor_sync(FULL_MASK, v[k], off);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < kNRed - 1; ++k) s_sum[0][k * kWarps + warp] = v[k];
+      }
+    }
+    __syncthreads();
+    if (tid < kNRed - 1) {
+      double v = 0.0;
+      for (int w = 0; w < kWarps; ++w) v += s_sum[0][tid * kWarps + w];
+      s_red[tid] = v;
+    }
+    __syncthreads();
+    if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_COUNT) {
+      // the groups' offsets in the compact numbering (exclusive prefix sum
+      // of their free counts, two groups per thread)
+      int t0, t1;
+      const double* P0 = I.part;
+      const int c0 = tid < I.n_groups ? (int)__ldcg(P0 + (long long)tid * kNRed + 4) : 0;
+      const int o0 = cta_excl_scan(c0, s_scan, t0);
+      const int g1 = tid + kThreads;
+      const int c1 = g1 < I.n_groups ? (int)__ldcg(P0 + (long long)g1 * kNRed + 4) : 0;
+      const int o1 = cta_excl_scan(c1, s_scan, t1);
+      if (tid < I.n_groups) I.goff[tid] = o0;
+      if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
+    }
+    // the state machine runs on a shared copy of the control block (one
+    // round trip in, one out, instead of dependent global accesses)
+    long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
+    long long* cs = reinterpret_cast<long long*>(&sC);
+    if (tid < (int)(sizeof(Ctl) / 8)) cs[tid] = __ldcg(cg + tid);
+    __syncthreads();
+    if (tid == 0) {
+      s_red[kNRed - 1] = 0.0;
+      sC.arrive = 0u;
+      finalize(I, sC, s_red, E.live);
+    }
+    __syncthreads();
+    if (tid < (int)(sizeof(Ctl) / 8)) __stcg(cg + tid, cs[tid]);
+  }
+
+  // the last CTA to leave resets the queue for the next launch
+  if (tid == 0) {
+    if (atomicAdd(E.exits, 1u) == gridDim.x - 1) {
+      *E.queue = 0;
+      *E.exits = 0u;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace
+}  // namespace gpcg
