@@ -39,7 +39,7 @@ TAU_REL = 1e-6
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass_kernel_traffic_single_large_1600.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_cs_0101018_gb300", "csrc", f)
-                  for f in ("gpcg_kernels.cu", "engine.h")]
+                  for f in ("pass_engine.cuh", "gpcg_kernels.cu", "engine.h")]
 
 
 def _kernel_sha():
