@@ -2585,7 +2585,7 @@ __device__ __forceinline__ void issue_gp(const DevInst& I, const Snap& S, int x0
 // the free set and |A|, |B|, ||pg||^2 (as OpCensus32).  Points past nx
 // arrive as zeros and contribute nothing.
 __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned char* st, int x0,
-                                               int yc, float* g_out, float* pg_out,
+                                               int yc, int rows, float* g_out, float* pg_out,
                                                unsigned* m_out, Acc& acc, FF& ff) {
   using G = GeoGP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2601,7 +2601,7 @@ __device__ __forceinline__ void census32_chunk(const DevInst& I, const unsigned 
   for (int k = 0; k < G::RPW; ++k) {
     const int r = warp * G::RPW + k;
     const int y = yc + r;
-    if (y >= I.ny) break;  // warp-uniform
+    if (r >= rows || y >= I.ny) break;  // warp-uniform
     const long long row = (long long)y * I.px + x0;
     bool fr[2];
 #pragma unroll
@@ -2678,14 +2678,15 @@ __device__ __forceinline__ void alpha32_chunk(const DevInst& I, const unsigned c
 // s = xt32 - x32.  `fbits` holds the lane's bits of the current free set.
 template <int DK>
 __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned char* st, int x0,
-                                              int yc, float alpha, const unsigned* fbits,
+                                              int yc, int rows, float alpha,
+                                              const unsigned* fbits,
                                               float* xt_out, float* gt_out, float* pg_out,
                                               unsigned* m_out, Acc& acc, FF* ff) {
   using G = GeoGP;
   constexpr int RPW = G::RPW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = warp * RPW;
-  if (yc + r0 >= I.ny) return;  // warp-uniform
+  if (r0 >= rows || yc + r0 >= I.ny) return;  // warp-uniform
   const float* XH = reinterpret_cast<const float*>(st + G::OFF_XH);
   const float* LH = reinterpret_cast<const float*>(st + G::OFF_LH);
   const float* UH = reinterpret_cast<const float*>(st + G::OFF_UH);
@@ -2712,7 +2713,7 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
   for (int k = 0; k < RPW; ++k) {
     const int r = r0 + k;
     const int y = yc + r;
-    if (y >= I.ny) break;  // warp-uniform
+    if (r >= rows || y >= I.ny) break;  // warp-uniform: a chunk may hold 8 of the box's rows
     const int q = k + 1;
     const int b = (r + 1) * G::BW + G::H + lane;  // box index of column `lane` of row r
     // west and east neighbours across the 64 columns
@@ -2890,17 +2891,18 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
   const int cur = S.cur;
   if (gp) {
     if (S.pass == P_CENSUS) {
-      census32_chunk(I, st, c.x0, c.yc, I.g32[cur], I.pg32[cur], I.mask[cur], acc, ffs[0]);
+      census32_chunk(I, st, c.x0, c.yc, c.rows, I.g32[cur], I.pg32[cur], I.mask[cur], acc,
+                     ffs[0]);
     } else if (S.pass == P_GP_ALPHA) {
       alpha32_chunk(I, st, c.yc, c.rows, ffs);
     } else {
       const float al = S.dir == D_ZERO ? 0.0f : (float)S.alpha;
       if (S.dir == D_W32)
-        trial32_chunk<D_W32>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
-                             I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
+        trial32_chunk<D_W32>(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1],
+                             I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
       else
-        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
-                               I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
+        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1],
+                               I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
     }
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {

@@ -276,6 +276,21 @@ def test_extracted_and_masked_solves_agree_in_a_batch():
         assert _rel_err(x, xm) <= 1e-9
 
 
+@pytest.mark.parametrize("side", [400, 130])
+def test_census_counts_every_point_once(side):
+    """The staged passes walk 8-row strips in chunks of up to 16 rows, so
+    group boundaries leave 8-row chunks (22 at 400^2); the FP32 census must
+    count each point once: ||pg(x0)|| of the mixed solve matches the oracle's
+    census at x0 to FP32 accuracy, and the FP64 one to FP64 accuracy."""
+    qp = gi.grid_qp_2d(side, side, seed=530, shift=1e-2, bounds="two_sided")
+    start = np.where(np.isfinite(qp.l), qp.l, np.where(np.isfinite(qp.u), qp.u, 0.0))
+    x0 = oracle.project(qp.l, qp.u, start)  # the default start point, P[l]
+    ref = np.sqrt(oracle.census(qp, x0).pg_norm2)
+    for prec, tol in ((g.MIXED, 1e-5), (g.FP64, 1e-12)):
+        _, _, st = _solve(qp, tau_rel=1e-6, precision=prec, max_outer=1)
+        assert abs(st["pg_norm0"] - ref) <= tol * ref, (prec, st["pg_norm0"], ref)
+
+
 def test_tile_preconditioner_needs_a_2d_staged_problem():
     qp = gi.grid_qp_3d(17, 9, 6, seed=503, shift=0.02, sigma=0.5, bounds="box1")
     prob = g.gpcg_problem_create(qp)
