@@ -73,6 +73,10 @@ enum TMap : int {
   MG_X32H0, MG_X32H1, MG_L32H, MG_U32H, MG_G32H0, MG_G32H1, MG_W32H,  // G18
   MG_PGH0, MG_PGH1,                                                  // G34
   MG_L32, MG_U32, MG_B32,                                            // 64 x 16
+  // the trial along -g with alpha0 at the trial point: halo-2 boxes 72 x 20
+  // from (x0-4, y-2) of x32[2], l32, u32, g32[2]; 72 x 18 from (x0-4, y-1) of
+  // b32 and the FP32 diag, cx; 72 x 19 from (x0-4, y-2) of the FP32 cy
+  MG_X2H0, MG_X2H1, MG_L2H, MG_U2H, MG_G2H0, MG_G2H1, MG_B18, MG_D18, MG_CX18, MG_CY19,
   M_MASK0, M_MASK1,  // free-set words of mask[0], mask[1]: box 4 words x 32 rows
   M_COUNT
 };

@@ -384,7 +384,11 @@ static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
   bool ok = f32(I.x32[0], 72, 18) && f32(I.x32[1], 72, 18) && f32(I.l32, 72, 18) &&
             f32(I.u32, 72, 18) && f32(I.g32[0], 72, 18) && f32(I.g32[1], 72, 18) &&
             f32(I.w32, 72, 18) && f32(I.pg32[0], 72, 34) && f32(I.pg32[1], 72, 34) &&
-            f32(I.l32, 64, 16) && f32(I.u32, 64, 16) && f32(I.b32, 64, 16);
+            f32(I.l32, 64, 16) && f32(I.u32, 64, 16) && f32(I.b32, 64, 16) &&
+            f32(I.x32[0], 72, 20) && f32(I.x32[1], 72, 20) && f32(I.l32, 72, 20) &&
+            f32(I.u32, 72, 20) && f32(I.g32[0], 72, 20) && f32(I.g32[1], 72, 20) &&
+            f32(I.b32, 72, 18) && f32(I.diag32, 72, 18) && f32(I.cx32, 72, 18) &&
+            f32(I.cy32, 72, 19);
   if (!ok || q != m + kGpMaps) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MG_X32H0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||

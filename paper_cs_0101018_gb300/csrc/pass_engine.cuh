@@ -1623,6 +1623,28 @@ __device__ void cg_advance(const DevInst& I, Ctl& C, double zAp, double ApMAp) {
   }
 }
 
+// The next gradient projection step (Eq. next-y) from <g_Omega, g_Omega> and
+// <g_Omega, A g_Omega> at the current iterate: alpha0 = the exact minimiser
+// along -grad_Omega q (Eq. bqpls), then trials alpha0, alpha0/2, ...
+__device__ void gp_step(Ctl& C, double gg, double gAg) {
+  if (!(gAg > 0.0) || !isfinite(gg)) {
+    set_done(C, S_NUMERIC);
+    return;
+  }
+  C.alpha0 = gg / gAg;
+  C.alpha = C.alpha0;
+  C.ls_i = 0;
+  C.dir = D_NEG_G;
+  C.trial_gp = 1;
+  C.pass = P_TRIAL;
+}
+
+// Whether the instance's mixed-phase GP passes are staged (then a trial along
+// -g also forms alpha0 at its trial point).
+__device__ __forceinline__ bool staged_gp32(const DevInst& I, const Ctl& C) {
+  return C.gp32 && I.dim == 2 && I.tma_gp && I.tma32 && I.tma_mask;
+}
+
 __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live) {
   for (int k = 0; k < kNRed; ++k) C.red[k] = red[k];
   if (C.hold) return;  // standalone timing/test launch: leave the state alone
@@ -1685,20 +1707,9 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       }
       break;
     }
-    case P_GP_ALPHA: {
-      const double gg = red[0], gAg = red[1];
-      if (!(gAg > 0.0) || !isfinite(gg)) {
-        set_done(C, S_NUMERIC);
-        break;
-      }
-      C.alpha0 = gg / gAg;  // Eq. bqpls: exact minimiser along -grad_Omega q
-      C.alpha = C.alpha0;
-      C.ls_i = 0;
-      C.dir = D_NEG_G;
-      C.trial_gp = 1;
-      C.pass = P_TRIAL;
+    case P_GP_ALPHA:
+      gp_step(C, red[0], red[1]);
       break;
-    }
     case P_TRIAL: {
       C.ls_trials++;
       const double gs = red[0];
@@ -1723,6 +1734,8 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
           if (dec > C.dmax) C.dmax = dec;
           if (stop) {
             begin_cg(I, C);
+          } else if (staged_gp32(I, C)) {
+            gp_step(C, red[2], red[3]);  // the trial formed alpha0 at the new iterate
           } else {
             C.pass = P_GP_ALPHA;
           }
@@ -2536,6 +2549,31 @@ struct GeoGP {
 static_assert(GeoGP::END <= kOffMask, "stage layout");
 static_assert(GeoGP::CH == GeoF<float>::CH, "the GP passes use the fused pass's band maps");
 
+// The trial along -g of the mixed phase also forms the next GP step's alpha0
+// (Eq. bqpls) at the trial point, <pg, A32 pg> with pg its projected
+// gradient, which needs pg one point around the chunk and so xt two: its
+// stage (boxes 128-byte aligned) holds
+//   X | L | U | G : FP32 72 x 20 from (x0-4, y-2): x32, l32, u32, g32
+//   B | D | CX : 72 x 18 from (x0-4, y-1)    CY : 72 x 19 from (x0-4, y-2).
+// The G box receives xt once the direction is used, the B box pg once b is.
+struct GeoGA {
+  static constexpr int CH = GeoGP::CH, H = 4, BW = 64 + 2 * H;
+  static constexpr int RH = CH + 4, RB = CH + 2, RY = CH + 3;
+  static constexpr int SZ_H = align128(RH * BW * 4), SZ_B = align128(RB * BW * 4);
+  static constexpr int OFF_X = 0, OFF_L = SZ_H, OFF_U = 2 * SZ_H, OFF_G = 3 * SZ_H;
+  static constexpr int OFF_B = 4 * SZ_H, OFF_D = OFF_B + SZ_B, OFF_CX = OFF_D + SZ_B;
+  static constexpr int OFF_CY = OFF_CX + SZ_B;
+  static constexpr int END = OFF_CY + align128(RY * BW * 4);
+  static constexpr unsigned TX = (4 * RH * BW + 3 * RB * BW + RY * BW) * 4;
+};
+static_assert(GeoGA::END <= kOffMask, "stage layout");
+
+// Whether the pass is the staged trial along -g that forms alpha0 (a trial
+// along w, the projected search, streams the GeoGP layout).
+__device__ __forceinline__ bool trial_alpha0(const Snap& S) {
+  return S.pass == P_TRIAL && S.dir != D_W32;
+}
+
 // Whether the item's pass is a mixed-phase GP pass on the TMA path.
 __device__ __forceinline__ bool gp_tma(const DevInst& I, const Snap& S) {
   return S.gp32 && I.dim == 2 && I.tma_gp && I.tma32 && I.tma_mask &&
@@ -2555,6 +2593,19 @@ __device__ __forceinline__ void issue_gp(const DevInst& I, const Snap& S, int x0
     tma_load2d(st + F::OFF_D, tmap(I, M32_D), x0, yc, bar);
     tma_load2d(st + F::OFF_CX, tmap(I, M32_CX), x0 - F::H, yc, bar);
     tma_load2d(st + F::OFF_CY, tmap(I, M32_CY), x0, yc - 1, bar);
+    return;
+  }
+  if (trial_alpha0(S)) {
+    using A = GeoGA;
+    mbar_expect(bar, A::TX);
+    tma_load2d(st + A::OFF_X, tmap(I, MG_X2H0 + cur), x0 - A::H, yc - 2, bar);
+    tma_load2d(st + A::OFF_L, tmap(I, MG_L2H), x0 - A::H, yc - 2, bar);
+    tma_load2d(st + A::OFF_U, tmap(I, MG_U2H), x0 - A::H, yc - 2, bar);
+    tma_load2d(st + A::OFF_G, tmap(I, MG_G2H0 + cur), x0 - A::H, yc - 2, bar);
+    tma_load2d(st + A::OFF_B, tmap(I, MG_B18), x0 - A::H, yc - 1, bar);
+    tma_load2d(st + A::OFF_D, tmap(I, MG_D18), x0 - A::H, yc - 1, bar);
+    tma_load2d(st + A::OFF_CX, tmap(I, MG_CX18), x0 - A::H, yc - 1, bar);
+    tma_load2d(st + A::OFF_CY, tmap(I, MG_CY19), x0 - A::H, yc - 2, bar);
     return;
   }
   const bool along_w = S.pass == P_TRIAL && S.dir == D_W32;
@@ -2775,6 +2826,133 @@ __device__ __forceinline__ void trial32_chunk(const DevInst& I, const unsigned c
   ff_acc(ff[2], s_pg);
 }
 
+// P_TRIAL along -g (mixed) on one staged chunk of `rows` rows, with the next
+// GP step's alpha0 terms at the trial point: (1) xt32 = P[x32 - alpha g32] on
+// the whole 20 x 72 box, in place of g32 (with <g,s> at the chunk's points);
+// (2) gt = A32 xt + b32 and pg at the chunk's points (the outputs, counts,
+// free set, <s,gt> and ||pg||^2 of trial32_chunk, in the same arithmetic),
+// then pg on the ring one point around them, each in place of b32; (3) the
+// sum <pg, A32 pg> over the chunk's points (the terms of alpha32_chunk).
+// Two block barriers; every thread calls it.
+__device__ __forceinline__ void trial32a_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                               int rows, float alpha, const unsigned* fbits,
+                                               float* xt_out, float* gt_out, float* pg_out,
+                                               unsigned* m_out, Acc& acc, FF* ff) {
+  using G = GeoGA;
+  constexpr int BW = G::BW, RPW = GeoGP::RPW;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* X = reinterpret_cast<const float*>(st + G::OFF_X);
+  const float* L = reinterpret_cast<const float*>(st + G::OFF_L);
+  const float* U = reinterpret_cast<const float*>(st + G::OFF_U);
+  float* XT = reinterpret_cast<float*>(st + G::OFF_G);  // g32, then xt
+  float* PG = reinterpret_cast<float*>(st + G::OFF_B);  // b32, then pg
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  const int ylim = min(rows, I.ny - yc);  // the chunk's rows inside the grid
+  // (1) xt on the box; <g, s> at the chunk's points
+  float s_gs = 0.0f;
+  for (int e = tid; e < G::RH * BW; e += kThreads) {
+    const int br = e / BW, bc = e - br * BW;
+    const float x = X[e], g = XT[e];
+    const float xt = mid3f(L[e], U[e], fmaf(alpha, -g, x));
+    const int r = br - 2, j = bc - G::H;
+    if (r >= 0 && r < ylim && j >= 0 && j < 64) s_gs = fmaf(g, xt - x, s_gs);
+    XT[e] = xt;
+  }
+  __syncthreads();
+  // gt at chunk row r, column j (-1 <= r <= 16, -1 <= j <= 64): diag, west,
+  // east, the row above, the row below (the order of the register sweep).
+  // Band boxes start one row above the chunk, the CY box two.
+  auto gt_at = [&](int r, int j) {
+    const int e = (r + 2) * BW + G::H + j, b = (r + 1) * BW + G::H + j;
+    float a = D[b] * XT[e];
+    a = fmaf(CX[b - 1], XT[e - 1], a);
+    a = fmaf(CX[b], XT[e + 1], a);
+    a = fmaf(CY[b], XT[e - BW], a);
+    a = fmaf(CY[b + BW], XT[e + BW], a);
+    return a + PG[b];
+  };
+  // (2) the chunk's points: warp w holds rows 2w and 2w+1
+  float s_sgt = 0.0f, s_pg = 0.0f;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = warp * RPW + k;
+    if (r >= ylim) break;  // warp-uniform
+    const int y = yc + r;
+    const long long row = (long long)y * I.px + x0;
+    bool fr[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = lane + 32 * h;
+      const bool ok = x0 + j < I.nx;
+      const int e = (r + 2) * BW + G::H + j, b = (r + 1) * BW + G::H + j;
+      const float gt = gt_at(r, j);
+      const float xt = XT[e];
+      const float sk = xt - X[e];
+      const bool al = xt == L[e], au = xt == U[e];
+      const bool act = al || au;
+      fr[h] = ok && !act;
+      const float pg = pg_compf(al, au, gt);
+      PG[b] = pg;
+      s_sgt = fmaf(sk, gt, s_sgt);
+      s_pg = fmaf(pg, pg, s_pg);
+      acc.c[0] += ok && act;
+      acc.c[1] += ok && ((al && gt >= 0.0f) || (au && gt <= 0.0f));
+      acc.c[2] += ok && (((fbits[k] >> h) & 1u) != (fr[h] ? 1u : 0u));
+      if (ok) {
+        xt_out[row + j] = xt;
+        gt_out[row + j] = gt;
+        pg_out[row + j] = pg;
+      }
+    }
+    const unsigned w0 = __ballot_sync(FULL_MASK, fr[0]);
+    const unsigned w1 = __ballot_sync(FULL_MASK, fr[1]);
+    const int wc = (x0 >> 5) + lane;
+    if (lane < 2 && wc < I.mw) m_out[(long long)y * I.mw + wc] = lane ? w1 : w0;
+  }
+  // the ring: rows -1 and ylim over columns -1..64, columns -1 and 64 of the
+  // chunk's rows (points outside the grid arrive as zeros and give pg = 0)
+  const int n_ring = 2 * (64 + 2) + 2 * ylim;
+  for (int t = tid; t < n_ring; t += kThreads) {
+    int r, j;
+    if (t < 2 * (64 + 2)) {
+      r = t < 64 + 2 ? -1 : ylim;
+      j = t % (64 + 2) - 1;
+    } else {
+      r = (t - 2 * (64 + 2)) >> 1;
+      j = (t & 1) ? 64 : -1;
+    }
+    const int e = (r + 2) * BW + G::H + j, b = (r + 1) * BW + G::H + j;
+    const float gt = gt_at(r, j);
+    const float xt = XT[e];
+    PG[b] = pg_compf(xt == L[e], xt == U[e], gt);
+  }
+  __syncthreads();
+  // (3) <pg, A32 pg> over the chunk's points
+  float s_pap = 0.0f;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = warp * RPW + k;
+    if (r >= ylim) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = (r + 1) * BW + G::H + lane + 32 * h;
+      const float v = PG[b];
+      float a = D[b] * v;
+      a = fmaf(CX[b - 1], PG[b - 1], a);
+      a = fmaf(CX[b], PG[b + 1], a);
+      a = fmaf(CY[b], PG[b - BW], a);
+      a = fmaf(CY[b + BW], PG[b + BW], a);
+      s_pap = fmaf(v, a, s_pap);
+    }
+  }
+  ff_acc(ff[0], s_gs);
+  ff_acc(ff[1], s_sgt);
+  ff_acc(ff[2], s_pg);
+  ff_acc(ff[3], s_pap);
+}
+
 // Whether the item's pass runs through the TMA pipeline.
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
@@ -2901,8 +3079,8 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
         trial32_chunk<D_W32>(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1],
                              I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
       else
-        trial32_chunk<D_NEG_G>(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1],
-                               I.g32[cur ^ 1], I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
+        trial32a_chunk(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
+                       I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
     }
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {
@@ -2961,7 +3139,7 @@ __device__ __forceinline__ int n_sums(int pass, int first, int gp32) {
   switch (pass) {
     case P_CENSUS: return gp32 ? 1 : 2;
     case P_GP_ALPHA: return 2;
-    case P_TRIAL: return 3;
+    case P_TRIAL: return 4;  // the staged trial along -g adds <pg, A pg> at the trial point
     case P_CG_B: return first ? 3 : 1;
     case P_CG_A: return 1;
     case P_CG_F: return 4;
@@ -3277,8 +3455,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       const int rpw = ch / kWarps;
       // chunks that write to their stage (and have block barriers inside)
       const bool writes_stage =
-          !gp && (S.pass == P_CG_B ||
-                  (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
+          gp ? trial_alpha0(S)
+             : (S.pass == P_CG_B ||
+                (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
       Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
       // the current chunk and the next two (h1, h2: they exist)
