@@ -1579,7 +1579,7 @@ __device__ void begin_outer(const DevInst& I, Ctl& C) {
 
 // ||grad_Omega q|| <= tau held.  In mixed precision the first time this
 // happens starts the closing FP64 CG phase on the identified face.
-__device__ void on_converged(const DevInst& I, Ctl& C) {
+__device__ void on_converged(const DevInst& I, Ctl& C, int* live) {
   if (C.gp32) {
     // the FP32-streamed estimate met tau: certify in FP64 and, with refine,
     // run the closing FP64 CG phase on the identified face
@@ -1592,7 +1592,13 @@ __device__ void on_converged(const DevInst& I, Ctl& C) {
     C.outer_iters++;
     begin_cg(I, C);
   } else {
-    set_done(C, S_OK);
+    // the accepted FP64 trial already gave g, ||pg||, |A| and |B| at the
+    // returned point, and q by its decrease: done without a final census
+    C.status = S_OK;
+    C.census_mode = CM_INIT;
+    C.pass = P_NONE;
+    C.done = 1;
+    atomicSub(live, 1);
   }
 }
 
@@ -1719,6 +1725,9 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         C.pg2 = red[2];
         C.nA = red[4];
         C.nB = red[5];
+        // <x, g + b> = 2 (q(x) - c) moves by 2 (q(xt) - q(x)) = <s, g + gt>,
+        // exact for a quadratic (every FP64 census sets it afresh)
+        C.xgb += 2.0 * dq;
         const double pgn = sqrt(C.pg2);
         if (C.trial_gp) {
           C.gp_iters++;
@@ -1726,7 +1735,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
           const double dec = -dq;
           const bool same = red[6] == 0.0;  // Eq. pgstop1
           if (pgn <= C.tau) {
-            on_converged(I, C);
+            on_converged(I, C, live);
             break;
           }
           const bool stop = same || (C.gp_j >= 2 && dec <= o.eta1 * C.dmax) ||  // Eq. pgstop2
@@ -1742,7 +1751,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         } else {
           C.refining = 0;
           if (pgn <= C.tau) {
-            on_converged(I, C);
+            on_converged(I, C, live);
             break;
           }
           if (C.gp32) {
