@@ -1015,10 +1015,12 @@ struct TileLine {
 // couplings at distance 1, 2, 4, 8, 16 by shuffles, after which each u_l
 // stands alone; last the even points are recovered.  The system is a
 // principal submatrix of A (symmetric positive definite), so no pivot vanishes.
+// The reciprocals are the hardware's approximate ones (__fdividef, within 2
+// ulp): M^-1 stays a fixed operator, which is all the recurrences need.
 __device__ __forceinline__ void line_solve(float b0, float b1, float cw, float cm, float d0,
                                            float d1, float& x0, float& x1) {
   const int lane = threadIdx.x & 31;
-  const float ie = __frcp_rn(b0);
+  const float ie = __fdividef(1.0f, b0);
   float ce = __shfl_down_sync(FULL_MASK, cw, 1);
   const float ie_n = __shfl_down_sync(FULL_MASK, ie, 1);
   const float d0_n = __shfl_down_sync(FULL_MASK, d0, 1);
@@ -1030,7 +1032,7 @@ __device__ __forceinline__ void line_solve(float b0, float b1, float cw, float c
   float d = d1 - cm * d0 * ie - ce * d0_n * ie_n;
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
-    const float ib = __frcp_rn(b);
+    const float ib = __fdividef(1.0f, b);
     float am = __shfl_up_sync(FULL_MASK, a, s), cmm = __shfl_up_sync(FULL_MASK, c, s);
     float dm = __shfl_up_sync(FULL_MASK, d, s), ibm = __shfl_up_sync(FULL_MASK, ib, s);
     float ap = __shfl_down_sync(FULL_MASK, a, s), cp = __shfl_down_sync(FULL_MASK, c, s);
@@ -1043,7 +1045,7 @@ __device__ __forceinline__ void line_solve(float b0, float b1, float cw, float c
     b = b - k1 * cmm - k2 * ap;
     d = d - k1 * dm - k2 * dp;
   }
-  const float u = __fdiv_rn(d, b);
+  const float u = __fdividef(d, b);
   float um = __shfl_up_sync(FULL_MASK, u, 1);
   if (lane == 0) um = 0.0f;
   x1 = u;
