@@ -78,6 +78,9 @@ enum TMap : int {
   // b32 and the FP32 diag, cx; 72 x 19 from (x0-4, y-2) of the FP32 cy
   MG_X2H0, MG_X2H1, MG_L2H, MG_U2H, MG_G2H0, MG_G2H1, MG_B18, MG_D18, MG_CX18, MG_CY19,
   M_MASK0, M_MASK1,  // free-set words of mask[0], mask[1]: box 4 words x 32 rows
+  // the FP64 alpha0 pass (staged, FEAT_F64 kernels): halo boxes 68 x 10 from
+  // (x0-2, y-1) of x[2], g[2], l, u
+  MF_X0, MF_X1, MF_G0, MF_G1, MF_L, MF_U,
   M_COUNT
 };
 constexpr int kGpMaps = M_MASK0 - MG_X32H0;  // the GP maps (make_gp_maps encodes them)
@@ -112,7 +115,7 @@ constexpr int kMaxNb = 6;
 
 // Optional pass families, compiled into their own instantiations of the
 // pass kernel so that the default kernel carries none of their code.
-enum Feature : int { FEAT_TILE = 1, FEAT_EXT = 2 };
+enum Feature : int { FEAT_TILE = 1, FEAT_EXT = 2, FEAT_F64 = 4 };
 
 // Preconditioners of the CG phase (Opts.precond; the public gpcg_precond).
 enum Precond : int { PC_NONE = 0, PC_JACOBI = 1, PC_TILE = 2 };
@@ -183,6 +186,7 @@ struct DevInst {
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
   int tma64, tma32;        // the FP64 / FP32 CG maps are valid
   int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid
+  int tma_f64gp, pad_f;    // the FP64 alpha0 maps are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   const double* dinv;      // 1/diag (0 in pad columns): the point-Jacobi preconditioner

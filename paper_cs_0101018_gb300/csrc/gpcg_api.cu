@@ -442,6 +442,22 @@ static bool make_tile_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   return true;
 }
 
+// Encode the FP64 alpha0 pass's maps: halo boxes 68 x 10 of x[2], g[2], l, u.
+static bool make_f64gp_maps(gpcg_problem* p, cudaStream_t s) {
+  if (!have_encode() || p->dim != 2) return false;
+  DevInst& I = p->inst;
+  const void* src[6] = {I.x[0], I.x[1], I.g[0], I.g[1], I.l, I.u};
+  CUtensorMap m[6];
+  static_assert(MF_U - MF_X0 == 5, "six FP64 alpha0 maps");
+  for (int k = 0; k < 6; ++k)
+    if (!encode_map(&m[k], false, src[k], p, 68, 10)) return false;
+  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MF_X0;
+  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return true;
+}
+
 static bool tma_disabled() {
   const char* e = getenv("GPCG_NO_TMA");
   return e && *e && *e != '0';
@@ -659,6 +675,7 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
   }
   p->inst.tma_mask = (!tma_disabled() && make_mask_maps(p, s)) ? 1 : 0;
   p->inst.tma64 = (p->inst.tma_mask && make_maps(p, false, s)) ? 1 : 0;
+  p->inst.tma_f64gp = (p->inst.tma64 && make_f64gp_maps(p, s)) ? 1 : 0;
   *out = p;
   return GPCG_OK;
 }
@@ -741,6 +758,7 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
 static int feature_set(const gpcg_options* o) {
   if (o->precond == GPCG_PRECOND_TILE) return FEAT_TILE;
   if (o->cg_system == GPCG_CG_EXTRACTED) return FEAT_EXT;
+  if (o->precision == GPCG_FP64) return FEAT_F64;
   return 0;
 }
 

@@ -351,12 +351,14 @@ template __global__ void pass_kernel<false, 0>(EngineArgs);
 // the instantiations with optional passes (their own translation units)
 const void* pass_kernel_ptr_tile(bool cond);
 const void* pass_kernel_ptr_rx(bool cond);
+const void* pass_kernel_ptr_f64(bool cond);
 
-// The pass kernel for a feature set (0, FEAT_TILE or FEAT_EXT); `cond`: the
+// The pass kernel for a feature set (0, FEAT_TILE, FEAT_EXT or FEAT_F64); `cond`: the
 // instantiation that may clear a WHILE graph's condition.
 const void* pass_kernel_ptr(bool cond, int feat) {
   if (feat == FEAT_TILE) return pass_kernel_ptr_tile(cond);
   if (feat == FEAT_EXT) return pass_kernel_ptr_rx(cond);
+  if (feat == FEAT_F64) return pass_kernel_ptr_f64(cond);
   return cond ? (const void*)pass_kernel<true, 0> : (const void*)pass_kernel<false, 0>;
 }
 
@@ -367,7 +369,7 @@ int pass_grid(int n_work) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT})
+    for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64})
       for (bool cond : {true, false})
         cudaFuncSetAttribute(pass_kernel_ptr(cond, feat),
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);

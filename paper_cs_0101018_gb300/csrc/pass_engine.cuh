@@ -2964,9 +2964,94 @@ __device__ __forceinline__ void trial32a_chunk(const DevInst& I, unsigned char* 
   ff_acc(ff[3], s_pap);
 }
 
+// P_GP_ALPHA in FP64 (FEAT_F64 kernels, 2-D): <pg,pg> and <pg, A pg> over
+// 8-row chunks.  Stage layout: X | G | L | U, FP64 halo boxes 68 x 10 from
+// (x0-2, y-1) | D 64 x 8 | CX 66 x 8 from x0-2 | CY 64 x 9 from y-1 (the fused
+// FP64 step's band boxes).  The projected gradient needs no FP64 arithmetic
+// (its tests are on bit patterns); it is formed once per staged element, in
+// place of g, then each warp applies the stencil to its row.
+struct GeoA64 {
+  static constexpr int CH = 8, H = 2, BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * 8);
+  static constexpr int OFF_X = 0, OFF_G = SZ_H, OFF_L = 2 * SZ_H, OFF_U = 3 * SZ_H;
+  static constexpr int OFF_D = 4 * SZ_H, OFF_CX = OFF_D + 64 * CH * 8;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 8);
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 8);
+  static constexpr unsigned TX =
+      (4 * (CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * 8;
+};
+static_assert(GeoA64::END <= kOffMask && GeoA64::CH == kWarps && GeoA64::CH == GeoF<double>::CH,
+              "stage layout (one row per warp; the fused FP64 step's band maps)");
+
+// Whether the item's pass is the staged FP64 alpha0 pass of a FEAT_F64 kernel.
+template <int kFeat>
+__device__ __forceinline__ bool alpha64_tma(const DevInst& I, const Snap& S) {
+  return (kFeat & FEAT_F64) != 0 && S.pass == P_GP_ALPHA && !S.gp32 && I.dim == 2 &&
+         I.tma_f64gp && I.tma64;
+}
+
+__device__ __forceinline__ void issue_alpha64(const DevInst& I, const Snap& S, int x0, int yc,
+                                              unsigned st, unsigned bar) {
+  using G = GeoA64;
+  const int cur = S.cur;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_X, tmap(I, MF_X0 + cur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_G, tmap(I, MF_G0 + cur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_L, tmap(I, MF_L), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_U, tmap(I, MF_U), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M64_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M64_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M64_FCY), x0, yc - 1, bar);
+}
+
+__device__ __forceinline__ void alpha64_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                              int rows, Acc& acc) {
+  using G = GeoA64;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
+  double* PG = reinterpret_cast<double*>(st + G::OFF_G);  // g, then pg
+  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
+  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
+  const double* D = reinterpret_cast<const double*>(st + G::OFF_D);
+  const double* CX = reinterpret_cast<const double*>(st + G::OFF_CX);
+  const double* CY = reinterpret_cast<const double*>(st + G::OFF_CY);
+  // points outside the grid arrive as zeros: l = u = x, pg = 0
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) PG[e] = pg_comp(X[e], PG[e], L[e], U[e]);
+  __syncthreads();
+  const int ry = warp;
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  if (ry >= min(rows, I.ny - yc) || !v0) return;
+  const double* Pr = PG + (ry + 1) * G::BW + G::H + c;
+  const double* Dr = D + ry * 64 + c;
+  const double* Xr = CX + ry * (64 + G::H) + G::H + c;
+  const double* Ys = CY + ry * 64 + c;
+  const double* Yn = CY + (ry + 1) * 64 + c;
+  // diag, west, east, south, north (the order of the register sweep)
+  double a0 = Dr[0] * Pr[0];
+  a0 = fma(Xr[-1], Pr[-1], a0);
+  a0 = fma(Xr[0], Pr[1], a0);
+  a0 = fma(Ys[0], Pr[-G::BW], a0);
+  a0 = fma(Yn[0], Pr[G::BW], a0);
+  acc.s[0] = fma(Pr[0], Pr[0], acc.s[0]);
+  acc.s[1] = fma(Pr[0], a0, acc.s[1]);
+  if (v1) {
+    double a1 = Dr[1] * Pr[1];
+    a1 = fma(Xr[0], Pr[0], a1);
+    a1 = fma(Xr[1], Pr[2], a1);
+    a1 = fma(Ys[1], Pr[1 - G::BW], a1);
+    a1 = fma(Yn[1], Pr[G::BW + 1], a1);
+    acc.s[0] = fma(Pr[1], Pr[1], acc.s[0]);
+    acc.s[1] = fma(Pr[1], a1, acc.s[1]);
+  }
+}
+
 // Whether the item's pass runs through the TMA pipeline.
+template <int kFeat>
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
+  if (alpha64_tma<kFeat>(I, S)) return true;
   if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
   if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
   if (!I.tma_mask) return false;
@@ -2979,6 +3064,7 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
 // Rows per chunk of the item's TMA pass.
 __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
+  if (S.pass == P_GP_ALPHA) return GeoA64::CH;  // the staged FP64 alpha0 pass
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
   if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
@@ -3055,6 +3141,8 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
   }
   if (gp) {
     issue_gp(I, S, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_GP_ALPHA) {
+    if constexpr ((kFeat & FEAT_F64) != 0) issue_alpha64(I, S, c.x0, c.yc, st, bar);
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {
       if (S.cg32) issue_cgt<float>(I, S.pcur, c.x0, c.yc, st, bar);
@@ -3093,6 +3181,8 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
         trial32a_chunk(I, st, c.x0, c.yc, c.rows, al, fbits, I.x32[cur ^ 1], I.g32[cur ^ 1],
                        I.pg32[cur ^ 1], I.mask[cur ^ 1], acc, ffs);
     }
+  } else if (S.pass == P_GP_ALPHA) {
+    if constexpr ((kFeat & FEAT_F64) != 0) alpha64_chunk(I, st, c.x0, c.yc, c.rows, acc);
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {
       const int q = S.pcur ^ 1;
@@ -3417,7 +3507,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
     FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const int grp = tr.y;
-    const bool tma = tma_pass(I, S);
+    const bool tma = tma_pass<kFeat>(I, S);
     if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
       if constexpr ((kFeat & FEAT_EXT) != 0) {
         // compact passes of the explicit reduced system: the group is a
@@ -3467,7 +3557,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       // chunks that write to their stage (and have block barriers inside)
       const bool writes_stage =
           gp ? trial_alpha0(S)
-             : (S.pass == P_CG_B ||
+             : (S.pass == P_CG_B || S.pass == P_GP_ALPHA ||
                 (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
       Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
