@@ -442,15 +442,16 @@ static bool make_tile_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   return true;
 }
 
-// Encode the FP64 alpha0 pass's maps: halo boxes 68 x 10 of x[2], g[2], l, u.
+// Encode the staged FP64 GP passes' maps: halo boxes 68 x 10 of x[2], g[2], l,
+// u, w; b as 64 x 8.
 static bool make_f64gp_maps(gpcg_problem* p, cudaStream_t s) {
   if (!have_encode() || p->dim != 2) return false;
   DevInst& I = p->inst;
-  const void* src[6] = {I.x[0], I.x[1], I.g[0], I.g[1], I.l, I.u};
-  CUtensorMap m[6];
-  static_assert(MF_U - MF_X0 == 5, "six FP64 alpha0 maps");
-  for (int k = 0; k < 6; ++k)
-    if (!encode_map(&m[k], false, src[k], p, 68, 10)) return false;
+  const void* src[8] = {I.x[0], I.x[1], I.g[0], I.g[1], I.l, I.u, I.w64, I.b};
+  CUtensorMap m[8];
+  static_assert(MF_B - MF_X0 == 7, "eight FP64 GP maps");
+  for (int k = 0; k < 8; ++k)
+    if (!encode_map(&m[k], false, src[k], p, k < 7 ? 68 : 64, k < 7 ? 10 : 8)) return false;
   char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MF_X0;
   if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -3047,11 +3047,136 @@ __device__ __forceinline__ void alpha64_chunk(const DevInst& I, unsigned char* s
   }
 }
 
+// P_TRIAL in FP64 (FEAT_F64 kernels, 2-D; along -g, or along an FP64 w):
+// the trial of OpTrial on 8-row chunks.  Stage layout: X | L | U | DH (g, or
+// w) | GH (g, along w) FP64 halo boxes 68 x 10 from (x0-2, y-1) | B 64 x 8 |
+// D 64 x 8 | CX 66 x 8 from x0-2 | CY 64 x 9 from y-1.  xt = P[x + alpha d]
+// is formed once per staged element, in place of the direction, with <g, s>
+// summed first at the chunk's points; then each warp forms gt = A xt + b,
+// the status of xt, the sums and the outputs of its row.
+struct GeoT64 {
+  static constexpr int CH = 8, H = 2, BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * 8), SZ_I = 64 * CH * 8;
+  static constexpr int OFF_X = 0, OFF_L = SZ_H, OFF_U = 2 * SZ_H, OFF_DH = 3 * SZ_H;
+  static constexpr int OFF_GH = 4 * SZ_H, OFF_B = 5 * SZ_H, OFF_D = OFF_B + SZ_I;
+  static constexpr int OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 8);
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 8);
+  static constexpr unsigned TX_H = (CH + 2) * BW * 8;
+  static constexpr unsigned TX_REST = (2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * 8;
+};
+static_assert(GeoT64::END <= kOffMask && GeoT64::CH == kWarps, "stage layout (one row per warp)");
+
+template <int kFeat>
+__device__ __forceinline__ bool trial64_tma(const DevInst& I, const Snap& S) {
+  return (kFeat & FEAT_F64) != 0 && S.pass == P_TRIAL && !S.gp32 && S.dir != D_W32 &&
+         I.dim == 2 && I.tma_f64gp && I.tma64;
+}
+
+__device__ __forceinline__ void issue_trial64(const DevInst& I, const Snap& S, int x0, int yc,
+                                              unsigned st, unsigned bar) {
+  using G = GeoT64;
+  const int cur = S.cur;
+  const bool along_w = S.dir == D_W64;
+  mbar_expect(bar, (along_w ? 5u : 4u) * G::TX_H + G::TX_REST);
+  tma_load2d(st + G::OFF_X, tmap(I, MF_X0 + cur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_L, tmap(I, MF_L), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_U, tmap(I, MF_U), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_DH, tmap(I, along_w ? MF_W : MF_G0 + cur), x0 - G::H, yc - 1, bar);
+  if (along_w) tma_load2d(st + G::OFF_GH, tmap(I, MF_G0 + cur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_B, tmap(I, MF_B), x0, yc, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M64_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M64_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M64_FCY), x0, yc - 1, bar);
+}
+
+template <int DK>
+__device__ __forceinline__ void trial64_chunk(const DevInst& I, unsigned char* st, int x0, int yc,
+                                              int rows, double alpha, double* xt_out,
+                                              double* gt_out, unsigned* m_out,
+                                              const unsigned* m_old, Acc& acc) {
+  using G = GeoT64;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* X = reinterpret_cast<const double*>(st + G::OFF_X);
+  const double* L = reinterpret_cast<const double*>(st + G::OFF_L);
+  const double* U = reinterpret_cast<const double*>(st + G::OFF_U);
+  double* XT = reinterpret_cast<double*>(st + G::OFF_DH);  // direction, then xt
+  const double* GH = reinterpret_cast<const double*>(st + (DK == D_W64 ? G::OFF_GH : G::OFF_DH));
+  const double* B = reinterpret_cast<const double*>(st + G::OFF_B);
+  const double* D = reinterpret_cast<const double*>(st + G::OFF_D);
+  const double* CX = reinterpret_cast<const double*>(st + G::OFF_CX);
+  const double* CY = reinterpret_cast<const double*>(st + G::OFF_CY);
+  const int ylim = min(rows, I.ny - yc);
+  // xt on the box (zeros outside the grid give xt = 0); <g, s> at the chunk's points
+  double s_gs = 0.0;
+  for (int e = tid; e < (G::CH + 2) * G::BW; e += kThreads) {
+    const int br = e / G::BW, bc = e - br * G::BW;
+    const int r = br - 1, j = bc - G::H;
+    const double x = X[e], g = GH[e];
+    const double d = DK == D_W64 ? XT[e] : -g;
+    const double xt = mid3(L[e], U[e], fma(alpha, d, x));
+    if (r >= 0 && r < ylim && j >= 0 && j < 64 && x0 + j < I.nx) s_gs = fma(g, xt - x, s_gs);
+    XT[e] = xt;
+  }
+  acc.s[0] += s_gs;
+  __syncthreads();
+  const int ry = warp;
+  if (ry >= ylim) return;  // warp-uniform
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const int b = (ry + 1) * G::BW + G::H + c;
+  const double* Pr = XT + b;
+  const double* Dr = D + ry * 64 + c;
+  const double* Xr = CX + ry * (64 + G::H) + G::H + c;
+  const double* Ys = CY + ry * 64 + c;
+  const double* Yn = CY + (ry + 1) * 64 + c;
+  // diag, west, east, south, north (the order of the register sweep)
+  double a[2];
+  a[0] = Dr[0] * Pr[0];
+  a[0] = fma(Xr[-1], Pr[-1], a[0]);
+  a[0] = fma(Xr[0], Pr[1], a[0]);
+  a[0] = fma(Ys[0], Pr[-G::BW], a[0]);
+  a[0] = fma(Yn[0], Pr[G::BW], a[0]);
+  a[1] = Dr[1] * Pr[1];
+  a[1] = fma(Xr[0], Pr[0], a[1]);
+  a[1] = fma(Xr[1], Pr[2], a[1]);
+  a[1] = fma(Ys[1], Pr[1 - G::BW], a[1]);
+  a[1] = fma(Yn[1], Pr[G::BW + 1], a[1]);
+  bool fr[2];
+  double gt[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool ok = k == 0 ? v0 : v1;
+    const int e = b + k;
+    const double v = Pr[k];
+    gt[k] = a[k] + B[ry * 64 + c + k];
+    const bool al = deq(v, L[e]), au = deq(v, U[e]);
+    const bool act = al || au;
+    const bool bind = (al && dge0(gt[k])) || (au && dle0(gt[k]));
+    fr[k] = ok && !act;
+    if (ok) {
+      const double sk = v - X[e];
+      acc.s[1] = fma(sk, gt[k], acc.s[1]);
+      const double pg = pg_comp(v, gt[k], L[e], U[e]);
+      acc.s[2] = fma(pg, pg, acc.s[2]);
+      acc.c[0] += act;
+      acc.c[1] += bind;
+    }
+  }
+  const long long i = (long long)(yc + ry) * I.px + e0;
+  if (v0) {
+    st2(xt_out, i, v0, v1, Pr[0], Pr[1]);
+    st2(gt_out, i, v0, v1, gt[0], gt[1]);
+  }
+  acc.c[2] += write_mask(I, m_out, m_old, yc + ry, 0, x0, lane, fr[0], fr[1]);
+}
+
 // Whether the item's pass runs through the TMA pipeline.
 template <int kFeat>
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
-  if (alpha64_tma<kFeat>(I, S)) return true;
+  if (alpha64_tma<kFeat>(I, S) || trial64_tma<kFeat>(I, S)) return true;
   if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
   if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
   if (!I.tma_mask) return false;
@@ -3064,7 +3189,8 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
 // Rows per chunk of the item's TMA pass.
 __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
-  if (S.pass == P_GP_ALPHA) return GeoA64::CH;  // the staged FP64 alpha0 pass
+  if (S.pass == P_GP_ALPHA) return GeoA64::CH;  // the staged FP64 GP passes
+  if (S.pass == P_TRIAL) return GeoT64::CH;
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
   if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
@@ -3143,6 +3269,8 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
     issue_gp(I, S, c.x0, c.yc, st, bar);
   } else if (S.pass == P_GP_ALPHA) {
     if constexpr ((kFeat & FEAT_F64) != 0) issue_alpha64(I, S, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_TRIAL) {
+    if constexpr ((kFeat & FEAT_F64) != 0) issue_trial64(I, S, c.x0, c.yc, st, bar);
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {
       if (S.cg32) issue_cgt<float>(I, S.pcur, c.x0, c.yc, st, bar);
@@ -3183,6 +3311,16 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
     }
   } else if (S.pass == P_GP_ALPHA) {
     if constexpr ((kFeat & FEAT_F64) != 0) alpha64_chunk(I, st, c.x0, c.yc, c.rows, acc);
+  } else if (S.pass == P_TRIAL) {
+    if constexpr ((kFeat & FEAT_F64) != 0) {
+      const double al = S.dir == D_ZERO ? 0.0 : S.alpha;
+      if (S.dir == D_W64)
+        trial64_chunk<D_W64>(I, st, c.x0, c.yc, c.rows, al, I.x[cur ^ 1], I.g[cur ^ 1],
+                             I.mask[cur ^ 1], I.mask[cur], acc);
+      else
+        trial64_chunk<D_NEG_G>(I, st, c.x0, c.yc, c.rows, al, I.x[cur ^ 1], I.g[cur ^ 1],
+                               I.mask[cur ^ 1], I.mask[cur], acc);
+    }
   } else if (S.pass == P_CG_F && I.opt.precond == PC_TILE) {
     if constexpr ((kFeat & FEAT_TILE) != 0) {
       const int q = S.pcur ^ 1;
@@ -3557,7 +3695,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       // chunks that write to their stage (and have block barriers inside)
       const bool writes_stage =
           gp ? trial_alpha0(S)
-             : (S.pass == P_CG_B || S.pass == P_GP_ALPHA ||
+             : (S.pass == P_CG_B || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
                 (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
       const long long n_strips = (long long)I.n_tiles * (kTY / 8);
       Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
