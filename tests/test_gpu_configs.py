@@ -179,3 +179,28 @@ def test_serving_budget_and_cancel():
         srv.stats(t2)
     assert e.value.status == g.ERR_CANCELLED
     srv.close()
+
+
+@pytest.mark.parametrize("opt", [dict(precond=1), dict(precond=2), dict(cg_system=1),
+                                 dict(precision=0)])
+def test_serving_with_options_same_alone_and_in_the_mix(opt):
+    """The server runs the options' own pass kernel (point Jacobi, the tile
+    preconditioner, the explicit reduced system, FP64): each result equals the
+    same QP solved alone, bit for bit."""
+    qps = [gi.grid_qp_2d(nx, ny, seed=600 + k, shift=1e-2, bounds="two_sided")
+           for k, (nx, ny) in enumerate([(200, 150), (64, 64), (300, 90), (130, 70), (70, 300)])]
+    base = dict(tau_rel=1e-6, precision=g.MIXED)
+    base.update(opt)
+    opts = g.default_options(**base)
+    srv = g.Server(hbm_budget=1 << 30, max_live=3, opts=opts)
+    tickets = [srv.submit(qp) for qp in qps]
+    while any(not srv.done(t) for t in tickets):
+        srv.step(16)
+    for qp, tk in zip(qps, tickets):
+        st, _ = srv.stats(tk)
+        assert st["status"] == 0
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, opts)
+        xa, _ = g.gpcg_result(prob)
+        assert np.array_equal(xa, tk.x)
+    srv.close()
