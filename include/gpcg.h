@@ -85,6 +85,16 @@ gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b, const do
                                 const double* u, double c, gpcg_problem** out);
 
 /* Release every resource of the handle (NULL is allowed). */
+/* Replace the data of a problem by a QP of the same grid (A->dim, nx, ny, nz
+ * equal to the problem's): the bands, b, l, u and c, with the same meaning,
+ * checks and error statuses as gpcg_problem_create (on an error the
+ * problem's data are undefined until the next successful update).  The
+ * problem keeps its device memory, tensor maps and launch graphs, so a
+ * stream of QPs of one shape pays for the copies of its data and nothing
+ * else.  gpcg_result reports GPCG_ERR_PENDING until the next solve. */
+gpcg_status gpcg_problem_update(gpcg_problem* p, const gpcg_stencil* A, const double* b,
+                                const double* l, const double* u, double c);
+
 void gpcg_problem_destroy(gpcg_problem* p);
 
 /* Problem size n = nx*ny*nz (0 for NULL). */

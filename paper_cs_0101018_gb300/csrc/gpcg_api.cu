@@ -464,6 +464,20 @@ static bool tma_disabled() {
   return e && *e && *e != '0';
 }
 
+// The FP32 copies of the bands, b, l, u and 1/diag in the mixed arena.
+static gpcg_status convert32(gpcg_problem* p, cudaStream_t s) {
+  DevInst& I = p->inst;
+  CK(launch_to_float(I.b, (float*)I.b32, p->pn, s));
+  CK(launch_to_float(I.l, (float*)I.l32, p->pn, s));
+  CK(launch_to_float(I.u, (float*)I.u32, p->pn, s));
+  CK(launch_to_float(I.diag, (float*)I.diag32, p->pn, s));
+  CK(launch_to_float(I.cx, (float*)I.cx32, p->pn, s));
+  CK(launch_to_float(I.cy, (float*)I.cy32, p->pn, s));
+  if (I.cz32) CK(launch_to_float(I.cz, (float*)I.cz32, p->pn, s));
+  CK(launch_recip(I.diag, nullptr, (float*)I.dinv32, p->pn, s));
+  return GPCG_OK;
+}
+
 static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   if (p->arena32) return GPCG_OK;
   const size_t bytes = arena32_bytes(p);
@@ -493,22 +507,16 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   float* l32 = take();
   float* u32 = take();
   for (int k = 0; k < 2; ++k) I.pg32[k] = take();
-  CK(launch_to_float(I.b, b32, p->pn, s));
-  CK(launch_to_float(I.l, l32, p->pn, s));
-  CK(launch_to_float(I.u, u32, p->pn, s));
   I.b32 = b32;
   I.l32 = l32;
   I.u32 = u32;
-  CK(launch_to_float(I.diag, d32, p->pn, s));
-  CK(launch_to_float(I.cx, x32, p->pn, s));
-  CK(launch_to_float(I.cy, y32, p->pn, s));
-  if (z32) CK(launch_to_float(I.cz, z32, p->pn, s));
   I.diag32 = d32;
   I.cx32 = x32;
   I.cy32 = y32;
   I.cz32 = z32;
-  CK(launch_recip(I.diag, nullptr, dinv32, p->pn, s));
   I.dinv32 = dinv32;
+  gpcg_status st = convert32(p, s);
+  if (st != GPCG_OK) return st;
   I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
   I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
@@ -609,11 +617,8 @@ static gpcg_status copy_in(const gpcg_problem* p, double* dst, const double* src
   return GPCG_OK;
 }
 
-extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b,
-                                           const double* l, const double* u, double c,
-                                           gpcg_problem** out) {
-  if (!out) return fail(GPCG_ERR_ARG, "out is NULL");
-  *out = nullptr;
+// Argument checks of a stencil problem (nothing is touched).
+static gpcg_status check_problem(const gpcg_stencil* A, const double* b, double c) {
   if (!A || !b) return fail(GPCG_ERR_ARG, "A or b is NULL");
   if (A->dim != 2 && A->dim != 3) return fail(GPCG_ERR_ARG, "dim must be 2 or 3");
   if (A->nx < 1 || A->ny < 1 || A->nz < 1) return fail(GPCG_ERR_ARG, "grid sizes must be >= 1");
@@ -624,26 +629,21 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
       A->nx * A->ny * A->nz >= (1LL << 31))
     return fail(GPCG_ERR_ARG, "problem too large (n must be below 2^31)");
   if (!std::isfinite(c)) return fail(GPCG_ERR_ARG, "c is not finite");
+  return GPCG_OK;
+}
 
-  gpcg_problem* p = new gpcg_problem();
-  geometry(A->dim, A->nx, A->ny, A->nz, p);
-  p->c = c;
-  p->bytes64 = arena64_bytes(p);
-  cudaError_t e = cudaMalloc(&p->arena64, p->bytes64);
-  if (e != cudaSuccess) {
-    const size_t bytes = p->bytes64;
-    delete p;
-    return fail(e == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
-                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-  }
-  carve64(p);
-  cudaStream_t s = 0;
+// Copy the bands, b, l and u into the problem's FP64 arrays and derive what
+// the passes read from them (couplings beyond the grid cleared, default
+// bounds, 1/diag; the FP32 copies when the mixed arena exists), checking the
+// values on the device.
+static gpcg_status upload(gpcg_problem* p, const gpcg_stencil* A, const double* b,
+                          const double* l, const double* u, cudaStream_t s) {
+  DevInst& I = p->inst;
   gpcg_status st = GPCG_OK;
+  cudaError_t e = cudaSuccess;
   int* d_flags = nullptr;
   int h_flags = 0;
-  DevInst& I = p->inst;
   do {
-    if ((e = cudaMemsetAsync(p->arena64, 0, p->bytes64, s)) != cudaSuccess) break;
     if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) break;
     if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) break;
     if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) break;
@@ -657,6 +657,7 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
                          (double*)I.u, l == nullptr, u == nullptr, d_flags, s)) != cudaSuccess)
       break;
     if ((e = launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s)) != cudaSuccess) break;
+    if (p->arena32 && (st = convert32(p, s)) != GPCG_OK) break;
     if ((e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
       break;
@@ -670,6 +671,32 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
     else if (h_flags & 2) st = fail(GPCG_ERR_ARG, "diagonal entry <= 0 or not finite");
     else st = fail(GPCG_ERR_INFEASIBLE, "empty box: some l > u, l = +inf or u = -inf");
   }
+  return st;
+}
+
+extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b,
+                                           const double* l, const double* u, double c,
+                                           gpcg_problem** out) {
+  if (!out) return fail(GPCG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  gpcg_status st = check_problem(A, b, c);
+  if (st != GPCG_OK) return st;
+  gpcg_problem* p = new gpcg_problem();
+  geometry(A->dim, A->nx, A->ny, A->nz, p);
+  p->c = c;
+  p->bytes64 = arena64_bytes(p);
+  cudaError_t e = cudaMalloc(&p->arena64, p->bytes64);
+  if (e != cudaSuccess) {
+    const size_t bytes = p->bytes64;
+    delete p;
+    return fail(e == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
+                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  carve64(p);
+  cudaStream_t s = 0;
+  e = cudaMemsetAsync(p->arena64, 0, p->bytes64, s);
+  if (e != cudaSuccess) st = fail(GPCG_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  if (st == GPCG_OK) st = upload(p, A, b, l, u, s);
   if (st != GPCG_OK) {
     delete p;
     return st;
@@ -678,6 +705,20 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
   p->inst.tma64 = (p->inst.tma_mask && make_maps(p, false, s)) ? 1 : 0;
   p->inst.tma_f64gp = (p->inst.tma64 && make_f64gp_maps(p, s)) ? 1 : 0;
   *out = p;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_problem_update(gpcg_problem* p, const gpcg_stencil* A,
+                                           const double* b, const double* l, const double* u,
+                                           double c) {
+  if (!p) return fail(GPCG_ERR_ARG, "problem is NULL");
+  gpcg_status st = check_problem(A, b, c);
+  if (st != GPCG_OK) return st;
+  if (A->dim != p->dim || A->nx != p->nx || A->ny != p->ny || A->nz != p->nz)
+    return fail(GPCG_ERR_ARG, "the update's grid differs from the problem's");
+  p->have = false;  // the previous result belongs to the old data
+  if ((st = upload(p, A, b, l, u, 0)) != GPCG_OK) return st;
+  p->c = c;
   return GPCG_OK;
 }
 

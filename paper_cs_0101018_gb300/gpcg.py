@@ -69,6 +69,8 @@ _lib = None
 _SIGNATURES = [
     ("gpcg_problem_create", C.c_int, [C.POINTER(gpcg_stencil), C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_double, C.POINTER(C.c_void_p)]),
+    ("gpcg_problem_update", C.c_int, [C.c_void_p, C.POINTER(gpcg_stencil), C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_double]),
     ("gpcg_problem_destroy", None, [C.c_void_p]),
     ("gpcg_problem_size", C.c_int64, [C.c_void_p]),
     ("gpcg_default_options", None, [C.POINTER(gpcg_options)]),
@@ -171,10 +173,11 @@ def default_options(**kw) -> gpcg_options:
 class Problem:
     """A gpcg_problem handle plus the host/device arrays it was made from."""
 
-    def __init__(self, handle, n, shape):
+    def __init__(self, handle, n, shape, dim=2):
         self.handle = handle
         self.n = n
         self.shape = shape
+        self.dim = dim
 
     def __del__(self):
         try:
@@ -201,7 +204,22 @@ def gpcg_problem_create(qp=None, *, dim=None, nx=None, ny=None, nz=1, diag=None,
     h = C.c_void_p()
     _check(load().gpcg_problem_create(C.byref(st), _ptr(b), _ptr(l), _ptr(u), float(c),
                                       C.byref(h)))
-    return Problem(h, nx * ny * nz, (nx, ny, nz))
+    return Problem(h, nx * ny * nz, (nx, ny, nz), dim)
+
+
+def gpcg_problem_update(prob: Problem, qp=None, *, diag=None, cx=None, cy=None, cz=None, b=None,
+                        l=None, u=None, c=0.0) -> None:
+    """Replace the problem's data by a QP of the same grid (a
+    :class:`gpcg_inputs.QP` or explicit arrays, numpy or CUDA tensors)."""
+    nx, ny, nz = prob.shape
+    dim = prob.dim
+    if qp is not None:
+        dim, nx, ny, nz = qp.dim, qp.nx, qp.ny, qp.nz
+        diag, cx, cy, cz, b, l, u, c = qp.diag, qp.cx, qp.cy, qp.cz, qp.b, qp.l, qp.u, qp.c
+    diag, cx, cy, cz, b, l, u = map(_f64, (diag, cx, cy, cz, b, l, u))
+    st = _stencil(dim, nx, ny, nz, diag, cx, cy, cz)
+    _check(load().gpcg_problem_update(prob.handle, C.byref(st), _ptr(b), _ptr(l), _ptr(u),
+                                      float(c)))
 
 
 def gpcg_solve(prob: Problem, opts: gpcg_options | None = None, check: bool = True) -> int:

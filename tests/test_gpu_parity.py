@@ -291,6 +291,31 @@ def test_census_counts_every_point_once(side):
         assert abs(st["pg_norm0"] - ref) <= tol * ref, (prec, st["pg_norm0"], ref)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_problem_update_equals_a_fresh_problem(prec):
+    """gpcg_problem_update replaces a problem's data by another QP of the same
+    grid: the solve equals a freshly created problem's bit for bit (and the
+    problem's derived data, the FP32 copies included, follow the new QP)."""
+    qa = gi.grid_qp_2d(130, 70, seed=540, shift=0.02, bounds="two_sided")
+    qb = gi.grid_qp_2d(130, 70, seed=541, shift=0.05, bounds="box1", sigma=1.0)
+    opts = g.default_options(tau_rel=1e-8, precision=prec)
+    prob = g.gpcg_problem_create(qa)
+    g.gpcg_solve(prob, opts)
+    g.gpcg_problem_update(prob, qb)
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_result(prob)
+    assert e.value.status == g.ERR_PENDING
+    g.gpcg_solve(prob, opts)
+    x, st = g.gpcg_result(prob)
+    fresh = g.gpcg_problem_create(qb)
+    g.gpcg_solve(fresh, opts)
+    xf, sf = g.gpcg_result(fresh)
+    assert np.array_equal(x, xf) and st["cg_iters"] == sf["cg_iters"]
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_problem_update(prob, gi.grid_qp_2d(70, 130, seed=542, shift=0.02))
+    assert e.value.status == g.ERR_ARG
+
+
 def test_tile_preconditioner_needs_a_2d_staged_problem():
     qp = gi.grid_qp_3d(17, 9, 6, seed=503, shift=0.02, sigma=0.5, bounds="box1")
     prob = g.gpcg_problem_create(qp)
