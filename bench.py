@@ -215,6 +215,140 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(g, stream, reps: int = 2) -> dict:
+    """The batched workload: 512 2-D QPs with sides uniform on {64..512}, all
+    advanced by one engine run (`gpcg_solve_batch`), mixed and FP64."""
+    import torch
+    sides = gi.batch_sides()
+    qps = [gi.batch_instance(k, s) for k, s in enumerate(sides)]
+    probs = [g.gpcg_problem_create(qp) for qp in qps]
+    out = {"instances": len(qps), "unknowns": int(sum(q.n for q in qps))}
+    del qps
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        opts = g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream)
+        g.gpcg_solve_batch(probs, opts)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gpcg_solve_batch(probs, opts)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        sts = [g.gpcg_result(p, None)[1] for p in probs]
+        t = min(ms)
+        out[name] = {"solves/s": len(probs) / (t / 1000.0), "ms_per_batch": t,
+                     "passes": int(max(st["passes"] for st in sts)),
+                     "cg_iters_total": int(sum(st["cg_iters"] for st in sts)),
+                     "all_converged": all(st["status"] == 0 for st in sts)}
+    del probs
+    return out
+
+
+def _pinned(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+def serve_trace(g, pool, reqs, opts, realtime: bool, max_live: int = 128,
+                passes: int = 16, xbufs=None) -> dict:
+    """Replays a request trace through the continuous-batching server.
+
+    realtime: each request is submitted at its arrival time (latency = server
+    latency + the wait for the host loop); otherwise requests are submitted
+    as fast as the server takes them, keeping 2 * max_live outstanding, and
+    the figure is the server's capacity (requests / makespan)."""
+    sides = {d: gi.serving_pool_sides(d) for d in (2, 3)}
+    srv = g.Server(hbm_budget=150 << 30, max_live=max_live, opts=opts)
+    lat = [0.0] * len(reqs)
+    pend = {}
+    i = finished = bad = steps = 0
+    last_counts, t_change = None, time.perf_counter()
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and (reqs[i].t_arrival <= now if realtime
+                                  else i - finished < 2 * max_live):
+            r = reqs[i]
+            qp = pool[(r.dim, gi.pool_side(r, sides[r.dim]), r.bounds)]
+            xb = None
+            if xbufs is not None:
+                free = xbufs.setdefault(qp.n, [])
+                xb = free.pop() if free else _pinned(np.empty(qp.n))
+            tk = srv.submit(qp, x_out=xb)
+            pend[tk.id] = (i, tk, r.t_arrival if realtime else 0.0, time.perf_counter() - t0)
+            i += 1
+        # one consistent snapshot: results are read back by the server's
+        # workers, so requests also finish between steps
+        q, run, f = srv.counts()
+        if (q, run, f) != last_counts:
+            last_counts, t_change = (q, run, f), time.perf_counter()
+        elif time.perf_counter() - t_change > 120.0:
+            raise RuntimeError(f"server made no progress for 120 s: queued {q}, running {run}, "
+                               f"finished {f} of {len(reqs)}")
+        if f > finished:
+            for tid in [t for t, v in pend.items() if srv.done(v[1])]:
+                k, tk, ta, ts = pend.pop(tid)
+                st, l = srv.stats(tk)
+                lat[k] = l + (ts - ta)
+                bad += st["status"] != 0
+                srv.release(tk)
+                if xbufs is not None:
+                    xbufs[tk.x.size].append(tk.x)
+            finished = f
+        if finished >= len(reqs):
+            break
+        if q + run == 0:
+            if realtime and i < len(reqs):
+                time.sleep(max(0.0, reqs[i].t_arrival - (time.perf_counter() - t0)))
+            continue
+        srv.step(passes)
+        steps += 1
+    wall = time.perf_counter() - t0
+    timing = {k: round(v, 4) for k, v in srv.timing().items()}
+    srv.close()
+    lat.sort()
+    pq = lambda q: 1000.0 * lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    return {"solves/s": len(reqs) / wall, "wall_s": wall, "p50_ms": pq(0.5), "p99_ms": pq(0.99),
+            "max_ms": 1000.0 * lat[-1], "server_steps": steps, "failed": bad,
+            "server_timing_s": timing}
+
+
+def bench_serving(g, seconds: float) -> dict:
+    """The serving workload: Poisson arrivals at 200/s, n log-uniform on
+    [1e3, 4e6], 70 % 2-D / 30 % 3-D, three bound kinds, 150 GB budget; mixed
+    and FP64, replayed in real time and queued at once (capacity)."""
+    import dataclasses
+    # requests arrive in pinned host buffers and their results go to pinned
+    # ones (recycled), as in a server that receives into registered memory
+    pool = {k: dataclasses.replace(
+        q, diag=_pinned(q.diag), cx=_pinned(q.cx), cy=_pinned(q.cy),
+        cz=_pinned(q.cz) if q.cz is not None else None, b=_pinned(q.b), l=_pinned(q.l),
+        u=_pinned(q.u)) for k, q in gi.serving_pool().items()}
+    xbufs = {}
+    for q in pool.values():
+        xbufs.setdefault(q.n, [])
+        while len(xbufs[q.n]) < 6:
+            xbufs[q.n].append(_pinned(np.empty(q.n)))
+    reqs = gi.serving_trace(duration=seconds)
+    sides = {d: gi.serving_pool_sides(d) for d in (2, 3)}
+    out = {"trace_s": seconds, "requests": len(reqs),
+           "unknowns_trace": int(sum(r.side ** r.dim for r in reqs)),
+           "unknowns_served": int(sum(gi.pool_side(r, sides[r.dim]) ** r.dim for r in reqs)),
+           "pool": "24 log-spaced sizes per dimension x 3 bound kinds; a request takes "
+                   "the pool QP of its dimension and bound kind nearest in log n",
+           "max_live": 128, "hbm_budget_GB": 150,
+           "host_buffers": "pinned (inputs and results)"}
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        opts = g.default_options(tau_rel=TAU_REL, precision=prec)
+        serve_trace(g, pool, reqs[:64], opts, realtime=False, xbufs=xbufs)  # warm-up
+        out[name] = {"realtime": serve_trace(g, pool, reqs, opts, realtime=True, xbufs=xbufs),
+                     "capacity": serve_trace(g, pool, reqs, opts, realtime=False, xbufs=xbufs)}
+    out["mixed_over_fp64_capacity"] = (out["mixed"]["capacity"]["solves/s"] /
+                                       out["fp64"]["capacity"]["solves/s"])
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -401,6 +535,9 @@ def run_ours(args):
     e2e = {"value": ws * e_steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    batched = bench_batched(g, stream) if args.serve_seconds > 0 else None
+    serving = bench_serving(g, args.serve_seconds) if args.serve_seconds > 0 else None
+
     if rank != 0:
         return
     cpu = cpu_baseline(qp) if ws == 1 else None
@@ -425,6 +562,8 @@ def run_ours(args):
         "tile": tile,
         "journal_bearing_1600": jb,
         "cg_system_1600_mixed": ablation,
+        "batched_512": batched,
+        "serving": serving,
         "roofline": roof_mx,
         "spmv": spmv,
         "solve": {k: st_mx[k] for k in ("outer_iters", "gp_iters", "cg_iters", "ls_trials",
@@ -461,21 +600,36 @@ def run_profile(args):
     torch.cuda.synchronize()
 
 
+def run_serve(args):
+    """The batched and serving workloads alone (the full 60-s trace with
+    `--serve-seconds 60`)."""
+    import torch
+    import paper_cs_0101018_gb300 as g
+    stream = torch.cuda.Stream()
+    print(json.dumps({"batched_512": bench_batched(g, stream),
+                      "serving": bench_serving(g, args.serve_seconds)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", choices=["solve", "spmv"], default=None,
+    ap.add_argument("--profile", choices=["solve", "spmv", "serve"], default=None,
                     help="run a small fixed workload for a profiler capture instead")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--precond", choices=["none", "jacobi", "tile"], default="none",
                     help="preconditioner of the CG phase (profile workloads only)")
     ap.add_argument("--side", type=int, default=1600,
                     help="grid side of the profile workloads (the benchmark QP at 1600)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the serving trace replayed (the full trace is 60 s; 0 "
+                         "skips the batched and serving workloads)")
     args = ap.parse_args()
-    if args.profile:
+    if args.profile == "serve":
+        run_serve(args)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -268,6 +268,53 @@ def serving_instance(r: Request) -> QP:
                       bounds=r.bounds, b_dist="uniform", name=f"req{r.seed}")
 
 
+def serving_pool_sides(dim: int, count: int = 24, n_lo: float = 1e3, n_hi: float = 4e6) -> np.ndarray:
+    """Grid sides of a size pool for the serving trace: n = side**dim
+    log-spaced over [n_lo, n_hi] (duplicates after rounding removed)."""
+    n = np.exp(np.linspace(math.log(n_lo), math.log(n_hi), count))
+    return np.unique(np.maximum(2, np.round(n ** (1.0 / dim)).astype(np.int64)))
+
+
+def pool_side(r: Request, sides: np.ndarray) -> int:
+    """The pool side whose n is nearest to the request's in log scale."""
+    k = int(np.argmin(np.abs(np.log(sides.astype(np.float64)) - math.log(r.side))))
+    return int(sides[k])
+
+
+def with_bounds(qp: QP, bounds: str, seed: int) -> QP:
+    """The same Hessian and b with other bounds (arrays of A and b shared)."""
+    if bounds == "lower0":
+        l, u = np.zeros(qp.n), np.full(qp.n, np.inf)
+    elif bounds == "two_sided":
+        l, u = uniform(seed, _S_L, qp.n, -0.5, 0.0), uniform(seed, _S_U, qp.n, 0.0, 0.5)
+    elif bounds == "box1":
+        l, u = np.full(qp.n, -1.0), np.full(qp.n, 1.0)
+    else:
+        raise ValueError(bounds)
+    return QP(qp.dim, qp.nx, qp.ny, qp.nz, qp.diag, qp.cx, qp.cy, qp.cz, qp.b, l, u, qp.c,
+              qp.shift, f"{qp.name}_{bounds}")
+
+
+def serving_pool(count: int = 24, seed: int = 6) -> dict:
+    """Pre-generated QPs standing in for the serving trace's requests: for each
+    dimension, the grids of :func:`serving_pool_sides` (shift 1e-2,
+    lognormal(0, 0.5) weights, b ~ U[-1,1]), each with the three bound kinds of
+    the trace.  Keys are (dim, side, bounds)."""
+    pool = {}
+    for dim in (2, 3):
+        for k, side in enumerate(serving_pool_sides(dim, count)):
+            s = int(side)
+            ps = 1000 * seed + 100 * dim + k
+            if dim == 2:
+                base = grid_qp_2d(s, s, seed=ps, shift=1e-2, bounds="box1", name=f"pool2d_{s}")
+            else:
+                base = grid_qp_3d(s, s, s, seed=ps, shift=1e-2, sigma=0.5, bounds="box1",
+                                  b_dist="uniform", name=f"pool3d_{s}")
+            for kind in ("lower0", "two_sided", "box1"):
+                pool[(dim, s, kind)] = base if kind == "box1" else with_bounds(base, kind, ps)
+    return pool
+
+
 def journal_bearing(nx: int, ny: int, eps: float, half_width: float = 10.0) -> QP:
     """The journal bearing problem of Sec. 5 as a finite-difference QP: minimise
     the integral of w_q |grad v|^2 / 2 - w_l v over D = (0, 2 pi) x (0, 2 b),

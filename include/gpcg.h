@@ -278,8 +278,11 @@ typedef struct gpcg_server gpcg_server;
 
 /* A server owns one engine whose passes advance every admitted solve in one
  * kernel launch.  Requests are admitted when their device footprint fits in
- * hbm_budget bytes (and fewer than max_live are running); finished solves are
- * retired and their memory released while others keep running.
+ * hbm_budget bytes; at most max_live run at once, and as many more may have
+ * their uploads in flight.  Finished solves are retired and their memory
+ * released while others keep running.  Four worker threads of the server,
+ * each on its own stream, copy requests in and results out while the passes
+ * run; device memory comes from the server's stream-ordered pool.
  * Errors: GPCG_ERR_ARG, GPCG_ERR_OOM, GPCG_ERR_CUDA. */
 gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const gpcg_options* opt,
                                gpcg_server** out);
@@ -292,9 +295,12 @@ gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A, const doub
                                const double* l, const double* u, double c, double* x_out,
                                int64_t* ticket);
 
-/* Advance the server: admit what fits, run up to `passes` engine passes,
- * retire what finished.  Returns after the passes (non-blocking w.r.t. new
- * submissions). */
+/* Advance the server: move finished requests out of and uploaded ones into
+ * the engine's slots, run `passes` engine passes over the running slots,
+ * admit what fits the budget (its upload starts on a worker) and hand what
+ * finished to a worker for the read-back of x.  Returns after the passes
+ * (submissions from other threads are not blocked meanwhile).  One thread at
+ * a time steps a server: a concurrent call returns GPCG_ERR_ARG. */
 gpcg_status gpcg_server_step(gpcg_server* s, int passes);
 
 /* 1 if the ticket finished (its x_out and stats are final), else 0. */
@@ -305,8 +311,17 @@ int gpcg_server_done(gpcg_server* s, int64_t ticket);
 gpcg_status gpcg_server_stats(gpcg_server* s, int64_t ticket, gpcg_stats* st,
                               double* latency_s);
 
-/* Cancel a queued or running request (its x_out is not written). */
+/* Cancel a request that has not finished.  Its x_out is not written, unless
+ * a worker was already copying its result out. */
 gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket);
+
+/* Where a server's steps spent their time so far, cumulative seconds:
+ * out[0] moving finished requests out of and uploaded ones into slots,
+ * out[1] launching the passes, out[2] reading back results, out[3] starting
+ * uploads (host side), out[4] waiting for the passes, out[5] device time of
+ * the passes (CUDA events); out[6] steps, out[7] steps that ran passes.
+ * out must hold 8 values.  Errors: GPCG_ERR_ARG. */
+gpcg_status gpcg_server_timing(gpcg_server* s, double* out);
 
 /* Counts of queued, running and finished requests. */
 void gpcg_server_counts(gpcg_server* s, int* queued, int* running, int* finished);

@@ -14,7 +14,9 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <condition_variable>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -98,6 +100,8 @@ struct Scratch {
   int cap_inst = 0;
   long long cap_tiles = 0;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;          // the graph gexec was instantiated from
+  std::vector<cudaGraphNode_t> nodes;  // its pass nodes (plain graphs: updated in place)
   long long g_tiles = -1;
   int g_mode = -1;
   int g_steps = 0;
@@ -106,14 +110,10 @@ struct Scratch {
   int g_feat = -1;         // the feature set of its pass kernel (Feature bits)
   ~Scratch() { release(); }
   void release() {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    gexec = nullptr;
-    cudaFree(d_insts);
-    cudaFree(d_ctl);
-    cudaFree(d_tiles);
-    cudaFree(d_live);
-    cudaFree(d_npass);
-    cudaFree(d_queue);
+    invalidate();
+    for (void* d : {(void*)d_insts, (void*)d_ctl, (void*)d_tiles, (void*)d_live, (void*)d_npass,
+                    (void*)d_queue})
+      if (d) cudaFree(d);
     if (h_pin) cudaFreeHost(h_pin);
     d_queue = nullptr;
     d_insts = nullptr;
@@ -155,7 +155,10 @@ struct Scratch {
   }
   void invalidate() {
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
     gexec = nullptr;
+    graph = nullptr;
+    nodes.clear();
     g_tiles = -1;
   }
 };
@@ -175,24 +178,44 @@ struct gpcg_problem {
   void* arena_x64 = nullptr;
   void* arena_x32 = nullptr;
   double* ms_buf = nullptr;  // standalone masked product: CTA partials, result, counter, flag
+  int* d_flags = nullptr;    // device-side input checks (a word in the FP64 arena)
   DevInst inst{};
   Scratch sc;
   Ctl last{};
   bool have = false;
   double lambda_min = 0.0;
   long long launches = 0;
+  // A server's problems take their arenas from its stream-ordered pool, on
+  // its side stream (no device-wide synchronisation at allocation or free).
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t pstream = nullptr;
+  CUtensorMap hmaps[M_COUNT];  // host copies of the tensor maps (their upload's source)
   ~gpcg_problem() {
     sc.release();
-    cudaFree(arena64);
-    cudaFree(arena32);
-    cudaFree(arena_t64);
-    cudaFree(arena_t32);
-    cudaFree(arena_xi);
-    cudaFree(arena_x64);
-    cudaFree(arena_x32);
-    cudaFree(ms_buf);
+    void* arenas[] = {arena64, arena32, arena_t64, arena_t32, arena_xi, arena_x64, arena_x32};
+    for (void* a : arenas)
+      if (a) {
+        if (pool) cudaFreeAsync(a, pstream);
+        else cudaFree(a);
+      }
+    if (ms_buf) cudaFree(ms_buf);
   }
 };
+
+// Device memory of a problem's arenas: from the owning server's pool when
+// there is one, else cudaMalloc.
+static cudaError_t dev_alloc(gpcg_problem* p, void** ptr, size_t bytes) {
+  if (!p->pool) return cudaMalloc(ptr, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p->pool, p->pstream);
+  // the arenas are carved in 256-byte steps for the tensor maps and vector
+  // accesses: a base off that boundary is refused
+  if (e == cudaSuccess && ((uintptr_t)*ptr & 255u) != 0) {
+    cudaFreeAsync(*ptr, p->pstream);
+    *ptr = nullptr;
+    e = cudaErrorInvalidValue;
+  }
+  return e;
+}
 
 static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_problem* p) {
   p->dim = dim;
@@ -213,13 +236,14 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
 }
 
 // Bytes of the FP64 arena: kc bands, 1/diag, b, l, u, x[2], g[2], r[2], w,
-// p[2], Ap[2], two masks and the tile partials.
+// p[2], Ap[2], two masks, the tile partials, the tensor maps and the word of
+// the input checks.
 static size_t arena64_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(double) * (size_t)p->pn);
   const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
   const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_groups);
   const size_t maps = align256(sizeof(CUtensorMap) * M_COUNT);
-  return (size_t)(p->kc + 15) * vec + 2 * msk + part + maps;
+  return (size_t)(p->kc + 15) * vec + 2 * msk + part + maps + 256;
 }
 
 // FP32 bands and 1/diag, the FP32 CG vectors r[2], w, p[2], Ap[2], and the
@@ -287,6 +311,7 @@ static void carve64(gpcg_problem* p) {
   for (int k = 0; k < 2; ++k) I.mask[k] = (unsigned*)take(msk);
   I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_groups));
   I.tmaps = take(align256(sizeof(CUtensorMap) * M_COUNT));
+  p->d_flags = (int*)take(256);
   I.tma64 = 0;
   I.tma32 = 0;
   I.tma_gp = 0;
@@ -328,6 +353,14 @@ static bool encode_map(CUtensorMap* m, bool f32, const void* base, const gpcg_pr
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Copy maps [b0, b0 + count) from the problem's host copies to its device
+// area (ordered on s; the host copies live as long as the problem).
+static bool put_maps(gpcg_problem* p, int b0, int count, cudaStream_t s) {
+  char* dst = (char*)const_cast<void*>(p->inst.tmaps) + sizeof(CUtensorMap) * b0;
+  return cudaMemcpyAsync(dst, &p->hmaps[b0], sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice,
+                         s) == cudaSuccess;
+}
+
 // Encode the maps of one precision (the box shapes of the CG stages, see the
 // kernels) and copy them to the problem's device area.  Returns false (and
 // leaves the TMA path off) when the driver cannot encode them.
@@ -347,7 +380,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
   const void* cy = f32 ? (const void*)I.cy32 : (const void*)I.cy;
   const void* w = f32 ? (const void*)I.w32 : (const void*)I.w64;
   const void* di = f32 ? (const void*)I.dinv32 : (const void*)I.dinv;
-  CUtensorMap m[kCgBase];
+  CUtensorMap* m = &p->hmaps[b0];
   CUtensorMap* q = m;
   auto e = [&](const void* base, int bw, int bh) { return encode_map(q++, f32, base, p, bw, bh); };
   const bool ok =
@@ -365,12 +398,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
       e(d, 64, f) && e(cx, 64 + h, f) && e(cy, 64, f + 1) &&
       // 1/diag: FDIH, ADI
       e(di, 64 + 2 * h, f + 2) && e(di, 64, a);
-  if (!ok || q != m + kCgBase) return false;
-  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
-  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return false;
-  return true;
+  return ok && q == m + kCgBase && put_maps(p, b0, kCgBase, s);
 }
 
 // Encode the maps of the mixed-phase gradient-projection passes (2-D only:
@@ -378,7 +406,7 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
 static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
   if (!have_encode() || p->dim != 2) return false;
   DevInst& I = p->inst;
-  CUtensorMap m[kGpMaps];
+  CUtensorMap* m = &p->hmaps[MG_X32H0];
   CUtensorMap* q = m;
   auto f32 = [&](const float* a, int bw, int bh) { return encode_map(q++, true, a, p, bw, bh); };
   bool ok = f32(I.x32[0], 72, 18) && f32(I.x32[1], 72, 18) && f32(I.l32, 72, 18) &&
@@ -389,19 +417,14 @@ static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
             f32(I.u32, 72, 20) && f32(I.g32[0], 72, 20) && f32(I.g32[1], 72, 20) &&
             f32(I.b32, 72, 18) && f32(I.diag32, 72, 18) && f32(I.cx32, 72, 18) &&
             f32(I.cy32, 72, 19);
-  if (!ok || q != m + kGpMaps) return false;
-  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MG_X32H0;
-  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return false;
-  return true;
+  return ok && q == m + kGpMaps && put_maps(p, MG_X32H0, kGpMaps, s);
 }
 
 // The free-set words as a 2-D u32 tensor (mw words x ny*nz rows), box 4 x 32.
 static bool make_mask_maps(gpcg_problem* p, cudaStream_t s) {
   if (!have_encode()) return false;
   DevInst& I = p->inst;
-  CUtensorMap m[2];
+  CUtensorMap* m = &p->hmaps[M_MASK0];
   for (int k = 0; k < 2; ++k) {
     cuuint64_t dims[2] = {(cuuint64_t)p->mw, (cuuint64_t)p->ny * (cuuint64_t)p->nz};
     cuuint64_t strides[1] = {(cuuint64_t)p->mw * 4};
@@ -413,11 +436,7 @@ static bool make_mask_maps(gpcg_problem* p, cudaStream_t s) {
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
-  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * M_MASK0;
-  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return false;
-  return true;
+  return put_maps(p, M_MASK0, 2, s);
 }
 
 // Encode the tile preconditioner's maps of one precision: FZH[2], FQH[2],
@@ -430,16 +449,11 @@ static bool make_tile_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
                        f32 ? (const void*)I.z32[1] : (const void*)I.z64[1],
                        f32 ? (const void*)I.q32[0] : (const void*)I.q64[0],
                        f32 ? (const void*)I.q32[1] : (const void*)I.q64[1]};
-  CUtensorMap m[kTileMaps];
   static_assert(kTileMaps == 4, "FZH[2], FQH[2]");
-  for (int k = 0; k < 4; ++k)
-    if (!encode_map(&m[k], f32, zq[k], p, 64 + 2 * h, f + 2)) return false;
   const int b0 = (f32 ? M32_RH0 : M64_RH0) + kCgBase;
-  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * b0;
-  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return false;
-  return true;
+  for (int k = 0; k < 4; ++k)
+    if (!encode_map(&p->hmaps[b0 + k], f32, zq[k], p, 64 + 2 * h, f + 2)) return false;
+  return put_maps(p, b0, kTileMaps, s);
 }
 
 // Encode the staged FP64 GP passes' maps: halo boxes 68 x 10 of x[2], g[2], l,
@@ -448,15 +462,11 @@ static bool make_f64gp_maps(gpcg_problem* p, cudaStream_t s) {
   if (!have_encode() || p->dim != 2) return false;
   DevInst& I = p->inst;
   const void* src[8] = {I.x[0], I.x[1], I.g[0], I.g[1], I.l, I.u, I.w64, I.b};
-  CUtensorMap m[8];
   static_assert(MF_B - MF_X0 == 7, "eight FP64 GP maps");
   for (int k = 0; k < 8; ++k)
-    if (!encode_map(&m[k], false, src[k], p, k < 7 ? 68 : 64, k < 7 ? 10 : 8)) return false;
-  char* dst = (char*)const_cast<void*>(I.tmaps) + sizeof(CUtensorMap) * MF_X0;
-  if (cudaMemcpyAsync(dst, m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return false;
-  return true;
+    if (!encode_map(&p->hmaps[MF_X0 + k], false, src[k], p, k < 7 ? 68 : 64, k < 7 ? 10 : 8))
+      return false;
+  return put_maps(p, MF_X0, 8, s);
 }
 
 static bool tma_disabled() {
@@ -478,11 +488,13 @@ static gpcg_status convert32(gpcg_problem* p, cudaStream_t s) {
   return GPCG_OK;
 }
 
-static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
+// init: zero the arena and fill the FP32 copies here (else device_init does,
+// on the stream of the first solve).
+static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s, bool init) {
   if (p->arena32) return GPCG_OK;
   const size_t bytes = arena32_bytes(p);
-  CK(cudaMalloc(&p->arena32, bytes));
-  CK(cudaMemsetAsync(p->arena32, 0, bytes, s));
+  CK(dev_alloc(p, &p->arena32, bytes));
+  if (init) CK(cudaMemsetAsync(p->arena32, 0, bytes, s));
   p->bytes32 = bytes;
   char* a = (char*)p->arena32;
   const size_t vec = align256(sizeof(float) * (size_t)p->pn);
@@ -515,8 +527,10 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
   I.cy32 = y32;
   I.cz32 = z32;
   I.dinv32 = dinv32;
-  gpcg_status st = convert32(p, s);
-  if (st != GPCG_OK) return st;
+  if (init) {
+    gpcg_status st = convert32(p, s);
+    if (st != GPCG_OK) return st;
+  }
   I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
   I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
@@ -526,7 +540,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s) {
 // solve (FP64 always; FP32 too in mixed precision), made on first use.  The
 // vectors start at zero and stay finite: the first fused step of a phase
 // multiplies them by alpha = beta = 0.
-static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s) {
+static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s, bool init) {
   DevInst& I = p->inst;
   if (p->dim != 2)
     return fail(GPCG_ERR_ARG, "the tile preconditioner is for 2-D problems only");
@@ -536,8 +550,8 @@ static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s) {
     void*& a = f32 ? p->arena_t32 : p->arena_t64;
     if (a) continue;
     const size_t bytes = arena_tile_bytes(p, f32);
-    CK(cudaMalloc(&a, bytes));
-    CK(cudaMemsetAsync(a, 0, bytes, s));
+    CK(dev_alloc(p, &a, bytes));
+    if (init) CK(cudaMemsetAsync(a, 0, bytes, s));
     const size_t vec = bytes / 4;
     char* c = (char*)a;
     for (int k = 0; k < 2; ++k) {
@@ -558,14 +572,14 @@ static gpcg_status ensure_tile(gpcg_problem* p, bool mixed, cudaStream_t s) {
 
 // The explicit reduced system's arrays for the CG precisions of a solve,
 // made on first use.
-static gpcg_status ensure_extract(gpcg_problem* p, bool mixed, cudaStream_t s) {
+static gpcg_status ensure_extract(gpcg_problem* p, bool mixed, cudaStream_t s, bool init) {
   DevInst& I = p->inst;
   if (p->pn >= (1LL << 31))
     return fail(GPCG_ERR_ARG, "the explicit reduced system needs fewer than 2^31 points");
   if (!p->arena_xi) {
     const size_t bytes = arena_rx_index_bytes(p);
-    CK(cudaMalloc(&p->arena_xi, bytes));
-    CK(cudaMemsetAsync(p->arena_xi, 0, bytes, s));
+    CK(dev_alloc(p, &p->arena_xi, bytes));
+    if (init) CK(cudaMemsetAsync(p->arena_xi, 0, bytes, s));
     char* a = (char*)p->arena_xi;
     I.cidx = (int*)a;
     a += align256(sizeof(int) * (size_t)p->pn);
@@ -579,8 +593,8 @@ static gpcg_status ensure_extract(gpcg_problem* p, bool mixed, cudaStream_t s) {
     void*& arena = f32 ? p->arena_x32 : p->arena_x64;
     if (arena) continue;
     const size_t bytes = arena_rx_value_bytes(p, f32);
-    CK(cudaMalloc(&arena, bytes));
-    CK(cudaMemsetAsync(arena, 0, bytes, s));
+    CK(dev_alloc(p, &arena, bytes));
+    if (init) CK(cudaMemsetAsync(arena, 0, bytes, s));
     const size_t vec = align256((f32 ? sizeof(float) : sizeof(double)) * (size_t)p->n);
     char* a = (char*)arena;
     auto take = [&](size_t k) {
@@ -632,46 +646,137 @@ static gpcg_status check_problem(const gpcg_stencil* A, const double* b, double 
   return GPCG_OK;
 }
 
-// Copy the bands, b, l and u into the problem's FP64 arrays and derive what
-// the passes read from them (couplings beyond the grid cleared, default
-// bounds, 1/diag; the FP32 copies when the mixed arena exists), checking the
-// values on the device.
+// Enqueue on s the copies of the bands, b, l and u into the problem's FP64
+// arrays and what the passes derive from them (couplings beyond the grid
+// cleared, default bounds, 1/diag; the FP32 copies when the mixed arena
+// exists), with the device-side checks of the values, whose result word is
+// p->d_flags (see flags_status).  Nothing waits.
+static gpcg_status upload_enqueue(gpcg_problem* p, const gpcg_stencil* A, const double* b,
+                                  const double* l, const double* u, cudaStream_t s) {
+  DevInst& I = p->inst;
+  gpcg_status st;
+  if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) return st;
+  if (A->dim == 3 && (st = copy_in(p, (double*)I.cz, A->cz, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.b, b, s)) != GPCG_OK) return st;
+  if (l && (st = copy_in(p, (double*)I.l, l, s)) != GPCG_OK) return st;
+  if (u && (st = copy_in(p, (double*)I.u, u, s)) != GPCG_OK) return st;
+  CK(cudaMemsetAsync(p->d_flags, 0, sizeof(int), s));
+  CK(launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l, (double*)I.u,
+                 l == nullptr, u == nullptr, p->d_flags, s));
+  CK(launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s));
+  if (p->arena32) return convert32(p, s);
+  return GPCG_OK;
+}
+
+// Enqueue on s the copies of the bands, b, l and u into the problem's FP64
+// arrays, nothing else (copy engines only; device_init derives the rest).
+static gpcg_status upload_copies(gpcg_problem* p, const gpcg_stencil* A, const double* b,
+                                 const double* l, const double* u, cudaStream_t s) {
+  DevInst& I = p->inst;
+  gpcg_status st;
+  if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) return st;
+  if (A->dim == 3 && (st = copy_in(p, (double*)I.cz, A->cz, s)) != GPCG_OK) return st;
+  if ((st = copy_in(p, (double*)I.b, b, s)) != GPCG_OK) return st;
+  if (l && (st = copy_in(p, (double*)I.l, l, s)) != GPCG_OK) return st;
+  if (u && (st = copy_in(p, (double*)I.u, u, s)) != GPCG_OK) return st;
+  return GPCG_OK;
+}
+
+// The device-side set-up of a problem whose arenas were allocated without
+// initialisation and whose input arrays were copied in by upload_copies:
+// zero the pad columns of the input arrays, the work vectors, masks and
+// partials (not the tensor maps), then everything upload_enqueue derives
+// (default bounds, cleared couplings, checks, 1/diag, the FP32 copies) and
+// zero the optional arenas.
+static gpcg_status device_init(gpcg_problem* p, bool fill_l, bool fill_u, cudaStream_t s) {
+  DevInst& I = p->inst;
+  if (p->px > p->nx) {
+    double* in[7] = {(double*)I.diag, (double*)I.cx, (double*)I.cy, (double*)I.cz,
+                     (double*)I.b, (double*)I.l, (double*)I.u};
+    for (double* a : in)
+      if (a)
+        CK(cudaMemset2DAsync(a + p->nx, sizeof(double) * p->px, 0,
+                             sizeof(double) * (p->px - p->nx), (size_t)p->ny * p->nz, s));
+  }
+  char* w0 = (char*)I.x[0];
+  CK(cudaMemsetAsync(w0, 0, (size_t)((const char*)I.tmaps - w0), s));
+  CK(cudaMemsetAsync(p->d_flags, 0, sizeof(int), s));
+  CK(launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l, (double*)I.u,
+                 fill_l, fill_u, p->d_flags, s));
+  CK(launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s));
+  if (p->arena32) {
+    CK(cudaMemsetAsync(p->arena32, 0, p->bytes32, s));
+    gpcg_status st = convert32(p, s);
+    if (st != GPCG_OK) return st;
+  }
+  for (int f32 = 0; f32 < 2; ++f32) {
+    void* a = f32 ? p->arena_t32 : p->arena_t64;
+    if (a) CK(cudaMemsetAsync(a, 0, arena_tile_bytes(p, f32), s));
+    void* x = f32 ? p->arena_x32 : p->arena_x64;
+    if (x) CK(cudaMemsetAsync(x, 0, arena_rx_value_bytes(p, f32), s));
+  }
+  if (p->arena_xi) CK(cudaMemsetAsync(p->arena_xi, 0, arena_rx_index_bytes(p), s));
+  return GPCG_OK;
+}
+
+// The status of the device-side input checks' result word.
+static gpcg_status flags_status(int h_flags) {
+  if (!h_flags) return GPCG_OK;
+  if (h_flags & 1) return fail(GPCG_ERR_ARG, "non-finite b, coupling or NaN bound");
+  if (h_flags & 2) return fail(GPCG_ERR_ARG, "diagonal entry <= 0 or not finite");
+  return fail(GPCG_ERR_INFEASIBLE, "empty box: some l > u, l = +inf or u = -inf");
+}
+
+// upload_enqueue, then wait for it and report the checks.
 static gpcg_status upload(gpcg_problem* p, const gpcg_stencil* A, const double* b,
                           const double* l, const double* u, cudaStream_t s) {
-  DevInst& I = p->inst;
-  gpcg_status st = GPCG_OK;
-  cudaError_t e = cudaSuccess;
-  int* d_flags = nullptr;
+  gpcg_status st = upload_enqueue(p, A, b, l, u, s);
   int h_flags = 0;
-  do {
-    if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) break;
-    if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) break;
-    if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) break;
-    if (A->dim == 3 && (st = copy_in(p, (double*)I.cz, A->cz, s)) != GPCG_OK) break;
-    if ((st = copy_in(p, (double*)I.b, b, s)) != GPCG_OK) break;
-    if (l && (st = copy_in(p, (double*)I.l, l, s)) != GPCG_OK) break;
-    if (u && (st = copy_in(p, (double*)I.u, u, s)) != GPCG_OK) break;
-    if ((e = cudaMalloc(&d_flags, sizeof(int))) != cudaSuccess) break;
-    if ((e = cudaMemsetAsync(d_flags, 0, sizeof(int), s)) != cudaSuccess) break;
-    if ((e = launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l,
-                         (double*)I.u, l == nullptr, u == nullptr, d_flags, s)) != cudaSuccess)
-      break;
-    if ((e = launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s)) != cudaSuccess) break;
-    if (p->arena32 && (st = convert32(p, s)) != GPCG_OK) break;
-    if ((e = cudaMemcpyAsync(&h_flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s)) !=
-        cudaSuccess)
-      break;
-    e = cudaStreamSynchronize(s);
-  } while (0);
-  cudaFree(d_flags);
-  if (st == GPCG_OK && e != cudaSuccess)
-    st = fail(GPCG_ERR_CUDA, "problem set-up failed: %s", cudaGetErrorString(e));
-  if (st == GPCG_OK && h_flags) {
-    if (h_flags & 1) st = fail(GPCG_ERR_ARG, "non-finite b, coupling or NaN bound");
-    else if (h_flags & 2) st = fail(GPCG_ERR_ARG, "diagonal entry <= 0 or not finite");
-    else st = fail(GPCG_ERR_INFEASIBLE, "empty box: some l > u, l = +inf or u = -inf");
+  if (st == GPCG_OK) {
+    CK(cudaMemcpyAsync(&h_flags, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
   }
-  return st;
+  return st != GPCG_OK ? st : flags_status(h_flags);
+}
+
+// A problem with its FP64 arena carved (zeroed on s unless zero is false:
+// device_init then clears what the copies do not write) and nothing copied in.
+static gpcg_status new_problem(const gpcg_stencil* A, double c, cudaMemPool_t pool,
+                               cudaStream_t s, gpcg_problem** out, bool zero = true) {
+  gpcg_problem* p = new gpcg_problem();
+  geometry(A->dim, A->nx, A->ny, A->nz, p);
+  p->c = c;
+  p->pool = pool;
+  p->pstream = s;
+  p->bytes64 = arena64_bytes(p);
+  cudaError_t e = dev_alloc(p, &p->arena64, p->bytes64);
+  if (e != cudaSuccess) {
+    const size_t bytes = p->bytes64;
+    p->arena64 = nullptr;
+    delete p;
+    return fail(e == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
+                "allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  carve64(p);
+  e = zero ? cudaMemsetAsync(p->arena64, 0, p->bytes64, s) : cudaSuccess;
+  if (e != cudaSuccess) {
+    delete p;
+    return fail(GPCG_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return GPCG_OK;
+}
+
+// The TMA descriptors of the FP64 passes (the mask maps first: every staged
+// pass reads the free set through them).
+static void make_fp64_maps(gpcg_problem* p, cudaStream_t s) {
+  p->inst.tma_mask = (!tma_disabled() && make_mask_maps(p, s)) ? 1 : 0;
+  p->inst.tma64 = (p->inst.tma_mask && make_maps(p, false, s)) ? 1 : 0;
+  p->inst.tma_f64gp = (p->inst.tma64 && make_f64gp_maps(p, s)) ? 1 : 0;
 }
 
 extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b,
@@ -681,29 +786,18 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
   *out = nullptr;
   gpcg_status st = check_problem(A, b, c);
   if (st != GPCG_OK) return st;
-  gpcg_problem* p = new gpcg_problem();
-  geometry(A->dim, A->nx, A->ny, A->nz, p);
-  p->c = c;
-  p->bytes64 = arena64_bytes(p);
-  cudaError_t e = cudaMalloc(&p->arena64, p->bytes64);
-  if (e != cudaSuccess) {
-    const size_t bytes = p->bytes64;
-    delete p;
-    return fail(e == cudaErrorMemoryAllocation ? GPCG_ERR_OOM : GPCG_ERR_CUDA,
-                "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-  }
-  carve64(p);
+  gpcg_problem* p = nullptr;
   cudaStream_t s = 0;
-  e = cudaMemsetAsync(p->arena64, 0, p->bytes64, s);
-  if (e != cudaSuccess) st = fail(GPCG_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
-  if (st == GPCG_OK) st = upload(p, A, b, l, u, s);
-  if (st != GPCG_OK) {
+  if ((st = new_problem(A, c, nullptr, s, &p)) != GPCG_OK) return st;
+  if ((st = upload(p, A, b, l, u, s)) != GPCG_OK) {
     delete p;
     return st;
   }
-  p->inst.tma_mask = (!tma_disabled() && make_mask_maps(p, s)) ? 1 : 0;
-  p->inst.tma64 = (p->inst.tma_mask && make_maps(p, false, s)) ? 1 : 0;
-  p->inst.tma_f64gp = (p->inst.tma64 && make_f64gp_maps(p, s)) ? 1 : 0;
+  make_fp64_maps(p, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    delete p;
+    return fail(GPCG_ERR_CUDA, "problem set-up failed");
+  }
   *out = p;
   return GPCG_OK;
 }
@@ -822,9 +916,34 @@ static constexpr int kBody = 8;
 
 static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap,
                              int feat) {
-  if (sc.gexec && sc.g_tiles == tiles && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps) &&
-      sc.g_no_pdl == env_no_pdl() && sc.g_feat == feat)
-    return GPCG_OK;
+  const bool same = sc.gexec && sc.g_mode == mode && (mode == 0 || sc.g_steps == steps) &&
+                    sc.g_no_pdl == env_no_pdl() && sc.g_feat == feat;
+  if (same && sc.g_tiles == tiles) return GPCG_OK;
+  if (same && mode == 1 && !sc.nodes.empty()) {
+    // only the work items changed: set the pass nodes' grid and arguments in
+    // the instantiated graph (no new instantiation)
+    EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+                    sc.d_live,   sc.d_npass, sc.d_queue + 2, cap, 0ull};
+    void* kp[] = {&args};
+    cudaKernelNodeParams k;
+    memset(&k, 0, sizeof(k));
+    k.func = const_cast<void*>(pass_kernel_ptr(false, feat));
+    k.gridDim = dim3((unsigned)pass_grid((int)tiles));
+    k.blockDim = dim3(kThreads);
+    k.sharedMemBytes = kDynSmem;
+    k.kernelParams = kp;
+    bool ok = true;
+    for (cudaGraphNode_t node : sc.nodes)
+      if (cudaGraphExecKernelNodeSetParams(sc.gexec, node, &k) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+        break;
+      }
+    if (ok) {
+      sc.g_tiles = tiles;
+      return GPCG_OK;
+    }
+  }
   sc.invalidate();
   EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
                   sc.d_live,   sc.d_npass, sc.d_queue + 2, cap, 0ull};
@@ -901,6 +1020,7 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
       break;
     }
     prev = node;
+    if (mode == 1) sc.nodes.push_back(node);
   }
   if (st == GPCG_OK) {
     cudaError_t e = cudaGraphInstantiate(&sc.gexec, g, 0);
@@ -909,11 +1029,13 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
   sc.g_pdl = pdl;
   sc.g_no_pdl = env_no_pdl();
   sc.g_feat = feat;
-  cudaGraphDestroy(g);
   if (st != GPCG_OK) {
+    cudaGraphDestroy(g);
     sc.gexec = nullptr;
+    sc.nodes.clear();
     return st;
   }
+  sc.graph = g;
   sc.g_tiles = tiles;
   sc.g_mode = mode;
   sc.g_steps = steps;
@@ -962,15 +1084,18 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   return GPCG_OK;
 }
 
+// The arenas and tensor maps a solve with options o needs.  init = false
+// leaves their device-side initialisation to device_init (a server's
+// uploads: only copies run on the worker's stream).
 static gpcg_status prepare_instance(gpcg_problem* p, const gpcg_options* o, cudaStream_t s,
-                                    DevInst* out) {
+                                    DevInst* out, bool init = true) {
   gpcg_status st;
-  if (o->precision == GPCG_MIXED && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if (o->precision == GPCG_MIXED && (st = ensure_mixed(p, s, init)) != GPCG_OK) return st;
   if (o->precond == GPCG_PRECOND_TILE &&
-      (st = ensure_tile(p, o->precision == GPCG_MIXED, s)) != GPCG_OK)
+      (st = ensure_tile(p, o->precision == GPCG_MIXED, s, init)) != GPCG_OK)
     return st;
   if (o->cg_system == GPCG_CG_EXTRACTED &&
-      (st = ensure_extract(p, o->precision == GPCG_MIXED, s)) != GPCG_OK)
+      (st = ensure_extract(p, o->precision == GPCG_MIXED, s, init)) != GPCG_OK)
     return st;
   const bool use_x0 = o->x0 != nullptr;
   if (use_x0 && (st = copy_in(p, (double*)p->inst.x0, o->x0, s)) != GPCG_OK) return st;
@@ -1193,7 +1318,7 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool f32 = precision == GPCG_MIXED;
   gpcg_status st;
-  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
   uint8_t* dm = nullptr;
   double* dp = nullptr;
   double* dy = nullptr;
@@ -1297,8 +1422,8 @@ extern "C" gpcg_status gpcg_reduced_system(gpcg_problem* p, const uint8_t* free_
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool f32 = precision == GPCG_MIXED;
   gpcg_status st;
-  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
-  if ((st = ensure_extract(p, f32, s)) != GPCG_OK) return st;
+  if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
+  if ((st = ensure_extract(p, f32, s, true)) != GPCG_OK) return st;
   DevInst& I = p->inst;
   uint8_t* dm = nullptr;
   CK(cudaMalloc(&dm, (size_t)p->n));
@@ -1390,8 +1515,8 @@ extern "C" gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* fr
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool f32 = precision == GPCG_MIXED;
   gpcg_status st;
-  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
-  if ((st = ensure_tile(p, f32, s)) != GPCG_OK) return st;
+  if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
+  if ((st = ensure_tile(p, f32, s, true)) != GPCG_OK) return st;
   std::vector<void*> temps;
   auto dev_copy = [&](const void* src, size_t bytes, void** out) -> gpcg_status {
     if (is_device_ptr(src)) {
@@ -1464,7 +1589,7 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool f32 = precision == GPCG_MIXED;
   gpcg_status st;
-  if (f32 && (st = ensure_mixed(p, s)) != GPCG_OK) return st;
+  if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
   int cur = p->have ? p->last.cur : 0;
   if (!p->have) {
     // all points free, p = 1
@@ -1553,9 +1678,22 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
 }
 
 // -------------------------------------------------------------- server --
+//
+// The host thread that calls gpcg_server_step moves requests in and out of
+// the engine's slots, launches the passes of the running slots and waits for
+// them.  Worker threads, each on its own stream, do the rest while the passes
+// run: they set up the uploads of admitted requests and read back the results
+// of finished ones.  Device memory comes from a stream-ordered pool, so
+// neither allocation nor release waits for the running passes.  An upload
+// joins a free slot at the first step after it has completed (its event); a
+// finished request leaves its slot at the next step, before the launch.
 
 namespace {
-enum ReqState { R_QUEUED = 0, R_RUNNING = 1, R_DONE = 2, R_CANCELLED = 3 };
+// R_QUEUED: waiting for memory; R_STAGING: a worker sets up its upload;
+// R_UPLOADING: the set-up is enqueued, waiting for its event; R_RUNNING: in an
+// engine slot; R_RETIRING: finished, a worker reads x back; R_DONE and
+// R_CANCELLED are final.
+enum ReqState { R_QUEUED, R_STAGING, R_UPLOADING, R_RUNNING, R_RETIRING, R_DONE, R_CANCELLED };
 
 struct Req {
   int64_t ticket = 0;
@@ -1564,40 +1702,84 @@ struct Req {
   double c = 0.0;
   double* x_out = nullptr;
   int state = R_QUEUED;
+  bool cancel = false;        // cancelled while a worker held it
   gpcg_problem* prob = nullptr;
   size_t bytes = 0;
+  bool held = false;          // bytes counted against the budget
+  bool fresh = false;         // took its slot in this step (its input checks are pending)
   int slot = -1;
+  int flag = -1;              // its word among the server's pinned check words
+  cudaEvent_t ev = nullptr;   // end of its upload on a worker's stream
+  DevInst inst{};
   double t_submit = 0.0, t_done = 0.0;
   gpcg_stats st{};
+};
+
+struct Job {
+  Req* r;
+  bool upload;  // else: read back
 };
 
 double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
+
+constexpr int kServerWorkers = 4;
 }  // namespace
 
 struct gpcg_server {
   size_t budget = 0, used = 0;
   int max_live = 0;
+  int dev = 0;
   gpcg_options opt{};
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the engine's passes
+  cudaMemPool_t pool = nullptr;
+  cudaEvent_t ev_start = nullptr;  // start and end of the running step's passes
+  cudaEvent_t ev_step = nullptr;
+  double timing[8] = {};           // gpcg_server_timing
+  int* h_flags = nullptr;          // pinned: the input-check word of each upload in flight
+  Ctl* h_ctl = nullptr;            // pinned: the slots' control blocks after a step
+  std::vector<int> free_flags;
   std::mutex mu;
+  std::condition_variable cv;       // a job is queued, or stop
+  std::condition_variable idle_cv;  // a step's passes are done
+  bool stop = false, stepping = false;
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> wstreams;  // per worker: uploads, then read-backs
+  std::deque<Job> jobs;
   std::deque<Req*> queue;
-  std::vector<Req*> slots;  // running request per slot (nullptr = free)
+  std::vector<Req*> uploading;
+  std::vector<Req*> slots;  // request per slot (nullptr = free)
   std::map<int64_t, Req*> all;
   int64_t next_ticket = 1;
-  int finished = 0;
+  int finished = 0, n_staging = 0, n_retiring = 0;
   Scratch sc;
   bool dirty = true;
   long long tiles = 0;
   ~gpcg_server() {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    for (std::thread& t : workers) t.join();
+    if (stream) cudaStreamSynchronize(stream);
+    for (cudaStream_t w : wstreams) cudaStreamSynchronize(w);
     for (auto& kv : all) {
-      delete kv.second->prob;
+      delete kv.second->prob;  // pool frees, ordered on the stream of its upload
+      if (kv.second->ev) cudaEventDestroy(kv.second->ev);
       delete kv.second;
     }
+    for (cudaStream_t w : wstreams) cudaStreamSynchronize(w);
     sc.release();
+    if (pool) cudaMemPoolDestroy(pool);
+    if (h_flags) cudaFreeHost(h_flags);
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (ev_step) cudaEventDestroy(ev_step);
+    if (ev_start) cudaEventDestroy(ev_start);
     if (stream) cudaStreamDestroy(stream);
+    for (cudaStream_t w : wstreams) cudaStreamDestroy(w);
   }
 };
 
@@ -1613,6 +1795,87 @@ static size_t footprint(const gpcg_stencil* A, bool mixed, bool tile, bool extra
   return b + 4096;
 }
 
+// A request reaches a final state (server lock held): its device memory goes
+// back to the pool (ordered on the stream of its upload) and its budget share
+// and check word are released.
+static void finish(gpcg_server* s, Req* r, int state) {
+  delete r->prob;
+  r->prob = nullptr;
+  if (r->held) s->used -= r->bytes;
+  r->held = false;
+  if (r->flag >= 0) s->free_flags.push_back(r->flag);
+  r->flag = -1;
+  if (r->ev) cudaEventDestroy(r->ev);
+  r->ev = nullptr;
+  r->state = state;
+  r->t_done = now_s();
+  s->finished++;
+}
+
+// Enqueue a request's upload on stream ws (no lock held): its arenas from
+// the pool, the copies of its arrays and of the tensor maps its options need,
+// then the event that marks the end.  Only copy engines work on ws: the
+// device-side set-up (device_init) runs on the engine's stream when the
+// request takes a slot, since a step's passes hold every SM until it ends.
+static gpcg_status start_upload(gpcg_server* s, Req* r, cudaStream_t ws) {
+  gpcg_status st = new_problem(&r->A, r->c, s->pool, ws, &r->prob, false);
+  if (st != GPCG_OK) return st;
+  if ((st = upload_copies(r->prob, &r->A, r->b, r->l, r->u, ws)) != GPCG_OK) return st;
+  make_fp64_maps(r->prob, ws);
+  if ((st = prepare_instance(r->prob, &s->opt, ws, &r->inst, false)) != GPCG_OK) return st;
+  CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(r->ev, ws));
+  return GPCG_OK;
+}
+
+// Copy a finished request's x to its caller's buffer and fill its statistics
+// (no lock held; its passes are complete).
+static gpcg_status read_back(Req* r, cudaStream_t ws) {
+  gpcg_problem* p = r->prob;
+  const double* x = p->inst.x[p->last.cur];
+  CK(cudaMemcpy2DAsync(r->x_out, sizeof(double) * p->nx, x, sizeof(double) * p->px,
+                       sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault, ws));
+  CK(cudaStreamSynchronize(ws));
+  fill_stats(p, &r->st);
+  return GPCG_OK;
+}
+
+static void server_worker(gpcg_server* s, int w) {
+  cudaSetDevice(s->dev);
+  // a read-back is ordered after no upload of the same worker
+  cudaStream_t up = s->wstreams[2 * (size_t)w], down = s->wstreams[2 * (size_t)w + 1];
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv.wait(lk, [&] { return s->stop || !s->jobs.empty(); });
+    if (s->stop) return;
+    const Job j = s->jobs.front();
+    s->jobs.pop_front();
+    Req* r = j.r;
+    lk.unlock();
+    const double t0 = now_s();
+    const gpcg_status st = j.upload ? start_upload(s, r, up) : read_back(r, down);
+    if (st == GPCG_OK && j.upload && r->cancel) cudaEventSynchronize(r->ev);
+    lk.lock();
+    s->timing[j.upload ? 3 : 2] += now_s() - t0;
+    if (j.upload) {
+      s->n_staging--;
+      if (r->cancel) {
+        finish(s, r, R_CANCELLED);
+      } else if (st != GPCG_OK) {
+        r->st.status = st;
+        finish(s, r, R_DONE);
+      } else {
+        r->state = R_UPLOADING;
+        s->uploading.push_back(r);
+      }
+    } else {
+      s->n_retiring--;
+      if (st != GPCG_OK) r->st.status = st;
+      finish(s, r, r->cancel ? R_CANCELLED : R_DONE);
+    }
+  }
+}
+
 extern "C" gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const gpcg_options* opt,
                                           gpcg_server** out) {
   if (!out) return fail(GPCG_ERR_ARG, "out is NULL");
@@ -1626,15 +1889,45 @@ extern "C" gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const
   s->opt = *opt;
   s->opt.x0 = nullptr;
   s->slots.assign(max_live, nullptr);
-  cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess && (st = s->sc.ensure(max_live, 1)) != GPCG_OK) {
+  for (int k = max_live - 1; k >= 0; --k) s->free_flags.push_back(k);
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  cudaError_t e = cudaGetDevice(&s->dev);
+  props.location.id = s->dev;
+  // the passes run at the lowest stream priority and the workers' streams at
+  // the highest: an upload's few small kernels take SMs as a pass's CTAs
+  // leave instead of waiting for the end of a step
+  int lo = 0, hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, lo);
+  for (int w = 0; w < 2 * kServerWorkers && e == cudaSuccess; ++w) {
+    cudaStream_t ws = nullptr;
+    e = cudaStreamCreateWithPriority(&ws, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) s->wstreams.push_back(ws);
+  }
+  if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
+  if (e == cudaSuccess) {
+    // keep released memory in the pool (the budget bounds what it holds)
+    cuuint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_step);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_start);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_flags, sizeof(int) * max_live);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctl, sizeof(Ctl) * max_live);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(GPCG_ERR_CUDA, "server set-up: %s", cudaGetErrorString(e));
+  }
+  // the work-item table is sized for max_live instances of the largest
+  // group count, so admissions never reallocate it
+  if ((st = s->sc.ensure(max_live, (long long)max_live * kMaxGroups)) != GPCG_OK) {
     delete s;
     return st;
   }
-  if (e != cudaSuccess) {
-    delete s;
-    return fail(GPCG_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
-  }
+  for (int w = 0; w < kServerWorkers; ++w) s->workers.emplace_back(server_worker, s, w);
   *out = s;
   return GPCG_OK;
 }
@@ -1643,9 +1936,8 @@ extern "C" gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A,
                                           const double* l, const double* u, double c,
                                           double* x_out, int64_t* ticket) {
   if (!s || !A || !b || !x_out || !ticket) return fail(GPCG_ERR_ARG, "NULL argument");
-  if (A->dim != 2 && A->dim != 3) return fail(GPCG_ERR_ARG, "dim must be 2 or 3");
-  if (A->nx < 1 || A->ny < 1 || A->nz < 1 || (A->dim == 2 && A->nz != 1))
-    return fail(GPCG_ERR_ARG, "bad grid size");
+  gpcg_status st = check_problem(A, b, c);
+  if (st != GPCG_OK) return st;
   if (s->opt.precond == GPCG_PRECOND_TILE && A->dim != 2)
     return fail(GPCG_ERR_ARG, "the tile preconditioner is for 2-D problems only");
   const size_t bytes =
@@ -1678,88 +1970,152 @@ static gpcg_status server_upload_table(gpcg_server* s) {
     for (int j = 0; j < r->prob->n_groups; ++j) table.push_back(make_int2(k, j));
   }
   s->tiles = (long long)table.size();
+  s->dirty = false;
   if (s->tiles == 0) return GPCG_OK;
   gpcg_status st = s->sc.ensure(s->max_live, s->tiles);
   if (st != GPCG_OK) return st;
   CK(cudaMemcpyAsync(s->sc.d_tiles, table.data(), sizeof(int2) * table.size(),
                      cudaMemcpyHostToDevice, s->stream));
-  s->sc.invalidate();
-  s->dirty = false;
   return GPCG_OK;
 }
 
 extern "C" gpcg_status gpcg_server_step(gpcg_server* s, int passes) {
   if (!s || passes < 1) return fail(GPCG_ERR_ARG, "bad argument");
-  std::lock_guard<std::mutex> g(s->mu);
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->stepping) return fail(GPCG_ERR_ARG, "another thread is stepping this server");
   cudaStream_t st_ = s->stream;
-  // admit what fits
+  double t0 = now_s(), t1;
+  // (1) requests that finished leave their slots; completed uploads take
+  // free ones
+  for (int k = 0; k < s->max_live; ++k) {
+    Req* r = s->slots[k];
+    if (r && r->state != R_RUNNING) {
+      r->slot = -1;
+      s->slots[k] = nullptr;
+      s->dirty = true;
+    }
+  }
+  for (size_t i = 0; i < s->uploading.size();) {
+    Req* r = s->uploading[i];
+    const cudaError_t q = cudaEventQuery(r->ev);
+    if (q == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    if (q != cudaSuccess) return fail(GPCG_ERR_CUDA, "upload: %s", cudaGetErrorString(q));
+    int slot = -1;
+    for (int k = 0; k < s->max_live && slot < 0; ++k)
+      if (!s->slots[k]) slot = k;
+    if (slot < 0) break;
+    s->uploading.erase(s->uploading.begin() + (long)i);
+    gpcg_status st = device_init(r->prob, r->l == nullptr, r->u == nullptr, st_);
+    if (st != GPCG_OK) return st;
+    CK(cudaMemcpyAsync(&s->h_flags[r->flag], r->prob->d_flags, sizeof(int),
+                       cudaMemcpyDeviceToHost, st_));
+    r->fresh = true;
+    Ctl C = fresh_ctl();
+    C.gp32 = s->opt.precision == GPCG_MIXED ? 1 : 0;
+    CK(cudaMemcpyAsync(s->sc.d_insts + slot, &r->inst, sizeof(DevInst), cudaMemcpyHostToDevice,
+                       st_));
+    CK(cudaMemcpyAsync(s->sc.d_ctl + slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice, st_));
+    r->slot = slot;
+    r->state = R_RUNNING;
+    s->slots[slot] = r;
+    s->dirty = true;
+  }
+  t1 = now_s();
+  s->timing[0] += t1 - t0;
+  t0 = t1;
+  // (2) launch the passes of the running slots
+  int live = 0;
+  for (Req* r : s->slots)
+    if (r) live++;
+  bool launched = false;
+  if (live > 0) {
+    gpcg_status st = s->dirty ? server_upload_table(s) : GPCG_OK;
+    if (st != GPCG_OK) return st;
+    s->sc.h_pin[0] = live;
+    CK(cudaMemcpyAsync(s->sc.d_live, &s->sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, st_));
+    st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu, feature_set(&s->opt));
+    if (st != GPCG_OK) return st;
+    CK(cudaEventRecord(s->ev_start, st_));
+    CK(cudaGraphLaunch(s->sc.gexec, st_));
+    CK(cudaMemcpyAsync(s->h_ctl, s->sc.d_ctl, sizeof(Ctl) * s->max_live, cudaMemcpyDeviceToHost,
+                       st_));
+    CK(cudaEventRecord(s->ev_step, st_));
+    launched = true;
+  }
+  // (3) admit queued requests that fit the budget: their uploads go to the
+  // workers
   while (!s->queue.empty()) {
     Req* r = s->queue.front();
     if (r->state == R_CANCELLED) {
       s->queue.pop_front();
       continue;
     }
-    int slot = -1;
-    for (int k = 0; k < s->max_live; ++k)
-      if (!s->slots[k]) {
-        slot = k;
-        break;
-      }
-    if (slot < 0 || s->used + r->bytes > s->budget) break;
+    if (s->free_flags.empty() || s->used + r->bytes > s->budget) break;
     s->queue.pop_front();
-    gpcg_status st = gpcg_problem_create(&r->A, r->b, r->l, r->u, r->c, &r->prob);
-    if (st != GPCG_OK) {
-      r->state = R_DONE;
-      r->st.status = st;
-      r->t_done = now_s();
-      s->finished++;
-      continue;
-    }
-    DevInst I;
-    if ((st = prepare_instance(r->prob, &s->opt, st_, &I)) != GPCG_OK) return st;
-    Ctl C = fresh_ctl();
-    C.gp32 = s->opt.precision == GPCG_MIXED ? 1 : 0;
-    CK(cudaMemcpyAsync(s->sc.d_insts + slot, &I, sizeof(DevInst), cudaMemcpyHostToDevice, st_));
-    CK(cudaMemcpyAsync(s->sc.d_ctl + slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice, st_));
-    r->slot = slot;
-    r->state = R_RUNNING;
-    s->slots[slot] = r;
     s->used += r->bytes;
-    s->dirty = true;
+    r->held = true;
+    r->flag = s->free_flags.back();
+    s->free_flags.pop_back();
+    r->state = R_STAGING;
+    s->n_staging++;
+    s->jobs.push_back(Job{r, true});
+    s->cv.notify_one();
   }
-  int live = 0;
-  for (Req* r : s->slots)
-    if (r) live++;
-  if (live == 0) return GPCG_OK;
-  if (s->dirty) {
-    gpcg_status st = server_upload_table(s);
-    if (st != GPCG_OK) return st;
+  t1 = now_s();
+  s->timing[1] += t1 - t0;
+  t0 = t1;
+  if (!launched) {
+    s->timing[6] += 1.0;
+    return GPCG_OK;
   }
-  s->sc.h_pin[0] = live;
-  CK(cudaMemcpyAsync(s->sc.d_live, &s->sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, st_));
-  gpcg_status st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu, feature_set(&s->opt));
-  if (st != GPCG_OK) return st;
-  CK(cudaGraphLaunch(s->sc.gexec, st_));
-  std::vector<Ctl> ctl(s->max_live);
-  CK(cudaMemcpyAsync(ctl.data(), s->sc.d_ctl, sizeof(Ctl) * s->max_live, cudaMemcpyDeviceToHost,
-                     st_));
-  CK(cudaStreamSynchronize(st_));
+  // (4) wait for the passes (lock released: the workers post their results
+  // meanwhile); finished requests go to the workers for read-back
+  s->stepping = true;
+  lk.unlock();
+  const cudaError_t we = cudaEventSynchronize(s->ev_step);
+  lk.lock();
+  s->stepping = false;
+  s->idle_cv.notify_all();
+  if (we != cudaSuccess) return fail(GPCG_ERR_CUDA, "server step: %s", cudaGetErrorString(we));
   for (int k = 0; k < s->max_live; ++k) {
     Req* r = s->slots[k];
-    if (!r || !ctl[k].done) continue;
-    r->prob->last = ctl[k];
+    if (!r || r->state != R_RUNNING) continue;
+    if (r->fresh) {
+      // the input checks of a request that joined in this step: one that
+      // fails them ends with that status (its passes ran on its data
+      // harmlessly, every loop of the engine being bounded)
+      r->fresh = false;
+      const gpcg_status fs = flags_status(s->h_flags[r->flag]);
+      if (fs != GPCG_OK) {
+        r->st.status = fs;
+        finish(s, r, R_DONE);
+        continue;
+      }
+    }
+    if (!s->h_ctl[k].done) continue;
+    r->prob->last = s->h_ctl[k];
     r->prob->have = true;
     r->prob->lambda_min = s->opt.lambda_min;
-    gpcg_result(r->prob, r->x_out, &r->st);
-    delete r->prob;
-    r->prob = nullptr;
-    s->used -= r->bytes;
-    s->slots[k] = nullptr;
-    r->state = R_DONE;
-    r->t_done = now_s();
-    s->finished++;
-    s->dirty = true;
+    r->state = R_RETIRING;
+    s->n_retiring++;
+    s->jobs.push_back(Job{r, false});
+    s->cv.notify_one();
   }
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, s->ev_start, s->ev_step) == cudaSuccess) s->timing[5] += 1e-3 * ms;
+  s->timing[4] += now_s() - t0;
+  s->timing[6] += 1.0;
+  s->timing[7] += 1.0;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_server_timing(gpcg_server* s, double* out) {
+  if (!s || !out) return fail(GPCG_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  for (int k = 0; k < 8; ++k) out[k] = s->timing[k];
   return GPCG_OK;
 }
 
@@ -1786,14 +2142,35 @@ extern "C" gpcg_status gpcg_server_stats(gpcg_server* s, int64_t ticket, gpcg_st
 
 extern "C" gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket) {
   if (!s) return fail(GPCG_ERR_ARG, "server is NULL");
-  std::lock_guard<std::mutex> g(s->mu);
+  std::unique_lock<std::mutex> lk(s->mu);
+  // a slot's control block is rewritten only between steps
+  s->idle_cv.wait(lk, [&] { return !s->stepping; });
   auto it = s->all.find(ticket);
   if (it == s->all.end()) return fail(GPCG_ERR_ARG, "unknown ticket");
   Req* r = it->second;
-  if (r->state == R_DONE) return fail(GPCG_ERR_ARG, "ticket already finished");
-  if (r->state == R_RUNNING) {
-    // the slot is released between passes: no kernel of this request is in
-    // flight while the host holds the lock
+  if (r->state == R_DONE || r->state == R_CANCELLED || r->cancel)
+    return fail(GPCG_ERR_ARG, "ticket already finished");
+  if (r->state == R_STAGING || r->state == R_RETIRING) {
+    // a job not yet taken is dropped here; one a worker holds ends cancelled
+    for (size_t i = 0; i < s->jobs.size(); ++i)
+      if (s->jobs[i].r == r) {
+        s->jobs.erase(s->jobs.begin() + (long)i);
+        if (r->state == R_STAGING) s->n_staging--;
+        else s->n_retiring--;
+        finish(s, r, R_CANCELLED);
+        return GPCG_OK;
+      }
+    r->cancel = true;
+    return GPCG_OK;
+  }
+  if (r->state == R_UPLOADING) {
+    CK(cudaEventSynchronize(r->ev));
+    for (size_t i = 0; i < s->uploading.size(); ++i)
+      if (s->uploading[i] == r) {
+        s->uploading.erase(s->uploading.begin() + (long)i);
+        break;
+      }
+  } else if (r->state == R_RUNNING) {
     Ctl C = fresh_ctl();
     C.pass = P_NONE;
     C.done = 1;
@@ -1801,25 +2178,24 @@ extern "C" gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket) {
     CK(cudaMemcpyAsync(s->sc.d_ctl + r->slot, &C, sizeof(Ctl), cudaMemcpyHostToDevice,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
+  }
+  if (r->slot >= 0) {
     s->slots[r->slot] = nullptr;
-    s->used -= r->bytes;
-    delete r->prob;
-    r->prob = nullptr;
+    r->slot = -1;
     s->dirty = true;
   }
-  r->state = R_CANCELLED;
-  s->finished++;
+  finish(s, r, R_CANCELLED);
   return GPCG_OK;
 }
 
 extern "C" void gpcg_server_counts(gpcg_server* s, int* queued, int* running, int* finished) {
   if (!s) return;
   std::lock_guard<std::mutex> g(s->mu);
-  int q = 0, run = 0;
+  int q = s->n_staging + (int)s->uploading.size(), run = s->n_retiring;
   for (Req* r : s->queue)
     if (r->state == R_QUEUED) q++;
   for (Req* r : s->slots)
-    if (r) run++;
+    if (r && r->state == R_RUNNING) run++;
   if (queued) *queued = q;
   if (running) *running = run;
   if (finished) *finished = s->finished;
@@ -1827,7 +2203,6 @@ extern "C" void gpcg_server_counts(gpcg_server* s, int* queued, int* running, in
 
 extern "C" void gpcg_server_destroy(gpcg_server* s) {
   if (!s) return;
-  cudaStreamSynchronize(s->stream);
   delete s;
 }
 

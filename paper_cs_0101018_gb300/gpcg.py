@@ -98,6 +98,7 @@ _SIGNATURES = [
     ("gpcg_server_stats", C.c_int, [C.c_void_p, C.c_int64, C.POINTER(gpcg_stats),
                                     C.POINTER(C.c_double)]),
     ("gpcg_server_cancel", C.c_int, [C.c_void_p, C.c_int64]),
+    ("gpcg_server_timing", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     ("gpcg_server_counts", None, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                   C.POINTER(C.c_int)]),
     ("gpcg_server_destroy", None, [C.c_void_p]),
@@ -314,12 +315,17 @@ class Server:
         self.handle = h
         self.tickets = {}
 
-    def submit(self, qp) -> Ticket:
+    def submit(self, qp, x_out=None) -> Ticket:
+        """Queue a QP (host arrays; pinned ones are copied by DMA without
+        staging).  x_out: a float64 host array of n values for the solution
+        (default: a new numpy array)."""
         arrs = tuple(np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
                      for a in (qp.diag, qp.cx, qp.cy, qp.cz, qp.b, qp.l, qp.u))
         diag, cx, cy, cz, b, l, u = arrs
         st = _stencil(qp.dim, qp.nx, qp.ny, qp.nz, diag, cx, cy, cz)
-        x = np.empty(qp.n)
+        x = np.empty(qp.n) if x_out is None else x_out
+        if x.dtype != np.float64 or x.size != qp.n or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("x_out must be a contiguous float64 array of n values")
         t = C.c_int64()
         _check(load().gpcg_server_submit(self.handle, C.byref(st), _ptr(b), _ptr(l), _ptr(u),
                                          float(qp.c), _ptr(x), C.byref(t)))
@@ -339,8 +345,21 @@ class Server:
         _check(load().gpcg_server_stats(self.handle, tk.id, C.byref(st), C.byref(lat)))
         return st.as_dict(), lat.value
 
+    def release(self, tk: Ticket):
+        """Drop the binding's references to a finished ticket's arrays (its x
+        stays with the Ticket object)."""
+        self.tickets.pop(tk.id, None)
+
     def cancel(self, tk: Ticket):
         _check(load().gpcg_server_cancel(self.handle, tk.id))
+
+    def timing(self) -> dict:
+        """Cumulative seconds of the server's step phases (gpcg_server_timing)."""
+        v = (C.c_double * 8)()
+        _check(load().gpcg_server_timing(self.handle, v))
+        keys = ("admit_to_slots", "launch", "read_back", "start_uploads", "wait_passes",
+                "device_passes", "steps", "steps_with_passes")
+        return dict(zip(keys, list(v)))
 
     def counts(self):
         q, r, f = C.c_int(), C.c_int(), C.c_int()

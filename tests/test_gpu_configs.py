@@ -204,3 +204,34 @@ def test_serving_with_options_same_alone_and_in_the_mix(opt):
         xa, _ = g.gpcg_result(prob)
         assert np.array_equal(xa, tk.x)
     srv.close()
+
+
+def test_serving_input_checks_in_the_mix():
+    """A request's input checks run on the device when it takes its slot: an
+    empty box or a NaN in b ends that request with its error status, and the
+    requests served in the same steps match their solo solves bit for bit."""
+    import dataclasses
+    good = [gi.grid_qp_2d(60 + 7 * k, 50, seed=700 + k, shift=1e-2, bounds="two_sided")
+            for k in range(3)]
+    base = gi.grid_qp_2d(40, 40, seed=710, shift=1e-2, bounds="two_sided")
+    l_bad = base.l.copy()
+    l_bad[5] = base.u[5] + 0.25
+    empty_box = dataclasses.replace(base, l=l_bad)
+    b_bad = base.b.copy()
+    b_bad[7] = np.nan
+    nan_b = dataclasses.replace(base, b=b_bad)
+    qps = [good[0], empty_box, good[1], nan_b, good[2]]
+    opts = g.default_options(tau_rel=1e-6, precision=g.MIXED)
+    srv = g.Server(hbm_budget=1 << 30, max_live=4, opts=opts)
+    tickets = [srv.submit(qp) for qp in qps]
+    while any(not srv.done(t) for t in tickets):
+        srv.step(16)
+    status = [srv.stats(t)[0]["status"] for t in tickets]
+    assert status == [0, g.ERR_INFEASIBLE, 0, g.ERR_ARG, 0]
+    for qp, tk in ((good[0], tickets[0]), (good[1], tickets[2]), (good[2], tickets[4])):
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, opts)
+        xa, _ = g.gpcg_result(prob)
+        assert np.array_equal(xa, tk.x)
+    assert srv.counts() == (0, 0, len(qps))
+    srv.close()
