@@ -245,13 +245,8 @@ def bench_batched(g, stream, reps: int = 2) -> dict:
     return out
 
 
-def _pinned(a):
-    import torch
-    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-
-
 def serve_trace(g, pool, reqs, opts, realtime: bool, max_live: int = 128,
-                passes: int = 16, xbufs=None) -> dict:
+                passes: int = 16) -> dict:
     """Replays a request trace through the continuous-batching server.
 
     realtime: each request is submitted at its arrival time (latency = server
@@ -270,12 +265,7 @@ def serve_trace(g, pool, reqs, opts, realtime: bool, max_live: int = 128,
         while i < len(reqs) and (reqs[i].t_arrival <= now if realtime
                                   else i - finished < 2 * max_live):
             r = reqs[i]
-            qp = pool[(r.dim, gi.pool_side(r, sides[r.dim]), r.bounds)]
-            xb = None
-            if xbufs is not None:
-                free = xbufs.setdefault(qp.n, [])
-                xb = free.pop() if free else _pinned(np.empty(qp.n))
-            tk = srv.submit(qp, x_out=xb)
+            tk = srv.submit(pool[(r.dim, gi.pool_side(r, sides[r.dim]), r.bounds)])
             pend[tk.id] = (i, tk, r.t_arrival if realtime else 0.0, time.perf_counter() - t0)
             i += 1
         # one consistent snapshot: results are read back by the server's
@@ -293,8 +283,6 @@ def serve_trace(g, pool, reqs, opts, realtime: bool, max_live: int = 128,
                 lat[k] = l + (ts - ta)
                 bad += st["status"] != 0
                 srv.release(tk)
-                if xbufs is not None:
-                    xbufs[tk.x.size].append(tk.x)
             finished = f
         if finished >= len(reqs):
             break
@@ -318,18 +306,9 @@ def bench_serving(g, seconds: float) -> dict:
     """The serving workload: Poisson arrivals at 200/s, n log-uniform on
     [1e3, 4e6], 70 % 2-D / 30 % 3-D, three bound kinds, 150 GB budget; mixed
     and FP64, replayed in real time and queued at once (capacity)."""
-    import dataclasses
-    # requests arrive in pinned host buffers and their results go to pinned
-    # ones (recycled), as in a server that receives into registered memory
-    pool = {k: dataclasses.replace(
-        q, diag=_pinned(q.diag), cx=_pinned(q.cx), cy=_pinned(q.cy),
-        cz=_pinned(q.cz) if q.cz is not None else None, b=_pinned(q.b), l=_pinned(q.l),
-        u=_pinned(q.u)) for k, q in gi.serving_pool().items()}
-    xbufs = {}
-    for q in pool.values():
-        xbufs.setdefault(q.n, [])
-        while len(xbufs[q.n]) < 6:
-            xbufs[q.n].append(_pinned(np.empty(q.n)))
+    # requests arrive in ordinary (pageable) numpy arrays and their results
+    # go to new ones; the server's workers stage both through pinned buffers
+    pool = gi.serving_pool()
     reqs = gi.serving_trace(duration=seconds)
     sides = {d: gi.serving_pool_sides(d) for d in (2, 3)}
     out = {"trace_s": seconds, "requests": len(reqs),
@@ -338,12 +317,12 @@ def bench_serving(g, seconds: float) -> dict:
            "pool": "24 log-spaced sizes per dimension x 3 bound kinds; a request takes "
                    "the pool QP of its dimension and bound kind nearest in log n",
            "max_live": 128, "hbm_budget_GB": 150,
-           "host_buffers": "pinned (inputs and results)"}
+           "host_buffers": "numpy arrays (pageable), inputs and results"}
     for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
         opts = g.default_options(tau_rel=TAU_REL, precision=prec)
-        serve_trace(g, pool, reqs[:64], opts, realtime=False, xbufs=xbufs)  # warm-up
-        out[name] = {"realtime": serve_trace(g, pool, reqs, opts, realtime=True, xbufs=xbufs),
-                     "capacity": serve_trace(g, pool, reqs, opts, realtime=False, xbufs=xbufs)}
+        serve_trace(g, pool, reqs[:64], opts, realtime=False)  # warm-up
+        out[name] = {"realtime": serve_trace(g, pool, reqs, opts, realtime=True),
+                     "capacity": serve_trace(g, pool, reqs, opts, realtime=False)}
     out["mixed_over_fp64_capacity"] = (out["mixed"]["capacity"]["solves/s"] /
                                        out["fp64"]["capacity"]["solves/s"])
     return out

@@ -670,19 +670,104 @@ static gpcg_status upload_enqueue(gpcg_problem* p, const gpcg_stencil* A, const 
   return GPCG_OK;
 }
 
+// Pinned staging of a server worker for transfers from and to pageable host
+// memory: two buffers used in turn, each with the event of its last copy.
+// The driver's own path for pageable memory stalls while a step's passes
+// hold the GPU; staged, the CPU moves the bytes and the copy engines DMA them.
+struct Stager {
+  static constexpr size_t kBytes = 8u << 20;
+  double* buf[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int next = 0;
+  cudaError_t init() {
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t e = cudaMallocHost(&buf[k], kBytes);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  void release() {
+    for (int k = 0; k < 2; ++k) {
+      if (ev[k]) cudaEventSynchronize(ev[k]);
+      if (ev[k]) cudaEventDestroy(ev[k]);
+      if (buf[k]) cudaFreeHost(buf[k]);
+      ev[k] = nullptr;
+      buf[k] = nullptr;
+    }
+  }
+};
+
+static bool pageable(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered;
+}
+
+// rows x nx values from host src (row length nx) into the device array dst
+// (row pitch px): whole rows, padded with zeros to px, through the staging
+// buffers.
+static gpcg_status staged_in(Stager& sg, double* dst, const double* src, size_t nx, size_t px,
+                             size_t rows, cudaStream_t s) {
+  const size_t per = Stager::kBytes / (sizeof(double) * px);
+  for (size_t r0 = 0; r0 < rows; r0 += per) {
+    const size_t nr = std::min(per, rows - r0);
+    const int k = sg.next;
+    sg.next ^= 1;
+    CK(cudaEventSynchronize(sg.ev[k]));  // its previous copy has left the buffer
+    double* b = sg.buf[k];
+    for (size_t i = 0; i < nr; ++i) {
+      memcpy(b + i * px, src + (r0 + i) * nx, sizeof(double) * nx);
+      if (px > nx) memset(b + i * px + nx, 0, sizeof(double) * (px - nx));
+    }
+    CK(cudaMemcpyAsync(dst + r0 * px, b, sizeof(double) * nr * px, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(sg.ev[k], s));
+  }
+  return GPCG_OK;
+}
+
+// rows x nx values from the device array src (row pitch px) to host dst (row
+// length nx) through the staging buffers.
+static gpcg_status staged_out(Stager& sg, double* dst, const double* src, size_t nx, size_t px,
+                              size_t rows, cudaStream_t s) {
+  const size_t per = Stager::kBytes / (sizeof(double) * px);
+  for (size_t r0 = 0; r0 < rows; r0 += per) {
+    const size_t nr = std::min(per, rows - r0);
+    double* b = sg.buf[0];
+    CK(cudaEventSynchronize(sg.ev[0]));
+    CK(cudaMemcpyAsync(b, src + r0 * px, sizeof(double) * nr * px, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < nr; ++i)
+      memcpy(dst + (r0 + i) * nx, b + i * px, sizeof(double) * nx);
+  }
+  return GPCG_OK;
+}
+
+// One input array of a server's request: staged when it is pageable host
+// memory (and a whole row fits a staging buffer), else copied directly.
+static gpcg_status copy_in_served(const gpcg_problem* p, double* dst, const double* src,
+                                  cudaStream_t s, Stager* sg) {
+  if (sg && sizeof(double) * (size_t)p->px <= Stager::kBytes && pageable(src))
+    return staged_in(*sg, dst, src, (size_t)p->nx, (size_t)p->px, (size_t)p->ny * p->nz, s);
+  return copy_in(p, dst, src, s);
+}
+
 // Enqueue on s the copies of the bands, b, l and u into the problem's FP64
 // arrays, nothing else (copy engines only; device_init derives the rest).
 static gpcg_status upload_copies(gpcg_problem* p, const gpcg_stencil* A, const double* b,
-                                 const double* l, const double* u, cudaStream_t s) {
+                                 const double* l, const double* u, cudaStream_t s, Stager* sg) {
   DevInst& I = p->inst;
   gpcg_status st;
-  if ((st = copy_in(p, (double*)I.diag, A->diag, s)) != GPCG_OK) return st;
-  if ((st = copy_in(p, (double*)I.cx, A->cx, s)) != GPCG_OK) return st;
-  if ((st = copy_in(p, (double*)I.cy, A->cy, s)) != GPCG_OK) return st;
-  if (A->dim == 3 && (st = copy_in(p, (double*)I.cz, A->cz, s)) != GPCG_OK) return st;
-  if ((st = copy_in(p, (double*)I.b, b, s)) != GPCG_OK) return st;
-  if (l && (st = copy_in(p, (double*)I.l, l, s)) != GPCG_OK) return st;
-  if (u && (st = copy_in(p, (double*)I.u, u, s)) != GPCG_OK) return st;
+  if ((st = copy_in_served(p, (double*)I.diag, A->diag, s, sg)) != GPCG_OK) return st;
+  if ((st = copy_in_served(p, (double*)I.cx, A->cx, s, sg)) != GPCG_OK) return st;
+  if ((st = copy_in_served(p, (double*)I.cy, A->cy, s, sg)) != GPCG_OK) return st;
+  if (A->dim == 3 && (st = copy_in_served(p, (double*)I.cz, A->cz, s, sg)) != GPCG_OK) return st;
+  if ((st = copy_in_served(p, (double*)I.b, b, s, sg)) != GPCG_OK) return st;
+  if (l && (st = copy_in_served(p, (double*)I.l, l, s, sg)) != GPCG_OK) return st;
+  if (u && (st = copy_in_served(p, (double*)I.u, u, s, sg)) != GPCG_OK) return st;
   return GPCG_OK;
 }
 
@@ -1747,6 +1832,7 @@ struct gpcg_server {
   bool stop = false, stepping = false;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> wstreams;  // per worker: uploads, then read-backs
+  std::vector<Stager> stagers;         // per worker
   std::deque<Job> jobs;
   std::deque<Req*> queue;
   std::vector<Req*> uploading;
@@ -1772,6 +1858,7 @@ struct gpcg_server {
       delete kv.second;
     }
     for (cudaStream_t w : wstreams) cudaStreamSynchronize(w);
+    for (Stager& g : stagers) g.release();
     sc.release();
     if (pool) cudaMemPoolDestroy(pool);
     if (h_flags) cudaFreeHost(h_flags);
@@ -1817,10 +1904,10 @@ static void finish(gpcg_server* s, Req* r, int state) {
 // then the event that marks the end.  Only copy engines work on ws: the
 // device-side set-up (device_init) runs on the engine's stream when the
 // request takes a slot, since a step's passes hold every SM until it ends.
-static gpcg_status start_upload(gpcg_server* s, Req* r, cudaStream_t ws) {
+static gpcg_status start_upload(gpcg_server* s, Req* r, cudaStream_t ws, Stager* sg) {
   gpcg_status st = new_problem(&r->A, r->c, s->pool, ws, &r->prob, false);
   if (st != GPCG_OK) return st;
-  if ((st = upload_copies(r->prob, &r->A, r->b, r->l, r->u, ws)) != GPCG_OK) return st;
+  if ((st = upload_copies(r->prob, &r->A, r->b, r->l, r->u, ws, sg)) != GPCG_OK) return st;
   make_fp64_maps(r->prob, ws);
   if ((st = prepare_instance(r->prob, &s->opt, ws, &r->inst, false)) != GPCG_OK) return st;
   CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
@@ -1830,12 +1917,18 @@ static gpcg_status start_upload(gpcg_server* s, Req* r, cudaStream_t ws) {
 
 // Copy a finished request's x to its caller's buffer and fill its statistics
 // (no lock held; its passes are complete).
-static gpcg_status read_back(Req* r, cudaStream_t ws) {
+static gpcg_status read_back(Req* r, cudaStream_t ws, Stager* sg) {
   gpcg_problem* p = r->prob;
   const double* x = p->inst.x[p->last.cur];
-  CK(cudaMemcpy2DAsync(r->x_out, sizeof(double) * p->nx, x, sizeof(double) * p->px,
-                       sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault, ws));
-  CK(cudaStreamSynchronize(ws));
+  if (sizeof(double) * (size_t)p->px <= Stager::kBytes && pageable(r->x_out)) {
+    gpcg_status st = staged_out(*sg, r->x_out, x, (size_t)p->nx, (size_t)p->px,
+                                (size_t)p->ny * p->nz, ws);
+    if (st != GPCG_OK) return st;
+  } else {
+    CK(cudaMemcpy2DAsync(r->x_out, sizeof(double) * p->nx, x, sizeof(double) * p->px,
+                         sizeof(double) * p->nx, (size_t)p->ny * p->nz, cudaMemcpyDefault, ws));
+    CK(cudaStreamSynchronize(ws));
+  }
   fill_stats(p, &r->st);
   return GPCG_OK;
 }
@@ -1853,7 +1946,8 @@ static void server_worker(gpcg_server* s, int w) {
     Req* r = j.r;
     lk.unlock();
     const double t0 = now_s();
-    const gpcg_status st = j.upload ? start_upload(s, r, up) : read_back(r, down);
+    Stager* sg = &s->stagers[(size_t)w];
+    const gpcg_status st = j.upload ? start_upload(s, r, up, sg) : read_back(r, down, sg);
     if (st == GPCG_OK && j.upload && r->cancel) cudaEventSynchronize(r->ev);
     lk.lock();
     s->timing[j.upload ? 3 : 2] += now_s() - t0;
@@ -1917,6 +2011,8 @@ extern "C" gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev_start);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_flags, sizeof(int) * max_live);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctl, sizeof(Ctl) * max_live);
+  s->stagers.resize(kServerWorkers);
+  for (int w = 0; w < kServerWorkers && e == cudaSuccess; ++w) e = s->stagers[(size_t)w].init();
   if (e != cudaSuccess) {
     delete s;
     return fail(GPCG_ERR_CUDA, "server set-up: %s", cudaGetErrorString(e));
