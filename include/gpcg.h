@@ -288,9 +288,16 @@ gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const gpcg_optio
                                gpcg_server** out);
 
 /* Queue one request.  The arrays (host pointers) must stay valid until the
- * request completes; x_out (host, n values) receives the solution.  *ticket
- * identifies the request.  Errors: GPCG_ERR_ARG, GPCG_ERR_BUDGET (the request
- * alone exceeds the budget). */
+ * request completes; x_out (host, n values) receives the solution.  Page-
+ * locked arrays are copied by DMA directly, pageable ones through the
+ * workers' pinned staging buffers.  The values are checked on the device
+ * when the request takes its slot: a NaN, a non-positive diagonal or an
+ * empty box ends the request with GPCG_ERR_ARG or GPCG_ERR_INFEASIBLE (see
+ * gpcg_server_stats).  *ticket identifies the request.  Errors: GPCG_ERR_ARG,
+ * GPCG_ERR_BUDGET (the request alone exceeds the budget).
+ * A server handle is the exception to the one-thread rule: submit, done,
+ * stats, cancel, counts and timing may be called from any thread while one
+ * thread steps it. */
 gpcg_status gpcg_server_submit(gpcg_server* s, const gpcg_stencil* A, const double* b,
                                const double* l, const double* u, double c, double* x_out,
                                int64_t* ticket);

@@ -157,6 +157,9 @@ def test_serving_same_alone_and_in_the_mix():
     q, r, f = srv.counts()
     assert (q, r, f) == (0, 0, len(qps))
     assert all(l > 0 for l in lat)
+    t = srv.timing()
+    assert t["steps"] >= t["steps_with_passes"] > 0 and t["device_passes"] > 0
+    assert min(t.values()) >= 0.0
     srv.close()
 
 
