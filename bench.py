@@ -514,6 +514,55 @@ def run_ours(args):
     e2e = {"value": ws * e_steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    # the small single QP (32 x 32, tau_rel 1e-8: latency-bound) and the 3-D
+    # precision-stress QP (128^3 7-point, anisotropic): latency and solves/s,
+    # and how far the mixed result is from the FP64 one
+    small = {}
+    sq = gi.single_small()
+    sp = g.gpcg_problem_create(sq)
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        so = g.default_options(tau_rel=1e-8, precision=prec, stream=stream)
+        for _ in range(3):
+            g.gpcg_solve(sp, so)
+        ms = []
+        for _ in range(50):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gpcg_solve(sp, so)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        ms.sort()
+        _, ss = g.gpcg_result(sp)
+        small[name] = {"p50_ms": ms[len(ms) // 2], "p99_ms": ms[min(len(ms) - 1, int(0.99 * len(ms)))],
+                       "solves/s": 1000.0 * len(ms) / sum(ms), "passes": ss["passes"],
+                       "status": ss["status"]}
+    small["n"] = sq.n
+    del sp
+    stress = {}
+    cq = gi.precision_stress()
+    cp = g.gpcg_problem_create(cq)
+    xs = {}
+    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
+        co = g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream)
+        g.gpcg_solve(cp, co)
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.gpcg_solve(cp, co)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        xs[name], cs = g.gpcg_result(cp)
+        stress[name] = {"solves/s": 1000.0 * len(ms) / sum(ms), "ms": min(ms),
+                        "passes": cs["passes"], "cg_iters": cs["cg_iters"],
+                        "pg_norm": cs["pg_norm"], "tau": cs["tau"], "status": cs["status"]}
+    stress["n"] = cq.n
+    stress["mixed_vs_fp64_rel_err"] = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) /
+                                            np.linalg.norm(xs["fp64"]))
+    del cp, cq, xs
+
     batched = bench_batched(g, stream) if args.serve_seconds > 0 else None
     serving = bench_serving(g, args.serve_seconds) if args.serve_seconds > 0 else None
 
@@ -541,6 +590,8 @@ def run_ours(args):
         "tile": tile,
         "journal_bearing_1600": jb,
         "cg_system_1600_mixed": ablation,
+        "single_small_32": small,
+        "precision_stress_128": stress,
         "batched_512": batched,
         "serving": serving,
         "roofline": roof_mx,
