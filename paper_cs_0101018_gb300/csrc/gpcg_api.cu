@@ -2253,6 +2253,11 @@ extern "C" gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket) {
         s->jobs.erase(s->jobs.begin() + (long)i);
         if (r->state == R_STAGING) s->n_staging--;
         else s->n_retiring--;
+        if (r->slot >= 0) {
+          s->slots[r->slot] = nullptr;
+          r->slot = -1;
+          s->dirty = true;
+        }
         finish(s, r, R_CANCELLED);
         return GPCG_OK;
       }

@@ -265,3 +265,51 @@ def test_serving_pinned_and_pageable_buffers_give_the_same_result():
         assert b.x is o
         assert np.array_equal(a.x, b.x)
     srv.close()
+
+
+def test_serving_cancel_in_any_state_and_close_with_work_in_flight():
+    """Cancelling requests wherever they are (queued, uploading, running or
+    being read back) ends them cancelled and leaves the others exact; a
+    server closed with requests in flight shuts down cleanly."""
+    qps = [gi.grid_qp_2d(40 + 9 * k, 30 + 5 * k, seed=730 + k, shift=1e-2, bounds="two_sided")
+           for k in range(10)]
+    opts = g.default_options(tau_rel=1e-6, precision=g.MIXED)
+    srv = g.Server(hbm_budget=1 << 30, max_live=3, opts=opts)
+    tickets = [srv.submit(q) for q in qps]
+    cancelled = set()
+    for step in range(6):
+        srv.step(4)
+        k = 1 + 3 * step
+        if k < len(tickets):
+            try:
+                srv.cancel(tickets[k])
+                cancelled.add(k)
+            except g.GpcgError as e:
+                # a worker finished it first
+                assert e.value.status == g.ERR_ARG and srv.done(tickets[k])
+    while True:
+        q, r, f = srv.counts()
+        if q + r == 0:
+            break
+        srv.step(16)
+    assert f == len(qps)
+    for k, (qp, tk) in enumerate(zip(qps, tickets)):
+        if k in cancelled:
+            with pytest.raises(g.GpcgError) as e:
+                srv.stats(tk)
+            assert e.value.status == g.ERR_CANCELLED
+            continue
+        st, _ = srv.stats(tk)
+        assert st["status"] == 0
+        prob = g.gpcg_problem_create(qp)
+        g.gpcg_solve(prob, opts)
+        xa, _ = g.gpcg_result(prob)
+        assert np.array_equal(xa, tk.x)
+    srv.close()
+    # closed while requests are queued, uploading and running
+    srv = g.Server(hbm_budget=1 << 30, max_live=2, opts=opts)
+    for q in qps:
+        srv.submit(q)
+    srv.step(4)
+    srv.step(4)
+    srv.close()
