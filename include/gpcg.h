@@ -88,12 +88,27 @@ gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b, const do
 /* Replace the data of a problem by a QP of the same grid (A->dim, nx, ny, nz
  * equal to the problem's): the bands, b, l, u and c, with the same meaning,
  * checks and error statuses as gpcg_problem_create (on an error the
- * problem's data are undefined until the next successful update).  The
+ * problem's data are undefined, and solves report GPCG_ERR_ARG, until the
+ * next successful update).  The
  * problem keeps its device memory, tensor maps and launch graphs, so a
  * stream of QPs of one shape pays for the copies of its data and nothing
  * else.  gpcg_result reports GPCG_ERR_PENDING until the next solve. */
 gpcg_status gpcg_problem_update(gpcg_problem* p, const gpcg_stencil* A, const double* b,
                                 const double* l, const double* u, double c);
+
+/* gpcg_problem_update without waiting: the copies are enqueued on `stream`
+ * (a cudaStream_t; page-locked host arrays make them asynchronous) and the
+ * call returns.  The arrays must stay valid until those copies are done.
+ * The device-side set-up and the value checks run on the stream of the next
+ * call that uses the problem's data (a solve, a masked product, ...).  That
+ * call waits for the checks before it computes anything; a failed check
+ * makes it return GPCG_ERR_ARG or GPCG_ERR_INFEASIBLE, and every later call
+ * on the problem does the same until the next update.  With two problems
+ * used in turn, the next QP's copies overlap the current solve.
+ * Errors at the call: GPCG_ERR_ARG, GPCG_ERR_CUDA. */
+gpcg_status gpcg_problem_update_async(gpcg_problem* p, const gpcg_stencil* A, const double* b,
+                                      const double* l, const double* u, double c,
+                                      void* stream);
 
 void gpcg_problem_destroy(gpcg_problem* p);
 

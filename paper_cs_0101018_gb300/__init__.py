@@ -7,6 +7,7 @@ from .gpcg import (CG_EXTRACTED, CG_MASKED, ERR_ARG, ERR_BUDGET, ERR_CANCELLED, 
                    ERR_CUDA, ERR_INFEASIBLE, ERR_LINESEARCH, ERR_MAXIT, ERR_NUMERIC, ERR_OOM,
                    ERR_PENDING, ERR_TIMEOUT, FP64, MIXED, OK, PRECOND_JACOBI, PRECOND_NONE,
                    PRECOND_TILE, GpcgError, Problem, Server, default_options, gpcg_masked_spmv,
-                   gpcg_problem_create, gpcg_problem_update, gpcg_reduced_system, gpcg_result,
+                   gpcg_problem_create, gpcg_problem_update, gpcg_problem_update_async,
+                   gpcg_reduced_system, gpcg_result,
                    gpcg_solve, gpcg_solve_batch, gpcg_tile_precondition, gpcg_time_masked_spmv,
                    library_path, load)

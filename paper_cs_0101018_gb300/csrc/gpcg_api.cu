@@ -190,6 +190,12 @@ struct gpcg_problem {
   cudaMemPool_t pool = nullptr;
   cudaStream_t pstream = nullptr;
   CUtensorMap hmaps[M_COUNT];  // host copies of the tensor maps (their upload's source)
+  // gpcg_problem_update_async: its copies end at up_ev; the device-side set-up
+  // (device_init) runs on the stream of the next call that uses the data
+  cudaEvent_t up_ev = nullptr;
+  bool pending = false, fill_l = false, fill_u = false;
+  bool bad = false;        // its data failed the value checks: no solve until an update
+  int* h_flags = nullptr;  // pinned word: the input checks of that set-up
   ~gpcg_problem() {
     sc.release();
     void* arenas[] = {arena64, arena32, arena_t64, arena_t32, arena_xi, arena_x64, arena_x32};
@@ -199,6 +205,8 @@ struct gpcg_problem {
         else cudaFree(a);
       }
     if (ms_buf) cudaFree(ms_buf);
+    if (up_ev) cudaEventDestroy(up_ev);
+    if (h_flags) cudaFreeHost(h_flags);
   }
 };
 
@@ -771,15 +779,15 @@ static gpcg_status upload_copies(gpcg_problem* p, const gpcg_stencil* A, const d
   return GPCG_OK;
 }
 
-// The device-side set-up of a problem whose arenas were allocated without
-// initialisation and whose input arrays were copied in by upload_copies:
-// zero the pad columns of the input arrays, the work vectors, masks and
-// partials (not the tensor maps), then everything upload_enqueue derives
-// (default bounds, cleared couplings, checks, 1/diag, the FP32 copies) and
-// zero the optional arenas.
-static gpcg_status device_init(gpcg_problem* p, bool fill_l, bool fill_u, cudaStream_t s) {
+// The device-side set-up after upload_copies: everything upload_enqueue
+// derives (default bounds, cleared couplings, checks, 1/diag, the FP32
+// copies).  fresh: the arenas were allocated without initialisation, so
+// first zero the pad columns of the input arrays, the work vectors, masks and
+// partials (not the tensor maps), and the optional arenas.
+static gpcg_status device_init(gpcg_problem* p, bool fill_l, bool fill_u, cudaStream_t s,
+                               bool fresh = true) {
   DevInst& I = p->inst;
-  if (p->px > p->nx) {
+  if (fresh && p->px > p->nx) {
     double* in[7] = {(double*)I.diag, (double*)I.cx, (double*)I.cy, (double*)I.cz,
                      (double*)I.b, (double*)I.l, (double*)I.u};
     for (double* a : in)
@@ -788,16 +796,17 @@ static gpcg_status device_init(gpcg_problem* p, bool fill_l, bool fill_u, cudaSt
                              sizeof(double) * (p->px - p->nx), (size_t)p->ny * p->nz, s));
   }
   char* w0 = (char*)I.x[0];
-  CK(cudaMemsetAsync(w0, 0, (size_t)((const char*)I.tmaps - w0), s));
+  if (fresh) CK(cudaMemsetAsync(w0, 0, (size_t)((const char*)I.tmaps - w0), s));
   CK(cudaMemsetAsync(p->d_flags, 0, sizeof(int), s));
   CK(launch_prep(I, (double*)I.cx, (double*)I.cy, (double*)I.cz, (double*)I.l, (double*)I.u,
                  fill_l, fill_u, p->d_flags, s));
   CK(launch_recip(I.diag, (double*)I.dinv, nullptr, p->pn, s));
   if (p->arena32) {
-    CK(cudaMemsetAsync(p->arena32, 0, p->bytes32, s));
+    if (fresh) CK(cudaMemsetAsync(p->arena32, 0, p->bytes32, s));
     gpcg_status st = convert32(p, s);
     if (st != GPCG_OK) return st;
   }
+  if (!fresh) return GPCG_OK;
   for (int f32 = 0; f32 < 2; ++f32) {
     void* a = f32 ? p->arena_t32 : p->arena_t64;
     if (a) CK(cudaMemsetAsync(a, 0, arena_tile_bytes(p, f32), s));
@@ -887,6 +896,48 @@ extern "C" gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* 
   return GPCG_OK;
 }
 
+// Wait for a pending asynchronous update's copies (no device-side work).
+static gpcg_status wait_pending_copies(gpcg_problem* p) {
+  if (p->pending) CK(cudaEventSynchronize(p->up_ev));
+  return GPCG_OK;
+}
+
+// A pending asynchronous update's device-side set-up, ordered on s after its
+// copies; its input checks are read back into p->h_flags (valid once s has
+// reached this point, see settle_status).
+static gpcg_status settle(gpcg_problem* p, cudaStream_t s) {
+  if (!p->pending) return GPCG_OK;
+  p->pending = false;
+  CK(cudaStreamWaitEvent(s, p->up_ev, 0));
+  gpcg_status st = device_init(p, p->fill_l, p->fill_u, s, false);
+  if (st != GPCG_OK) return st;
+  *p->h_flags = 0;
+  CK(cudaMemcpyAsync(p->h_flags, p->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return GPCG_OK;
+}
+
+// The input checks of the last settled set-up, once its stream has been
+// synchronised (GPCG_OK when there was none).
+static gpcg_status settle_status(gpcg_problem* p) {
+  if (!p->h_flags || *p->h_flags == 0) return GPCG_OK;
+  const int f = *p->h_flags;
+  *p->h_flags = 0;
+  return flags_status(f);
+}
+
+// settle on the legacy stream, wait, and report the checks (the synchronous
+// entry points other than the solves).
+static gpcg_status settle_now(gpcg_problem* p) {
+  if (p->bad) return fail(GPCG_ERR_ARG, "the problem's data failed the value checks");
+  if (!p->pending) return GPCG_OK;
+  gpcg_status st = settle(p, 0);
+  if (st != GPCG_OK) return st;
+  CK(cudaStreamSynchronize(0));
+  st = settle_status(p);
+  p->bad = st != GPCG_OK;
+  return st;
+}
+
 extern "C" gpcg_status gpcg_problem_update(gpcg_problem* p, const gpcg_stencil* A,
                                            const double* b, const double* l, const double* u,
                                            double c) {
@@ -895,8 +946,40 @@ extern "C" gpcg_status gpcg_problem_update(gpcg_problem* p, const gpcg_stencil* 
   if (st != GPCG_OK) return st;
   if (A->dim != p->dim || A->nx != p->nx || A->ny != p->ny || A->nz != p->nz)
     return fail(GPCG_ERR_ARG, "the update's grid differs from the problem's");
+  if ((st = wait_pending_copies(p)) != GPCG_OK) return st;
+  p->pending = false;
   p->have = false;  // the previous result belongs to the old data
-  if ((st = upload(p, A, b, l, u, 0)) != GPCG_OK) return st;
+  st = upload(p, A, b, l, u, 0);
+  p->bad = st != GPCG_OK;
+  if (st != GPCG_OK) return st;
+  p->c = c;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_problem_update_async(gpcg_problem* p, const gpcg_stencil* A,
+                                                 const double* b, const double* l,
+                                                 const double* u, double c, void* stream) {
+  if (!p) return fail(GPCG_ERR_ARG, "problem is NULL");
+  gpcg_status st = check_problem(A, b, c);
+  if (st != GPCG_OK) return st;
+  if (A->dim != p->dim || A->nx != p->nx || A->ny != p->ny || A->nz != p->nz)
+    return fail(GPCG_ERR_ARG, "the update's grid differs from the problem's");
+  if ((st = wait_pending_copies(p)) != GPCG_OK) return st;
+  if (!p->up_ev) CK(cudaEventCreateWithFlags(&p->up_ev, cudaEventDisableTiming));
+  if (!p->h_flags) {
+    CK(cudaMallocHost(&p->h_flags, sizeof(int)));
+    *p->h_flags = 0;
+  }
+  // every other entry point returns with its work on p complete, so nothing
+  // in flight still reads the arrays these copies overwrite
+  cudaStream_t s = (cudaStream_t)stream;
+  p->have = false;
+  if ((st = upload_copies(p, A, b, l, u, s, nullptr)) != GPCG_OK) return st;
+  CK(cudaEventRecord(p->up_ev, s));
+  p->pending = true;
+  p->bad = false;
+  p->fill_l = l == nullptr;
+  p->fill_u = u == nullptr;
   p->c = c;
   return GPCG_OK;
 }
@@ -1213,6 +1296,23 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   std::vector<Ctl> ctl(count, c0);
   std::vector<int2> table((size_t)tiles);
   long long t = 0;
+  // pending asynchronous updates: their set-up, and their value checks
+  // before anything runs on the data
+  bool settled = false;
+  for (int k = 0; k < count; ++k) {
+    if (probs[k]->bad)
+      return fail(GPCG_ERR_ARG, "problem %d: its data failed the value checks", k);
+    settled |= probs[k]->pending;
+    if ((st = settle(probs[k], s)) != GPCG_OK) return st;
+  }
+  if (settled) {
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < count; ++k)
+      if ((st = settle_status(probs[k])) != GPCG_OK) {
+        probs[k]->bad = true;
+        return st;
+      }
+  }
   for (int k = 0; k < count; ++k) {
     if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
     for (int j = 0; j < probs[k]->n_groups; ++j) table[(size_t)t++] = make_int2(k, j);
@@ -1398,6 +1498,10 @@ extern "C" gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mas
                                         const double* pv, double* y, double* pAp, int precision,
                                         void* cuda_stream) {
   if (!p || !free_mask || !pv || !y) return fail(GPCG_ERR_ARG, "NULL argument");
+  {
+    const gpcg_status ps = settle_now(p);
+    if (ps != GPCG_OK) return ps;
+  }
   if (precision != GPCG_FP64 && precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1507,6 +1611,7 @@ extern "C" gpcg_status gpcg_reduced_system(gpcg_problem* p, const uint8_t* free_
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const bool f32 = precision == GPCG_MIXED;
   gpcg_status st;
+  if ((st = settle_now(p)) != GPCG_OK) return st;
   if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
   if ((st = ensure_extract(p, f32, s, true)) != GPCG_OK) return st;
   DevInst& I = p->inst;
@@ -1595,6 +1700,10 @@ extern "C" gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* fr
                                               const double* r, double* z, double* rz,
                                               int precision, void* cuda_stream) {
   if (!p || !free_mask || !r || !z) return fail(GPCG_ERR_ARG, "NULL argument");
+  {
+    const gpcg_status ps = settle_now(p);
+    if (ps != GPCG_OK) return ps;
+  }
   if (precision != GPCG_FP64 && precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
   cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -1669,6 +1778,10 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
                                              int flush_l2, void* cuda_stream,
                                              double* ms_per_launch, double* bytes_per_launch) {
   if (!p || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
+  {
+    const gpcg_status ps = settle_now(p);
+    if (ps != GPCG_OK) return ps;
+  }
   if (precision != GPCG_FP64 && precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
   cudaStream_t s = (cudaStream_t)cuda_stream;

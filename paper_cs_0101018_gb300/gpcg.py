@@ -71,6 +71,8 @@ _SIGNATURES = [
                                       C.c_void_p, C.c_double, C.POINTER(C.c_void_p)]),
     ("gpcg_problem_update", C.c_int, [C.c_void_p, C.POINTER(gpcg_stencil), C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_double]),
+    ("gpcg_problem_update_async", C.c_int, [C.c_void_p, C.POINTER(gpcg_stencil), C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     ("gpcg_problem_destroy", None, [C.c_void_p]),
     ("gpcg_problem_size", C.c_int64, [C.c_void_p]),
     ("gpcg_default_options", None, [C.POINTER(gpcg_options)]),
@@ -221,6 +223,25 @@ def gpcg_problem_update(prob: Problem, qp=None, *, diag=None, cx=None, cy=None, 
     st = _stencil(dim, nx, ny, nz, diag, cx, cy, cz)
     _check(load().gpcg_problem_update(prob.handle, C.byref(st), _ptr(b), _ptr(l), _ptr(u),
                                       float(c)))
+
+
+def gpcg_problem_update_async(prob: Problem, qp=None, *, diag=None, cx=None, cy=None, cz=None,
+                              b=None, l=None, u=None, c=0.0, stream=None) -> None:
+    """gpcg_problem_update whose copies are only enqueued on `stream` (a
+    torch.cuda.Stream, a raw handle or None); the next solve of the problem
+    waits for them.  Pinned host arrays make the copies asynchronous; the
+    problem keeps references to the arrays until its next update."""
+    nx, ny, nz = prob.shape
+    dim = prob.dim
+    if qp is not None:
+        dim, nx, ny, nz = qp.dim, qp.nx, qp.ny, qp.nz
+        diag, cx, cy, cz, b, l, u, c = qp.diag, qp.cx, qp.cy, qp.cz, qp.b, qp.l, qp.u, qp.c
+    diag, cx, cy, cz, b, l, u = map(_f64, (diag, cx, cy, cz, b, l, u))
+    st = _stencil(dim, nx, ny, nz, diag, cx, cy, cz)
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(load().gpcg_problem_update_async(prob.handle, C.byref(st), _ptr(b), _ptr(l), _ptr(u),
+                                            float(c), sp))
+    prob.keep = (diag, cx, cy, cz, b, l, u, st)
 
 
 def gpcg_solve(prob: Problem, opts: gpcg_options | None = None, check: bool = True) -> int:

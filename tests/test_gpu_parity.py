@@ -316,6 +316,53 @@ def test_problem_update_equals_a_fresh_problem(prec):
     assert e.value.status == g.ERR_ARG
 
 
+@pytest.mark.parametrize("prec", [g.FP64, g.MIXED])
+def test_problem_update_async_equals_a_fresh_problem(prec):
+    """gpcg_problem_update_async only enqueues the copies (from pinned arrays,
+    on a side stream); the next solve waits for them and derives the rest.
+    Two problems used in turn give the same solves as fresh problems, bit for
+    bit; a QP that fails the value checks makes its solve fail and leaves no
+    result; the masked product settles a pending update too."""
+    import dataclasses
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    qps = [gi.grid_qp_2d(130, 70, seed=550 + k, shift=0.02 + 0.01 * k,
+                         bounds=("two_sided", "box1", "lower0")[k]) for k in range(3)]
+    pinned = [dataclasses.replace(q, diag=pin(q.diag), cx=pin(q.cx), cy=pin(q.cy), b=pin(q.b),
+                                  l=pin(q.l), u=pin(q.u)) for q in qps]
+    opts = g.default_options(tau_rel=1e-8, precision=prec)
+    side = torch.cuda.Stream()
+    probs = [g.gpcg_problem_create(qps[2]), g.gpcg_problem_create(qps[2])]
+    g.gpcg_problem_update_async(probs[0], pinned[0], stream=side)
+    xs = []
+    for k in range(3):
+        if k + 1 < 3:
+            g.gpcg_problem_update_async(probs[(k + 1) % 2], pinned[k + 1], stream=side)
+        g.gpcg_solve(probs[k % 2], opts)
+        xs.append(g.gpcg_result(probs[k % 2])[0])
+    for q, x in zip(qps, xs):
+        fresh = g.gpcg_problem_create(q)
+        g.gpcg_solve(fresh, opts)
+        assert np.array_equal(x, g.gpcg_result(fresh)[0])
+    b_bad = qps[0].b.copy()
+    b_bad[11] = np.nan
+    g.gpcg_problem_update_async(probs[0], dataclasses.replace(qps[0], b=b_bad), stream=side)
+    assert g.gpcg_solve(probs[0], opts, check=False) == g.ERR_ARG
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_result(probs[0])
+    assert e.value.status == g.ERR_PENDING
+    g.gpcg_problem_update_async(probs[0], qps[1], stream=side)
+    rng = np.random.default_rng(5)
+    mask = (rng.random(qps[1].n) < 0.6).astype(np.uint8)
+    pv = rng.standard_normal(qps[1].n)
+    y, pap = g.gpcg_masked_spmv(probs[0], mask, pv)
+    fresh = g.gpcg_problem_create(qps[1])
+    yf, papf = g.gpcg_masked_spmv(fresh, mask, pv)
+    assert np.array_equal(y, yf) and pap == papf
+    g.gpcg_solve(probs[0], opts)
+    assert np.array_equal(g.gpcg_result(probs[0])[0], xs[1])
+
+
 def test_tile_preconditioner_needs_a_2d_staged_problem():
     qp = gi.grid_qp_3d(17, 9, 6, seed=503, shift=0.02, sigma=0.5, bounds="box1")
     prob = g.gpcg_problem_create(qp)
