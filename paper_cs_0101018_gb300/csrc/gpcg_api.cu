@@ -1942,6 +1942,7 @@ struct gpcg_server {
   std::mutex mu;
   std::condition_variable cv;       // a job is queued, or stop
   std::condition_variable idle_cv;  // a step's passes are done
+  std::condition_variable job_cv;   // a worker finished a job
   bool stop = false, stepping = false;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> wstreams;  // per worker: uploads, then read-backs
@@ -2061,8 +2062,13 @@ static void server_worker(gpcg_server* s, int w) {
     const double t0 = now_s();
     Stager* sg = &s->stagers[(size_t)w];
     const gpcg_status st = j.upload ? start_upload(s, r, up, sg) : read_back(r, down, sg);
-    if (st == GPCG_OK && j.upload && r->cancel) cudaEventSynchronize(r->ev);
     lk.lock();
+    if (st == GPCG_OK && j.upload && r->cancel) {
+      // cancelled meanwhile: its copies finish before the request ends
+      lk.unlock();
+      cudaEventSynchronize(r->ev);
+      lk.lock();
+    }
     s->timing[j.upload ? 3 : 2] += now_s() - t0;
     if (j.upload) {
       s->n_staging--;
@@ -2080,6 +2086,7 @@ static void server_worker(gpcg_server* s, int w) {
       if (st != GPCG_OK) r->st.status = st;
       finish(s, r, r->cancel ? R_CANCELLED : R_DONE);
     }
+    s->job_cv.notify_all();
   }
 }
 
@@ -2374,8 +2381,12 @@ extern "C" gpcg_status gpcg_server_cancel(gpcg_server* s, int64_t ticket) {
         finish(s, r, R_CANCELLED);
         return GPCG_OK;
       }
+    // a worker holds it: wait until it lets go (no copy of the request's
+    // arrays is in flight when cancel returns)
     r->cancel = true;
-    return GPCG_OK;
+    s->job_cv.wait(lk, [&] { return r->state == R_CANCELLED || r->state == R_UPLOADING ||
+                                    r->state == R_DONE; });
+    if (r->state != R_UPLOADING) return GPCG_OK;
   }
   if (r->state == R_UPLOADING) {
     CK(cudaEventSynchronize(r->ev));
