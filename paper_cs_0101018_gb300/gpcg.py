@@ -120,7 +120,7 @@ def load(build_if_missing: bool = True):
         path = _build.build() if build_if_missing else _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"libgpcg.so not found at {path}: build it with "
-                               "__graft_entry__.build() (there is no CPU fallback)")
+                               "paper_cs_0101018_gb300._build.build() (there is no CPU fallback)")
         L = C.CDLL(path)
         for name, res, args in _SIGNATURES:
             f = getattr(L, name)
