@@ -88,3 +88,22 @@ def test_oracle_and_library_share_no_code():
         with open(os.path.join(ROOT, "oracle", fn)) as f:
             txt = f.read()
         assert "paper_cs_0101018_gb300" not in txt and "csrc" not in txt, fn
+
+
+def test_update_and_server_calls_reject_bad_arguments_without_a_gpu():
+    import paper_cs_0101018_gb300 as g
+    L = g.load()
+    from paper_cs_0101018_gb300.gpcg import gpcg_stencil
+    st = gpcg_stencil(2, 4, 4, 1, None, None, None, None)
+    # NULL problem handle: rejected before any CUDA call
+    assert L.gpcg_problem_update(None, C.byref(st), None, None, None, 0.0) == g.ERR_ARG
+    assert L.gpcg_problem_update_async(None, C.byref(st), None, None, None, 0.0,
+                                       None) == g.ERR_ARG
+    v = (C.c_double * 8)()
+    assert L.gpcg_server_timing(None, v) == g.ERR_ARG
+    assert L.gpcg_server_step(None, 16) == g.ERR_ARG
+    assert L.gpcg_server_cancel(None, 1) == g.ERR_ARG
+    assert L.gpcg_server_done(None, 1) == 0
+    t = C.c_int64()
+    assert L.gpcg_server_submit(None, C.byref(st), None, None, None, 0.0, None,
+                                C.byref(t)) == g.ERR_ARG
