@@ -551,6 +551,18 @@ def test_argument_errors():
     assert e.value.status == g.ERR_PENDING
 
 
+def test_pass_cap_gives_timeout(monkeypatch):
+    """The engine's pass cap (GPCG_PASS_CAP) ends a solve that has not
+    converged with GPCG_ERR_TIMEOUT; its statistics stay readable."""
+    qp = gi.grid_qp_2d(60, 60, seed=641, shift=0.001, bounds="two_sided")
+    monkeypatch.setenv("GPCG_PASS_CAP", "16")
+    prob = g.gpcg_problem_create(qp)
+    assert g.gpcg_solve(prob, g.default_options(tau_rel=1e-12), check=False) == g.ERR_TIMEOUT
+    x, st = g.gpcg_result(prob)
+    assert st["status"] == g.ERR_TIMEOUT and 0 < st["passes"] < 100
+    assert np.all((x >= qp.l) & (x <= qp.u))
+
+
 def test_caps_give_distinct_statuses():
     qp = gi.grid_qp_2d(60, 60, seed=640, shift=0.001, bounds="two_sided")
     prob = g.gpcg_problem_create(qp)
