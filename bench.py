@@ -8,7 +8,11 @@ One step = one complete GPCG solve (every pass of the hot path) of that QP.
 `value` is the mixed-precision (FP32-stream / FP64-reduce) rate; the plain
 FP64 path is reported beside it.  Inputs are resident in HBM before the
 timed region; `e2e` repeats the measurement through the C ABI with pinned
-host buffers (create + solve + result per step).
+host buffers (each step: the QP's copies in, overlapped with the previous
+step's solve, the solve, and the read-back of x).  The same line reports the
+masked product alone, the preconditioners, the journal bearing, the
+extracted reduced system, the 32x32 and 128^3 QPs, the 512-QP batch and the
+serving trace (`--serve-seconds`, 0 to skip the last two).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own replica (weak scaling, no collective
