@@ -563,6 +563,18 @@ def test_pass_cap_gives_timeout(monkeypatch):
     assert np.all((x >= qp.l) & (x <= qp.u))
 
 
+def test_line_search_cap_matches_oracle():
+    """max_ls = 0 with mu close to 1/2: the GPU's FP64 path fails the same
+    gradient-projection trial as the oracle and stops with
+    GPCG_ERR_LINESEARCH at the same point."""
+    qp = gi.grid_qp_2d(6, 5, seed=2, shift=0.01, sigma=1.5, bounds="two_sided")
+    ref = oracle.solve(qp, tau_rel=1e-10, mu=0.49, max_ls=0)
+    assert ref.status == oracle.ERR_LINESEARCH
+    status, x, st = _solve(qp, tau_rel=1e-10, mu=0.49, max_ls=0)
+    assert status == g.ERR_LINESEARCH and st["status"] == g.ERR_LINESEARCH
+    assert _rel_err(x, ref.x) <= 1e-9
+
+
 def test_caps_give_distinct_statuses():
     qp = gi.grid_qp_2d(60, 60, seed=640, shift=0.001, bounds="two_sided")
     prob = g.gpcg_problem_create(qp)

@@ -213,6 +213,32 @@ def test_gp_step_sufficient_decrease_and_backtracking(seed):
         assert q(yp) > q(y) + mu * g @ (yp - y) - 1e-13 * scale
 
 
+def test_line_search_cap_gives_its_status():
+    """With no backtracking allowed (max_ls = 0) and mu close to 1/2, a
+    gradient-projection trial of this QP fails the sufficient-decrease test
+    (Eq. gplsstop): the oracle stops in the GP phase with its line-search
+    status at the last accepted point.  Recomputed here from the definitions
+    (dense A, g = Ax + b, the projected gradient, alpha0 of Eq. bqpls and
+    y = P[x - alpha0 g]), that trial violates the Armijo inequality.  With the
+    default cap the same QP is solved."""
+    qp = gi.grid_qp_2d(6, 5, seed=2, shift=0.01, sigma=1.5, bounds="two_sided")
+    mu = 0.49
+    r = oracle.solve(qp, tau_rel=1e-10, mu=mu, max_ls=0, trace_cap=1000)
+    assert r.status == oracle.ERR_LINESEARCH
+    assert r.events[-1]["kind"] == oracle.EV_DONE
+    assert r.events[-2]["kind"] == oracle.EV_GP_STEP
+    x = r.x
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    A = bf.dense_matrix(qp)
+    g = A @ x + qp.b
+    pg = np.where(x <= qp.l, np.minimum(g, 0.0), np.where(x >= qp.u, np.maximum(g, 0.0), g))
+    alpha0 = (pg @ pg) / (pg @ (A @ pg))
+    y = np.minimum(np.maximum(x - alpha0 * g, qp.l), qp.u)
+    q = lambda z: 0.5 * z @ (A @ z) + qp.b @ z
+    assert q(y) > q(x) + mu * (g @ (y - x))
+    assert oracle.solve(qp, tau_rel=1e-10, mu=mu).status == oracle.OK
+
+
 def test_reduced_cg_exact_solve_and_closed_form_decrease():
     """With eta2 = 0 the CG phase runs to the solution of A_FF w = -g_F (it
     terminates in at most m_k steps in exact arithmetic, Sec. 3); and the sum of
