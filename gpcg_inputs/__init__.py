@@ -20,6 +20,11 @@ shapes and sparsity):
 * Band layout: ``diag[i] = A(i,i)``, ``cx[i] = A(i,i+1)``, ``cy[i] = A(i,i+nx)``,
   ``cz[i] = A(i,i+nx*ny)``, point ``i = ix + nx*(iy + ny*iz)``; the entry of the
   last point along an axis is stored as 0.
+
+Workloads: the single small and single large QPs, the 512-instance batch, the
+3-D precision-stress QP, the serving trace (Poisson arrivals; its requests
+draw their QPs from a pool of log-spaced grid sizes), the journal bearing of
+the paper's Sec. 5 and QPs whose solutions are free on a disc.
 """
 from __future__ import annotations
 
