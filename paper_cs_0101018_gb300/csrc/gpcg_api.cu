@@ -2111,9 +2111,9 @@ extern "C" gpcg_status gpcg_server_create(size_t hbm_budget, int max_live, const
   cudaError_t e = cudaGetDevice(&s->dev);
   props.location.id = s->dev;
   // the passes run at the lowest stream priority and the workers' streams at
-  // the highest.  The workers' streams carry copies only (the device-side
-  // set-up of a request runs on the passes' stream), so the priorities only
-  // matter to a caller that adds kernels of its own there.
+  // the highest; the workers' streams carry copies only (a request's
+  // device-side set-up runs on the passes' stream), which the copy engines
+  // move while the passes hold the SMs
   int lo = 0, hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, lo);
