@@ -239,6 +239,45 @@ def test_line_search_cap_gives_its_status():
     assert oracle.solve(qp, tau_rel=1e-10, mu=mu).status == oracle.OK
 
 
+def _lbfgsb_cases():
+    out = [gi.grid_qp_2d(24, 20, seed=811, shift=0.05, bounds=b)
+           for b in ("lower0", "two_sided", "box1")]
+    out.append(gi.grid_qp_3d(8, 7, 6, seed=812, shift=0.05, sigma=0.5, bounds="box1"))
+    return out
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_gpcg_agrees_with_lbfgsb_within_certified_radii(case):
+    """An independent algorithm (scipy's L-BFGS-B, a limited-memory
+    quasi-Newton method with bounds) reaches the same unique minimiser, at
+    sizes brute force cannot reach.  With r(x) = ||grad_Omega q(x)|| /
+    lambda_min and lambda_min >= s, each point lies within r of x* (strong
+    convexity), so ||x_gpcg - x_lbfgsb|| <= r(x_gpcg) + r(x_lbfgsb); the
+    projected gradients are formed here from the definitions on dense A."""
+    from scipy.optimize import minimize
+    qp = _lbfgsb_cases()[case]
+    A = bf.dense_matrix(qp)
+    r = oracle.solve(qp, tau_rel=1e-12)
+    assert r.status == oracle.OK
+
+    def qg(x):
+        g = A @ x + qp.b
+        return 0.5 * x @ (A @ x) + qp.b @ x, g
+
+    def radius(x):
+        g = A @ x + qp.b
+        pg = np.where(x <= qp.l, np.minimum(g, 0.0), np.where(x >= qp.u, np.maximum(g, 0.0), g))
+        return float(np.linalg.norm(pg)) / qp.shift
+
+    bounds = list(zip(np.where(np.isinf(qp.l), None, qp.l), np.where(np.isinf(qp.u), None, qp.u)))
+    res = minimize(qg, np.clip(np.zeros(qp.n), qp.l, qp.u), jac=True, method="L-BFGS-B",
+                   bounds=bounds, options=dict(maxiter=20000, ftol=1e-15, gtol=1e-12, maxcor=30))
+    xl = np.clip(res.x, qp.l, qp.u)
+    assert radius(xl) < 1e-4  # L-BFGS-B converged
+    assert float(np.linalg.norm(xl - r.x)) <= radius(r.x) + radius(xl)
+    assert radius(r.x) <= 1e-9
+
+
 def test_reduced_cg_exact_solve_and_closed_form_decrease():
     """With eta2 = 0 the CG phase runs to the solution of A_FF w = -g_F (it
     terminates in at most m_k steps in exact arithmetic, Sec. 3); and the sum of
