@@ -575,6 +575,24 @@ def test_line_search_cap_matches_oracle():
     assert _rel_err(x, ref.x) <= 1e-9
 
 
+def test_reported_error_bound_is_certified():
+    """With lambda_min given (a lower bound on A's smallest eigenvalue: the
+    generator's shift s, the Laplacian being positive semidefinite),
+    gpcg_stats.err_bound = ||grad_Omega q(x)|| / lambda_min, and the distance
+    to the oracle's tight solution lies within the two points' certified
+    radii.  Without lambda_min no bound is reported (-1)."""
+    qp = gi.grid_qp_2d(65, 33, seed=650, shift=0.02, bounds="two_sided")
+    ref = oracle.solve(qp, tau_rel=1e-12)
+    prob = g.gpcg_problem_create(qp)
+    g.gpcg_solve(prob, g.default_options(tau_rel=1e-4, lambda_min=qp.shift))
+    x, st = g.gpcg_result(prob)
+    assert st["err_bound"] == pytest.approx(st["pg_norm"] / qp.shift, rel=1e-12)
+    ref_radius = ref.stats["pg_norm"] / qp.shift
+    assert np.linalg.norm(x - ref.x) <= (st["err_bound"] + ref_radius) * (1 + 1e-9)
+    g.gpcg_solve(prob, g.default_options(tau_rel=1e-4))
+    assert g.gpcg_result(prob)[1]["err_bound"] == -1.0
+
+
 def test_caps_give_distinct_statuses():
     qp = gi.grid_qp_2d(60, 60, seed=640, shift=0.001, bounds="two_sided")
     prob = g.gpcg_problem_create(qp)
