@@ -53,3 +53,24 @@ def test_serving_pool_covers_every_dimension_size_and_bound_kind():
             for kind in ("lower0", "two_sided", "box1"):
                 q = pool[(dim, int(side), kind)]
                 assert q.dim == dim and q.nx == side and q.n == side ** dim
+
+
+def test_disc_free_qp_is_free_on_its_disc():
+    """The free-set ablation workload: the oracle's solution is free on the
+    whole disc and at its bound beyond a thin band around it (a few cells, the
+    reach of the Laplacian's coupling), so the free fraction follows the disc."""
+    import oracle
+    side = 64
+    fracs = []
+    for frac in (0.1, 0.3, 0.6):
+        qp = gi.disc_free_qp(side, frac)
+        r = oracle.solve(qp, tau_rel=1e-10)
+        assert r.status == oracle.OK
+        iy, ix = np.divmod(np.arange(side * side), side)
+        c = (side - 1) / 2.0
+        d = np.hypot(ix - c, iy - c) - side * math.sqrt(frac / math.pi)
+        free = r.x > 0.0
+        assert np.all(free[d <= 0.0])
+        assert np.max(d[free]) <= 8.0
+        fracs.append(float(np.mean(free)))
+    assert fracs[0] < fracs[1] < fracs[2]
