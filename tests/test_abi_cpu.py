@@ -107,3 +107,19 @@ def test_update_and_server_calls_reject_bad_arguments_without_a_gpu():
     t = C.c_int64()
     assert L.gpcg_server_submit(None, C.byref(st), None, None, None, 0.0, None,
                                 C.byref(t)) == g.ERR_ARG
+
+
+def test_size_limit_is_checked_before_any_copy():
+    """n = nx*ny*nz must stay below 2^31 (and so must each extent): larger
+    problems are refused with GPCG_ERR_ARG before any array is read."""
+    import numpy as np
+    import paper_cs_0101018_gb300 as g
+    from paper_cs_0101018_gb300.gpcg import gpcg_stencil
+    L = g.load()
+    dummy = np.zeros(4)
+    p = dummy.ctypes.data
+    out = C.c_void_p()
+    for dims in ((2, 1 << 16, 1 << 16, 1), (3, 1 << 11, 1 << 10, 1 << 10), (2, 1 << 31, 1, 1)):
+        st = gpcg_stencil(dims[0], dims[1], dims[2], dims[3], p, p, p, p)
+        assert L.gpcg_problem_create(C.byref(st), p, None, None, 0.0, C.byref(out)) == g.ERR_ARG
+        assert b"too large" in L.gpcg_last_error()
