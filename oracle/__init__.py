@@ -6,8 +6,11 @@ compared against.  The CUDA library never imports, links or runs it, and it
 imports nothing from the CUDA library: the two meet only in the seeded inputs
 of :mod:`gpcg_inputs`.
 
-The C code is built on first use with ``gcc -O2 -ffp-contract=off`` (every
-multiply and add separately rounded, identical on x86-64 and aarch64).
+The C code is built on first use with ``gcc -O2 -ffp-contract=off -fopenmp``
+(every multiply and add separately rounded, identical on x86-64 and aarch64).
+Loops whose rows are independent may run on several threads
+(:func:`set_threads`); sums always run on one thread in index order, so
+results do not depend on the thread count.  The default is one thread.
 """
 from __future__ import annotations
 
@@ -72,7 +75,8 @@ def build(force: bool = False) -> str:
                 os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "gpcg_oracle.h"))):
             tmp = _LIB + f".{os.getpid()}.tmp"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                                   "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+                                   "-ffp-contract=off", "-fno-fast-math", "-fopenmp", _SRC,
+                                   "-o", tmp, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -83,6 +87,11 @@ def lib():
         build()
         L = C.CDLL(_LIB)
         vp, i64, dbl, ci = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        L.ora_set_threads.argtypes = [C.c_int]
+        L.ora_set_threads.restype = None
+        L.ora_get_threads.argtypes = []
+        L.ora_get_threads.restype = C.c_int
+        L.ora_set_threads(1)
         L.ora_default_options.argtypes = [C.POINTER(Options)]
         L.ora_matvec.argtypes = [C.POINTER(_Stencil), vp, vp]
         L.ora_masked_matvec.argtypes = [C.POINTER(_Stencil), vp, vp, vp]
@@ -109,6 +118,17 @@ def lib():
         L.ora_gpcg.restype = ci
         _lib = L
     return _lib
+
+
+def set_threads(t: int) -> int:
+    """Threads for the row loops (t <= 0: every processor); returns the count
+    in force.  Results are bit-identical for every count."""
+    lib().ora_set_threads(int(t))
+    return int(lib().ora_get_threads())
+
+
+def threads() -> int:
+    return int(lib().ora_get_threads())
 
 
 def _f64(a):

@@ -14,9 +14,13 @@
  *
  * Every function follows one passage of Benson, McInnes & More, "GPCG: a case
  * study in the performance and scalability of optimization algorithms"
- * (2000), cited by section and equation label.  Loops are sequential, sums run
+ * (2000), cited by section and equation label.  Every sum runs sequentially
  * in index order, and the file is compiled with -ffp-contract=off so that
  * every multiply and add is a separately rounded IEEE operation on every host.
+ * Loops whose rows are independent (y = Ax, projections, vector updates) may
+ * be split over OpenMP threads (ora_set_threads): each row is computed by the
+ * same operations whichever thread runs it, so results are bit-identical for
+ * every thread count.  Reductions (dot products, the census) are never split.
  *
  * Readings where the paper is silent (all documented in the design notes):
  *   - mu (Armijo constant, "some mu in (0,1/2)") defaults to 0.01.
@@ -43,6 +47,34 @@
 #include <string.h>
 
 #include "gpcg_oracle.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Row loops run in parallel only above this many rows (below it a thread team
+ * costs more than it saves). */
+#define ORA_PAR_MIN 32768
+#ifdef _OPENMP
+#define ORA_ROWS _Pragma("omp parallel for schedule(static) if (n >= ORA_PAR_MIN)")
+#else
+#define ORA_ROWS
+#endif
+
+static int ora_threads = 1;
+
+void ora_set_threads(int t)
+{
+#ifdef _OPENMP
+    ora_threads = t > 0 ? t : omp_get_num_procs();
+    omp_set_num_threads(ora_threads);
+#else
+    (void)t;
+    ora_threads = 1;
+#endif
+}
+
+int ora_get_threads(void) { return ora_threads; }
 
 /* ------------------------------------------------------------------------ */
 /* The Hessian A as a stencil.                                               */
@@ -77,6 +109,7 @@ static double row_times(const ora_stencil* A, int64_t i, const double* x)
 void ora_matvec(const ora_stencil* A, const double* x, double* y)
 {
     const int64_t n = ora_n(A);
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) y[i] = row_times(A, i, x);
 }
 
@@ -88,7 +121,9 @@ void ora_masked_matvec(const ora_stencil* A, const uint8_t* free_mask,
 {
     const int64_t n = ora_n(A);
     double* pz = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) pz[i] = free_mask[i] ? p[i] : 0.0;
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) y[i] = free_mask[i] ? row_times(A, i, pz) : 0.0;
     free(pz);
 }
@@ -122,6 +157,7 @@ static double mid(double l, double u, double x)
 void ora_project(int64_t n, const double* l, const double* u, const double* x,
                  double* out)
 {
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) out[i] = mid(l[i], u[i], x[i]);
 }
 
@@ -139,6 +175,7 @@ static double pg_component(double x, double g, double l, double u)
 void ora_proj_gradient(int64_t n, const double* x, const double* g,
                        const double* l, const double* u, double* pg)
 {
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) pg[i] = pg_component(x[i], g[i], l[i], u[i]);
 }
 
@@ -181,6 +218,7 @@ void ora_census(const ora_stencil* A, const double* b, double c, const double* l
 {
     const int64_t n = ora_n(A);
     ora_matvec(A, x, g);
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) g[i] = g[i] + b[i];
     classify(n, b, c, l, u, x, g, active, out);
 }
@@ -227,8 +265,10 @@ static int armijo_trial(const ora_stencil* A, const double* b, const double* l,
                         double* gt, double* dq)
 {
     const int64_t n = ora_n(A);
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) xt[i] = mid(l[i], u[i], x[i] + alpha * dir[i]);
     ora_matvec(A, xt, gt);
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) gt[i] = gt[i] + b[i];
     double gs = 0.0, sgg = 0.0;
     for (int64_t i = 0; i < n; i++) {
@@ -273,6 +313,7 @@ int ora_gp_step(const ora_stencil* A, const double* b, const double* l,
     }
     const double alpha0 = gg / gAg;
     *alpha0_out = alpha0;
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) dir[i] = -g[i];
     for (int i = 0; i <= max_ls; i++) {
         const double alpha = ldexp(alpha0, -i);
@@ -381,6 +422,7 @@ static void precondition(const ora_stencil* A, const uint8_t* free_mask, int pre
         tile_sweep(A, free_mask, r, z);
         return;
     }
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) {
         if (!free_mask[i]) z[i] = 0.0;
         else if (precond == ORA_PRECOND_JACOBI) z[i] = r[i] / A->diag[i];
@@ -411,11 +453,13 @@ static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const doub
     double* p = (double*)malloc(bytes);
     double* Ap = (double*)malloc(bytes);
     int status = ORA_OK;
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) {
         r[i] = free_mask[i] ? g[i] : 0.0;
         w[i] = 0.0;
     }
     precondition(A, free_mask, precond, r, z);
+    ORA_ROWS
     for (int64_t i = 0; i < n; i++) p[i] = -z[i];
     double rr = dot(n, r, z);
     double dmax = 0.0;
@@ -429,6 +473,7 @@ static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const doub
             break;
         }
         const double alpha = rr / pAp;
+        ORA_ROWS
         for (int64_t i = 0; i < n; i++) {
             w[i] += alpha * p[i];
             r[i] += alpha * Ap[i];
@@ -452,6 +497,7 @@ static int reduced_cg(const ora_stencil* A, const uint8_t* free_mask, const doub
         }
         if (delta > dmax) dmax = delta;
         const double beta = rr_new / rr;
+        ORA_ROWS
         for (int64_t i = 0; i < n; i++) p[i] = -z[i] + beta * p[i];
         rr = rr_new;
     }
@@ -600,6 +646,7 @@ int ora_gpcg(const ora_stencil* A, const double* b, double c, const double* l,
             }
         }
         /* conjugate gradient phase on the face of x_k */
+        ORA_ROWS
         for (int64_t i = 0; i < n; i++) fr[i] = (uint8_t)!act[i];
         int iters = 0, reason = 0;
         int s = reduced_cg(A, fr, g, eta2, opt->max_cg, opt->precond, w, &iters, &reason, &tr,

@@ -87,6 +87,12 @@ typedef struct {
     double a, b, c, d;
 } ora_event;
 
+/* Threads for the loops whose rows are independent (results do not depend on
+ * the count; reductions always run on one thread).  t <= 0: all processors.
+ * Without OpenMP the count stays 1. */
+void ora_set_threads(int t);
+int ora_get_threads(void);
+
 void ora_default_options(ora_options* o);
 void ora_matvec(const ora_stencil* A, const double* x, double* y);
 void ora_masked_matvec(const ora_stencil* A, const uint8_t* free_mask, const double* p,
