@@ -647,8 +647,13 @@ static gpcg_status check_problem(const gpcg_stencil* A, const double* b, double 
   if (A->dim == 2 && A->nz != 1) return fail(GPCG_ERR_ARG, "nz must be 1 when dim == 2");
   if (!A->diag || !A->cx || !A->cy || (A->dim == 3 && !A->cz))
     return fail(GPCG_ERR_ARG, "missing stencil band");
-  if (A->nx >= (1LL << 31) || A->ny >= (1LL << 31) || A->nz >= (1LL << 31) ||
-      A->nx * A->ny * A->nz >= (1LL << 31))
+  // The padded point count px*ny*nz (px = nx rounded up to a multiple of 8)
+  // must stay below 2^31, checked without forming a product that could wrap.
+  constexpr long long kLim = 1LL << 31;
+  if (A->nx > kLim - 9 || A->ny >= kLim || A->nz >= kLim)
+    return fail(GPCG_ERR_ARG, "problem too large (n must be below 2^31)");
+  const long long px = (A->nx + 7) / 8 * 8;
+  if (A->ny > (kLim - 1) / px || A->nz > (kLim - 1) / (px * A->ny))
     return fail(GPCG_ERR_ARG, "problem too large (n must be below 2^31)");
   if (!std::isfinite(c)) return fail(GPCG_ERR_ARG, "c is not finite");
   return GPCG_OK;
@@ -1071,6 +1076,7 @@ static Ctl fresh_ctl() {
   memset(&C, 0, sizeof(C));
   C.pass = P_START;
   C.status = S_RUNNING;
+  C.mixed_nA = -1.0;
   return C;
 }
 
@@ -1380,7 +1386,8 @@ static void fill_stats(const gpcg_problem* p, gpcg_stats* s) {
   s->launches = p->launches;
   const DevInst& I = p->inst;
   s->staged = (I.tma_mask ? 1 : 0) | (I.tma64 ? 2 : 0) | (I.tma32 ? 4 : 0) | (I.tma_gp ? 8 : 0);
-  s->reserved = 0;
+  s->fp64_gp_iters = C.fp64_gp;
+  s->mixed_n_active = (int64_t)C.mixed_nA;
 }
 
 extern "C" gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats) {

@@ -1,6 +1,8 @@
 // gpcg_kernels.cu -- device side of the GB300 GPCG engine: the default
 // instantiation of the pass kernel (pass_engine.cuh), the standalone masked
 // product, the set-up kernels and the host-side launch wrappers.
+#include <mutex>
+
 #include "pass_engine.cuh"
 
 namespace gpcg {
@@ -180,18 +182,37 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
 
 // Grid of the standalone masked product: the resident CTAs of the GPU, at
 // most one per chunk.
+// The shared-memory attribute and the occupancy are per device: each device
+// gets its own entry, set once under a lock (the server's workers and the
+// caller's threads may reach these functions at the same time).
+constexpr int kMaxDevices = 64;
+
+static int device_now() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  return dev;
+}
+
 static int ms_grid(int n_chunks) {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(mspmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMsSmem);
-    cudaFuncSetAttribute(mspmv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMsSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mspmv_kernel<float>, kThreads, kMsSmem);
-    cached = sms * (per > 0 ? per : 1);
+  static std::mutex mu;
+  static int cached[kMaxDevices] = {0};
+  const int dev = device_now();
+  int c;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!cached[dev]) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaFuncSetAttribute(mspmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kMsSmem);
+      cudaFuncSetAttribute(mspmv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kMsSmem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mspmv_kernel<float>, kThreads, kMsSmem);
+      cached[dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }
+    c = cached[dev];
   }
-  return n_chunks < cached ? (n_chunks > 0 ? n_chunks : 1) : cached;
+  return n_chunks < c ? (n_chunks > 0 ? n_chunks : 1) : c;
 }
 
 // Launch the standalone masked product of a 2-D instance whose CG maps are
@@ -364,20 +385,26 @@ const void* pass_kernel_ptr(bool cond, int feat) {
 
 int pass_grid(int n_work) {
   // persistent grid: the resident CTAs of the whole GPU, at most one per item
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64})
-      for (bool cond : {true, false})
-        cudaFuncSetAttribute(pass_kernel_ptr(cond, feat),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel<false, 0>, kThreads,
-                                                  kDynSmem);
-    cached = sms * (per > 0 ? per : 1);
+  static std::mutex mu;
+  static int cached[kMaxDevices] = {0};
+  const int dev = device_now();
+  int c;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!cached[dev]) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64})
+        for (bool cond : {true, false})
+          cudaFuncSetAttribute(pass_kernel_ptr(cond, feat),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel<false, 0>, kThreads,
+                                                    kDynSmem);
+      cached[dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }
+    c = cached[dev];
   }
-  return n_work < cached ? (n_work > 0 ? n_work : 1) : cached;
+  return n_work < c ? (n_work > 0 ? n_work : 1) : c;
 }
 
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat) {

@@ -132,9 +132,12 @@ extern "C" gpcg_status gpcg_masked_spmv_noalloc(const gpcg_stencil* A, const uin
     return bad(GPCG_ERR_ARG, "bad grid size");
   if (!A->diag || !A->cx || !A->cy || (A->dim == 3 && !A->cz))
     return bad(GPCG_ERR_ARG, "missing stencil band");
+  // each factor is bounded before the product is formed, so it cannot wrap
   const long long tiles_x = (A->nx + kTX - 1) / kTX, tiles_y = (A->ny + kTY - 1) / kTY;
-  const long long n_tiles = tiles_x * tiles_y * A->nz;
-  if (n_tiles > kMaxTiles)
+  const bool huge = A->nx >= (1LL << 31) || A->ny >= (1LL << 31) || A->nz >= (1LL << 31) ||
+                    tiles_x > kMaxTiles || tiles_y > kMaxTiles || A->nz > kMaxTiles;
+  const long long n_tiles = huge ? (long long)kMaxTiles + 1 : tiles_x * tiles_y * A->nz;
+  if (n_tiles < 1 || n_tiles > kMaxTiles)
     return bad(GPCG_ERR_ARG,
                "problem too large for the no-allocation entry point: %lld tiles of 64x32 points, "
                "at most %d",
@@ -143,6 +146,28 @@ extern "C" gpcg_status gpcg_masked_spmv_noalloc(const gpcg_stencil* A, const uin
   for (const void* q : arrays)
     if (!on_device(q)) return bad(GPCG_ERR_ARG, "every array must be a device pointer");
   if (A->dim == 3 && !on_device(A->cz)) return bad(GPCG_ERR_ARG, "cz must be a device pointer");
+  // y is written while neighbouring CTAs still read p, the mask and the
+  // bands: it must not overlap any input
+  const long long n = A->nx * A->ny * A->nz;
+  const uintptr_t y0 = (uintptr_t)y, y1 = y0 + sizeof(double) * (size_t)n;
+  const void* inputs[] = {A->diag, A->cx, A->cy, A->dim == 3 ? A->cz : nullptr, p, free_mask};
+  const size_t elem[] = {8, 8, 8, 8, 8, 1};
+  for (int k = 0; k < 6; ++k) {
+    if (!inputs[k]) continue;
+    const uintptr_t a0 = (uintptr_t)inputs[k], a1 = a0 + elem[k] * (size_t)n;
+    if (a0 < y1 && y0 < a1) return bad(GPCG_ERR_ARG, "y must not overlap an input array");
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (pAp) {
+    // returning <p_F, y_F> waits for the stream, which a capture cannot do
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return bad(GPCG_ERR_CUDA, "cudaStreamIsCapturing failed");
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+      return bad(GPCG_ERR_ARG, "pAp must be NULL while the stream is being captured");
+  }
 
   // once per device, with that device current: the device address of the
   // scratch (the host-side name of the array is not a device address)
@@ -161,7 +186,6 @@ extern "C" gpcg_status gpcg_masked_spmv_noalloc(const gpcg_stencil* A, const uin
     }
     scratch = g_addr[dev];
   }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaMemsetAsync((char*)scratch + kCounterOff, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return bad(GPCG_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   const Geo G{A->dim, (int)A->nx, (int)A->ny, (int)A->nz, (int)tiles_x, (int)tiles_y,

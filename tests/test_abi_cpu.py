@@ -110,8 +110,10 @@ def test_update_and_server_calls_reject_bad_arguments_without_a_gpu():
 
 
 def test_size_limit_is_checked_before_any_copy():
-    """n = nx*ny*nz must stay below 2^31 (and so must each extent): larger
-    problems are refused with GPCG_ERR_ARG before any array is read."""
+    """The padded count px*ny*nz (px = nx rounded up to 8) must stay below
+    2^31: larger problems are refused with GPCG_ERR_ARG before any array is
+    read, also where the plain product nx*ny*nz would wrap around (to 0 for
+    (2^22, 2^22, 2^20)) or where padding nx would leave the int range."""
     import numpy as np
     import paper_cs_0101018_gb300 as g
     from paper_cs_0101018_gb300.gpcg import gpcg_stencil
@@ -119,7 +121,27 @@ def test_size_limit_is_checked_before_any_copy():
     dummy = np.zeros(4)
     p = dummy.ctypes.data
     out = C.c_void_p()
-    for dims in ((2, 1 << 16, 1 << 16, 1), (3, 1 << 11, 1 << 10, 1 << 10), (2, 1 << 31, 1, 1)):
+    for dims in ((2, 1 << 16, 1 << 16, 1), (3, 1 << 11, 1 << 10, 1 << 10), (2, 1 << 31, 1, 1),
+                 (3, 1 << 22, 1 << 22, 1 << 20), (2, (1 << 31) - 1, 1, 1),
+                 (2, (1 << 31) - 8, 1, 1), (2, 1, 1 << 28, 1), (3, 8, 1 << 14, 1 << 14),
+                 (3, 1 << 62, 1 << 2, 1 << 0)):
         st = gpcg_stencil(dims[0], dims[1], dims[2], dims[3], p, p, p, p)
         assert L.gpcg_problem_create(C.byref(st), p, None, None, 0.0, C.byref(out)) == g.ERR_ARG
+        assert b"too large" in L.gpcg_last_error()
+
+
+def test_noalloc_size_limit_is_checked_before_any_cuda_call():
+    """The allocation-free product refuses grids beyond its fixed scratch
+    (4096 tiles of 64x32 points) and extents whose tile product would wrap,
+    before it asks CUDA anything."""
+    import numpy as np
+    import paper_cs_0101018_gb300 as g
+    from paper_cs_0101018_gb300.gpcg import gpcg_stencil
+    L = g.load()
+    dummy = np.zeros(4)
+    p = dummy.ctypes.data
+    for dims in ((2, 4096, 4096, 1), (2, 1 << 31, 1, 1), (3, 1 << 40, 1 << 40, 1 << 40),
+                 (3, 64, 32, 4097), (3, 1 << 21, 1 << 21, 1 << 22)):
+        st = gpcg_stencil(dims[0], dims[1], dims[2], dims[3], p, p, p, p)
+        assert L.gpcg_masked_spmv_noalloc(C.byref(st), p, p, p, None, None) == g.ERR_ARG
         assert b"too large" in L.gpcg_last_error()
