@@ -74,3 +74,29 @@ def test_disc_free_qp_is_free_on_its_disc():
         assert np.max(d[free]) <= 8.0
         fracs.append(float(np.mean(free)))
     assert fracs[0] < fracs[1] < fracs[2]
+
+
+def test_precision_stress_golden_is_current():
+    """The stored oracle solution of the 128^3 precision-stress QP belongs to
+    the current generator (same fingerprint of the arrays, same sample points),
+    lies in the box, and meets its own termination test."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location(
+        "make_precision_stress_golden", os.path.join(here, "make_precision_stress_golden.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    d = np.load(mk.OUT)
+    qp = gi.precision_stress()
+    assert mk.fingerprint_matches(mk.qp_fingerprint(qp), d["fingerprint"])
+    assert int(d["n"]) == qp.n
+    assert np.array_equal(d["idx"], mk.sample_indices(qp.n))
+    xs = d["x_sample"]
+    assert np.all((xs >= qp.l[d["idx"]]) & (xs <= qp.u[d["idx"]]))
+    assert float(d["x_inf"]) >= float(np.max(np.abs(xs)))
+    assert float(d["pg_norm"]) <= float(d["tau_rel"]) * float(d["pg_norm0"])
+    act = np.unpackbits(d["active"], count=qp.n).astype(bool)
+    near = np.unpackbits(d["near"], count=qp.n).astype(bool)
+    assert np.all(near[act])  # a point at a bound is within the band
+    assert int(d["stats"][4]) == int(act.sum())
