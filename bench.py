@@ -41,7 +41,7 @@ METRIC = "GPCG solves/s (single large QP, 1600x1600 5-point, tau_rel 1e-6)"
 TAU_REL = 1e-6
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass_kernel_traffic_single_large_1600.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass_kernel_traffic_single_large_1600.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_cs_0101018_gb300", "csrc", f)
                   for f in ("pass_engine.cuh", "gpcg_kernels.cu", "engine.h")]
 
@@ -57,14 +57,11 @@ def _kernel_sha():
 
 def _traffic():
     """DRAM bytes per pass of the benchmark solve, from the committed ncu
-    summary, or None when the kernel sources changed since it was taken."""
+    summary (JSON), or None when the kernel sources changed since it was
+    taken."""
     try:
-        kv = {}
         with open(TRAFFIC_FILE) as f:
-            for line in f:
-                if ":" in line and line.startswith("- "):
-                    k, v = line[2:].split(":", 1)
-                    kv[k.strip()] = v.strip().strip("`")
+            kv = json.load(f)
         if kv.get("kernel_sources_sha256") != _kernel_sha():
             return None, None
         return float(kv["mixed_dram_bytes_per_pass"]), float(kv["fp64_dram_bytes_per_pass"])
@@ -172,21 +169,65 @@ def _max_over_ranks(ws, v):
     return float(t.item())
 
 
-def cpu_baseline(qp, budget_s: float = 25.0):
-    """The oracle as it stands, on one host core: full solves of the workload
-    until about budget_s seconds have passed (at least one)."""
+def host_cpu():
+    """The host's processor count and model (from os and /proc/cpuinfo or
+    lscpu), recorded beside the oracle's timings."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Model"):
+                if model is None or k.strip() == "Model name":
+                    model = v.strip()
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _oracle_solves(qp, threads: int, budget_s: float, max_solves: int):
+    """Complete oracle solves on `threads` row-loop threads until about
+    budget_s seconds have passed (at least one); returns (solves/s, solves,
+    threads in force, status)."""
     import oracle
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        r = oracle.solve(qp, tau_rel=TAU_REL)
-        k += 1
-        if time.perf_counter() - t0 > budget_s * 0.5 or k >= 5:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": k / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} complete FP64 solve(s) of the 1600x1600 workload on one core",
-            "status": r.status}
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            r = oracle.solve(qp, tau_rel=TAU_REL)
+            k += 1
+            if time.perf_counter() - t0 > budget_s or k >= max_solves:
+                break
+        return k / (time.perf_counter() - t0), k, used, r.status
+    finally:
+        oracle.set_threads(1)
+
+
+def cpu_baseline(qp, budget_s: float = 25.0):
+    """The oracle as it stands, timed on the host: on one core, and with its
+    row loops (matrix-vector products, projections, vector updates) on every
+    core (its sums stay sequential, so both give the same x bit for bit).
+    `value` is the all-core figure; about budget_s seconds in all."""
+    import oracle
+    v1, k1, _, s1 = _oracle_solves(qp, 1, budget_s * 0.5, 3)
+    va, ka, used, sa = _oracle_solves(qp, 0, budget_s * 0.5, 6)
+    # the 32x32 QP (tau_rel 1e-8) on one core: its latency beside the GPU's
+    sq = gi.single_small()
+    oracle.solve(sq, tau_rel=1e-8)
+    ms = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        oracle.solve(sq, tau_rel=1e-8)
+        ms.append(1000.0 * (time.perf_counter() - t0))
+    ms.sort()
+    return {"value": va, "unit": "solves/s", "cores": used, "kind": "oracle",
+            "sample": f"{ka} complete FP64 solve(s) of the 1600x1600 workload with the row "
+                      f"loops on {used} threads; {k1} on one core",
+            "single_core": {"value": v1, "unit": "solves/s", "cores": 1, "solves": k1},
+            "single_small_32": {"p50_ms": ms[len(ms) // 2], "p99_ms": ms[-1], "cores": 1,
+                                "solves": len(ms)},
+            "host": host_cpu(), "status": max(s1, sa)}
 
 
 def run_reference(args):
@@ -196,6 +237,7 @@ def run_reference(args):
     qp = gi.single_large()
     import oracle
     oracle.build()
+    used = oracle.set_threads(0)
     times = []
     for _ in range(args.warmup):
         oracle.solve(qp, tau_rel=TAU_REL)
@@ -203,6 +245,7 @@ def run_reference(args):
         t0 = time.perf_counter()
         r = oracle.solve(qp, tau_rel=TAU_REL)
         times.append(time.perf_counter() - t0)
+    oracle.set_threads(1)
     tot = sum(times)
     value = args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
@@ -210,9 +253,10 @@ def run_reference(args):
             "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": qp.n, "tau_rel": TAU_REL},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": used, "kind": "oracle",
                              "sample": "one complete FP64 solve of the 1600x1600 workload "
-                                       "per step, one core"},
+                                       f"per step, row loops on {used} threads",
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "status": r.status}
@@ -347,9 +391,9 @@ def run_ours(args):
     prob = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, **d_in)
     hbm_peak, peak_kind = _peaks()
 
-    def timed(precision, steps, warmup, precond=0):
+    def timed(precision, steps, warmup, precond=0, refine=2):
         opts = g.default_options(tau_rel=TAU_REL, precision=precision, stream=stream,
-                                 precond=precond)
+                                 precond=precond, refine=refine)
         for _ in range(warmup):
             g.gpcg_solve(prob, opts)
         torch.cuda.synchronize()
@@ -375,6 +419,9 @@ def run_ours(args):
     # mixed precision (headline) and plain FP64
     ms_mx, st_mx, clk_mx, wall_mx = timed(g.MIXED, args.steps, args.warmup)
     ms_64, st_64, clk_64, wall_64 = timed(g.FP64, args.steps, args.warmup)
+    # mixed with the FP64 phase's CG phases in FP64 (refine 1; the default,
+    # refine 2, runs them as FP32 correction solves on the FP64 gradient)
+    ms_r1, st_r1, _, _ = timed(g.MIXED, max(1, min(args.steps, 20)), 2, refine=1)
     # the preconditioned CG phases (Sec. 6) on the same workload: point
     # Jacobi and the tile block Jacobi (zebra line sweep in 64 x 8 tiles)
     jac, tile = {}, {}
@@ -530,8 +577,11 @@ def run_ours(args):
     small = {}
     sq = gi.single_small()
     sp = g.gpcg_problem_create(sq)
-    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
-        so = g.default_options(tau_rel=1e-8, precision=prec, stream=stream)
+    # the resident solver (taken by default at this size) and the pass engine
+    for name, prec, path in (("mixed", g.MIXED, g.PATH_AUTO), ("fp64", g.FP64, g.PATH_AUTO),
+                             ("mixed_engine", g.MIXED, g.PATH_ENGINE),
+                             ("fp64_engine", g.FP64, g.PATH_ENGINE)):
+        so = g.default_options(tau_rel=1e-8, precision=prec, stream=stream, path=path)
         for _ in range(3):
             g.gpcg_solve(sp, so)
         ms = []
@@ -546,15 +596,18 @@ def run_ours(args):
         _, ss = g.gpcg_result(sp)
         small[name] = {"p50_ms": ms[len(ms) // 2], "p99_ms": ms[min(len(ms) - 1, int(0.99 * len(ms)))],
                        "solves/s": 1000.0 * len(ms) / sum(ms), "passes": ss["passes"],
-                       "status": ss["status"]}
+                       "status": ss["status"],
+                       "solver": "resident" if ss["path"] == g.PATH_RESIDENT else "engine",
+                       "cg_iters": ss["cg_iters"], "gp_iters": ss["gp_iters"]}
     small["n"] = sq.n
     del sp
     stress = {}
     cq = gi.precision_stress()
     cp = g.gpcg_problem_create(cq)
     xs = {}
-    for name, prec in (("mixed", g.MIXED), ("fp64", g.FP64)):
-        co = g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream)
+    for name, prec, rf in (("mixed", g.MIXED, 2), ("fp64", g.FP64, 2),
+                           ("mixed_refine1", g.MIXED, 1)):
+        co = g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream, refine=rf)
         g.gpcg_solve(cp, co)
         ms = []
         for _ in range(3):
@@ -571,6 +624,18 @@ def run_ours(args):
     stress["n"] = cq.n
     stress["mixed_vs_fp64_rel_err"] = float(np.linalg.norm(xs["mixed"] - xs["fp64"]) /
                                             np.linalg.norm(xs["fp64"]))
+    # the error against the FP64 oracle's solution at tau_rel 1e-12 (stored,
+    # sampled at 65,536 points: tests/golden/precision_stress_128_oracle.npz)
+    golden = os.path.join(ROOT, "tests", "golden", "precision_stress_128_oracle.npz")
+    if os.path.exists(golden):
+        gd = np.load(golden)
+        idx = gd["idx"]
+        for name in ("mixed", "fp64", "mixed_refine1"):
+            stress[name]["max_err_vs_oracle_sampled"] = float(
+                np.max(np.abs(xs[name][idx] - gd["x_sample"])) / max(1.0, float(gd["x_inf"])))
+        stress["oracle_reference"] = (f"oracle at tau_rel {float(gd['tau_rel']):g}, "
+                                      f"{idx.size} sampled points; the GPU solves above stop "
+                                      f"at tau_rel {TAU_REL:g}")
     del cp, cq, xs
 
     batched = bench_batched(g, stream) if args.serve_seconds > 0 else None
@@ -596,6 +661,12 @@ def run_ours(args):
                  "solve": {k: st_64[k] for k in ("outer_iters", "gp_iters", "cg_iters",
                                                  "ls_trials", "passes", "pg_norm", "tau")}},
         "mixed_over_fp64": value / value_64,
+        "mixed_refine1": {"value": ws * len(ms_r1) / _max_over_ranks(ws, sum(ms_r1) / 1000.0),
+                          "unit": "solves/s", "ms_per_step": sum(ms_r1) / len(ms_r1),
+                          "roofline": roof(ms_r1, st_r1, None),
+                          "solve": {k: st_r1[k] for k in ("outer_iters", "gp_iters", "cg_iters",
+                                                          "refine_cg_iters", "passes",
+                                                          "pg_norm", "tau")}},
         "jacobi": jac,
         "tile": tile,
         "journal_bearing_1600": jb,

@@ -25,7 +25,9 @@
  *     _destroy call.  A handle must not be used from two threads at once;
  *     distinct handles may be used concurrently.
  *   - Infinite bounds are written as -INFINITY / +INFINITY.
- *   - n = nx*ny*nz must be below 2^31 and each of nx, ny, nz below 2^31.
+ *   - The padded point count px*ny*nz, with px = nx rounded up to a multiple
+ *     of 8, must be below 2^31 (so n = nx*ny*nz is too); larger problems are
+ *     refused with GPCG_ERR_ARG before any array is read.
  */
 #ifndef GPCG_H
 #define GPCG_H
@@ -52,12 +54,35 @@ typedef enum {
     GPCG_ERR_CANCELLED = 11   /* request cancelled before it finished */
 } gpcg_status;
 
+/* Precision modes.
+ *   GPCG_FP64: every vector, coefficient and reduction in FP64.
+ *   GPCG_MIXED: two phases.
+ *     1. An FP32 phase runs Algorithm GPCG on an FP32 copy of the iterate,
+ *        kept inside the FP32 box [RN(l), RN(u)]: coefficients, vectors,
+ *        gradient, projection and search directions are FP32, and a point
+ *        is active when its FP32 value equals its FP32 bound bit for bit.
+ *        Each thread sums its FP32 products over a chunk of rows in FP32 and
+ *        folds the chunk sums into compensated (float-float) accumulators,
+ *        which are reduced over the grid and converted to FP64; the CG step
+ *        lengths, the
+ *        Armijo comparisons (Eq. gplsstop, cglsstop2), q(x) and the phase's
+ *        tau test are FP64 decisions on those sums.  The phase ends at its
+ *        first tau hit, after a failed projected search, or when ||pg||
+ *        stops decreasing (FP32 noise).
+ *     2. An FP64 phase: an FP64 census rebuilds x (the FP64 bound where the
+ *        FP32 value sat at its FP32 bound, else the FP64 projection) and
+ *        recomputes g, the active and binding sets, q and ||pg|| in FP64;
+ *        with refine, one CG phase on that face (eta2 reduced) and an FP64
+ *        projected search follow; GPCG then continues in FP64 until the FP64
+ *        tau test holds.  The CG phases of the FP64 phase run in FP64
+ *        (refine 1) or, as correction solves on the FP64 gradient, in FP32
+ *        streams with the same compensated sums (refine 2).  The returned x, its statistics and the final
+ *        termination test are FP64.
+ *   gpcg_stats.mixed_n_active and fp64_gp_iters tell whether the FP64 phase
+ *   changed the face the FP32 phase identified. */
 typedef enum {
-    GPCG_FP64 = 0,   /* every vector, coefficient and reduction in FP64 */
-    GPCG_MIXED = 1   /* CG streams FP32 coefficients and vectors with FP64
-                        reductions; gradient projection, projected search,
-                        q(x), the active/binding sets and the termination test
-                        stay FP64; a closing FP64 CG phase refines the result */
+    GPCG_FP64 = 0,
+    GPCG_MIXED = 1
 } gpcg_precision;
 
 /* The Hessian as stencil bands (Sec. 2: A symmetric positive definite).
@@ -84,7 +109,6 @@ typedef struct gpcg_problem gpcg_problem;
 gpcg_status gpcg_problem_create(const gpcg_stencil* A, const double* b, const double* l,
                                 const double* u, double c, gpcg_problem** out);
 
-/* Release every resource of the handle (NULL is allowed). */
 /* Replace the data of a problem by a QP of the same grid (A->dim, nx, ny, nz
  * equal to the problem's): the bands, b, l, u and c, with the same meaning,
  * checks and error statuses as gpcg_problem_create (on an error the
@@ -110,6 +134,7 @@ gpcg_status gpcg_problem_update_async(gpcg_problem* p, const gpcg_stencil* A, co
                                       const double* l, const double* u, double c,
                                       void* stream);
 
+/* Release every resource of the handle (NULL is allowed). */
 void gpcg_problem_destroy(gpcg_problem* p);
 
 /* Problem size n = nx*ny*nz (0 for NULL). */
@@ -122,22 +147,52 @@ int64_t gpcg_problem_size(const gpcg_problem* p);
  * mu 0.01 (Eq. gplsstop / cglsstop2, the paper only asks mu in (0,1/2));
  * eta2_shrink 0.1 and eta2_floor 1e-12 (the reduction of eta2 when Eq.
  * cgstop3 holds, unspecified in the paper); max_outer 10000, max_gp 50,
- * max_cg 10000, max_ls 60; precision GPCG_FP64; refine 1; x0 NULL (start at
+ * max_cg 10000, max_ls 60; precision GPCG_FP64; refine 2; x0 NULL (start at
  * P[l], falling back to u then 0 where a bound is infinite: Sec. 5 uses
  * x0 = l); cuda_stream NULL (the legacy default stream); lambda_min 0;
- * precond GPCG_PRECOND_NONE. */
+ * precond GPCG_PRECOND_NONE; cg_system GPCG_CG_MASKED; path
+ * GPCG_PATH_AUTO. */
 typedef struct {
     double tau_abs, tau_rel;
     double eta1, eta2, mu, eta2_shrink, eta2_floor;
     int max_outer, max_gp, max_cg, max_ls;
     int precision;          /* gpcg_precision */
-    int refine;             /* GPCG_MIXED: run the closing FP64 CG phase */
+    int refine;             /* GPCG_MIXED, after the FP32 phase: 0 no closing CG phase;
+                               1 the closing CG phase and every later one in FP64;
+                               2 every later CG phase in FP32 streams on the FP64
+                               gradient (a correction solve: mixed-precision iterative
+                               refinement, the FP64 search and census deciding) */
     const double* x0;       /* optional start (host or device, n values), projected onto Omega */
     void* cuda_stream;      /* cudaStream_t the solve is ordered on */
     double lambda_min;      /* optional lower bound on lambda_min(A), for err_bound */
     int precond;            /* gpcg_precond: preconditioner of the CG phase (Sec. 6) */
     int cg_system;          /* gpcg_cg_system: how the CG phase applies A_k (Sec. 4) */
+    int path;               /* gpcg_path: which solver runs the problem */
 } gpcg_options;
+
+/* Which solver runs a problem of gpcg_solve / gpcg_solve_batch.
+ *   GPCG_PATH_AUTO (default): the resident solver when the problem fits it,
+ *     else the pass engine.
+ *   GPCG_PATH_ENGINE: the pass engine (persistent passes over the grid, one
+ *     launch per pass), whatever the size.
+ *   GPCG_PATH_RESIDENT: the resident solver; GPCG_ERR_ARG when the problem
+ *     does not fit it.
+ * The resident solver runs the whole of Algorithm GPCG for one problem in
+ * one thread block, every vector in shared memory: problems of at most 2048
+ * points whose FP64 arrays (and, in GPCG_MIXED, their FP32 copies) fit one
+ * block's 227 KB of shared memory (about 1200 points in mixed precision,
+ * 1800 in FP64), with GPCG_PRECOND_NONE or GPCG_PRECOND_JACOBI and
+ * GPCG_CG_MASKED.  It follows the same algorithm, readings and precision
+ * modes as the engine; its sums reduce in another fixed order, so its path
+ * can differ from the engine's where a test is marginal.  In a batch every
+ * fitting problem gets its own block in one launch, next to the engine's
+ * run of the others; each result is still the same as solving that problem
+ * alone with the same options.  The server always uses the engine. */
+typedef enum {
+    GPCG_PATH_AUTO = 0,
+    GPCG_PATH_ENGINE = 1,
+    GPCG_PATH_RESIDENT = 2
+} gpcg_path;
 
 /* How the CG phase works on the reduced system A_k = Z_k' A Z_k (Sec. 4).
  *   GPCG_CG_MASKED (default): full-length vectors, the free set a bitmask
@@ -207,12 +262,27 @@ typedef struct {
                                1 free-set words, 2 FP64 CG passes, 4 FP32 CG passes,
                                8 mixed-precision gradient-projection passes (2-D only; the
                                other passes and 3-D problems use the register sweep) */
+    int fp64_gp_iters;      /* GPCG_MIXED: gradient projection steps taken in FP64 after
+                               the FP32 phase (0 in FP64 mode) */
+    int64_t mixed_n_active; /* GPCG_MIXED: |A(x)| at the first FP64 census after the FP32
+                               phase, i.e. the face that phase identified (-1 in FP64
+                               mode).  The closing CG phase and projected search only add
+                               points to the active set (the step is zero on it), so
+                               mixed_n_active == n_active with fp64_gp_iters == 0 means
+                               the FP32 phase found the returned face exactly. */
+    int path;               /* the solver that ran: GPCG_PATH_ENGINE or GPCG_PATH_RESIDENT
+                               (whose passes count 1: one launch, one read of the
+                               problem and one write of the result) */
     int reserved;
 } gpcg_stats;
 
 /* Copy the latest solution (n values, host or device x_out; NULL skips it)
- * and statistics (NULL skips them).  GPCG_ERR_PENDING before the first
- * solve. */
+ * and statistics (NULL skips them): q(x) (Eq. def-quadratic), the projected
+ * gradient norm ||grad_Omega q(x)|| (Eq. proj-gradient) the termination test
+ * of Eq. bqp_approximate_sol compares with tau, and the sizes of the active
+ * set A(x) and binding set B(x) (Sec. 2), all evaluated in FP64 at the
+ * returned x; the iteration counts of Algorithm GPCG (Sec. 3).
+ * GPCG_ERR_PENDING before the first solve. */
 gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats);
 
 /* y = Z Z' A Z Z' p on the free set given by free_mask (one byte per point,
@@ -225,15 +295,6 @@ gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats)
 gpcg_status gpcg_masked_spmv(gpcg_problem* p, const uint8_t* free_mask, const double* pv,
                              double* y, double* pAp, int precision, void* cuda_stream);
 
-/* z = M^-1 r for the tile preconditioner (GPCG_PRECOND_TILE) on the free set
- * given by free_mask (one byte per point, nonzero = free): the pass that
- * starts a tile-preconditioned CG phase, run once on r in place of the
- * gradient.  z is 0 off the free set.  precision GPCG_MIXED rounds r to FP32
- * and returns FP32 values widened to FP64 (M^-1 itself is applied in FP32 in
- * both modes).  *rz (optional) receives <r_F, z_F> accumulated in FP64.
- * Arrays: n values each, host or device.  2-D problems on the staged path
- * only (GPCG_ERR_ARG otherwise).  Overwrites the problem's CG vectors, so
- * gpcg_result reports GPCG_ERR_PENDING until the next solve. */
 /* The explicit reduced system of GPCG_CG_EXTRACTED for the free set given by
  * free_mask (one byte per point, nonzero = free), built by the same passes
  * as in a solve: *m receives the number of free points; fidx (m values) the
@@ -249,6 +310,15 @@ gpcg_status gpcg_reduced_system(gpcg_problem* p, const uint8_t* free_mask, int p
                                 int64_t* m, int32_t* fidx, double* diag, int32_t* nb,
                                 double* val, void* cuda_stream);
 
+/* z = M^-1 r for the tile preconditioner (GPCG_PRECOND_TILE) on the free set
+ * given by free_mask (one byte per point, nonzero = free): the pass that
+ * starts a tile-preconditioned CG phase, run once on r in place of the
+ * gradient.  z is 0 off the free set.  precision GPCG_MIXED rounds r to FP32
+ * and returns FP32 values widened to FP64 (M^-1 itself is applied in FP32 in
+ * both modes).  *rz (optional) receives <r_F, z_F> accumulated in FP64.
+ * Arrays: n values each, host or device.  2-D problems on the staged path
+ * only (GPCG_ERR_ARG otherwise).  Overwrites the problem's CG vectors, so
+ * gpcg_result reports GPCG_ERR_PENDING until the next solve. */
 gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* free_mask, const double* r,
                                    double* z, double* rz, int precision, void* cuda_stream);
 
@@ -271,9 +341,12 @@ gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int 
  * counterpart; this is a deployment variant of the reduced-Hessian product.
  *
  * Computes y = Z Z' A Z Z' p and, if pAp != NULL, writes <p_F, y_F> to the
- * host or device address pAp (the call then waits for the stream).  A's
- * bands, free_mask (one byte per point, nonzero = free), p and y must be
- * device pointers owned by the caller; nothing is copied or allocated.  The
+ * host or device address pAp (the call then waits for the stream, so pAp
+ * must be NULL while the stream is being captured: GPCG_ERR_ARG otherwise).
+ * A's bands, free_mask (one byte per point, nonzero = free), p and y must be
+ * device pointers owned by the caller; y must not overlap any of the inputs
+ * (GPCG_ERR_ARG: other threads still read p where y is written).  Nothing is
+ * copied or allocated.  The
  * only scratch is a fixed array of about 33 KB in device memory, held by every
  * GPU that loads the library until the process exits; it allows at most 4096
  * tiles of 64x32 points (for example 8.4e6 points on a 2-D grid), and larger
@@ -282,7 +355,8 @@ gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int 
  * before any stream capture.  All calls on a device share the array: calls
  * whose kernels overlap on the GPU (different streams, other host threads)
  * race and must be serialised by the caller.
- * Errors: GPCG_ERR_ARG (NULL, host pointer, bad size, too large), GPCG_ERR_CUDA. */
+ * Errors: GPCG_ERR_ARG (NULL, host pointer, bad size, too large, y overlapping
+ * an input, pAp during a capture), GPCG_ERR_CUDA. */
 gpcg_status gpcg_masked_spmv_noalloc(const gpcg_stencil* A, const uint8_t* free_mask,
                                      const double* p, double* y, double* pAp,
                                      void* cuda_stream);

@@ -166,7 +166,7 @@ struct Ctl {
   int stall;         // mixed phase: outer iterates without progress of ||pg||
   int slow;          // mixed phase: consecutive iterates on an unchanged face without
                      // a halving of ||pg|| (the FP32 noise floor)
-  int pad_c;
+  int fp64_gp;       // mixed precision: GP steps taken in FP64 after the FP32 phase
   int cg_finish;     // the pending P_CG_A only completes w before the search
   int m;             // explicit reduced system: free points of the current phase
   int pad_m;
@@ -175,6 +175,7 @@ struct Ctl {
   double alpha0, alpha, beta, rr, dmax, cdmax, eta2, tau, pg0;
   double pg2, nA, nB, xgb, gF2;  // census of the current iterate
   double alg_bytes;              // algorithmic HBM bytes of all passes so far
+  double mixed_nA;               // |A| at the first FP64 census after the FP32 phase (-1: none)
   double red[kNRed];             // reduced sums of the latest pass
 };
 

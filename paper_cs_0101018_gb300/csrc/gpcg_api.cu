@@ -27,6 +27,9 @@ namespace gpcg {
 const void* pass_kernel_ptr(bool cond, int feat);
 int pass_grid(int n_work);
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
+size_t resident_smem(int dim, long long n, bool mixed, bool jacobi);
+cudaError_t launch_resident(const DevInst* insts, const int* ids, Ctl* ctl, int count,
+                            size_t smem, unsigned sweep_cap, cudaStream_t s);
 cudaError_t launch_prep(const DevInst& I, double* cx, double* cy, double* cz, double* l, double* u,
                         int fill_l, int fill_u, int* flags, cudaStream_t s);
 cudaError_t launch_to_float(const double* src, float* dst, long long count, cudaStream_t s);
@@ -97,6 +100,7 @@ struct Scratch {
   int* d_queue = nullptr;  // [0] work queue head, [1] exit counter (zero between launches),
                            // [2] error flag of the bounded waits
   int* h_pin = nullptr;  // pinned: [0] live, [1] npass
+  int* d_ids = nullptr;  // slots of the instances the resident solver takes
   int cap_inst = 0;
   long long cap_tiles = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -112,8 +116,9 @@ struct Scratch {
   void release() {
     invalidate();
     for (void* d : {(void*)d_insts, (void*)d_ctl, (void*)d_tiles, (void*)d_live, (void*)d_npass,
-                    (void*)d_queue})
+                    (void*)d_queue, (void*)d_ids})
       if (d) cudaFree(d);
+    d_ids = nullptr;
     if (h_pin) cudaFreeHost(h_pin);
     d_queue = nullptr;
     d_insts = nullptr;
@@ -137,10 +142,13 @@ struct Scratch {
     if (n_inst > cap_inst) {
       cudaFree(d_insts);
       cudaFree(d_ctl);
+      cudaFree(d_ids);
       d_insts = nullptr;
       d_ctl = nullptr;
+      d_ids = nullptr;
       CK(cudaMalloc(&d_insts, sizeof(DevInst) * n_inst));
       CK(cudaMalloc(&d_ctl, sizeof(Ctl) * n_inst));
+      CK(cudaMalloc(&d_ids, sizeof(int) * n_inst));
       cap_inst = n_inst;
       invalidate();
     }
@@ -182,6 +190,7 @@ struct gpcg_problem {
   DevInst inst{};
   Scratch sc;
   Ctl last{};
+  int last_path = 0;  // GPCG_PATH_ENGINE / GPCG_PATH_RESIDENT of the latest solve
   bool have = false;
   double lambda_min = 0.0;
   long long launches = 0;
@@ -1008,12 +1017,13 @@ extern "C" void gpcg_default_options(gpcg_options* o) {
   o->max_cg = 10000;
   o->max_ls = 60;
   o->precision = GPCG_FP64;
-  o->refine = 1;
+  o->refine = 2;
   o->x0 = nullptr;
   o->cuda_stream = nullptr;
   o->lambda_min = 0.0;
   o->precond = GPCG_PRECOND_NONE;
   o->cg_system = GPCG_CG_MASKED;
+  o->path = GPCG_PATH_AUTO;
 }
 
 static gpcg_status check_options(const gpcg_options* o) {
@@ -1028,6 +1038,7 @@ static gpcg_status check_options(const gpcg_options* o) {
     return fail(GPCG_ERR_ARG, "bad iteration caps");
   if (o->precision != GPCG_FP64 && o->precision != GPCG_MIXED)
     return fail(GPCG_ERR_ARG, "unknown precision");
+  if (o->refine < 0 || o->refine > 2) return fail(GPCG_ERR_ARG, "refine must be 0, 1 or 2");
   if (o->precond != GPCG_PRECOND_NONE && o->precond != GPCG_PRECOND_JACOBI &&
       o->precond != GPCG_PRECOND_TILE)
     return fail(GPCG_ERR_ARG, "unknown preconditioner");
@@ -1035,6 +1046,8 @@ static gpcg_status check_options(const gpcg_options* o) {
     return fail(GPCG_ERR_ARG, "unknown CG system");
   if (o->cg_system == GPCG_CG_EXTRACTED && o->precond == GPCG_PRECOND_TILE)
     return fail(GPCG_ERR_ARG, "the tile preconditioner works on the masked system only");
+  if (o->path != GPCG_PATH_AUTO && o->path != GPCG_PATH_ENGINE && o->path != GPCG_PATH_RESIDENT)
+    return fail(GPCG_ERR_ARG, "unknown path");
   return GPCG_OK;
 }
 
@@ -1054,7 +1067,7 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   r.max_cg = o->max_cg;
   r.max_ls = o->max_ls;
   r.mixed = o->precision == GPCG_MIXED;
-  r.refine = o->refine ? 1 : 0;
+  r.refine = o->refine;
   r.use_x0 = use_x0 ? 1 : 0;
   r.extract = o->cg_system == GPCG_CG_EXTRACTED ? 1 : 0;
   r.precond = o->precond == GPCG_PRECOND_JACOBI ? PC_JACOBI
@@ -1289,12 +1302,37 @@ static int to_status(int s) {
   }
 }
 
+// Shared-memory bytes of the resident solve of p under options o, 0 when
+// that solver does not take it.
+static size_t resident_fit(const gpcg_problem* p, const gpcg_options* o) {
+  if (o->path == GPCG_PATH_ENGINE) return 0;
+  if (o->precond == GPCG_PRECOND_TILE || o->cg_system != GPCG_CG_MASKED) return 0;
+  return resident_smem(p->dim, p->n, o->precision == GPCG_MIXED,
+                       o->precond == GPCG_PRECOND_JACOBI);
+}
+
 static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_options* o,
                              Scratch& sc) {
   cudaStream_t s = (cudaStream_t)o->cuda_stream;
+  // the problems the resident solver takes; the others go to the engine
+  std::vector<int> res_ids;
+  std::vector<char> resident(count, 0);
+  size_t res_smem = 0;
   long long tiles = 0;
-  for (int k = 0; k < count; ++k) tiles += probs[k]->n_groups;
-  gpcg_status st = sc.ensure(count, tiles);
+  for (int k = 0; k < count; ++k) {
+    const size_t b = resident_fit(probs[k], o);
+    if (b == 0 && o->path == GPCG_PATH_RESIDENT)
+      return fail(GPCG_ERR_ARG, "problem %d does not fit the resident solver", k);
+    if (b > 0) {
+      resident[k] = 1;
+      res_ids.push_back(k);
+      res_smem = std::max(res_smem, b);
+    } else {
+      tiles += probs[k]->n_groups;
+    }
+  }
+  const int n_eng = count - (int)res_ids.size();
+  gpcg_status st = sc.ensure(count, std::max(tiles, 1LL));
   if (st != GPCG_OK) return st;
   std::vector<DevInst> insts(count);
   Ctl c0 = fresh_ctl();
@@ -1321,19 +1359,31 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   }
   for (int k = 0; k < count; ++k) {
     if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
+    if (resident[k]) continue;
     for (int j = 0; j < probs[k]->n_groups; ++j) table[(size_t)t++] = make_int2(k, j);
   }
   CK(cudaMemcpyAsync(sc.d_insts, insts.data(), sizeof(DevInst) * count, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_ctl, ctl.data(), sizeof(Ctl) * count, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(sc.d_tiles, table.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice, s));
-  gpcg_status run = run_engine(sc, count, tiles, s, feature_set(o));
+  if (tiles > 0)
+    CK(cudaMemcpyAsync(sc.d_tiles, table.data(), sizeof(int2) * tiles, cudaMemcpyHostToDevice,
+                       s));
+  if (!res_ids.empty()) {
+    CK(cudaMemcpyAsync(sc.d_ids, res_ids.data(), sizeof(int) * res_ids.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(launch_resident(sc.d_insts, sc.d_ids, sc.d_ctl, (int)res_ids.size(), res_smem,
+                       env_pass_cap(), s));
+  }
+  gpcg_status run = GPCG_OK;
+  sc.h_pin[1] = 0;
+  if (n_eng > 0) run = run_engine(sc, n_eng, tiles, s, feature_set(o));
   if (run != GPCG_OK && run != GPCG_ERR_TIMEOUT) return run;
   CK(cudaMemcpyAsync(ctl.data(), sc.d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   gpcg_status first_bad = GPCG_OK;
   for (int k = 0; k < count; ++k) {
     if (!ctl[k].done) ctl[k].status = S_TIMEOUT;
-    probs[k]->launches = (unsigned)sc.h_pin[1];
+    probs[k]->launches = resident[k] ? 1 : (unsigned)sc.h_pin[1];
+    probs[k]->last_path = resident[k] ? GPCG_PATH_RESIDENT : GPCG_PATH_ENGINE;
     probs[k]->last = ctl[k];
     probs[k]->have = true;
     probs[k]->lambda_min = o->lambda_min;
@@ -1388,6 +1438,8 @@ static void fill_stats(const gpcg_problem* p, gpcg_stats* s) {
   s->staged = (I.tma_mask ? 1 : 0) | (I.tma64 ? 2 : 0) | (I.tma32 ? 4 : 0) | (I.tma_gp ? 8 : 0);
   s->fp64_gp_iters = C.fp64_gp;
   s->mixed_n_active = (int64_t)C.mixed_nA;
+  s->path = p->last_path;
+  s->reserved = 0;
 }
 
 extern "C" gpcg_status gpcg_result(const gpcg_problem* p, double* x_out, gpcg_stats* stats) {

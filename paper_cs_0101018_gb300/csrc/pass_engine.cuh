@@ -1541,7 +1541,9 @@ __device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
 
 // Start a CG phase on the face of the current iterate (Eq. cg, cg2), w0 = 0.
 __device__ void begin_cg(const DevInst& I, Ctl& C) {
-  C.cg32 = (I.opt.mixed && !C.refined) ? 1 : 0;
+  // mixed precision: FP32 streams in the FP32 phase; after it, FP64 CG (refine
+  // 1) or FP32 correction CG on the FP64 gradient (refine 2)
+  C.cg32 = (I.opt.mixed && (!C.refined || I.opt.refine == 2)) ? 1 : 0;
   C.cg_j = 0;
   C.cdmax = 0.0;
   C.cg_finish = 0;
@@ -1670,6 +1672,8 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
       C.xgb = red[1];
       C.nA = red[4];
       C.nB = red[5];
+      if ((C.census_mode == CM_REFINE || C.census_mode == CM_RESUME) && C.mixed_nA < 0.0)
+        C.mixed_nA = C.nA;  // the face the FP32 phase handed over
       if (C.census_mode == CM_FINAL) {
         C.pass = P_NONE;
         C.done = 1;
@@ -1734,6 +1738,7 @@ __device__ void finalize(const DevInst& I, Ctl& C, const double* red, int* live)
         if (C.trial_gp) {
           C.gp_iters++;
           C.gp_j++;
+          if (o.mixed && !C.gp32) C.fp64_gp++;
           const double dec = -dq;
           const bool same = red[6] == 0.0;  // Eq. pgstop1
           if (pgn <= C.tau) {

@@ -20,6 +20,7 @@ ERR_MAXIT, ERR_LINESEARCH, ERR_TIMEOUT, ERR_PENDING, ERR_CANCELLED = 7, 8, 9, 10
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_TILE = 0, 1, 2
 CG_MASKED, CG_EXTRACTED = 0, 1
+PATH_AUTO, PATH_ENGINE, PATH_RESIDENT = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_INFEASIBLE", 3: "ERR_NUMERIC", 4: "ERR_OOM",
                 5: "ERR_BUDGET", 6: "ERR_CUDA", 7: "ERR_MAXIT", 8: "ERR_LINESEARCH",
@@ -44,7 +45,8 @@ class gpcg_options(C.Structure):
                 ("eta2_floor", C.c_double), ("max_outer", C.c_int), ("max_gp", C.c_int),
                 ("max_cg", C.c_int), ("max_ls", C.c_int), ("precision", C.c_int),
                 ("refine", C.c_int), ("x0", C.c_void_p), ("cuda_stream", C.c_void_p),
-                ("lambda_min", C.c_double), ("precond", C.c_int), ("cg_system", C.c_int)]
+                ("lambda_min", C.c_double), ("precond", C.c_int), ("cg_system", C.c_int),
+                ("path", C.c_int)]
 
 
 _OPTION_FIELDS = frozenset(f for f, _ in gpcg_options._fields_)
@@ -57,7 +59,8 @@ class gpcg_stats(C.Structure):
                 ("cg_iters", C.c_int), ("ls_trials", C.c_int), ("refine_cg_iters", C.c_int),
                 ("passes", C.c_int), ("status", C.c_int), ("err_bound", C.c_double),
                 ("alg_bytes", C.c_double), ("launches", C.c_int64), ("staged", C.c_int),
-                ("reserved", C.c_int)]
+                ("fp64_gp_iters", C.c_int), ("mixed_n_active", C.c_int64),
+                ("path", C.c_int), ("reserved", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -43,7 +43,7 @@ def test_default_options_are_the_papers():
     o = g.default_options()
     assert (o.eta1, o.eta2) == (0.1, 0.05)     # Sec. 5
     assert 0 < o.mu < 0.5                      # Eq. gplsstop asks mu in (0, 1/2)
-    assert o.precision == g.FP64 and o.refine == 1
+    assert o.precision == g.FP64 and o.refine == 2 and o.path == g.PATH_AUTO
 
 
 def test_argument_checks_need_no_gpu():

@@ -10,6 +10,8 @@ Tolerances (stated once, used everywhere below):
     error of a dot product of at most 7 terms, with margin); mixed (FP32
     streams): <= 8 eps32 (|A| |p|)_i + the error of rounding A and p to FP32.
 """
+import warnings
+
 import numpy as np
 import pytest
 
@@ -28,6 +30,22 @@ def _solve(qp, **opts):
     prob = g.gpcg_problem_create(qp)
     status = g.gpcg_solve(prob, g.default_options(**opts), check=False)
     x, st = g.gpcg_result(prob)
+    return status, x, st
+
+
+PATHS = {"engine": 1, "resident": 2}
+
+
+def _solve_on(path, qp, **opts):
+    """_solve on the named solver; skips when the resident solver cannot take
+    the problem (more than 2048 points or more than one block's shared
+    memory)."""
+    prob = g.gpcg_problem_create(qp)
+    status = g.gpcg_solve(prob, g.default_options(path=PATHS[path], **opts), check=False)
+    if status == g.ERR_ARG and path == "resident":
+        pytest.skip("does not fit the resident solver")
+    x, st = g.gpcg_result(prob)
+    assert st["path"] == PATHS[path]
     return status, x, st
 
 
@@ -62,37 +80,72 @@ def _problems():
 
 PROBLEMS = _problems()
 
+PATH_KEYS = ("outer_iters", "gp_iters", "cg_iters", "ls_trials")
+# problems whose GPU path left the oracle's, with both count tuples
+_FLIPS = {}
+_PATH_RUNS = set()
+
+
+def _path_parity(name, qp, x, st, ref):
+    """Path parity (the same decisions give the same counts): the GP, CG,
+    outer-iterate and line-search counts must equal the oracle's.  The GPU
+    sums in a different order than the oracle's sequential loops, so a
+    progress or face test that is marginal (Eq. cgstop1, pgstop2, pgstop1,
+    cgstop3) can come out the other way; such a flip is recorded (warning and
+    the module's flip list) and the result-level bound takes the place of
+    path parity: both points are within ||grad_Omega q|| / lambda_min of the
+    unique minimiser x* (Sec. 2), lambda_min >= the generator's shift."""
+    _PATH_RUNS.add(name)
+    got = tuple(int(st[k]) for k in PATH_KEYS)
+    want = tuple(int(ref.stats[k]) for k in PATH_KEYS)
+    if got == want:
+        return
+    _FLIPS[name] = (got, want)
+    warnings.warn(f"path flip on {name}: GPU {dict(zip(PATH_KEYS, got))} vs oracle "
+                  f"{dict(zip(PATH_KEYS, want))}")
+    assert qp.shift > 0.0
+    pg_gpu = float(np.sqrt(oracle.census(qp, x).pg_norm2))
+    bound = (pg_gpu + float(ref.stats["pg_norm"])) / qp.shift
+    assert float(np.linalg.norm(x - ref.x)) <= bound * (1 + 1e-9) + 1e-300, (name, bound)
+
 
 @pytest.mark.parametrize("k", range(len(PROBLEMS)))
-def test_fp64_matches_oracle(k):
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_fp64_matches_oracle(k, path):
     qp = PROBLEMS[k]
     ref = oracle.solve(qp, tau_rel=1e-10)
-    status, x, st = _solve(qp, tau_rel=1e-10)
+    status, x, st = _solve_on(path, qp, tau_rel=1e-10)
     assert status == ref.status == 0
     assert _rel_err(x, ref.x) <= 1e-9
     assert _active_sets_agree(qp, x, ref.x)
     assert np.all((x >= qp.l) & (x <= qp.u))
-    # path parity: the same decisions give the same counts.  The reductions
-    # sum in a different order than the oracle's sequential loops; over
-    # hundreds of CG steps the rounding differences grow until a progress
-    # test (Eq. cgstop1 / pgstop2) that is marginal flips, so the counts may
-    # drift apart by a few percent at tight tolerances; x must agree anyway.
-    for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
-        a, b = st[key], ref.stats[key]
-        assert abs(a - b) <= 3 + 0.10 * b, (key, a, b)
-    assert abs(st["n_active"] - ref.stats["n_active"]) <= 0.001 * qp.n + 1
+    _path_parity(f"fp64-{path}-{k}", qp, x, st, ref)
+    assert st["mixed_n_active"] == -1 and st["fp64_gp_iters"] == 0
     assert st["n_binding"] <= st["n_active"]
     assert st["pg_norm"] <= st["tau"]
     assert np.isclose(st["q"], ref.stats["q"], rtol=1e-12, atol=1e-12)
 
 
 @pytest.mark.parametrize("k", range(len(PROBLEMS)))
-def test_mixed_matches_oracle(k):
+@pytest.mark.parametrize("refine", [1, 2])
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_mixed_matches_oracle(k, refine, path):
+    """Mixed precision: the FP32 phase, then the FP64 phase whose CG phases
+    run in FP64 (refine 1) or as FP32 correction solves on the FP64 gradient
+    (refine 2); the result is within 1e-5 of the oracle either way, on the
+    pass engine and on the resident solver."""
     qp = PROBLEMS[k]
     ref = oracle.solve(qp, tau_rel=1e-10)
-    status, x, st = _solve(qp, tau_rel=1e-10, precision=g.MIXED)
+    status, x, st = _solve_on(path, qp, tau_rel=1e-10, precision=g.MIXED, refine=refine)
     assert status == 0
     assert _rel_err(x, ref.x) <= 1e-5
+    # the FP32 phase hands a face to the FP64 phase (a census at the rebuilt
+    # x); the closing CG phase and search can only add points to it, so with
+    # no FP64 gradient projection step the returned face contains it.  A
+    # solve that ends at its start (||pg(x0)|| <= tau) hands nothing over.
+    assert st["mixed_n_active"] >= 0 or st["outer_iters"] == 0
+    if st["mixed_n_active"] >= 0 and st["fp64_gp_iters"] == 0:
+        assert st["n_active"] >= st["mixed_n_active"]
     assert _active_sets_agree(qp, x, ref.x)
     assert np.all((x >= qp.l) & (x <= qp.u))
     # the termination test is evaluated in FP64 on the returned point
@@ -105,21 +158,21 @@ JACOBI = [PROBLEMS[k] for k in (0, 2, 5, 10, 14, 20, 24, 26, 28, 29, 30)]
 
 @pytest.mark.parametrize("k", range(len(JACOBI)))
 @pytest.mark.parametrize("prec", [0, 1])
-def test_jacobi_pcg_matches_oracle(k, prec):
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_jacobi_pcg_matches_oracle(k, prec, path):
     """Point-Jacobi preconditioned CG phase (Sec. 6, M = diag of the reduced
     Hessian): the same tolerances as the plain CG phase, against the oracle
     running the same preconditioner; FP64 also follows the oracle's path."""
     qp = JACOBI[k]
     ref = oracle.solve(qp, tau_rel=1e-10, precond=oracle.PRECOND_JACOBI)
-    status, x, st = _solve(qp, tau_rel=1e-10, precision=prec, precond=g.PRECOND_JACOBI)
+    status, x, st = _solve_on(path, qp, tau_rel=1e-10, precision=prec,
+                              precond=g.PRECOND_JACOBI)
     assert status == ref.status == 0
     assert _rel_err(x, ref.x) <= (1e-9 if prec == g.FP64 else 1e-5)
     assert _active_sets_agree(qp, x, ref.x)
     assert np.all((x >= qp.l) & (x <= qp.u))
     if prec == g.FP64:
-        for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
-            a, b = st[key], ref.stats[key]
-            assert abs(a - b) <= 3 + 0.10 * b, (key, a, b)
+        _path_parity(f"jacobi-{path}-{k}", qp, x, st, ref)
     c = oracle.census(qp, x)
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
@@ -255,9 +308,7 @@ def test_extracted_cg_matches_oracle(k, prec, pc):
     assert _active_sets_agree(qp, x, ref.x)
     assert np.all((x >= qp.l) & (x <= qp.u))
     if prec == g.FP64:
-        for key in ("outer_iters", "gp_iters", "cg_iters", "ls_trials"):
-            a, b = st[key], ref.stats[key]
-            assert abs(a - b) <= 3 + 0.10 * b, (key, a, b)
+        _path_parity(f"extracted-{k}-pc{pc}", qp, x, st, ref)
     c = oracle.census(qp, x)
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
@@ -401,13 +452,18 @@ def test_journal_bearing_matches_oracle(shape, eps, prec):
     assert np.all(x >= 0)
 
 
-def test_single_small_workload_fp64_and_mixed():
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_single_small_workload_fp64_and_mixed(path):
+    """The 32x32 workload on both solvers (the resident one takes it by
+    default)."""
     qp = gi.single_small()
     ref = oracle.solve(qp, tau_rel=1e-8)
     for prec, tol in ((g.FP64, 1e-9), (g.MIXED, 1e-5)):
-        status, x, st = _solve(qp, tau_rel=1e-8, precision=prec)
+        status, x, st = _solve_on(path, qp, tau_rel=1e-8, precision=prec)
         assert status == 0 and _rel_err(x, ref.x) <= tol
         assert _active_sets_agree(qp, x, ref.x)
+    _, _, st = _solve(qp, tau_rel=1e-8)
+    assert st["path"] == PATHS["resident"]
 
 
 def _abs_a_abs_p(qp, fm, p):
@@ -457,6 +513,9 @@ def test_batch_is_bitwise_identical_to_alone():
             xb, sb = g.gpcg_result(prob)
             assert np.array_equal(xa, xb)
             assert sa["cg_iters"] == sb["cg_iters"] and sa["passes"] == sb["passes"]
+            assert sa["path"] == sb["path"]
+        # the small members ran on the resident solver, the others on the engine
+        assert {g.gpcg_result(p)[1]["path"] for p in probs} == {1, 2}
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -509,7 +568,8 @@ def test_staged_paths_enabled(monkeypatch):
     assert status == 0 and st["staged"] == 0
 
 
-def test_x0_and_device_arrays():
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_x0_and_device_arrays(path):
     import torch
     qp = gi.grid_qp_2d(48, 40, seed=620, shift=0.02, bounds="box1")
     x0 = gi.uniform(620, 9, qp.n, -2, 2)
@@ -517,7 +577,8 @@ def test_x0_and_device_arrays():
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     prob = g.gpcg_problem_create(dim=2, nx=qp.nx, ny=qp.ny, diag=dev(qp.diag), cx=dev(qp.cx),
                                  cy=dev(qp.cy), b=dev(qp.b), l=dev(qp.l), u=dev(qp.u))
-    g.gpcg_solve(prob, g.default_options(tau_rel=1e-10, x0=dev(x0)))
+    g.gpcg_solve(prob, g.default_options(tau_rel=1e-10, x0=dev(x0), path=PATHS[path]))
+    assert g.gpcg_result(prob)[1]["path"] == PATHS[path]
     xd = torch.empty(qp.n, dtype=torch.float64, device="cuda")
     g.gpcg_result(prob, xd)
     assert _rel_err(xd.cpu().numpy(), ref.x) <= 1e-9
@@ -563,14 +624,15 @@ def test_pass_cap_gives_timeout(monkeypatch):
     assert np.all((x >= qp.l) & (x <= qp.u))
 
 
-def test_line_search_cap_matches_oracle():
+@pytest.mark.parametrize("path", ["engine", "resident"])
+def test_line_search_cap_matches_oracle(path):
     """max_ls = 0 with mu close to 1/2: the GPU's FP64 path fails the same
     gradient-projection trial as the oracle and stops with
     GPCG_ERR_LINESEARCH at the same point."""
     qp = gi.grid_qp_2d(6, 5, seed=2, shift=0.01, sigma=1.5, bounds="two_sided")
     ref = oracle.solve(qp, tau_rel=1e-10, mu=0.49, max_ls=0)
     assert ref.status == oracle.ERR_LINESEARCH
-    status, x, st = _solve(qp, tau_rel=1e-10, mu=0.49, max_ls=0)
+    status, x, st = _solve_on(path, qp, tau_rel=1e-10, mu=0.49, max_ls=0)
     assert status == g.ERR_LINESEARCH and st["status"] == g.ERR_LINESEARCH
     assert _rel_err(x, ref.x) <= 1e-9
 
@@ -600,3 +662,57 @@ def test_caps_give_distinct_statuses():
     assert s == g.ERR_MAXIT
     _, st = g.gpcg_result(prob)
     assert st["outer_iters"] == 1 and st["status"] == g.ERR_MAXIT
+
+
+def test_path_flips_are_rare():
+    """After the FP64 parity tests above (pytest runs a module's tests in
+    order): most solves follow the oracle's path exactly.  A wrong stop rule
+    would move the counts of most problems, not of a few; the flips are
+    listed in the message."""
+    if len(_PATH_RUNS) < 10:
+        pytest.skip("the FP64 path-parity tests did not run in this session")
+    assert len(_FLIPS) <= len(_PATH_RUNS) // 5, sorted(_FLIPS.items())
+    if _FLIPS:
+        warnings.warn(f"{len(_FLIPS)} of {len(_PATH_RUNS)} FP64 solves flipped a marginal "
+                      f"test: {sorted(_FLIPS.items())}")
+
+
+def test_resident_solver_refuses_what_it_cannot_take():
+    """GPCG_PATH_RESIDENT on a problem beyond its size, with the tile
+    preconditioner or with the extracted system gives GPCG_ERR_ARG; the
+    automatic choice hands those to the engine."""
+    big = gi.grid_qp_2d(100, 70, seed=660, shift=0.02, bounds="two_sided")
+    small = gi.grid_qp_2d(30, 20, seed=661, shift=0.02, bounds="two_sided")
+    for qp, extra in ((big, {}), (small, dict(precond=g.PRECOND_TILE)),
+                      (small, dict(cg_system=g.CG_EXTRACTED))):
+        prob = g.gpcg_problem_create(qp)
+        assert g.gpcg_solve(prob, g.default_options(path=g.PATH_RESIDENT, **extra),
+                            check=False) == g.ERR_ARG
+        assert g.gpcg_solve(prob, g.default_options(**extra), check=False) == 0
+        assert g.gpcg_result(prob)[1]["path"] == g.PATH_ENGINE
+
+
+def test_resident_solver_caps():
+    """On the resident solver the sweep cap (GPCG_PASS_CAP, counted in block
+    sweeps) ends an unconverged solve with GPCG_ERR_TIMEOUT and max_outer
+    with GPCG_ERR_MAXIT, x staying in the box."""
+    import os
+    qp = gi.grid_qp_2d(40, 30, seed=662, shift=0.001, bounds="two_sided")
+    prob = g.gpcg_problem_create(qp)
+    s = g.gpcg_solve(prob, g.default_options(tau_rel=1e-12, max_outer=1), check=False)
+    assert s == g.ERR_MAXIT
+    x, st = g.gpcg_result(prob)
+    assert st["outer_iters"] == 1 and st["path"] == g.PATH_RESIDENT
+    assert np.all((x >= qp.l) & (x <= qp.u))
+    old = os.environ.get("GPCG_PASS_CAP")
+    os.environ["GPCG_PASS_CAP"] = "16"
+    try:
+        assert g.gpcg_solve(prob, g.default_options(tau_rel=1e-12), check=False) == g.ERR_TIMEOUT
+    finally:
+        if old is None:
+            os.environ.pop("GPCG_PASS_CAP")
+        else:
+            os.environ["GPCG_PASS_CAP"] = old
+    x, st = g.gpcg_result(prob)
+    assert st["status"] == g.ERR_TIMEOUT
+    assert np.all((x >= qp.l) & (x <= qp.u))

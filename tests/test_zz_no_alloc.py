@@ -1,5 +1,6 @@
 """The allocation-free masked product (gpcg_masked_spmv_noalloc) against the
-regular one (gpcg_masked_spmv, FP64), through the C ABI.
+regular one (gpcg_masked_spmv, FP64) and against the oracle's masked product,
+through the C ABI.
 
 This entry point serves callers that cannot allocate device memory (their
 device memory belongs to their own pool allocator, or they run in loops that
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import gpcg_inputs as gi
+import oracle
 
 g = pytest.importorskip("paper_cs_0101018_gb300")
 from paper_cs_0101018_gb300.gpcg import gpcg_stencil  # noqa: E402
@@ -50,6 +52,8 @@ def test_noalloc_matches_masked_spmv(shape):
     p = gi.normal(12, 2, qp.n)
     prob = g.gpcg_problem_create(qp)
     y_ref, pap_ref = g.gpcg_masked_spmv(prob, fm, p, precision=g.FP64)
+    y_ora = oracle.masked_matvec(qp, fm, p)
+    pap_ora = float(np.dot(p[fm], y_ora[fm]))
 
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     bands = [dev(qp.diag), dev(qp.cx), dev(qp.cy), dev(qp.cz) if nz > 1 else None]
@@ -67,8 +71,10 @@ def test_noalloc_matches_masked_spmv(shape):
         assert s == g.OK, L.gpcg_last_error()
         y = d_y.cpu().numpy()
         assert np.all(np.abs(y - y_ref) <= 16 * EPS64 * bound + 1e-300), call
+        assert np.all(np.abs(y - y_ora) <= 8 * EPS64 * bound + 1e-300), call
         assert np.all(y[~fm] == 0.0)
         assert np.isclose(pap.value, pap_ref, rtol=1e-12, atol=1e-300), (call, pap.value, pap_ref)
+        assert np.isclose(pap.value, pap_ora, rtol=1e-12, atol=1e-300), (call, pap.value, pap_ora)
 
 
 def test_noalloc_rejects_what_it_cannot_serve():
@@ -80,6 +86,18 @@ def test_noalloc_rejects_what_it_cannot_serve():
     assert L.gpcg_masked_spmv_noalloc(C.byref(st), one.data_ptr(), one.data_ptr(),
                                       one.data_ptr(), None, None) == g.ERR_ARG
     assert b"too large" in L.gpcg_last_error()
+    # y must not overlap an input: neighbouring CTAs still read p where y is written
+    qp = gi.grid_qp_2d(40, 30, seed=13, shift=0.1)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    bands = [dev(qp.diag), dev(qp.cx), dev(qp.cy)]
+    st = gpcg_stencil(2, qp.nx, qp.ny, 1, *[b.data_ptr() for b in bands], None)
+    d_fm = dev(np.ones(qp.n, dtype=np.uint8))
+    d_p = dev(gi.normal(13, 1, qp.n))
+    assert L.gpcg_masked_spmv_noalloc(C.byref(st), d_fm.data_ptr(), d_p.data_ptr(),
+                                      d_p.data_ptr(), None, None) == g.ERR_ARG
+    assert b"overlap" in L.gpcg_last_error()
+    assert L.gpcg_masked_spmv_noalloc(C.byref(st), d_fm.data_ptr(), d_p.data_ptr(),
+                                      bands[0].data_ptr() + 8, None, None) == g.ERR_ARG
     host = np.ones(16)
     st = gpcg_stencil(2, 4, 4, 1, host.ctypes.data, host.ctypes.data, host.ctypes.data, None)
     assert L.gpcg_masked_spmv_noalloc(C.byref(st), host.ctypes.data, host.ctypes.data,
