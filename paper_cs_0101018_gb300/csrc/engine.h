@@ -30,11 +30,15 @@ constexpr int kThreads = 32 * kWarps;
 constexpr int kNRed = 8;         // partial sums per tile: 4 FP64 sums, 3 counts, 1 spare
 constexpr int kMinBlocks = 2;    // resident CTAs per SM the pass kernel is compiled for
 
-// A work item is a group of consecutive tiles of one instance; the groups of
-// an instance depend only on its shape (about kGroupTiles tiles each, at most
-// kMaxGroups groups), and each group has one partial-sum slot.
-constexpr int kGroupTiles = 4;
+// The groups of an instance are consecutive ranges of its tiles; they depend
+// only on its shape (about group_tiles tiles each, chosen per shape by the
+// tuned table, at most kMaxGroups groups), and each group has one
+// partial-sum slot, so the order of every sum is fixed by the shape.  A work
+// item of a launch is a run of up to kMaxSpan consecutive groups of one
+// instance (DevInst.span, the launch's choice): coarser items for crowded
+// launches, one group per item for a lone solve, the same sums either way.
 constexpr int kMaxGroups = 304;
+constexpr int kMaxSpan = 2;
 
 // TMA staging: a work item is streamed through shared memory in chunks of
 // 64 columns by 8-32 rows, kStages stages deep (the next chunk is in flight
@@ -181,7 +185,7 @@ struct Ctl {
 
 struct DevInst {
   int dim, nx, ny, nz, px, mw, tiles_x, tiles_y, n_tiles, kc;
-  int n_groups, pad_g;
+  int n_groups, span;      // groups of the instance; groups per work item of this launch
   long long n, plane;
   double* part;            // [n_groups][kNRed] group partial sums of this instance
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)

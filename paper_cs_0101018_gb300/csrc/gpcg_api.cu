@@ -22,6 +22,7 @@
 
 #include "../../include/gpcg.h"
 #include "engine.h"
+#include "tuned.h"
 
 namespace gpcg {
 const void* pass_kernel_ptr(bool cond, int feat);
@@ -234,6 +235,39 @@ static cudaError_t dev_alloc(gpcg_problem* p, void** ptr, size_t bytes) {
   return e;
 }
 
+// Tiles per group of an instance from the tuned table (GPCG_GROUP_TILES
+// overrides it, for the tuner's measurements).
+static int group_tiles(int dim, int n_tiles) {
+  const char* e = getenv("GPCG_GROUP_TILES");
+  if (e && *e) return std::max(1, atoi(e));
+  for (const TunedGroup& t : kTunedGroups)
+    if (t.dim == dim && n_tiles >= t.tiles_lo && n_tiles <= t.tiles_hi)
+      return std::max(1, t.group_tiles);
+  return 4;
+}
+
+// Tiles per work item of a crowded launch (GPCG_ITEM_TILES overrides it).
+static int item_tiles() {
+  const char* e = getenv("GPCG_ITEM_TILES");
+  if (e && *e) return std::max(1, atoi(e));
+  return std::max(1, kTunedItemTiles);
+}
+
+// Groups per work item of problem p: one when the launch's groups fit the
+// resident CTAs at once (a lone solve takes all the parallelism it can),
+// else about item_tiles() tiles per item, the groups spread evenly over the
+// instance's items (an instance's pass lasts as long as its longest item).
+// The explicit reduced system's passes keep one group per item.
+static int item_span(const gpcg_problem* p, long long launch_groups, bool extract) {
+  if (extract || launch_groups <= (long long)pass_grid(1 << 30)) return 1;
+  const int ng = std::max(1, p->n_groups);
+  const double tiles_per_group = (double)p->n_tiles / (double)ng;
+  const int target = std::min(std::max((int)std::lround((double)item_tiles() / tiles_per_group),
+                                       1), kMaxSpan);
+  const int items = (ng + target - 1) / target;
+  return (ng + items - 1) / items;
+}
+
 static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_problem* p) {
   p->dim = dim;
   p->nx = (int)nx;
@@ -249,7 +283,8 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
   p->tiles_x = (int)((nx + kTX - 1) / kTX);
   p->tiles_y = (int)((ny + kTY - 1) / kTY);
   p->n_tiles = p->tiles_x * p->tiles_y * (int)nz;
-  p->n_groups = std::min((p->n_tiles + kGroupTiles - 1) / kGroupTiles, kMaxGroups);
+  const int gt = group_tiles(dim, p->n_tiles);
+  p->n_groups = std::min((p->n_tiles + gt - 1) / gt, kMaxGroups);
 }
 
 // Bytes of the FP64 arena: kc bands, 1/diag, b, l, u, x[2], g[2], r[2], w,
@@ -1357,11 +1392,16 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
         return st;
       }
   }
+  const bool extract = o->cg_system == GPCG_CG_EXTRACTED;
   for (int k = 0; k < count; ++k) {
     if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
     if (resident[k]) continue;
-    for (int j = 0; j < probs[k]->n_groups; ++j) table[(size_t)t++] = make_int2(k, j);
+    // work items of `span` consecutive groups (their sums stay per group)
+    const int span = item_span(probs[k], tiles, extract);
+    insts[k].span = span;
+    for (int j = 0; j < probs[k]->n_groups; j += span) table[(size_t)t++] = make_int2(k, j);
   }
+  tiles = t;  // work items of the launch
   CK(cudaMemcpyAsync(sc.d_insts, insts.data(), sizeof(DevInst) * count, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_ctl, ctl.data(), sizeof(Ctl) * count, cudaMemcpyHostToDevice, s));
   if (tiles > 0)
@@ -2083,6 +2123,8 @@ static gpcg_status start_upload(gpcg_server* s, Req* r, cudaStream_t ws, Stager*
   if ((st = upload_copies(r->prob, &r->A, r->b, r->l, r->u, ws, sg)) != GPCG_OK) return st;
   make_fp64_maps(r->prob, ws);
   if ((st = prepare_instance(r->prob, &s->opt, ws, &r->inst, false)) != GPCG_OK) return st;
+  // a server's launches are crowded: coarse work items
+  r->inst.span = item_span(r->prob, 1LL << 40, s->opt.cg_system == GPCG_CG_EXTRACTED);
   CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
   CK(cudaEventRecord(r->ev, ws));
   return GPCG_OK;
@@ -2243,7 +2285,8 @@ static gpcg_status server_upload_table(gpcg_server* s) {
   for (int k = 0; k < s->max_live; ++k) {
     Req* r = s->slots[k];
     if (!r) continue;
-    for (int j = 0; j < r->prob->n_groups; ++j) table.push_back(make_int2(k, j));
+    for (int j = 0; j < r->prob->n_groups; j += std::max(1, r->inst.span))
+      table.push_back(make_int2(k, j));
   }
   s->tiles = (long long)table.size();
   s->dirty = false;

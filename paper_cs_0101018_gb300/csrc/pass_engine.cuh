@@ -3202,28 +3202,70 @@ __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
 }
 
 // A chunk of a TMA pass: rows yc .. yc+rows-1 (rows a multiple of 8, at most
-// the pass's chunk height) of the tile at column x0 of plane z.
+// the pass's chunk height) of the tile at column x0 of plane z; gi: its
+// group's place in the work item, last: the group's last chunk.
 struct Chunk {
-  int x0, yc, z, rows;
+  int x0, yc, z, rows, gi, last;
 };
 
-// Walks a group's strips [u, u_hi) in chunks: a chunk starts at the current
-// strip and takes up to ch/8 strips without leaving its tile or the group.
-// Tile coordinates are divided out once, at the group's first strip.
+// The boundaries floor(g * total / n_groups), g = g0, g0+1, ..., of an even
+// split of `total` units into n_groups (the groups of an instance depend on
+// its shape only): one division at the first group, then a running
+// remainder (integer division is a long instruction sequence on the GPU).
+struct Split {
+  int at, q, r, rem, n;  // current boundary, total / n, total % n, running remainder
+  __device__ Split(long long total, int g0, int n_groups) : n(n_groups) {
+    const long long p = (long long)g0 * total;
+    at = (int)(p / n_groups);
+    rem = (int)(p - (long long)at * n_groups);
+    q = (int)(total / n_groups);
+    r = (int)(total - (long long)q * n_groups);
+  }
+  // advance to the next group's boundary and return it
+  __device__ int next() {
+    at += q;
+    rem += r;
+    if (rem >= n) {
+      rem -= n;
+      ++at;
+    }
+    return at;
+  }
+};
+
+// Walks the strips of a work item's groups [g0, g1) in chunks: a chunk
+// starts at the current strip and takes up to ch/8 strips without leaving
+// its tile or its group, so that every group is cut into the same chunks
+// whatever the item.  Tile coordinates are divided out once, at the item's
+// first strip.
 struct Walk {
   int u, u_hi, ch8, tx, ty, z, s;
-  __device__ Walk(const DevInst& I, int u0, int hi, int ch) : u(u0), u_hi(hi), ch8(ch >> 3) {
-    const int t = u0 >> 2, rest = t / I.tiles_x;
-    s = u0 & 3;
+  int g, gend;  // current group (relative to the item) and the strip where it ends
+  Split sp;
+  __device__ Walk(const DevInst& I, int grp0, int grp1, int ch)
+      : ch8(ch >> 3), g(0), sp((long long)I.n_tiles * (kTY / 8), grp0, I.n_groups) {
+    u = sp.at;
+    gend = sp.next();
+    u_hi = gend;
+    {
+      Split e = sp;
+      for (int k = grp0 + 1; k < grp1; ++k) u_hi = e.next();
+    }
+    const int t = u >> 2, rest = t / I.tiles_x;
+    s = u & 3;
     tx = t - rest * I.tiles_x;
     ty = rest % I.tiles_y;
     z = rest / I.tiles_y;
   }
   __device__ bool done() const { return u >= u_hi; }
   __device__ Chunk take(const DevInst& I) {
-    const int k = min(min(ch8, 4 - s), u_hi - u);
-    const Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k};
+    const int k = min(min(ch8, 4 - s), gend - u);
+    const Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k, g, u + k == gend};
     u += k;
+    if (u == gend && u < u_hi) {
+      ++g;
+      gend = sp.next();
+    }
     s += k;
     if (s == 4) {
       s = 0;
@@ -3545,9 +3587,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ DevInst sI;
   __shared__ Snap sS;
   __shared__ Ctl sC;
-  __shared__ int s_cnt[3][kWarps];
   __shared__ int s_scan[kWarps];
   __shared__ double s_red[kNRed];
+  __shared__ double s_stash[kMaxSpan][4][kThreads];  // per group of the item: the threads' sums
+  __shared__ double s_gsum[kMaxSpan][4];              // ... reduced
+  __shared__ int s_gcnt[kMaxSpan][3][kWarps];         // ... and the warps' counts
   __shared__ int s_t, s_inst, s_last;
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
@@ -3561,8 +3605,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   // the group reduction's scratch lives in the first stage (no copy is in
   // flight between groups)
   double(*s_sum)[kThreads] = reinterpret_cast<double(*)[kThreads]>(stage0);
-  float(*s_ffh)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + 4 * 8 * kThreads);
-  float(*s_ffl)[kThreads] = reinterpret_cast<float(*)[kThreads]>(stage0 + (32 + 16) * kThreads);
   static_assert((32 + 32) * kThreads <= kStageBytes, "reduction scratch");
 
   if (tid == 0) {
@@ -3649,7 +3691,45 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
     acc.c[0] = acc.c[1] = acc.c[2] = 0;
     FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    // the work item: groups [grp, grp_end) of the instance (the partition
+    // into groups depends on the shape only; how many groups an item spans
+    // is the launch's choice, and every group keeps its own sums, so the
+    // results do not depend on it)
     const int grp = tr.y;
+    const int grp_end = min(grp + max(1, min(I.span, kMaxSpan)), I.n_groups);
+    const int nspan = grp_end - grp;
+    // group sums: FP32 passes carry float-float accumulators (FP64 adds are
+    // slow and long-latency on GB300), the others FP64
+    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
+                        S.pass == P_CG_Z || S.pass == P_RX_BUILD || S.pass == P_RCG)
+                           ? S.cg32 != 0
+                           : (S.pass != P_START && S.gp32 != 0);
+    const int ns = n_sums(S.pass, S.first_cg, S.gp32);
+    // the end of group gi of the item: every thread stores its sums for the
+    // group in shared memory (float-float pairs packed in 8 bytes for the
+    // FP32 passes) and each warp its counts; no barrier and no reduction
+    // here (a barrier at every group end would take away the slack between
+    // warps that hides latency).  The item's end reduces its groups in the
+    // same fixed order as one group alone, so the order of every group's sum
+    // depends only on the group, not on the item.
+    auto flush = [&](int gi) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        s_stash[gi][k][tid] = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
+                                                       __float_as_int(ffs[k].lo))
+                                    : acc.s[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
+        if (lane == 0) s_gcnt[gi][k][warp] = c;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc.s[k] = 0.0;
+        ffs[k] = FF{0.f, 0.f};
+      }
+      acc.c[0] = acc.c[1] = acc.c[2] = 0;
+    };
     const bool tma = tma_pass<kFeat>(I, S);
     if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
       if constexpr ((kFeat & FEAT_EXT) != 0) {
@@ -3669,6 +3749,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
         }
       }
+      flush(0);  // the explicit system's passes take one group per item
     } else if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_MAP) {
       if constexpr ((kFeat & FEAT_EXT) != 0) {
         const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
@@ -3676,21 +3757,27 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
         else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
       }
+      flush(0);
     } else if (!tma) {
-      // register sweep: the group is a range of whole tiles
-      const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
-      const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
-      for (int tile = t_lo; tile < t_hi; ++tile) {
-        const int rest = tile / I.tiles_x;
-        run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
-                        rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
+      // register sweep: a group is a range of whole tiles
+      Split sp(I.n_tiles, grp, I.n_groups);
+      for (int gi = 0; gi < nspan; ++gi) {
+        const int t_lo = sp.at;
+        const int t_hi = sp.next();
+        for (int tile = t_lo; tile < t_hi; ++tile) {
+          const int rest = tile / I.tiles_x;
+          run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
+                          rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
+        }
+        flush(gi);
       }
     } else {
-      // TMA pipeline: the group is a range of 8-row strips (4 per tile), cut
-      // into chunks of up to `ch` rows that stay inside one tile; the next
-      // kStages-1 chunks are in flight while chunk k is computed (the stage
-      // refilled at the top of an iteration is the one computed in the
-      // previous iteration).  Nothing is in flight between groups.
+      // TMA pipeline: a group is a range of 8-row strips (4 per tile), cut
+      // into chunks of up to `ch` rows that stay inside one tile and one
+      // group; the next kStages-1 chunks are in flight while chunk k is
+      // computed (the stage refilled at the top of an iteration is the one
+      // computed in the previous iteration), across the groups of the item.
+      // Nothing is in flight between work items.
       constexpr int kDepth = kStages - 1;
       static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
       const bool gp = gp_tma(I, S);
@@ -3702,8 +3789,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           gp ? trial_alpha0(S)
              : (S.pass == P_CG_B || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
                 (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
-      const long long n_strips = (long long)I.n_tiles * (kTY / 8);
-      Walk wk(I, (int)(grp * n_strips / I.n_groups), (int)((grp + 1) * n_strips / I.n_groups), ch);
+      Walk wk(I, grp, grp_end, ch);
       // the current chunk and the next two (h1, h2: they exist)
       Chunk c0 = wk.take(I);
       const bool hh1 = !wk.done();
@@ -3745,6 +3831,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           if (ok) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
           failed = __syncthreads_or(!ok);
         }
+        if (c0.last) flush(c0.gi);
         if (failed) {
           // a copy never completed: record it, give the copies still in
           // flight a bounded chance to land, and leave; the engine's loop
@@ -3765,59 +3852,56 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (h2) c2 = wk.take(I);
       }
     }
-    // fixed-order group reduction: every thread's sums go to shared memory;
-    // warp k adds up sum k (lane j sums threads j, j+32, ..., then a
-    // butterfly).  FP32 passes reduce their float-float accumulators in
-    // float-float arithmetic: FP64 adds are slow and long-latency on GB300.
-    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
-                        S.pass == P_CG_Z || S.pass == P_RX_BUILD || S.pass == P_RCG)
-                           ? S.cg32 != 0
-                                                              : (S.pass != P_START && S.gp32 != 0);
-    const int ns = n_sums(S.pass, S.first_cg, S.gp32);
-    for (int k = 0; k < ns; ++k) {
-      if (ffred) {
-        s_ffh[k][tid] = ffs[k].hi;
-        s_ffl[k][tid] = ffs[k].lo;
-      } else {
-        s_sum[k][tid] = acc.s[k];
-      }
-    }
+    // the item's groups: warp w reduces sum w & 3 of group w >> 2 (lane j
+    // adds the threads j, j+32, ..., then a butterfly; float-float for the
+    // FP32 passes), then one thread per slot (kNRed per group: the sums, the
+    // counts summed in warp order, a spare) writes the group's partials, and
+    // the instance's arrival counter advances by the item's groups
+    __syncthreads();
+    {
+      static_assert(kWarps == 4 * kMaxSpan, "one warp per sum of each group of an item");
+      const int gi = warp >> 2, k = warp & 3;
+      if (gi < nspan && k < ns) {
+        double v;
+        if (ffred) {
+          auto ld = [&](int t) {
+            const double d = s_stash[gi][k][t];
+            return FF{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
+          };
+          FF a = ld(lane);
+          for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
-      if (lane == 0) s_cnt[k][warp] = c;
+          for (int off = 16; off > 0; off >>= 1)
+            a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
+                             __shfl_xor_sync(FULL_MASK, a.lo, off)});
+          v = ff_val(a);
+        } else {
+          v = s_stash[gi][k][lane];
+          for (int j = 1; j < kWarps; ++j) v += s_stash[gi][k][lane + 32 * j];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+        }
+        if (lane == 0) s_gsum[gi][k] = v;
+      }
     }
     __syncthreads();
-    if (warp < ns) {
-      double v;
-      if (ffred) {
-        FF a{s_ffh[warp][lane], s_ffl[warp][lane]};
-        for (int j = 1; j < kWarps; ++j)
-          a = ff_add(a, FF{s_ffh[warp][lane + 32 * j], s_ffl[warp][lane + 32 * j]});
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-          a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off), __shfl_xor_sync(FULL_MASK, a.lo, off)});
-        v = ff_val(a);
-      } else {
-        v = s_sum[warp][lane];
-        for (int j = 1; j < kWarps; ++j) v += s_sum[warp][lane + 32 * j];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+    if (tid < nspan * kNRed) {
+      const int gi = tid / kNRed, k = tid - gi * kNRed;
+      double v = 0.0;
+      if (k < ns) {
+        v = s_gsum[gi][k];
+      } else if (k >= 4 && k < 7) {
+        int c = 0;
+        for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k - 4][w];
+        v = (double)c;
       }
-      if (lane == 0) s_red[warp] = v;
+      I.part[(long long)(grp + gi) * kNRed + k] = v;
+      __threadfence();
     }
     __syncthreads();
     if (tid == 0) {
-      double* P = I.part + (long long)grp * kNRed;
-      for (int k = 0; k < 4; ++k) P[k] = k < ns ? s_red[k] : 0.0;
-      for (int k = 0; k < 3; ++k) {
-        int c = 0;
-        for (int w = 0; w < kWarps; ++w) c += s_cnt[k][w];
-        P[4 + k] = (double)c;
-      }
-      __threadfence();
-      const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, 1u);
-      s_last = (prev == (unsigned)(I.n_groups - 1));
+      const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, (unsigned)nspan);
+      s_last = (prev + (unsigned)nspan == (unsigned)I.n_groups);
     }
     __syncthreads();
     if (!s_last) continue;

@@ -145,3 +145,23 @@ def test_noalloc_size_limit_is_checked_before_any_cuda_call():
         st = gpcg_stencil(dims[0], dims[1], dims[2], dims[3], p, p, p, p)
         assert L.gpcg_masked_spmv_noalloc(C.byref(st), p, p, p, None, None) == g.ERR_ARG
         assert b"too large" in L.gpcg_last_error()
+
+
+def test_tuner_table_construction():
+    """The tuner keys group sizes by tile count: the fastest measured size
+    (at least the floor) owns the range up to the geometric mid-point
+    towards the next measured size; sizes with equal tile counts are one
+    point."""
+    from paper_cs_0101018_gb300 import tune
+    rows = [(2, 32, 1, {1: 1.0, 2: 2.0, 4: 3.0}, 1),
+            (2, 48, 2, {1: 1.0, 2: 0.9, 4: 1.0}, 2),
+            (2, 64, 2, {1: 1.0, 2: 0.9, 4: 1.0}, 2),
+            (2, 128, 8, {1: 1.0, 2: 2.0, 4: 0.5}, 4),
+            (3, 16, 16, {1: 1.0, 2: 2.0, 4: 3.0}, 1)]
+    t = tune.table_from(rows)
+    assert t[0] == (2, 1, 1, 1) and t[1] == (2, 2, 4, 2) and t[2][:2] == (2, 5)
+    assert tune.group_for(t, 2, 3) == 2 and tune.group_for(t, 2, 100) == 4
+    assert tune.group_for(t, 3, 10 ** 6) == 1
+    t2 = tune.table_from(rows, g_min=2)
+    assert tune.group_for(t2, 2, 1) == 2 and tune.group_for(t2, 3, 16) == 2
+    assert tune.n_tiles(2, 1600) == 25 * 50 and tune.n_tiles(3, 128) == 2 * 4 * 128
