@@ -3201,56 +3201,29 @@ __device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
 }
 
-// A chunk of a TMA pass: rows yc .. yc+rows-1 (rows a multiple of 8, at most
-// the pass's chunk height) of the tile at column x0 of plane z; gi: its
-// group's place in the work item, last: the group's last chunk.
+// A chunk of a TMA pass: rows yc .. yc+(rows & (kEndG0-1))-1 (a multiple of
+// 8, at most the pass's chunk height) of the tile at column x0 of plane z;
+// bit kEndG0 of `rows` marks the last chunk of the first group of a
+// two-group work item (the group's sums are set aside after it).
+constexpr int kEndG0 = 1 << 8;
 struct Chunk {
-  int x0, yc, z, rows, gi, last;
+  int x0, yc, z, rows;
 };
 
-// The boundaries floor(g * total / n_groups), g = g0, g0+1, ..., of an even
-// split of `total` units into n_groups (the groups of an instance depend on
-// its shape only): one division at the first group, then a running
-// remainder (integer division is a long instruction sequence on the GPU).
-struct Split {
-  int at, q, r, rem, n;  // current boundary, total / n, total % n, running remainder
-  __device__ Split(long long total, int g0, int n_groups) : n(n_groups) {
-    const long long p = (long long)g0 * total;
-    at = (int)(p / n_groups);
-    rem = (int)(p - (long long)at * n_groups);
-    q = (int)(total / n_groups);
-    r = (int)(total - (long long)q * n_groups);
-  }
-  // advance to the next group's boundary and return it
-  __device__ int next() {
-    at += q;
-    rem += r;
-    if (rem >= n) {
-      rem -= n;
-      ++at;
-    }
-    return at;
-  }
-};
-
-// Walks the strips of a work item's groups [g0, g1) in chunks: a chunk
-// starts at the current strip and takes up to ch/8 strips without leaving
-// its tile or its group, so that every group is cut into the same chunks
-// whatever the item.  Tile coordinates are divided out once, at the item's
-// first strip.
+// Walks the 8-row strips of a work item's groups [g0, g1) (g1 - g0 <=
+// kMaxSpan = 2) in chunks: a chunk starts at the current strip and takes up
+// to ch/8 strips without leaving its tile or its group, so that every group
+// is cut into the same chunks whatever the item.  Group g covers the strips
+// [g * S / n_groups, (g+1) * S / n_groups), S = 4 n_tiles; tile coordinates
+// are divided out once, at the item's first strip.
 struct Walk {
-  int u, u_hi, ch8, tx, ty, z, s;
-  int g, gend;  // current group (relative to the item) and the strip where it ends
-  Split sp;
-  __device__ Walk(const DevInst& I, int grp0, int grp1, int ch)
-      : ch8(ch >> 3), g(0), sp((long long)I.n_tiles * (kTY / 8), grp0, I.n_groups) {
-    u = sp.at;
-    gend = sp.next();
-    u_hi = gend;
-    {
-      Split e = sp;
-      for (int k = grp0 + 1; k < grp1; ++k) u_hi = e.next();
-    }
+  int u, u_hi, gend, ch8, tx, ty, z, s;
+  __device__ Walk(const DevInst& I, int g0, int g1, int ch) : ch8(ch >> 3) {
+    static_assert(kMaxSpan == 2, "a work item ends at most one group before its own end");
+    const long long strips = (long long)I.n_tiles * (kTY / 8);
+    u = (int)((long long)g0 * strips / I.n_groups);
+    gend = (int)((long long)(g0 + 1) * strips / I.n_groups);
+    u_hi = g1 == g0 + 1 ? gend : (int)((long long)g1 * strips / I.n_groups);
     const int t = u >> 2, rest = t / I.tiles_x;
     s = u & 3;
     tx = t - rest * I.tiles_x;
@@ -3260,11 +3233,11 @@ struct Walk {
   __device__ bool done() const { return u >= u_hi; }
   __device__ Chunk take(const DevInst& I) {
     const int k = min(min(ch8, 4 - s), gend - u);
-    const Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k, g, u + k == gend};
+    Chunk c{tx * kTX, ty * kTY + 8 * s, z, 8 * k};
     u += k;
     if (u == gend && u < u_hi) {
-      ++g;
-      gend = sp.next();
+      c.rows |= kEndG0;
+      gend = u_hi;
     }
     s += k;
     if (s == 4) {
@@ -3338,8 +3311,9 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
 // Compute a staged chunk of the item's pass.
 template <int kFeat>
 __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool gp,
-                                          unsigned char* st, const Chunk& c,
+                                          unsigned char* st, const Chunk& cf,
                                           const unsigned* fbits, Acc& acc, FF* ffs) {
+  const Chunk c{cf.x0, cf.yc, cf.z, cf.rows & (kEndG0 - 1)};
   const int cur = S.cur;
   if (gp) {
     if (S.pass == P_CENSUS) {
@@ -3589,9 +3563,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ Ctl sC;
   __shared__ int s_scan[kWarps];
   __shared__ double s_red[kNRed];
-  __shared__ double s_stash[kMaxSpan][4][kThreads];  // per group of the item: the threads' sums
-  __shared__ double s_gsum[kMaxSpan][4];              // ... reduced
-  __shared__ int s_gcnt[kMaxSpan][3][kWarps];         // ... and the warps' counts
+  // the threads' sums of the first group of a two-group work item (those of
+  // an item's last group go to the first stage once the copies have landed)
+  __shared__ double s_stash[4][kThreads];
+  __shared__ int s_gcnt[kMaxSpan][3][kWarps];  // the warps' counts per group of the item
   __shared__ int s_t, s_inst, s_last;
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
@@ -3697,27 +3672,31 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     // results do not depend on it)
     const int grp = tr.y;
     const int grp_end = min(grp + max(1, min(I.span, kMaxSpan)), I.n_groups);
-    const int nspan = grp_end - grp;
     // group sums: FP32 passes carry float-float accumulators (FP64 adds are
     // slow and long-latency on GB300), the others FP64
-    const bool ffred = (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F ||
-                        S.pass == P_CG_Z || S.pass == P_RX_BUILD || S.pass == P_RCG)
-                           ? S.cg32 != 0
-                           : (S.pass != P_START && S.gp32 != 0);
-    const int ns = n_sums(S.pass, S.first_cg, S.gp32);
-    // the end of group gi of the item: every thread stores its sums for the
-    // group in shared memory (float-float pairs packed in 8 bytes for the
-    // FP32 passes) and each warp its counts; no barrier and no reduction
-    // here (a barrier at every group end would take away the slack between
-    // warps that hides latency).  The item's end reduces its groups in the
-    // same fixed order as one group alone, so the order of every group's sum
-    // depends only on the group, not on the item.
-    auto flush = [&](int gi) {
+    auto ff_pass = [&]() {
+      return (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F || S.pass == P_CG_Z ||
+              S.pass == P_RX_BUILD || S.pass == P_RCG)
+                 ? S.cg32 != 0
+                 : (S.pass != P_START && S.gp32 != 0);
+    };
+    // the end of a group: every thread stores its sums for the group in
+    // shared memory (float-float pairs packed in 8 bytes for the FP32
+    // passes, plain stores that the compiler need not order against the
+    // stages) and each warp its counts, then the accumulators restart.  No
+    // barrier and no reduction here (a barrier inside the item would take
+    // away the slack between warps that hides latency); the item's end
+    // reduces every group in the same fixed order as a group alone, so each
+    // group's sums do not depend on the item that holds it.
+    auto stash = [&](double* dst, int gi) {
+      const bool ffred = ff_pass();
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        s_stash[gi][k][tid] = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
-                                                       __float_as_int(ffs[k].lo))
-                                    : acc.s[k];
+      for (int k = 0; k < 4; ++k) {
+        const double v = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
+                                                  __float_as_int(ffs[k].lo))
+                               : acc.s[k];
+        asm volatile("st.shared.f64 [%0], %1;" ::"r"(smem_u32(dst + k * kThreads + tid)), "d"(v));
+      }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
@@ -3734,7 +3713,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
       if constexpr ((kFeat & FEAT_EXT) != 0) {
         // compact passes of the explicit reduced system: the group is a
-        // range of compact indices
+        // range of compact indices (one group per item)
         const long long lo = (long long)grp * S.m / I.n_groups;
         const long long hi = (long long)(grp + 1) * S.m / I.n_groups;
         const bool jac = I.opt.precond == PC_JACOBI;
@@ -3749,7 +3728,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
         }
       }
-      flush(0);  // the explicit system's passes take one group per item
     } else if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_MAP) {
       if constexpr ((kFeat & FEAT_EXT) != 0) {
         const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
@@ -3757,19 +3735,17 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
         else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
       }
-      flush(0);
     } else if (!tma) {
       // register sweep: a group is a range of whole tiles
-      Split sp(I.n_tiles, grp, I.n_groups);
-      for (int gi = 0; gi < nspan; ++gi) {
-        const int t_lo = sp.at;
-        const int t_hi = sp.next();
+      for (int g = grp; g < grp_end; ++g) {
+        const int t_lo = (int)((long long)g * I.n_tiles / I.n_groups);
+        const int t_hi = (int)((long long)(g + 1) * I.n_tiles / I.n_groups);
         for (int tile = t_lo; tile < t_hi; ++tile) {
           const int rest = tile / I.tiles_x;
           run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
                           rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
         }
-        flush(gi);
+        if (g + 1 < grp_end) stash(&s_stash[0][0], 0);
       }
     } else {
       // TMA pipeline: a group is a range of 8-row strips (4 per tile), cut
@@ -3831,7 +3807,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
           if (ok) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
           failed = __syncthreads_or(!ok);
         }
-        if (c0.last) flush(c0.gi);
+        if (c0.rows & kEndG0) stash(&s_stash[0][0], 0);
         if (failed) {
           // a copy never completed: record it, give the copies still in
           // flight a bounded chance to land, and leave; the engine's loop
@@ -3852,54 +3828,62 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (h2) c2 = wk.take(I);
       }
     }
-    // the item's groups: warp w reduces sum w & 3 of group w >> 2 (lane j
-    // adds the threads j, j+32, ..., then a butterfly; float-float for the
-    // FP32 passes), then one thread per slot (kNRed per group: the sums, the
-    // counts summed in warp order, a spare) writes the group's partials, and
-    // the instance's arrival counter advances by the item's groups
+    // the item's end: the last group's sums go to the first stage, past the
+    // zebra sweep's line buffer (a slow warp may still read that buffer; no
+    // copy is in flight, and every thread has passed the last chunk's
+    // barrier);
+    // warp w reduces sum w & 3 of group w >> 2 (lane j adds the threads j,
+    // j+32, ..., then a butterfly; float-float for the FP32 passes) and
+    // writes it, with the group's counts summed in warp order, to the
+    // group's partial slot (kNRed: 4 sums, 3 counts, a spare); thread 0 then
+    // advances the instance's arrival counter by the item's groups
+    const int nspan = grp_end - grp;
+    constexpr int kScrBytes = kTY * kTX * (int)sizeof(float);  // the register sweep's line buffer
+    double* last_sums = reinterpret_cast<double*>(stage0 + kScrBytes);
+    stash(last_sums, nspan - 1);
     __syncthreads();
     {
       static_assert(kWarps == 4 * kMaxSpan, "one warp per sum of each group of an item");
+      static_assert(kScrBytes + 4 * kThreads * 8 <= kStageBytes, "last group's sums in the first stage");
       const int gi = warp >> 2, k = warp & 3;
-      if (gi < nspan && k < ns) {
-        double v;
-        if (ffred) {
-          auto ld = [&](int t) {
-            const double d = s_stash[gi][k][t];
-            return FF{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
-          };
-          FF a = ld(lane);
-          for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
+      if (gi < nspan) {
+        const int ns = n_sums(S.pass, S.first_cg, S.gp32);
+        const double* src = (gi == nspan - 1 ? last_sums : &s_stash[0][0]) + k * kThreads;
+        double v = 0.0;
+        if (k < ns) {
+          if (ff_pass()) {
+            auto ld = [&](int t) {
+              const double d = src[t];
+              return FF{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
+            };
+            FF a = ld(lane);
+            for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1)
-            a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
-                             __shfl_xor_sync(FULL_MASK, a.lo, off)});
-          v = ff_val(a);
-        } else {
-          v = s_stash[gi][k][lane];
-          for (int j = 1; j < kWarps; ++j) v += s_stash[gi][k][lane + 32 * j];
+            for (int off = 16; off > 0; off >>= 1)
+              a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
+                               __shfl_xor_sync(FULL_MASK, a.lo, off)});
+            v = ff_val(a);
+          } else {
+            v = src[lane];
+            for (int j = 1; j < kWarps; ++j) v += src[lane + 32 * j];
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+          }
         }
-        if (lane == 0) s_gsum[gi][k] = v;
+        double* P = I.part + (long long)(grp + gi) * kNRed;
+        if (lane == 0) {
+          P[k] = v;
+        } else if (lane == 1) {
+          int c = 0;
+          if (k < 3)
+            for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k][w];
+          P[4 + k] = (double)c;  // k == 3: the spare slot
+        }
       }
-    }
-    __syncthreads();
-    if (tid < nspan * kNRed) {
-      const int gi = tid / kNRed, k = tid - gi * kNRed;
-      double v = 0.0;
-      if (k < ns) {
-        v = s_gsum[gi][k];
-      } else if (k >= 4 && k < 7) {
-        int c = 0;
-        for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k - 4][w];
-        v = (double)c;
-      }
-      I.part[(long long)(grp + gi) * kNRed + k] = v;
-      __threadfence();
     }
     __syncthreads();
     if (tid == 0) {
+      __threadfence();  // the block's partial writes (ordered by the barrier) before the arrival
       const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, (unsigned)nspan);
       s_last = (prev + (unsigned)nspan == (unsigned)I.n_groups);
     }
