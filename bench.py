@@ -471,6 +471,24 @@ def run_ours(args):
                       "l2": "flushed before each launch",
                       "GB/s_l2_warm": by / (ms2 / 1000.0) / 1e9,
                       "kernel": "gpcg::mspmv_kernel"}
+    # the same kernel as an iterative method issues it: back-to-back launches
+    # over 6 distinct 1600^2 problems of the generator (seeds 2, 11..15;
+    # their operands, 6 x 51 MB mixed and 6 x 103 MB FP64, exceed the L2
+    # twice over, so each launch streams from HBM), each launch free to start
+    # while the previous one drains
+    sprobs = [prob] + [g.gpcg_problem_create(gi.grid_qp_2d(qp.nx, qp.ny, seed=sd, shift=1e-3,
+                                                           bounds="two_sided"))
+                       for sd in (11, 12, 13, 14, 15)]
+    for name, prec in (("mixed_stream", g.MIXED), ("fp64_stream", g.FP64)):
+        for sp_ in sprobs:
+            g.gpcg_solve(sp_, g.default_options(tau_rel=TAU_REL, precision=prec, stream=stream))
+        ms1, by = g.gpcg_time_masked_spmv_stream(sprobs, prec, reps=10, stream=stream)
+        gbs = by / (ms1 / 1000.0) / 1e9
+        spmv[name] = {"GB/s": gbs, "frac": gbs / hbm_peak, "ms_per_launch": ms1,
+                      "alg_bytes_per_launch": by, "grid": [qp.nx, qp.ny],
+                      "l2": "6 distinct problems in turn (operands > 2x L2)",
+                      "launches": 10 * len(sprobs), "kernel": "gpcg::mspmv_kernel"}
+    del sprobs
     big = gi.grid_qp_2d(4096, 4096, seed=2, shift=1e-3, bounds="two_sided")
     pbig = g.gpcg_problem_create(big)
     for name, prec in (("mixed_4096", g.MIXED), ("fp64_4096", g.FP64)):
@@ -691,7 +709,8 @@ def run_ours(args):
 def run_profile(args):
     """Small fixed workloads for profiler captures: `solve` runs `--steps`
     solves of the benchmark QP, `spmv` a few launches of the masked product
-    alone (L2 flushed before each)."""
+    alone (L2 flushed before each), `spmv_stream` `--steps` rounds of
+    back-to-back products over 6 distinct problems of the same shape."""
     import torch
     import paper_cs_0101018_gb300 as g
     prec = g.MIXED if args.precision == "mixed" else g.FP64
@@ -704,6 +723,13 @@ def run_profile(args):
         _, st = g.gpcg_result(prob)
         print(json.dumps({"profile": "solve", "precision": args.precision, "passes": st["passes"],
                           "launches": st["launches"]}))
+    elif args.profile == "spmv_stream":
+        probs = [prob] + [g.gpcg_problem_create(gi.grid_qp_2d(qp.nx, qp.ny, seed=sd, shift=1e-3,
+                                                              bounds="two_sided"))
+                          for sd in (11, 12, 13, 14, 15)]
+        ms, by = g.gpcg_time_masked_spmv_stream(probs, prec, reps=args.steps)
+        print(json.dumps({"profile": "spmv_stream", "precision": args.precision, "us": 1000 * ms,
+                          "GB/s": by / ms / 1e6}))
     else:
         ms, by = g.gpcg_time_masked_spmv(prob, prec, reps=args.steps, flush_l2=True)
         print(json.dumps({"profile": "spmv", "precision": args.precision, "us": 1000 * ms,
@@ -727,7 +753,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", choices=["solve", "spmv", "serve"], default=None,
+    ap.add_argument("--profile", choices=["solve", "spmv", "spmv_stream", "serve"], default=None,
                     help="run a small fixed workload for a profiler capture instead")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--precond", choices=["none", "jacobi", "tile"], default="none",

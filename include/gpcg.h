@@ -334,6 +334,26 @@ gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int 
                                   void* cuda_stream, double* ms_per_launch,
                                   double* bytes_per_launch);
 
+/* Throughput of the masked matrix-vector kernel of Eq. cg2 (y = Z Z' A Z Z' p
+ * and <p_F, y_F>) in a stream of launches, as an iterative method issues
+ * them: `count` distinct problems (2 <= count <= 64, 2-D, on the staged
+ * path) are multiplied in turn, `reps` rounds, back to back on the given
+ * stream.  Each launch may start while the previous one (another problem's)
+ * drains: launch latency and the final reduction's tail overlap the stream's
+ * other work instead of adding to each launch.  With distinct problems whose
+ * operands together exceed the L2 cache, every launch streams its operands
+ * from HBM.  The operand of each problem is that of gpcg_time_masked_spmv
+ * (the latest solve's free set and p, else all points free and p = 1); one
+ * untimed launch per problem precedes the timed region, which one event pair
+ * brackets.  *ms_per_launch receives the timed region over reps * count and
+ * *bytes_per_launch the mean algorithmic bytes of a launch (as for
+ * gpcg_time_masked_spmv).  Errors: GPCG_ERR_ARG (NULL, count out of range, a
+ * problem given twice, a 3-D problem or one off the staged path),
+ * GPCG_ERR_TIMEOUT (a bounded wait gave up), GPCG_ERR_CUDA. */
+gpcg_status gpcg_time_masked_spmv_stream(gpcg_problem** probs, int count, int precision,
+                                         int reps, void* cuda_stream, double* ms_per_launch,
+                                         double* bytes_per_launch);
+
 /* The product of gpcg_masked_spmv (FP64) for callers that cannot allocate
  * device memory: processes whose device memory belongs entirely to their own
  * pool allocator, and latency-critical loops that cannot take the device-wide

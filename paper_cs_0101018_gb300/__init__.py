@@ -11,4 +11,5 @@ from .gpcg import (CG_EXTRACTED, CG_MASKED, ERR_ARG, ERR_BUDGET, ERR_CANCELLED, 
                    gpcg_problem_create, gpcg_problem_update, gpcg_problem_update_async,
                    gpcg_reduced_system, gpcg_result,
                    gpcg_solve, gpcg_solve_batch, gpcg_tile_precondition, gpcg_time_masked_spmv,
+                   gpcg_time_masked_spmv_stream,
                    library_path, load)

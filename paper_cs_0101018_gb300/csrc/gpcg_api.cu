@@ -39,7 +39,8 @@ cudaError_t launch_recip(const double* d, double* out64, float* out32, long long
 cudaError_t launch_spmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
                               unsigned* mask, void* r, void* pold, bool f32, cudaStream_t s);
 cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* part,
-                         unsigned* counter, double* result, int* err, cudaStream_t s);
+                         unsigned* counter, double* result, int* err, cudaStream_t s,
+                         bool pdl = false);
 int ms_max_ctas();
 cudaError_t launch_mspmv_setup(const DevInst& I, const uint8_t* fm, const double* pv,
                                unsigned* mask, void* pm, bool f32, cudaStream_t s);
@@ -1566,13 +1567,14 @@ static gpcg_status ms_scratch(gpcg_problem* p, cudaStream_t s) {
 
 // One launch of the standalone kernel on the problem's p[0] (operand) and
 // Ap[1] (result) with free-set words `mask`.
-static gpcg_status ms_launch(gpcg_problem* p, bool f32, int mask, cudaStream_t s) {
+static gpcg_status ms_launch(gpcg_problem* p, bool f32, int mask, cudaStream_t s,
+                             bool pdl = false) {
   const size_t c = (size_t)ms_max_ctas();
   double* part = p->ms_buf;
   DevInst& I = p->inst;
   void* y = f32 ? (void*)I.Ap32[1] : (void*)I.Ap64[1];
   CK(launch_mspmv(I, f32, mask, y, part, (unsigned*)(part + c + 1), part + c, (int*)(part + c + 2),
-                  s));
+                  s, pdl));
   return GPCG_OK;
 }
 
@@ -1873,23 +1875,13 @@ extern "C" gpcg_status gpcg_tile_precondition(gpcg_problem* p, const uint8_t* fr
   return st;
 }
 
-extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps,
-                                             int flush_l2, void* cuda_stream,
-                                             double* ms_per_launch, double* bytes_per_launch) {
-  if (!p || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
-  {
-    const gpcg_status ps = settle_now(p);
-    if (ps != GPCG_OK) return ps;
-  }
-  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
-    return fail(GPCG_ERR_ARG, "unknown precision");
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  const bool f32 = precision == GPCG_MIXED;
+// The operand of the timed products: the free set and p of the latest solve
+// (words mask[*cur]), or all points free and p = 1 before any solve.
+static gpcg_status ms_prepare(gpcg_problem* p, bool f32, cudaStream_t s, int* cur) {
   gpcg_status st;
   if (f32 && (st = ensure_mixed(p, s, true)) != GPCG_OK) return st;
-  int cur = p->have ? p->last.cur : 0;
+  *cur = p->have ? p->last.cur : 0;
   if (!p->have) {
-    // all points free, p = 1
     uint8_t* dm = nullptr;
     double* dp = nullptr;
     CK(cudaMalloc(&dm, p->n));
@@ -1907,8 +1899,84 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
     CK(cudaStreamSynchronize(s));
     cudaFree(dm);
     cudaFree(dp);
-    cur = 0;
+    *cur = 0;
   }
+  return GPCG_OK;
+}
+
+// Algorithmic bytes of one masked product: the bands and p read once, y
+// written once, the mask bits.
+static double ms_bytes(const gpcg_problem* p, bool f32) {
+  const double sv = f32 ? 4.0 : 8.0;
+  return (double)p->n * (sv * p->kc + 2.0 * sv + 0.125);
+}
+
+extern "C" gpcg_status gpcg_time_masked_spmv_stream(gpcg_problem** probs, int count,
+                                                    int precision, int reps, void* cuda_stream,
+                                                    double* ms_per_launch,
+                                                    double* bytes_per_launch) {
+  if (!probs || count < 2 || count > 64 || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  const bool f32 = precision == GPCG_MIXED;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  for (int k = 0; k < count; ++k) {
+    if (!probs[k]) return fail(GPCG_ERR_ARG, "NULL problem %d", k);
+    for (int j = 0; j < k; ++j)
+      if (probs[j] == probs[k]) return fail(GPCG_ERR_ARG, "problem %d appears twice", k);
+  }
+  std::vector<int> cur((size_t)count, 0);
+  double bytes = 0.0;
+  gpcg_status st;
+  for (int k = 0; k < count; ++k) {
+    gpcg_problem* p = probs[k];
+    if ((st = settle_now(p)) != GPCG_OK) return st;
+    if ((st = ms_prepare(p, f32, s, &cur[(size_t)k])) != GPCG_OK) return st;
+    if (!lean_spmv(p, f32))
+      return fail(GPCG_ERR_ARG, "problem %d: not a 2-D problem on the staged path", k);
+    if ((st = ms_scratch(p, s)) != GPCG_OK) return st;
+    if ((st = ms_launch(p, f32, cur[(size_t)k], s)) != GPCG_OK) return st;  // untimed
+    bytes += ms_bytes(p, f32);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // consecutive launches are distinct problems, so each may start while the
+  // previous one drains (programmatic dependent launches)
+  for (int r = 0; r < reps && st == GPCG_OK; ++r)
+    for (int k = 0; k < count && st == GPCG_OK; ++k)
+      st = ms_launch(probs[k], f32, cur[(size_t)k], s, true);
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  const cudaError_t et = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != GPCG_OK) return st;
+  if (et != cudaSuccess) return fail(GPCG_ERR_CUDA, "event timing: %s", cudaGetErrorString(et));
+  for (int k = 0; k < count; ++k)
+    if ((st = ms_check(probs[k], s, nullptr)) != GPCG_OK) return st;
+  if (ms_per_launch) *ms_per_launch = (double)ms / ((double)reps * count);
+  if (bytes_per_launch) *bytes_per_launch = bytes / count;
+  return GPCG_OK;
+}
+
+extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps,
+                                             int flush_l2, void* cuda_stream,
+                                             double* ms_per_launch, double* bytes_per_launch) {
+  if (!p || reps < 1) return fail(GPCG_ERR_ARG, "bad argument");
+  {
+    const gpcg_status ps = settle_now(p);
+    if (ps != GPCG_OK) return ps;
+  }
+  if (precision != GPCG_FP64 && precision != GPCG_MIXED)
+    return fail(GPCG_ERR_ARG, "unknown precision");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const bool f32 = precision == GPCG_MIXED;
+  gpcg_status st;
+  int cur = 0;
+  if ((st = ms_prepare(p, f32, s, &cur)) != GPCG_OK) return st;
   if (lean_spmv(p, f32)) {
     DevInst& I = p->inst;
     const int mask = cur;
@@ -1937,9 +2005,7 @@ extern "C" gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int
     if (flush) cudaFree(flush);
     if ((st = ms_check(p, s, nullptr)) != GPCG_OK) return st;
     if (ms_per_launch) *ms_per_launch = total / reps;
-    // p and y, the bands and the mask words
-    const double sv = f32 ? 4.0 : 8.0;
-    if (bytes_per_launch) *bytes_per_launch = (double)p->n * (sv * p->kc + 2.0 * sv + 0.125);
+    if (bytes_per_launch) *bytes_per_launch = ms_bytes(p, f32);
     return GPCG_OK;
   }
   // one untimed launch sets up the tables, then `reps` timed launches

@@ -1,6 +1,7 @@
 // gpcg_kernels.cu -- device side of the GB300 GPCG engine: the default
 // instantiation of the pass kernel (pass_engine.cuh), the standalone masked
 // product, the set-up kernels and the host-side launch wrappers.
+#include <cstring>
 #include <mutex>
 
 #include "pass_engine.cuh"
@@ -94,6 +95,11 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
   };
   if (tid == 0)
     for (int k = 0; k < kMsStages - 1 && k < my; ++k) issue(k);
+  // launched as a programmatic dependent of the previous product in the
+  // stream (a different problem's): the next launch may start its own
+  // prologue as this one's CTAs drain.  The operands and y are this launch's
+  // own; only the CTA partials and the counter wait for the previous launch.
+  asm volatile("griddepcontrol.launch_dependents;" :::);
   T sum = T(0);  // this thread's terms of the current chunk
   FF ffs{0.f, 0.f};
   double dsum = 0.0;
@@ -152,6 +158,8 @@ __global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
     }
   }
   // fixed-order CTA sum, then the last CTA adds the CTA partials in order
+  // (after the previous launch in the stream has finished with its own)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   double v = sizeof(T) == 4 ? ff_val(ffs) : dsum;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
@@ -218,15 +226,28 @@ static int ms_grid(int n_chunks) {
 // Launch the standalone masked product of a 2-D instance whose CG maps are
 // valid, with free-set words mask[mask]; `part` holds at least ms_max_ctas()
 // doubles.
+// With pdl the launch is a programmatic dependent of the stream's previous
+// kernel (its CTAs may start while that kernel's last CTAs run); the caller
+// guarantees that the previous kernel writes nothing this one reads.
 cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* part,
-                         unsigned* counter, double* result, int* err, cudaStream_t s) {
+                         unsigned* counter, double* result, int* err, cudaStream_t s, bool pdl) {
   const int ch = f32 ? GeoMS<float>::CH : GeoMS<double>::CH;
   MsArgs A{I.tmaps, mask, y, part, counter, result, err,
            I.nx, I.ny, I.px, I.mw, I.tiles_x, I.tiles_x * ((I.ny + ch - 1) / ch)};
   const int grid = ms_grid(A.n_chunks);
-  if (f32) mspmv_kernel<float><<<grid, kThreads, kMsSmem, s>>>(A);
-  else mspmv_kernel<double><<<grid, kThreads, kMsSmem, s>>>(A);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kMsSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (f32) return cudaLaunchKernelEx(&cfg, mspmv_kernel<float>, A);
+  return cudaLaunchKernelEx(&cfg, mspmv_kernel<double>, A);
 }
 
 int ms_max_ctas() { return ms_grid(1 << 30); }

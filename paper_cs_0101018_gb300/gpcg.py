@@ -91,6 +91,9 @@ _SIGNATURES = [
                                          C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     ("gpcg_time_masked_spmv", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("gpcg_time_masked_spmv_stream", C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int,
+                                               C.c_void_p, C.POINTER(C.c_double),
+                                               C.POINTER(C.c_double)]),
     ("gpcg_masked_spmv_noalloc", C.c_int, [C.POINTER(gpcg_stencil), C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     ("gpcg_server_create", C.c_int, [C.c_size_t, C.c_int, C.POINTER(gpcg_options),
@@ -319,6 +322,17 @@ def gpcg_time_masked_spmv(prob: Problem, precision=FP64, reps=20, flush_l2=True,
     sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     _check(load().gpcg_time_masked_spmv(prob.handle, precision, reps, int(bool(flush_l2)), sp,
                                         C.byref(ms), C.byref(by)))
+    return ms.value, by.value
+
+
+def gpcg_time_masked_spmv_stream(probs, precision=FP64, reps=10, stream=None):
+    """(ms per launch, mean algorithmic bytes per launch) of the masked
+    product in a stream of back-to-back launches over distinct problems."""
+    ms, by = C.c_double(), C.c_double()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    arr = (C.c_void_p * len(probs))(*[p.handle for p in probs])
+    _check(load().gpcg_time_masked_spmv_stream(arr, len(probs), precision, reps, sp,
+                                               C.byref(ms), C.byref(by)))
     return ms.value, by.value
 
 

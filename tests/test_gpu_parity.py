@@ -496,6 +496,41 @@ def test_masked_spmv_matches_oracle(shape, prec):
     assert np.all(y[~fm] == 0.0)
 
 
+@pytest.mark.parametrize("prec", [g.FP64, g.MIXED])
+def test_masked_spmv_stream_timing(prec):
+    """Back-to-back masked products over distinct problems (each launch may
+    start while the previous one drains) leave every problem's product state
+    sound: the next product of each still meets the oracle (a CTA partial or
+    counter clobbered by an overlapping launch would give a wrong <p, y>)."""
+    qps = [gi.grid_qp_2d(nx, ny, seed=40 + k, shift=0.1)
+           for k, (nx, ny) in enumerate(((200, 130), (256, 256), (96, 300)))]
+    probs = [g.gpcg_problem_create(qp) for qp in qps]
+    ms, by = g.gpcg_time_masked_spmv_stream(probs, prec, reps=5)
+    sv = 4.0 if prec == g.MIXED else 8.0
+    assert ms > 0.0
+    assert by == pytest.approx(np.mean([q.n * (3 * sv + 2 * sv + 0.125) for q in qps]), rel=1e-12)
+    for k, (qp, prob) in enumerate(zip(qps, probs)):
+        fm = gi.uniform(50 + k, 1, qp.n) < 0.7
+        p = gi.normal(50 + k, 2, qp.n)
+        y, pap = g.gpcg_masked_spmv(prob, fm, p, precision=prec)
+        ref = oracle.masked_matvec(qp, fm, p)
+        rtol = 1e-12 if prec == g.FP64 else 1e-5
+        assert np.isclose(pap, float(np.dot(p * fm, ref)), rtol=rtol, atol=1e-12)
+    # the timed stream itself again, after the products above
+    ms2, _ = g.gpcg_time_masked_spmv_stream(probs[::-1], prec, reps=3)
+    assert ms2 > 0.0
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_time_masked_spmv_stream(probs[:1], prec)
+    assert e.value.status == g.ERR_ARG
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_time_masked_spmv_stream([probs[0], probs[1], probs[0]], prec)
+    assert e.value.status == g.ERR_ARG
+    p3 = g.gpcg_problem_create(gi.grid_qp_3d(20, 18, 9, seed=3, shift=0.1))
+    with pytest.raises(g.GpcgError) as e:
+        g.gpcg_time_masked_spmv_stream([probs[0], p3], prec)
+    assert e.value.status == g.ERR_ARG
+
+
 def test_batch_is_bitwise_identical_to_alone():
     qps = [gi.grid_qp_2d(s, s + 3, seed=500 + s, shift=0.01,
                          bounds="two_sided" if s % 2 else "lower0") for s in (8, 33, 64, 97)]
