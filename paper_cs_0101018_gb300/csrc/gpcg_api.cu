@@ -1135,7 +1135,7 @@ static Ctl fresh_ctl() {
 // mode 0: WHILE-conditional graph whose body is kBody passes; the pass kernel
 // clears the condition once every instance is done or the pass cap is hit.
 // mode 1: a plain graph of `steps` passes replayed by the host.
-static constexpr int kBody = 8;
+static constexpr int kBody = 16;
 
 static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, unsigned cap,
                              int feat) {

@@ -3577,10 +3577,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   // shared address space)
   unsigned char* stage0 = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(stage0 + kStages * kStageBytes);
-  // the group reduction's scratch lives in the first stage (no copy is in
-  // flight between groups)
-  double(*s_sum)[kThreads] = reinterpret_cast<double(*)[kThreads]>(stage0);
-  static_assert((32 + 32) * kThreads <= kStageBytes, "reduction scratch");
 
   if (tid == 0) {
     s_inst = -1;
@@ -3874,10 +3870,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
         if (lane == 0) {
           P[k] = v;
         } else if (lane == 1) {
-          int c = 0;
+          // the counts as integers in the slots' bits (k == 3: the spare)
+          long long c = 0;
           if (k < 3)
             for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k][w];
-          P[4 + k] = (double)c;  // k == 3: the spare slot
+          P[4 + k] = __longlong_as_double(c);
         }
       }
     }
@@ -3890,59 +3887,66 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     __syncthreads();
     if (!s_last) continue;
 
-    // last group of this instance: reduce the group slots in a fixed order.
-    // Thread j loads the 7 sums of groups j and j+256 (independent loads, all
-    // in flight at once), warps reduce by butterfly, and thread k adds the 8
-    // warp results of sum k.
+    // last group of this instance: reduce the group slots in a fixed order
+    // that depends on the shape only.  Warp k < 7 takes slot k: lane j loads
+    // the slots of groups j, j+32, ... (all loads in flight at once) and adds
+    // them in that order, then a butterfly; the sums in FP64, the counts
+    // (integers in the slots' bits) in integer arithmetic.  The last warp
+    // reads the control block meanwhile.  FP64 arithmetic is slow on GB300:
+    // one FP64 add per group and slot, none for the counts.
     if (tid == 0) __threadfence();
     __syncthreads();
+    long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
+    long long* cs = reinterpret_cast<long long*>(&sC);
     {
-      static_assert(kMaxGroups <= 2 * kThreads, "finalizer covers two groups per thread");
-      double v[kNRed - 1];
-      const double* P0 = I.part;
+      static_assert(kWarps >= kNRed, "one warp per reduced slot and one for the control block");
+      constexpr int kPer = (kMaxGroups + 31) / 32;
+      if (warp == kWarps - 1) {
+        for (int j = lane; j < (int)(sizeof(Ctl) / 8); j += 32) cs[j] = __ldcg(cg + j);
+      } else if (warp < kNRed - 1) {
+        const int k = warp;
+        const double* P0 = I.part + k;
+        double v[kPer];
 #pragma unroll
-      for (int k = 0; k < kNRed - 1; ++k) {
-        const double a = tid < I.n_groups ? __ldcg(P0 + (long long)tid * kNRed + k) : 0.0;
-        const double b =
-            tid + kThreads < I.n_groups ? __ldcg(P0 + (long long)(tid + kThreads) * kNRed + k) : 0.0;
-        v[k] = a + b;
+        for (int q = 0; q < kPer; ++q) {
+          const int gi = lane + 32 * q;
+          v[q] = gi < I.n_groups ? __ldcg(P0 + (long long)gi * kNRed) : 0.0;
+        }
+        if (k < 4) {
+          double t = v[0];
+#pragma unroll
+          for (int q = 1; q < kPer; ++q) t += v[q];
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL_MASK, t, off);
+          if (lane == 0) s_red[k] = t;
+        } else {
+          int c = 0;  // at most n < 2^31 points
+#pragma unroll
+          for (int q = 0; q < kPer; ++q) c += (int)__double_as_longlong(v[q]);
+          c = __reduce_add_sync(FULL_MASK, c);
+          if (lane == 0) s_red[k] = (double)c;
+        }
       }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-        for (int k = 0; k < kNRed - 1; ++k) v[k] += __shfl_xor_sync(FULL_MASK, v[k], off);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < kNRed - 1; ++k) s_sum[0][k * kWarps + warp] = v[k];
-      }
-    }
-    __syncthreads();
-    if (tid < kNRed - 1) {
-      double v = 0.0;
-      for (int w = 0; w < kWarps; ++w) v += s_sum[0][tid * kWarps + w];
-      s_red[tid] = v;
     }
     __syncthreads();
     if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_COUNT) {
       // the groups' offsets in the compact numbering (exclusive prefix sum
       // of their free counts, two groups per thread)
+      static_assert(kMaxGroups <= 2 * kThreads, "two groups per thread");
       int t0, t1;
       const double* P0 = I.part;
-      const int c0 = tid < I.n_groups ? (int)__ldcg(P0 + (long long)tid * kNRed + 4) : 0;
+      const int c0 =
+          tid < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)tid * kNRed + 4)) : 0;
       const int o0 = cta_excl_scan(c0, s_scan, t0);
       const int g1 = tid + kThreads;
-      const int c1 = g1 < I.n_groups ? (int)__ldcg(P0 + (long long)g1 * kNRed + 4) : 0;
+      const int c1 =
+          g1 < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)g1 * kNRed + 4)) : 0;
       const int o1 = cta_excl_scan(c1, s_scan, t1);
       if (tid < I.n_groups) I.goff[tid] = o0;
       if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
     }
-    // the state machine runs on a shared copy of the control block (one
+    // the state machine runs on the shared copy of the control block (one
     // round trip in, one out, instead of dependent global accesses)
-    long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
-    long long* cs = reinterpret_cast<long long*>(&sC);
-    if (tid < (int)(sizeof(Ctl) / 8)) cs[tid] = __ldcg(cg + tid);
-    __syncthreads();
     if (tid == 0) {
       s_red[kNRed - 1] = 0.0;
       sC.arrive = 0u;
