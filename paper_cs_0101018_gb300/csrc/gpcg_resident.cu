@@ -3,10 +3,12 @@
 // inside one thread block, every pass of the engine becoming a block-level
 // phase between barriers.  The engine pays a launch, a first copy and a
 // grid-wide reduction for every pass; at this size those fixed costs are the
-// whole solve, so here every vector stays in shared memory, the reductions
-// are block reductions and the state machine is straight-line code executed
-// redundantly (and identically) by every thread.  A batch launches one CTA
-// per small instance.
+// whole solve, so here every vector stays in shared memory and the
+// reductions are block reductions.  The scalar control (FP64 on GB300: slow
+// and long-latency) runs in the controlling warp alone, which receives the
+// reduced sums and hands its decisions (a code, an index, the step lengths)
+// to the block through shared memory.  A batch launches one CTA per small
+// instance.
 //
 // The arithmetic follows Algorithm GPCG step by step: the gradient
 // projection phase (Eq. next-y with alpha0 of Eq. bqpls and the sufficient
@@ -15,8 +17,9 @@
 // cglsstop2) and the switch of Eq. cgstop3, with the termination test of Eq.
 // bqp_approximate_sol; the readings of the paper are those of the engine.  In
 // mixed precision an FP32 phase (FP32 iterate in the FP32 box, FP32 vectors
-// and bands, compensated sums reduced in FP64) precedes the FP64 phase, with
-// the same hand-over rules as the engine.
+// and bands, each thread's few terms summed in FP32 and the block reduction
+// carried in float-float) precedes the FP64 phase, with the same hand-over
+// rules as the engine.
 #include <cuda_runtime.h>
 
 #include <cstdint>
