@@ -708,21 +708,23 @@ def run_ours(args):
 
 def run_profile(args):
     """Small fixed workloads for profiler captures: `solve` runs `--steps`
-    solves of the benchmark QP, `spmv` a few launches of the masked product
+    solves of the benchmark QP (`solve3d`: of the 3-D precision-stress QP,
+    side `--side`), `spmv` a few launches of the masked product
     alone (L2 flushed before each), `spmv_stream` `--steps` rounds of
     back-to-back products over 6 distinct problems of the same shape."""
     import torch
     import paper_cs_0101018_gb300 as g
     prec = g.MIXED if args.precision == "mixed" else g.FP64
     pc = {"none": g.PRECOND_NONE, "jacobi": g.PRECOND_JACOBI, "tile": g.PRECOND_TILE}[args.precond]
-    qp = gi.single_large(args.side)
+    qp = gi.precision_stress(args.side) if args.profile == "solve3d" else gi.single_large(args.side)
     prob = g.gpcg_problem_create(qp)
-    if args.profile == "solve":
+    if args.profile in ("solve", "solve3d"):
         for _ in range(args.steps):
             g.gpcg_solve(prob, g.default_options(tau_rel=TAU_REL, precision=prec, precond=pc))
         _, st = g.gpcg_result(prob)
-        print(json.dumps({"profile": "solve", "precision": args.precision, "passes": st["passes"],
-                          "launches": st["launches"]}))
+        print(json.dumps({"profile": args.profile, "precision": args.precision,
+                          "passes": st["passes"], "launches": st["launches"],
+                          "cg_iters": st["cg_iters"]}))
     elif args.profile == "spmv_stream":
         probs = [prob] + [g.gpcg_problem_create(gi.grid_qp_2d(qp.nx, qp.ny, seed=sd, shift=1e-3,
                                                               bounds="two_sided"))
@@ -753,7 +755,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", choices=["solve", "spmv", "spmv_stream", "serve"], default=None,
+    ap.add_argument("--profile", choices=["solve", "solve3d", "spmv", "spmv_stream", "serve"],
+                    default=None,
                     help="run a small fixed workload for a profiler capture instead")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--precond", choices=["none", "jacobi", "tile"], default="none",

@@ -85,12 +85,20 @@ enum TMap : int {
   // the staged FP64 GP passes (FEAT_F64 kernels): halo boxes 68 x 10 from
   // (x0-2, y-1) of x[2], g[2], l, u, w (FP64), and b as a 64 x 8 box
   MF_X0, MF_X1, MF_G0, MF_G1, MF_L, MF_U, MF_W, MF_B,
+  // the fused CG step of 3-D grids (FP32, 8-row chunks of one plane): halo
+  // boxes 72 x 10 from (x0-4, row-1) of r[2], p[2], Ap[2]; 64 x 8 boxes of w
+  // and diag; 68 x 8 of cx from x0-4; 64 x 9 of cy from row-1; 64 x 8 boxes of
+  // cz and of r[2], p[2], Ap[2] (taken at the rows of the planes below and
+  // above: row -+ ny)
+  M3_RH0, M3_RH1, M3_PH0, M3_PH1, M3_APH0, M3_APH1, M3_W, M3_D, M3_CX, M3_CY, M3_CZ,
+  M3_R0, M3_R1, M3_P0, M3_P1, M3_AP0, M3_AP1,
   M_COUNT
 };
 constexpr int kGpMaps = M_MASK0 - MG_X32H0;  // the GP maps (make_gp_maps encodes them)
 constexpr int kCgMaps = M64_RH0 - M32_RH0;  // maps of one precision's CG passes
 constexpr int kCgBase = M32_FZH0 - M32_RH0;  // of which make_maps encodes the first kCgBase
 constexpr int kTileMaps = kCgMaps - kCgBase;  // and the tile preconditioner's the rest
+constexpr int k3dMaps = M3_AP1 - M3_RH0 + 1;  // the 3-D fused step's maps
 
 enum Pass : int {
   P_NONE = 0,
@@ -100,7 +108,7 @@ enum Pass : int {
   P_TRIAL = 4,     // trial point P[x + alpha*dir] with gradient and census
   P_CG_B = 5,      // p = -r + beta p; Ap = A_FF p; <p, Ap>
   P_CG_A = 6,      // w += alpha p; r += alpha Ap; ||r||^2
-  P_CG_F = 7,      // fused CG step (2-D, staged): r += alpha Ap, w += alpha p,
+  P_CG_F = 7,      // fused CG step (staged; 3-D: FP32 only): r += alpha Ap, w += alpha p,
                    // p = -r + beta p, Ap = A_FF p; ||r||^2, <p,Ap>, <r,Ap>, ||Ap||^2
   P_CG_Z = 8,      // first step of a tile-preconditioned CG phase: r = g_F,
                    // z = M^-1 r, <r, z>; p, Ap, q = M^-1 Ap and w set to 0
@@ -191,7 +199,8 @@ struct DevInst {
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
   int tma64, tma32;        // the FP64 / FP32 CG maps are valid
   int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid
-  int tma_f64gp, pad_f;    // the FP64 alpha0 maps are valid
+  int tma_f64gp;           // the FP64 alpha0 maps are valid
+  int tma3;                // the 3-D fused step's maps (FP32) are valid
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   const double* dinv;      // 1/diag (0 in pad columns): the point-Jacobi preconditioner

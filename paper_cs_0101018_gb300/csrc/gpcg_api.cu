@@ -369,6 +369,7 @@ static void carve64(gpcg_problem* p) {
   I.tma32 = 0;
   I.tma_gp = 0;
   I.tma_mask = 0;
+  I.tma3 = 0;
   I.x0 = I.r64[0];  // a given start point is staged in r (unused until CG starts)
 }
 
@@ -452,6 +453,23 @@ static bool make_maps(gpcg_problem* p, bool f32, cudaStream_t s) {
       // 1/diag: FDIH, ADI
       e(di, 64 + 2 * h, f + 2) && e(di, 64, a);
   return ok && q == m + kCgBase && put_maps(p, b0, kCgBase, s);
+}
+
+// Encode the maps of the 3-D fused CG step (FP32; box shapes of GeoF3 in the
+// kernels) and copy them to the problem's device area.
+static bool make_3d_maps(gpcg_problem* p, cudaStream_t s) {
+  if (!have_encode() || p->dim != 3) return false;
+  DevInst& I = p->inst;
+  CUtensorMap* m = &p->hmaps[M3_RH0];
+  CUtensorMap* q = m;
+  auto e = [&](const float* a, int bw, int bh) { return encode_map(q++, true, a, p, bw, bh); };
+  const bool ok = e(I.r32[0], 72, 10) && e(I.r32[1], 72, 10) && e(I.p32[0], 72, 10) &&
+                  e(I.p32[1], 72, 10) && e(I.Ap32[0], 72, 10) && e(I.Ap32[1], 72, 10) &&
+                  e(I.w32, 64, 8) && e(I.diag32, 64, 8) && e(I.cx32, 68, 8) &&
+                  e(I.cy32, 64, 9) && e(I.cz32, 64, 8) && e(I.r32[0], 64, 8) &&
+                  e(I.r32[1], 64, 8) && e(I.p32[0], 64, 8) && e(I.p32[1], 64, 8) &&
+                  e(I.Ap32[0], 64, 8) && e(I.Ap32[1], 64, 8);
+  return ok && q == m + k3dMaps && put_maps(p, M3_RH0, k3dMaps, s);
 }
 
 // Encode the maps of the mixed-phase gradient-projection passes (2-D only:
@@ -586,6 +604,7 @@ static gpcg_status ensure_mixed(gpcg_problem* p, cudaStream_t s, bool init) {
   }
   I.tma32 = (I.tma_mask && make_maps(p, true, s)) ? 1 : 0;
   I.tma_gp = (I.tma_mask && make_gp_maps(p, s)) ? 1 : 0;
+  I.tma3 = (I.tma32 && make_3d_maps(p, s)) ? 1 : 0;
   return GPCG_OK;
 }
 

@@ -1535,7 +1535,11 @@ __device__ void start_search(Ctl& C, int dir) {
 // Whether the instance's CG phase runs fused steps (P_CG_F): 2-D grids whose
 // tensor maps of the CG precision are valid (and, under the tile preconditioner, its maps).
 __device__ __forceinline__ bool cg_fused(const DevInst& I, const Ctl& C) {
-  if (I.dim != 2 || I.tmaps == nullptr || !(C.cg32 ? I.tma32 : I.tma64)) return false;
+  if (I.tmaps == nullptr) return false;
+  // 3-D: the FP32 step without a preconditioner (its stage has no room for
+  // FP64 boxes or for 1/diag of three planes)
+  if (I.dim == 3) return C.cg32 && I.tma3 && I.opt.precond == PC_NONE;
+  if (I.dim != 2 || !(C.cg32 ? I.tma32 : I.tma64)) return false;
   return I.opt.precond != PC_TILE || ((I.tma_tile >> (C.cg32 ? 1 : 0)) & 1);
 }
 
@@ -2132,6 +2136,158 @@ __device__ __forceinline__ void issue_cgf(const DevInst& I, int pcur, int x0, in
   tma_load2d(st + G::OFF_D, tmap(I, o + M32_FD), x0, yc, bar);
   tma_load2d(st + G::OFF_CX, tmap(I, o + M32_FCX), x0 - G::H, yc, bar);
   tma_load2d(st + G::OFF_CY, tmap(I, o + M32_FCY), x0, yc - 1, bar);
+}
+
+// The fused CG step on a 3-D grid (FP32): 8-row chunks of one plane, one row
+// per warp.  Stage layout: RH | PH | APH (72 x 10 from (x0-4, row-1)) | W | D
+// (64 x 8) | CX (68 x 8 from x0-4) | CY (64 x 9 from row-1) | CZD | CZU (cz of
+// the plane below and of this plane) | RD | RU | PD | PU | APD | APU (r, p, Ap
+// of the planes below and above), all 64 x 8 unless stated.  In the row space
+// (nx, ny*nz) of the maps, the halo rows of a plane's first and last chunk
+// rows are rows of the neighbouring planes; their couplings cy are zero (the
+// last row of every plane has none), so they contribute nothing.  The planes
+// below the first and above the last are out of range: zero-filled.
+struct GeoF3 {
+  static constexpr int H = 4, CH = 8, BW = 64 + 2 * H;
+  static constexpr int SZ_H = align128((CH + 2) * BW * 4);
+  static constexpr int SZ_I = 64 * CH * 4;
+  static constexpr int OFF_R = 0, OFF_P = SZ_H, OFF_AP = 2 * SZ_H;
+  static constexpr int OFF_W = 3 * SZ_H, OFF_D = OFF_W + SZ_I, OFF_CX = OFF_D + SZ_I;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
+  static constexpr int OFF_CZD = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr int OFF_CZU = OFF_CZD + SZ_I;
+  static constexpr int OFF_RD = OFF_CZU + SZ_I, OFF_RU = OFF_RD + SZ_I;
+  static constexpr int OFF_PD = OFF_RU + SZ_I, OFF_PU = OFF_PD + SZ_I;
+  static constexpr int OFF_APD = OFF_PU + SZ_I, OFF_APU = OFF_APD + SZ_I;
+  static constexpr int END = OFF_APU + SZ_I;
+  static constexpr unsigned TX =
+      (3 * (CH + 2) * BW + 2 * 64 * CH + (64 + H) * CH + 64 * (CH + 1) + 8 * 64 * CH) * 4;
+};
+static_assert(GeoF3::END <= kOffMask && GeoF3::CH == kWarps, "stage layout (one row per warp)");
+
+// row: the chunk's first row in the row space (z * ny + yc).
+__device__ __forceinline__ void issue_cgf3(const DevInst& I, int pcur, int x0, int row,
+                                           unsigned st, unsigned bar) {
+  using G = GeoF3;
+  const int dn = row - I.ny, up = row + I.ny;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_R, tmap(I, M3_RH0 + pcur), x0 - G::H, row - 1, bar);
+  tma_load2d(st + G::OFF_P, tmap(I, M3_PH0 + pcur), x0 - G::H, row - 1, bar);
+  tma_load2d(st + G::OFF_AP, tmap(I, M3_APH0 + pcur), x0 - G::H, row - 1, bar);
+  tma_load2d(st + G::OFF_W, tmap(I, M3_W), x0, row, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M3_D), x0, row, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M3_CX), x0 - G::H, row, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M3_CY), x0, row - 1, bar);
+  tma_load2d(st + G::OFF_CZD, tmap(I, M3_CZ), x0, dn, bar);
+  tma_load2d(st + G::OFF_CZU, tmap(I, M3_CZ), x0, row, bar);
+  tma_load2d(st + G::OFF_RD, tmap(I, M3_R0 + pcur), x0, dn, bar);
+  tma_load2d(st + G::OFF_RU, tmap(I, M3_R0 + pcur), x0, up, bar);
+  tma_load2d(st + G::OFF_PD, tmap(I, M3_P0 + pcur), x0, dn, bar);
+  tma_load2d(st + G::OFF_PU, tmap(I, M3_P0 + pcur), x0, up, bar);
+  tma_load2d(st + G::OFF_APD, tmap(I, M3_AP0 + pcur), x0, dn, bar);
+  tma_load2d(st + G::OFF_APU, tmap(I, M3_AP0 + pcur), x0, up, bar);
+}
+
+// P_CG_F on one staged chunk of a 3-D grid (FP32): the 2-D step's arithmetic
+// (sums [0] ||r_j||^2, [1] <p_j,Ap_j>, [2] <r_j,Ap_j>, [3] ||Ap_j||^2) with
+// the couplings to the planes below and above, whose p_j each lane forms at
+// its two points from their staged r, p, Ap.  row0: the chunk's first row in
+// the row space; yc: in its plane.
+__device__ __forceinline__ void cgf3_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                           int row0, int yc, int rows, float alpha, float beta,
+                                           const unsigned* fbits, float* w, float* r_out,
+                                           float* p_out, float* ap_out, FF* ff) {
+  using G = GeoF3;
+  const float* R = reinterpret_cast<const float*>(st + G::OFF_R);
+  const float* P = reinterpret_cast<const float*>(st + G::OFF_P);
+  const float* AP = reinterpret_cast<const float*>(st + G::OFF_AP);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int ry = warp;
+  if (ry >= ylim) return;  // warp-uniform
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  // rows ry-1, ry, ry+1 of the chunk (box rows ry .. ry+2)
+  float pn[3][2], rn[2], po[2];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int b = (ry + q) * G::BW + G::H + c;
+    const float2 rv = *reinterpret_cast<const float2*>(R + b);
+    const float2 pv = *reinterpret_cast<const float2*>(P + b);
+    const float2 av = *reinterpret_cast<const float2*>(AP + b);
+    const float ra = fmaf(alpha, av.x, rv.x), rb = fmaf(alpha, av.y, rv.y);
+    pn[q][0] = fmaf(beta, pv.x, -ra);
+    pn[q][1] = fmaf(beta, pv.y, -rb);
+    if (q == 1) {
+      rn[0] = ra;
+      rn[1] = rb;
+      po[0] = pv.x;
+      po[1] = pv.y;
+    }
+  }
+  float pw = __shfl_up_sync(FULL_MASK, pn[1][1], 1);
+  float pe = __shfl_down_sync(FULL_MASK, pn[1][0], 1);
+  {
+    const int b = (ry + 1) * G::BW + G::H + c;
+    if (lane == 0) pw = fmaf(beta, P[b - 1], -fmaf(alpha, AP[b - 1], R[b - 1]));
+    if (lane == 31) pe = fmaf(beta, P[b + 2], -fmaf(alpha, AP[b + 2], R[b + 2]));
+  }
+  // p_j of the planes below (d) and above (u) at the lane's points
+  const int bi = ry * 64 + c;
+  auto plane_p = [&](int o_r, int o_p, int o_a, float out[2]) {
+    const float2 rv = *reinterpret_cast<const float2*>(st + o_r + 4 * bi);
+    const float2 pv = *reinterpret_cast<const float2*>(st + o_p + 4 * bi);
+    const float2 av = *reinterpret_cast<const float2*>(st + o_a + 4 * bi);
+    out[0] = fmaf(beta, pv.x, -fmaf(alpha, av.x, rv.x));
+    out[1] = fmaf(beta, pv.y, -fmaf(alpha, av.y, rv.y));
+  };
+  float pd[2], pu[2];
+  plane_p(G::OFF_RD, G::OFF_PD, G::OFF_APD, pd);
+  plane_p(G::OFF_RU, G::OFF_PU, G::OFF_APU, pu);
+  const float* Dr = reinterpret_cast<const float*>(st + G::OFF_D) + bi;
+  const float* Xr = reinterpret_cast<const float*>(st + G::OFF_CX) + ry * (64 + G::H) + G::H + c;
+  const float* Ys = reinterpret_cast<const float*>(st + G::OFF_CY) + bi;
+  const float* Yn = Ys + 64;
+  const float* Zd = reinterpret_cast<const float*>(st + G::OFF_CZD) + bi;
+  const float* Zu = reinterpret_cast<const float*>(st + G::OFF_CZU) + bi;
+  // diag, west, east, south, north, down, up (the order of the register sweep)
+  float a0 = Dr[0] * pn[1][0];
+  a0 = fmaf(Xr[-1], pw, a0);
+  a0 = fmaf(Xr[0], pn[1][1], a0);
+  a0 = fmaf(Ys[0], pn[0][0], a0);
+  a0 = fmaf(Yn[0], pn[2][0], a0);
+  a0 = fmaf(Zd[0], pd[0], a0);
+  a0 = fmaf(Zu[0], pu[0], a0);
+  float a1 = Dr[1] * pn[1][1];
+  a1 = fmaf(Xr[0], pn[1][0], a1);
+  a1 = fmaf(Xr[1], pe, a1);
+  a1 = fmaf(Ys[1], pn[0][1], a1);
+  a1 = fmaf(Yn[1], pn[2][1], a1);
+  a1 = fmaf(Zd[1], pd[1], a1);
+  a1 = fmaf(Zu[1], pu[1], a1);
+  const unsigned fb = fbits[0] & 3u;
+  a0 = (fb & 1u) ? a0 : 0.0f;
+  a1 = (fb & 2u) ? a1 : 0.0f;
+  const float2 wv = *reinterpret_cast<const float2*>(st + G::OFF_W + 4 * bi);
+  const long long i = (long long)(row0 + ry) * I.px + e0;
+  st2(w, i, v0, v1, fmaf(alpha, po[0], wv.x), fmaf(alpha, po[1], wv.y));
+  st2(r_out, i, v0, v1, rn[0], rn[1]);
+  st2(p_out, i, v0, v1, pn[1][0], pn[1][1]);
+  st2(ap_out, i, v0, v1, a0, a1);
+  // points past nx hold zeros (the boxes are zero-filled there)
+  float s_rr = rn[0] * rn[0];
+  s_rr = fmaf(rn[1], rn[1], s_rr);
+  float s_pap = pn[1][0] * a0;
+  s_pap = fmaf(pn[1][1], a1, s_pap);
+  float s_rap = rn[0] * a0;
+  s_rap = fmaf(rn[1], a1, s_rap);
+  float s_apap = a0 * a0;
+  s_apap = fmaf(a1, a1, s_apap);
+  ff_acc(ff[0], s_rr);
+  ff_acc(ff[1], s_pap);
+  ff_acc(ff[2], s_rap);
+  ff_acc(ff[3], s_apap);
 }
 
 // P_CG_F, FP64 (one row per warp): r_j and p_j are formed once per element
@@ -3192,11 +3348,12 @@ __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
 }
 
 // Rows per chunk of the item's TMA pass.
-__device__ __forceinline__ int chunk_rows(const Snap& S, bool gp) {
+__device__ __forceinline__ int chunk_rows(const DevInst& I, const Snap& S, bool gp) {
   if (gp) return S.pass == P_GP_ALPHA ? ChunkGeo<float>::CH : GeoGP::CH;
   if (S.pass == P_GP_ALPHA) return GeoA64::CH;  // the staged FP64 GP passes
   if (S.pass == P_TRIAL) return GeoT64::CH;
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
+  if (S.pass == P_CG_F && I.dim == 3) return GeoF3::CH;
   if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
 }
@@ -3296,6 +3453,8 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
       if (S.cg32) issue_cgt<float>(I, S.pcur, c.x0, c.yc, st, bar);
       else issue_cgt<double>(I, S.pcur, c.x0, c.yc, st, bar);
     }
+  } else if (S.pass == P_CG_F && I.dim == 3) {
+    issue_cgf3(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);  // FP32 only (cg_fused)
   } else if (S.pass == P_CG_F) {
     if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
@@ -3352,6 +3511,10 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
         cgt_chunk<double>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
                           I.z64[q], I.p64[q], I.Ap64[q], I.q64[q], acc, ffs);
     }
+  } else if (S.pass == P_CG_F && I.dim == 3) {
+    const int q = S.pcur ^ 1;
+    cgf3_chunk(I, st, c.x0, c.z * I.ny + c.yc, c.yc, c.rows, (float)S.alpha, (float)S.beta,
+               fbits, I.w32, I.r32[q], I.p32[q], I.Ap32[q], ffs);
   } else if (S.pass == P_CG_F) {
     const int q = S.pcur ^ 1;
     const bool jac = I.opt.precond == PC_JACOBI;
@@ -3754,7 +3917,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
       static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
       const bool gp = gp_tma(I, S);
       const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
-      const int ch = chunk_rows(S, gp);
+      const int ch = chunk_rows(I, S, gp);
       const int rpw = ch / kWarps;
       // chunks that write to their stage (and have block barriers inside)
       const bool writes_stage =

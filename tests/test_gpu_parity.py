@@ -153,6 +153,25 @@ def test_mixed_matches_oracle(k, refine, path):
     assert np.sqrt(c.pg_norm2) <= st["tau"] * (1 + 1e-9) + 1e-300
 
 
+def test_3d_cg_steps_take_one_pass_in_fp32():
+    """3-D grids: the FP32 CG phases of a mixed solve run the staged fused
+    step, one pass per CG step (a phase costs its steps plus its first step's
+    and its last completion pass); FP64 CG steps take two passes (P_CG_B,
+    P_CG_A).  The result meets the oracle either way."""
+    qp = gi.precision_stress(24)
+    ref = oracle.solve(qp, tau_rel=1e-10)
+    for prec, tol in ((g.MIXED, 1e-5), (g.FP64, 1e-9)):
+        status, x, st = _solve_on("engine", qp, tau_rel=1e-10, precision=prec)
+        assert status == 0
+        assert _rel_err(x, ref.x) <= tol
+        other = st["outer_iters"] + st["gp_iters"] + st["ls_trials"]
+        assert st["cg_iters"] >= 500
+        if prec == g.MIXED:
+            assert st["passes"] <= 1.2 * st["cg_iters"] + 3 * other + 10, st
+        else:
+            assert st["passes"] >= 1.9 * st["cg_iters"], st
+
+
 JACOBI = [PROBLEMS[k] for k in (0, 2, 5, 10, 14, 20, 24, 26, 28, 29, 30)]
 
 
