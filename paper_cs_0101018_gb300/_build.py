@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpcg.so")
 SOURCES = ["gpcg_kernels.cu", "gpcg_pass_tile.cu", "gpcg_pass_rx.cu", "gpcg_pass_f64.cu",
-           "gpcg_api.cu", "gpcg_noalloc.cu", "gpcg_resident.cu"]
+           "gpcg_pass_3d.cu", "gpcg_api.cu", "gpcg_noalloc.cu", "gpcg_resident.cu"]
 HEADERS = ["engine.h", "pass_engine.cuh", "tuned.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -127,7 +127,7 @@ constexpr int kMaxNb = 6;
 
 // Optional pass families, compiled into their own instantiations of the
 // pass kernel so that the default kernel carries none of their code.
-enum Feature : int { FEAT_TILE = 1, FEAT_EXT = 2, FEAT_F64 = 4 };
+enum Feature : int { FEAT_TILE = 1, FEAT_EXT = 2, FEAT_F64 = 4, FEAT_3D = 8 };
 
 // Preconditioners of the CG phase (Opts.precond; the public gpcg_precond).
 enum Precond : int { PC_NONE = 0, PC_JACOBI = 1, PC_TILE = 2 };
@@ -200,7 +200,8 @@ struct DevInst {
   int tma64, tma32;        // the FP64 / FP32 CG maps are valid
   int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid
   int tma_f64gp;           // the FP64 alpha0 maps are valid
-  int tma3;                // the 3-D fused step's maps (FP32) are valid
+  int tma3;                // the 3-D fused step's maps (FP32) are valid, and this launch's
+                           // kernel has the step (FEAT_3D; the host clears it otherwise)
   const double *diag, *cx, *cy, *cz, *b, *l, *u, *x0;
   const float *diag32, *cx32, *cy32, *cz32;
   const double* dinv;      // 1/diag (0 in pad columns): the point-Jacobi preconditioner

@@ -1131,11 +1131,14 @@ static Opts make_opts(const gpcg_options* o, double c, bool use_x0) {
   return r;
 }
 
-// The pass kernel instantiation a solve with these options needs.
-static int feature_set(const gpcg_options* o) {
+// The pass kernel instantiation a solve with these options needs; `any3d`:
+// the launch has 3-D instances (a mixed solve without preconditioner then
+// takes the kernel with the fused 3-D step).
+static int feature_set(const gpcg_options* o, bool any3d) {
   if (o->precond == GPCG_PRECOND_TILE) return FEAT_TILE;
   if (o->cg_system == GPCG_CG_EXTRACTED) return FEAT_EXT;
   if (o->precision == GPCG_FP64) return FEAT_F64;
+  if (any3d && o->precond == GPCG_PRECOND_NONE) return FEAT_3D;
   return 0;
 }
 
@@ -1413,9 +1416,13 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
       }
   }
   const bool extract = o->cg_system == GPCG_CG_EXTRACTED;
+  bool any3d = false;
+  for (int k = 0; k < count; ++k) any3d |= !resident[k] && probs[k]->dim == 3;
+  const int feat = feature_set(o, any3d);
   for (int k = 0; k < count; ++k) {
     if ((st = prepare_instance(probs[k], o, s, &insts[k])) != GPCG_OK) return st;
     if (resident[k]) continue;
+    if ((feat & FEAT_3D) == 0) insts[k].tma3 = 0;  // this launch's kernel lacks the 3-D step
     // work items of `span` consecutive groups (their sums stay per group)
     const int span = item_span(probs[k], tiles, extract);
     insts[k].span = span;
@@ -1435,7 +1442,7 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   }
   gpcg_status run = GPCG_OK;
   sc.h_pin[1] = 0;
-  if (n_eng > 0) run = run_engine(sc, n_eng, tiles, s, feature_set(o));
+  if (n_eng > 0) run = run_engine(sc, n_eng, tiles, s, feat);
   if (run != GPCG_OK && run != GPCG_ERR_TIMEOUT) return run;
   CK(cudaMemcpyAsync(ctl.data(), sc.d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -2440,7 +2447,9 @@ extern "C" gpcg_status gpcg_server_step(gpcg_server* s, int passes) {
     if (st != GPCG_OK) return st;
     s->sc.h_pin[0] = live;
     CK(cudaMemcpyAsync(s->sc.d_live, &s->sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, st_));
-    st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu, feature_set(&s->opt));
+    // a server may admit 3-D requests at any time: its kernel has the fused
+    // 3-D step whenever its options allow it
+    st = get_graph(s->sc, s->tiles, 1, passes, 0xffffffffu, feature_set(&s->opt, true));
     if (st != GPCG_OK) return st;
     CK(cudaEventRecord(s->ev_start, st_));
     CK(cudaGraphLaunch(s->sc.gexec, st_));

@@ -394,6 +394,7 @@ template __global__ void pass_kernel<false, 0>(EngineArgs);
 const void* pass_kernel_ptr_tile(bool cond);
 const void* pass_kernel_ptr_rx(bool cond);
 const void* pass_kernel_ptr_f64(bool cond);
+const void* pass_kernel_ptr_3d(bool cond);
 
 // The pass kernel for a feature set (0, FEAT_TILE, FEAT_EXT or FEAT_F64); `cond`: the
 // instantiation that may clear a WHILE graph's condition.
@@ -401,6 +402,7 @@ const void* pass_kernel_ptr(bool cond, int feat) {
   if (feat == FEAT_TILE) return pass_kernel_ptr_tile(cond);
   if (feat == FEAT_EXT) return pass_kernel_ptr_rx(cond);
   if (feat == FEAT_F64) return pass_kernel_ptr_f64(cond);
+  if (feat == FEAT_3D) return pass_kernel_ptr_3d(cond);
   return cond ? (const void*)pass_kernel<true, 0> : (const void*)pass_kernel<false, 0>;
 }
 
@@ -415,7 +417,7 @@ int pass_grid(int n_work) {
     if (!cached[dev]) {
       int sms = 0, per = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64})
+      for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64, (int)FEAT_3D})
         for (bool cond : {true, false})
           cudaFuncSetAttribute(pass_kernel_ptr(cond, feat),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);

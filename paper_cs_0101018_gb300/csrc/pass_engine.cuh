@@ -3454,7 +3454,8 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
       else issue_cgt<double>(I, S.pcur, c.x0, c.yc, st, bar);
     }
   } else if (S.pass == P_CG_F && I.dim == 3) {
-    issue_cgf3(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);  // FP32 only (cg_fused)
+    // FP32 only, and only scheduled in a FEAT_3D kernel (cg_fused)
+    if constexpr ((kFeat & FEAT_3D) != 0) issue_cgf3(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
   } else if (S.pass == P_CG_F) {
     if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
@@ -3512,9 +3513,11 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
                           I.z64[q], I.p64[q], I.Ap64[q], I.q64[q], acc, ffs);
     }
   } else if (S.pass == P_CG_F && I.dim == 3) {
-    const int q = S.pcur ^ 1;
-    cgf3_chunk(I, st, c.x0, c.z * I.ny + c.yc, c.yc, c.rows, (float)S.alpha, (float)S.beta,
-               fbits, I.w32, I.r32[q], I.p32[q], I.Ap32[q], ffs);
+    if constexpr ((kFeat & FEAT_3D) != 0) {
+      const int q = S.pcur ^ 1;
+      cgf3_chunk(I, st, c.x0, c.z * I.ny + c.yc, c.yc, c.rows, (float)S.alpha, (float)S.beta,
+                 fbits, I.w32, I.r32[q], I.p32[q], I.Ap32[q], ffs);
+    }
   } else if (S.pass == P_CG_F) {
     const int q = S.pcur ^ 1;
     const bool jac = I.opt.precond == PC_JACOBI;
@@ -3716,7 +3719,9 @@ template <int kFeat>
 __device__ __forceinline__ bool pass_supported(const DevInst& I, const Snap& S) {
   const bool tile = S.pass == P_CG_Z || (S.pass == P_CG_F && I.opt.precond == PC_TILE);
   const bool ext = S.pass >= P_RX_COUNT && S.pass <= P_RW;
-  return (!tile || (kFeat & FEAT_TILE) != 0) && (!ext || (kFeat & FEAT_EXT) != 0);
+  const bool f3 = S.pass == P_CG_F && I.dim == 3;
+  return (!tile || (kFeat & FEAT_TILE) != 0) && (!ext || (kFeat & FEAT_EXT) != 0) &&
+         (!f3 || (kFeat & FEAT_3D) != 0);
 }
 
 template <bool kCond, int kFeat>
