@@ -338,9 +338,11 @@ gpcg_status gpcg_time_masked_spmv(gpcg_problem* p, int precision, int reps, int 
  * and <p_F, y_F>) in a stream of launches, as an iterative method issues
  * them: `count` distinct problems (2 <= count <= 64, 2-D, on the staged
  * path) are multiplied in turn, `reps` rounds, back to back on the given
- * stream.  Each launch may start while the previous one (another problem's)
- * drains: launch latency and the final reduction's tail overlap the stream's
- * other work instead of adding to each launch.  With distinct problems whose
+ * stream.  Each launch takes one CTA per SM and waits for the previous one
+ * (another problem's) only before its final sum, so up to three consecutive
+ * products stream at the same time: launch latency, the first copies and the
+ * final reduction's tail overlap the stream's other work instead of adding to
+ * each launch.  With distinct problems whose
  * operands together exceed the L2 cache, every launch streams its operands
  * from HBM.  The operand of each problem is that of gpcg_time_masked_spmv
  * (the latest solve's free set and p, else all points free and p = 1); one

@@ -1,6 +1,7 @@
 // gpcg_kernels.cu -- device side of the GB300 GPCG engine: the default
 // instantiation of the pass kernel (pass_engine.cuh), the standalone masked
 // product, the set-up kernels and the host-side launch wrappers.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -33,6 +34,7 @@ struct GeoMS {
       ((CH + 2) * BW + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * sizeof(T) + kMaskBox;
 };
 constexpr int kMsStage = GeoMS<float>::END > GeoMS<double>::END ? GeoMS<float>::END : GeoMS<double>::END;
+constexpr int kMsCtasPerSm = 3;  // the launch bounds below
 constexpr int kMsSmem = kMsStages * kMsStage + 128 + 8 * kMsStages;
 
 struct MsArgs {
@@ -47,7 +49,7 @@ struct MsArgs {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, 3) mspmv_kernel(MsArgs A) {
+__global__ void __launch_bounds__(kThreads, kMsCtasPerSm) mspmv_kernel(MsArgs A) {
   using G = GeoMS<T>;
   constexpr int RPW = G::CH / kWarps;
   extern __shared__ unsigned char dyn_smem[];
@@ -234,7 +236,12 @@ cudaError_t launch_mspmv(const DevInst& I, bool f32, int mask, void* y, double* 
   const int ch = f32 ? GeoMS<float>::CH : GeoMS<double>::CH;
   MsArgs A{I.tmaps, mask, y, part, counter, result, err,
            I.nx, I.ny, I.px, I.mw, I.tiles_x, I.tiles_x * ((I.ny + ch - 1) / ch)};
-  const int grid = ms_grid(A.n_chunks);
+  // in a stream of products each launch takes one CTA per SM (a third of
+  // what the GPU holds at once): its CTAs wait for the previous launch only
+  // before their CTA sums, so up to three consecutive products stream at the
+  // same time and the copies of one cover the start and the tail of another
+  int grid = ms_grid(A.n_chunks);
+  if (pdl) grid = std::max(1, std::min(grid, ms_grid(1 << 30) / kMsCtasPerSm));
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)grid);
