@@ -129,35 +129,39 @@ __device__ __forceinline__ void block_reduce(Sum<double> (&s)[K], int (&c)[M], R
   for (int m = 0; m < M; ++m) cnt[m] = __reduce_add_sync(kFull, lane < kRWarps ? Q[m * kRWarps + lane] : 0);
 }
 
-template <int K, int M>
+// The FP32 phases: each warp adds its lanes' FP32 sums (a few terms each)
+// by an FP32 butterfly, and the controlling warp adds the warps' sums in
+// float-float (the engine likewise folds short FP32 sums into float-float
+// accumulators); tot receives hi + lo in FP64, or in FP32 for the FP32 CG
+// steps, whose step lengths are FP32 (TT = float).
+template <int K, int M, class TT>
 __device__ __forceinline__ void block_reduce(Sum<float> (&s)[K], int (&c)[M], Red& R,
-                                             double (&tot)[K], int (&cnt)[M]) {
+                                             TT (&tot)[K], int (&cnt)[M]) {
   static_assert(K <= kRSums && M <= kRCnts, "reduction scratch");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float2* P = reinterpret_cast<float2*>(R.part) + R.flip * kRSums * kRWarps;
   int* Q = R.ipart + R.flip * kRCnts * kRWarps;
   R.flip ^= 1;
-  F2 v[K];
+  float u[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = F2{s[k].v, 0.0f};
+  for (int k = 0; k < K; ++k) u[k] = s[k].v;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-      v[k] = f2_add(v[k], F2{__shfl_xor_sync(kFull, v[k].hi, off),
-                             __shfl_xor_sync(kFull, v[k].lo, off)});
+    for (int k = 0; k < K; ++k) u[k] += __shfl_xor_sync(kFull, u[k], off);
   }
   int w[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) w[m] = __reduce_add_sync(kFull, c[m]);
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) P[k * kRWarps + warp] = make_float2(v[k].hi, v[k].lo);
+    for (int k = 0; k < K; ++k) P[k * kRWarps + warp] = make_float2(u[k], 0.0f);
 #pragma unroll
     for (int m = 0; m < M; ++m) Q[m * kRWarps + warp] = w[m];
   }
   __syncthreads();
   if (warp != 0) return;  // the controlling warp reduces the warps' partials
+  F2 v[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float2 t = lane < kRWarps ? P[k * kRWarps + lane] : make_float2(0.0f, 0.0f);
@@ -171,7 +175,10 @@ __device__ __forceinline__ void block_reduce(Sum<float> (&s)[K], int (&c)[M], Re
                              __shfl_xor_sync(kFull, v[k].lo, off)});
   }
 #pragma unroll
-  for (int k = 0; k < K; ++k) tot[k] = (double)v[k].hi + (double)v[k].lo;
+  for (int k = 0; k < K; ++k) {
+    if constexpr (sizeof(TT) == 4) tot[k] = v[k].hi + v[k].lo;
+    else tot[k] = (double)v[k].hi + (double)v[k].lo;
+  }
 #pragma unroll
   for (int m = 0; m < M; ++m) cnt[m] = __reduce_add_sync(kFull, lane < kRWarps ? Q[m * kRWarps + lane] : 0);
 }
@@ -258,6 +265,10 @@ struct Bc {
 
 __device__ __forceinline__ Bc mk(int code, double a = 0.0, double b = 0.0) {
   return Bc{code, 0, a, b, (float)a, (float)b};
+}
+// A decision whose step lengths are FP32 only (the FP32 CG steps).
+__device__ __forceinline__ Bc mkf(int code, float a, float b) {
+  return Bc{code, 0, 0.0, 0.0, a, b};
 }
 
 // Runs f in the controlling warp and publishes its result to the block.
@@ -524,6 +535,8 @@ __device__ bool cg_phase(const Vecs<T>& V, Vecs<TC>& C, const Own& O, Red& R, Bc
     C.w[i] = TC(0);
   }
   double cdmax = 0.0;  // controlling warp
+  float cdmaxf = 0.0f;  // (FP32 steps)
+  const float eta2f = (float)S.eta2;
   TC alpha = TC(0), beta = TC(0);
   *empty = o.max_cg < 1;
   if (*empty) return true;
@@ -557,9 +570,29 @@ __device__ bool cg_phase(const Vecs<T>& V, Vecs<TC>& C, const Own& O, Red& R, Bc
       a[2].fma(z, ap);
       a[3].fma(ap, jac ? ap * C.dinv[i] : ap);
     }
+    Bc d;
+    if constexpr (sizeof(TC) == 4) {
+      // FP32 steps: the step lengths are FP32 numbers, and so is their
+      // control (an FP64 division alone takes over a thousand cycles on
+      // GB300, at every step of a latency-bound solve)
+      float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      block_reduce(a, c, R, t, n);
+      d = decide(bc, S, [&] {
+        const float rho = t[0], pAp = t[1];
+        if (j == 0 && !(rho > 0.0f)) return mk(D_EMPTY);  // r = g_F vanished
+        if (!(pAp > 0.0f)) return mk(D_FAIL);
+        const float al = rho / pAp, inv_rho = 1.0f / rho;
+        const float rho_next = fmaf(al * al, t[3], fmaf(2.0f * al, t[2], rho));
+        const float delta = 0.5f * al * rho;  // q_k(w_j) - q_k(w_{j+1})
+        const bool stop = (j >= 1 && delta <= eta2f * cdmaxf) ||  // Eq. cgstop1 (steps 2, 3, ...)
+                          rho_next <= 0.0f || j + 1 >= o.max_cg;
+        if (delta > cdmaxf) cdmaxf = delta;
+        return mkf(stop ? D_ACC_STOP : D_NEXT, al, stop ? 0.0f : rho_next * inv_rho);
+      });
+    } else {
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     block_reduce(a, c, R, t, n);
-    const Bc d = decide(bc, S, [&] {
+    d = decide(bc, S, [&] {
       const double rho = t[0], pAp = t[1];
       if (j == 0 && !(rho > 0.0)) return mk(D_EMPTY);  // r = g_F vanished
       if (!(pAp > 0.0)) return mk(D_FAIL);
@@ -574,6 +607,7 @@ __device__ bool cg_phase(const Vecs<T>& V, Vecs<TC>& C, const Own& O, Red& R, Bc
       if (delta > cdmax) cdmax = delta;
       return mk(stop ? D_ACC_STOP : D_NEXT, al, stop ? 0.0 : rho_next * inv_rho);
     });
+    }
     if (d.code == D_EMPTY) {
       *empty = true;
       return true;
