@@ -227,15 +227,28 @@ struct Own {
 
 // Row i of A a (Sec. 2), terms in the order diagonal, west, east, south,
 // north, below, above.
+// A neighbour outside the grid takes the row's own index and a zero
+// coupling, so that every load is unconditional and the loads of a thread's
+// points issue together (the term adds 0 x a[i], exactly 0 for the finite
+// vectors of the solver).
 template <class T>
 __device__ __forceinline__ T arow(const Vecs<T>& V, const Own& O, int i, unsigned nb, const T* a) {
+  const bool hw = nb & 1u, he = nb & 2u, hs = nb & 4u, hn = nb & 8u;
+  const int iw = hw ? i - 1 : i, ie = he ? i + 1 : i;
+  const int is = hs ? i - O.nx : i, in = hn ? i + O.nx : i;
+  const T cw = V.cx[iw], ce = V.cx[i], cs = V.cy[is], cn = V.cy[i];
   T v = V.d[i] * a[i];
-  if (nb & 1u) v = fma(V.cx[i - 1], a[i - 1], v);
-  if (nb & 2u) v = fma(V.cx[i], a[i + 1], v);
-  if (nb & 4u) v = fma(V.cy[i - O.nx], a[i - O.nx], v);
-  if (nb & 8u) v = fma(V.cy[i], a[i + O.nx], v);
-  if (nb & 16u) v = fma(V.cz[i - O.plane], a[i - O.plane], v);
-  if (nb & 32u) v = fma(V.cz[i], a[i + O.plane], v);
+  v = fma(hw ? cw : T(0), a[iw], v);
+  v = fma(he ? ce : T(0), a[ie], v);
+  v = fma(hs ? cs : T(0), a[is], v);
+  v = fma(hn ? cn : T(0), a[in], v);
+  if (O.dim == 3) {
+    const bool hd = nb & 16u, hu = nb & 32u;
+    const int id = hd ? i - O.plane : i, iu = hu ? i + O.plane : i;
+    const T cd = V.cz[id], cu = V.cz[i];
+    v = fma(hd ? cd : T(0), a[id], v);
+    v = fma(hu ? cu : T(0), a[iu], v);
+  }
   return v;
 }
 
