@@ -43,7 +43,8 @@ TAU_REL = 1e-6
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pass_kernel_traffic_single_large_1600.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_cs_0101018_gb300", "csrc", f)
-                  for f in ("pass_engine.cuh", "gpcg_kernels.cu", "engine.h")]
+                  for f in ("pass_engine.cuh", "gpcg_kernels.cu", "engine.h", "gpcg_coop.cu",
+                            "gpcg_coop_f64.cu")]
 
 
 def _kernel_sha():
@@ -452,7 +453,8 @@ def run_ours(args):
                 "frac": ach / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": "gpcg::pass_kernel", "alg_bytes_per_launch": per_pass_b,
                 "launch_ms": 1000 * per_pass_t,
-                "note": "per engine pass of one solve; time = solve time / passes"}
+                "note": "per engine pass of one solve (all passes of a lone solve run in one "
+                        "cooperative launch); time = solve time / passes"}
 
     roof_mx, roof_64 = roof(ms_mx, st_mx, traffic_mx), roof(ms_64, st_64, traffic_64)
 

@@ -255,9 +255,11 @@ typedef struct {
     double err_bound;       /* ||x - x*|| <= pg_norm / lambda_min when lambda_min > 0, else -1 */
     double alg_bytes;       /* algorithmic HBM bytes of all passes of the solve (the bytes
                                each pass must read and write once, summed) */
-    int64_t launches;       /* kernel launches of the engine for the latest solve (passes
-                               plus the empty launches of the final loop iteration); for a
-                               batch, the launches of the whole batch */
+    int64_t launches;       /* kernel launches of the engine for the latest solve: 1 when
+                               all its passes ran in one cooperative launch (a solve with
+                               one engine instance, the default), else the passes plus the
+                               empty launches of the final loop iteration; for a batch,
+                               the launches of the whole batch */
     int staged;             /* the shared-memory (TMA) staged paths available to the problem:
                                1 free-set words, 2 FP64 CG passes, 4 FP32 CG passes,
                                8 mixed-precision gradient-projection passes (2-D only; the

@@ -1,8 +1,8 @@
 """Build libgpcg.so in-tree with nvcc for sm_103a (GB300).
 
 The translation units (the default pass kernel, its tile-preconditioner,
-reduced-system and FP64 instantiations, the host API, the allocation-free
-product) are
+reduced-system, FP64 and 3-D instantiations, the cooperative pass kernels,
+the host API, the allocation-free product, the one-block solver) are
 compiled in parallel and linked into a shared
 library with the CUDA runtime linked statically, so the library needs nothing
 at run time but the NVIDIA driver.
@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpcg.so")
 SOURCES = ["gpcg_kernels.cu", "gpcg_pass_tile.cu", "gpcg_pass_rx.cu", "gpcg_pass_f64.cu",
-           "gpcg_pass_3d.cu", "gpcg_api.cu", "gpcg_noalloc.cu", "gpcg_resident.cu"]
+           "gpcg_pass_3d.cu", "gpcg_coop.cu", "gpcg_coop_f64.cu", "gpcg_api.cu",
+           "gpcg_noalloc.cu", "gpcg_resident.cu"]
 HEADERS = ["engine.h", "pass_engine.cuh", "tuned.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -235,10 +235,13 @@ struct EngineArgs {
   int* queue;             // next work item (dynamic scheduling; reset by the last CTA)
   unsigned* exits;        // CTAs that found the queue empty
   int* live;              // instances not yet done
-  unsigned* npass;        // launches so far (block 0 increments)
-  int* err;               // set when a bounded wait gave up
-  unsigned pass_cap;      // launches after which the loop condition is cleared
+  unsigned* npass;        // passes so far (block 0 increments)
+  int* err;               // bit 0: a copy's bounded wait gave up; bit 1: the pass is not in
+                          // this instantiation; bit 2: the grid barrier's bounded wait gave up
+  unsigned pass_cap;      // passes after which the loop (condition) ends
   unsigned long long cond;  // cudaGraphConditionalHandle, 0 when not in a WHILE graph
+  unsigned* gbar;           // arrivals at the cooperative kernel's grid barrier (zero before
+                            // its launch); unused by the other launches
 };
 
 }  // namespace gpcg

@@ -28,6 +28,7 @@ namespace gpcg {
 const void* pass_kernel_ptr(bool cond, int feat);
 int pass_grid(int n_work);
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
+cudaError_t launch_pass_coop(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
 size_t resident_smem(int dim, long long n, bool mixed, bool jacobi);
 cudaError_t launch_resident(const DevInst* insts, const int* ids, Ctl* ctl, int count,
                             size_t smem, unsigned sweep_cap, cudaStream_t s);
@@ -83,6 +84,12 @@ static int env_engine_mode() {
   // loop of fixed-length graphs.
   const char* s = getenv("GPCG_ENGINE_MODE");
   return (s && *s) ? atoi(s) : 0;
+}
+
+static bool env_no_coop() {
+  // GPCG_NO_COOP=1: a lone solve runs its passes as graph launches too
+  const char* s = getenv("GPCG_NO_COOP");
+  return s && *s && *s != '0';
 }
 
 static bool env_no_pdl() {
@@ -289,12 +296,12 @@ static void geometry(int dim, long long nx, long long ny, long long nz, gpcg_pro
 }
 
 // Bytes of the FP64 arena: kc bands, 1/diag, b, l, u, x[2], g[2], r[2], w,
-// p[2], Ap[2], two masks, the tile partials, the tensor maps and the word of
-// the input checks.
+// p[2], Ap[2], two masks, the group partials (two arrays: the cooperative
+// kernel alternates them), the tensor maps and the word of the input checks.
 static size_t arena64_bytes(const gpcg_problem* p) {
   const size_t vec = align256(sizeof(double) * (size_t)p->pn);
   const size_t msk = align256(sizeof(unsigned) * (size_t)p->mwords);
-  const size_t part = align256(sizeof(double) * kNRed * (size_t)p->n_groups);
+  const size_t part = align256(sizeof(double) * kNRed * 2 * (size_t)p->n_groups);
   const size_t maps = align256(sizeof(CUtensorMap) * M_COUNT);
   return (size_t)(p->kc + 15) * vec + 2 * msk + part + maps + 256;
 }
@@ -362,7 +369,7 @@ static void carve64(gpcg_problem* p) {
   for (int k = 0; k < 2; ++k) I.p64[k] = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.Ap64[k] = (double*)take(vec);
   for (int k = 0; k < 2; ++k) I.mask[k] = (unsigned*)take(msk);
-  I.part = (double*)take(align256(sizeof(double) * kNRed * (size_t)p->n_groups));
+  I.part = (double*)take(align256(sizeof(double) * kNRed * 2 * (size_t)p->n_groups));
   I.tmaps = take(align256(sizeof(CUtensorMap) * M_COUNT));
   p->d_flags = (int*)take(256);
   I.tma64 = 0;
@@ -1288,15 +1295,37 @@ static gpcg_status get_graph(Scratch& sc, long long tiles, int mode, int steps, 
 }
 
 // Run the engine until every instance in the scratch tables is done.
+// coop: the launch's work items all belong to one instance and may run as
+// one cooperative launch (*coop_used tells whether they did).
 static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStream_t s,
-                              int feat) {
+                              int feat, bool coop, bool* coop_used) {
   const unsigned cap = env_pass_cap();
   const int mode = env_engine_mode();
+  *coop_used = false;
   sc.h_pin[0] = n_live;
   sc.h_pin[1] = 0;
   CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(sc.d_npass, &sc.h_pin[1], sizeof(unsigned), cudaMemcpyHostToDevice, s));
-  if (mode == 0) {
+  if (mode == 0 && coop && tiles > 0 && tiles <= (long long)pass_grid(1 << 30)) {
+    // every pass in one launch: the counters (queue, exits, barrier) start
+    // at zero; the pass cap keeps the barrier's running count below 2^32
+    CK(cudaMemsetAsync(sc.d_queue, 0, 4 * sizeof(int), s));
+    EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
+                    sc.d_live,   sc.d_npass, sc.d_queue + 2, cap, 0ull};
+    args.gbar = (unsigned*)(sc.d_queue + 3);
+    args.pass_cap = std::min<unsigned>(cap, 0xffffffffu / (unsigned)tiles - 1u);
+    const cudaError_t e = launch_pass_coop(args, (int)tiles, s, feat);
+    if (e == cudaSuccess) {
+      *coop_used = true;
+    } else {
+      cudaGetLastError();  // not launched (no room for every block): run the graph below
+    }
+  }
+  if (*coop_used) {
+    CK(cudaMemcpyAsync(&sc.h_pin[0], sc.d_live, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&sc.h_pin[1], sc.d_npass, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  } else if (mode == 0) {
     gpcg_status st = get_graph(sc, tiles, 0, kBody, cap, feat);
     if (st != GPCG_OK) return st;
     CK(cudaGraphLaunch(sc.gexec, s));
@@ -1321,9 +1350,12 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   CK(cudaMemcpyAsync(&sc.h_pin[2], sc.d_queue + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (sc.h_pin[2] != 0) {
+    const int bits = sc.h_pin[2];
     const int zero = 0;
     cudaMemcpy(sc.d_queue + 2, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    return fail(GPCG_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
+    if (bits & 2) return fail(GPCG_ERR_CUDA, "a pass ran in a kernel without its code");
+    return fail(GPCG_ERR_TIMEOUT, "a bounded wait %s gave up",
+                (bits & 4) ? "at the grid barrier" : "for a TMA copy");
   }
   if (sc.h_pin[0] != 0) return fail(GPCG_ERR_TIMEOUT, "pass cap reached with live solves");
   return GPCG_OK;
@@ -1442,14 +1474,17 @@ static gpcg_status solve_set(gpcg_problem* const* probs, int count, const gpcg_o
   }
   gpcg_status run = GPCG_OK;
   sc.h_pin[1] = 0;
-  if (n_eng > 0) run = run_engine(sc, n_eng, tiles, s, feat);
+  // one engine instance: its passes may run in one cooperative launch
+  const bool coop = n_eng == 1 && !extract && !env_no_coop();
+  bool coop_used = false;
+  if (n_eng > 0) run = run_engine(sc, n_eng, tiles, s, feat, coop, &coop_used);
   if (run != GPCG_OK && run != GPCG_ERR_TIMEOUT) return run;
   CK(cudaMemcpyAsync(ctl.data(), sc.d_ctl, sizeof(Ctl) * count, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   gpcg_status first_bad = GPCG_OK;
   for (int k = 0; k < count; ++k) {
     if (!ctl[k].done) ctl[k].status = S_TIMEOUT;
-    probs[k]->launches = resident[k] ? 1 : (unsigned)sc.h_pin[1];
+    probs[k]->launches = (resident[k] || coop_used) ? 1 : (unsigned)sc.h_pin[1];
     probs[k]->last_path = resident[k] ? GPCG_PATH_RESIDENT : GPCG_PATH_ENGINE;
     probs[k]->last = ctl[k];
     probs[k]->have = true;

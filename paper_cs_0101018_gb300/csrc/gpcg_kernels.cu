@@ -402,6 +402,8 @@ const void* pass_kernel_ptr_tile(bool cond);
 const void* pass_kernel_ptr_rx(bool cond);
 const void* pass_kernel_ptr_f64(bool cond);
 const void* pass_kernel_ptr_3d(bool cond);
+const void* pass_kernel_coop_ptr_a(int feat);
+const void* pass_kernel_coop_ptr_b(int feat);
 
 // The pass kernel for a feature set (0, FEAT_TILE, FEAT_EXT or FEAT_F64); `cond`: the
 // instantiation that may clear a WHILE graph's condition.
@@ -411,6 +413,14 @@ const void* pass_kernel_ptr(bool cond, int feat) {
   if (feat == FEAT_F64) return pass_kernel_ptr_f64(cond);
   if (feat == FEAT_3D) return pass_kernel_ptr_3d(cond);
   return cond ? (const void*)pass_kernel<true, 0> : (const void*)pass_kernel<false, 0>;
+}
+
+// The cooperative pass kernel for a feature set (nullptr for the explicit
+// reduced system, whose passes exchange group offsets through the finalizer).
+const void* pass_kernel_coop_ptr(int feat) {
+  if (feat == 0 || feat == FEAT_3D) return pass_kernel_coop_ptr_a(feat);
+  if (feat == FEAT_F64 || feat == FEAT_TILE) return pass_kernel_coop_ptr_b(feat);
+  return nullptr;
 }
 
 int pass_grid(int n_work) {
@@ -424,10 +434,13 @@ int pass_grid(int n_work) {
     if (!cached[dev]) {
       int sms = 0, per = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64, (int)FEAT_3D})
+      for (int feat : {0, (int)FEAT_TILE, (int)FEAT_EXT, (int)FEAT_F64, (int)FEAT_3D}) {
         for (bool cond : {true, false})
           cudaFuncSetAttribute(pass_kernel_ptr(cond, feat),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+        if (const void* k = pass_kernel_coop_ptr(feat))
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+      }
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pass_kernel<false, 0>, kThreads,
                                                     kDynSmem);
       cached[dev] = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
@@ -443,6 +456,19 @@ cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int f
   void* args[] = {&a};
   return cudaLaunchKernel(pass_kernel_ptr(false, feat), dim3(n_blocks), dim3(kThreads), args,
                           kDynSmem, s);
+}
+
+// Every pass of one solve in one cooperative launch of n_blocks blocks (one
+// work item each).  Fails without launching when the blocks cannot all be
+// resident at once (cudaErrorCooperativeLaunchTooLarge) or the feature set
+// has no cooperative kernel; the caller then runs the passes as launches.
+cudaError_t launch_pass_coop(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat) {
+  pass_grid(1);  // sets the shared-memory attribute once
+  const void* k = pass_kernel_coop_ptr(feat);
+  if (k == nullptr || n_blocks != E.n_work) return cudaErrorInvalidValue;
+  EngineArgs a = E;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(k, dim3(n_blocks), dim3(kThreads), args, kDynSmem, s);
 }
 
 static int grid_for(long long work) {

@@ -3,17 +3,21 @@
 // Included by the translation units that instantiate the pass kernel: one
 // per feature set (gpcg_kernels.cu: the default passes; gpcg_pass_tile.cu:
 // with the tile preconditioner; gpcg_pass_rx.cu: with the explicit reduced
-// system), so that the default kernel carries none of the optional code.
+// system; gpcg_pass_f64.cu, gpcg_pass_3d.cu), so that the default kernel
+// carries none of the optional code, and by gpcg_coop.cu and
+// gpcg_coop_f64.cu, which instantiate the cooperative kernel (GPCG_COOP).
 //
 // One kernel, pass_kernel, runs every pass of Algorithm GPCG (Sec. 3 of
 // Benson, McInnes & More) for every live instance.  The grid is persistent
-// (a few CTAs per SM); CTAs pull work items -- one 64x32 tile of one plane of
-// one instance -- from a queue, perform the pass the instance's state machine
-// asks for, and deposit the tile's partial sums in the tile's own slot.  The
-// last CTA to finish a tile of an instance reduces that instance's slots in a
-// fixed order and runs the state-machine transition (finalize below), so an
-// instance's arithmetic depends only on the instance, never on the schedule or
-// on the other instances in the launch.
+// (two CTAs per SM); CTAs take work items -- one or two groups of 64x32
+// tiles of one instance -- perform the pass the instance's state machine
+// asks for, and deposit each group's partial sums in the group's own slot.
+// The last CTA to finish an instance's groups reduces its slots in a fixed
+// order and runs the state-machine transition (finalize below), so an
+// instance's arithmetic depends only on the instance, never on the schedule
+// or on the other instances in the launch.  The cooperative kernel,
+// pass_kernel_coop, runs all passes of one instance in one launch: every
+// CTA reduces the slots and runs the transition after a grid barrier.
 //
 // Stencil passes stream each operand once: a warp walks down its 64-column
 // strip keeping the operand of rows y-1, y, y+1 in registers; east/west
@@ -39,12 +43,40 @@
 
 #include "engine.h"
 
+// GPCG_COOP = 1: the translation unit instantiates the cooperative pass
+// kernel, which runs pass after pass of one solve in a single launch (see
+// pass_kernel).  A vector written by one pass and read by the next is then
+// written and read within one launch, so every load of engine data takes the
+// coherent path: no read-only-cache loads and no restrict-qualified pointers
+// (which allow the compiler to use that cache); both promise data constant
+// for the launch's lifetime.  The other translation units keep both.
+#ifndef GPCG_COOP
+#define GPCG_COOP 0
+#endif
+#if GPCG_COOP
+#define GPCG_RESTRICT
+#else
+#define GPCG_RESTRICT __restrict__
+#endif
+
 namespace gpcg {
 // internal linkage: every translation unit that includes this header has its
 // own copy of the device code and instantiates the pass kernel it needs
 namespace {
 
 #define FULL_MASK 0xffffffffu
+
+// A load of engine data: the read-only cache path in a kernel that runs one
+// pass per launch, the L1-cached coherent path in the cooperative kernel
+// (whose grid barrier orders it after the previous pass's stores).
+template <class T>
+__device__ __forceinline__ T ldro(const T* p) {
+#if GPCG_COOP
+  return __ldca(p);
+#else
+  return __ldg(p);
+#endif
+}
 
 // ------------------------------------------------- FP64 tests on the bits --
 // Inputs are checked to be NaN-free when a problem is created, so every value
@@ -176,6 +208,31 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   return false;
 }
 
+// Grid barrier of the cooperative pass kernel, run by thread 0 of each block
+// after a block barrier (so the block's global stores precede it).  Every
+// block of a cooperative launch is resident, so no block waits for one that
+// cannot run.  The fence before the arrival publishes the block's stores; the
+// acquire load and the fence after the wait make the other blocks' stores
+// visible to this block's loads, and the proxy fence to its tensor copies.
+// Returns false (the arrivals did not come) after a bounded number of polls.
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target) {
+  __threadfence();
+  atomicAdd(ctr, 1u);
+  bool ok = false;
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) {
+      ok = true;
+      break;
+    }
+    if (it >= 64) __nanosleep(100);
+  }
+  __threadfence();
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return ok;
+}
+
 // 2-D tiled bulk tensor copy global -> shared, completing on `bar`.  The x
 // coordinate is always a multiple of 16 bytes; y may be -1 or beyond the
 // last row (the unit fills zeros there).
@@ -198,26 +255,26 @@ __device__ __forceinline__ void tmap_acquire(const void* map) {
 
 // --------------------------------------------------------- memory helpers --
 
-__device__ __forceinline__ void ld2(const double* __restrict__ p, long long i, bool v0, bool v1,
+__device__ __forceinline__ void ld2(const double* GPCG_RESTRICT p, long long i, bool v0, bool v1,
                                     double o[2]) {
   if (v1) {
-    const double2 t = __ldg(reinterpret_cast<const double2*>(p + i));
+    const double2 t = ldro(reinterpret_cast<const double2*>(p + i));
     o[0] = t.x;
     o[1] = t.y;
   } else {
-    o[0] = v0 ? __ldg(p + i) : 0.0;
+    o[0] = v0 ? ldro(p + i) : 0.0;
     o[1] = 0.0;
   }
 }
 
-__device__ __forceinline__ void ld2(const float* __restrict__ p, long long i, bool v0, bool v1,
+__device__ __forceinline__ void ld2(const float* GPCG_RESTRICT p, long long i, bool v0, bool v1,
                                     float o[2]) {
   if (v1) {
-    const float2 t = __ldg(reinterpret_cast<const float2*>(p + i));
+    const float2 t = ldro(reinterpret_cast<const float2*>(p + i));
     o[0] = t.x;
     o[1] = t.y;
   } else {
-    o[0] = v0 ? __ldg(p + i) : 0.0f;
+    o[0] = v0 ? ldro(p + i) : 0.0f;
     o[1] = 0.0f;
   }
 }
@@ -274,15 +331,15 @@ __device__ __forceinline__ long long pidx(const DevInst& I, int y, int z, int co
 }
 
 // The two free bits of this lane's points (e0, e0+1) in row (y, z).
-__device__ __forceinline__ unsigned my_free_bits(const DevInst& I, const unsigned* __restrict__ m,
+__device__ __forceinline__ unsigned my_free_bits(const DevInst& I, const unsigned* GPCG_RESTRICT m,
                                                  int y, int z, int e0) {
-  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (e0 >> 5));
+  const unsigned w = ldro(m + row_index(I, y, z) * I.mw + (e0 >> 5));
   return (w >> (e0 & 31)) & 3u;
 }
 
-__device__ __forceinline__ bool free_bit(const DevInst& I, const unsigned* __restrict__ m, int y,
+__device__ __forceinline__ bool free_bit(const DevInst& I, const unsigned* GPCG_RESTRICT m, int y,
                                          int z, int col) {
-  const unsigned w = __ldg(m + row_index(I, y, z) * I.mw + (col >> 5));
+  const unsigned w = ldro(m + row_index(I, y, z) * I.mw + (col >> 5));
   return (w >> (col & 31)) & 1u;
 }
 
@@ -301,7 +358,7 @@ __device__ __forceinline__ int write_mask(const DevInst& I, unsigned* m, const u
       const unsigned word = spread16(b0 >> (16 * h)) | (spread16(b1 >> (16 * h)) << 1);
       const long long wi = row_index(I, y, z) * I.mw + wcol;
       m[wi] = word;
-      if (old) diff = __popc(word ^ __ldg(old + wi));
+      if (old) diff = __popc(word ^ ldro(old + wi));
     }
   }
   return diff;
@@ -324,10 +381,10 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
   const int e0 = x0 + 2 * lane;
   const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
   const long long zb = (long long)z * I.plane;
-  const T* __restrict__ diag = op.diag();
-  const T* __restrict__ cx = op.cx();
-  const T* __restrict__ cy = op.cy();
-  const T* __restrict__ cz = op.cz();
+  const T* GPCG_RESTRICT diag = op.diag();
+  const T* GPCG_RESTRICT cx = op.cx();
+  const T* GPCG_RESTRICT cy = op.cy();
+  const T* GPCG_RESTRICT cz = op.cz();
 
   T vm[2], vc[2], vn[2], cs[2];
   op.operand_row(ya - 1, z, e0, v0, v1, vm);
@@ -351,7 +408,7 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
     if (lane == 0) {
       const bool has = v0 && e0 > 0;
       vw = has ? op.operand_at(i - 1, y, z, e0 - 1) : T(0);
-      cw = has ? __ldg(cx + i - 1) : T(0);
+      cw = has ? ldro(cx + i - 1) : T(0);
     }
     if (lane == 31) ve = (e0 + 2 < I.nx) ? op.operand_at(i + 2, y, z, e0 + 2) : T(0);
     T av[2];
@@ -400,10 +457,10 @@ __device__ __forceinline__ void stencil_tile(const DevInst& I, const Op& op, int
 struct OpCensus {
   using T = double;
   const DevInst& I;
-  const double* __restrict__ x;
+  const double* GPCG_RESTRICT x;
   double* g_out;
   unsigned* m_out;
-  const float* __restrict__ x32;
+  const float* GPCG_RESTRICT x32;
   double* x_out;
   __device__ const double* diag() const { return I.diag; }
   __device__ const double* cx() const { return I.cx; }
@@ -436,9 +493,9 @@ struct OpCensus {
   }
   __device__ double operand_at(long long i, int, int, int) const {
     if (x32)
-      return rebuild(__ldg(x32 + i), __ldg(I.l + i), __ldg(I.u + i), __ldg(I.l32 + i),
-                     __ldg(I.u32 + i));
-    return __ldg(x + i);
+      return rebuild(ldro(x32 + i), ldro(I.l + i), ldro(I.u + i), ldro(I.l32 + i),
+                     ldro(I.u32 + i));
+    return ldro(x + i);
   }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const double v[2], const double av[2], Acc& acc) const {
@@ -473,8 +530,8 @@ struct OpCensus {
 struct OpGpAlpha {
   using T = double;
   const DevInst& I;
-  const double* __restrict__ x;
-  const double* __restrict__ g;
+  const double* GPCG_RESTRICT x;
+  const double* GPCG_RESTRICT g;
   __device__ const double* diag() const { return I.diag; }
   __device__ const double* cx() const { return I.cx; }
   __device__ const double* cy() const { return I.cy; }
@@ -494,7 +551,7 @@ struct OpGpAlpha {
     o[1] = v1 ? pg_comp(xv[1], gv[1], l[1], u[1]) : 0.0;
   }
   __device__ double operand_at(long long i, int, int, int) const {
-    return pg_comp(__ldg(x + i), __ldg(g + i), __ldg(I.l + i), __ldg(I.u + i));
+    return pg_comp(ldro(x + i), ldro(g + i), ldro(I.l + i), ldro(I.u + i));
   }
   __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const double v[2],
                          const double av[2], Acc& acc) const {
@@ -518,15 +575,15 @@ template <int DK>
 struct OpTrial {
   using T = double;
   const DevInst& I;
-  const double* __restrict__ x;
-  const double* __restrict__ g;
-  const double* __restrict__ w64;
-  const float* __restrict__ w32;
+  const double* GPCG_RESTRICT x;
+  const double* GPCG_RESTRICT g;
+  const double* GPCG_RESTRICT w64;
+  const float* GPCG_RESTRICT w32;
   double alpha;
   double* xt_out;
   double* gt_out;
   unsigned* m_out;
-  const unsigned* __restrict__ m_old;
+  const unsigned* GPCG_RESTRICT m_old;
   __device__ const double* diag() const { return I.diag; }
   __device__ const double* cx() const { return I.cx; }
   __device__ const double* cy() const { return I.cy; }
@@ -561,10 +618,10 @@ struct OpTrial {
   }
   __device__ double operand_at(long long i, int, int, int) const {
     double dv;
-    if (DK == D_NEG_G) dv = -__ldg(g + i);
-    else if (DK == D_W64) dv = __ldg(w64 + i);
-    else dv = (double)__ldg(w32 + i);
-    return mid3(__ldg(I.l + i), __ldg(I.u + i), fma(alpha, dv, __ldg(x + i)));
+    if (DK == D_NEG_G) dv = -ldro(g + i);
+    else if (DK == D_W64) dv = ldro(w64 + i);
+    else dv = (double)ldro(w32 + i);
+    return mid3(ldro(I.l + i), ldro(I.u + i), fma(alpha, dv, ldro(x + i)));
   }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const double v[2], const double av[2], Acc& acc) const {
@@ -614,7 +671,7 @@ struct OpTrial {
 struct OpCensus32 {
   using T = float;
   const DevInst& I;
-  const float* __restrict__ x32;
+  const float* GPCG_RESTRICT x32;
   float* g_out;
   float* pg_out;
   unsigned* m_out;
@@ -630,7 +687,7 @@ struct OpCensus32 {
     }
     ld2(x32, pidx(I, y, z, e0), v0, v1, o);
   }
-  __device__ float operand_at(long long i, int, int, int) const { return __ldg(x32 + i); }
+  __device__ float operand_at(long long i, int, int, int) const { return ldro(x32 + i); }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const float v[2], const float av[2], Acc& acc) const {
     float l[2], u[2], b[2], g[2], pg[2];
@@ -663,7 +720,7 @@ struct OpCensus32 {
 struct OpGpAlpha32 {
   using T = float;
   const DevInst& I;
-  const float* __restrict__ pg32;
+  const float* GPCG_RESTRICT pg32;
   FF* ff;  // [2]
   __device__ const float* diag() const { return I.diag32; }
   __device__ const float* cx() const { return I.cx32; }
@@ -676,7 +733,7 @@ struct OpGpAlpha32 {
     }
     ld2(pg32, pidx(I, y, z, e0), v0, v1, o);
   }
-  __device__ float operand_at(long long i, int, int, int) const { return __ldg(pg32 + i); }
+  __device__ float operand_at(long long i, int, int, int) const { return ldro(pg32 + i); }
   __device__ void output(int, int, long long, int, int, int, bool v0, bool v1, const float v[2],
                          const float av[2], Acc&) const {
     if (v0) {
@@ -697,22 +754,22 @@ template <int DK>
 struct OpTrial32 {
   using T = float;
   const DevInst& I;
-  const float* __restrict__ x32;
-  const float* __restrict__ g32;
-  const float* __restrict__ w32;
+  const float* GPCG_RESTRICT x32;
+  const float* GPCG_RESTRICT g32;
+  const float* GPCG_RESTRICT w32;
   float alpha;
   float* xt32_out;
   float* gt_out;
   float* pg_out;
   unsigned* m_out;
-  const unsigned* __restrict__ m_old;
+  const unsigned* GPCG_RESTRICT m_old;
   FF* ff;  // [3]: <g,s>, <s,gt>, ||pg||^2
   __device__ const float* diag() const { return I.diag32; }
   __device__ const float* cx() const { return I.cx32; }
   __device__ const float* cy() const { return I.cy32; }
   __device__ const float* cz() const { return I.cz32; }
   __device__ float dir_at(long long i) const {
-    return DK == D_NEG_G ? -__ldg(g32 + i) : __ldg(w32 + i);
+    return DK == D_NEG_G ? -ldro(g32 + i) : ldro(w32 + i);
   }
   __device__ void operand_row(int y, int z, int e0, bool v0, bool v1, float o[2]) const {
     if (!row_ok(I, y, z)) {
@@ -735,7 +792,7 @@ struct OpTrial32 {
     o[1] = v1 ? mid3f(l[1], u[1], fmaf(alpha, d[1], xv[1])) : 0.0f;
   }
   __device__ float operand_at(long long i, int, int, int) const {
-    return mid3f(__ldg(I.l32 + i), __ldg(I.u32 + i), fmaf(alpha, dir_at(i), __ldg(x32 + i)));
+    return mid3f(ldro(I.l32 + i), ldro(I.u32 + i), fmaf(alpha, dir_at(i), ldro(x32 + i)));
   }
   __device__ void output(int y, int z, long long i, int x0, int, int lane, bool v0, bool v1,
                          const float v[2], const float av[2], Acc& acc) const {
@@ -774,9 +831,9 @@ struct OpTrial32 {
 // it runs once per CG phase and, inlined, raises the register pressure of the
 // whole sweep.
 template <class T>
-__device__ __noinline__ void first_step_jacobi(const float* __restrict__ g32,
-                                               const double* __restrict__ g,
-                                               const T* __restrict__ dinv, long long i, bool v0,
+__device__ __noinline__ void first_step_jacobi(const float* GPCG_RESTRICT g32,
+                                               const double* GPCG_RESTRICT g,
+                                               const T* GPCG_RESTRICT dinv, long long i, bool v0,
                                                bool v1, unsigned fb, T* rv, T* da) {
   T di[2];
   ld2(dinv, i, v0, v1, di);
@@ -804,12 +861,12 @@ struct OpCgB {
   using T = TV;
   static constexpr bool kF32 = sizeof(TV) == 4;
   const DevInst& I;
-  const T* __restrict__ r;
-  const T* __restrict__ p_old;
-  const double* __restrict__ g;
-  const unsigned* __restrict__ m;
+  const T* GPCG_RESTRICT r;
+  const T* GPCG_RESTRICT p_old;
+  const double* GPCG_RESTRICT g;
+  const unsigned* GPCG_RESTRICT m;
   T beta;
-  const float* __restrict__ g32;  // mixed phase: the gradient is FP32 (FIRST)
+  const float* GPCG_RESTRICT g32;  // mixed phase: the gradient is FP32 (FIRST)
   T* p_out;
   T* ap_out;
   T* r_out;
@@ -819,7 +876,7 @@ struct OpCgB {
   const T* by;
   const T* bz;
   FF* ff;  // [3] FP32 accumulators (kF32)
-  const T* __restrict__ dinv;  // 1/diag (point Jacobi, z = r / diag), or nullptr
+  const T* GPCG_RESTRICT dinv;  // 1/diag (point Jacobi, z = r / diag), or nullptr
   __device__ const T* diag() const { return bd; }
   __device__ const T* cx() const { return bx; }
   __device__ const T* cy() const { return by; }
@@ -865,12 +922,12 @@ struct OpCgB {
     }
   }
   __device__ T operand_at(long long i, int y, int z, int col) const {
-    const T di = JAC ? __ldg(dinv + i) : T(1);
+    const T di = JAC ? ldro(dinv + i) : T(1);
     if (FIRST) {
       if (!free_bit(I, m, y, z, col)) return T(0);
-      return -(g32 ? (T)__ldg(g32 + i) : (T)__ldg(g + i)) * di;
+      return -(g32 ? (T)ldro(g32 + i) : (T)ldro(g + i)) * di;
     } else {
-      return fma(beta, __ldg(p_old + i), -__ldg(r + i) * di);
+      return fma(beta, ldro(p_old + i), -ldro(r + i) * di);
     }
   }
   __device__ void output(int y, int z, long long i, int, int e0, int, bool v0, bool v1,
@@ -914,9 +971,9 @@ struct OpCgB {
 // P_CG_A: w += alpha p, r_out = r + alpha Ap, <r_out, M^-1 r_out> (M = I or
 // diag(A) with dinv).
 template <class T, bool JAC>
-__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* __restrict__ r,
-                                          T* r_out, const T* __restrict__ p,
-                                          const T* __restrict__ ap, const T* __restrict__ dinv,
+__device__ __forceinline__ void cg_a_tile(const DevInst& I, T* w, const T* GPCG_RESTRICT r,
+                                          T* r_out, const T* GPCG_RESTRICT p,
+                                          const T* GPCG_RESTRICT ap, const T* GPCG_RESTRICT dinv,
                                           double alpha, int x0, int y0, int z, Acc& acc,
                                           FF* ffs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1401,17 +1458,17 @@ __device__ __noinline__ void rcg_range(const DevInst& I, const Snap& S, long lon
                           FF* ffs) {
   const bool f32 = sizeof(T) == 4;
   const int pc = S.pcur;
-  const T* __restrict__ r = f32 ? (const T*)I.rc32[pc] : (const T*)I.rc64[pc];
-  const T* __restrict__ p = f32 ? (const T*)I.pc32[pc] : (const T*)I.pc64[pc];
-  const T* __restrict__ ap = f32 ? (const T*)I.apc32[pc] : (const T*)I.apc64[pc];
-  const T* __restrict__ rd = f32 ? (const T*)I.rd32 : (const T*)I.rd64;
-  const T* __restrict__ rv = f32 ? (const T*)I.rv32 : (const T*)I.rv64;
-  const T* __restrict__ di = f32 ? (const T*)I.rdi32 : (const T*)I.rdi64;
+  const T* GPCG_RESTRICT r = f32 ? (const T*)I.rc32[pc] : (const T*)I.rc64[pc];
+  const T* GPCG_RESTRICT p = f32 ? (const T*)I.pc32[pc] : (const T*)I.pc64[pc];
+  const T* GPCG_RESTRICT ap = f32 ? (const T*)I.apc32[pc] : (const T*)I.apc64[pc];
+  const T* GPCG_RESTRICT rd = f32 ? (const T*)I.rd32 : (const T*)I.rd64;
+  const T* GPCG_RESTRICT rv = f32 ? (const T*)I.rv32 : (const T*)I.rv64;
+  const T* GPCG_RESTRICT di = f32 ? (const T*)I.rdi32 : (const T*)I.rdi64;
   T* r_o = f32 ? (T*)I.rc32[pc ^ 1] : (T*)I.rc64[pc ^ 1];
   T* p_o = f32 ? (T*)I.pc32[pc ^ 1] : (T*)I.pc64[pc ^ 1];
   T* ap_o = f32 ? (T*)I.apc32[pc ^ 1] : (T*)I.apc64[pc ^ 1];
   T* w = f32 ? (T*)I.wc32 : (T*)I.wc64;
-  const int* __restrict__ rnb = I.rnb;
+  const int* GPCG_RESTRICT rnb = I.rnb;
   const long long st = I.n;
   const int nn = 2 * I.dim;
   const T a = (T)S.alpha, b = (T)S.beta;
@@ -1423,7 +1480,7 @@ __device__ __noinline__ void rcg_range(const DevInst& I, const Snap& S, long lon
     w[k] = fma(a, pk, w[k]);
     T y = rd[k] * pn;
     for (int j = 0; j < nn; ++j) {
-      const int q = __ldg(rnb + j * st + k);
+      const int q = ldro(rnb + j * st + k);
       const T rq = fma(a, ap[q], r[q]);
       const T pq = fma(b, p[q], -(JAC ? rq * di[q] : rq));
       y = fma(rv[j * st + k], pq, y);
@@ -1456,7 +1513,7 @@ __device__ __noinline__ void rw_range(const DevInst& I, const Snap& S, long long
   T* wf = f32 ? (T*)I.w32 : (T*)I.w64;
   const T a = (T)S.alpha;
   for (long long k = lo + threadIdx.x; k < hi; k += kThreads)
-    wf[__ldg(I.fidx + k)] = fma(a, p[k], wc[k]);
+    wf[ldro(I.fidx + k)] = fma(a, p[k], wc[k]);
 }
 
 // ---------------------------------------------------------------- control --
@@ -3711,9 +3768,6 @@ __device__ __forceinline__ void run_tile(const DevInst& I, const Snap& S, int x0
   }
 }
 
-// kCond: the launch belongs to a WHILE-conditional graph whose condition this
-// kernel clears (a separate instantiation, because profilers cannot capture
-// graph nodes able to set a condition).
 // Whether this instantiation has the code of the item's pass.
 template <int kFeat>
 __device__ __forceinline__ bool pass_supported(const DevInst& I, const Snap& S) {
@@ -3724,8 +3778,27 @@ __device__ __forceinline__ bool pass_supported(const DevInst& I, const Snap& S) 
          (!f3 || (kFeat & FEAT_3D) != 0);
 }
 
+// The body of the pass kernels: pass_kernel runs one pass of every live
+// instance per launch; pass_kernel_coop (GPCG_COOP) runs every pass of one
+// instance in a cooperative launch.
+//
+// kCond: the launch belongs to a WHILE-conditional graph whose condition this
+// kernel clears (a separate instantiation, because profilers cannot capture
+// graph nodes able to set a condition).
+//
+// The cooperative kernel takes one work item per block, every block
+// resident.  After a pass the blocks meet at a grid barrier instead of a
+// kernel boundary; then every block reduces the group partials and runs the
+// state machine on its own copy of the control block -- the same arithmetic
+// in the same order, so the copies agree bit for bit and every block knows
+// the next pass without a round trip to global memory -- and block 0 alone
+// writes the control block back, counts the pass and counts the instance out
+// when it is done.  The partials alternate between two slot arrays, so a
+// block that starts the next pass never overwrites slots another block is
+// still reducing.
 template <bool kCond, int kFeat>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
+__device__ __forceinline__ void pass_body(const EngineArgs& E) {
+  constexpr bool kCoop = GPCG_COOP != 0;
   __shared__ DevInst sI;
   __shared__ Snap sS;
   __shared__ Ctl sC;
@@ -3736,6 +3809,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   __shared__ double s_stash[4][kThreads];
   __shared__ int s_gcnt[kMaxSpan][3][kWarps];  // the warps' counts per group of the item
   __shared__ int s_t, s_inst, s_last;
+  __shared__ int s_live;  // the cooperative kernel's blocks other than 0 count out here
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   static_assert(sizeof(Ctl) % 8 == 0 && sizeof(Ctl) / 8 <= kThreads, "control block copy");
@@ -3767,7 +3841,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // the next pass may start its own prologue as soon as SMs free up
   asm volatile("griddepcontrol.launch_dependents;" :::);
-  if (blockIdx.x == 0 && tid == 0) {
+  if (!kCoop && blockIdx.x == 0 && tid == 0) {
     const unsigned np = atomicAdd(E.npass, 1u) + 1u;
     if (kCond && E.cond != 0ull && (*((volatile int*)E.live) <= 0 || np >= E.pass_cap)) {
       cudaGraphSetConditional((cudaGraphConditionalHandle)E.cond, 0u);
@@ -3775,353 +3849,385 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
   }
   int seq = 0;  // chunks of the TMA pipeline consumed so far (same in all threads)
 
-  for (int first = 1;; first = 0) {
-    __syncthreads();  // the previous item's shared state is no longer read
-    // the first item of a CTA is its own index; later ones are claimed
-    if (tid == 0) s_t = first ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(E.queue, 1);
-    __syncthreads();
-    const int t = s_t;
-    if (t >= E.n_work) break;
-    const int2 tr = __ldg(E.tiles + t);
-    if (tr.x != s_inst || first) {
-      // a new instance (or the first item, whose descriptor the prologue
-      // loaded): read the snapshot of its state, the control block in one
-      // round trip (the finalizer's shared copy sC is free here)
-      const bool fresh = tr.x != s_inst;
-      __syncthreads();  // everyone compared against the old s_inst
-      if (tid < (int)(sizeof(Ctl) / 8))
-        reinterpret_cast<long long*>(&sC)[tid] =
-            __ldcg(reinterpret_cast<const long long*>(E.ctl + tr.x) + tid);
+  for (int pi = 0;; ++pi) {  // passes of the launch (one unless cooperative)
+    bool again = false;        // the cooperative kernel runs another pass
+    for (int first = 1;; first = 0) {
+      __syncthreads();  // the previous item's shared state is no longer read
+      // the first item of a CTA is its own index; later ones are claimed (the
+      // cooperative kernel has one item per block)
+      if (tid == 0)
+        s_t = first ? (int)blockIdx.x : (kCoop ? E.n_work : (int)gridDim.x + atomicAdd(E.queue, 1));
       __syncthreads();
-      const bool skip = sC.pass == P_NONE;
-      // a finished instance's groups are skipped without loading its descriptor
-      if (fresh && !skip && tid < (int)(sizeof(DevInst) / 8))
-        reinterpret_cast<long long*>(&sI)[tid] =
-            __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
-      if (tid == 0) {
-        sS.pass = sC.pass;
-        sS.cur = sC.cur;
-        sS.pcur = sC.pcur;
-        sS.cg32 = sC.cg32;
-        sS.first_cg = sC.first_cg;
-        sS.dir = sC.dir;
-        sS.gp32 = sC.gp32;
-        sS.x32_live = sC.x32_live;
-        sS.m = sC.m;
-        sS.alpha = sC.alpha;
-        sS.beta = sC.beta;
-        s_inst = tr.x;
+      const int t = s_t;
+      if (t >= E.n_work) break;
+      const int2 tr = __ldg(E.tiles + t);
+      if (tr.x != s_inst || first) {
+        // a new instance (or the first item, whose descriptor the prologue
+        // loaded): read the snapshot of its state, the control block in one
+        // round trip (the finalizer's shared copy sC is free here); after the
+        // cooperative kernel's first pass sC already holds the state
+        const bool fresh = tr.x != s_inst;
+        __syncthreads();  // everyone compared against the old s_inst
+        if ((!kCoop || pi == 0) && tid < (int)(sizeof(Ctl) / 8))
+          reinterpret_cast<long long*>(&sC)[tid] =
+              __ldcg(reinterpret_cast<const long long*>(E.ctl + tr.x) + tid);
+        __syncthreads();
+        const bool skip = sC.pass == P_NONE;
+        // a finished instance's groups are skipped without loading its descriptor
+        if (fresh && !skip && tid < (int)(sizeof(DevInst) / 8))
+          reinterpret_cast<long long*>(&sI)[tid] =
+              __ldg(reinterpret_cast<const long long*>(E.insts + tr.x) + tid);
+        if (tid == 0) {
+          sS.pass = sC.pass;
+          sS.cur = sC.cur;
+          sS.pcur = sC.pcur;
+          sS.cg32 = sC.cg32;
+          sS.first_cg = sC.first_cg;
+          sS.dir = sC.dir;
+          sS.gp32 = sC.gp32;
+          sS.x32_live = sC.x32_live;
+          sS.m = sC.m;
+          sS.alpha = sC.alpha;
+          sS.beta = sC.beta;
+          s_inst = tr.x;
+        }
+        __syncthreads();
+        if (fresh && !skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
       }
-      __syncthreads();
-      if (fresh && !skip && sI.tmaps && tid < M_COUNT) tmap_acquire(tmap(sI, tid));
-    }
-    const DevInst& I = sI;
-    const Snap& S = sS;
-    if (S.pass == P_NONE) continue;
-    if (!pass_supported<kFeat>(I, S)) {
-      // launched with the wrong instantiation: report it and leave the
-      // instance unfinished (the engine stops at its pass cap)
-      if (tid == 0) atomicOr(E.err, 2);
-      continue;
-    }
+      const DevInst& I = sI;
+      const Snap& S = sS;
+      // this pass's group partials (the cooperative kernel alternates two arrays)
+      double* const part = I.part + (kCoop && (pi & 1) ? (long long)I.n_groups * kNRed : 0LL);
+      if (S.pass == P_NONE) continue;
+      if (!pass_supported<kFeat>(I, S)) {
+        // launched with the wrong instantiation: report it and leave the
+        // instance unfinished (the engine stops at its pass cap)
+        if (tid == 0) atomicOr(E.err, 2);
+        continue;
+      }
 
-    Acc acc;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
-    acc.c[0] = acc.c[1] = acc.c[2] = 0;
-    FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    // the work item: groups [grp, grp_end) of the instance (the partition
-    // into groups depends on the shape only; how many groups an item spans
-    // is the launch's choice, and every group keeps its own sums, so the
-    // results do not depend on it)
-    const int grp = tr.y;
-    const int grp_end = min(grp + max(1, min(I.span, kMaxSpan)), I.n_groups);
-    // group sums: FP32 passes carry float-float accumulators (FP64 adds are
-    // slow and long-latency on GB300), the others FP64
-    auto ff_pass = [&]() {
-      return (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F || S.pass == P_CG_Z ||
-              S.pass == P_RX_BUILD || S.pass == P_RCG)
-                 ? S.cg32 != 0
-                 : (S.pass != P_START && S.gp32 != 0);
-    };
-    // the end of a group: every thread stores its sums for the group in
-    // shared memory (float-float pairs packed in 8 bytes for the FP32
-    // passes, plain stores that the compiler need not order against the
-    // stages) and each warp its counts, then the accumulators restart.  No
-    // barrier and no reduction here (a barrier inside the item would take
-    // away the slack between warps that hides latency); the item's end
-    // reduces every group in the same fixed order as a group alone, so each
-    // group's sums do not depend on the item that holds it.
-    auto stash = [&](double* dst, int gi) {
-      const bool ffred = ff_pass();
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const double v = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
-                                                  __float_as_int(ffs[k].lo))
-                               : acc.s[k];
-        asm volatile("st.shared.f64 [%0], %1;" ::"r"(smem_u32(dst + k * kThreads + tid)), "d"(v));
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
-        if (lane == 0) s_gcnt[gi][k][warp] = c;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        acc.s[k] = 0.0;
-        ffs[k] = FF{0.f, 0.f};
-      }
+      Acc acc;
+  #pragma unroll
+      for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
       acc.c[0] = acc.c[1] = acc.c[2] = 0;
-    };
-    const bool tma = tma_pass<kFeat>(I, S);
-    if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
-      if constexpr ((kFeat & FEAT_EXT) != 0) {
-        // compact passes of the explicit reduced system: the group is a
-        // range of compact indices (one group per item)
-        const long long lo = (long long)grp * S.m / I.n_groups;
-        const long long hi = (long long)(grp + 1) * S.m / I.n_groups;
-        const bool jac = I.opt.precond == PC_JACOBI;
-        if (S.pass == P_RW) {
-          if (S.cg32) rw_range<float>(I, S, lo, hi);
-          else rw_range<double>(I, S, lo, hi);
-        } else if (S.cg32) {
-          if (jac) rcg_range<float, true>(I, S, lo, hi, acc, ffs);
-          else rcg_range<float, false>(I, S, lo, hi, acc, ffs);
-        } else {
-          if (jac) rcg_range<double, true>(I, S, lo, hi, acc, ffs);
-          else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
+      FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+      // the work item: groups [grp, grp_end) of the instance (the partition
+      // into groups depends on the shape only; how many groups an item spans
+      // is the launch's choice, and every group keeps its own sums, so the
+      // results do not depend on it)
+      const int grp = tr.y;
+      const int grp_end = min(grp + max(1, min(I.span, kMaxSpan)), I.n_groups);
+      // group sums: FP32 passes carry float-float accumulators (FP64 adds are
+      // slow and long-latency on GB300), the others FP64
+      auto ff_pass = [&]() {
+        return (S.pass == P_CG_A || S.pass == P_CG_B || S.pass == P_CG_F || S.pass == P_CG_Z ||
+                S.pass == P_RX_BUILD || S.pass == P_RCG)
+                   ? S.cg32 != 0
+                   : (S.pass != P_START && S.gp32 != 0);
+      };
+      // the end of a group: every thread stores its sums for the group in
+      // shared memory (float-float pairs packed in 8 bytes for the FP32
+      // passes, plain stores that the compiler need not order against the
+      // stages) and each warp its counts, then the accumulators restart.  No
+      // barrier and no reduction here (a barrier inside the item would take
+      // away the slack between warps that hides latency); the item's end
+      // reduces every group in the same fixed order as a group alone, so each
+      // group's sums do not depend on the item that holds it.
+      auto stash = [&](double* dst, int gi) {
+        const bool ffred = ff_pass();
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double v = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
+                                                    __float_as_int(ffs[k].lo))
+                                 : acc.s[k];
+          asm volatile("st.shared.f64 [%0], %1;" ::"r"(smem_u32(dst + k * kThreads + tid)), "d"(v));
         }
-      }
-    } else if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_MAP) {
-      if constexpr ((kFeat & FEAT_EXT) != 0) {
-        const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
-        const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
-        if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
-        else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
-      }
-    } else if (!tma) {
-      // register sweep: a group is a range of whole tiles
-      for (int g = grp; g < grp_end; ++g) {
-        const int t_lo = (int)((long long)g * I.n_tiles / I.n_groups);
-        const int t_hi = (int)((long long)(g + 1) * I.n_tiles / I.n_groups);
-        for (int tile = t_lo; tile < t_hi; ++tile) {
-          const int rest = tile / I.tiles_x;
-          run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
-                          rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
+  #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
+          if (lane == 0) s_gcnt[gi][k][warp] = c;
         }
-        if (g + 1 < grp_end) stash(&s_stash[0][0], 0);
-      }
-    } else {
-      // TMA pipeline: a group is a range of 8-row strips (4 per tile), cut
-      // into chunks of up to `ch` rows that stay inside one tile and one
-      // group; the next kStages-1 chunks are in flight while chunk k is
-      // computed (the stage refilled at the top of an iteration is the one
-      // computed in the previous iteration), across the groups of the item.
-      // Nothing is in flight between work items.
-      constexpr int kDepth = kStages - 1;
-      static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
-      const bool gp = gp_tma(I, S);
-      const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
-      const int ch = chunk_rows(I, S, gp);
-      const int rpw = ch / kWarps;
-      // chunks that write to their stage (and have block barriers inside)
-      const bool writes_stage =
-          gp ? trial_alpha0(S)
-             : (S.pass == P_CG_B || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
-                (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
-      Walk wk(I, grp, grp_end, ch);
-      // the current chunk and the next two (h1, h2: they exist)
-      Chunk c0 = wk.take(I);
-      const bool hh1 = !wk.done();
-      Chunk c1 = hh1 ? wk.take(I) : c0;
-      const bool hh2 = !wk.done();
-      Chunk c2 = hh2 ? wk.take(I) : c0;
-      bool h1 = hh1, h2 = hh2;
-      auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
-      auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
-      if (tid == 0) {
-        // order earlier generic writes to the stages before the copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_chunk<kFeat>(I, S, gp, c0, smem_u32(stage(seq)), bar(seq), want_bits);
-        if (kDepth == 2 && h1)
-          issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
-      }
-      unsigned fbits[4] = {0u, 0u, 0u, 0u};
-      for (;;) {
-        if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
-          if (writes_stage)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (kDepth == 2)
-            issue_chunk<kFeat>(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2), want_bits);
-          else
+  #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc.s[k] = 0.0;
+          ffs[k] = FF{0.f, 0.f};
+        }
+        acc.c[0] = acc.c[1] = acc.c[2] = 0;
+      };
+      const bool tma = tma_pass<kFeat>(I, S);
+      if ((kFeat & FEAT_EXT) != 0 && (S.pass == P_RCG || S.pass == P_RW)) {
+        if constexpr ((kFeat & FEAT_EXT) != 0) {
+          // compact passes of the explicit reduced system: the group is a
+          // range of compact indices (one group per item)
+          const long long lo = (long long)grp * S.m / I.n_groups;
+          const long long hi = (long long)(grp + 1) * S.m / I.n_groups;
+          const bool jac = I.opt.precond == PC_JACOBI;
+          if (S.pass == P_RW) {
+            if (S.cg32) rw_range<float>(I, S, lo, hi);
+            else rw_range<double>(I, S, lo, hi);
+          } else if (S.cg32) {
+            if (jac) rcg_range<float, true>(I, S, lo, hi, acc, ffs);
+            else rcg_range<float, false>(I, S, lo, hi, acc, ffs);
+          } else {
+            if (jac) rcg_range<double, true>(I, S, lo, hi, acc, ffs);
+            else rcg_range<double, false>(I, S, lo, hi, acc, ffs);
+          }
+        }
+      } else if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_MAP) {
+        if constexpr ((kFeat & FEAT_EXT) != 0) {
+          const int t_lo = (int)((long long)grp * I.n_tiles / I.n_groups);
+          const int t_hi = (int)((long long)(grp + 1) * I.n_tiles / I.n_groups);
+          if (S.cg32) rx_map_group<float>(I, S, grp, t_lo, t_hi, s_scan);
+          else rx_map_group<double>(I, S, grp, t_lo, t_hi, s_scan);
+        }
+      } else if (!tma) {
+        // register sweep: a group is a range of whole tiles
+        for (int g = grp; g < grp_end; ++g) {
+          const int t_lo = (int)((long long)g * I.n_tiles / I.n_groups);
+          const int t_hi = (int)((long long)(g + 1) * I.n_tiles / I.n_groups);
+          for (int tile = t_lo; tile < t_hi; ++tile) {
+            const int rest = tile / I.tiles_x;
+            run_tile<kFeat>(I, S, (tile % I.tiles_x) * kTX, (rest % I.tiles_y) * kTY,
+                            rest / I.tiles_y, acc, ffs, reinterpret_cast<float*>(stage0));
+          }
+          if (g + 1 < grp_end) stash(&s_stash[0][0], 0);
+        }
+      } else {
+        // TMA pipeline: a group is a range of 8-row strips (4 per tile), cut
+        // into chunks of up to `ch` rows that stay inside one tile and one
+        // group; the next kStages-1 chunks are in flight while chunk k is
+        // computed (the stage refilled at the top of an iteration is the one
+        // computed in the previous iteration), across the groups of the item.
+        // Nothing is in flight between work items.
+        constexpr int kDepth = kStages - 1;
+        static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
+        const bool gp = gp_tma(I, S);
+        const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
+        const int ch = chunk_rows(I, S, gp);
+        const int rpw = ch / kWarps;
+        // chunks that write to their stage (and have block barriers inside)
+        const bool writes_stage =
+            gp ? trial_alpha0(S)
+               : (S.pass == P_CG_B || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
+                  (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
+        Walk wk(I, grp, grp_end, ch);
+        // the current chunk and the next two (h1, h2: they exist)
+        Chunk c0 = wk.take(I);
+        const bool hh1 = !wk.done();
+        Chunk c1 = hh1 ? wk.take(I) : c0;
+        const bool hh2 = !wk.done();
+        Chunk c2 = hh2 ? wk.take(I) : c0;
+        bool h1 = hh1, h2 = hh2;
+        auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
+        auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
+        if (tid == 0) {
+          // order earlier generic writes to the stages before the copies
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue_chunk<kFeat>(I, S, gp, c0, smem_u32(stage(seq)), bar(seq), want_bits);
+          if (kDepth == 2 && h1)
             issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
         }
-        unsigned char* st = stage(seq);
-        const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
-        bool failed;
-        if (ok && want_bits) stage_bits(st, c0.x0, rpw, gp, fbits);
-        if (writes_stage) {
-          // the chunk has a barrier inside: agree on the wait first
-          failed = __syncthreads_or(!ok);
-          if (!failed) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
-          __syncthreads();  // the stage may be refilled
-        } else {
-          // one barrier per chunk: every thread is done with the stage (which
-          // may then be refilled) and no bounded wait gave up
-          if (ok) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
-          failed = __syncthreads_or(!ok);
-        }
-        if (c0.rows & kEndG0) stash(&s_stash[0][0], 0);
-        if (failed) {
-          // a copy never completed: record it, give the copies still in
-          // flight a bounded chance to land, and leave; the engine's loop
-          // then ends on its pass cap and the host reports the error
-          if (tid == 0) {
-            atomicOr(E.err, 1);
-            if (h1) mbar_wait(bar(seq + 1), ((seq + 1) / kStages) & 1);
-            if (kDepth == 2 && h2) mbar_wait(bar(seq + 2), ((seq + 2) / kStages) & 1);
+        unsigned fbits[4] = {0u, 0u, 0u, 0u};
+        for (;;) {
+          if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
+            if (writes_stage)
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (kDepth == 2)
+              issue_chunk<kFeat>(I, S, gp, c2, smem_u32(stage(seq + 2)), bar(seq + 2), want_bits);
+            else
+              issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
           }
-          return;
-        }
-        seq++;
-        if (!h1) break;
-        c0 = c1;
-        c1 = c2;
-        h1 = h2;
-        h2 = !wk.done();
-        if (h2) c2 = wk.take(I);
-      }
-    }
-    // the item's end: the last group's sums go to the first stage, past the
-    // zebra sweep's line buffer (a slow warp may still read that buffer; no
-    // copy is in flight, and every thread has passed the last chunk's
-    // barrier);
-    // warp w reduces sum w & 3 of group w >> 2 (lane j adds the threads j,
-    // j+32, ..., then a butterfly; float-float for the FP32 passes) and
-    // writes it, with the group's counts summed in warp order, to the
-    // group's partial slot (kNRed: 4 sums, 3 counts, a spare); thread 0 then
-    // advances the instance's arrival counter by the item's groups
-    const int nspan = grp_end - grp;
-    constexpr int kScrBytes = kTY * kTX * (int)sizeof(float);  // the register sweep's line buffer
-    double* last_sums = reinterpret_cast<double*>(stage0 + kScrBytes);
-    stash(last_sums, nspan - 1);
-    __syncthreads();
-    {
-      static_assert(kWarps == 4 * kMaxSpan, "one warp per sum of each group of an item");
-      static_assert(kScrBytes + 4 * kThreads * 8 <= kStageBytes, "last group's sums in the first stage");
-      const int gi = warp >> 2, k = warp & 3;
-      if (gi < nspan) {
-        const int ns = n_sums(S.pass, S.first_cg, S.gp32);
-        const double* src = (gi == nspan - 1 ? last_sums : &s_stash[0][0]) + k * kThreads;
-        double v = 0.0;
-        if (k < ns) {
-          if (ff_pass()) {
-            auto ld = [&](int t) {
-              const double d = src[t];
-              return FF{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
-            };
-            FF a = ld(lane);
-            for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-              a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
-                               __shfl_xor_sync(FULL_MASK, a.lo, off)});
-            v = ff_val(a);
+          unsigned char* st = stage(seq);
+          const bool ok = mbar_wait(bar(seq), (seq / kStages) & 1);
+          bool failed;
+          if (ok && want_bits) stage_bits(st, c0.x0, rpw, gp, fbits);
+          if (writes_stage) {
+            // the chunk has a barrier inside: agree on the wait first
+            failed = __syncthreads_or(!ok);
+            if (!failed) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
+            __syncthreads();  // the stage may be refilled
           } else {
-            v = src[lane];
-            for (int j = 1; j < kWarps; ++j) v += src[lane + 32 * j];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+            // one barrier per chunk: every thread is done with the stage (which
+            // may then be refilled) and no bounded wait gave up
+            if (ok) run_chunk<kFeat>(I, S, gp, st, c0, fbits, acc, ffs);
+            failed = __syncthreads_or(!ok);
+          }
+          if (c0.rows & kEndG0) stash(&s_stash[0][0], 0);
+          if (failed) {
+            // a copy never completed: record it, give the copies still in
+            // flight a bounded chance to land, and leave; the engine's loop
+            // then ends on its pass cap and the host reports the error
+            if (tid == 0) {
+              atomicOr(E.err, 1);
+              if (h1) mbar_wait(bar(seq + 1), ((seq + 1) / kStages) & 1);
+              if (kDepth == 2 && h2) mbar_wait(bar(seq + 2), ((seq + 2) / kStages) & 1);
+            }
+            return;
+          }
+          seq++;
+          if (!h1) break;
+          c0 = c1;
+          c1 = c2;
+          h1 = h2;
+          h2 = !wk.done();
+          if (h2) c2 = wk.take(I);
+        }
+      }
+      // the item's end: the last group's sums go to the first stage, past the
+      // zebra sweep's line buffer (a slow warp may still read that buffer; no
+      // copy is in flight, and every thread has passed the last chunk's
+      // barrier);
+      // warp w reduces sum w & 3 of group w >> 2 (lane j adds the threads j,
+      // j+32, ..., then a butterfly; float-float for the FP32 passes) and
+      // writes it, with the group's counts summed in warp order, to the
+      // group's partial slot (kNRed: 4 sums, 3 counts, a spare); thread 0 then
+      // advances the instance's arrival counter by the item's groups
+      const int nspan = grp_end - grp;
+      constexpr int kScrBytes = kTY * kTX * (int)sizeof(float);  // the register sweep's line buffer
+      double* last_sums = reinterpret_cast<double*>(stage0 + kScrBytes);
+      stash(last_sums, nspan - 1);
+      __syncthreads();
+      {
+        static_assert(kWarps == 4 * kMaxSpan, "one warp per sum of each group of an item");
+        static_assert(kScrBytes + 4 * kThreads * 8 <= kStageBytes, "last group's sums in the first stage");
+        const int gi = warp >> 2, k = warp & 3;
+        if (gi < nspan) {
+          const int ns = n_sums(S.pass, S.first_cg, S.gp32);
+          const double* src = (gi == nspan - 1 ? last_sums : &s_stash[0][0]) + k * kThreads;
+          double v = 0.0;
+          if (k < ns) {
+            if (ff_pass()) {
+              auto ld = [&](int t) {
+                const double d = src[t];
+                return FF{__int_as_float(__double2hiint(d)), __int_as_float(__double2loint(d))};
+              };
+              FF a = ld(lane);
+              for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
+  #pragma unroll
+              for (int off = 16; off > 0; off >>= 1)
+                a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
+                                 __shfl_xor_sync(FULL_MASK, a.lo, off)});
+              v = ff_val(a);
+            } else {
+              v = src[lane];
+              for (int j = 1; j < kWarps; ++j) v += src[lane + 32 * j];
+  #pragma unroll
+              for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+            }
+          }
+          double* P = part + (long long)(grp + gi) * kNRed;
+          if (lane == 0) {
+            P[k] = v;
+          } else if (lane == 1) {
+            // the counts as integers in the slots' bits (k == 3: the spare)
+            long long c = 0;
+            if (k < 3)
+              for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k][w];
+            P[4 + k] = __longlong_as_double(c);
           }
         }
-        double* P = I.part + (long long)(grp + gi) * kNRed;
-        if (lane == 0) {
-          P[k] = v;
-        } else if (lane == 1) {
-          // the counts as integers in the slots' bits (k == 3: the spare)
-          long long c = 0;
-          if (k < 3)
-            for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k][w];
-          P[4 + k] = __longlong_as_double(c);
-        }
       }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();  // the block's partial writes (ordered by the barrier) before the arrival
-      const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, (unsigned)nspan);
-      s_last = (prev + (unsigned)nspan == (unsigned)I.n_groups);
-    }
-    __syncthreads();
-    if (!s_last) continue;
-
-    // last group of this instance: reduce the group slots in a fixed order
-    // that depends on the shape only.  Warp k < 7 takes slot k: lane j loads
-    // the slots of groups j, j+32, ... (all loads in flight at once) and adds
-    // them in that order, then a butterfly; the sums in FP64, the counts
-    // (integers in the slots' bits) in integer arithmetic.  The last warp
-    // reads the control block meanwhile.  FP64 arithmetic is slow on GB300:
-    // one FP64 add per group and slot, none for the counts.
-    if (tid == 0) __threadfence();
-    __syncthreads();
-    long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
-    long long* cs = reinterpret_cast<long long*>(&sC);
-    {
-      static_assert(kWarps >= kNRed, "one warp per reduced slot and one for the control block");
-      constexpr int kPer = (kMaxGroups + 31) / 32;
-      if (warp == kWarps - 1) {
-        for (int j = lane; j < (int)(sizeof(Ctl) / 8); j += 32) cs[j] = __ldcg(cg + j);
-      } else if (warp < kNRed - 1) {
-        const int k = warp;
-        const double* P0 = I.part + k;
-        double v[kPer];
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-          const int gi = lane + 32 * q;
-          v[q] = gi < I.n_groups ? __ldcg(P0 + (long long)gi * kNRed) : 0.0;
-        }
-        if (k < 4) {
-          double t = v[0];
-#pragma unroll
-          for (int q = 1; q < kPer; ++q) t += v[q];
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL_MASK, t, off);
-          if (lane == 0) s_red[k] = t;
+      __syncthreads();
+      if (tid == 0) {
+        if (kCoop) {
+          // every block reduces: wait for all of them (the grid's arrivals
+          // accumulate over the launch's passes)
+          if (grid_barrier(E.gbar, (unsigned)(pi + 1) * gridDim.x)) {
+            s_last = 1;
+          } else {
+            atomicOr(E.err, 4);
+            s_last = -1;
+          }
         } else {
-          int c = 0;  // at most n < 2^31 points
-#pragma unroll
-          for (int q = 0; q < kPer; ++q) c += (int)__double_as_longlong(v[q]);
-          c = __reduce_add_sync(FULL_MASK, c);
-          if (lane == 0) s_red[k] = (double)c;
+          __threadfence();  // the block's partial writes (ordered by the barrier) before the arrival
+          const unsigned prev = atomicAdd(&E.ctl[tr.x].arrive, (unsigned)nspan);
+          s_last = (prev + (unsigned)nspan == (unsigned)I.n_groups);
         }
       }
+      __syncthreads();
+      if (s_last < 0) return;  // the grid barrier gave up: nothing is in flight
+      if (!s_last) continue;
+
+      // last group of this instance: reduce the group slots in a fixed order
+      // that depends on the shape only.  Warp k < 7 takes slot k: lane j loads
+      // the slots of groups j, j+32, ... (all loads in flight at once) and adds
+      // them in that order, then a butterfly; the sums in FP64, the counts
+      // (integers in the slots' bits) in integer arithmetic.  The last warp
+      // reads the control block meanwhile.  FP64 arithmetic is slow on GB300:
+      // one FP64 add per group and slot, none for the counts.
+      if (!kCoop && tid == 0) __threadfence();  // (the grid barrier has fenced)
+      __syncthreads();
+      long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
+      long long* cs = reinterpret_cast<long long*>(&sC);
+      {
+        static_assert(kWarps >= kNRed, "one warp per reduced slot and one for the control block");
+        constexpr int kPer = (kMaxGroups + 31) / 32;
+        if (warp == kWarps - 1) {
+          // (the cooperative kernel's own copy is the state: block 0 may be
+          // rewriting the global one already)
+          if (!kCoop)
+            for (int j = lane; j < (int)(sizeof(Ctl) / 8); j += 32) cs[j] = __ldcg(cg + j);
+        } else if (warp < kNRed - 1) {
+          const int k = warp;
+          const double* P0 = part + k;
+          double v[kPer];
+  #pragma unroll
+          for (int q = 0; q < kPer; ++q) {
+            const int gi = lane + 32 * q;
+            v[q] = gi < I.n_groups ? __ldcg(P0 + (long long)gi * kNRed) : 0.0;
+          }
+          if (k < 4) {
+            double t = v[0];
+  #pragma unroll
+            for (int q = 1; q < kPer; ++q) t += v[q];
+  #pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL_MASK, t, off);
+            if (lane == 0) s_red[k] = t;
+          } else {
+            int c = 0;  // at most n < 2^31 points
+  #pragma unroll
+            for (int q = 0; q < kPer; ++q) c += (int)__double_as_longlong(v[q]);
+            c = __reduce_add_sync(FULL_MASK, c);
+            if (lane == 0) s_red[k] = (double)c;
+          }
+        }
+      }
+      __syncthreads();
+      if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_COUNT) {
+        // the groups' offsets in the compact numbering (exclusive prefix sum
+        // of their free counts, two groups per thread)
+        static_assert(kMaxGroups <= 2 * kThreads, "two groups per thread");
+        int t0, t1;
+        const double* P0 = I.part;
+        const int c0 =
+            tid < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)tid * kNRed + 4)) : 0;
+        const int o0 = cta_excl_scan(c0, s_scan, t0);
+        const int g1 = tid + kThreads;
+        const int c1 =
+            g1 < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)g1 * kNRed + 4)) : 0;
+        const int o1 = cta_excl_scan(c1, s_scan, t1);
+        if (tid < I.n_groups) I.goff[tid] = o0;
+        if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
+      }
+      // the state machine runs on the shared copy of the control block (one
+      // round trip in, one out, instead of dependent global accesses)
+      if (tid == 0) {
+        s_red[kNRed - 1] = 0.0;
+        sC.arrive = 0u;
+        finalize(I, sC, s_red, (!kCoop || blockIdx.x == 0) ? E.live : &s_live);
+        if (kCoop && blockIdx.x == 0) atomicAdd(E.npass, 1u);
+      }
+      __syncthreads();
+      if ((!kCoop || blockIdx.x == 0) && tid < (int)(sizeof(Ctl) / 8)) __stcg(cg + tid, cs[tid]);
+      if (kCoop) {
+        // every block holds the same next state: run it, unless the instance
+        // is done, the state is held (a standalone launch) or the pass cap is
+        // reached
+        again = sC.pass != P_NONE && !sC.hold && (unsigned)(pi + 1) < E.pass_cap;
+        break;
+      }
     }
-    __syncthreads();
-    if ((kFeat & FEAT_EXT) != 0 && S.pass == P_RX_COUNT) {
-      // the groups' offsets in the compact numbering (exclusive prefix sum
-      // of their free counts, two groups per thread)
-      static_assert(kMaxGroups <= 2 * kThreads, "two groups per thread");
-      int t0, t1;
-      const double* P0 = I.part;
-      const int c0 =
-          tid < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)tid * kNRed + 4)) : 0;
-      const int o0 = cta_excl_scan(c0, s_scan, t0);
-      const int g1 = tid + kThreads;
-      const int c1 =
-          g1 < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)g1 * kNRed + 4)) : 0;
-      const int o1 = cta_excl_scan(c1, s_scan, t1);
-      if (tid < I.n_groups) I.goff[tid] = o0;
-      if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
-    }
-    // the state machine runs on the shared copy of the control block (one
-    // round trip in, one out, instead of dependent global accesses)
-    if (tid == 0) {
-      s_red[kNRed - 1] = 0.0;
-      sC.arrive = 0u;
-      finalize(I, sC, s_red, E.live);
-    }
-    __syncthreads();
-    if (tid < (int)(sizeof(Ctl) / 8)) __stcg(cg + tid, cs[tid]);
+    if (!again) break;
   }
 
   // the last CTA to leave resets the queue for the next launch
@@ -4129,10 +4235,23 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E
     if (atomicAdd(E.exits, 1u) == gridDim.x - 1) {
       *E.queue = 0;
       *E.exits = 0u;
+      if (kCoop) *E.gbar = 0u;
       __threadfence();
     }
   }
 }
+
+#if GPCG_COOP
+template <int kFeat>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel_coop(EngineArgs E) {
+  pass_body<false, kFeat>(E);
+}
+#else
+template <bool kCond, int kFeat>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) pass_kernel(EngineArgs E) {
+  pass_body<kCond, kFeat>(E);
+}
+#endif
 
 }  // namespace
 }  // namespace gpcg

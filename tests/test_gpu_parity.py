@@ -590,6 +590,67 @@ def test_engine_modes_agree(monkeypatch, prec):
         assert res[0][1]["passes"] == st["passes"]
 
 
+def _qp2(nx, ny, seed, bounds="two_sided"):
+    return gi.grid_qp_2d(nx, ny, seed=seed, shift=0.01, bounds=bounds)
+
+
+def _qp3(nx, ny, nz, seed):
+    return gi.grid_qp_3d(nx, ny, nz, seed=seed, shift=0.02, sigma=0.5,
+                         axis_scale=(1.0, 3.0, 9.0), bounds="box1")
+
+
+COOP_CASES = {
+    "2d_mixed": (lambda: _qp2(200, 150, 660), dict(precision=g.MIXED)),
+    "2d_mixed_refine1": (lambda: _qp2(200, 150, 660), dict(precision=g.MIXED, refine=1)),
+    "2d_fp64": (lambda: _qp2(200, 150, 660), dict(precision=g.FP64)),
+    "2d_large_mixed": (lambda: _qp2(700, 611, 661, "box1"), dict(precision=g.MIXED)),
+    "2d_ragged_fp64": (lambda: _qp2(129, 5, 662, "lower0"), dict(precision=g.FP64)),
+    "3d_mixed": (lambda: _qp3(40, 33, 20, 663), dict(precision=g.MIXED)),
+    "3d_fp64": (lambda: _qp3(40, 33, 20, 663), dict(precision=g.FP64)),
+    "jacobi_mixed": (lambda: _qp2(130, 70, 664), dict(precision=g.MIXED,
+                                                      precond=g.PRECOND_JACOBI)),
+    "tile_mixed": (lambda: _qp2(130, 70, 665), dict(precision=g.MIXED, precond=g.PRECOND_TILE)),
+    "tile_fp64": (lambda: _qp2(130, 70, 665), dict(precision=g.FP64, precond=g.PRECOND_TILE)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(COOP_CASES))
+def test_cooperative_solve_equals_pass_launches(monkeypatch, case):
+    """A lone engine solve runs every pass in one cooperative launch (a grid
+    barrier between passes; every block reduces the partials and steps the
+    state machine on its own copy); with GPCG_NO_COOP=1 the same passes run as
+    launches of a WHILE graph.  The arithmetic and its order are the same, so
+    the results are identical bit for bit, and the cooperative solve meets the
+    oracle's tolerance."""
+    make, opts = COOP_CASES[case]
+    qp = make()
+    res = {}
+    for off in ("0", "1"):
+        monkeypatch.setenv("GPCG_NO_COOP", off)
+        status, x, st = _solve_on("engine", qp, tau_rel=1e-10, **opts)
+        assert status == 0, (off, status)
+        res[off] = (x, st)
+    (xc, sc), (xg, sg) = res["0"], res["1"]
+    assert sc["launches"] == 1 and sg["launches"] >= sg["passes"] > 1
+    assert np.array_equal(xc, xg)
+    for key in ("passes", "outer_iters", "gp_iters", "cg_iters", "ls_trials", "n_active",
+                "n_binding", "q", "pg_norm", "alg_bytes", "staged"):
+        assert sc[key] == sg[key], key
+    if opts.get("precond", 0) != g.PRECOND_TILE:  # (its parity needs tau 1e-12: tested apart)
+        ref = oracle.solve(qp, tau_rel=1e-10, precond=opts.get("precond", 0))
+        assert _rel_err(xc, ref.x) <= (1e-9 if opts["precision"] == g.FP64 else 1e-5)
+
+
+def test_cooperative_solve_pass_cap(monkeypatch):
+    """The pass cap ends a cooperative solve after exactly that many passes,
+    with the state of its last pass readable."""
+    qp = _qp2(90, 70, 666)
+    monkeypatch.setenv("GPCG_PASS_CAP", "23")
+    status, x, st = _solve_on("engine", qp, tau_rel=1e-12, precision=g.MIXED)
+    assert status == g.ERR_TIMEOUT and st["launches"] == 1 and st["passes"] == 23
+    assert np.all((x >= qp.l) & (x <= qp.u))
+
+
 @pytest.mark.parametrize("shape,bounds", [((65, 33), "two_sided"), ((100, 70), "box1"),
                                           ((129, 5), "lower0"), ((200, 131), "two_sided")])
 def test_mixed_staged_and_register_paths(monkeypatch, shape, bounds):
