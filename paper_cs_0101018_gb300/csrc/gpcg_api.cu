@@ -29,6 +29,7 @@ const void* pass_kernel_ptr(bool cond, int feat);
 int pass_grid(int n_work);
 cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
 cudaError_t launch_pass_coop(const EngineArgs& E, int n_blocks, cudaStream_t s, int feat);
+std::mutex& coop_mutex();
 size_t resident_smem(int dim, long long n, bool mixed, bool jacobi);
 cudaError_t launch_resident(const DevInst* insts, const int* ids, Ctl* ctl, int count,
                             size_t smem, unsigned sweep_cap, cudaStream_t s);
@@ -1302,6 +1303,7 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   const unsigned cap = env_pass_cap();
   const int mode = env_engine_mode();
   *coop_used = false;
+  std::unique_lock<std::mutex> coop_lock;  // held until a cooperative kernel has finished
   sc.h_pin[0] = n_live;
   sc.h_pin[1] = 0;
   CK(cudaMemcpyAsync(sc.d_live, &sc.h_pin[0], sizeof(int), cudaMemcpyHostToDevice, s));
@@ -1309,6 +1311,7 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   if (mode == 0 && coop && tiles > 0 && tiles <= (long long)pass_grid(1 << 30)) {
     // every pass in one launch: the counters (queue, exits, barrier) start
     // at zero; the pass cap keeps the barrier's running count below 2^32
+    coop_lock = std::unique_lock<std::mutex>(coop_mutex());
     CK(cudaMemsetAsync(sc.d_queue, 0, 4 * sizeof(int), s));
     EngineArgs args{sc.d_insts, sc.d_ctl,  sc.d_tiles, (int)tiles, sc.d_queue, (unsigned*)(sc.d_queue + 1),
                     sc.d_live,   sc.d_npass, sc.d_queue + 2, cap, 0ull};
@@ -1319,6 +1322,7 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
       *coop_used = true;
     } else {
       cudaGetLastError();  // not launched (no room for every block): run the graph below
+      coop_lock.unlock();
     }
   }
   if (*coop_used) {

@@ -458,6 +458,15 @@ cudaError_t launch_pass(const EngineArgs& E, int n_blocks, cudaStream_t s, int f
                           kDynSmem, s);
 }
 
+// One cooperative pass kernel at a time per device: two whose blocks were
+// resident only in part could each wait at its grid barrier for blocks that
+// the other keeps from running.  The caller holds this lock from the launch
+// until the kernel has finished.
+std::mutex& coop_mutex() {
+  static std::mutex mu[kMaxDevices];
+  return mu[device_now()];
+}
+
 // Every pass of one solve in one cooperative launch of n_blocks blocks (one
 // work item each).  Fails without launching when the blocks cannot all be
 // resident at once (cudaErrorCooperativeLaunchTooLarge) or the feature set
