@@ -3810,6 +3810,7 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
   __shared__ int s_gcnt[kMaxSpan][3][kWarps];  // the warps' counts per group of the item
   __shared__ int s_t, s_inst, s_last;
   __shared__ int s_live;  // the cooperative kernel's blocks other than 0 count out here
+  __shared__ int s_spec;  // cooperative kernel: chunks of the next pass issued ahead (< 0: dropped)
   extern __shared__ unsigned char dyn_smem[];
   static_assert(sizeof(DevInst) % 8 == 0 && sizeof(DevInst) / 8 <= kThreads, "descriptor copy");
   static_assert(sizeof(Ctl) % 8 == 0 && sizeof(Ctl) / 8 <= kThreads, "control block copy");
@@ -3848,6 +3849,7 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
     }
   }
   int seq = 0;  // chunks of the TMA pipeline consumed so far (same in all threads)
+  int pre = 0;  // chunks of this pass already issued by the previous one (cooperative kernel)
 
   for (int pi = 0;; ++pi) {  // passes of the launch (one unless cooperative)
     bool again = false;        // the cooperative kernel runs another pass
@@ -3855,8 +3857,10 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
       __syncthreads();  // the previous item's shared state is no longer read
       // the first item of a CTA is its own index; later ones are claimed (the
       // cooperative kernel has one item per block)
-      if (tid == 0)
+      if (tid == 0) {
         s_t = first ? (int)blockIdx.x : (kCoop ? E.n_work : (int)gridDim.x + atomicAdd(E.queue, 1));
+        s_spec = 0;
+      }
       __syncthreads();
       const int t = s_t;
       if (t >= E.n_work) break;
@@ -3907,7 +3911,7 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
       }
 
       Acc acc;
-  #pragma unroll
+#pragma unroll
       for (int k = 0; k < 4; ++k) acc.s[k] = 0.0;
       acc.c[0] = acc.c[1] = acc.c[2] = 0;
       FF ffs[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -3935,19 +3939,19 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
       // group's sums do not depend on the item that holds it.
       auto stash = [&](double* dst, int gi) {
         const bool ffred = ff_pass();
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           const double v = ffred ? __hiloint2double(__float_as_int(ffs[k].hi),
                                                     __float_as_int(ffs[k].lo))
                                  : acc.s[k];
           asm volatile("st.shared.f64 [%0], %1;" ::"r"(smem_u32(dst + k * kThreads + tid)), "d"(v));
         }
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int c = __reduce_add_sync(FULL_MASK, acc.c[k]);
           if (lane == 0) s_gcnt[gi][k][warp] = c;
         }
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
           acc.s[k] = 0.0;
           ffs[k] = FF{0.f, 0.f};
@@ -4020,13 +4024,14 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
         bool h1 = hh1, h2 = hh2;
         auto stage = [&](int q) { return stage0 + (q % kStages) * kStageBytes; };
         auto bar = [&](int q) { return smem_u32(&bars[q % kStages]); };
-        if (tid == 0) {
+        if (tid == 0 && pre == 0) {
           // order earlier generic writes to the stages before the copies
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           issue_chunk<kFeat>(I, S, gp, c0, smem_u32(stage(seq)), bar(seq), want_bits);
           if (kDepth == 2 && h1)
             issue_chunk<kFeat>(I, S, gp, c1, smem_u32(stage(seq + 1)), bar(seq + 1), want_bits);
         }
+        pre = 0;  // (the previous pass issued exactly these chunks)
         unsigned fbits[4] = {0u, 0u, 0u, 0u};
         for (;;) {
           if (tid == 0 && (kDepth == 2 ? h2 : h1)) {
@@ -4103,7 +4108,7 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
               };
               FF a = ld(lane);
               for (int j = 1; j < kWarps; ++j) a = ff_add(a, ld(lane + 32 * j));
-  #pragma unroll
+#pragma unroll
               for (int off = 16; off > 0; off >>= 1)
                 a = ff_add(a, FF{__shfl_xor_sync(FULL_MASK, a.hi, off),
                                  __shfl_xor_sync(FULL_MASK, a.lo, off)});
@@ -4111,7 +4116,7 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
             } else {
               v = src[lane];
               for (int j = 1; j < kWarps; ++j) v += src[lane + 32 * j];
-  #pragma unroll
+#pragma unroll
               for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
             }
           }
@@ -4157,6 +4162,27 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
       // one FP64 add per group and slot, none for the counts.
       if (!kCoop && tid == 0) __threadfence();  // (the grid barrier has fenced)
       __syncthreads();
+      if (kCoop && warp == kWarps - 1 && lane == 0 && S.pass == P_CG_F &&
+          I.opt.precond != PC_TILE) {
+        // cooperative kernel: the next pass's first chunks, issued now on the
+        // guess that a fused CG step is followed by another (most are).  The
+        // copies read what this pass wrote, which the grid barrier has
+        // published, and none of the step's scalars, so their latency hides
+        // behind this reduction and the state machine; a wrong guess only
+        // lets them land and drops them.
+        Snap nx = S;
+        nx.pcur ^= 1;
+        Walk w2(I, grp, grp_end, chunk_rows(I, nx, false));
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        int n = 0;
+        for (; n < kStages - 1 && !w2.done(); ++n) {
+          const int q = (seq + n) % kStages;
+          issue_chunk<kFeat>(I, nx, false, w2.take(I), smem_u32(stage0 + q * kStageBytes),
+                             smem_u32(&bars[q]), true);
+        }
+        s_spec = n;
+      }
       long long* cg = reinterpret_cast<long long*>(E.ctl + tr.x);
       long long* cs = reinterpret_cast<long long*>(&sC);
       {
@@ -4171,21 +4197,21 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
           const int k = warp;
           const double* P0 = part + k;
           double v[kPer];
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < kPer; ++q) {
             const int gi = lane + 32 * q;
             v[q] = gi < I.n_groups ? __ldcg(P0 + (long long)gi * kNRed) : 0.0;
           }
           if (k < 4) {
             double t = v[0];
-  #pragma unroll
+#pragma unroll
             for (int q = 1; q < kPer; ++q) t += v[q];
-  #pragma unroll
+#pragma unroll
             for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(FULL_MASK, t, off);
             if (lane == 0) s_red[k] = t;
           } else {
             int c = 0;  // at most n < 2^31 points
-  #pragma unroll
+#pragma unroll
             for (int q = 0; q < kPer; ++q) c += (int)__double_as_longlong(v[q]);
             c = __reduce_add_sync(FULL_MASK, c);
             if (lane == 0) s_red[k] = (double)c;
@@ -4216,6 +4242,20 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
         sC.arrive = 0u;
         finalize(I, sC, s_red, (!kCoop || blockIdx.x == 0) ? E.live : &s_live);
         if (kCoop && blockIdx.x == 0) atomicAdd(E.npass, 1u);
+        if (kCoop && s_spec > 0) {
+          // the guess holds when another fused step of this block's item
+          // follows on the other buffers; else the issued chunks land and
+          // their stages count as consumed
+          const bool next = sC.pass != P_NONE && !sC.hold && (unsigned)(pi + 1) < E.pass_cap;
+          if (!(next && sC.pass == P_CG_F && sC.pcur == (S.pcur ^ 1) && sC.cur == S.cur &&
+                sC.cg32 == S.cg32)) {
+            bool ok = true;
+            for (int n = 0; n < s_spec; ++n)
+              ok = mbar_wait(smem_u32(&bars[(seq + n) % kStages]), ((seq + n) / kStages) & 1) && ok;
+            if (!ok) atomicOr(E.err, 1);
+            s_spec = -s_spec;
+          }
+        }
       }
       __syncthreads();
       if ((!kCoop || blockIdx.x == 0) && tid < (int)(sizeof(Ctl) / 8)) __stcg(cg + tid, cs[tid]);
@@ -4224,6 +4264,9 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
         // is done, the state is held (a standalone launch) or the pass cap is
         // reached
         again = sC.pass != P_NONE && !sC.hold && (unsigned)(pi + 1) < E.pass_cap;
+        const int sp = s_spec;
+        if (sp < 0) seq -= sp;  // dropped chunks
+        pre = sp > 0 ? sp : 0;
         break;
       }
     }
