@@ -651,6 +651,45 @@ def test_cooperative_solve_pass_cap(monkeypatch):
     assert np.all((x >= qp.l) & (x <= qp.u))
 
 
+def test_concurrent_cooperative_solves():
+    """Lone solves issued from several host threads on their own streams (each
+    a cooperative launch; the library runs one at a time per device) give the
+    same bits as the same solves one after the other."""
+    import threading
+
+    torch = pytest.importorskip("torch")
+    qps = [_qp2(300, 260, 670 + k, ("two_sided", "box1", "lower0")[k % 3]) for k in range(4)]
+    qps.append(_qp3(30, 28, 26, 675))
+    precs = [g.MIXED, g.FP64, g.MIXED, g.FP64, g.MIXED]
+    probs = [g.gpcg_problem_create(qp) for qp in qps]
+    alone = []
+    for prob, prec in zip(probs, precs):
+        g.gpcg_solve(prob, g.default_options(tau_rel=1e-9, precision=prec, path=g.PATH_ENGINE))
+        alone.append(g.gpcg_result(prob))
+    streams = [torch.cuda.Stream() for _ in probs]
+    status = [None] * len(probs)
+
+    def work(k):
+        for _ in range(3):
+            status[k] = g.gpcg_solve(probs[k], g.default_options(
+                tau_rel=1e-9, precision=precs[k], path=g.PATH_ENGINE, stream=streams[k]),
+                check=False)
+            if status[k] != 0:
+                return
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(len(probs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    for k, prob in enumerate(probs):
+        assert status[k] == 0, (k, status[k])
+        x, st = g.gpcg_result(prob)
+        assert st["launches"] == 1
+        assert np.array_equal(x, alone[k][0]) and st["passes"] == alone[k][1]["passes"]
+
+
 @pytest.mark.parametrize("shape,bounds", [((65, 33), "two_sided"), ((100, 70), "box1"),
                                           ((129, 5), "lower0"), ((200, 131), "two_sided")])
 def test_mixed_staged_and_register_paths(monkeypatch, shape, bounds):
