@@ -232,7 +232,14 @@ typedef enum {
 void gpcg_default_options(gpcg_options* o);
 
 /* Run GPCG (Sec. 3, Algorithm GPCG) on one problem; blocks until it ends.
- * Returns the solve's status (GPCG_OK when the tolerance was met). */
+ * Returns the solve's status (GPCG_OK when the tolerance was met).
+ * On the pass engine every pass of the solve runs in one cooperative kernel
+ * launch (all blocks resident; a grid barrier between passes), except with
+ * GPCG_CG_EXTRACTED, when the launch is refused, or when the environment
+ * sets GPCG_NO_COOP=1: the passes then run as launches of a CUDA graph, with
+ * bit-identical results.  Solves may be issued from several host threads on
+ * their own streams; the cooperative kernels of one device run one at a
+ * time. */
 gpcg_status gpcg_solve(gpcg_problem* p, const gpcg_options* opt);
 
 /* Run GPCG on `count` independent problems at once: every pass of the engine
