@@ -195,7 +195,8 @@ struct DevInst {
   int dim, nx, ny, nz, px, mw, tiles_x, tiles_y, n_tiles, kc;
   int n_groups, span;      // groups of the instance; groups per work item of this launch
   long long n, plane;
-  double* part;            // [n_groups][kNRed] group partial sums of this instance
+  double* part;            // [2][kNRed][n_groups] group partial sums of this instance
+                           // (slot-major; the cooperative kernel alternates the two)
   const void* tmaps;       // M_COUNT CUtensorMaps in device memory (64-byte aligned)
   int tma64, tma32;        // the FP64 / FP32 CG maps are valid
   int tma_gp, tma_mask;    // the mixed-phase GP maps / the mask maps are valid

@@ -4085,8 +4085,10 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
       // warp w reduces sum w & 3 of group w >> 2 (lane j adds the threads j,
       // j+32, ..., then a butterfly; float-float for the FP32 passes) and
       // writes it, with the group's counts summed in warp order, to the
-      // group's partial slot (kNRed: 4 sums, 3 counts, a spare); thread 0 then
-      // advances the instance's arrival counter by the item's groups
+      // group's partial slots (kNRed per group: 4 sums, 3 counts, a spare;
+      // stored slot-major, [k][group], so that the finalizer's loads of one
+      // slot over the groups are contiguous); thread 0 then advances the
+      // instance's arrival counter by the item's groups
       const int nspan = grp_end - grp;
       constexpr int kScrBytes = kTY * kTX * (int)sizeof(float);  // the register sweep's line buffer
       double* last_sums = reinterpret_cast<double*>(stage0 + kScrBytes);
@@ -4120,15 +4122,16 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
               for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
             }
           }
-          double* P = part + (long long)(grp + gi) * kNRed;
+          double* P = part + grp + gi;
+          const long long ng = I.n_groups;
           if (lane == 0) {
-            P[k] = v;
+            P[k * ng] = v;
           } else if (lane == 1) {
             // the counts as integers in the slots' bits (k == 3: the spare)
             long long c = 0;
             if (k < 3)
               for (int w = 0; w < kWarps; ++w) c += s_gcnt[gi][k][w];
-            P[4 + k] = __longlong_as_double(c);
+            P[(4 + k) * ng] = __longlong_as_double(c);
           }
         }
       }
@@ -4155,10 +4158,12 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
 
       // last group of this instance: reduce the group slots in a fixed order
       // that depends on the shape only.  Warp k < 7 takes slot k: lane j loads
-      // the slots of groups j, j+32, ... (all loads in flight at once) and adds
-      // them in that order, then a butterfly; the sums in FP64, the counts
-      // (integers in the slots' bits) in integer arithmetic.  The last warp
-      // reads the control block meanwhile.  FP64 arithmetic is slow on GB300:
+      // the slots of groups j, j+32, ... (all loads in flight at once; each
+      // load of the warp reads 32 consecutive groups) and adds them in that
+      // order, then a butterfly; the sums in FP64, the counts (integers in the
+      // slots' bits) in integer arithmetic.  The last warp reads the control
+      // block meanwhile (the cooperative kernel: issues the guessed next
+      // pass's first chunks).  FP64 arithmetic is slow on GB300:
       // one FP64 add per group and slot, none for the counts.
       if (!kCoop && tid == 0) __threadfence();  // (the grid barrier has fenced)
       __syncthreads();
@@ -4195,12 +4200,12 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
             for (int j = lane; j < (int)(sizeof(Ctl) / 8); j += 32) cs[j] = __ldcg(cg + j);
         } else if (warp < kNRed - 1) {
           const int k = warp;
-          const double* P0 = part + k;
+          const double* P0 = part + (long long)k * I.n_groups;
           double v[kPer];
 #pragma unroll
           for (int q = 0; q < kPer; ++q) {
             const int gi = lane + 32 * q;
-            v[q] = gi < I.n_groups ? __ldcg(P0 + (long long)gi * kNRed) : 0.0;
+            v[q] = gi < I.n_groups ? __ldcg(P0 + gi) : 0.0;
           }
           if (k < 4) {
             double t = v[0];
@@ -4224,13 +4229,11 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
         // of their free counts, two groups per thread)
         static_assert(kMaxGroups <= 2 * kThreads, "two groups per thread");
         int t0, t1;
-        const double* P0 = I.part;
-        const int c0 =
-            tid < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)tid * kNRed + 4)) : 0;
+        const double* P0 = I.part + 4LL * I.n_groups;  // slot 4: the free counts
+        const int c0 = tid < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + tid)) : 0;
         const int o0 = cta_excl_scan(c0, s_scan, t0);
         const int g1 = tid + kThreads;
-        const int c1 =
-            g1 < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + (long long)g1 * kNRed + 4)) : 0;
+        const int c1 = g1 < I.n_groups ? (int)__double_as_longlong(__ldcg(P0 + g1)) : 0;
         const int o1 = cta_excl_scan(c1, s_scan, t1);
         if (tid < I.n_groups) I.goff[tid] = o0;
         if (g1 < I.n_groups) I.goff[g1] = t0 + o1;
