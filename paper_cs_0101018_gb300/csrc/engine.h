@@ -82,6 +82,7 @@ enum TMap : int {
   // b32 and the FP32 diag, cx; 72 x 19 from (x0-4, y-2) of the FP32 cy
   MG_X2H0, MG_X2H1, MG_L2H, MG_U2H, MG_G2H0, MG_G2H1, MG_B18, MG_D18, MG_CX18, MG_CY19,
   M_MASK0, M_MASK1,  // free-set words of mask[0], mask[1]: box 4 words x 32 rows
+  M_MASKH0, M_MASKH1,  // the same words, box 8 words x 18 rows (staged first CG step)
   // the staged FP64 GP passes (FEAT_F64 kernels): halo boxes 68 x 10 from
   // (x0-2, y-1) of x[2], g[2], l, u, w (FP64), and b as a 64 x 8 box
   MF_X0, MF_X1, MF_G0, MF_G1, MF_L, MF_U, MF_W, MF_B,

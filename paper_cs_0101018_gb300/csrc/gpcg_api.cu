@@ -499,23 +499,25 @@ static bool make_gp_maps(gpcg_problem* p, cudaStream_t s) {
   return ok && q == m + kGpMaps && put_maps(p, MG_X32H0, kGpMaps, s);
 }
 
-// The free-set words as a 2-D u32 tensor (mw words x ny*nz rows), box 4 x 32.
+// The free-set words as a 2-D u32 tensor (mw words x ny*nz rows): boxes 4 x 32
+// (M_MASK0/1) and 8 x 18 (M_MASKH0/1, the staged first CG step's halo).
 static bool make_mask_maps(gpcg_problem* p, cudaStream_t s) {
   if (!have_encode()) return false;
+  static_assert(M_MASKH0 == M_MASK0 + 2, "mask maps in a row");
   DevInst& I = p->inst;
   CUtensorMap* m = &p->hmaps[M_MASK0];
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 4; ++k) {
     cuuint64_t dims[2] = {(cuuint64_t)p->mw, (cuuint64_t)p->ny * (cuuint64_t)p->nz};
     cuuint64_t strides[1] = {(cuuint64_t)p->mw * 4};
-    cuuint32_t box[2] = {4, 32};
+    cuuint32_t box[2] = {k < 2 ? 4u : 8u, k < 2 ? 32u : 18u};
     cuuint32_t estr[2] = {1, 1};
-    if (g_encode(&m[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, I.mask[k], dims, strides, box, estr,
-                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    if (g_encode(&m[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, I.mask[k & 1], dims, strides, box,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                  CU_TENSOR_MAP_L2_PROMOTION_NONE,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
-  return put_maps(p, M_MASK0, 2, s);
+  return put_maps(p, M_MASK0, 4, s);
 }
 
 // Encode the tile preconditioner's maps of one precision: FZH[2], FQH[2],

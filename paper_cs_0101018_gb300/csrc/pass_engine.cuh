@@ -3390,12 +3390,141 @@ __device__ __forceinline__ void trial64_chunk(const DevInst& I, unsigned char* s
   acc.c[2] += write_mask(I, m_out, m_old, yc + ry, 0, x0, lane, fr[0], fr[1]);
 }
 
+// The first CG step of a mixed-phase CG phase (P_CG_B with first_cg: FP32
+// CG, FP32 gradient, 2-D, no preconditioner), staged: the operand p_0 =
+// -g_F needs the free bits of the halo points, taken from a mask box 8
+// words wide (from word ((x0/32) - 1) rounded down to a multiple of 4, so
+// that it covers columns x0-4 .. x0+67) and 18 rows high from y-1.  Stage
+// layout: G (g32, 72 x 18 from (x0-4, y-1)) | M (8 x 18 words) | D 64 x 16 |
+// CX 68 x 16 from x0-4 | CY 64 x 17 from y-1 (the fused step's band maps).
+struct GeoB0 {
+  static constexpr int CH = 16, H = 4, BW = 64 + 2 * H, MW = 8;
+  static constexpr int OFF_G = 0, OFF_M = align128((CH + 2) * BW * 4);
+  static constexpr int OFF_D = OFF_M + align128(MW * (CH + 2) * 4);
+  static constexpr int OFF_CX = OFF_D + 64 * CH * 4;
+  static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
+  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr unsigned TX =
+      ((CH + 2) * BW + MW * (CH + 2) + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * 4;
+};
+static_assert(GeoB0::END <= kOffMask && GeoB0::CH == GeoF<float>::CH && GeoB0::H == GeoGP::H,
+              "stage layout (the fused FP32 step's band maps, the GP passes' g32 maps)");
+
+__device__ __forceinline__ bool first_staged(const DevInst& I, const Snap& S) {
+  return S.pass == P_CG_B && S.first_cg && S.cg32 && S.gp32 && I.dim == 2 &&
+         I.opt.precond == PC_NONE && I.tma32 && I.tma_gp && I.tma_mask;
+}
+
+// The mask box's first word column for a chunk at column x0 (a multiple of
+// 4 words, 16 bytes; negative at the grid's west edge, where the box is
+// zero-filled).
+__device__ __forceinline__ int first_mask_word(int x0) { return ((x0 >> 5) - 1) & ~3; }
+
+__device__ __forceinline__ void issue_cgb0(const DevInst& I, int cur, int x0, int yc, unsigned st,
+                                           unsigned bar) {
+  using G = GeoB0;
+  mbar_expect(bar, G::TX);
+  tma_load2d(st + G::OFF_G, tmap(I, MG_G32H0 + cur), x0 - G::H, yc - 1, bar);
+  tma_load2d(st + G::OFF_M, tmap(I, M_MASKH0 + cur), first_mask_word(x0), yc - 1, bar);
+  tma_load2d(st + G::OFF_D, tmap(I, M32_FD), x0, yc, bar);
+  tma_load2d(st + G::OFF_CX, tmap(I, M32_FCX), x0 - G::H, yc, bar);
+  tma_load2d(st + G::OFF_CY, tmap(I, M32_FCY), x0, yc - 1, bar);
+}
+
+// The staged first step on one chunk (warp w: rows 2w, 2w+1): p_0 = -g on
+// the free set (0 elsewhere), Ap_0 = Z Z' A Z Z' p_0 (the stencil in the
+// order of the register sweep), r_0 = g_F, w = 0; sums <p_0, Ap_0>,
+// <r_0, r_0> (= rho_0 = <r_0, z_0>) and <Ap_0, Ap_0>, the sums of P_CG_B's
+// first step.
+__device__ __forceinline__ void cgb0_chunk(const DevInst& I, const unsigned char* st, int x0,
+                                           int yc, int rows, float* p_out, float* ap_out,
+                                           float* r_out, float* w, FF* ff) {
+  using G = GeoB0;
+  constexpr int RPW = G::CH / kWarps;
+  const float* GS = reinterpret_cast<const float*>(st + G::OFF_G);
+  const unsigned* M = reinterpret_cast<const unsigned*>(st + G::OFF_M);
+  const float* D = reinterpret_cast<const float*>(st + G::OFF_D);
+  const float* CX = reinterpret_cast<const float*>(st + G::OFF_CX);
+  const float* CY = reinterpret_cast<const float*>(st + G::OFF_CY);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ylim = min(rows, I.ny - yc);
+  const int r0 = warp * RPW;  // first chunk row of this warp
+  if (r0 >= ylim) return;     // warp-uniform
+  const int c = 2 * lane;
+  const int e0 = x0 + c;
+  const bool v0 = e0 < I.nx, v1 = e0 + 1 < I.nx;
+  const int wx = first_mask_word(x0);
+  // the free bit of column col (x0-4 <= col < x0+68) in box row br
+  auto free_at = [&](int br, int col) {
+    return (M[br * G::MW + ((col >> 5) - wx)] >> (col & 31)) & 1u;
+  };
+  // window q = 0 .. RPW+1 is chunk row r0-1+q (box row r0+q)
+  float pn[RPW + 2][2], pw[RPW], pe[RPW];
+#pragma unroll
+  for (int q = 0; q < RPW + 2; ++q) {
+    const int br = r0 + q;
+    const float2 gv = *reinterpret_cast<const float2*>(GS + br * G::BW + G::H + c);
+    const unsigned wd = M[br * G::MW + ((e0 >> 5) - wx)] >> (e0 & 31);
+    pn[q][0] = (wd & 1u) ? -gv.x : 0.0f;
+    pn[q][1] = (wd & 2u) ? -gv.y : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
+    pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
+    const int br = r0 + k + 1, b = br * G::BW + G::H;
+    if (lane == 0) pw[k] = free_at(br, x0 - 1) ? -GS[b - 1] : 0.0f;
+    if (lane == 31) pe[k] = free_at(br, x0 + 64) ? -GS[b + 64] : 0.0f;
+  }
+  float s_pap = 0.0f, s_rr = 0.0f, s_apap = 0.0f;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int ry = r0 + k;
+    if (ry >= ylim) break;
+    const int q = k + 1;
+    const float* Dr = D + ry * 64 + c;
+    const float* Xr = CX + ry * (64 + G::H) + G::H + c;
+    const float* Ys = CY + ry * 64 + c;
+    const float* Yn = CY + (ry + 1) * 64 + c;
+    // diag, west, east, south, north (the order of the register sweep)
+    float a0 = Dr[0] * pn[q][0];
+    a0 = fmaf(Xr[-1], pw[k], a0);
+    a0 = fmaf(Xr[0], pn[q][1], a0);
+    a0 = fmaf(Ys[0], pn[q - 1][0], a0);
+    a0 = fmaf(Yn[0], pn[q + 1][0], a0);
+    float a1 = Dr[1] * pn[q][1];
+    a1 = fmaf(Xr[0], pn[q][0], a1);
+    a1 = fmaf(Xr[1], pe[k], a1);
+    a1 = fmaf(Ys[1], pn[q - 1][1], a1);
+    a1 = fmaf(Yn[1], pn[q + 1][1], a1);
+    const unsigned wd = M[(ry + 1) * G::MW + ((e0 >> 5) - wx)] >> (e0 & 31);
+    a0 = (wd & 1u) ? a0 : 0.0f;
+    a1 = (wd & 2u) ? a1 : 0.0f;
+    const long long i = (long long)(yc + ry) * I.px + e0;
+    st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
+    st2(ap_out, i, v0, v1, a0, a1);
+    st2(r_out, i, v0, v1, -pn[q][0], -pn[q][1]);
+    st2(w, i, v0, v1, 0.0f, 0.0f);
+    // points past nx hold zeros (the boxes are zero-filled there)
+    s_pap = fmaf(pn[q][0], a0, s_pap);
+    s_pap = fmaf(pn[q][1], a1, s_pap);
+    s_rr = fmaf(pn[q][0], pn[q][0], s_rr);
+    s_rr = fmaf(pn[q][1], pn[q][1], s_rr);
+    s_apap = fmaf(a0, a0, s_apap);
+    s_apap = fmaf(a1, a1, s_apap);
+  }
+  ff_acc(ff[0], s_pap);
+  ff_acc(ff[1], s_rr);
+  ff_acc(ff[2], s_apap);
+}
+
 // Whether the item's pass runs through the TMA pipeline.
 template <int kFeat>
 __device__ __forceinline__ bool tma_pass(const DevInst& I, const Snap& S) {
   if (gp_tma(I, S)) return true;
   if (alpha64_tma<kFeat>(I, S) || trial64_tma<kFeat>(I, S)) return true;
   if (S.pass == P_CG_F) return true;  // scheduled only for instances with the maps
+  if (first_staged(I, S)) return true;
   if (S.pass != P_CG_A && S.pass != P_CG_B) return false;
   if (!I.tma_mask) return false;
   const int ok = S.cg32 ? I.tma32 : I.tma64;
@@ -3412,6 +3541,7 @@ __device__ __forceinline__ int chunk_rows(const DevInst& I, const Snap& S, bool 
   if (S.pass == P_CG_A) return S.cg32 ? ChunkGeo<float>::CH_A : ChunkGeo<double>::CH_A;
   if (S.pass == P_CG_F && I.dim == 3) return GeoF3::CH;
   if (S.pass == P_CG_F) return S.cg32 ? GeoF<float>::CH : GeoF<double>::CH;
+  if (S.pass == P_CG_B && S.first_cg) return GeoB0::CH;  // (staged only as first_staged)
   return S.cg32 ? ChunkGeo<float>::CH : ChunkGeo<double>::CH;
 }
 
@@ -3516,6 +3646,8 @@ __device__ __forceinline__ void issue_chunk(const DevInst& I, const Snap& S, boo
   } else if (S.pass == P_CG_F) {
     if (S.cg32) issue_cgf<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cgf<double>(I, S.pcur, c.x0, c.yc, st, bar);
+  } else if (S.pass == P_CG_B && S.first_cg) {
+    issue_cgb0(I, S.cur, c.x0, c.yc, st, bar);  // (staged only as first_staged)
   } else if (S.cg32) {
     if (S.pass == P_CG_B) issue_cgb<float>(I, S.pcur, c.x0, c.yc, st, bar);
     else issue_cga<float>(I, S.pcur, c.x0, c.z * I.ny + c.yc, st, bar);
@@ -3590,6 +3722,9 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
     else
       cgf_chunk_box<false>(I, st, c.x0, c.yc, c.rows, S.alpha, S.beta, fbits, I.w64, I.r64[q],
                            I.p64[q], I.Ap64[q], acc);
+  } else if (S.pass == P_CG_B && S.first_cg) {
+    const int q = S.pcur ^ 1;
+    cgb0_chunk(I, st, c.x0, c.yc, c.rows, I.p32[q], I.Ap32[q], I.r32[q], I.w32, ffs);
   } else if (S.pass == P_CG_B) {
     const int q = S.pcur ^ 1;
     if (S.cg32)
@@ -4006,13 +4141,14 @@ __device__ __forceinline__ void pass_body(const EngineArgs& E) {
         constexpr int kDepth = kStages - 1;
         static_assert(kDepth == 1 || kDepth == 2, "prefetch depth");
         const bool gp = gp_tma(I, S);
-        const bool want_bits = S.pass == P_CG_B || S.pass == P_CG_F || (gp && S.pass == P_TRIAL);
+        const bool want_bits = (S.pass == P_CG_B && !S.first_cg) || S.pass == P_CG_F ||
+                               (gp && S.pass == P_TRIAL);
         const int ch = chunk_rows(I, S, gp);
         const int rpw = ch / kWarps;
         // chunks that write to their stage (and have block barriers inside)
         const bool writes_stage =
             gp ? trial_alpha0(S)
-               : (S.pass == P_CG_B || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
+               : ((S.pass == P_CG_B && !S.first_cg) || S.pass == P_GP_ALPHA || S.pass == P_TRIAL ||
                   (S.pass == P_CG_F && (!S.cg32 || I.opt.precond == PC_TILE)));
         Walk wk(I, grp, grp_end, ch);
         // the current chunk and the next two (h1, h2: they exist)
