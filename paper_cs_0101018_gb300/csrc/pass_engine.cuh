@@ -3391,28 +3391,33 @@ __device__ __forceinline__ void trial64_chunk(const DevInst& I, unsigned char* s
 }
 
 // The first CG step of a mixed-phase CG phase (P_CG_B with first_cg: FP32
-// CG, FP32 gradient, 2-D, no preconditioner), staged: the operand p_0 =
-// -g_F needs the free bits of the halo points, taken from a mask box 8
-// words wide (from word ((x0/32) - 1) rounded down to a multiple of 4, so
-// that it covers columns x0-4 .. x0+67) and 18 rows high from y-1.  Stage
-// layout: G (g32, 72 x 18 from (x0-4, y-1)) | M (8 x 18 words) | D 64 x 16 |
-// CX 68 x 16 from x0-4 | CY 64 x 17 from y-1 (the fused step's band maps).
+// CG, FP32 gradient, 2-D, no preconditioner or point Jacobi), staged: the
+// operand p_0 = -z_F (z = g, or g / diag) needs the free bits of the halo
+// points, taken from a mask box 8 words wide (from word ((x0/32) - 1)
+// rounded down to a multiple of 4, so that it covers columns x0-4 .. x0+67)
+// and 18 rows high from y-1.  Stage layout: G (g32, 72 x 18 from (x0-4,
+// y-1)) | M (8 x 18 words) | D 64 x 16 | CX 68 x 16 from x0-4 | CY 64 x 17
+// from y-1 (the fused step's band maps) | DI (1/diag, 72 x 18 from (x0-4,
+// y-1); point Jacobi only).
 struct GeoB0 {
   static constexpr int CH = 16, H = 4, BW = 64 + 2 * H, MW = 8;
   static constexpr int OFF_G = 0, OFF_M = align128((CH + 2) * BW * 4);
   static constexpr int OFF_D = OFF_M + align128(MW * (CH + 2) * 4);
   static constexpr int OFF_CX = OFF_D + 64 * CH * 4;
   static constexpr int OFF_CY = OFF_CX + align128((64 + H) * CH * 4);
-  static constexpr int END = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr int OFF_DI = OFF_CY + align128(64 * (CH + 1) * 4);
+  static constexpr int END = OFF_DI + align128((CH + 2) * BW * 4);
   static constexpr unsigned TX =
       ((CH + 2) * BW + MW * (CH + 2) + 64 * CH + (64 + H) * CH + 64 * (CH + 1)) * 4;
+  static constexpr unsigned TX_DI = (CH + 2) * BW * 4;
 };
 static_assert(GeoB0::END <= kOffMask && GeoB0::CH == GeoF<float>::CH && GeoB0::H == GeoGP::H,
               "stage layout (the fused FP32 step's band maps, the GP passes' g32 maps)");
 
 __device__ __forceinline__ bool first_staged(const DevInst& I, const Snap& S) {
   return S.pass == P_CG_B && S.first_cg && S.cg32 && S.gp32 && I.dim == 2 &&
-         I.opt.precond == PC_NONE && I.tma32 && I.tma_gp && I.tma_mask;
+         (I.opt.precond == PC_NONE || I.opt.precond == PC_JACOBI) && I.tma32 && I.tma_gp &&
+         I.tma_mask;
 }
 
 // The mask box's first word column for a chunk at column x0 (a multiple of
@@ -3423,7 +3428,9 @@ __device__ __forceinline__ int first_mask_word(int x0) { return ((x0 >> 5) - 1) 
 __device__ __forceinline__ void issue_cgb0(const DevInst& I, int cur, int x0, int yc, unsigned st,
                                            unsigned bar) {
   using G = GeoB0;
-  mbar_expect(bar, G::TX);
+  const bool jac = I.opt.precond == PC_JACOBI;
+  mbar_expect(bar, G::TX + (jac ? G::TX_DI : 0u));
+  if (jac) tma_load2d(st + G::OFF_DI, tmap(I, M32_FDIH), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_G, tmap(I, MG_G32H0 + cur), x0 - G::H, yc - 1, bar);
   tma_load2d(st + G::OFF_M, tmap(I, M_MASKH0 + cur), first_mask_word(x0), yc - 1, bar);
   tma_load2d(st + G::OFF_D, tmap(I, M32_FD), x0, yc, bar);
@@ -3431,15 +3438,17 @@ __device__ __forceinline__ void issue_cgb0(const DevInst& I, int cur, int x0, in
   tma_load2d(st + G::OFF_CY, tmap(I, M32_FCY), x0, yc - 1, bar);
 }
 
-// The staged first step on one chunk (warp w: rows 2w, 2w+1): p_0 = -g on
-// the free set (0 elsewhere), Ap_0 = Z Z' A Z Z' p_0 (the stencil in the
-// order of the register sweep), r_0 = g_F, w = 0; sums <p_0, Ap_0>,
-// <r_0, r_0> (= rho_0 = <r_0, z_0>) and <Ap_0, Ap_0>, the sums of P_CG_B's
-// first step.
+// The staged first step on one chunk (warp w: rows 2w, 2w+1): p_0 = -z on
+// the free set (0 elsewhere; z = g, or g / diag under point Jacobi), Ap_0 =
+// Z Z' A Z Z' p_0 (the stencil in the order of the register sweep), r_0 =
+// g_F, w = 0; sums <p_0, Ap_0>, rho_0 = <r_0, z_0> and <Ap_0, M^-1 Ap_0>,
+// the sums of P_CG_B's first step.
+template <bool JAC>
 __device__ __forceinline__ void cgb0_chunk(const DevInst& I, const unsigned char* st, int x0,
                                            int yc, int rows, float* p_out, float* ap_out,
                                            float* r_out, float* w, FF* ff) {
   using G = GeoB0;
+  const float* DI = reinterpret_cast<const float*>(st + G::OFF_DI);
   constexpr int RPW = G::CH / kWarps;
   const float* GS = reinterpret_cast<const float*>(st + G::OFF_G);
   const unsigned* M = reinterpret_cast<const unsigned*>(st + G::OFF_M);
@@ -3463,7 +3472,12 @@ __device__ __forceinline__ void cgb0_chunk(const DevInst& I, const unsigned char
 #pragma unroll
   for (int q = 0; q < RPW + 2; ++q) {
     const int br = r0 + q;
-    const float2 gv = *reinterpret_cast<const float2*>(GS + br * G::BW + G::H + c);
+    float2 gv = *reinterpret_cast<const float2*>(GS + br * G::BW + G::H + c);
+    if (JAC) {
+      const float2 dv = *reinterpret_cast<const float2*>(DI + br * G::BW + G::H + c);
+      gv.x *= dv.x;
+      gv.y *= dv.y;
+    }
     const unsigned wd = M[br * G::MW + ((e0 >> 5) - wx)] >> (e0 & 31);
     pn[q][0] = (wd & 1u) ? -gv.x : 0.0f;
     pn[q][1] = (wd & 2u) ? -gv.y : 0.0f;
@@ -3473,8 +3487,8 @@ __device__ __forceinline__ void cgb0_chunk(const DevInst& I, const unsigned char
     pw[k] = __shfl_up_sync(FULL_MASK, pn[k + 1][1], 1);
     pe[k] = __shfl_down_sync(FULL_MASK, pn[k + 1][0], 1);
     const int br = r0 + k + 1, b = br * G::BW + G::H;
-    if (lane == 0) pw[k] = free_at(br, x0 - 1) ? -GS[b - 1] : 0.0f;
-    if (lane == 31) pe[k] = free_at(br, x0 + 64) ? -GS[b + 64] : 0.0f;
+    if (lane == 0) pw[k] = free_at(br, x0 - 1) ? -GS[b - 1] * (JAC ? DI[b - 1] : 1.0f) : 0.0f;
+    if (lane == 31) pe[k] = free_at(br, x0 + 64) ? -GS[b + 64] * (JAC ? DI[b + 64] : 1.0f) : 0.0f;
   }
   float s_pap = 0.0f, s_rr = 0.0f, s_apap = 0.0f;
 #pragma unroll
@@ -3501,17 +3515,27 @@ __device__ __forceinline__ void cgb0_chunk(const DevInst& I, const unsigned char
     a0 = (wd & 1u) ? a0 : 0.0f;
     a1 = (wd & 2u) ? a1 : 0.0f;
     const long long i = (long long)(yc + ry) * I.px + e0;
+    // r_0 = g_F (under point Jacobi g_F, not z_F) and M^-1 Ap_0
+    float r0v = -pn[q][0], r1v = -pn[q][1], d0 = 1.0f, d1 = 1.0f;
+    if (JAC) {
+      const float2 gv = *reinterpret_cast<const float2*>(GS + (ry + 1) * G::BW + G::H + c);
+      const float2 dv = *reinterpret_cast<const float2*>(DI + (ry + 1) * G::BW + G::H + c);
+      r0v = (wd & 1u) ? gv.x : 0.0f;
+      r1v = (wd & 2u) ? gv.y : 0.0f;
+      d0 = dv.x;
+      d1 = dv.y;
+    }
     st2(p_out, i, v0, v1, pn[q][0], pn[q][1]);
     st2(ap_out, i, v0, v1, a0, a1);
-    st2(r_out, i, v0, v1, -pn[q][0], -pn[q][1]);
+    st2(r_out, i, v0, v1, r0v, r1v);
     st2(w, i, v0, v1, 0.0f, 0.0f);
     // points past nx hold zeros (the boxes are zero-filled there)
     s_pap = fmaf(pn[q][0], a0, s_pap);
     s_pap = fmaf(pn[q][1], a1, s_pap);
-    s_rr = fmaf(pn[q][0], pn[q][0], s_rr);
-    s_rr = fmaf(pn[q][1], pn[q][1], s_rr);
-    s_apap = fmaf(a0, a0, s_apap);
-    s_apap = fmaf(a1, a1, s_apap);
+    s_rr = fmaf(r0v, -pn[q][0], s_rr);
+    s_rr = fmaf(r1v, -pn[q][1], s_rr);
+    s_apap = fmaf(a0, a0 * d0, s_apap);
+    s_apap = fmaf(a1, a1 * d1, s_apap);
   }
   ff_acc(ff[0], s_pap);
   ff_acc(ff[1], s_rr);
@@ -3724,7 +3748,10 @@ __device__ __forceinline__ void run_chunk(const DevInst& I, const Snap& S, bool 
                            I.p64[q], I.Ap64[q], acc);
   } else if (S.pass == P_CG_B && S.first_cg) {
     const int q = S.pcur ^ 1;
-    cgb0_chunk(I, st, c.x0, c.yc, c.rows, I.p32[q], I.Ap32[q], I.r32[q], I.w32, ffs);
+    if (I.opt.precond == PC_JACOBI)
+      cgb0_chunk<true>(I, st, c.x0, c.yc, c.rows, I.p32[q], I.Ap32[q], I.r32[q], I.w32, ffs);
+    else
+      cgb0_chunk<false>(I, st, c.x0, c.yc, c.rows, I.p32[q], I.Ap32[q], I.r32[q], I.w32, ffs);
   } else if (S.pass == P_CG_B) {
     const int q = S.pcur ^ 1;
     if (S.cg32)
