@@ -1356,9 +1356,10 @@ static gpcg_status run_engine(Scratch& sc, int n_live, long long tiles, cudaStre
   CK(cudaMemcpyAsync(&sc.h_pin[2], sc.d_queue + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (sc.h_pin[2] != 0) {
+    // blocks that gave up left without counting their exit: clear the queue,
+    // exit and barrier counters with the error word for the next launch
     const int bits = sc.h_pin[2];
-    const int zero = 0;
-    cudaMemcpy(sc.d_queue + 2, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemset(sc.d_queue, 0, 4 * sizeof(int));
     if (bits & 2) return fail(GPCG_ERR_CUDA, "a pass ran in a kernel without its code");
     return fail(GPCG_ERR_TIMEOUT, "a bounded wait %s gave up",
                 (bits & 4) ? "at the grid barrier" : "for a TMA copy");
