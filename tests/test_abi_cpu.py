@@ -147,6 +147,17 @@ def test_noalloc_size_limit_is_checked_before_any_cuda_call():
         assert b"too large" in L.gpcg_last_error()
 
 
+def test_first_step_mask_box_covers_the_halo():
+    """The staged first CG step reads the free bits of columns x0-4 .. x0+67
+    (its halo) from one box of 8 mask words whose first word is
+    ((x0 >> 5) - 1) rounded down to a multiple of 4: a tensor copy must start
+    on a 16-byte boundary, and the box must hold every halo column."""
+    for x0 in range(0, 1 << 21, 64):  # chunk columns are multiples of 64
+        wx = ((x0 >> 5) - 1) & ~3
+        assert wx % 4 == 0
+        assert wx <= (x0 - 4) >> 5 and (x0 + 67) >> 5 <= wx + 7
+
+
 def test_tuner_table_construction():
     """The tuner keys group sizes by tile count: the fastest measured size
     (at least the floor) owns the range up to the geometric mid-point
