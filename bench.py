@@ -582,7 +582,7 @@ def run_ours(args):
     e2e_run(3)
     torch.cuda.synchronize()
     _barrier(ws)
-    e_steps = max(1, min(args.steps, 10))
+    e_steps = max(1, min(args.steps, 30))
     t0 = time.perf_counter()
     e2e_run(e_steps)
     torch.cuda.synchronize()
